@@ -1,0 +1,56 @@
+"""Plant plausible mistakes in a copy of the oracle and check that the pins
+catch every one (the oracle's own source is never modified).
+
+Each mutation is a dropped term, a wrong sign, a swapped index or operand, or
+min/max confusion; the pin suite must fail on each mutated build.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "sta_oracle.c")
+
+MUTATIONS = {
+    "late_max_becomes_min": ("if (v > best_at) best_at = v;", "if (v < best_at) best_at = v;"),
+    "wire_delay_dropped": ("at[4 * p + q] = at[4 * d + q] + wd[p];", "at[4 * p + q] = at[4 * d + q];"),
+    "unateness_ignored": ("int rfi = nl->arc_unate[OR_MAXA * t + ai] > 0 ? rf : 1 - rf;\n"
+                          "                        size_t tab",
+                          "int rfi = rf;\n                        size_t tab"),
+    "no_slew_degradation": ("sl[4 * p + q] = sqrt(sl[4 * d + q] * sl[4 * d + q] + imp[p] * imp[p]);",
+                            "sl[4 * p + q] = sl[4 * d + q];"),
+    "driver_wire_cap_dropped": ("tcap[0] += 0.5 * cw * len;", ""),
+    "table_axes_transposed": ("double t00 = tab[i * OR_LUT + j], t01 = tab[i * OR_LUT + j + 1];",
+                              "double t00 = tab[j * OR_LUT + i], t01 = tab[i * OR_LUT + j + 1];"),
+    "driver_gradient_sign": ("grad[2 * d] -= gd * sx;", "grad[2 * d] += gd * sx;"),
+    "load_gradient_dropped": ("gload[p] += gD * dDl;", ""),
+    "rat_adds_wire_delay": ("double v = rat[4 * s + q] - wd[s];", "double v = rat[4 * s + q] + wd[s];"),
+    "early_rat_uses_min": ("if (q < 2) { if (v > rat[4 * p + q]) rat[4 * p + q] = v; }",
+                           "if (q < 2) { if (v < rat[4 * p + q]) rat[4 * p + q] = v; }"),
+    "lse_weight_sign": ("double w = exp((ats[2 * i + rfi] + D - ats[2 * p + rf]) / gamma);",
+                        "double w = exp(-(ats[2 * i + rfi] + D - ats[2 * p + rf]) / gamma);"),
+    "second_moment_factor": ("double m = 2.0 * beta[u] - delay[u] * delay[u];",
+                             "double m = beta[u] - delay[u] * delay[u];"),
+    "endpoint_slack_early_sign": ("double se = fmin(at[4 * p] - con[0], at[4 * p + 1] - con[1]);",
+                                  "double se = fmin(con[0] - at[4 * p], con[1] - at[4 * p + 1]);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", str(so), str(mutated), "-lm"])
+    env = dict(os.environ, ORACLE_SO=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_rc_nldm.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_sta.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutation {name} survived the pin suite"
