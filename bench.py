@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Throughput of one differentiable STA step on a ~2.5M-pin netlist.
+
+A step is the whole hot path on one placement: sta_set_positions (device
+positions), sta_forward with LSE arrival times and required times, and
+sta_backward_grad (d(TNS_gamma + WNS_gamma)/d(x, y)).  The workload is the
+superblue4-shaped synthetic netlist (seed 1: ~2.5M pins, 150 levels,
+power-law fanout capped at 2000, eight 20k-sink nets, 3000x3000 um, gamma =
+10 ps).  The metric is pins per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle (the only
+reference this method has) on the machine's host cores on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pins/s fwd+grad at 2.5M pins (% HBM roofline); served p50/p99 latency vs plain"
+GAMMA = 10.0
+WEIGHTS = (1.0, 1.0)
+L2_BYTES = 129 * 2 ** 20
+FLUSH_BYTES = 512 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    import netgen
+    return netgen.superblue_like(args.seed, scale=args.scale)
+
+
+def config_of(w, args, extra=None):
+    st = w.netlist.stats()
+    cfg = {"workload": f"superblue4-shaped synthetic netlist, seed {args.seed}: {st['pins']} pins, "
+                       f"{st['nets']} nets, {st['cells']} cells, depth {w.info['depth']}, "
+                       f"power-law(2.2) fanout <= 2000 plus 8 x {w.info['huge_sinks']}-sink nets, "
+                       f"3000x3000 um, gamma {GAMMA} ps, fwd (AT+LSE+RAT) + gradient",
+           "pins": st["pins"], "nets": st["nets"], "arcs": st["arcs"], "endpoints": st["endpoints"],
+           "levels": int(w.info["depth"]) + 1, "gamma_ps": GAMMA}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes per kernel kind (each array crosses HBM once per producer
+# and once per consumer; tables, level pointers and constants not counted)
+# --------------------------------------------------------------------------
+def algorithmic_bytes(sizes, S):
+    P, N, A = sizes["pins"], sizes["nets"], sizes["arcs"]
+    return {
+        # xy gather: index 4P + positions read 8P + write 8P
+        "positions": 20 * P,
+        # pin xy 8 + cap 4 per net pin, write (delay, impulse) 8 per sink, net_ptr + load 8 per net
+        "net_rc": 12 * (N + S) + 8 * S + 8 * N,
+        # per arc: pin id 4, fanin AT+slew+LSE-AT 40, arc delay write 16; per net: topology 16,
+        # load 4, driver AT+slew+LSE-AT write 40; per sink: (delay, impulse) 8, AT+slew+LSE-AT write 40
+        "fwd_level": 60 * A + 60 * N + 48 * S,
+        # per endpoint: pin 4, constraint 16, AT 16, LSE-AT 8, slack write 8
+        "endpoints": 52 * sizes["endpoints"],
+        # per sink: RAT 16 + delay 8; per net: RAT write 16 + topology 16; per arc: pin 4, arc
+        # delay 16, RAT write 16
+        "rat_level": 24 * S + 32 * N + 36 * A,
+        "seed": 36 * sizes["endpoints"],
+        # per sink: adjoints 16, late slew 8, (delay, impulse) 8, xy 8, cap 4, pin id 4, grad 8;
+        # per net: topology 16, driver slew 8 + LSE-AT 8 + xy 8 + load 4 + grad 8 + pin id 4;
+        # per arc: pin id 4, late slew 8, LSE-AT 8, arc delay 16, adjoint writes 16
+        "adj_level": 56 * S + 56 * N + 52 * A,
+    }
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.idx = gpu_index
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# --------------------------------------------------------------------------
+def time_oracle(w, budget_s=20.0, max_calls=5):
+    import oracle
+    oracle.build()
+    t_calls = []
+    t0 = time.perf_counter()
+    while len(t_calls) < max_calls:
+        t = time.perf_counter()
+        oracle.sta(w.netlist, w.library, w.xy, GAMMA, *WEIGHTS, want={"grad"})
+        t_calls.append(time.perf_counter() - t)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return t_calls
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(args)
+    import oracle
+    oracle.build()
+    P = w.netlist.num_pins
+    sample = w
+    sample_note = "the whole netlist per step"
+    # bound the run: the whole --steps/--warmup run should end within a few minutes
+    t = time.perf_counter()
+    oracle.sta(w.netlist, w.library, w.xy, GAMMA, *WEIGHTS, want={"grad"})
+    t_full = time.perf_counter() - t
+    if t_full * (args.steps + args.warmup) > 200.0:
+        import netgen
+        scale = max(0.002, 200.0 / ((args.steps + args.warmup) * t_full) * args.scale * 0.8)
+        sample = netgen.superblue_like(args.seed, scale=scale)
+        sample_note = (f"a {sample.netlist.num_pins}-pin netlist from the same generator "
+                       f"(scale {scale:.3g}) per step, to bound the run")
+    Ps = sample.netlist.num_pins
+    for _ in range(max(0, args.warmup - 1)):
+        oracle.sta(sample.netlist, sample.library, sample.xy, GAMMA, *WEIGHTS, want={"grad"})
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.sta(sample.netlist, sample.library, sample.xy, GAMMA, *WEIGHTS, want={"grad"})
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    value = Ps * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pins/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, args, {"reference": "FP64 CPU oracle (oracle/sta_oracle.c), "
+                                                       "single thread, as it stands"}),
+            "cpu_baseline": {"value": value, "unit": "pins/s", "cores": 1, "kind": "oracle",
+                             "sample": sample_note},
+            "e2e": {"value": value, "unit": "pins/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import paper_2603_28381_gb300 as sta
+
+    w = workload(args)
+    nl = w.netlist
+    P = nl.num_pins
+    S = int(nl.net_ptr[-1]) - nl.num_nets
+    dev = torch.device("cuda", local)
+    xy = torch.as_tensor(w.xy).to(dev)
+    wts = torch.tensor(WEIGHTS, dtype=torch.float32, device=dev)
+    grad = torch.empty(P, 2, dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(eng, out=grad):
+        eng.set_positions(xy)
+        eng.forward(gamma=GAMMA, lse=True, rat=True)
+        eng.backward_grad(wts, out=out)
+        eng.stream_wait()      # the step ends when the required-time sweep has ended too
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    eng = sta.StaEngine(nl, w.library)
+    for _ in range(args.warmup):
+        step(eng)
+    cur = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = Clocks(local)
+    barrier()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()          # evict L2 (512 MB > 129 MB) between steps, outside the events
+        ev[k][0].record(cur)
+        step(eng)
+        ev[k][1].record(cur)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(ms) / 1e3
+    t_local = torch.tensor([total_s], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    total_s = float(t_local.item())
+    value = world * P * args.steps / total_s
+    _, launches = eng.profile(with_times=False)
+    launches_per_step = int(sum(launches.values()))
+
+    # end to end through the public API with host buffers: pinned positions in,
+    # gradient and summary out, every step
+    e2e = None
+    if not args.no_e2e:
+        xy_h = torch.as_tensor(w.xy).pin_memory()
+        g_h = torch.empty(P, 2, dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            eng.set_positions(xy_h)
+            eng.forward(gamma=GAMMA)
+            eng.backward_grad(WEIGHTS, out=g_h)
+            eng.summary()
+        barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            eng.set_positions(xy_h)
+            eng.forward(gamma=GAMMA)
+            eng.backward_grad(WEIGHTS, out=g_h)
+            eng.summary()
+        barrier()
+        te = time.perf_counter() - t
+        t_e = torch.tensor([te], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * P * args.steps / float(t_e.item()), "unit": "pins/s",
+               "h2d_bytes_per_step": 8 * P, "d2h_bytes_per_step": 8 * P + 64}
+    eng.close()
+
+    # roofline of the dominant kernel kind, from CUDA events around every launch of
+    # the same steps (a handle with StaOptions.profile = 1)
+    prof_eng = sta.StaEngine(nl, w.library, profile=True)
+    for _ in range(2):
+        step(prof_eng)
+    acc = {}
+    nprof = min(args.steps, 10)
+    for _ in range(nprof):
+        flush.zero_()
+        step(prof_eng)
+        msk, launches = prof_eng.profile()
+        for k, v in msk.items():
+            acc[k] = acc.get(k, 0.0) + v / nprof
+    prof_eng.close()
+    sizes = dict(pins=P, nets=prof_eng.sizes["nets"], arcs=prof_eng.sizes["arcs"],
+                 endpoints=prof_eng.sizes["endpoints"])
+    abytes = algorithmic_bytes(sizes, S)
+    dom = max(acc, key=lambda k: acc[k])
+    peak, peak_src = load_peaks()
+    achieved = abytes[dom] / (acc[dom] / 1e3) / 1e9 if acc[dom] > 0 else 0.0
+    traffic = os.environ.get("STA_TRAFFIC_BYTES")  # filled in from an ncu capture, if any
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": None if traffic is None else float(traffic),
+                "launches_per_step": launches[dom],
+                "avg_launch_us": 1e3 * acc[dom] / max(launches[dom], 1),
+                "ms_by_kind": {k: round(v, 4) for k, v in acc.items()},
+                "step_algorithmic_bytes": int(sum(abytes.values())),
+                "step_frac": sum(abytes.values()) / (total_s / args.steps) / 1e9 / peak}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        tc = time_oracle(w, budget_s=20.0, max_calls=4)
+        cpu = {"value": P / (sum(tc) / len(tc)), "unit": "pins/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(tc)} full FP64 oracle calls (forward, required times, gradient) "
+                         f"on the same {P}-pin netlist, single thread"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_of(w, args, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                              "l2": "flushed between steps (512 MB write)",
+                                              "wall_s": round(t_wall, 3)}),
+                "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * sta.h -- C ABI of libsta: levelized, differentiable static timing analysis
+ * on one GB300 GPU (sm_103a).
+ *
+ * The method is Warp-STAR (arXiv 2603.28381): per-net Elmore RC (Eqs. 1-3,
+ * Section 3.1.1), NLDM cell-arc table lookup and level-by-level arrival-time
+ * propagation (Section 3.1.2), backward required-time propagation and slack
+ * (Section 2.1, 3.1.2), and the LogSumExp-smoothed arrival time (Eq. 4,
+ * Section 3.2) whose smoothed TNS/WNS is differentiated with respect to pin
+ * positions (Section 3.2).
+ *
+ * Problem statement (Section 2.1): a netlist of pins, cells and nets forms a
+ * DAG; a net has one driver pin (its first pin, Algorithm 1's netRoot) and any
+ * number of sink pins; a cell has input pins and one output pin and one timing
+ * arc from each input to the output.
+ *
+ * Conventions
+ *   units       ps, fF, Ohm, um; Ohm * fF = 1e-3 ps.
+ *   conditions  4 per pin, index cond = 2*el + rf, el 0 early / 1 late,
+ *               rf 0 rise / 1 fall (Section 3.1.1).
+ *   wires       every net is a star: one wire of Manhattan length d from the
+ *               driver to each sink, resistance r*d, capacitance c*d split half
+ *               at each end.
+ *   pins        every pin has exactly one source of arrival time: it is a
+ *               startpoint (asserted AT/slew), a net sink, or a cell output.
+ *               Endpoints must be net sinks that are not cell inputs.
+ *   ownership   all input arrays are caller-owned host memory and are copied by
+ *               sta_create; the handle owns every device allocation it makes.
+ *   streams     calls taking `stream` (a cudaStream_t, NULL = legacy default)
+ *               are asynchronous on it unless stated otherwise.  A handle is
+ *               not thread-safe; use one handle per host thread.
+ *   errors      every call returns a StaStatus; sta_last_error() gives a
+ *               human-readable message for the calling thread's last failure.
+ *               No call aborts the process.
+ */
+#ifndef STA_H_
+#define STA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STA_ABI_VERSION 1
+#define STA_LUT 7       /* table points per axis */
+#define STA_MAX_ARCS 4  /* arcs (input pins) per cell type */
+
+typedef enum {
+    STA_OK = 0,
+    STA_ERR_INVALID_ARG = 1, /* malformed netlist / library / argument */
+    STA_ERR_NOT_DAG = 2,     /* the timing graph has a cycle */
+    STA_ERR_OOM = 3,         /* device or host allocation failed */
+    STA_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    STA_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired */
+    STA_ERR_STATE = 6        /* call out of order (e.g. gradient before forward) */
+} StaStatus;
+
+/* Netlist in CSR form (Algorithm 1 inputs netlist / netlist_ind).  Host arrays,
+ * read during sta_create / sta_levelize only. */
+typedef struct {
+    int32_t num_pins, num_nets, num_cells;
+    const int32_t *net_ptr;      /* [num_nets+1] pin range of each net in net_pins */
+    const int32_t *net_pins;     /* [net_ptr[num_nets]] first pin of a net = its driver */
+    const int32_t *cell_type;    /* [num_cells] index into the library */
+    const int32_t *cell_in_ptr;  /* [num_cells+1] input-pin range of each cell */
+    const int32_t *cell_in_pins; /* [cell_in_ptr[num_cells]] input k uses arc k of the type */
+    const int32_t *cell_out_pin; /* [num_cells] */
+    const float *pin_cap;        /* [num_pins] pin capacitance, fF */
+    int32_t num_start;
+    const int32_t *start_pins;   /* [num_start] startpoints (primary inputs, clock pins) */
+    const float *start_at;       /* [num_start][4] asserted arrival time, ps */
+    const float *start_slew;     /* [num_start][4] asserted slew, ps */
+    int32_t num_end;
+    const int32_t *end_pins;     /* [num_end] endpoints (primary outputs, flop D pins) */
+    const float *end_rat;        /* [num_end][4] required time: early = hold bound,
+                                    late = setup bound, ps */
+    float r_per_um, c_per_um;    /* wire resistance (Ohm/um) and capacitance (fF/um) */
+} StaNetlistDesc;
+
+/* Liberty-like library (Section 3.1.2): per type and arc, per output
+ * transition, a 7x7 delay and output-slew table indexed [slew][load]. */
+typedef struct {
+    int32_t num_types;
+    const int32_t *type_num_arcs; /* [num_types] number of input pins, 1..4 */
+    const int8_t *arc_unate;      /* [num_types][4] +1 positive unate (out rise <- in rise),
+                                     -1 negative unate (out rise <- in fall) */
+    const float *slew_index;      /* [num_types][7] strictly increasing, ps */
+    const float *load_index;      /* [num_types][7] strictly increasing, fF */
+    const float *delay_tab;       /* [num_types][4][2][7][7] ps, [type][arc][rf_out][slew][load] */
+    const float *slew_tab;        /* [num_types][4][2][7][7] ps */
+} StaLibrary;
+
+typedef struct {
+    int32_t use_graphs;  /* 1 (default): replay each level sweep as a CUDA graph */
+    int32_t profile;     /* 1: bracket every launch with CUDA events (see sta_query_profile) */
+    int32_t reserved[6];
+} StaOptions;
+
+typedef struct StaHandle StaHandle;
+
+/* sta_forward flags */
+#define STA_FWD_LSE 1u  /* also propagate LSE arrival times (needed before sta_backward_grad) */
+#define STA_FWD_RAT 2u  /* also propagate required times and per-pin slack */
+
+/* summary slots written by sta_forward and read by sta_query_summary */
+enum {
+    STA_SUM_WNS_EARLY = 0, STA_SUM_TNS_EARLY = 1, /* hold: slack = AT - RAT_c */
+    STA_SUM_WNS_LATE = 2, STA_SUM_TNS_LATE = 3,   /* setup: slack = RAT_c - AT */
+    STA_SUM_TNS_GAMMA = 4, STA_SUM_WNS_GAMMA = 5, /* smoothed, from LSE arrival times */
+    STA_SUM_LATE_VIOLATIONS = 6, STA_SUM_NUM_ENDPOINTS = 7,
+    STA_SUM_COUNT = 8
+};
+
+/* Validate, levelize and lay out a netlist and library, copy them to the
+ * current CUDA device and allocate every device buffer the analysis needs.
+ * opts may be NULL.  On success *out owns the device memory (free with
+ * sta_destroy).  Errors: INVALID_ARG (malformed input), NOT_DAG, OOM, CUDA. */
+StaStatus sta_create(const StaNetlistDesc *nl, const StaLibrary *lib, const StaOptions *opts,
+                     StaHandle **out);
+
+/* Set pin positions xy [num_pins][2] (um, the netlist's pin order).  xy is a
+ * device pointer if on_device != 0, else host memory (copied through pinned
+ * staging inside this call).  The positions are copied; the caller may reuse
+ * xy when the call's work on `stream` completes. */
+StaStatus sta_set_positions(StaHandle *h, const float *xy, int on_device, void *stream);
+
+/* One forward pass: net RC for every net (Eqs. 1-3), then, level by level,
+ * cell-arc NLDM delays and slews, late max / early min arrival times and wire
+ * propagation to sinks (Section 3.1.2); with STA_FWD_LSE also the LSE arrival
+ * time of Eq. 4 with smoothing gamma (ps, > 0); then endpoint slacks, WNS, TNS
+ * and their smoothed forms; with STA_FWD_RAT required times propagated back
+ * level by level and per-pin slack.  Needs sta_set_positions first (STATE).
+ * The required-time sweep runs on a stream owned by the handle, ordered after
+ * this call's arrival-time pass; `stream` is free for further work (such as
+ * sta_backward_grad) as soon as arrival times exist, and every later call on
+ * the handle waits for the sweep where it needs to. */
+StaStatus sta_forward(StaHandle *h, uint32_t flags, float gamma, void *stream);
+
+/* Gradient of loss = w[0] * TNS_gamma + w[1] * WNS_gamma with respect to the
+ * pin positions, by a hand-written adjoint swept over the levels in reverse
+ * (Section 3.2).  w is a device pointer if w_on_device != 0, else host.  The
+ * result goes to grad_xy [num_pins][2] in the netlist's pin order, a device
+ * pointer if on_device != 0, else host memory (this call then synchronizes
+ * `stream`).  Requires a preceding sta_forward with STA_FWD_LSE (STATE).
+ * The sweep waits for the forward's arrival-time pass only, so it overlaps the
+ * forward's required-time sweep on the GPU (operation fusion, Section 3.2).
+ * Positions, forward state and the gradient buffer are shared by every call on
+ * the handle: a later sta_set_positions / sta_forward waits for this sweep. */
+StaStatus sta_backward_grad(StaHandle *h, const float *w, int w_on_device, float *grad_xy,
+                            int on_device, void *stream);
+
+/* Make `stream` wait (on the GPU, without blocking the host) for all work the
+ * handle has queued so far, including the required-time sweep that runs on
+ * the handle's own stream. */
+StaStatus sta_stream_wait(StaHandle *h, void *stream);
+
+/* Copy the STA_SUM_COUNT summary values (double) to out, a device pointer if
+ * on_device != 0 (asynchronous), else host (synchronizes `stream`). */
+StaStatus sta_query_summary(StaHandle *h, double *out, int on_device, void *stream);
+
+/* Per-pin results in the netlist's pin order (any output may be NULL):
+ * at, slew, rat [num_pins][4]; ats [num_pins][2] (late rise/fall LSE arrival);
+ * slack [num_pins][2] (early, late; minimum over rise/fall).  Device pointers if
+ * on_device != 0 (asynchronous), else host (synchronizes `stream`). */
+StaStatus sta_query_pins(StaHandle *h, float *at, float *slew, float *rat, float *ats,
+                         float *slack, int on_device, void *stream);
+
+/* Endpoint slacks [num_end][2] (early, late), in the order of end_pins. */
+StaStatus sta_query_endpoints(StaHandle *h, float *slack, int on_device, void *stream);
+
+/* Host-only levelization (no device use): the level of every net, computed by
+ * a breadth-first (Kahn) sweep over nets: level 0 if the driver is not a cell
+ * output, else 1 + the largest level among the nets feeding the driver cell's
+ * inputs (Section 2.1 stage 2).  net_level [num_nets]; *num_levels = max + 1.
+ * If net_order != NULL it receives the original net ids in processing order
+ * (level, then nets of <= 32 pins before larger ones, then original id), and
+ * if pin_order != NULL [net_ptr[num_nets]] the original pin ids in device
+ * layout order (each net's driver, then its sinks by ascending id). */
+StaStatus sta_levelize(const StaNetlistDesc *nl, int32_t *net_level, int32_t *num_levels,
+                       int32_t *net_order, int32_t *pin_order);
+
+/* Sizes of a created handle: [0] pins, [1] nets (including one internal
+ * net per cell output that drives no net), [2] levels, [3] arcs, [4] endpoints,
+ * [5] warp tasks, [6] block tasks, [7] device bytes held. */
+StaStatus sta_query_sizes(const StaHandle *h, int64_t *out8);
+
+/* Kernel kinds reported by sta_query_profile. */
+enum {
+    STA_PROF_POSITIONS = 0,  /* gather of positions into device order */
+    STA_PROF_NET_RC = 1,     /* Eqs. 1-3 over every net */
+    STA_PROF_FWD_LEVEL = 2,  /* one forward level (cell arcs, AT/slew/LSE, wire) */
+    STA_PROF_ENDPOINTS = 3,  /* endpoint slack / WNS / TNS reduction (two launches) */
+    STA_PROF_RAT_LEVEL = 4,  /* one required-time level */
+    STA_PROF_SEED = 5,       /* adjoint seeds at the endpoints (with the weights) */
+    STA_PROF_ADJ_LEVEL = 6,  /* one adjoint level */
+    STA_PROF_KINDS = 7
+};
+
+/* Per-kind launch counts of one set_positions + forward(LSE|RAT) +
+ * backward_grad step (always), and, for a handle created with
+ * StaOptions.profile = 1, the summed CUDA-event durations (ms) of the most
+ * recent execution of each kind's launches, measured on the stream each kernel
+ * ran on.  Synchronizes the device.  ms and launches have STA_PROF_KINDS
+ * entries; ms may be NULL. */
+StaStatus sta_query_profile(StaHandle *h, double *ms, int32_t *launches);
+
+/* Release every resource of the handle (NULL is a no-op). */
+void sta_destroy(StaHandle *h);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *sta_last_error(void);
+
+/* STA_ABI_VERSION of the loaded library. */
+int sta_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STA_H_ */

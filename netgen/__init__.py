@@ -402,14 +402,15 @@ def superblue_like(seed: int = 1, scale: float = 1.0, depth: int = 150,
                    huge: bool = True) -> Workload:
     """~2.5M pins (superblue4-sized at scale 1), 150 levels, 64 types with
     1-4 inputs, power-law(2.2) fanout capped at 2000, 8 primary-input nets with
-    20k sinks each, 3000x3000 um."""
+    20k sinks each (20k * scale below scale 1), 3000x3000 um."""
     n_comb = max(depth, int(round(613_000 * scale)))
+    huge_sinks = int(round(20_000 * min(scale, 1.0)))
     return make_netlist(seed, n_comb=n_comb, arcs_per_type=[1, 2, 3, 4] * 16,
                         n_ff=max(1, n_comb // 10), n_pi=max(16, n_comb // 20),
                         n_po=max(1, n_comb // 20), depth=depth,
                         fanout=("power", 2.2, 2000), box=3000.0,
-                        n_huge=(8 if huge else 0),
-                        huge_sinks=(20_000 if huge else 0),
+                        n_huge=(8 if huge and huge_sinks > 0 else 0),
+                        huge_sinks=(huge_sinks if huge else 0),
                         name=f"superblue_like_x{scale:g}_d{depth}")
 
 

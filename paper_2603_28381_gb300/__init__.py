@@ -1,0 +1,175 @@
+"""GB300-native levelized, differentiable static timing analysis (Warp-STAR, arXiv 2603.28381).
+
+The whole analysis runs in libsta's sm_103a kernels (``csrc/``), behind the C
+ABI of ``include/sta.h``; ``_sta`` binds it with ctypes under the same names.
+PyTorch provides device memory, streams and autograd plumbing only.
+
+    eng = StaEngine(netlist, library)        # sta_create: validate, levelize, upload
+    eng.set_positions(xy)                    # sta_set_positions
+    eng.forward(gamma=10.0)                  # sta_forward: RC, AT/slew, LSE-AT, slack, RAT
+    g = eng.backward_grad((1.0, 0.0))        # sta_backward_grad: d(TNS_gamma)/d(x, y)
+    tns_g, wns_g = timing_loss(xy_tensor, eng, 10.0)   # autograd wrapper
+"""
+from __future__ import annotations
+
+from typing import Dict, Optional, Tuple, Union
+
+import numpy as np
+
+from . import _sta
+from ._sta import (STA_FWD_LSE, STA_FWD_RAT, SUMMARY_KEYS, StaError, sta_abi_version,
+                   sta_last_error, sta_levelize)
+
+__all__ = ["StaEngine", "timing_loss", "TimingLoss", "StaError", "sta_levelize", "STA_FWD_LSE",
+           "STA_FWD_RAT", "SUMMARY_KEYS", "sta_abi_version", "sta_last_error"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class StaEngine:
+    """One netlist resident on the current CUDA device."""
+
+    def __init__(self, netlist, library, use_graphs: bool = True, profile: bool = False):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("StaEngine needs a CUDA device (there is no CPU path)")
+        torch.cuda.init()
+        self.num_pins = int(netlist.num_pins)
+        self.num_end = int(netlist.end_pins.shape[0])
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.h = _sta.sta_create(netlist, library, use_graphs, profile)
+        self.sizes = _sta.sta_query_sizes(self.h)
+        self.gamma = None
+
+    # -- lifetime --
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            _sta.sta_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls --
+    def profile(self, with_times: bool = True):
+        """(ms by kernel kind, launches by kind) of the latest step (sta_query_profile)."""
+        return _sta.sta_query_profile(self.h, with_times)
+
+    def set_positions(self, xy, stream=None) -> None:
+        torch = _torch()
+        if isinstance(xy, torch.Tensor):
+            t = xy.detach()
+            assert t.dtype == torch.float32 and t.is_contiguous() and t.numel() == 2 * self.num_pins
+            _sta.sta_set_positions(self.h, t.data_ptr(), 1 if t.is_cuda else 0, _stream_ptr(stream))
+            self._xy_keep = t
+        else:
+            a = np.ascontiguousarray(np.asarray(xy, np.float32)).reshape(-1)
+            assert a.size == 2 * self.num_pins
+            _sta.sta_set_positions(self.h, a.ctypes.data, 0, _stream_ptr(stream))
+
+    def forward(self, gamma: float = 10.0, lse: bool = True, rat: bool = True, stream=None) -> None:
+        flags = (STA_FWD_LSE if lse else 0) | (STA_FWD_RAT if rat else 0)
+        _sta.sta_forward(self.h, flags, float(gamma), _stream_ptr(stream))
+        self.gamma = gamma
+
+    def backward_grad(self, w: Union[Tuple[float, float], "object"] = (1.0, 0.0), out=None,
+                      stream=None):
+        """d(w[0] TNS_gamma + w[1] WNS_gamma)/d(x, y) as a [P,2] float32 CUDA tensor."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.num_pins, 2, dtype=torch.float32, device=self.device)
+        assert out.dtype == torch.float32 and out.is_contiguous() and out.numel() == 2 * self.num_pins
+        on_dev = 1 if out.is_cuda else 0
+        if isinstance(w, torch.Tensor) and w.is_cuda:
+            wt = w.detach().to(torch.float32).contiguous()
+            _sta.sta_backward_grad(self.h, wt.data_ptr(), 1, out.data_ptr(), on_dev, _stream_ptr(stream))
+            self._w_keep = wt
+        else:
+            wa = np.asarray(w, np.float32)
+            _sta.sta_backward_grad(self.h, wa.ctypes.data, 0, out.data_ptr(), on_dev, _stream_ptr(stream))
+        return out
+
+    def stream_wait(self, stream=None) -> None:
+        """Order `stream` after all queued work of the handle (sta_stream_wait)."""
+        _sta.sta_stream_wait(self.h, _stream_ptr(stream))
+
+    def summary(self, stream=None) -> Dict[str, float]:
+        out = np.zeros(8, np.float64)
+        _sta.sta_query_summary(self.h, out.ctypes.data, 0, _stream_ptr(stream))
+        return dict(zip(SUMMARY_KEYS, out.tolist()))
+
+    def summary_device(self, out, stream=None):
+        _sta.sta_query_summary(self.h, out.data_ptr(), 1, _stream_ptr(stream))
+        return out
+
+    def pins(self, at=True, slew=True, rat=True, ats=True, slack=True, stream=None) -> Dict[str, np.ndarray]:
+        P = self.num_pins
+        res = {}
+        bufs = {}
+        for k, want, width in (("at", at, 4), ("slew", slew, 4), ("rat", rat, 4), ("ats", ats, 2),
+                               ("slack", slack, 2)):
+            if want:
+                bufs[k] = np.zeros((P, width), np.float32)
+        ptr = lambda k: bufs[k].ctypes.data if k in bufs else None
+        _sta.sta_query_pins(self.h, ptr("at"), ptr("slew"), ptr("rat"), ptr("ats"), ptr("slack"), 0,
+                            _stream_ptr(stream))
+        res.update(bufs)
+        return res
+
+    def endpoints(self, stream=None) -> np.ndarray:
+        out = np.zeros((max(self.num_end, 1), 2), np.float32)
+        _sta.sta_query_endpoints(self.h, out.ctypes.data, 0, _stream_ptr(stream))
+        return out[:self.num_end]
+
+
+class TimingLoss:
+    """torch.autograd.Function: xy [P,2] -> (TNS_gamma, WNS_gamma).
+
+    The forward leaves the required-time sweep running on libsta's own stream,
+    so the adjoint sweep queued by the backward on the caller's stream overlaps
+    it on the GPU (the paper's operation fusion, Section 3.2)."""
+
+    _fn = None
+
+    @classmethod
+    def fn(cls):
+        if cls._fn is None:
+            torch = _torch()
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, xy, engine, gamma):
+                    engine.set_positions(xy)
+                    engine.forward(gamma=gamma, lse=True, rat=True)
+                    summ = torch.empty(8, dtype=torch.float64, device=xy.device)
+                    engine.summary_device(summ)
+                    ctx.engine = engine
+                    return summ[4].to(torch.float32), summ[5].to(torch.float32)
+
+                @staticmethod
+                def backward(ctx, g_tns, g_wns):
+                    eng = ctx.engine
+                    w = torch.stack([g_tns.reshape(()), g_wns.reshape(())]).to(torch.float32)
+                    grad = eng.backward_grad(w)
+                    return grad, None, None
+
+            cls._fn = _F
+        return cls._fn
+
+
+def timing_loss(xy, engine: StaEngine, gamma: float = 10.0):
+    """(TNS_gamma, WNS_gamma) of positions ``xy`` (a CUDA tensor), differentiable."""
+    return TimingLoss.fn().apply(xy, engine, gamma)

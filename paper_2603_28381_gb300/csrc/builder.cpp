@@ -1,0 +1,422 @@
+// builder.cpp -- host-side validation, levelization and device layout.
+//
+// Levelization follows the paper's stage (2) (Section 2.1): nets are grouped
+// into levels so that the pins of level i only need arrival times of levels
+// < i; it is computed once per netlist (Section 2.1, "needs to be computed only
+// once").  Here it is a Kahn breadth-first sweep over the net graph: level 0
+// for a net whose driver is not a cell output, else 1 + the largest level of
+// the nets feeding the driver cell's inputs.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <numeric>
+
+#include "sta_internal.h"
+
+namespace sta {
+namespace {
+
+struct Roles {
+    std::vector<int32_t> sink_net, drv_net, out_cell, in_cell, start_of, end_of;
+};
+
+bool fail(std::string& err, const std::string& msg) {
+    err = msg;
+    return false;
+}
+
+// Structural checks on the description; fills the role of every pin.
+StaStatus check_netlist(const StaNetlistDesc& nl, const StaLibrary* lib, Roles& r, std::string& err) {
+    const int32_t P = nl.num_pins, N = nl.num_nets, C = nl.num_cells;
+    if (P < 0 || N < 0 || C < 0 || nl.num_start < 0 || nl.num_end < 0)
+        return err = "negative size", STA_ERR_INVALID_ARG;
+    if ((N > 0 && (!nl.net_ptr || !nl.net_pins)) || (C > 0 && (!nl.cell_type || !nl.cell_in_ptr ||
+        !nl.cell_in_pins || !nl.cell_out_pin)) || (P > 0 && !nl.pin_cap) ||
+        (nl.num_start > 0 && (!nl.start_pins || !nl.start_at || !nl.start_slew)) ||
+        (nl.num_end > 0 && (!nl.end_pins || !nl.end_rat)))
+        return err = "null array with non-zero size", STA_ERR_INVALID_ARG;
+    if (!(std::isfinite(nl.r_per_um) && nl.r_per_um >= 0 && std::isfinite(nl.c_per_um) && nl.c_per_um >= 0))
+        return err = "r_per_um / c_per_um must be finite and >= 0", STA_ERR_INVALID_ARG;
+    r.sink_net.assign(P, -1);
+    r.drv_net.assign(P, -1);
+    r.out_cell.assign(P, -1);
+    r.in_cell.assign(P, -1);
+    r.start_of.assign(P, -1);
+    r.end_of.assign(P, -1);
+    if (N > 0 && nl.net_ptr[0] != 0) return err = "net_ptr[0] must be 0", STA_ERR_INVALID_ARG;
+    for (int32_t n = 0; n < N; ++n) {
+        const int32_t b = nl.net_ptr[n], e = nl.net_ptr[n + 1];
+        if (e <= b) return err = "net " + std::to_string(n) + " has no driver", STA_ERR_INVALID_ARG;
+        for (int32_t k = b; k < e; ++k) {
+            const int32_t p = nl.net_pins[k];
+            if (p < 0 || p >= P) return err = "net pin out of range", STA_ERR_INVALID_ARG;
+            if (k == b) {
+                if (r.drv_net[p] >= 0 || r.sink_net[p] >= 0)
+                    return err = "pin " + std::to_string(p) + " on two nets", STA_ERR_INVALID_ARG;
+                r.drv_net[p] = n;
+            } else {
+                if (r.sink_net[p] >= 0 || r.drv_net[p] >= 0)
+                    return err = "pin " + std::to_string(p) + " on two nets", STA_ERR_INVALID_ARG;
+                r.sink_net[p] = n;
+            }
+        }
+    }
+    for (int32_t c = 0; c < C; ++c) {
+        const int32_t t = nl.cell_type[c], o = nl.cell_out_pin[c];
+        const int32_t k = nl.cell_in_ptr[c + 1] - nl.cell_in_ptr[c];
+        if (nl.cell_in_ptr[0] != 0 || k < 1 || k > STA_MAX_ARCS)
+            return err = "cell " + std::to_string(c) + " must have 1..4 inputs", STA_ERR_INVALID_ARG;
+        if (lib && (t < 0 || t >= lib->num_types || lib->type_num_arcs[t] != k))
+            return err = "cell " + std::to_string(c) + " type / input count mismatch", STA_ERR_INVALID_ARG;
+        if (o < 0 || o >= P || r.out_cell[o] >= 0)
+            return err = "bad or repeated cell output pin", STA_ERR_INVALID_ARG;
+        r.out_cell[o] = c;
+        for (int32_t a = nl.cell_in_ptr[c]; a < nl.cell_in_ptr[c + 1]; ++a) {
+            const int32_t p = nl.cell_in_pins[a];
+            if (p < 0 || p >= P || r.in_cell[p] >= 0)
+                return err = "bad or repeated cell input pin", STA_ERR_INVALID_ARG;
+            r.in_cell[p] = c;
+        }
+    }
+    for (int32_t s = 0; s < nl.num_start; ++s) {
+        const int32_t p = nl.start_pins[s];
+        if (p < 0 || p >= P || r.start_of[p] >= 0) return err = "bad or repeated startpoint", STA_ERR_INVALID_ARG;
+        for (int q = 0; q < 4; ++q)
+            if (!std::isfinite(nl.start_at[4 * s + q]) || !std::isfinite(nl.start_slew[4 * s + q]) ||
+                nl.start_slew[4 * s + q] < 0)
+                return err = "startpoint AT/slew must be finite, slew >= 0", STA_ERR_INVALID_ARG;
+        r.start_of[p] = s;
+    }
+    for (int32_t e = 0; e < nl.num_end; ++e) {
+        const int32_t p = nl.end_pins[e];
+        if (p < 0 || p >= P || r.end_of[p] >= 0) return err = "bad or repeated endpoint", STA_ERR_INVALID_ARG;
+        if (r.sink_net[p] < 0 || r.in_cell[p] >= 0)
+            return err = "endpoint " + std::to_string(p) + " must be a net sink that is not a cell input",
+                   STA_ERR_INVALID_ARG;
+        for (int q = 0; q < 4; ++q)
+            if (!std::isfinite(nl.end_rat[4 * e + q])) return err = "endpoint RAT must be finite", STA_ERR_INVALID_ARG;
+        r.end_of[p] = e;
+    }
+    for (int32_t p = 0; p < P; ++p) {
+        const int nsrc = (r.start_of[p] >= 0) + (r.sink_net[p] >= 0) + (r.out_cell[p] >= 0);
+        if (nsrc != 1)
+            return err = "pin " + std::to_string(p) + " must have exactly one arrival source "
+                         "(startpoint, net sink or cell output)", STA_ERR_INVALID_ARG;
+        if (r.drv_net[p] >= 0 && r.in_cell[p] >= 0)
+            return err = "pin " + std::to_string(p) + " drives a net and is a cell input", STA_ERR_INVALID_ARG;
+        if (!(std::isfinite(nl.pin_cap[p]) && nl.pin_cap[p] >= 0))
+            return err = "pin_cap must be finite and >= 0", STA_ERR_INVALID_ARG;
+    }
+    return STA_OK;
+}
+
+StaStatus check_library(const StaLibrary& lib, std::string& err) {
+    if (lib.num_types < 1 || !lib.type_num_arcs || !lib.arc_unate || !lib.slew_index || !lib.load_index ||
+        !lib.delay_tab || !lib.slew_tab)
+        return err = "library arrays missing", STA_ERR_INVALID_ARG;
+    for (int32_t t = 0; t < lib.num_types; ++t) {
+        if (lib.type_num_arcs[t] < 1 || lib.type_num_arcs[t] > STA_MAX_ARCS)
+            return err = "type_num_arcs must be 1..4", STA_ERR_INVALID_ARG;
+        for (int a = 0; a < STA_MAX_ARCS; ++a)
+            if (lib.arc_unate[t * STA_MAX_ARCS + a] != 1 && lib.arc_unate[t * STA_MAX_ARCS + a] != -1)
+                return err = "arc_unate must be +1 or -1", STA_ERR_INVALID_ARG;
+        for (int k = 0; k < STA_LUT; ++k) {
+            const float s = lib.slew_index[t * STA_LUT + k], l = lib.load_index[t * STA_LUT + k];
+            if (!std::isfinite(s) || !std::isfinite(l)) return err = "non-finite table index", STA_ERR_INVALID_ARG;
+            if (k > 0 && !(s > lib.slew_index[t * STA_LUT + k - 1] && l > lib.load_index[t * STA_LUT + k - 1]))
+                return err = "table indices must be strictly increasing", STA_ERR_INVALID_ARG;
+        }
+    }
+    const size_t ntab = (size_t)lib.num_types * STA_MAX_ARCS * 2 * STA_LUT * STA_LUT;
+    for (size_t i = 0; i < ntab; ++i)
+        if (!std::isfinite(lib.delay_tab[i]) || !std::isfinite(lib.slew_tab[i]))
+            return err = "non-finite table value", STA_ERR_INVALID_ARG;
+    return STA_OK;
+}
+
+// Kahn sweep over "level nodes": description nets 0..N-1 then one node per
+// dangling cell.  level = 0 without fanin nets, else 1 + max fanin level.
+StaStatus kahn_levels(const StaNetlistDesc& nl, const Roles& r, const std::vector<int32_t>& dangling,
+                      std::vector<int32_t>& level, int32_t& num_levels, std::string& err) {
+    const int32_t N = nl.num_nets, D = (int32_t)dangling.size(), V = N + D;
+    // fanin nets of each node
+    auto node_cell = [&](int32_t v) -> int32_t {
+        return v < N ? r.out_cell[nl.net_pins[nl.net_ptr[v]]] : dangling[v - N];
+    };
+    std::vector<int32_t> indeg(V, 0), fo_cnt(N + 1, 0);
+    for (int32_t v = 0; v < V; ++v) {
+        const int32_t c = node_cell(v);
+        if (c < 0) continue;
+        for (int32_t a = nl.cell_in_ptr[c]; a < nl.cell_in_ptr[c + 1]; ++a) {
+            const int32_t m = r.sink_net[nl.cell_in_pins[a]];
+            if (m >= 0) { ++indeg[v]; ++fo_cnt[m + 1]; }
+        }
+    }
+    for (int32_t m = 0; m < N; ++m) fo_cnt[m + 1] += fo_cnt[m];
+    std::vector<int32_t> fo(fo_cnt[N]), fill(fo_cnt.begin(), fo_cnt.end() - 1);
+    for (int32_t v = 0; v < V; ++v) {
+        const int32_t c = node_cell(v);
+        if (c < 0) continue;
+        for (int32_t a = nl.cell_in_ptr[c]; a < nl.cell_in_ptr[c + 1]; ++a) {
+            const int32_t m = r.sink_net[nl.cell_in_pins[a]];
+            if (m >= 0) fo[fill[m]++] = v;
+        }
+    }
+    level.assign(V, 0);
+    std::vector<int32_t> queue;
+    queue.reserve(V);
+    for (int32_t v = 0; v < V; ++v) if (indeg[v] == 0) queue.push_back(v);
+    size_t head = 0;
+    int32_t maxl = -1;
+    while (head < queue.size()) {
+        const int32_t m = queue[head++];
+        maxl = std::max(maxl, level[m]);
+        if (m >= N) continue;
+        for (int32_t k = fo_cnt[m]; k < fo_cnt[m + 1]; ++k) {
+            const int32_t v = fo[k];
+            level[v] = std::max(level[v], level[m] + 1);
+            if (--indeg[v] == 0) queue.push_back(v);
+        }
+    }
+    if ((int32_t)queue.size() != V) return err = "timing graph has a cycle", STA_ERR_NOT_DAG;
+    num_levels = maxl + 1;
+    return STA_OK;
+}
+
+std::vector<int32_t> dangling_cells(const StaNetlistDesc& nl, const Roles& r) {
+    std::vector<int32_t> d;
+    for (int32_t c = 0; c < nl.num_cells; ++c)
+        if (r.drv_net[nl.cell_out_pin[c]] < 0) d.push_back(c);
+    return d;
+}
+
+}  // namespace
+
+StaStatus levelize(const StaNetlistDesc& nl, const StaLibrary* lib, std::vector<int32_t>& net_level,
+                   std::vector<int32_t>* dangling_out, std::vector<int32_t>* dangling_level,
+                   int32_t& num_levels, std::string& err) {
+    Roles r;
+    StaStatus st = check_netlist(nl, lib, r, err);
+    if (st != STA_OK) return st;
+    std::vector<int32_t> dang = dangling_cells(nl, r), lv;
+    st = kahn_levels(nl, r, dang, lv, num_levels, err);
+    if (st != STA_OK) return st;
+    net_level.assign(lv.begin(), lv.begin() + nl.num_nets);
+    if (dangling_out) *dangling_out = dang;
+    if (dangling_level) dangling_level->assign(lv.begin() + nl.num_nets, lv.end());
+    return STA_OK;
+}
+
+namespace {
+
+// Internal net order: (level, size class, id); ids >= num_nets are dangling cells.
+struct NetOrder {
+    std::vector<int32_t> order;   // internal -> level-node id
+    std::vector<int32_t> level;   // per level-node
+    int32_t L = 0;
+};
+
+StaStatus make_order(const StaNetlistDesc& nl, const Roles& r, const std::vector<int32_t>& dang,
+                     NetOrder& no, std::string& err) {
+    StaStatus st = kahn_levels(nl, r, dang, no.level, no.L, err);
+    if (st != STA_OK) return st;
+    const int32_t N = nl.num_nets, V = N + (int32_t)dang.size();
+    std::vector<int64_t> key(V);
+    for (int32_t v = 0; v < V; ++v) {
+        const int32_t size = v < N ? nl.net_ptr[v + 1] - nl.net_ptr[v] : 1;
+        key[v] = ((int64_t)no.level[v] << 33) | ((int64_t)(size > kWarpPins) << 32) | (int64_t)v;
+    }
+    no.order.resize(V);
+    std::iota(no.order.begin(), no.order.end(), 0);
+    std::sort(no.order.begin(), no.order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    return STA_OK;
+}
+
+}  // namespace
+
+StaStatus ordering(const StaNetlistDesc& nl, std::vector<int32_t>& net_level, int32_t& num_levels,
+                   std::vector<int32_t>& net_order, std::vector<int32_t>& pin_order, std::string& err) {
+    Roles r;
+    StaStatus st = check_netlist(nl, nullptr, r, err);
+    if (st != STA_OK) return st;
+    std::vector<int32_t> dang = dangling_cells(nl, r);
+    NetOrder no;
+    st = make_order(nl, r, dang, no, err);
+    if (st != STA_OK) return st;
+    num_levels = no.L;
+    net_level.assign(no.level.begin(), no.level.begin() + nl.num_nets);
+    net_order.clear();
+    pin_order.clear();
+    for (int32_t v : no.order) {
+        if (v >= nl.num_nets) continue;
+        net_order.push_back(v);
+        const int32_t b = nl.net_ptr[v], e = nl.net_ptr[v + 1];
+        pin_order.push_back(nl.net_pins[b]);
+        std::vector<int32_t> s(nl.net_pins + b + 1, nl.net_pins + e);
+        std::sort(s.begin(), s.end());
+        pin_order.insert(pin_order.end(), s.begin(), s.end());
+    }
+    return STA_OK;
+}
+
+StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& out, std::string& err) {
+    StaStatus st = check_library(lib, err);
+    if (st != STA_OK) return st;
+    Roles r;
+    st = check_netlist(nl, &lib, r, err);
+    if (st != STA_OK) return st;
+    std::vector<int32_t> dang = dangling_cells(nl, r);
+    NetOrder no;
+    st = make_order(nl, r, dang, no, err);
+    if (st != STA_OK) return st;
+
+    const int32_t P = nl.num_pins, Nreal = nl.num_nets, V = (int32_t)no.order.size();
+    Layout& o = out;
+    o.P = P;
+    o.Nreal = Nreal;
+    o.N = V;
+    o.L = no.L;
+    o.E = nl.num_end;
+    o.T = lib.num_types;
+    o.r_per_um = nl.r_per_um;
+    o.c_per_um = nl.c_per_um;
+
+    // ---- pins ----
+    std::vector<int32_t> internal(P, -1);
+    o.pin_orig.clear();
+    o.pin_orig.reserve(P);
+    o.net_ptr.assign(V + 1, 0);
+    o.net_drv.assign(V, -1);
+    o.net_arc_ptr.assign(V + 1, 0);
+    o.arc_pin.clear();
+    std::vector<int32_t> net_cell(V, -1);
+    for (int32_t i = 0; i < V; ++i) {
+        const int32_t v = no.order[i];
+        o.net_ptr[i] = (int32_t)o.pin_orig.size();
+        if (v < Nreal) {
+            const int32_t b = nl.net_ptr[v], e = nl.net_ptr[v + 1];
+            o.pin_orig.push_back(nl.net_pins[b]);
+            std::vector<int32_t> s(nl.net_pins + b + 1, nl.net_pins + e);
+            std::sort(s.begin(), s.end());
+            o.pin_orig.insert(o.pin_orig.end(), s.begin(), s.end());
+            net_cell[i] = r.out_cell[nl.net_pins[b]];
+        } else {
+            net_cell[i] = dang[v - Nreal];
+            o.pin_orig.push_back(nl.cell_out_pin[net_cell[i]]);
+        }
+    }
+    o.net_ptr[V] = (int32_t)o.pin_orig.size();
+    o.Pnet = o.net_ptr[V];
+    for (int32_t p = 0; p < P; ++p)
+        if (r.sink_net[p] < 0 && r.drv_net[p] < 0 && r.out_cell[p] < 0) o.pin_orig.push_back(p);
+    if ((int32_t)o.pin_orig.size() != P) return err = "internal: pin layout size mismatch", STA_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < P; ++i) internal[o.pin_orig[i]] = i;
+
+    // ---- arcs ----
+    for (int32_t i = 0; i < V; ++i) {
+        o.net_arc_ptr[i] = (int32_t)o.arc_pin.size();
+        const int32_t c = net_cell[i];
+        if (c >= 0) {
+            o.net_drv[i] = nl.cell_type[c];
+            for (int32_t a = nl.cell_in_ptr[c]; a < nl.cell_in_ptr[c + 1]; ++a)
+                o.arc_pin.push_back(internal[nl.cell_in_pins[a]]);
+        }
+    }
+    o.net_arc_ptr[V] = (int32_t)o.arc_pin.size();
+    o.A = o.net_arc_ptr[V];
+
+    o.pin_cap.resize(P);
+    for (int32_t i = 0; i < P; ++i) o.pin_cap[i] = nl.pin_cap[o.pin_orig[i]];
+
+    // ---- tasks per level ----
+    o.lvl_wtask.assign(o.L + 1, 0);
+    o.lvl_ctask.assign(o.L + 1, 0);
+    o.wtask.clear();
+    o.ctask.clear();
+    int32_t i = 0;
+    for (int32_t l = 0; l < o.L; ++l) {
+        o.lvl_wtask[l] = (int32_t)(o.wtask.size() / 2);
+        o.lvl_ctask[l] = (int32_t)o.ctask.size();
+        while (i < V && no.level[no.order[i]] == l) {
+            const int32_t size = o.net_ptr[i + 1] - o.net_ptr[i];
+            if (size > kWarpPins) {
+                o.ctask.push_back(i);
+                ++i;
+                continue;
+            }
+            // greedy pack of consecutive small nets of this level
+            int32_t n0 = i, pins = 0, cnt = 0;
+            while (i < V && no.level[no.order[i]] == l && cnt < kWarpNets) {
+                const int32_t sz = o.net_ptr[i + 1] - o.net_ptr[i];
+                if (sz > kWarpPins || pins + sz > kWarpPins) break;
+                pins += sz;
+                ++cnt;
+                ++i;
+            }
+            o.wtask.push_back(n0);
+            o.wtask.push_back(cnt);
+        }
+    }
+    if (i != V) return err = "internal: task layout did not cover every net", STA_ERR_INVALID_ARG;
+    o.lvl_wtask[o.L] = (int32_t)(o.wtask.size() / 2);
+    o.lvl_ctask[o.L] = (int32_t)o.ctask.size();
+
+    // ---- constant per-pin state ----
+    const float inf = std::numeric_limits<float>::infinity();
+    o.at0.assign((size_t)P * 4, 0.f);
+    o.slew0.assign((size_t)P * 4, 0.f);
+    o.rat0.resize((size_t)P * 4);
+    for (int32_t p = 0; p < P; ++p) {
+        o.rat0[4 * p + 0] = o.rat0[4 * p + 1] = -inf;
+        o.rat0[4 * p + 2] = o.rat0[4 * p + 3] = inf;
+    }
+    for (int32_t s = 0; s < nl.num_start; ++s) {
+        const int32_t p = internal[nl.start_pins[s]];
+        for (int q = 0; q < 4; ++q) {
+            o.at0[4 * (size_t)p + q] = nl.start_at[4 * s + q];
+            o.slew0[4 * (size_t)p + q] = nl.start_slew[4 * s + q];
+        }
+    }
+    o.ep_pin.resize(o.E);
+    o.ep_rat.resize((size_t)o.E * 4);
+    for (int32_t e = 0; e < o.E; ++e) {
+        const int32_t p = internal[nl.end_pins[e]];
+        o.ep_pin[e] = p;
+        for (int q = 0; q < 4; ++q) {
+            o.ep_rat[4 * (size_t)e + q] = nl.end_rat[4 * e + q];
+            o.rat0[4 * (size_t)p + q] = nl.end_rat[4 * e + q];
+        }
+    }
+
+    // ---- library ----
+    const int32_t T = lib.num_types;
+    o.lib_idx.assign((size_t)T * kLibStride, 0.f);
+    o.lib_inv.assign((size_t)T * kLibStride, 0.f);
+    o.lib_unate.assign(T, 0);
+    o.lib_tab.resize((size_t)T * STA_MAX_ARCS * 2 * kTabPerArcRf);
+    for (int32_t t = 0; t < T; ++t) {
+        for (int k = 0; k < STA_LUT; ++k) {
+            o.lib_idx[t * kLibStride + k] = lib.slew_index[t * STA_LUT + k];
+            o.lib_idx[t * kLibStride + 8 + k] = lib.load_index[t * STA_LUT + k];
+        }
+        for (int k = 0; k + 1 < STA_LUT; ++k) {
+            o.lib_inv[t * kLibStride + k] =
+                (float)(1.0 / ((double)lib.slew_index[t * STA_LUT + k + 1] - lib.slew_index[t * STA_LUT + k]));
+            o.lib_inv[t * kLibStride + 8 + k] =
+                (float)(1.0 / ((double)lib.load_index[t * STA_LUT + k + 1] - lib.load_index[t * STA_LUT + k]));
+        }
+        for (int a = 0; a < STA_MAX_ARCS; ++a) {
+            if (lib.arc_unate[t * STA_MAX_ARCS + a] < 0) o.lib_unate[t] |= 1 << a;
+            for (int rf = 0; rf < 2; ++rf) {
+                const size_t src = (((size_t)t * STA_MAX_ARCS + a) * 2 + rf) * STA_LUT * STA_LUT;
+                float* dst = &o.lib_tab[(((size_t)t * STA_MAX_ARCS + a) * 2 + rf) * kTabPerArcRf];
+                std::memcpy(dst, lib.delay_tab + src, sizeof(float) * STA_LUT * STA_LUT);
+                std::memcpy(dst + STA_LUT * STA_LUT, lib.slew_tab + src, sizeof(float) * STA_LUT * STA_LUT);
+            }
+        }
+    }
+    return STA_OK;
+}
+
+}  // namespace sta

@@ -1,0 +1,568 @@
+// capi.cu -- the C ABI declared in include/sta.h.
+//
+// Execution model: one handle per netlist keeps every array resident on the
+// device.  A forward pass is a sequence of kernels (net RC over every net,
+// then one launch per level, then the endpoint reduction, then one launch per
+// level in reverse for required times); the gradient pass is one launch per
+// level in reverse.  Each sequence is captured once into a CUDA graph and
+// replayed, so the per-level launches cost a graph node each, not a host
+// launch.  The required-time sweep runs on a stream of the handle's own that
+// waits for the arrival-time pass only, so the caller's stream is free as
+// soon as arrival times exist and a gradient sweep queued there overlaps the
+// required-time sweep on the GPU: the GB300 counterpart of the paper's
+// two-stream operation fusion (Section 3.2).
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "sta_internal.h"
+
+using namespace sta;
+
+namespace {
+
+thread_local std::string g_err;
+
+StaStatus set_err(StaStatus st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return set_err(e_ == cudaErrorMemoryAllocation ? STA_ERR_OOM : STA_ERR_CUDA,     \
+                           std::string(#expr) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+}  // namespace
+
+struct StaHandle {
+    Layout lay;
+    DevNet g{};
+    DevState s{};
+    std::vector<void*> allocs;
+    size_t dev_bytes = 0;
+    int device = 0;
+    bool use_graphs = true;
+    bool have_pos = false, have_fwd = false, have_lse = false, have_rat = false;
+    float gamma_fwd = 1.f;
+    cudaEvent_t ev_at = nullptr;    // arrival-time pass of the latest forward done
+    cudaEvent_t ev_fwd = nullptr;   // whole latest forward (required times included) done
+    cudaEvent_t ev_bwd = nullptr;   // latest gradient sweep done
+    cudaStream_t cap = nullptr;     // private stream used for graph capture
+    cudaStream_t side = nullptr;    // required-time sweep
+    // graph cache
+    cudaGraphExec_t gx_fwd[2] = {nullptr, nullptr};  // [lse]
+    float gx_fwd_gamma[2] = {0.f, 0.f};
+    cudaGraphExec_t gx_rat = nullptr;
+    cudaGraphExec_t gx_adj = nullptr;
+    float gx_adj_gamma = 0.f;
+    // staging for host inputs / outputs
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    // profiling: event pairs around every launch of each sequence
+    bool profile = false;
+    struct Prof {
+        std::vector<cudaEvent_t> ev;  // 2 per launch
+        std::vector<int> kind;        // 1 per launch
+        size_t next = 0;
+    } prof_pos, prof_fwd, prof_rat, prof_adj;
+
+    template <typename T>
+    StaStatus alloc(T*& p, size_t n) {
+        void* q = nullptr;
+        const size_t bytes = (n ? n : 1) * sizeof(T);
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) return set_err(STA_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        allocs.push_back(q);
+        dev_bytes += bytes;
+        p = static_cast<T*>(q);
+        return STA_OK;
+    }
+    template <typename T>
+    StaStatus upload(const T*& dst, const std::vector<T>& src) {
+        T* p = nullptr;
+        StaStatus st = alloc(p, src.size());
+        if (st != STA_OK) return st;
+        if (!src.empty()) CUDA_TRY(cudaMemcpy(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+        dst = p;
+        return STA_OK;
+    }
+    StaStatus staging(size_t bytes) {
+        if (bytes <= stage_bytes) return STA_OK;
+        if (stage) cudaFree(stage);
+        stage = nullptr;
+        stage_bytes = 0;
+        CUDA_TRY(cudaMalloc(&stage, bytes));
+        stage_bytes = bytes;
+        return STA_OK;
+    }
+    ~StaHandle() {
+        for (auto* gx : {gx_fwd[0], gx_fwd[1], gx_rat, gx_adj})
+            if (gx) cudaGraphExecDestroy(gx);
+        for (void* p : allocs) cudaFree(p);
+        if (stage) cudaFree(stage);
+        for (auto* ev : {ev_at, ev_fwd, ev_bwd})
+            if (ev) cudaEventDestroy(ev);
+        for (Prof* pr : {&prof_pos, &prof_fwd, &prof_rat, &prof_adj})
+            for (cudaEvent_t e : pr->ev) cudaEventDestroy(e);
+        if (cap) cudaStreamDestroy(cap);
+        if (side) cudaStreamDestroy(side);
+    }
+};
+
+namespace {
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+// ---- sequences (also what the graphs capture) ----
+// With profiling on, every launch is bracketed by an event pair (event record
+// nodes when captured).  Events are created on first use.
+struct ProfScope {
+    StaHandle::Prof* pr;
+    cudaStream_t st;
+    size_t i;
+    ProfScope(StaHandle* h, StaHandle::Prof* p, int kind, cudaStream_t s) : pr(h->profile ? p : nullptr), st(s), i(0) {
+        if (!pr) return;
+        i = pr->next++;
+        while (pr->ev.size() < 2 * pr->next) {
+            cudaEvent_t e = nullptr;
+            cudaEventCreate(&e);
+            pr->ev.push_back(e);
+        }
+        if (pr->kind.size() < pr->next) pr->kind.resize(pr->next);
+        pr->kind[i] = kind;
+        cudaEventRecord(pr->ev[2 * i], st);
+    }
+    ~ProfScope() {
+        if (pr) cudaEventRecord(pr->ev[2 * i + 1], st);
+    }
+};
+
+void enqueue_forward(StaHandle* h, int lse, float gamma, cudaStream_t st) {
+    const Layout& L = h->lay;
+    h->prof_fwd.next = 0;
+    {
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
+        launch_rc(h->g, h->s, L.lvl_wtask[L.L], L.lvl_ctask[L.L], st);
+    }
+    for (int l = 0; l < L.L; ++l) {
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_FWD_LEVEL, st);
+        launch_fwd_level(h->g, h->s, L.lvl_wtask[l], L.lvl_wtask[l + 1] - L.lvl_wtask[l], L.lvl_ctask[l],
+                         L.lvl_ctask[l + 1] - L.lvl_ctask[l], gamma, lse, st);
+    }
+    ProfScope ps(h, &h->prof_fwd, STA_PROF_ENDPOINTS, st);
+    launch_endpoints(h->g, h->s, gamma, lse, st);
+}
+
+void enqueue_backward(StaHandle* h, int mode, float gamma, cudaStream_t st) {
+    const Layout& L = h->lay;
+    StaHandle::Prof* pr = (mode & 2) ? &h->prof_adj : &h->prof_rat;
+    pr->next = 0;
+    if (mode & 2) {
+        ProfScope ps(h, pr, STA_PROF_SEED, st);
+        launch_seed(h->g, h->s, gamma, st);
+    }
+    for (int l = L.L - 1; l >= 0; --l) {
+        ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJ_LEVEL : STA_PROF_RAT_LEVEL, st);
+        launch_bwd_level(h->g, h->s, L.lvl_wtask[l], L.lvl_wtask[l + 1] - L.lvl_wtask[l], L.lvl_ctask[l],
+                         L.lvl_ctask[l + 1] - L.lvl_ctask[l], gamma, mode, st);
+    }
+}
+
+template <typename F>
+StaStatus capture(StaHandle* h, cudaGraphExec_t* out, F&& body) {
+    if (*out) {
+        cudaGraphExecDestroy(*out);
+        *out = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    body(h->cap);
+    cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    if (e != cudaSuccess) return set_err(STA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return set_err(STA_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return STA_OK;
+}
+
+StaStatus check_launch() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(STA_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return STA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sta_abi_version(void) { return STA_ABI_VERSION; }
+
+const char* sta_last_error(void) { return g_err.c_str(); }
+
+StaStatus sta_levelize(const StaNetlistDesc* nl, int32_t* net_level, int32_t* num_levels, int32_t* net_order,
+                       int32_t* pin_order) {
+    if (!nl || !net_level || !num_levels) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    try {
+        std::vector<int32_t> lv, order, pins;
+        int32_t L = 0;
+        std::string err;
+        StaStatus st = ordering(*nl, lv, L, order, pins, err);
+        if (st != STA_OK) return set_err(st, err);
+        std::memcpy(net_level, lv.data(), lv.size() * sizeof(int32_t));
+        *num_levels = L;
+        if (net_order) std::memcpy(net_order, order.data(), order.size() * sizeof(int32_t));
+        if (pin_order) std::memcpy(pin_order, pins.data(), pins.size() * sizeof(int32_t));
+        return STA_OK;
+    } catch (const std::bad_alloc&) {
+        return set_err(STA_ERR_OOM, "host allocation failed");
+    }
+}
+
+StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaOptions* opts, StaHandle** out) {
+    if (!nl || !lib || !out) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    StaHandle* h = nullptr;
+    try {
+        h = new StaHandle();
+    } catch (const std::bad_alloc&) {
+        return set_err(STA_ERR_OOM, "host allocation failed");
+    }
+    auto fail = [&](StaStatus st) {
+        std::string keep = g_err;
+        delete h;
+        g_err = keep;
+        return st;
+    };
+    try {
+        std::string err;
+        StaStatus st = build_layout(*nl, *lib, h->lay, err);
+        if (st != STA_OK) return fail(set_err(st, err));
+    } catch (const std::bad_alloc&) {
+        return fail(set_err(STA_ERR_OOM, "host allocation failed"));
+    }
+    if (opts) {
+        h->use_graphs = opts->use_graphs != 0;
+        h->profile = opts->profile != 0;
+    }
+    const Layout& L = h->lay;
+    cudaError_t ce = cudaGetDevice(&h->device);
+    if (ce != cudaSuccess) return fail(set_err(STA_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce)));
+
+    DevNet& g = h->g;
+    DevState& s = h->s;
+    StaStatus st = STA_OK;
+#define STEP(x)                      \
+    do {                             \
+        st = (x);                    \
+        if (st != STA_OK) return fail(st); \
+    } while (0)
+    STEP(h->upload(g.net_ptr, L.net_ptr));
+    STEP(h->upload(g.net_drv, L.net_drv));
+    STEP(h->upload(g.net_arc_ptr, L.net_arc_ptr));
+    STEP(h->upload(g.arc_pin, L.arc_pin));
+    STEP(h->upload(g.pin_orig, L.pin_orig));
+    STEP(h->upload(g.pin_cap, L.pin_cap));
+    STEP(h->upload(g.wtask, L.wtask));
+    STEP(h->upload(g.ctask, L.ctask));
+    STEP(h->upload(g.lib_idx, L.lib_idx));
+    STEP(h->upload(g.lib_inv, L.lib_inv));
+    STEP(h->upload(g.lib_unate, L.lib_unate));
+    STEP(h->upload(g.lib_tab, L.lib_tab));
+    STEP(h->upload(g.ep_pin, L.ep_pin));
+    STEP(h->upload(g.ep_rat, L.ep_rat));
+    g.r = L.r_per_um;
+    g.c = L.c_per_um;
+    g.P = L.P;
+    g.Pnet = L.Pnet;
+    g.N = L.N;
+    g.E = L.E;
+
+    const size_t P = L.P;
+    STEP(h->alloc(s.xy, P));
+    STEP(h->alloc(s.load, L.N));
+    STEP(h->alloc(s.wdi, P));
+    STEP(h->alloc(s.at, 4 * P));
+    STEP(h->alloc(s.slew, 4 * P));
+    STEP(h->alloc(s.ats, 2 * P));
+    STEP(h->alloc(s.adel, 4 * (size_t)L.A));
+    STEP(h->alloc(s.rat, 4 * P));
+    STEP(h->alloc(s.g_ats, 2 * P));
+    STEP(h->alloc(s.g_slew, 2 * P));
+    STEP(h->alloc(s.grad, P));
+    STEP(h->alloc(s.ep_slack, L.E));
+    STEP(h->alloc(s.red, (size_t)kRedBlocks * 8));
+    STEP(h->alloc(s.summary, STA_SUM_COUNT));
+    STEP(h->alloc(s.params, 4));
+#undef STEP
+    auto zero = [&](void* p, size_t bytes) { return cudaMemset(p, 0, bytes); };
+    if (zero(s.xy, P * 8) || zero(s.load, L.N * 4) || zero(s.wdi, P * 8) || zero(s.ats, P * 8) ||
+        zero(s.adel, (size_t)L.A * 16) || zero(s.g_ats, P * 8) || zero(s.g_slew, P * 8) || zero(s.grad, P * 8) ||
+        zero(s.summary, STA_SUM_COUNT * 8) || zero(s.params, 16) || zero(s.red, (size_t)kRedBlocks * 64))
+        return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
+    // constant state: asserted AT/slew (and LSE AT = late AT), required-time seeds
+    if (cudaMemcpy(s.at, L.at0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(s.slew, L.slew0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(s.rat, L.rat0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(set_err(STA_ERR_CUDA, "initial state upload failed"));
+    launch_init_ats(s, L.P, 0);
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_at, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fwd, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_bwd, cudaEventDisableTiming) != cudaSuccess)
+        return fail(set_err(STA_ERR_CUDA, "stream/event creation failed"));
+    ce = cudaDeviceSynchronize();
+    if (ce != cudaSuccess) return fail(set_err(STA_ERR_CUDA, std::string("init: ") + cudaGetErrorString(ce)));
+    cudaEventRecord(h->ev_at, 0);
+    cudaEventRecord(h->ev_fwd, 0);
+    cudaEventRecord(h->ev_bwd, 0);
+    *out = h;
+    return STA_OK;
+}
+
+void sta_destroy(StaHandle* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    delete h;
+}
+
+StaStatus sta_set_positions(StaHandle* h, const float* xy, int on_device, void* stream) {
+    if (!h || (!xy && h->lay.P > 0)) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    cudaStream_t st = as_stream(stream);
+    // do not overwrite positions that a pending sweep still reads
+    CUDA_TRY(cudaStreamWaitEvent(st, h->ev_bwd, 0));
+    CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
+    const float2* src = reinterpret_cast<const float2*>(xy);
+    if (!on_device) {
+        StaStatus s2 = h->staging((size_t)h->lay.P * 8);
+        if (s2 != STA_OK) return s2;
+        CUDA_TRY(cudaMemcpyAsync(h->stage, xy, (size_t)h->lay.P * 8, cudaMemcpyHostToDevice, st));
+        src = static_cast<const float2*>(h->stage);
+    }
+    {
+        h->prof_pos.next = 0;
+        ProfScope ps(h, &h->prof_pos, STA_PROF_POSITIONS, st);
+        launch_gather_xy(h->g, h->s, src, st);
+    }
+    StaStatus s3 = check_launch();
+    if (s3 != STA_OK) return s3;
+    h->have_pos = true;
+    h->have_fwd = h->have_lse = h->have_rat = false;
+    return STA_OK;
+}
+
+StaStatus sta_forward(StaHandle* h, uint32_t flags, float gamma, void* stream) {
+    if (!h) return set_err(STA_ERR_INVALID_ARG, "null handle");
+    if (!h->have_pos) return set_err(STA_ERR_STATE, "sta_set_positions must come before sta_forward");
+    const int lse = (flags & STA_FWD_LSE) ? 1 : 0;
+    if (lse && !(std::isfinite(gamma) && gamma > 0.f)) return set_err(STA_ERR_INVALID_ARG, "gamma must be > 0");
+    if (!lse) gamma = 1.f;
+    cudaStream_t st = as_stream(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, h->ev_bwd, 0));
+    CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
+    if (h->use_graphs) {
+        if (!h->gx_fwd[lse] || h->gx_fwd_gamma[lse] != gamma) {
+            StaStatus s2 = capture(h, &h->gx_fwd[lse], [&](cudaStream_t c) { enqueue_forward(h, lse, gamma, c); });
+            if (s2 != STA_OK) return s2;
+            h->gx_fwd_gamma[lse] = gamma;
+        }
+        CUDA_TRY(cudaGraphLaunch(h->gx_fwd[lse], st));
+    } else {
+        enqueue_forward(h, lse, gamma, st);
+        StaStatus s2 = check_launch();
+        if (s2 != STA_OK) return s2;
+    }
+    CUDA_TRY(cudaEventRecord(h->ev_at, st));
+    if (flags & STA_FWD_RAT) {
+        CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_at, 0));
+        if (h->use_graphs) {
+            if (!h->gx_rat) {
+                StaStatus s2 = capture(h, &h->gx_rat, [&](cudaStream_t c) { enqueue_backward(h, 1, 1.f, c); });
+                if (s2 != STA_OK) return s2;
+            }
+            CUDA_TRY(cudaGraphLaunch(h->gx_rat, h->side));
+        } else {
+            enqueue_backward(h, 1, 1.f, h->side);
+            StaStatus s2 = check_launch();
+            if (s2 != STA_OK) return s2;
+        }
+        CUDA_TRY(cudaEventRecord(h->ev_fwd, h->side));
+    } else {
+        CUDA_TRY(cudaEventRecord(h->ev_fwd, st));
+    }
+    h->have_fwd = true;
+    h->have_lse = lse != 0;
+    h->have_rat = (flags & STA_FWD_RAT) != 0;
+    h->gamma_fwd = gamma;
+    return STA_OK;
+}
+
+StaStatus sta_backward_grad(StaHandle* h, const float* w, int w_on_device, float* grad_xy, int on_device,
+                            void* stream) {
+    if (!h || !w || (!grad_xy && h->lay.P > 0)) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    if (!h->have_lse) return set_err(STA_ERR_STATE, "sta_forward with STA_FWD_LSE must come before sta_backward_grad");
+    cudaStream_t st = as_stream(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, h->ev_at, 0));
+    launch_set_weights(h->s, w_on_device ? w : nullptr, w_on_device ? 0.f : w[0], w_on_device ? 0.f : w[1], st);
+    const float gamma = h->gamma_fwd;
+    if (h->use_graphs) {
+        if (!h->gx_adj || h->gx_adj_gamma != gamma) {
+            StaStatus s2 = capture(h, &h->gx_adj, [&](cudaStream_t c) { enqueue_backward(h, 2, gamma, c); });
+            if (s2 != STA_OK) return s2;
+            h->gx_adj_gamma = gamma;
+        }
+        CUDA_TRY(cudaGraphLaunch(h->gx_adj, st));
+    } else {
+        enqueue_backward(h, 2, gamma, st);
+    }
+    StaStatus s2 = check_launch();
+    if (s2 != STA_OK) return s2;
+    const size_t bytes = (size_t)h->lay.P * 8;
+    if (bytes) {
+        CUDA_TRY(cudaMemcpyAsync(grad_xy, h->s.grad, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 st));
+    }
+    CUDA_TRY(cudaEventRecord(h->ev_bwd, st));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(st));
+    return STA_OK;
+}
+
+StaStatus sta_stream_wait(StaHandle* h, void* stream) {
+    if (!h) return set_err(STA_ERR_INVALID_ARG, "null handle");
+    cudaStream_t st = as_stream(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
+    CUDA_TRY(cudaStreamWaitEvent(st, h->ev_bwd, 0));
+    return STA_OK;
+}
+
+StaStatus sta_query_summary(StaHandle* h, double* out, int on_device, void* stream) {
+    if (!h || !out) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    if (!h->have_fwd) return set_err(STA_ERR_STATE, "no forward pass yet");
+    cudaStream_t st = as_stream(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
+    CUDA_TRY(cudaMemcpyAsync(out, h->s.summary, STA_SUM_COUNT * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(st));
+    return STA_OK;
+}
+
+namespace {
+
+StaStatus deliver(StaHandle* h, const float* internal, int k, float* out, int on_device, cudaStream_t st) {
+    const size_t bytes = (size_t)h->lay.P * k * sizeof(float);
+    if (!bytes) return STA_OK;
+    float* dst = out;
+    if (!on_device) {
+        StaStatus s2 = h->staging(bytes);
+        if (s2 != STA_OK) return s2;
+        dst = static_cast<float*>(h->stage);
+    }
+    launch_scatter(h->g, internal, dst, k, h->lay.P, st);
+    StaStatus s3 = check_launch();
+    if (s3 != STA_OK) return s3;
+    if (!on_device) {
+        CUDA_TRY(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return STA_OK;
+}
+
+}  // namespace
+
+StaStatus sta_query_pins(StaHandle* h, float* at, float* slew, float* rat, float* ats, float* slack, int on_device,
+                         void* stream) {
+    if (!h) return set_err(STA_ERR_INVALID_ARG, "null handle");
+    if (!h->have_fwd) return set_err(STA_ERR_STATE, "no forward pass yet");
+    if ((rat || slack) && !h->have_rat) return set_err(STA_ERR_STATE, "required times need STA_FWD_RAT");
+    if (ats && !h->have_lse) return set_err(STA_ERR_STATE, "LSE arrival times need STA_FWD_LSE");
+    cudaStream_t st = as_stream(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
+    StaStatus s2 = STA_OK;
+    if (at && (s2 = deliver(h, h->s.at, 4, at, on_device, st)) != STA_OK) return s2;
+    if (slew && (s2 = deliver(h, h->s.slew, 4, slew, on_device, st)) != STA_OK) return s2;
+    if (rat && (s2 = deliver(h, h->s.rat, 4, rat, on_device, st)) != STA_OK) return s2;
+    if (ats && (s2 = deliver(h, h->s.ats, 2, ats, on_device, st)) != STA_OK) return s2;
+    if (slack) {
+        const size_t bytes = (size_t)h->lay.P * 8;
+        if (bytes) {
+            float* dst = slack;
+            if (!on_device) {
+                if ((s2 = h->staging(bytes)) != STA_OK) return s2;
+                dst = static_cast<float*>(h->stage);
+            }
+            launch_pin_slack(h->g, h->s, dst, st);
+            if ((s2 = check_launch()) != STA_OK) return s2;
+            if (!on_device) {
+                CUDA_TRY(cudaMemcpyAsync(slack, dst, bytes, cudaMemcpyDeviceToHost, st));
+                CUDA_TRY(cudaStreamSynchronize(st));
+            }
+        }
+    }
+    return STA_OK;
+}
+
+StaStatus sta_query_endpoints(StaHandle* h, float* slack, int on_device, void* stream) {
+    if (!h || (!slack && h->lay.E > 0)) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    if (!h->have_fwd) return set_err(STA_ERR_STATE, "no forward pass yet");
+    cudaStream_t st = as_stream(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
+    if (h->lay.E) {
+        CUDA_TRY(cudaMemcpyAsync(slack, h->s.ep_slack, (size_t)h->lay.E * 8,
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        if (!on_device) CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return STA_OK;
+}
+
+StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
+    if (!h || !launches) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    const Layout& L = h->lay;
+    // launches of one step, by kind (levels with no task launch nothing)
+    int32_t nonempty = 0;
+    for (int l = 0; l < L.L; ++l)
+        nonempty += (L.lvl_wtask[l + 1] > L.lvl_wtask[l] || L.lvl_ctask[l + 1] > L.lvl_ctask[l]) ? 1 : 0;
+    const int32_t nw = L.lvl_wtask.empty() ? 0 : L.lvl_wtask.back(), nc = L.lvl_ctask.empty() ? 0 : L.lvl_ctask.back();
+    launches[STA_PROF_POSITIONS] = L.P > 0 ? 1 : 0;
+    launches[STA_PROF_NET_RC] = (nw + nc) > 0 ? 1 : 0;
+    launches[STA_PROF_FWD_LEVEL] = nonempty;
+    launches[STA_PROF_ENDPOINTS] = 2;
+    launches[STA_PROF_RAT_LEVEL] = nonempty;
+    launches[STA_PROF_SEED] = 1 + (L.E > 0 ? 1 : 0);  // weights + seeds
+    launches[STA_PROF_ADJ_LEVEL] = nonempty;
+    if (!ms) return STA_OK;
+    for (int k = 0; k < STA_PROF_KINDS; ++k) ms[k] = 0.0;
+    if (!h->profile) return set_err(STA_ERR_STATE, "handle was created without StaOptions.profile");
+    CUDA_TRY(cudaDeviceSynchronize());
+    for (StaHandle::Prof* pr : {&h->prof_pos, &h->prof_fwd, &h->prof_rat, &h->prof_adj}) {
+        for (size_t i = 0; i < pr->kind.size() && 2 * i + 1 < pr->ev.size(); ++i) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, pr->ev[2 * i], pr->ev[2 * i + 1]) == cudaSuccess) ms[pr->kind[i]] += t;
+            else cudaGetLastError();
+        }
+    }
+    return STA_OK;
+}
+
+StaStatus sta_query_sizes(const StaHandle* h, int64_t* o) {
+    if (!h || !o) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    const Layout& L = h->lay;
+    o[0] = L.P;
+    o[1] = L.N;
+    o[2] = L.L;
+    o[3] = L.A;
+    o[4] = L.E;
+    o[5] = L.lvl_wtask.empty() ? 0 : L.lvl_wtask.back();
+    o[6] = L.lvl_ctask.empty() ? 0 : L.lvl_ctask.back();
+    o[7] = (int64_t)h->dev_bytes;
+    return STA_OK;
+}
+
+}  // extern "C"

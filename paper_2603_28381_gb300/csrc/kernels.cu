@@ -1,0 +1,798 @@
+// kernels.cu -- sm_103a kernels of the levelized STA path.
+//
+// Work decomposition (replacing the paper's (4 x 8 x NETS_PER_BLOCK) thread
+// layout of Algorithm 1): per level the builder packs consecutive nets of at
+// most 32 pins, at most 8 of them, into one warp ("warp task"): lanes map to
+// the task's pins, so a net of 3 pins uses 3 lanes and a warp stays busy
+// whatever the fanout mix; the per-net reductions of Eq. 1 (load) and of the
+// required-time / adjoint passes are segmented warp-shuffle scans, with no
+// shared memory and no atomics.  The driver-cell evaluation of a task uses 4
+// lanes per net, one per timing condition (cond = 2*el + rf).  Nets of more
+// than 32 pins get a whole 256-thread block each ("block task") with a
+// fixed-order block reduction.  Every reduction order depends on the netlist
+// only, so results are bit-identical run to run.
+#include <cfloat>
+#include <cmath>
+
+#include "kernels.h"
+
+namespace sta {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kInf = __builtin_huge_valf();
+
+__device__ __forceinline__ unsigned lanes_upto(int lane) { return kFull >> (31 - lane); }
+
+// largest k in [0,5] with idx[k] <= v (0 below the range): right-continuous
+// segment of a 7-point table axis, extended linearly outside [idx0, idx6].
+__device__ __forceinline__ int axis_seg(const float* __restrict__ idx, float v) {
+    int k = 0;
+#pragma unroll
+    for (int j = 1; j <= 5; ++j) k += (__ldg(idx + j) <= v) ? 1 : 0;
+    return k;
+}
+
+// bilinear inter/extrapolation of a 7x7 table [slew i][load j]
+__device__ __forceinline__ float bilerp(const float* __restrict__ T, int i, int j, float ts, float ul) {
+    const float* q = T + i * STA_LUT + j;
+    const float t00 = __ldg(q), t01 = __ldg(q + 1), t10 = __ldg(q + STA_LUT), t11 = __ldg(q + STA_LUT + 1);
+    const float r0 = fmaf(ul, t01 - t00, t00);
+    const float r1 = fmaf(ul, t11 - t10, t10);
+    return fmaf(ts, r1 - r0, r0);
+}
+
+__device__ __forceinline__ float bilerp_grad(const float* __restrict__ T, int i, int j, float ts, float ul,
+                                             float inv_s, float inv_l, float& d_ds, float& d_dl) {
+    const float* q = T + i * STA_LUT + j;
+    const float t00 = __ldg(q), t01 = __ldg(q + 1), t10 = __ldg(q + STA_LUT), t11 = __ldg(q + STA_LUT + 1);
+    const float r0 = fmaf(ul, t01 - t00, t00);
+    const float r1 = fmaf(ul, t11 - t10, t10);
+    d_ds = (r1 - r0) * inv_s;
+    d_dl = fmaf(ts, (t11 - t10) - (t01 - t00), t01 - t00) * inv_l;
+    return fmaf(ts, r1 - r0, r0);
+}
+
+struct DrvOut {
+    float at, slew, ats;
+};
+
+// Arrival time, slew and (late) LSE arrival time of net n's driver d for one
+// condition c (Section 3.1.2; Eq. 4 for the LSE).  Writes the arc delays.
+__device__ DrvOut eval_driver(const DevNet& g, const DevState& s, int n, int d, int c, float gamma, bool lse) {
+    DrvOut o;
+    const int t = g.net_drv[n];
+    if (t < 0) {  // asserted driver: constant values set at creation
+        o.at = s.at[4 * d + c];
+        o.slew = s.slew[4 * d + c];
+        o.ats = c >= 2 ? s.ats[2 * d + c - 2] : 0.f;
+        return o;
+    }
+    const int el = c >> 1, rf = c & 1;
+    const int a0 = g.net_arc_ptr[n], a1 = g.net_arc_ptr[n + 1];
+    const float ld = s.load[n];
+    const float* li = g.lib_idx + t * kLibStride + 8;
+    const int jl = axis_seg(li, ld);
+    const float ul = (ld - __ldg(li + jl)) * __ldg(g.lib_inv + t * kLibStride + 8 + jl);
+    const float* si = g.lib_idx + t * kLibStride;
+    const int un = g.lib_unate[t];
+    float best_at = el ? -kInf : kInf, best_sl = el ? -kInf : kInf;
+    float cand[STA_MAX_ARCS];
+    float m = -kInf;
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        if (a0 + k < a1) {
+            const int a = a0 + k, i = g.arc_pin[a];
+            const int rfi = rf ^ ((un >> k) & 1);
+            const float sin = s.slew[4 * i + 2 * el + rfi];
+            const float ain = s.at[4 * i + 2 * el + rfi];
+            const int is = axis_seg(si, sin);
+            const float ts = (sin - __ldg(si + is)) * __ldg(g.lib_inv + t * kLibStride + is);
+            const float* T = g.lib_tab + ((t * STA_MAX_ARCS + k) * 2 + rf) * kTabPerArcRf;
+            const float D = bilerp(T, is, jl, ts, ul);
+            const float S = bilerp(T + STA_LUT * STA_LUT, is, jl, ts, ul);
+            s.adel[4 * a + c] = D;
+            if (el) {
+                best_at = fmaxf(best_at, ain + D);
+                best_sl = fmaxf(best_sl, S);
+                if (lse) {
+                    cand[k] = s.ats[2 * i + rfi] + D;
+                    m = fmaxf(m, cand[k]);
+                }
+            } else {
+                best_at = fminf(best_at, ain + D);
+                best_sl = fminf(best_sl, S);
+            }
+        }
+    }
+    o.at = best_at;
+    o.slew = best_sl;
+    o.ats = 0.f;
+    if (el && lse) {
+        float sum = 0.f;
+#pragma unroll
+        for (int k = 0; k < STA_MAX_ARCS; ++k)
+            if (a0 + k < a1) sum += expf((cand[k] - m) / gamma);
+        o.ats = m + gamma * logf(sum);
+    }
+    return o;
+}
+
+// Adjoint of one late output transition rf of net n's driver cell.  Writes
+// g_ats / g_slew of the cell's input pins (one writer per component) and
+// returns this transition's contribution to d loss / d load.
+__device__ float arc_adjoint(const DevNet& g, const DevState& s, int n, int d, int t, int rf, float GA, float GS,
+                             float gamma) {
+    const int a0 = g.net_arc_ptr[n], a1 = g.net_arc_ptr[n + 1];
+    const float ld = s.load[n];
+    const float* li = g.lib_idx + t * kLibStride + 8;
+    const int jl = axis_seg(li, ld);
+    const float inv_l = __ldg(g.lib_inv + t * kLibStride + 8 + jl);
+    const float ul = (ld - __ldg(li + jl)) * inv_l;
+    const float* si = g.lib_idx + t * kLibStride;
+    const int un = g.lib_unate[t];
+    const float atsd = s.ats[2 * d + rf];
+    float best = -kInf, dss = 0.f, dsl = 0.f, gl = 0.f;
+    int amax = -1;
+    float gsl[STA_MAX_ARCS];
+    int pin_c[STA_MAX_ARCS];
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        gsl[k] = 0.f;
+        pin_c[k] = -1;
+        if (a0 + k < a1) {
+            const int a = a0 + k, i = g.arc_pin[a];
+            const int rfi = rf ^ ((un >> k) & 1);
+            const float sin = s.slew[4 * i + 2 + rfi];
+            const int is = axis_seg(si, sin);
+            const float inv_s = __ldg(g.lib_inv + t * kLibStride + is);
+            const float ts = (sin - __ldg(si + is)) * inv_s;
+            const float* T = g.lib_tab + ((t * STA_MAX_ARCS + k) * 2 + rf) * kTabPerArcRf;
+            float dDs, dDl, dSs, dSl;
+            bilerp_grad(T, is, jl, ts, ul, inv_s, inv_l, dDs, dDl);
+            const float S = bilerp_grad(T + STA_LUT * STA_LUT, is, jl, ts, ul, inv_s, inv_l, dSs, dSl);
+            const float D = s.adel[4 * a + 2 + rf];
+            const float w = expf((s.ats[2 * i + rfi] + D - atsd) / gamma);
+            const float gD = GA * w;
+            s.g_ats[2 * i + rfi] = gD;
+            gsl[k] = gD * dDs;
+            gl = fmaf(gD, dDl, gl);
+            pin_c[k] = 2 * i + rfi;
+            if (S > best) {
+                best = S;
+                amax = k;
+                dss = dSs;
+                dsl = dSl;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k)
+        if (k == amax) gsl[k] = fmaf(GS, dss, gsl[k]);
+    if (amax >= 0) gl = fmaf(GS, dsl, gl);
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k)
+        if (pin_c[k] >= 0) s.g_slew[pin_c[k]] = gsl[k];
+    return gl;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-task geometry: pins [pin0, pin0 + npins) of nets [n0, n0 + nn).
+// ---------------------------------------------------------------------------
+struct WarpGeom {
+    int lane, pin0, npins, h;  // h: head offset of net `lane` (lane <= nn)
+    unsigned heads;            // bit k set = pin0 + k is a driver
+    int hd, j, last;           // for this lane's pin: driver offset, local net, last pin of its net
+    bool valid;
+};
+
+__device__ __forceinline__ WarpGeom warp_geom(const DevNet& g, int n0, int nn) {
+    WarpGeom w;
+    w.lane = threadIdx.x & 31;
+    w.pin0 = g.net_ptr[n0];
+    w.h = (w.lane <= nn) ? g.net_ptr[n0 + w.lane] - w.pin0 : 0;
+    w.npins = __shfl_sync(kFull, w.h, nn);
+    w.heads = __reduce_or_sync(kFull, (w.lane < nn) ? (1u << w.h) : 0u);
+    const unsigned upto = w.heads & lanes_upto(w.lane);
+    w.hd = 31 - __clz(upto);
+    w.j = __popc(upto) - 1;
+    const unsigned after = w.heads & ~lanes_upto(w.lane);
+    w.last = (after ? __ffs(after) - 1 : w.npins) - 1;
+    w.valid = w.lane < w.npins;
+    return w;
+}
+
+// fixed-order block reductions (256 threads)
+template <typename Op>
+__device__ __forceinline__ float block_reduce(float v, float* sh, Op op) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = op(v, __shfl_xor_sync(kFull, v, off));
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    float r = sh[0];
+#pragma unroll
+    for (int k = 1; k < kWarpsPerBlock; ++k) r = op(r, sh[k]);
+    return r;
+}
+
+struct OpSum { __device__ float operator()(float a, float b) const { return a + b; } };
+struct OpMax { __device__ float operator()(float a, float b) const { return fmaxf(a, b); } };
+struct OpMin { __device__ float operator()(float a, float b) const { return fminf(a, b); } };
+
+// ---------------------------------------------------------------------------
+// positions: internal order <- caller's pin order
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_gather_xy(DevNet g, DevState s, const float2* __restrict__ xy) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x)
+        s.xy[p] = xy[g.pin_orig[p]];
+}
+
+// ---------------------------------------------------------------------------
+// Net RC, Eqs. 1-3 on a star: for a sink at Manhattan distance d,
+//   R = r d, C = cap + c d / 2, Delay = R C, Impulse = sqrt(2 R C Delay - Delay^2)
+// and the driver's Load = cap_driver + sum_sinks (cap + c d).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rc_sink(const DevNet& g, const DevState& s, int p, float2 xy, float2 xyd, float cap) {
+    const float dist = fabsf(xy.x - xyd.x) + fabsf(xy.y - xyd.y);
+    const float R = g.r * dist;
+    const float C = fmaf(0.5f * g.c, dist, cap);
+    const float D = R * C * kKrc;
+    const float m = 2.f * R * C * D * kKrc - D * D;
+    s.wdi[p] = make_float2(D, sqrtf(fmaxf(m, 0.f)));
+    return fmaf(g.c, dist, cap);
+}
+
+__device__ void rc_warp(const DevNet& g, const DevState& s, int n0, int nn) {
+    const WarpGeom w = warp_geom(g, n0, nn);
+    const int p = w.pin0 + w.lane;
+    const float2 xy = w.valid ? s.xy[p] : make_float2(0.f, 0.f);
+    const float cap = w.valid ? g.pin_cap[p] : 0.f;
+    const float2 xyd = make_float2(__shfl_sync(kFull, xy.x, w.hd), __shfl_sync(kFull, xy.y, w.hd));
+    float v = cap;
+    if (w.valid && w.lane != w.hd) v = rc_sink(g, s, p, xy, xyd, cap);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float u = __shfl_up_sync(kFull, v, off);
+        if (w.lane - off >= w.hd) v += u;
+    }
+    if (w.valid && w.lane == w.last) s.load[n0 + w.j] = v;
+}
+
+__device__ void rc_block(const DevNet& g, const DevState& s, int n) {
+    __shared__ float sh[kWarpsPerBlock];
+    const int d = g.net_ptr[n], e = g.net_ptr[n + 1];
+    const float2 xyd = s.xy[d];
+    float acc = 0.f;
+#pragma unroll 4
+    for (int p = d + 1 + threadIdx.x; p < e; p += kBlock) acc += rc_sink(g, s, p, s.xy[p], xyd, g.pin_cap[p]);
+    acc = block_reduce(acc, sh, OpSum());
+    if (threadIdx.x == 0) s.load[n] = g.pin_cap[d] + acc;
+}
+
+__global__ void __launch_bounds__(kBlock) k_rc(DevNet g, DevState s, int nw, int nc) {
+    const int nwb = (nw + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if ((int)blockIdx.x < nwb) {
+        const int t = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+        if (t >= nw) return;
+        rc_warp(g, s, g.wtask[2 * t], g.wtask[2 * t + 1]);
+    } else {
+        rc_block(g, s, g.ctask[blockIdx.x - nwb]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward level: driver cells (4 lanes per net), then wire propagation to
+// every sink: AT_s = AT_d + Delay_s, slew_s = sqrt(slew_d^2 + Impulse_s^2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void store_sink(const DevState& s, int p, const float* A, const float* S, float z0,
+                                           float z1, bool lse) {
+    const float2 w = s.wdi[p];
+    const float i2 = w.y * w.y;
+    reinterpret_cast<float4*>(s.at)[p] = make_float4(A[0] + w.x, A[1] + w.x, A[2] + w.x, A[3] + w.x);
+    reinterpret_cast<float4*>(s.slew)[p] =
+        make_float4(sqrtf(fmaf(S[0], S[0], i2)), sqrtf(fmaf(S[1], S[1], i2)), sqrtf(fmaf(S[2], S[2], i2)),
+                    sqrtf(fmaf(S[3], S[3], i2)));
+    if (lse) reinterpret_cast<float2*>(s.ats)[p] = make_float2(z0 + w.x, z1 + w.x);
+}
+
+__device__ void fwd_warp(const DevNet& g, const DevState& s, int n0, int nn, float gamma, bool lse) {
+    const WarpGeom w = warp_geom(g, n0, nn);
+    const int j1 = w.lane >> 2, c = w.lane & 3;
+    const int hj = __shfl_sync(kFull, w.h, j1);
+    DrvOut o{0.f, 0.f, 0.f};
+    if (j1 < nn) {
+        const int n = n0 + j1, d = w.pin0 + hj;
+        o = eval_driver(g, s, n, d, c, gamma, lse);
+        if (g.net_drv[n] >= 0) {
+            s.at[4 * d + c] = o.at;
+            s.slew[4 * d + c] = o.slew;
+            if (lse && c >= 2) s.ats[2 * d + c - 2] = o.ats;
+        }
+    }
+    const int src = 4 * max(w.j, 0);
+    float A[4], S[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        A[k] = __shfl_sync(kFull, o.at, src + k);
+        S[k] = __shfl_sync(kFull, o.slew, src + k);
+    }
+    const float z0 = __shfl_sync(kFull, o.ats, src + 2), z1 = __shfl_sync(kFull, o.ats, src + 3);
+    if (w.valid && w.lane != w.hd) store_sink(s, w.pin0 + w.lane, A, S, z0, z1, lse);
+}
+
+__device__ void fwd_block(const DevNet& g, const DevState& s, int n, float gamma, bool lse) {
+    __shared__ float sh[12];
+    const int d = g.net_ptr[n], e = g.net_ptr[n + 1];
+    if (threadIdx.x < 4) {
+        const int c = threadIdx.x;
+        const DrvOut o = eval_driver(g, s, n, d, c, gamma, lse);
+        if (g.net_drv[n] >= 0) {
+            s.at[4 * d + c] = o.at;
+            s.slew[4 * d + c] = o.slew;
+            if (lse && c >= 2) s.ats[2 * d + c - 2] = o.ats;
+        }
+        sh[c] = o.at;
+        sh[4 + c] = o.slew;
+        if (c >= 2) sh[8 + c - 2] = o.ats;
+    }
+    __syncthreads();
+    float A[4], S[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        A[k] = sh[k];
+        S[k] = sh[4 + k];
+    }
+    const float z0 = sh[8], z1 = sh[9];
+#pragma unroll 4
+    for (int p = d + 1 + threadIdx.x; p < e; p += kBlock) store_sink(s, p, A, S, z0, z1, lse);
+}
+
+__global__ void __launch_bounds__(kBlock) k_fwd(DevNet g, DevState s, int w0, int nw, int c0, int nc, float gamma,
+                                                int lse) {
+    const int nwb = (nw + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if ((int)blockIdx.x < nwb) {
+        const int t = w0 + blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+        if (t >= w0 + nw) return;
+        fwd_warp(g, s, g.wtask[2 * t], g.wtask[2 * t + 1], gamma, lse != 0);
+    } else {
+        fwd_block(g, s, g.ctask[c0 + blockIdx.x - nwb], gamma, lse != 0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward level (reverse order).  mode & 1: required times
+//   RAT_d = min over sinks (RAT_s - Delay_s) late / max early,
+//   RAT_in = RAT_out - arc delay through each arc's unateness.
+// mode & 2: adjoint of the smoothed loss through the wire step, the LSE cell
+// step (softmax weights), the NLDM bilinear partials, the hard late-slew max
+// (to the first arc attaining it) and the star RC, down to d/d(x, y).
+// ---------------------------------------------------------------------------
+struct SinkBwd {
+    float r[4];      // RAT_s - Delay_s
+    float ga[2];     // g_ats of the sink
+    float gs[2];     // g_slew_s * slew_d / slew_s
+    float gwire;     // d loss / d Delay_s + d loss / d Impulse_s
+};
+
+__device__ __forceinline__ SinkBwd sink_bwd(const DevState& s, int p, float2 sld, int mode) {
+    SinkBwd b;
+    const float2 w = s.wdi[p];
+    if (mode & 1) {
+        const float4 rr = reinterpret_cast<const float4*>(s.rat)[p];
+        b.r[0] = rr.x - w.x;
+        b.r[1] = rr.y - w.x;
+        b.r[2] = rr.z - w.x;
+        b.r[3] = rr.w - w.x;
+    } else {
+        b.r[0] = b.r[1] = -kInf;
+        b.r[2] = b.r[3] = kInf;
+    }
+    b.ga[0] = b.ga[1] = b.gs[0] = b.gs[1] = b.gwire = 0.f;
+    if (mode & 2) {
+        const float2 ga = reinterpret_cast<const float2*>(s.g_ats)[p];
+        const float2 gs = reinterpret_cast<const float2*>(s.g_slew)[p];
+        const float2 sl = reinterpret_cast<const float2*>(s.slew)[2 * p + 1];
+        const float q0 = sl.x > 0.f ? gs.x / sl.x : 0.f;
+        const float q1 = sl.y > 0.f ? gs.y / sl.y : 0.f;
+        b.ga[0] = ga.x;
+        b.ga[1] = ga.y;
+        b.gs[0] = q0 * sld.x;
+        b.gs[1] = q1 * sld.y;
+        b.gwire = ga.x + ga.y + (q0 + q1) * w.y;
+    }
+    return b;
+}
+
+// d loss / d (x, y) of sink p given d loss / d Load of its net (star RC).
+__device__ __forceinline__ float2 sink_grad(const DevNet& g, const DevState& s, int p, float2 xy, float2 xyd, float gwire,
+                                            float gload) {
+    const float dx = xy.x - xyd.x, dy = xy.y - xyd.y;
+    const float dist = fabsf(dx) + fabsf(dy);
+    const float cap = g.pin_cap[p];
+    // dDelay/dd = k r (cap + c d); on a star Eq. 3 gives Impulse = Delay, same slope
+    const float gd = fmaf(gload, g.c, gwire * kKrc * g.r * fmaf(g.c, dist, cap));
+    const float sx = (dx > 0.f) - (dx < 0.f), sy = (dy > 0.f) - (dy < 0.f);
+    return make_float2(gd * sx, gd * sy);
+}
+
+__device__ void bwd_warp(const DevNet& g, const DevState& s, int n0, int nn, float gamma, int mode) {
+    const WarpGeom w = warp_geom(g, n0, nn);
+    const int p = w.pin0 + w.lane;
+    const bool sink = w.valid && w.lane != w.hd;
+    float2 sld = make_float2(0.f, 0.f);
+    if (mode & 2) {
+        const float2 sl = w.valid ? reinterpret_cast<const float2*>(s.slew)[2 * p + 1] : make_float2(0.f, 0.f);
+        sld = make_float2(__shfl_sync(kFull, sl.x, w.hd), __shfl_sync(kFull, sl.y, w.hd));
+    }
+    SinkBwd b;
+    if (sink) {
+        b = sink_bwd(s, p, sld, mode);
+    } else {
+        b.r[0] = b.r[1] = -kInf;
+        b.r[2] = b.r[3] = kInf;
+        b.ga[0] = b.ga[1] = b.gs[0] = b.gs[1] = b.gwire = 0.f;
+    }
+    // segmented inclusive scans: totals land on the last pin of each net
+    float r0 = b.r[0], r1 = b.r[1], r2 = b.r[2], r3 = b.r[3];
+    float ga0 = b.ga[0], ga1 = b.ga[1], gs0 = b.gs[0], gs1 = b.gs[1];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const bool take = w.lane - off >= w.hd;
+        if (mode & 1) {
+            const float u0 = __shfl_up_sync(kFull, r0, off), u1 = __shfl_up_sync(kFull, r1, off);
+            const float u2 = __shfl_up_sync(kFull, r2, off), u3 = __shfl_up_sync(kFull, r3, off);
+            if (take) {
+                r0 = fmaxf(r0, u0);
+                r1 = fmaxf(r1, u1);
+                r2 = fminf(r2, u2);
+                r3 = fminf(r3, u3);
+            }
+        }
+        if (mode & 2) {
+            const float u0 = __shfl_up_sync(kFull, ga0, off), u1 = __shfl_up_sync(kFull, ga1, off);
+            const float u2 = __shfl_up_sync(kFull, gs0, off), u3 = __shfl_up_sync(kFull, gs1, off);
+            if (take) {
+                ga0 += u0;
+                ga1 += u1;
+                gs0 += u2;
+                gs1 += u3;
+            }
+        }
+    }
+    if ((mode & 1) && w.valid && w.lane == w.last)
+        reinterpret_cast<float4*>(s.rat)[w.pin0 + w.hd] = make_float4(r0, r1, r2, r3);
+
+    // driver cell step: lane 4 j + c handles net j, condition c
+    const int j1 = w.lane >> 2, c = w.lane & 3;
+    const int hj = __shfl_sync(kFull, w.h, j1);
+    const int lastj = __shfl_sync(kFull, w.h, j1 + 1) - 1;
+    const float R0 = __shfl_sync(kFull, r0, lastj & 31), R1 = __shfl_sync(kFull, r1, lastj & 31);
+    const float R2 = __shfl_sync(kFull, r2, lastj & 31), R3 = __shfl_sync(kFull, r3, lastj & 31);
+    const float GA0 = __shfl_sync(kFull, ga0, lastj & 31), GA1 = __shfl_sync(kFull, ga1, lastj & 31);
+    const float GS0 = __shfl_sync(kFull, gs0, lastj & 31), GS1 = __shfl_sync(kFull, gs1, lastj & 31);
+    float gl = 0.f;
+    if (j1 < nn) {
+        const int n = n0 + j1, d = w.pin0 + hj, t = g.net_drv[n];
+        if (t >= 0) {
+            const int el = c >> 1, rf = c & 1;
+            if (mode & 1) {
+                const float Rc = c == 0 ? R0 : c == 1 ? R1 : c == 2 ? R2 : R3;
+                const int a0 = g.net_arc_ptr[n], a1 = g.net_arc_ptr[n + 1], un = g.lib_unate[t];
+                for (int a = a0; a < a1; ++a) {
+                    const int rfi = rf ^ ((un >> (a - a0)) & 1);
+                    s.rat[4 * g.arc_pin[a] + 2 * el + rfi] = Rc - s.adel[4 * a + c];
+                }
+            }
+            if ((mode & 2) && el == 1)
+                gl = arc_adjoint(g, s, n, d, t, rf, rf ? GA1 : GA0, rf ? GS1 : GS0, gamma);
+        }
+    }
+    if (mode & 2) {
+        gl += __shfl_down_sync(kFull, gl, 1);  // lane 4j+2: rise + fall
+        const float gload = __shfl_sync(kFull, gl, (4 * max(w.j, 0) + 2) & 31);
+        const float2 xy = w.valid ? s.xy[p] : make_float2(0.f, 0.f);
+        const float2 xyd = make_float2(__shfl_sync(kFull, xy.x, w.hd), __shfl_sync(kFull, xy.y, w.hd));
+        float2 gxy = make_float2(0.f, 0.f);
+        if (sink) {
+            gxy = sink_grad(g, s, p, xy, xyd, b.gwire, gload);
+            s.grad[g.pin_orig[p]] = gxy;
+        }
+        float sx = gxy.x, sy = gxy.y;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float u = __shfl_up_sync(kFull, sx, off), v = __shfl_up_sync(kFull, sy, off);
+            if (w.lane - off >= w.hd) {
+                sx += u;
+                sy += v;
+            }
+        }
+        if (w.valid && w.lane == w.last) s.grad[g.pin_orig[w.pin0 + w.hd]] = make_float2(-sx, -sy);
+    }
+}
+
+__device__ void bwd_block(const DevNet& g, const DevState& s, int n, float gamma, int mode) {
+    __shared__ float sh[kWarpsPerBlock];
+    __shared__ float bc[2];
+    const int d = g.net_ptr[n], e = g.net_ptr[n + 1];
+    const float2 sld = (mode & 2) ? reinterpret_cast<const float2*>(s.slew)[2 * d + 1] : make_float2(0.f, 0.f);
+    float r0 = -kInf, r1 = -kInf, r2 = kInf, r3 = kInf, ga0 = 0.f, ga1 = 0.f, gs0 = 0.f, gs1 = 0.f;
+#pragma unroll 2
+    for (int p = d + 1 + threadIdx.x; p < e; p += kBlock) {
+        const SinkBwd b = sink_bwd(s, p, sld, mode);
+        r0 = fmaxf(r0, b.r[0]);
+        r1 = fmaxf(r1, b.r[1]);
+        r2 = fminf(r2, b.r[2]);
+        r3 = fminf(r3, b.r[3]);
+        ga0 += b.ga[0];
+        ga1 += b.ga[1];
+        gs0 += b.gs[0];
+        gs1 += b.gs[1];
+    }
+    if (mode & 1) {
+        r0 = block_reduce(r0, sh, OpMax());
+        r1 = block_reduce(r1, sh, OpMax());
+        r2 = block_reduce(r2, sh, OpMin());
+        r3 = block_reduce(r3, sh, OpMin());
+        if (threadIdx.x == 0) reinterpret_cast<float4*>(s.rat)[d] = make_float4(r0, r1, r2, r3);
+    }
+    if (mode & 2) {
+        ga0 = block_reduce(ga0, sh, OpSum());
+        ga1 = block_reduce(ga1, sh, OpSum());
+        gs0 = block_reduce(gs0, sh, OpSum());
+        gs1 = block_reduce(gs1, sh, OpSum());
+    }
+    const int t = g.net_drv[n];
+    if (threadIdx.x < 4 && t >= 0) {
+        const int c = threadIdx.x, el = c >> 1, rf = c & 1;
+        if (mode & 1) {
+            const float Rc = c == 0 ? r0 : c == 1 ? r1 : c == 2 ? r2 : r3;
+            const int a0 = g.net_arc_ptr[n], a1 = g.net_arc_ptr[n + 1], un = g.lib_unate[t];
+            for (int a = a0; a < a1; ++a) {
+                const int rfi = rf ^ ((un >> (a - a0)) & 1);
+                s.rat[4 * g.arc_pin[a] + 2 * el + rfi] = Rc - s.adel[4 * a + c];
+            }
+        }
+        if ((mode & 2) && el == 1) bc[rf] = arc_adjoint(g, s, n, d, t, rf, rf ? ga1 : ga0, rf ? gs1 : gs0, gamma);
+    }
+    if (!(mode & 2)) return;
+    __syncthreads();
+    const float gload = t >= 0 ? bc[0] + bc[1] : 0.f;
+    const float2 xyd = s.xy[d];
+    float sx = 0.f, sy = 0.f;
+#pragma unroll 2
+    for (int p = d + 1 + threadIdx.x; p < e; p += kBlock) {
+        const SinkBwd b = sink_bwd(s, p, sld, 2);
+        const float2 gxy = sink_grad(g, s, p, s.xy[p], xyd, b.gwire, gload);
+        s.grad[g.pin_orig[p]] = gxy;
+        sx += gxy.x;
+        sy += gxy.y;
+    }
+    sx = block_reduce(sx, sh, OpSum());
+    sy = block_reduce(sy, sh, OpSum());
+    if (threadIdx.x == 0) s.grad[g.pin_orig[d]] = make_float2(-sx, -sy);
+}
+
+__global__ void __launch_bounds__(kBlock) k_bwd(DevNet g, DevState s, int w0, int nw, int c0, int nc, float gamma,
+                                                int mode) {
+    const int nwb = (nw + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if ((int)blockIdx.x < nwb) {
+        const int t = w0 + blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+        if (t >= w0 + nw) return;
+        bwd_warp(g, s, g.wtask[2 * t], g.wtask[2 * t + 1], gamma, mode);
+    } else {
+        bwd_block(g, s, g.ctask[c0 + blockIdx.x - nwb], gamma, mode);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Endpoints: slack, WNS, TNS and the smoothed TNS_gamma / WNS_gamma, by a
+// two-pass fixed-order reduction (partials per block in s.red).
+//   TNS_gamma = sum_e softmin_gamma(s_rise, s_fall, 0),
+//   WNS_gamma = softmin_gamma over every endpoint rise/fall slack,
+//   softmin_gamma(x) = -LSE_gamma(-x), stabilised by the minimum (Eq. 4).
+// ---------------------------------------------------------------------------
+struct EpAcc {
+    double tns_e, tns_l, tns_g, wsum;  // wsum = sum exp(-(s - wmin) / gamma)
+    double wns_e, wns_l, wmin, viol;
+};
+
+__device__ __forceinline__ void ep_merge(EpAcc& a, const EpAcc& b, double gamma) {
+    a.tns_e += b.tns_e;
+    a.tns_l += b.tns_l;
+    a.tns_g += b.tns_g;
+    a.viol += b.viol;
+    a.wns_e = fmin(a.wns_e, b.wns_e);
+    a.wns_l = fmin(a.wns_l, b.wns_l);
+    const double m = fmin(a.wmin, b.wmin);
+    double sum = 0.0;
+    if (a.wsum > 0.0) sum += a.wsum * exp(-(a.wmin - m) / gamma);
+    if (b.wsum > 0.0) sum += b.wsum * exp(-(b.wmin - m) / gamma);
+    a.wsum = sum;
+    a.wmin = m;
+}
+
+__device__ __forceinline__ double softmin3(double a, double b, double c, double gamma) {
+    const double m = fmin(a, fmin(b, c));
+    return m - gamma * log(exp(-(a - m) / gamma) + exp(-(b - m) / gamma) + exp(-(c - m) / gamma));
+}
+
+__device__ __forceinline__ EpAcc ep_identity() {
+    EpAcc a;
+    a.tns_e = a.tns_l = a.tns_g = a.wsum = a.viol = 0.0;
+    a.wns_e = a.wns_l = a.wmin = (double)kInf;
+    return a;
+}
+
+__device__ void ep_block_reduce(EpAcc& acc, double gamma) {
+    __shared__ EpAcc sh[kBlock];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int stride = kBlock / 2; stride > 0; stride >>= 1) {
+        if ((int)threadIdx.x < stride) ep_merge(sh[threadIdx.x], sh[threadIdx.x + stride], gamma);
+        __syncthreads();
+    }
+    acc = sh[0];
+}
+
+__global__ void __launch_bounds__(kBlock) k_ep1(DevNet g, DevState s, float gamma, int lse) {
+    EpAcc acc = ep_identity();
+    const double gm = gamma;
+    for (int e = blockIdx.x * kBlock + threadIdx.x; e < g.E; e += gridDim.x * kBlock) {
+        const int p = g.ep_pin[e];
+        const float4 con = reinterpret_cast<const float4*>(g.ep_rat)[e];
+        const float4 at = reinterpret_cast<const float4*>(s.at)[p];
+        const float se = fminf(at.x - con.x, at.y - con.y);
+        const float sl = fminf(con.z - at.z, con.w - at.w);
+        s.ep_slack[e] = make_float2(se, sl);
+        EpAcc b = ep_identity();
+        b.wns_e = se;
+        b.wns_l = sl;
+        b.tns_e = fmin((double)se, 0.0);
+        b.tns_l = fmin((double)sl, 0.0);
+        b.viol = sl < 0.f ? 1.0 : 0.0;
+        if (lse) {
+            const float2 z = reinterpret_cast<const float2*>(s.ats)[p];
+            const double sr = (double)con.z - z.x, sf = (double)con.w - z.y;
+            b.tns_g = softmin3(sr, sf, 0.0, gm);
+            b.wmin = fmin(sr, sf);
+            b.wsum = exp(-(sr - b.wmin) / gm) + exp(-(sf - b.wmin) / gm);
+        }
+        ep_merge(acc, b, gm);
+    }
+    ep_block_reduce(acc, gm);
+    if (threadIdx.x == 0) reinterpret_cast<EpAcc*>(s.red)[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kBlock) k_ep2(DevNet g, DevState s, float gamma, int lse, int nparts) {
+    EpAcc acc = ep_identity();
+    if ((int)threadIdx.x < nparts) acc = reinterpret_cast<const EpAcc*>(s.red)[threadIdx.x];
+    ep_block_reduce(acc, gamma);
+    if (threadIdx.x == 0) {
+        double* o = s.summary;
+        o[STA_SUM_WNS_EARLY] = acc.wns_e;
+        o[STA_SUM_TNS_EARLY] = acc.tns_e;
+        o[STA_SUM_WNS_LATE] = acc.wns_l;
+        o[STA_SUM_TNS_LATE] = acc.tns_l;
+        o[STA_SUM_TNS_GAMMA] = lse ? acc.tns_g : 0.0;
+        o[STA_SUM_WNS_GAMMA] = (lse && acc.wsum > 0.0) ? acc.wmin - (double)gamma * log(acc.wsum) : (double)kInf;
+        o[STA_SUM_LATE_VIOLATIONS] = acc.viol;
+        o[STA_SUM_NUM_ENDPOINTS] = g.E;
+    }
+}
+
+// Adjoint seeds at the endpoints: d loss / d ats = -(w_tns dTNS_g/ds + w_wns dWNS_g/ds).
+__global__ void __launch_bounds__(kBlock) k_seed(DevNet g, DevState s, float gamma) {
+    const double gm = gamma, W = s.summary[STA_SUM_WNS_GAMMA];
+    const double wt = s.params[0], ww = s.params[1];
+    for (int e = blockIdx.x * kBlock + threadIdx.x; e < g.E; e += gridDim.x * kBlock) {
+        const int p = g.ep_pin[e];
+        const float4 con = reinterpret_cast<const float4*>(g.ep_rat)[e];
+        const float2 z = reinterpret_cast<const float2*>(s.ats)[p];
+        const double sr = (double)con.z - z.x, sf = (double)con.w - z.y;
+        const double te = softmin3(sr, sf, 0.0, gm);
+        double gr = wt * exp(-(sr - te) / gm), gf = wt * exp(-(sf - te) / gm);
+        if (isfinite(W)) {
+            gr += ww * exp(-(sr - W) / gm);
+            gf += ww * exp(-(sf - W) / gm);
+        }
+        reinterpret_cast<float2*>(s.g_ats)[p] = make_float2((float)-gr, (float)-gf);
+    }
+}
+
+__global__ void k_set_weights(float* params, const float* w_dev, float w0, float w1) {
+    if (w_dev) {
+        params[0] = w_dev[0];
+        params[1] = w_dev[1];
+    } else {
+        params[0] = w0;
+        params[1] = w1;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_scatter(DevNet g, const float* __restrict__ in, float* __restrict__ out,
+                                                    int k, int np) {
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < np * k; i += gridDim.x * kBlock) {
+        const int p = i / k, q = i - p * k;
+        out[(size_t)g.pin_orig[p] * k + q] = in[i];
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_pin_slack(DevNet g, DevState s, float2* __restrict__ out) {
+    for (int p = blockIdx.x * kBlock + threadIdx.x; p < g.P; p += gridDim.x * kBlock) {
+        const float4 at = reinterpret_cast<const float4*>(s.at)[p];
+        const float4 rt = reinterpret_cast<const float4*>(s.rat)[p];
+        out[g.pin_orig[p]] = make_float2(fminf(at.x - rt.x, at.y - rt.y), fminf(rt.z - at.z, rt.w - at.w));
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_init_ats(DevState s, int P) {
+    for (int p = blockIdx.x * kBlock + threadIdx.x; p < P; p += gridDim.x * kBlock)
+        reinterpret_cast<float2*>(s.ats)[p] = reinterpret_cast<const float2*>(s.at)[2 * p + 1];
+}
+
+int grid_for(long long n) {
+    long long b = (n + kBlock - 1) / kBlock;
+    if (b < 1) b = 1;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)b;
+}
+
+}  // namespace
+
+void launch_gather_xy(const DevNet& g, const DevState& s, const float2* xy_user, cudaStream_t st) {
+    if (g.P == 0) return;
+    k_gather_xy<<<grid_for(g.P), kBlock, 0, st>>>(g, s, xy_user);
+}
+
+void launch_rc(const DevNet& g, const DevState& s, int nw, int nc, cudaStream_t st) {
+    const int blocks = (nw + kWarpsPerBlock - 1) / kWarpsPerBlock + nc;
+    if (blocks == 0) return;
+    k_rc<<<blocks, kBlock, 0, st>>>(g, s, nw, nc);
+}
+
+void launch_fwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0, int nc, float gamma, int lse,
+                      cudaStream_t st) {
+    const int blocks = (nw + kWarpsPerBlock - 1) / kWarpsPerBlock + nc;
+    if (blocks == 0) return;
+    k_fwd<<<blocks, kBlock, 0, st>>>(g, s, w0, nw, c0, nc, gamma, lse);
+}
+
+void launch_endpoints(const DevNet& g, const DevState& s, float gamma, int lse, cudaStream_t st) {
+    k_ep1<<<kRedBlocks, kBlock, 0, st>>>(g, s, gamma, lse);
+    k_ep2<<<1, kBlock, 0, st>>>(g, s, gamma, lse, kRedBlocks);
+}
+
+void launch_bwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0, int nc, float gamma, int mode,
+                      cudaStream_t st) {
+    const int blocks = (nw + kWarpsPerBlock - 1) / kWarpsPerBlock + nc;
+    if (blocks == 0) return;
+    k_bwd<<<blocks, kBlock, 0, st>>>(g, s, w0, nw, c0, nc, gamma, mode);
+}
+
+void launch_set_weights(const DevState& s, const float* w_dev, float w0, float w1, cudaStream_t st) {
+    k_set_weights<<<1, 1, 0, st>>>(s.params, w_dev, w0, w1);
+}
+
+void launch_seed(const DevNet& g, const DevState& s, float gamma, cudaStream_t st) {
+    if (g.E == 0) return;
+    k_seed<<<grid_for(g.E), kBlock, 0, st>>>(g, s, gamma);
+}
+
+void launch_scatter(const DevNet& g, const float* in, float* out, int k, int np, cudaStream_t st) {
+    if (np == 0) return;
+    k_scatter<<<grid_for((long long)np * k), kBlock, 0, st>>>(g, in, out, k, np);
+}
+
+void launch_pin_slack(const DevNet& g, const DevState& s, float* out, cudaStream_t st) {
+    if (g.P == 0) return;
+    k_pin_slack<<<grid_for(g.P), kBlock, 0, st>>>(g, s, reinterpret_cast<float2*>(out));
+}
+
+void launch_init_ats(const DevState& s, int P, cudaStream_t st) {
+    if (P == 0) return;
+    k_init_ats<<<grid_for(P), kBlock, 0, st>>>(s, P);
+}
+
+}  // namespace sta

@@ -1,0 +1,64 @@
+// kernels.h -- device views of a handle's buffers and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sta_internal.h"
+
+namespace sta {
+
+// Read-only topology, library and constraints (internal order).
+struct DevNet {
+    const int32_t* net_ptr;      // [N+1]
+    const int32_t* net_drv;      // [N]
+    const int32_t* net_arc_ptr;  // [N+1]
+    const int32_t* arc_pin;      // [A]
+    const int32_t* pin_orig;     // [P]
+    const float* pin_cap;        // [P]
+    const int32_t* wtask;        // [2W]
+    const int32_t* ctask;        // [Cb]
+    const float* lib_idx;        // [T*16]
+    const float* lib_inv;        // [T*16]
+    const int32_t* lib_unate;    // [T]
+    const float* lib_tab;        // [T*4*2*98]
+    const int32_t* ep_pin;       // [E]
+    const float* ep_rat;         // [E*4]
+    float r, c;                  // Ohm/um, fF/um
+    int32_t P, Pnet, N, E;
+};
+
+// Mutable per-call state (internal order unless stated).
+struct DevState {
+    float2* xy;        // [P] positions
+    float* load;       // [N] net load (Eq. 1 at the driver)
+    float2* wdi;       // [P] (wire delay, impulse) at sink pins (Eqs. 2-3)
+    float* at;         // [P*4]
+    float* slew;       // [P*4]
+    float* ats;        // [P*2] late rise/fall LSE arrival time (Eq. 4)
+    float* adel;       // [A*4] cell-arc delays
+    float* rat;        // [P*4]
+    float* g_ats;      // [P*2] adjoint of ats
+    float* g_slew;     // [P*2] adjoint of the late slews
+    float2* grad;      // [P] d loss / d (x, y), ORIGINAL pin order
+    float2* ep_slack;  // [E] (early, late)
+    double* red;       // [kRedBlocks * 8] endpoint-reduction partials (scratch)
+    double* summary;   // [STA_SUM_COUNT]
+    float* params;     // [4] w_tns, w_wns
+};
+
+void launch_gather_xy(const DevNet& g, const DevState& s, const float2* xy_user, cudaStream_t st);
+void launch_rc(const DevNet& g, const DevState& s, int nw, int nc, cudaStream_t st);
+void launch_fwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0, int nc, float gamma,
+                      int lse, cudaStream_t st);
+void launch_endpoints(const DevNet& g, const DevState& s, float gamma, int lse, cudaStream_t st);
+// mode bit 1 = required times, bit 2 = adjoint
+void launch_bwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0, int nc, float gamma,
+                      int mode, cudaStream_t st);
+void launch_set_weights(const DevState& s, const float* w_dev, float w0, float w1, cudaStream_t st);
+void launch_seed(const DevNet& g, const DevState& s, float gamma, cudaStream_t st);
+// out[orig(p)*k + q] = in[p*k + q] for the first `np` internal pins
+void launch_scatter(const DevNet& g, const float* in, float* out, int k, int np, cudaStream_t st);
+void launch_pin_slack(const DevNet& g, const DevState& s, float* out, cudaStream_t st);
+void launch_init_ats(const DevState& s, int P, cudaStream_t st);
+
+}  // namespace sta

@@ -1,0 +1,83 @@
+// sta_internal.h -- layout shared by the host builder and the device kernels.
+//
+// Device layout ("internal order"), built once per netlist by builder.cpp:
+//   nets    sorted by (level, size class, original id); size class 0 = at most
+//           kWarpPins pins (packed several to a warp), 1 = larger (one thread
+//           block each).  Every cell output that drives no net gets an internal
+//           net with no sinks, so that every cell is evaluated by exactly one net.
+//   pins    net-contiguous: each net's driver then its sinks by ascending
+//           original id; pins on no net (asserted clock pins) come last.
+//   arcs    grouped by the net their cell drives, in the cell's input order.
+// All per-pin state is structure-of-arrays in internal order; float4 holds the
+// four timing conditions (cond = 2*el + rf), float2 the two late ones.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sta.h"
+
+namespace sta {
+
+constexpr int kWarpPins = 32;       // nets of <= 32 pins go to warp tasks
+constexpr int kWarpNets = 8;        // at most 8 nets per warp task (4 lanes per net)
+constexpr int kBlock = 256;         // threads per block in every task kernel
+constexpr int kWarpsPerBlock = kBlock / 32;
+constexpr int kLibStride = 16;      // floats per type in lib_idx / lib_inv
+constexpr int kTabPerArcRf = 2 * STA_LUT * STA_LUT;  // delay table then slew table
+constexpr int kRedBlocks = 152;     // endpoint reduction partials (one per SM)
+constexpr float kKrc = 1e-3f;       // Ohm * fF in ps
+
+struct Layout {
+    int32_t P = 0;       // pins
+    int32_t Pnet = 0;    // pins on nets (prefix of the internal order)
+    int32_t N = 0;       // internal nets (real + one per dangling cell output)
+    int32_t Nreal = 0;   // nets of the description
+    int32_t L = 0;       // levels
+    int32_t A = 0;       // arcs
+    int32_t E = 0;       // endpoints
+    int32_t T = 0;       // library types
+
+    std::vector<int32_t> net_ptr;      // [N+1] internal pin range
+    std::vector<int32_t> net_drv;      // [N] cell type if cell-driven, -1 if asserted
+    std::vector<int32_t> net_arc_ptr;  // [N+1]
+    std::vector<int32_t> arc_pin;      // [A] internal input pin of each arc
+    std::vector<int32_t> pin_orig;     // [P] original id of each internal pin
+    std::vector<float> pin_cap;        // [P]
+    std::vector<int32_t> lvl_wtask;    // [L+1] warp-task ranges per level
+    std::vector<int32_t> lvl_ctask;    // [L+1] block-task ranges per level
+    std::vector<int32_t> wtask;        // [2*W] (first net, number of nets)
+    std::vector<int32_t> ctask;        // [Cb] net of each block task
+
+    // constant per-pin state written once at creation
+    std::vector<float> at0, slew0;     // [P*4] asserted values (0 elsewhere)
+    std::vector<float> rat0;           // [P*4] endpoint constraint, else -inf/+inf
+    std::vector<int32_t> ep_pin;       // [E] internal pin of each endpoint
+    std::vector<float> ep_rat;         // [E*4]
+
+    // library, device form
+    std::vector<float> lib_idx;        // [T*16] slew index (0..6), load index (8..14)
+    std::vector<float> lib_inv;        // [T*16] 1/(idx[k+1]-idx[k]) for k = 0..5 (slew), 8..13 (load)
+    std::vector<int32_t> lib_unate;    // [T] bit a set = arc a negative unate
+    std::vector<float> lib_tab;        // [T*4*2*98] per (type, arc, rf_out): delay 7x7, slew 7x7
+
+    float r_per_um = 0.f, c_per_um = 0.f;
+};
+
+// Validate and levelize (Kahn sweep over nets).  net_level receives the level
+// of every description net and, if dangling != nullptr, of every dangling cell
+// (cells whose output drives no net) in cell order.  Returns the level count
+// through num_levels.
+StaStatus levelize(const StaNetlistDesc& nl, const StaLibrary* lib, std::vector<int32_t>& net_level,
+                   std::vector<int32_t>* dangling_cells, std::vector<int32_t>* dangling_level,
+                   int32_t& num_levels, std::string& err);
+
+// Full host-side layout for the device.
+StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& out, std::string& err);
+
+// Processing order of description nets and device pin order (sta_levelize).
+StaStatus ordering(const StaNetlistDesc& nl, std::vector<int32_t>& net_level, int32_t& num_levels,
+                   std::vector<int32_t>& net_order, std::vector<int32_t>& pin_order, std::string& err);
+
+}  // namespace sta

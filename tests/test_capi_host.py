@@ -1,0 +1,113 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+entry point include/sta.h declares; the host-side levelization and layout
+order are bit-exact against independent computations; malformed netlists are
+rejected with the documented status codes."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import netgen
+import oracle
+from tests import _tinydag as td
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sta():
+    from paper_2603_28381_gb300 import build_ext
+    build_ext.build()
+    import paper_2603_28381_gb300 as mod
+    return mod
+
+
+def test_library_exports_every_declared_symbol(sta):
+    header = open(os.path.join(ROOT, "include", "sta.h")).read()
+    declared = set(re.findall(r"^\S.*?\b(sta_\w+)\s*\(", header, flags=re.M))
+    assert {"sta_create", "sta_forward", "sta_backward_grad", "sta_set_positions",
+            "sta_query_summary", "sta_destroy"} <= declared
+    lib = ctypes.CDLL(sta._sta.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(lib, name), f"libsta.so does not export {name}"
+    assert set(sta._sta.EXPORTS) == declared
+    assert sta.sta_abi_version() == 1
+
+
+@pytest.mark.parametrize("make", [lambda: netgen.tiny_design(0), lambda: netgen.tiny_design(5),
+                                  lambda: td.tiny_netlist(3),
+                                  lambda: netgen.superblue_like(2, scale=0.01, depth=25)])
+def test_levelize_bit_exact_against_oracle_dfs(sta, make):
+    w = make()
+    nl = w.netlist
+    lv, L, order, pins = sta.sta_levelize(nl)
+    ref = oracle.levels(nl)
+    np.testing.assert_array_equal(lv, ref)
+    assert L == ref.max() + 1
+    # processing order: (level, nets of > 32 pins after the others, id)
+    size = np.diff(nl.net_ptr)
+    expect = np.lexsort((np.arange(nl.num_nets), size > 32, ref))
+    np.testing.assert_array_equal(order, expect)
+    # device pin order: per net in processing order, driver then sinks ascending
+    exp_pins = []
+    for n in expect:
+        seg = nl.net_pins[nl.net_ptr[n]:nl.net_ptr[n + 1]]
+        exp_pins.append(seg[:1])
+        exp_pins.append(np.sort(seg[1:]))
+    np.testing.assert_array_equal(pins, np.concatenate(exp_pins))
+
+
+def test_levelize_rejects_cycles_and_malformed_netlists(sta):
+    b = netgen.NetlistBuilder()
+    i0, o0, i1, o1 = (b.pin(1.0) for _ in range(4))
+    b.net(o0, [i1])
+    b.net(o1, [i0])
+    b.cell(0, [i0], o0)
+    b.cell(0, [i1], o1)
+    nl, _ = b.build()
+    with pytest.raises(sta.StaError) as e:
+        sta.sta_levelize(nl)
+    assert e.value.status == 2  # STA_ERR_NOT_DAG
+    # a pin on two nets
+    b = netgen.NetlistBuilder()
+    d, s = b.pin(), b.pin(1.0)
+    b.net(d, [s])
+    b.net(d, [s])
+    b.start(d)
+    nl, _ = b.build()
+    with pytest.raises(sta.StaError) as e:
+        sta.sta_levelize(nl)
+    assert e.value.status == 1  # STA_ERR_INVALID_ARG
+    assert "two nets" in sta.sta_last_error()
+    # an endpoint that is a cell input
+    b = netgen.NetlistBuilder()
+    d, s, o, t = b.pin(), b.pin(1.0), b.pin(), b.pin(1.0)
+    b.net(d, [s])
+    b.cell(0, [s], o)
+    b.net(o, [t])
+    b.start(d)
+    b.end(s)
+    nl, _ = b.build()
+    with pytest.raises(sta.StaError) as e:
+        sta.sta_levelize(nl)
+    assert e.value.status == 1
+    # an orphan pin (no arrival source)
+    b = netgen.NetlistBuilder()
+    b.pin()
+    nl, _ = b.build()
+    with pytest.raises(sta.StaError):
+        sta.sta_levelize(nl)
+
+
+def test_product_path_fails_loudly_without_gpu(sta):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    w = netgen.tiny_design(0)
+    with pytest.raises(RuntimeError):
+        sta.StaEngine(w.netlist, w.library)
+    with pytest.raises(sta.StaError) as e:
+        sta._sta.sta_create(w.netlist, w.library)
+    assert e.value.status == 4  # STA_ERR_CUDA, no CPU fallback

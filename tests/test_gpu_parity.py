@@ -1,0 +1,144 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle,
+element by element, at the tolerances stated in tests/_parity.py."""
+import numpy as np
+import pytest
+
+import netgen
+import oracle
+from tests import _parity as tp
+from tests import _tinydag as td
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2603_28381_gb300 import build_ext
+    build_ext.build()
+
+
+def _check(w_or_parts, gamma=10.0, weights=(1.0, 0.5), **kw):
+    if isinstance(w_or_parts, tuple):
+        nl, xy, lib = w_or_parts
+    else:
+        nl, xy, lib = w_or_parts.netlist, w_or_parts.xy, w_or_parts.library
+    ora = oracle.sta(nl, lib, xy, gamma, *weights)
+    gpu = tp.run_gpu(nl, lib, xy, gamma, weights, **kw)
+    return tp.assert_parity(gpu, ora), gpu, ora
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tiny_design(seed):
+    _check(netgen.tiny_design(seed))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tiny_dags_slew_independent_library(seed):
+    w = td.tiny_netlist(seed)
+    lib, _, _ = td.linear_library(5, [1, 2, 3, 4, 1], seed=seed)
+    _check((w.netlist, w.xy, lib), gamma=3.0)
+
+
+@pytest.mark.parametrize("idx", range(3))
+def test_edge_netlists(idx):
+    name, nl, xy, lib = tp.edge_netlists()[idx]
+    errs, gpu, ora = _check((nl, xy, lib))
+    if name == "no_endpoints":
+        assert gpu["summary"]["tns_late"] == 0.0 and np.isinf(gpu["summary"]["wns_late"])
+        assert np.all(gpu["grad"] == 0.0)
+
+
+@pytest.mark.parametrize("gamma", [1.0, 50.0])
+def test_mid_size_many_tiles(gamma):
+    # ~50k pins over 40 levels: thousands of warp tasks, block tasks for the
+    # power-law nets above 32 pins and the 400-sink primary-input nets
+    _check(netgen.superblue_like(3, scale=0.02, depth=40), gamma=gamma, weights=(0.8, 0.2))
+
+
+def test_full_size_superblue_like():
+    # the benchmark's workload and launch configuration (CUDA graphs), all outputs
+    w = netgen.superblue_like(1)
+    errs, gpu, ora = _check(w)
+    assert gpu["summary"]["num_endpoints"] == w.netlist.end_pins.shape[0]
+
+
+def test_deterministic_graphs_and_host_input():
+    w = netgen.superblue_like(4, scale=0.01, depth=30)
+    a = tp.run_gpu(w.netlist, w.library, w.xy)
+    b = tp.run_gpu(w.netlist, w.library, w.xy)
+    c = tp.run_gpu(w.netlist, w.library, w.xy, use_graphs=False)
+    d = tp.run_gpu(w.netlist, w.library, w.xy, host_xy=True)
+    for k in ("at", "slew", "rat", "ats", "slack", "ep_slack", "grad"):
+        for other in (b, c, d):
+            assert np.array_equal(a[k], other[k], equal_nan=True), k
+    assert a["summary"] == b["summary"] == c["summary"] == d["summary"]
+
+
+def test_repeated_calls_follow_new_positions():
+    import paper_2603_28381_gb300 as sta
+    w = netgen.tiny_design(2)
+    eng = sta.StaEngine(w.netlist, w.library)
+    rng = np.random.default_rng(0)
+    for it in range(3):
+        xy = (w.xy + rng.normal(0, 20, w.xy.shape)).astype(np.float32)
+        gpu = tp.run_gpu(w.netlist, w.library, xy, engine=eng)
+        tp.assert_parity(gpu, oracle.sta(w.netlist, w.library, xy, 10.0, 1.0, 0.5))
+    eng.close()
+
+
+def test_gradient_against_finite_differences():
+    # FP64 central differences (h = 1e-3 um) on 200 random pins; entries whose
+    # perturbation changes a table segment, slew argmax or sign are excluded
+    w = netgen.tiny_design(0)
+    gamma, wts = 10.0, (1.0, 0.5)
+    gpu = tp.run_gpu(w.netlist, w.library, w.xy, gamma, wts)
+    pins = np.random.default_rng(2).choice(w.netlist.num_pins, 200, replace=False)
+    fd, ok = oracle.finite_difference(w.netlist, w.library, w.xy, pins, gamma, *wts)
+    assert ok.mean() > 0.8
+    scale = max(np.abs(fd[ok]).max(), 1e-20)
+    err = np.abs(gpu["grad"][pins] - fd)[ok]
+    assert err.max() <= tp.GRAD_RTOL * scale, (err.max(), scale)
+
+
+def test_autograd_function_matches_engine():
+    import torch
+
+    import paper_2603_28381_gb300 as sta
+    w = netgen.tiny_design(1)
+    eng = sta.StaEngine(w.netlist, w.library)
+    xy = torch.tensor(w.xy, device="cuda", requires_grad=True)
+    tns_g, wns_g = sta.timing_loss(xy, eng, 10.0)
+    loss = 2.0 * tns_g - 0.5 * wns_g
+    loss.backward()
+    ora = oracle.sta(w.netlist, w.library, w.xy, 10.0, 2.0, -0.5)
+    assert abs(tns_g.item() - ora["summary"]["tns_gamma"]) <= 1e-4 * abs(ora["summary"]["tns_gamma"])
+    g = xy.grad.cpu().numpy()
+    assert np.abs(g - ora["grad"]).max() <= tp.GRAD_RTOL * np.abs(ora["grad"]).max()
+    eng.close()
+
+
+def test_call_order_and_argument_errors():
+    import torch
+
+    import paper_2603_28381_gb300 as sta
+    w = netgen.tiny_design(0)
+    eng = sta.StaEngine(w.netlist, w.library)
+    with pytest.raises(sta.StaError) as e:
+        eng.forward()
+    assert e.value.status == 6  # STA_ERR_STATE: positions first
+    eng.set_positions(w.xy)
+    with pytest.raises(sta.StaError) as e:
+        eng.backward_grad()
+    assert e.value.status == 6  # gradient before an LSE forward
+    with pytest.raises(sta.StaError) as e:
+        eng.forward(gamma=0.0)
+    assert e.value.status == 1
+    eng.forward(gamma=10.0, lse=False, rat=False)
+    with pytest.raises(sta.StaError) as e:
+        eng.backward_grad()
+    assert e.value.status == 6
+    with pytest.raises(sta.StaError) as e:
+        eng.pins(at=False, slew=False, rat=True, ats=False, slack=False)
+    assert e.value.status == 6  # required times were not propagated
+    torch.cuda.synchronize()
+    eng.close()
