@@ -129,19 +129,17 @@ struct ProfScope {
     cudaStream_t st;
     size_t i;
     ProfScope(StaHandle* h, StaHandle::Prof* p, int kind, cudaStream_t s) : pr(h->profile ? p : nullptr), st(s), i(0) {
-        if (!pr) return;
-        i = pr->next++;
-        while (pr->ev.size() < 2 * pr->next) {
-            cudaEvent_t e = nullptr;
-            cudaEventCreate(&e);
-            pr->ev.push_back(e);
+        if (!pr || 2 * pr->next + 1 >= pr->ev.size()) {  // events are made at creation
+            pr = nullptr;
+            return;
         }
-        if (pr->kind.size() < pr->next) pr->kind.resize(pr->next);
+        i = pr->next++;
         pr->kind[i] = kind;
-        cudaEventRecord(pr->ev[2 * i], st);
+        // External: under stream capture this becomes an event-record node
+        cudaEventRecordWithFlags(pr->ev[2 * i], st, cudaEventRecordExternal);
     }
     ~ProfScope() {
-        if (pr) cudaEventRecord(pr->ev[2 * i + 1], st);
+        if (pr) cudaEventRecordWithFlags(pr->ev[2 * i + 1], st, cudaEventRecordExternal);
     }
 };
 
@@ -319,6 +317,19 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         cudaEventCreateWithFlags(&h->ev_fwd, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_bwd, cudaEventDisableTiming) != cudaSuccess)
         return fail(set_err(STA_ERR_CUDA, "stream/event creation failed"));
+    if (h->profile) {  // event pairs for every launch of each sequence, made before any capture
+        const size_t nl = (size_t)L.L;
+        const std::pair<StaHandle::Prof*, size_t> sizes[] = {
+            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 2}, {&h->prof_rat, nl}, {&h->prof_adj, nl + 1}};
+        for (const auto& ps : sizes) {
+            ps.first->kind.assign(ps.second, 0);
+            for (size_t k = 0; k < 2 * ps.second; ++k) {
+                cudaEvent_t e = nullptr;
+                if (cudaEventCreate(&e) != cudaSuccess) return fail(set_err(STA_ERR_CUDA, "cudaEventCreate failed"));
+                ps.first->ev.push_back(e);
+            }
+        }
+    }
     ce = cudaDeviceSynchronize();
     if (ce != cudaSuccess) return fail(set_err(STA_ERR_CUDA, std::string("init: ") + cudaGetErrorString(ce)));
     cudaEventRecord(h->ev_at, 0);
@@ -542,7 +553,7 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
     if (!h->profile) return set_err(STA_ERR_STATE, "handle was created without StaOptions.profile");
     CUDA_TRY(cudaDeviceSynchronize());
     for (StaHandle::Prof* pr : {&h->prof_pos, &h->prof_fwd, &h->prof_rat, &h->prof_adj}) {
-        for (size_t i = 0; i < pr->kind.size() && 2 * i + 1 < pr->ev.size(); ++i) {
+        for (size_t i = 0; i < pr->next && 2 * i + 1 < pr->ev.size(); ++i) {
             float t = 0.f;
             if (cudaEventElapsedTime(&t, pr->ev[2 * i], pr->ev[2 * i + 1]) == cudaSuccess) ms[pr->kind[i]] += t;
             else cudaGetLastError();

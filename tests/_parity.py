@@ -121,11 +121,12 @@ def _close(name, gpu, ora, tol):
     inf_o = ~np.isfinite(ora)
     assert np.array_equal(inf_o, ~np.isfinite(gpu)), f"{name}: infinite entries differ"
     assert np.array_equal(ora[inf_o], gpu[inf_o]), f"{name}: infinite signs differ"
-    if (~inf_o).any():
-        err = np.abs(gpu - ora)[~inf_o]
-        k = int(np.argmax(err))
-        assert err.max() <= tol, f"{name}: max err {err.max():.4g} > tol {tol:.4g} (index {k})"
-    return float(np.abs(gpu - ora)[~inf_o].max()) if (~inf_o).any() else 0.0
+    if not (~inf_o).any():
+        return 0.0
+    err = np.abs(gpu[~inf_o] - ora[~inf_o])
+    k = int(np.argmax(err))
+    assert err.max() <= tol, f"{name}: max err {err.max():.4g} > tol {tol:.4g} (index {k})"
+    return float(err.max())
 
 
 def assert_parity(gpu, ora, grad=True):

@@ -18,8 +18,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def sta():
-    from paper_2603_28381_gb300 import build_ext
-    build_ext.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_2603_28381_gb300 as mod
     return mod
 

@@ -13,8 +13,8 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module", autouse=True)
 def built():
-    from paper_2603_28381_gb300 import build_ext
-    build_ext.build()
+    import __graft_entry__
+    __graft_entry__.build()
 
 
 def _check(w_or_parts, gamma=10.0, weights=(1.0, 0.5), **kw):
