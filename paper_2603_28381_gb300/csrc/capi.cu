@@ -135,11 +135,18 @@ struct ProfScope {
         }
         i = pr->next++;
         pr->kind[i] = kind;
-        // External: under stream capture this becomes an event-record node
-        cudaEventRecordWithFlags(pr->ev[2 * i], st, cudaEventRecordExternal);
+        record(pr->ev[2 * i]);
     }
     ~ProfScope() {
-        if (pr) cudaEventRecordWithFlags(pr->ev[2 * i + 1], st, cudaEventRecordExternal);
+        if (pr) record(pr->ev[2 * i + 1]);
+    }
+    // under stream capture an event-record node needs the External flag; outside
+    // capture that flag is not accepted, so a plain record is used
+    void record(cudaEvent_t e) const {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+        else cudaEventRecord(e, st);
     }
 };
 
