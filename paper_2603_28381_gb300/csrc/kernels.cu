@@ -588,44 +588,48 @@ __global__ void __launch_bounds__(kBlock) k_bwd(DevNet g, DevState s, int w0, in
 
 // ---------------------------------------------------------------------------
 // Endpoints: slack, WNS, TNS and the smoothed TNS_gamma / WNS_gamma, by a
-// two-pass fixed-order reduction (partials per block in s.red).
+// two-pass fixed-order reduction (partials per block in s.red).  Exponentials
+// and logarithms are single precision (FP64 transcendentals are slow on this
+// part); every sum over endpoints is accumulated in double.
 //   TNS_gamma = sum_e softmin_gamma(s_rise, s_fall, 0),
 //   WNS_gamma = softmin_gamma over every endpoint rise/fall slack,
 //   softmin_gamma(x) = -LSE_gamma(-x), stabilised by the minimum (Eq. 4).
 // ---------------------------------------------------------------------------
 struct EpAcc {
-    double tns_e, tns_l, tns_g, wsum;  // wsum = sum exp(-(s - wmin) / gamma)
-    double wns_e, wns_l, wmin, viol;
+    double tns_e, tns_l, tns_g, viol;  // sums in double (deterministic order)
+    float wns_e, wns_l, wmin, wsum;    // wsum = sum exp(-(s - wmin) / gamma)
 };
 
-__device__ __forceinline__ void ep_merge(EpAcc& a, const EpAcc& b, double gamma) {
+__device__ __forceinline__ void ep_merge(EpAcc& a, const EpAcc& b, float gamma) {
     a.tns_e += b.tns_e;
     a.tns_l += b.tns_l;
     a.tns_g += b.tns_g;
     a.viol += b.viol;
-    a.wns_e = fmin(a.wns_e, b.wns_e);
-    a.wns_l = fmin(a.wns_l, b.wns_l);
-    const double m = fmin(a.wmin, b.wmin);
-    double sum = 0.0;
-    if (a.wsum > 0.0) sum += a.wsum * exp(-(a.wmin - m) / gamma);
-    if (b.wsum > 0.0) sum += b.wsum * exp(-(b.wmin - m) / gamma);
+    a.wns_e = fminf(a.wns_e, b.wns_e);
+    a.wns_l = fminf(a.wns_l, b.wns_l);
+    const float m = fminf(a.wmin, b.wmin);
+    float sum = 0.f;
+    if (a.wsum > 0.f) sum += a.wsum * expf(-(a.wmin - m) / gamma);
+    if (b.wsum > 0.f) sum += b.wsum * expf(-(b.wmin - m) / gamma);
     a.wsum = sum;
     a.wmin = m;
 }
 
-__device__ __forceinline__ double softmin3(double a, double b, double c, double gamma) {
-    const double m = fmin(a, fmin(b, c));
-    return m - gamma * log(exp(-(a - m) / gamma) + exp(-(b - m) / gamma) + exp(-(c - m) / gamma));
+// softmin_gamma(a, b, 0) = m - gamma log(sum exp(-(x - m) / gamma)), m = min
+__device__ __forceinline__ float softmin3(float a, float b, float gamma) {
+    const float m = fminf(fminf(a, b), 0.f);
+    return m - gamma * logf(expf(-(a - m) / gamma) + expf(-(b - m) / gamma) + expf(m / gamma));
 }
 
 __device__ __forceinline__ EpAcc ep_identity() {
     EpAcc a;
-    a.tns_e = a.tns_l = a.tns_g = a.wsum = a.viol = 0.0;
-    a.wns_e = a.wns_l = a.wmin = (double)kInf;
+    a.tns_e = a.tns_l = a.tns_g = a.viol = 0.0;
+    a.wns_e = a.wns_l = a.wmin = kInf;
+    a.wsum = 0.f;
     return a;
 }
 
-__device__ void ep_block_reduce(EpAcc& acc, double gamma) {
+__device__ void ep_block_reduce(EpAcc& acc, float gamma) {
     __shared__ EpAcc sh[kBlock];
     sh[threadIdx.x] = acc;
     __syncthreads();
@@ -638,7 +642,6 @@ __device__ void ep_block_reduce(EpAcc& acc, double gamma) {
 
 __global__ void __launch_bounds__(kBlock) k_ep1(DevNet g, DevState s, float gamma, int lse) {
     EpAcc acc = ep_identity();
-    const double gm = gamma;
     for (int e = blockIdx.x * kBlock + threadIdx.x; e < g.E; e += gridDim.x * kBlock) {
         const int p = g.ep_pin[e];
         const float4 con = reinterpret_cast<const float4*>(g.ep_rat)[e];
@@ -649,19 +652,19 @@ __global__ void __launch_bounds__(kBlock) k_ep1(DevNet g, DevState s, float gamm
         EpAcc b = ep_identity();
         b.wns_e = se;
         b.wns_l = sl;
-        b.tns_e = fmin((double)se, 0.0);
-        b.tns_l = fmin((double)sl, 0.0);
+        b.tns_e = fminf(se, 0.f);
+        b.tns_l = fminf(sl, 0.f);
         b.viol = sl < 0.f ? 1.0 : 0.0;
         if (lse) {
             const float2 z = reinterpret_cast<const float2*>(s.ats)[p];
-            const double sr = (double)con.z - z.x, sf = (double)con.w - z.y;
-            b.tns_g = softmin3(sr, sf, 0.0, gm);
-            b.wmin = fmin(sr, sf);
-            b.wsum = exp(-(sr - b.wmin) / gm) + exp(-(sf - b.wmin) / gm);
+            const float sr = con.z - z.x, sf = con.w - z.y;
+            b.tns_g = softmin3(sr, sf, gamma);
+            b.wmin = fminf(sr, sf);
+            b.wsum = expf(-(sr - b.wmin) / gamma) + expf(-(sf - b.wmin) / gamma);
         }
-        ep_merge(acc, b, gm);
+        ep_merge(acc, b, gamma);
     }
-    ep_block_reduce(acc, gm);
+    ep_block_reduce(acc, gamma);
     if (threadIdx.x == 0) reinterpret_cast<EpAcc*>(s.red)[blockIdx.x] = acc;
 }
 
@@ -676,7 +679,8 @@ __global__ void __launch_bounds__(kBlock) k_ep2(DevNet g, DevState s, float gamm
         o[STA_SUM_WNS_LATE] = acc.wns_l;
         o[STA_SUM_TNS_LATE] = acc.tns_l;
         o[STA_SUM_TNS_GAMMA] = lse ? acc.tns_g : 0.0;
-        o[STA_SUM_WNS_GAMMA] = (lse && acc.wsum > 0.0) ? acc.wmin - (double)gamma * log(acc.wsum) : (double)kInf;
+        o[STA_SUM_WNS_GAMMA] =
+            (lse && acc.wsum > 0.f) ? (double)acc.wmin - (double)gamma * log((double)acc.wsum) : (double)kInf;
         o[STA_SUM_LATE_VIOLATIONS] = acc.viol;
         o[STA_SUM_NUM_ENDPOINTS] = g.E;
     }
@@ -684,20 +688,20 @@ __global__ void __launch_bounds__(kBlock) k_ep2(DevNet g, DevState s, float gamm
 
 // Adjoint seeds at the endpoints: d loss / d ats = -(w_tns dTNS_g/ds + w_wns dWNS_g/ds).
 __global__ void __launch_bounds__(kBlock) k_seed(DevNet g, DevState s, float gamma) {
-    const double gm = gamma, W = s.summary[STA_SUM_WNS_GAMMA];
-    const double wt = s.params[0], ww = s.params[1];
+    const float W = (float)s.summary[STA_SUM_WNS_GAMMA];
+    const float wt = s.params[0], ww = s.params[1];
     for (int e = blockIdx.x * kBlock + threadIdx.x; e < g.E; e += gridDim.x * kBlock) {
         const int p = g.ep_pin[e];
         const float4 con = reinterpret_cast<const float4*>(g.ep_rat)[e];
         const float2 z = reinterpret_cast<const float2*>(s.ats)[p];
-        const double sr = (double)con.z - z.x, sf = (double)con.w - z.y;
-        const double te = softmin3(sr, sf, 0.0, gm);
-        double gr = wt * exp(-(sr - te) / gm), gf = wt * exp(-(sf - te) / gm);
+        const float sr = con.z - z.x, sf = con.w - z.y;
+        const float te = softmin3(sr, sf, gamma);
+        float gr = wt * expf(-(sr - te) / gamma), gf = wt * expf(-(sf - te) / gamma);
         if (isfinite(W)) {
-            gr += ww * exp(-(sr - W) / gm);
-            gf += ww * exp(-(sf - W) / gm);
+            gr += ww * expf(-(sr - W) / gamma);
+            gf += ww * expf(-(sf - W) / gamma);
         }
-        reinterpret_cast<float2*>(s.g_ats)[p] = make_float2((float)-gr, (float)-gf);
+        reinterpret_cast<float2*>(s.g_ats)[p] = make_float2(-gr, -gf);
     }
 }
 
