@@ -206,6 +206,39 @@ enum {
  * entries; ms may be NULL. */
 StaStatus sta_query_profile(StaHandle *h, double *ms, int32_t *launches);
 
+/* ---- Allocation-free endpoint summary.  The paper has no counterpart. ----
+ *
+ * For callers that cannot call cudaMalloc: code running while a stream is
+ * being captured into a CUDA graph (allocation cannot be captured), and
+ * processes whose device memory is fully reserved by another framework's pool
+ * allocator.  Computes, from per-pin arrays the caller holds, the same
+ * endpoint slacks, WNS, TNS and smoothed TNS/WNS that sta_forward reduces, and
+ * allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+ *
+ * at       [num_pins][4] device, arrival times (cond = 2*el + rf)
+ * ats      [num_pins][2] device, late rise/fall LSE arrival times, or NULL
+ *          (then the smoothed slots of the summary are 0 / +inf)
+ * end_pins [num_end] device, pin index of each endpoint; an index outside
+ *          [0, num_pins) gives that endpoint NaN slacks and leaves it out of the
+ *          summary (STA_SUM_NUM_ENDPOINTS counts the endpoints used)
+ * end_rat  [num_end][4] device, endpoint constraints as in StaNetlistDesc
+ * ep_slack [num_end][2] device output (early, late); summary [STA_SUM_COUNT]
+ *          device output, same slots as sta_query_summary.
+ * Asynchronous on `stream`.  num_end may not exceed STA_NOALLOC_MAX_ENDPOINTS
+ * (STA_ERR_INVALID_ARG otherwise).
+ *
+ * Scratch: a file-scope device array of STA_NOALLOC_MAX_ENDPOINTS / 256
+ * partials (1 MiB) that every GPU loading libsta holds until the process
+ * exits.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and each call rewrites every partial it reads, so
+ * nothing needs clearing, but calls that overlap on the GPU (concurrent
+ * streams, or graphs replayed concurrently) race on it. */
+#define STA_NOALLOC_MAX_ENDPOINTS (1 << 22)
+StaStatus sta_endpoint_summary_noalloc(const float *at, const float *ats, int32_t num_pins,
+                                       const int32_t *end_pins, const float *end_rat, int32_t num_end,
+                                       float gamma, float *ep_slack, double *summary, void *stream);
+
 /* Release every resource of the handle (NULL is a no-op). */
 void sta_destroy(StaHandle *h);
 

@@ -71,6 +71,8 @@ def _load() -> ctypes.CDLL:
         "sta_levelize": ([ctypes.POINTER(StaNetlistDesc), _p, _p, _p, _p], ctypes.c_int),
         "sta_query_sizes": ([H, _p], ctypes.c_int),
         "sta_query_profile": ([H, _p, _p], ctypes.c_int),
+        "sta_endpoint_summary_noalloc": ([_p, _p, _i32, _p, _p, _i32, ctypes.c_float, _p, _p, _p],
+                                         ctypes.c_int),
         "sta_destroy": ([H], None),
         "sta_last_error": ([], ctypes.c_char_p),
         "sta_abi_version": ([], ctypes.c_int),
@@ -88,7 +90,7 @@ _lib = _load()
 EXPORTS = ("sta_create", "sta_set_positions", "sta_forward", "sta_backward_grad",
            "sta_query_summary", "sta_query_pins", "sta_query_endpoints", "sta_levelize",
            "sta_query_sizes", "sta_query_profile", "sta_stream_wait", "sta_destroy",
-           "sta_last_error", "sta_abi_version")
+           "sta_last_error", "sta_abi_version", "sta_endpoint_summary_noalloc")
 
 
 def _check(status: int, where: str) -> None:
@@ -217,3 +219,12 @@ def sta_query_profile(h: int, with_times: bool = True):
            "sta_query_profile")
     return (dict(zip(PROF_KINDS, ms.tolist())) if with_times else {},
             dict(zip(PROF_KINDS, n.tolist())))
+
+
+def sta_endpoint_summary_noalloc(at_ptr: int, ats_ptr: int, num_pins: int, end_pins_ptr: int,
+                                 end_rat_ptr: int, num_end: int, gamma: float, ep_slack_ptr: int,
+                                 summary_ptr: int, stream: int) -> None:
+    """Allocation-free endpoint summary on device arrays (see include/sta.h)."""
+    _check(_lib.sta_endpoint_summary_noalloc(at_ptr, ats_ptr, num_pins, end_pins_ptr, end_rat_ptr,
+                                             num_end, gamma, ep_slack_ptr, summary_ptr, stream),
+           "sta_endpoint_summary_noalloc")

@@ -42,6 +42,11 @@ StaStatus set_err(StaStatus st, const std::string& msg) {
 
 }  // namespace
 
+namespace sta {
+// lets other translation units of the library report through sta_last_error()
+void set_last_error_text(const std::string& msg) { g_err = msg; }
+}  // namespace sta
+
 struct StaHandle {
     Layout lay;
     DevNet g{};
