@@ -53,7 +53,8 @@ typedef enum {
     STA_ERR_NOT_DAG = 2,     /* the timing graph has a cycle */
     STA_ERR_OOM = 3,         /* device or host allocation failed */
     STA_ERR_CUDA = 4,        /* a CUDA runtime call failed */
-    STA_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired */
+    STA_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired (reported by the next
+                                synchronizing call: summary / host-output queries) */
     STA_ERR_STATE = 6        /* call out of order (e.g. gradient before forward) */
 } StaStatus;
 
@@ -93,10 +94,22 @@ typedef struct {
 } StaLibrary;
 
 typedef struct {
-    int32_t use_graphs;  /* 1 (default): replay each level sweep as a CUDA graph */
+    int32_t use_graphs;  /* 1 (default): replay each sweep as a CUDA graph */
     int32_t profile;     /* 1: bracket every launch with CUDA events (see sta_query_profile) */
-    int32_t reserved[6];
+    int32_t schedule;    /* STA_SCHED_DATAFLOW (default) or STA_SCHED_LEVELS */
+    int32_t reserved[5];
 } StaOptions;
+
+/* StaOptions.schedule.  Both compute the same quantities: arrival, slew,
+ * LSE and required times are bit-identical; gradient sums over the sinks of
+ * nets of more than 32 pins are reassociated (32-sink partials here, a
+ * 256-thread block reduction there), so gradients agree to rounding.
+ *   DATAFLOW  one persistent kernel per sweep; warp-sized tasks taken from a
+ *             queue in topological order, each waiting (bounded in time) only
+ *             for the tasks that produce its inputs.
+ *   LEVELS    one kernel launch per level per sweep (Section 3.1.2). */
+#define STA_SCHED_DATAFLOW 0
+#define STA_SCHED_LEVELS 1
 
 typedef struct StaHandle StaHandle;
 
@@ -189,12 +202,12 @@ StaStatus sta_query_sizes(const StaHandle *h, int64_t *out8);
 /* Kernel kinds reported by sta_query_profile. */
 enum {
     STA_PROF_POSITIONS = 0,  /* gather of positions into device order */
-    STA_PROF_NET_RC = 1,     /* Eqs. 1-3 over every net */
-    STA_PROF_FWD_LEVEL = 2,  /* one forward level (cell arcs, AT/slew/LSE, wire) */
+    STA_PROF_NET_RC = 1,     /* Eqs. 1-3: every net (LEVELS), nets > 32 pins (DATAFLOW) */
+    STA_PROF_FORWARD = 2,    /* forward propagation: one launch per level, or one persistent launch */
     STA_PROF_ENDPOINTS = 3,  /* endpoint slack / WNS / TNS reduction (two launches) */
-    STA_PROF_RAT_LEVEL = 4,  /* one required-time level */
-    STA_PROF_SEED = 5,       /* adjoint seeds at the endpoints (with the weights) */
-    STA_PROF_ADJ_LEVEL = 6,  /* one adjoint level */
+    STA_PROF_REQUIRED = 4,   /* required-time sweep */
+    STA_PROF_SEED = 5,       /* loss weights (and, LEVELS only, endpoint seeds) */
+    STA_PROF_ADJOINT = 6,    /* adjoint sweep */
     STA_PROF_KINDS = 7
 };
 

@@ -39,7 +39,8 @@ def _stream_ptr(stream) -> int:
 class StaEngine:
     """One netlist resident on the current CUDA device."""
 
-    def __init__(self, netlist, library, use_graphs: bool = True, profile: bool = False):
+    def __init__(self, netlist, library, use_graphs: bool = True, profile: bool = False,
+                 schedule: str = "dataflow"):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("StaEngine needs a CUDA device (there is no CPU path)")
@@ -47,7 +48,9 @@ class StaEngine:
         self.num_pins = int(netlist.num_pins)
         self.num_end = int(netlist.end_pins.shape[0])
         self.device = torch.device("cuda", torch.cuda.current_device())
-        self.h = _sta.sta_create(netlist, library, use_graphs, profile)
+        sched = {"dataflow": _sta.SCHED_DATAFLOW, "levels": _sta.SCHED_LEVELS}[schedule]
+        self.schedule = schedule
+        self.h = _sta.sta_create(netlist, library, use_graphs, profile, sched)
         self.sizes = _sta.sta_query_sizes(self.h)
         self.gamma = None
 

@@ -40,10 +40,12 @@ class StaLibrary(ctypes.Structure):
 
 
 class StaOptions(ctypes.Structure):
-    _fields_ = [("use_graphs", _i32), ("profile", _i32), ("reserved", _i32 * 6)]
+    _fields_ = [("use_graphs", _i32), ("profile", _i32), ("schedule", _i32), ("reserved", _i32 * 5)]
 
 
-PROF_KINDS = ("positions", "net_rc", "fwd_level", "endpoints", "rat_level", "seed", "adj_level")
+PROF_KINDS = ("positions", "net_rc", "forward", "endpoints", "required", "seed", "adjoint")
+SCHED_DATAFLOW = 0
+SCHED_LEVELS = 1
 
 
 class StaError(RuntimeError):
@@ -158,11 +160,13 @@ def sta_levelize(nl):
     return lv[:N], int(nlev[0]), order[:N], pins[:npins]
 
 
-def sta_create(nl, lib, use_graphs: bool = True, profile: bool = False) -> int:
+def sta_create(nl, lib, use_graphs: bool = True, profile: bool = False,
+               schedule: int = SCHED_DATAFLOW) -> int:
     keep = _Keep()
     d = netlist_desc(nl, keep)
     l = library_desc(lib, keep)
-    opts = StaOptions(use_graphs=1 if use_graphs else 0, profile=1 if profile else 0)
+    opts = StaOptions(use_graphs=1 if use_graphs else 0, profile=1 if profile else 0,
+                      schedule=int(schedule))
     h = ctypes.c_void_p()
     _check(_lib.sta_create(ctypes.byref(d), ctypes.byref(l), ctypes.byref(opts), ctypes.byref(h)),
            "sta_create")

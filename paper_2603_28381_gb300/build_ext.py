@@ -1,6 +1,6 @@
 """Build libsta.so (the C-ABI library) in-tree for sm_103a.
 
-Four translation units are compiled in parallel (three CUDA, one host C++) and
+Five translation units are compiled in parallel (four CUDA, one host C++) and
 linked with a static CUDA runtime into ``paper_2603_28381_gb300/_build/libsta.so``.
 """
 from __future__ import annotations
@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libsta.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "capi.cu", "builder.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "dataflow.cu", "capi.cu", "builder.cpp", "noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -51,6 +51,9 @@ struct StaHandle {
     Layout lay;
     DevNet g{};
     DevState s{};
+    DfState d{};
+    int schedule = STA_SCHED_DATAFLOW;
+    int grid_fwd = 0, grid_bwd = 0;  // dataflow grids (blocks)
     std::vector<void*> allocs;
     size_t dev_bytes = 0;
     int device = 0;
@@ -66,8 +69,15 @@ struct StaHandle {
     cudaGraphExec_t gx_fwd[2] = {nullptr, nullptr};  // [lse]
     float gx_fwd_gamma[2] = {0.f, 0.f};
     cudaGraphExec_t gx_rat = nullptr;
+    float gx_rat_gamma = 0.f;
     cudaGraphExec_t gx_adj = nullptr;
     float gx_adj_gamma = 0.f;
+    cudaGraphExec_t gx_fused = nullptr;  // dataflow: required times + adjoint in one sweep
+    float gx_fused_gamma = 0.f;
+    // dataflow: the required-time sweep of the latest forward is deferred until a
+    // gradient sweep can carry it or a query needs it
+    bool rat_pending = false;
+    bool last_fused = false;
     // staging for host inputs / outputs
     void* stage = nullptr;
     size_t stage_bytes = 0;
@@ -109,7 +119,7 @@ struct StaHandle {
         return STA_OK;
     }
     ~StaHandle() {
-        for (auto* gx : {gx_fwd[0], gx_fwd[1], gx_rat, gx_adj})
+        for (auto* gx : {gx_fwd[0], gx_fwd[1], gx_rat, gx_adj, gx_fused})
             if (gx) cudaGraphExecDestroy(gx);
         for (void* p : allocs) cudaFree(p);
         if (stage) cudaFree(stage);
@@ -155,7 +165,39 @@ struct ProfScope {
     }
 };
 
+void enqueue_forward_dataflow(StaHandle* h, int lse, float gamma, cudaStream_t st) {
+    const Layout& L = h->lay;
+    cudaMemsetAsync(h->d.fcnt, 0, sizeof(int32_t) * (L.TF ? L.TF : 1), st);
+    cudaMemsetAsync(h->d.heads, 0, sizeof(int32_t), st);
+    cudaMemsetAsync(h->d.abort_word, 0, sizeof(int32_t), st);
+    {
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
+        launch_rc(h->g, h->s, 0, L.lvl_ctask[L.L], st);  // load and wire RC of the nets > 32 pins
+    }
+    {
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
+        launch_fwd_dataflow(h->g, h->s, h->d, h->grid_fwd, gamma, lse, st);
+    }
+    ProfScope ps(h, &h->prof_fwd, STA_PROF_ENDPOINTS, st);
+    launch_endpoints(h->g, h->s, gamma, lse, st);
+}
+
+void enqueue_backward_dataflow(StaHandle* h, int mode, float gamma, cudaStream_t st) {
+    const Layout& L = h->lay;
+    StaHandle::Prof* pr = (mode & 2) ? &h->prof_adj : &h->prof_rat;
+    pr->next = 0;
+    cudaMemsetAsync((mode & 2) ? h->d.acnt : h->d.rcnt, 0, sizeof(int32_t) * (L.TB ? L.TB : 1), st);
+    cudaMemsetAsync(h->d.heads + ((mode & 2) ? 2 : 1), 0, sizeof(int32_t), st);
+    ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJOINT : STA_PROF_REQUIRED, st);
+    launch_bwd_dataflow(h->g, h->s, h->d, h->grid_bwd, gamma, mode, st);
+}
+
 void enqueue_forward(StaHandle* h, int lse, float gamma, cudaStream_t st) {
+    if (h->schedule == STA_SCHED_DATAFLOW) {
+        h->prof_fwd.next = 0;
+        enqueue_forward_dataflow(h, lse, gamma, st);
+        return;
+    }
     const Layout& L = h->lay;
     h->prof_fwd.next = 0;
     {
@@ -163,7 +205,7 @@ void enqueue_forward(StaHandle* h, int lse, float gamma, cudaStream_t st) {
         launch_rc(h->g, h->s, L.lvl_wtask[L.L], L.lvl_ctask[L.L], st);
     }
     for (int l = 0; l < L.L; ++l) {
-        ProfScope ps(h, &h->prof_fwd, STA_PROF_FWD_LEVEL, st);
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
         launch_fwd_level(h->g, h->s, L.lvl_wtask[l], L.lvl_wtask[l + 1] - L.lvl_wtask[l], L.lvl_ctask[l],
                          L.lvl_ctask[l + 1] - L.lvl_ctask[l], gamma, lse, st);
     }
@@ -172,6 +214,10 @@ void enqueue_forward(StaHandle* h, int lse, float gamma, cudaStream_t st) {
 }
 
 void enqueue_backward(StaHandle* h, int mode, float gamma, cudaStream_t st) {
+    if (h->schedule == STA_SCHED_DATAFLOW) {
+        enqueue_backward_dataflow(h, mode, gamma, st);
+        return;
+    }
     const Layout& L = h->lay;
     StaHandle::Prof* pr = (mode & 2) ? &h->prof_adj : &h->prof_rat;
     pr->next = 0;
@@ -180,7 +226,7 @@ void enqueue_backward(StaHandle* h, int mode, float gamma, cudaStream_t st) {
         launch_seed(h->g, h->s, gamma, st);
     }
     for (int l = L.L - 1; l >= 0; --l) {
-        ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJ_LEVEL : STA_PROF_RAT_LEVEL, st);
+        ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJOINT : STA_PROF_REQUIRED, st);
         launch_bwd_level(h->g, h->s, L.lvl_wtask[l], L.lvl_wtask[l + 1] - L.lvl_wtask[l], L.lvl_ctask[l],
                          L.lvl_ctask[l + 1] - L.lvl_ctask[l], gamma, mode, st);
     }
@@ -203,10 +249,42 @@ StaStatus capture(StaHandle* h, cudaGraphExec_t* out, F&& body) {
     return STA_OK;
 }
 
+StaStatus launch_graph_or_direct(StaHandle* h, cudaGraphExec_t* gx, float* key, float gamma, int mode,
+                                 cudaStream_t st);
+
+// Launch the deferred required-time sweep (dataflow schedule) on the handle's
+// stream, after the latest arrival-time pass.
+StaStatus flush_rat(StaHandle* h) {
+    if (!h->rat_pending) return STA_OK;
+    h->rat_pending = false;
+    if (cudaStreamWaitEvent(h->side, h->ev_at, 0) != cudaSuccess) return set_err(STA_ERR_CUDA, "cudaStreamWaitEvent");
+    StaStatus st = launch_graph_or_direct(h, &h->gx_rat, &h->gx_rat_gamma, 1.f, 1, h->side);
+    if (st != STA_OK) return st;
+    if (cudaEventRecord(h->ev_fwd, h->side) != cudaSuccess) return set_err(STA_ERR_CUDA, "cudaEventRecord");
+    return STA_OK;
+}
+
 StaStatus check_launch() {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(STA_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return STA_OK;
+}
+
+// A backward sweep of the given mode, as a cached graph (re-captured when
+// gamma changes) or as direct launches.
+StaStatus launch_graph_or_direct(StaHandle* h, cudaGraphExec_t* gx, float* key, float gamma, int mode,
+                                 cudaStream_t st) {
+    if (h->use_graphs) {
+        if (!*gx || *key != gamma) {
+            StaStatus s2 = capture(h, gx, [&](cudaStream_t c) { enqueue_backward(h, mode, gamma, c); });
+            if (s2 != STA_OK) return s2;
+            *key = gamma;
+        }
+        CUDA_TRY(cudaGraphLaunch(*gx, st));
+        return STA_OK;
+    }
+    enqueue_backward(h, mode, gamma, st);
+    return check_launch();
 }
 
 }  // namespace
@@ -261,6 +339,12 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     if (opts) {
         h->use_graphs = opts->use_graphs != 0;
         h->profile = opts->profile != 0;
+        if (opts->schedule != STA_SCHED_DATAFLOW && opts->schedule != STA_SCHED_LEVELS) {
+            std::string keep = "StaOptions.schedule must be STA_SCHED_DATAFLOW or STA_SCHED_LEVELS";
+            delete h;
+            return set_err(STA_ERR_INVALID_ARG, keep);
+        }
+        h->schedule = opts->schedule;
     }
     const Layout& L = h->lay;
     cudaError_t ce = cudaGetDevice(&h->device);
@@ -286,6 +370,11 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     STEP(h->upload(g.lib_inv, L.lib_inv));
     STEP(h->upload(g.lib_unate, L.lib_unate));
     STEP(h->upload(g.lib_tab, L.lib_tab));
+    {
+        const float* cp = nullptr;
+        STEP(h->upload(cp, L.lib_cell));
+        g.lib_cell = reinterpret_cast<const float4*>(cp);
+    }
     STEP(h->upload(g.ep_pin, L.ep_pin));
     STEP(h->upload(g.ep_rat, L.ep_rat));
     g.r = L.r_per_um;
@@ -311,11 +400,39 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     STEP(h->alloc(s.red, (size_t)kRedBlocks * 8));
     STEP(h->alloc(s.summary, STA_SUM_COUNT));
     STEP(h->alloc(s.params, 4));
+    DfState& d = h->d;
+    {
+        const int32_t* cp = nullptr;
+        STEP(h->upload(cp, L.ftask));
+        d.ftask = reinterpret_cast<const int4*>(cp);
+        STEP(h->upload(d.arc_prod, L.arc_prod));
+        STEP(h->upload(cp, L.btask));
+        d.btask = reinterpret_cast<const int4*>(cp);
+        STEP(h->upload(d.baux, L.baux));
+        STEP(h->upload(d.pin_cons, L.pin_cons));
+        STEP(h->upload(d.f_indeg, L.f_indeg));
+        STEP(h->upload(d.f_out_ptr, L.f_out_ptr));
+        STEP(h->upload(d.f_out, L.f_out));
+        STEP(h->upload(d.b_indeg, L.b_indeg));
+        STEP(h->upload(d.b_out_ptr, L.b_out_ptr));
+        STEP(h->upload(d.b_out, L.b_out));
+    }
+    STEP(h->alloc(d.fcnt, L.TF));
+    STEP(h->alloc(d.rcnt, L.TB));
+    STEP(h->alloc(d.acnt, L.TB));
+    STEP(h->alloc(d.heads, 4));
+    STEP(h->alloc(d.rpart, (size_t)L.npart * kPartFloats));
+    STEP(h->alloc(d.apart, (size_t)L.npart * kPartFloats));
+    STEP(h->alloc(d.net_gload, L.N));
+    STEP(h->alloc(d.abort_word, 1));
+    d.TF = L.TF;
+    d.TB = L.TB;
 #undef STEP
     auto zero = [&](void* p, size_t bytes) { return cudaMemset(p, 0, bytes); };
     if (zero(s.xy, P * 8) || zero(s.load, L.N * 4) || zero(s.wdi, P * 8) || zero(s.ats, P * 8) ||
         zero(s.adel, (size_t)L.A * 16) || zero(s.g_ats, P * 8) || zero(s.g_slew, P * 8) || zero(s.grad, P * 8) ||
-        zero(s.summary, STA_SUM_COUNT * 8) || zero(s.params, 16) || zero(s.red, (size_t)kRedBlocks * 64))
+        zero(s.summary, STA_SUM_COUNT * 8) || zero(s.params, 16) || zero(s.red, (size_t)kRedBlocks * 64) ||
+        zero(d.abort_word, 4) || zero(d.heads, 16) || zero(d.net_gload, (size_t)L.N * 4))
         return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
     // constant state: asserted AT/slew (and LSE AT = late AT), required-time seeds
     if (cudaMemcpy(s.at, L.at0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -329,10 +446,17 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         cudaEventCreateWithFlags(&h->ev_fwd, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_bwd, cudaEventDisableTiming) != cudaSuccess)
         return fail(set_err(STA_ERR_CUDA, "stream/event creation failed"));
+    {   // dataflow grids: the whole GPU for the forward sweep; half each for the
+        // required-time and adjoint sweeps, which run concurrently
+        const int fmax = dataflow_max_blocks(1), bmax = dataflow_max_blocks(0);
+        h->grid_fwd = fmax > 0 ? fmax : 1;
+        h->grid_bwd = bmax > 1 ? bmax / 2 : 1;
+        if (cudaGetLastError() != cudaSuccess) return fail(set_err(STA_ERR_CUDA, "occupancy query failed"));
+    }
     if (h->profile) {  // event pairs for every launch of each sequence, made before any capture
         const size_t nl = (size_t)L.L;
         const std::pair<StaHandle::Prof*, size_t> sizes[] = {
-            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 2}, {&h->prof_rat, nl}, {&h->prof_adj, nl + 1}};
+            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 2}, {&h->prof_rat, nl + 1}, {&h->prof_adj, nl + 1}};
         for (const auto& ps : sizes) {
             ps.first->kind.assign(ps.second, 0);
             for (size_t k = 0; k < 2 * ps.second; ++k) {
@@ -379,6 +503,7 @@ StaStatus sta_set_positions(StaHandle* h, const float* xy, int on_device, void* 
     if (s3 != STA_OK) return s3;
     h->have_pos = true;
     h->have_fwd = h->have_lse = h->have_rat = false;
+    h->rat_pending = false;  // its results could no longer be queried
     return STA_OK;
 }
 
@@ -404,19 +529,15 @@ StaStatus sta_forward(StaHandle* h, uint32_t flags, float gamma, void* stream) {
         if (s2 != STA_OK) return s2;
     }
     CUDA_TRY(cudaEventRecord(h->ev_at, st));
-    if (flags & STA_FWD_RAT) {
+    h->rat_pending = false;
+    if ((flags & STA_FWD_RAT) && h->schedule == STA_SCHED_DATAFLOW) {
+        // deferred: carried by the next gradient sweep, or launched when queried
+        h->rat_pending = true;
+        CUDA_TRY(cudaEventRecord(h->ev_fwd, st));
+    } else if (flags & STA_FWD_RAT) {
         CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_at, 0));
-        if (h->use_graphs) {
-            if (!h->gx_rat) {
-                StaStatus s2 = capture(h, &h->gx_rat, [&](cudaStream_t c) { enqueue_backward(h, 1, 1.f, c); });
-                if (s2 != STA_OK) return s2;
-            }
-            CUDA_TRY(cudaGraphLaunch(h->gx_rat, h->side));
-        } else {
-            enqueue_backward(h, 1, 1.f, h->side);
-            StaStatus s2 = check_launch();
-            if (s2 != STA_OK) return s2;
-        }
+        StaStatus s2 = launch_graph_or_direct(h, &h->gx_rat, &h->gx_rat_gamma, 1.f, 1, h->side);
+        if (s2 != STA_OK) return s2;
         CUDA_TRY(cudaEventRecord(h->ev_fwd, h->side));
     } else {
         CUDA_TRY(cudaEventRecord(h->ev_fwd, st));
@@ -436,18 +557,16 @@ StaStatus sta_backward_grad(StaHandle* h, const float* w, int w_on_device, float
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_at, 0));
     launch_set_weights(h->s, w_on_device ? w : nullptr, w_on_device ? 0.f : w[0], w_on_device ? 0.f : w[1], st);
     const float gamma = h->gamma_fwd;
-    if (h->use_graphs) {
-        if (!h->gx_adj || h->gx_adj_gamma != gamma) {
-            StaStatus s2 = capture(h, &h->gx_adj, [&](cudaStream_t c) { enqueue_backward(h, 2, gamma, c); });
-            if (s2 != STA_OK) return s2;
-            h->gx_adj_gamma = gamma;
-        }
-        CUDA_TRY(cudaGraphLaunch(h->gx_adj, st));
+    h->last_fused = h->rat_pending;
+    if (h->rat_pending) {  // one sweep for the required times and the adjoint
+        h->rat_pending = false;
+        StaStatus s2 = launch_graph_or_direct(h, &h->gx_fused, &h->gx_fused_gamma, gamma, 3, st);
+        if (s2 != STA_OK) return s2;
+        CUDA_TRY(cudaEventRecord(h->ev_fwd, st));
     } else {
-        enqueue_backward(h, 2, gamma, st);
+        StaStatus s2 = launch_graph_or_direct(h, &h->gx_adj, &h->gx_adj_gamma, gamma, 2, st);
+        if (s2 != STA_OK) return s2;
     }
-    StaStatus s2 = check_launch();
-    if (s2 != STA_OK) return s2;
     const size_t bytes = (size_t)h->lay.P * 8;
     if (bytes) {
         CUDA_TRY(cudaMemcpyAsync(grad_xy, h->s.grad, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -506,6 +625,10 @@ StaStatus sta_query_pins(StaHandle* h, float* at, float* slew, float* rat, float
     if (!h->have_fwd) return set_err(STA_ERR_STATE, "no forward pass yet");
     if ((rat || slack) && !h->have_rat) return set_err(STA_ERR_STATE, "required times need STA_FWD_RAT");
     if (ats && !h->have_lse) return set_err(STA_ERR_STATE, "LSE arrival times need STA_FWD_LSE");
+    if (rat || slack) {
+        StaStatus s1 = flush_rat(h);
+        if (s1 != STA_OK) return s1;
+    }
     cudaStream_t st = as_stream(stream);
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
     StaStatus s2 = STA_OK;
@@ -554,12 +677,20 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
         nonempty += (L.lvl_wtask[l + 1] > L.lvl_wtask[l] || L.lvl_ctask[l + 1] > L.lvl_ctask[l]) ? 1 : 0;
     const int32_t nw = L.lvl_wtask.empty() ? 0 : L.lvl_wtask.back(), nc = L.lvl_ctask.empty() ? 0 : L.lvl_ctask.back();
     launches[STA_PROF_POSITIONS] = L.P > 0 ? 1 : 0;
-    launches[STA_PROF_NET_RC] = (nw + nc) > 0 ? 1 : 0;
-    launches[STA_PROF_FWD_LEVEL] = nonempty;
     launches[STA_PROF_ENDPOINTS] = 2;
-    launches[STA_PROF_RAT_LEVEL] = nonempty;
-    launches[STA_PROF_SEED] = 1 + (L.E > 0 ? 1 : 0);  // weights + seeds
-    launches[STA_PROF_ADJ_LEVEL] = nonempty;
+    if (h->schedule == STA_SCHED_DATAFLOW) {
+        launches[STA_PROF_NET_RC] = nc > 0 ? 1 : 0;
+        launches[STA_PROF_FORWARD] = L.TF > 0 ? 1 : 0;
+        launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 1 : 0;  // fused into the adjoint sweep
+        launches[STA_PROF_SEED] = 1;  // weights
+        launches[STA_PROF_ADJOINT] = L.TB > 0 ? 1 : 0;
+    } else {
+        launches[STA_PROF_NET_RC] = (nw + nc) > 0 ? 1 : 0;
+        launches[STA_PROF_FORWARD] = nonempty;
+        launches[STA_PROF_REQUIRED] = nonempty;
+        launches[STA_PROF_SEED] = 1 + (L.E > 0 ? 1 : 0);  // weights + seeds
+        launches[STA_PROF_ADJOINT] = nonempty;
+    }
     if (!ms) return STA_OK;
     for (int k = 0; k < STA_PROF_KINDS; ++k) ms[k] = 0.0;
     if (!h->profile) return set_err(STA_ERR_STATE, "handle was created without StaOptions.profile");

@@ -1,0 +1,849 @@
+// dataflow.cu -- persistent, dependency-driven schedule of the level sweeps.
+//
+// The level-synchronous scheme of the paper launches one kernel per level
+// (Section 3.1.2), so a sweep costs (levels) x (launch + the longest chain of
+// dependent loads of the level).  Here each sweep is ONE kernel: the builder
+// lists the warp-sized tasks of the sweep in a topological order (the levels
+// in order, or reversed), every warp takes the next task from a queue
+// (atomicAdd on a head), waits only for the specific tasks that produce what
+// it reads and then signals the tasks that consume its results: every task has
+// a counter that each of its producers increments (red.release at GPU scope)
+// and that one lane polls until it reaches the task's producer count
+// (ld.acquire once reached).  One polled word per waiting warp keeps the
+// polling traffic far below the memory system's capacity.  Work of different
+// levels overlaps; no grid-wide barrier exists.  A waiting warp only ever waits for tasks with smaller
+// indices, which warps that are already running hold, so the sweep always
+// progresses; every wait is nevertheless bounded in time and reports expiry
+// through an abort word instead of spinning forever.
+//
+// Tasks are one warp each: packed small nets (as in the level schedule), and,
+// for nets of more than 32 pins, 32-sink chunks.  In the forward pass a chunk
+// re-evaluates the net's driver cell (cheap) with the load computed by a
+// prologue kernel; in the backward pass a large net becomes partial-reduction
+// chunks, one driver task that combines them in a fixed order, and gradient
+// chunks, so every reduction stays deterministic.
+#include "device_common.cuh"
+
+namespace sta {
+namespace {
+
+constexpr unsigned long long kWaitBudgetNs = 1000000000ull;  // 1 s per wait
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int32_t* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until cnt[t] reaches need (its producer count).  The whole warp polls
+// the one counter together (the lanes read the same address, one transaction)
+// with relaxed loads and acquires it once the count is reached; every branch
+// is decided by a warp vote, so the warp never splits into a polling lane and
+// waiting lanes (a split warp would run the rest of the task as separate
+// groups).  Bounded: after kWaitBudgetNs, or once any wait of the launch has
+// expired, it sets the abort word and returns (the host then reports
+// STA_ERR_TIMEOUT).
+__device__ __forceinline__ void wait_ready(const int32_t* cnt, int t, int need, int32_t* abort_word) {
+    if (need <= 0) return;
+    if (__all_sync(kFull, ld_acquire(cnt + t) >= need)) return;
+    unsigned long long t0 = 0;
+    for (unsigned it = 1;; ++it) {
+        __nanosleep(64);
+        if (__all_sync(kFull, ld_relaxed(cnt + t) >= need)) {
+            (void)ld_acquire(cnt + t);
+            return;
+        }
+        if ((it & 63) == 0) {
+            if (__any_sync(kFull, ld_relaxed(abort_word) != 0)) return;
+            const unsigned long long now = __shfl_sync(kFull, global_ns(), 0);
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kWaitBudgetNs) {
+                if ((threadIdx.x & 31) == 0) atomicExch(abort_word, 1);
+                __syncwarp();
+                return;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int grab(int32_t* head) {
+    int t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(head, 1);
+    return __shfl_sync(kFull, t, 0);
+}
+
+__device__ __forceinline__ void red_release_add(int32_t* p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Signal the task's consumers: one release increment per consumer, after a
+// warp barrier, so every lane's stores happen before each increment (the
+// barrier orders the lanes, the release makes their writes visible at GPU
+// scope to whoever acquires the counter).
+__device__ __forceinline__ void signal_consumers(int32_t* cnt, const int32_t* out_ptr, const int32_t* out, int t) {
+    __syncwarp();
+    const int k1 = out_ptr[t + 1];
+    for (int k = out_ptr[t] + (int)(threadIdx.x & 31); k < k1; k += 32) red_release_add(cnt + out[k], 1);
+}
+
+// ---------------------------------------------------------------------------
+// Forward
+// ---------------------------------------------------------------------------
+
+// What a driver-cell lane (net n, condition c) can load before its inputs
+// exist: cell type, arcs, input pins and transitions, the load's table segment.
+struct FwdPre {
+    int t;    // cell type, -1 if the driver is asserted
+    int a0, na;
+    int pin[STA_MAX_ARCS];
+    int rfi;  // bit k: input transition of arc k
+    int jl;   // load segment and fraction
+    float ul;
+    float sidx[6], sinv[6];  // slew index points 0..5 of the type and 1/width of each segment
+};
+
+// slew segment and fraction from registers (same result as axis_seg)
+__device__ __forceinline__ void slew_seg(const float* sidx, const float* sinv, float v, int& is, float& ts) {
+    float base = sidx[0], inv = sinv[0];
+    is = 0;
+#pragma unroll
+    for (int j = 1; j <= 5; ++j)
+        if (sidx[j] <= v) {
+            base = sidx[j];
+            inv = sinv[j];
+            is = j;
+        }
+    ts = (v - base) * inv;
+}
+
+__device__ __forceinline__ FwdPre fwd_pre(const DevNet& g, int n, int c, float ld) {
+    FwdPre f;
+    f.t = g.net_drv[n];
+    f.a0 = f.na = f.rfi = f.jl = 0;
+    f.ul = 0.f;
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) f.pin[k] = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) f.sidx[j] = f.sinv[j] = 0.f;
+    if (f.t < 0) return f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        f.sidx[j] = __ldg(g.lib_idx + f.t * kLibStride + j);
+        f.sinv[j] = __ldg(g.lib_inv + f.t * kLibStride + j);
+    }
+    f.a0 = g.net_arc_ptr[n];
+    f.na = g.net_arc_ptr[n + 1] - f.a0;
+    const int un = g.lib_unate[f.t], rf = c & 1;
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k)
+        if (k < f.na) {
+            f.pin[k] = g.arc_pin[f.a0 + k];
+            f.rfi |= (rf ^ ((un >> k) & 1)) << k;
+        }
+    const float* li = g.lib_idx + f.t * kLibStride + 8;
+    f.jl = axis_seg(li, ld);
+    f.ul = (ld - __ldg(li + f.jl)) * __ldg(g.lib_inv + f.t * kLibStride + 8 + f.jl);
+    return f;
+}
+
+// After the wait: fanin arrival / slew / LSE arrival (through L2, issued
+// together), NLDM lookups, late max / early min and the LSE of Eq. 4.  The
+// code is branch-free across lanes: every lane issues the same loads (unused
+// arcs and asserted drivers read a harmless valid address) and results are
+// selected, so a warp never splits into groups whose memory round trips would
+// run one after another.  `dp` must be a valid pin.
+__device__ __forceinline__ DrvOut fwd_eval(const DevNet& g, const DevState& s, const FwdPre& f, int dp, int c,
+                                           float gamma, bool lse, bool write_adel) {
+    const int el = c >> 1, rf = c & 1;
+    const bool cell = f.t >= 0;
+    const int ty = cell ? f.t : 0;
+    float sin[STA_MAX_ARCS], ain[STA_MAX_ARCS], zin[STA_MAX_ARCS];
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        const int pin = k < f.na ? f.pin[k] : dp;
+        const int r = (f.rfi >> k) & 1;
+        const int q = 4 * pin + 2 * el + r;
+        sin[k] = __ldcg(s.slew + q);
+        ain[k] = __ldcg(s.at + q);
+        zin[k] = __ldcg(s.ats + 2 * pin + r);
+    }
+    // asserted driver: its constant values (set at creation)
+    const float at_c = __ldcg(s.at + 4 * dp + c), sl_c = __ldcg(s.slew + 4 * dp + c);
+    const float ats_c = __ldcg(s.ats + 2 * dp + rf);
+    float best_at = el ? -kInf : kInf, best_sl = el ? -kInf : kInf, m = -kInf;
+    float cand[STA_MAX_ARCS];
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        const bool use = k < f.na;
+        int is;
+        float ts;
+        slew_seg(f.sidx, f.sinv, sin[k], is, ts);
+        float4 dq, sq;
+        cell_corners(g, ty, k, rf, is, f.jl, dq, sq);
+        const float D = lerp_cell(dq, ts, f.ul);
+        const float S = lerp_cell(sq, ts, f.ul);
+        if (write_adel && use) s.adel[4 * (f.a0 + k) + c] = D;
+        const float v = ain[k] + D;
+        const float ba = el ? fmaxf(best_at, v) : fminf(best_at, v);
+        const float bs = el ? fmaxf(best_sl, S) : fminf(best_sl, S);
+        best_at = use ? ba : best_at;
+        best_sl = use ? bs : best_sl;
+        cand[k] = use ? zin[k] + D : -kInf;
+        m = fmaxf(m, cand[k]);
+    }
+    float sum = 0.f;
+    const float mm = f.na > 0 ? m : 0.f;
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        const float e = expf((cand[k] - mm) / gamma);
+        sum += k < f.na ? e : 0.f;
+    }
+    const float lse_v = mm + gamma * logf(f.na > 0 ? sum : 1.f);
+    DrvOut o;
+    o.at = cell ? best_at : at_c;
+    o.slew = cell ? best_sl : sl_c;
+    o.ats = (el && lse) ? (cell ? lse_v : ats_c) : 0.f;
+    return o;
+}
+
+// Packed small nets: net RC (Eqs. 1-3) of the task's own pins and every
+// static load first; then the wait; then the driver cells (4 lanes per net)
+// and the wire step to every sink.
+template <bool lse>
+__device__ void fwd_df_warp(const DevNet& g, const DevState& s, const DfState& d, int t, int n0, int nn,
+                            float gamma) {
+    const WarpGeom w = warp_geom(g, n0, nn);
+    const int p = w.pin0 + w.lane;
+    const bool sink = w.valid && w.lane != w.hd;
+    const float2 xy = w.valid ? s.xy[p] : make_float2(0.f, 0.f);
+    const float cap = w.valid ? g.pin_cap[p] : 0.f;
+    const float2 xyd = make_float2(__shfl_sync(kFull, xy.x, w.hd), __shfl_sync(kFull, xy.y, w.hd));
+    float v = cap;
+    float2 wdi = make_float2(0.f, 0.f);
+    if (sink) {
+        const float dist = fabsf(xy.x - xyd.x) + fabsf(xy.y - xyd.y);
+        const float R = g.r * dist;
+        const float C = fmaf(0.5f * g.c, dist, cap);
+        const float D = R * C * kKrc;
+        const float m = 2.f * R * C * D * kKrc - D * D;
+        wdi = make_float2(D, sqrtf(fmaxf(m, 0.f)));
+        s.wdi[p] = wdi;
+        v = fmaf(g.c, dist, cap);
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float u = __shfl_up_sync(kFull, v, off);
+        v = (w.lane - off >= w.hd) ? v + u : v;
+    }
+    if (w.valid && w.lane == w.last) s.load[n0 + w.j] = v;
+
+    const int j1 = w.lane >> 2, c = w.lane & 3;
+    const int hj = __shfl_sync(kFull, w.h, j1);
+    const int lastj = __shfl_sync(kFull, w.h, j1 + 1) - 1;
+    const float ldj = __shfl_sync(kFull, v, lastj & 31);
+    FwdPre f = fwd_pre(g, n0 + min(j1, nn - 1), c, ldj);
+    if (j1 >= nn) {  // idle lanes evaluate a dummy: no arcs, results unused
+        f.t = -1;
+        f.na = 0;
+    }
+    const int dp = w.pin0 + (j1 < nn ? hj : 0);
+
+    wait_ready(d.fcnt, t, d.f_indeg[t], d.abort_word);
+
+    const DrvOut o = fwd_eval(g, s, f, dp, c, gamma, lse, true);
+    if (j1 < nn && f.t >= 0) {
+        s.at[4 * dp + c] = o.at;
+        s.slew[4 * dp + c] = o.slew;
+        if (lse && c >= 2) s.ats[2 * dp + c - 2] = o.ats;
+    }
+    const int src = 4 * max(w.j, 0);
+    float A[4], S[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        A[k] = __shfl_sync(kFull, o.at, src + k);
+        S[k] = __shfl_sync(kFull, o.slew, src + k);
+    }
+    const float z0 = __shfl_sync(kFull, o.ats, src + 2), z1 = __shfl_sync(kFull, o.ats, src + 3);
+    if (sink) {
+        const float i2 = wdi.y * wdi.y;
+        reinterpret_cast<float4*>(s.at)[p] = make_float4(A[0] + wdi.x, A[1] + wdi.x, A[2] + wdi.x, A[3] + wdi.x);
+        reinterpret_cast<float4*>(s.slew)[p] =
+            make_float4(sqrtf(fmaf(S[0], S[0], i2)), sqrtf(fmaf(S[1], S[1], i2)), sqrtf(fmaf(S[2], S[2], i2)),
+                        sqrtf(fmaf(S[3], S[3], i2)));
+        if (lse) reinterpret_cast<float2*>(s.ats)[p] = make_float2(z0 + wdi.x, z1 + wdi.x);
+    }
+}
+
+// A 32-sink chunk of a large net: the net's load and wire RC come from the
+// prologue kernel; lanes 0-3 evaluate the driver (the first chunk also stores it).
+template <bool lse>
+__device__ void fwd_df_chunk(const DevNet& g, const DevState& s, const DfState& d, int t, int n, int p0, int cnt,
+                             float gamma) {
+    const int lane = threadIdx.x & 31;
+    const int dp = g.net_ptr[n];
+    const bool first = p0 == dp + 1;
+    FwdPre f = fwd_pre(g, n, lane & 3, s.load[n]);
+    if (lane >= 4) {  // lanes 4-31 evaluate a dummy: no arcs, results unused
+        f.t = -1;
+        f.na = 0;
+    }
+    float2 wdi = make_float2(0.f, 0.f);
+    if (lane < cnt) wdi = s.wdi[p0 + lane];
+
+    wait_ready(d.fcnt, t, d.f_indeg[t], d.abort_word);
+
+    const DrvOut o = fwd_eval(g, s, f, dp, lane & 3, gamma, lse, first && lane < 4);
+    if (lane < 4 && first && f.t >= 0) {
+        s.at[4 * dp + lane] = o.at;
+        s.slew[4 * dp + lane] = o.slew;
+        if (lse && lane >= 2) s.ats[2 * dp + lane - 2] = o.ats;
+    }
+    float A[4], S[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        A[k] = __shfl_sync(kFull, o.at, k);
+        S[k] = __shfl_sync(kFull, o.slew, k);
+    }
+    const float z0 = __shfl_sync(kFull, o.ats, 2), z1 = __shfl_sync(kFull, o.ats, 3);
+    if (lane < cnt) {
+        const int q = p0 + lane;
+        const float i2 = wdi.y * wdi.y;
+        reinterpret_cast<float4*>(s.at)[q] = make_float4(A[0] + wdi.x, A[1] + wdi.x, A[2] + wdi.x, A[3] + wdi.x);
+        reinterpret_cast<float4*>(s.slew)[q] =
+            make_float4(sqrtf(fmaf(S[0], S[0], i2)), sqrtf(fmaf(S[1], S[1], i2)), sqrtf(fmaf(S[2], S[2], i2)),
+                        sqrtf(fmaf(S[3], S[3], i2)));
+        if (lse) reinterpret_cast<float2*>(s.ats)[q] = make_float2(z0 + wdi.x, z1 + wdi.x);
+    }
+}
+
+template <bool lse>
+__global__ void __launch_bounds__(kBlock) k_fwd_df(DevNet g, DevState s, DfState d, float gamma) {
+    int t = grab(d.heads + 0);
+    while (t < d.TF) {
+        const int next = grab(d.heads + 0);
+        const int4 task = d.ftask[t];
+        if (task.y > 0) fwd_df_warp<lse>(g, s, d, t, task.x, task.y, gamma);
+        else fwd_df_chunk<lse>(g, s, d, t, task.x, task.z, task.w, gamma);
+        signal_consumers(d.fcnt, d.f_out_ptr, d.f_out, t);
+        t = next;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward (mode 1 required times, mode 2 adjoint, 3 both)
+// ---------------------------------------------------------------------------
+struct SeedCtx {
+    float W, wt, ww;  // WNS_gamma, w_tns, w_wns
+};
+
+// What a sink lane can load before the wait.  Cell-input sinks get their
+// required time and adjoints from the task that does their cell's arc step
+// (read after the wait); other sinks are constant: an endpoint carries its
+// constraint and, in the adjoint, the seed d loss / d LSE-AT =
+// -(w_tns dTNS_g/ds + w_wns dWNS_g/ds); a dangling sink has +-inf required
+// times and zero adjoints.
+struct SinkPre {
+    int cons;
+    float2 wdi, sl;  // wire (delay, impulse), late slews (rise, fall)
+    float4 rat;      // constant required times
+    float2 ga;       // constant adjoint of the LSE arrival
+};
+
+__device__ __forceinline__ SinkPre sink_pre(const DevState& s, const DfState& d, int p, int mode, float gamma,
+                                            const SeedCtx& sc) {
+    SinkPre q;
+    q.cons = d.pin_cons[p];
+    q.wdi = s.wdi[p];
+    q.sl = (mode & 2) ? reinterpret_cast<const float2*>(s.slew)[2 * p + 1] : make_float2(0.f, 0.f);
+    q.rat = make_float4(0.f, 0.f, 0.f, 0.f);
+    q.ga = make_float2(0.f, 0.f);
+    if (q.cons < 0) {
+        q.rat = reinterpret_cast<const float4*>(s.rat)[p];
+        if ((mode & 2) && isfinite(q.rat.z)) {
+            const float2 z = reinterpret_cast<const float2*>(s.ats)[p];
+            const float sr = q.rat.z - z.x, sf = q.rat.w - z.y;
+            const float te = softmin3(sr, sf, gamma);
+            float gr = sc.wt * expf(-(sr - te) / gamma), gf = sc.wt * expf(-(sf - te) / gamma);
+            if (isfinite(sc.W)) {
+                gr += sc.ww * expf(-(sr - sc.W) / gamma);
+                gf += sc.ww * expf(-(sf - sc.W) / gamma);
+            }
+            q.ga = make_float2(-gr, -gf);
+        }
+    }
+    return q;
+}
+
+// After the wait: the sink's terms of the backward reductions (see sink_bwd).
+// Branch-free across lanes: every lane loads (pin p must be valid) and selects.
+__device__ __forceinline__ SinkBwd sink_post(const DevState& s, int p, const SinkPre& q, float2 sld, int mode) {
+    const bool dyn = q.cons >= 0;
+    float4 rat = q.rat;
+    float2 ga = q.ga, gs = make_float2(0.f, 0.f);
+    if (mode & 1) {
+        const float4 r = __ldcg(reinterpret_cast<const float4*>(s.rat) + p);
+        rat = dyn ? r : q.rat;
+    }
+    if (mode & 2) {
+        const float2 a = __ldcg(reinterpret_cast<const float2*>(s.g_ats) + p);
+        const float2 b = __ldcg(reinterpret_cast<const float2*>(s.g_slew) + p);
+        ga = dyn ? a : q.ga;
+        gs = dyn ? b : make_float2(0.f, 0.f);
+    }
+    SinkBwd b;
+    if (mode & 1) {
+        b.r[0] = rat.x - q.wdi.x;
+        b.r[1] = rat.y - q.wdi.x;
+        b.r[2] = rat.z - q.wdi.x;
+        b.r[3] = rat.w - q.wdi.x;
+    } else {
+        b.r[0] = b.r[1] = -kInf;
+        b.r[2] = b.r[3] = kInf;
+    }
+    b.ga[0] = b.ga[1] = b.gs[0] = b.gs[1] = b.gwire = 0.f;
+    if (mode & 2) {
+        const float q0 = q.sl.x > 0.f ? gs.x / q.sl.x : 0.f;
+        const float q1 = q.sl.y > 0.f ? gs.y / q.sl.y : 0.f;
+        b.ga[0] = ga.x;
+        b.ga[1] = ga.y;
+        b.gs[0] = q0 * sld.x;
+        b.gs[1] = q1 * sld.y;
+        b.gwire = ga.x + ga.y + (q0 + q1) * q.wdi.y;
+    }
+    return b;
+}
+
+// identity terms of a lane that carries no sink
+__device__ __forceinline__ SinkBwd sink_none() {
+    SinkBwd b;
+    b.r[0] = b.r[1] = -kInf;
+    b.r[2] = b.r[3] = kInf;
+    b.ga[0] = b.ga[1] = b.gs[0] = b.gs[1] = b.gwire = 0.f;
+    return b;
+}
+
+// select between two term sets without branching
+__device__ __forceinline__ SinkBwd sink_pick(bool take, const SinkBwd& a, const SinkBwd& b) {
+    SinkBwd r;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.r[k] = take ? a.r[k] : b.r[k];
+    r.ga[0] = take ? a.ga[0] : b.ga[0];
+    r.ga[1] = take ? a.ga[1] : b.ga[1];
+    r.gs[0] = take ? a.gs[0] : b.gs[0];
+    r.gs[1] = take ? a.gs[1] : b.gs[1];
+    r.gwire = take ? a.gwire : b.gwire;
+    return r;
+}
+
+// What a driver-cell lane (net n, condition c) of the backward sweep can
+// compute from forward results before the wait: its arc delays (required
+// times) and, for the late conditions, the LSE weights of the arcs, the
+// bilinear partials of delay and slew, and the arc that attains the late
+// slew (first one on ties).
+struct BwdPre {
+    int t, a0, na, rfi;
+    int pin[STA_MAX_ARCS];
+    float adel[STA_MAX_ARCS];
+    float w[STA_MAX_ARCS], dDs[STA_MAX_ARCS], dDl[STA_MAX_ARCS];
+    int amax;
+    float dSs, dSl;
+};
+
+// a lane with no driver cell (asserted driver or idle lane)
+__device__ __forceinline__ BwdPre bwd_none() {
+    BwdPre b;
+    b.t = -1;
+    b.a0 = b.na = b.rfi = 0;
+    b.amax = -1;
+    b.dSs = b.dSl = 0.f;
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        b.pin[k] = 0;
+        b.adel[k] = b.w[k] = b.dDs[k] = b.dDl[k] = 0.f;
+    }
+    return b;
+}
+
+__device__ __forceinline__ BwdPre bwd_pre(const DevNet& g, const DevState& s, int n, int dp, int c, float gamma,
+                                          int mode) {
+    BwdPre b;
+    b.t = g.net_drv[n];
+    b.a0 = b.na = b.rfi = 0;
+    b.amax = -1;
+    b.dSs = b.dSl = 0.f;
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        b.pin[k] = 0;
+        b.adel[k] = b.w[k] = b.dDs[k] = b.dDl[k] = 0.f;
+    }
+    if (b.t < 0) return b;
+    const int el = c >> 1, rf = c & 1;
+    b.a0 = g.net_arc_ptr[n];
+    b.na = g.net_arc_ptr[n + 1] - b.a0;
+    const int un = g.lib_unate[b.t];
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k)
+        if (k < b.na) {
+            b.pin[k] = g.arc_pin[b.a0 + k];
+            b.rfi |= (rf ^ ((un >> k) & 1)) << k;
+            if (mode & 1) b.adel[k] = s.adel[4 * (b.a0 + k) + c];
+        }
+    if ((mode & 2) && el == 1) {
+        const float ld = s.load[n];
+        const float* li = g.lib_idx + b.t * kLibStride + 8;
+        const int jl = axis_seg(li, ld);
+        const float inv_l = __ldg(g.lib_inv + b.t * kLibStride + 8 + jl);
+        const float ul = (ld - __ldg(li + jl)) * inv_l;
+        const float* si = g.lib_idx + b.t * kLibStride;
+        const float atsd = s.ats[2 * dp + rf];
+        float best = -kInf;
+#pragma unroll
+        for (int k = 0; k < STA_MAX_ARCS; ++k)
+            if (k < b.na) {
+                const int r = (b.rfi >> k) & 1;
+                const float sin = s.slew[4 * b.pin[k] + 2 + r];
+                const int is = axis_seg(si, sin);
+                const float inv_s = __ldg(g.lib_inv + b.t * kLibStride + is);
+                const float ts = (sin - __ldg(si + is)) * inv_s;
+                float4 dq, sq;
+                cell_corners(g, b.t, k, rf, is, jl, dq, sq);
+                float dSs, dSl;
+                lerp_cell_grad(dq, ts, ul, inv_s, inv_l, b.dDs[k], b.dDl[k]);
+                const float S = lerp_cell_grad(sq, ts, ul, inv_s, inv_l, dSs, dSl);
+                b.w[k] = expf((s.ats[2 * b.pin[k] + r] + s.adel[4 * (b.a0 + k) + 2 + rf] - atsd) / gamma);
+                if (S > best) {
+                    best = S;
+                    b.amax = k;
+                    b.dSs = dSs;
+                    b.dSl = dSl;
+                }
+            }
+    }
+    return b;
+}
+
+// After the wait: required times of the cell's inputs (R = the output's
+// required time for this condition) and, for the late conditions, the adjoint
+// through the LSE, the NLDM partials and the late-slew max; returns this
+// transition's d loss / d load.
+__device__ __forceinline__ float bwd_apply(const DevState& s, const BwdPre& b, int c, float R, float GA, float GS,
+                                           int mode) {
+    const int el = c >> 1;
+    const bool adj = (mode & 2) && el == 1;
+    float gl = 0.f;
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        const bool use = k < b.na;  // na = 0 for asserted drivers and idle lanes
+        const int r = (b.rfi >> k) & 1;
+        const int qr = 4 * b.pin[k] + 2 * el + r, qa = 2 * b.pin[k] + r;
+        const float rv = R - b.adel[k];
+        const float gD = GA * b.w[k];
+        const float gsv = fmaf(gD, b.dDs[k], k == b.amax ? GS * b.dSs : 0.f);
+        if ((mode & 1) && use) s.rat[qr] = rv;
+        if (adj && use) s.g_ats[qa] = gD;
+        if (adj && use) s.g_slew[qa] = gsv;
+        gl = (adj && use) ? fmaf(gD, b.dDl[k], gl) : gl;
+    }
+    return (adj && b.amax >= 0) ? fmaf(GS, b.dSl, gl) : gl;
+}
+
+template <int mode>
+__device__ void bwd_df_warp(const DevNet& g, const DevState& s, const DfState& d, int32_t* cnt, int t, int n0,
+                            int nn, float gamma, const SeedCtx& sc) {
+    const WarpGeom w = warp_geom(g, n0, nn);
+    const int p = w.pin0 + w.lane;
+    const bool sink = w.valid && w.lane != w.hd;
+    // static part
+    float2 sld = make_float2(0.f, 0.f);
+    if (mode & 2) {
+        const float2 sl = w.valid ? reinterpret_cast<const float2*>(s.slew)[2 * p + 1] : make_float2(0.f, 0.f);
+        sld = make_float2(__shfl_sync(kFull, sl.x, w.hd), __shfl_sync(kFull, sl.y, w.hd));
+    }
+    const int pl = w.valid ? p : w.pin0;  // a valid pin for every lane
+    SinkPre q = sink_pre(s, d, pl, mode, gamma, sc);
+    const int j1 = w.lane >> 2, c = w.lane & 3;
+    const int hj = __shfl_sync(kFull, w.h, j1);
+    const int lastj = (__shfl_sync(kFull, w.h, j1 + 1) - 1) & 31;
+    const BwdPre bp = j1 < nn ? bwd_pre(g, s, n0 + j1, w.pin0 + hj, c, gamma, mode) : bwd_none();
+    float2 xy = make_float2(0.f, 0.f), xyd = make_float2(0.f, 0.f);
+    float cap = 0.f;
+    int orig = 0;
+    if (mode & 2) {
+        xy = s.xy[pl];
+        xyd = make_float2(__shfl_sync(kFull, xy.x, w.hd), __shfl_sync(kFull, xy.y, w.hd));
+        cap = g.pin_cap[pl];
+        orig = g.pin_orig[pl];
+    }
+
+    wait_ready(cnt, t, d.b_indeg[t], d.abort_word);
+
+    const SinkBwd b = sink_pick(sink, sink_post(s, pl, q, sld, mode), sink_none());
+    float r0 = b.r[0], r1 = b.r[1], r2 = b.r[2], r3 = b.r[3];
+    float ga0 = b.ga[0], ga1 = b.ga[1], gs0 = b.gs[0], gs1 = b.gs[1];
+    // segmented inclusive scans; updates are selects, not branches, so the
+    // warp stays converged between the shuffles
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const bool take = w.lane - off >= w.hd;
+        if (mode & 1) {
+            const float u0 = __shfl_up_sync(kFull, r0, off), u1 = __shfl_up_sync(kFull, r1, off);
+            const float u2 = __shfl_up_sync(kFull, r2, off), u3 = __shfl_up_sync(kFull, r3, off);
+            r0 = take ? fmaxf(r0, u0) : r0;
+            r1 = take ? fmaxf(r1, u1) : r1;
+            r2 = take ? fminf(r2, u2) : r2;
+            r3 = take ? fminf(r3, u3) : r3;
+        }
+        if (mode & 2) {
+            const float u0 = __shfl_up_sync(kFull, ga0, off), u1 = __shfl_up_sync(kFull, ga1, off);
+            const float u2 = __shfl_up_sync(kFull, gs0, off), u3 = __shfl_up_sync(kFull, gs1, off);
+            ga0 = take ? ga0 + u0 : ga0;
+            ga1 = take ? ga1 + u1 : ga1;
+            gs0 = take ? gs0 + u2 : gs0;
+            gs1 = take ? gs1 + u3 : gs1;
+        }
+    }
+    if ((mode & 1) && w.valid && w.lane == w.last)
+        reinterpret_cast<float4*>(s.rat)[w.pin0 + w.hd] = make_float4(r0, r1, r2, r3);
+    const float R0 = __shfl_sync(kFull, r0, lastj), R1 = __shfl_sync(kFull, r1, lastj);
+    const float R2 = __shfl_sync(kFull, r2, lastj), R3 = __shfl_sync(kFull, r3, lastj);
+    const float GA0 = __shfl_sync(kFull, ga0, lastj), GA1 = __shfl_sync(kFull, ga1, lastj);
+    const float GS0 = __shfl_sync(kFull, gs0, lastj), GS1 = __shfl_sync(kFull, gs1, lastj);
+    const float Rc = c == 0 ? R0 : c == 1 ? R1 : c == 2 ? R2 : R3;
+    float gl = bwd_apply(s, bp, c, Rc, (c & 1) ? GA1 : GA0, (c & 1) ? GS1 : GS0, mode);
+    if (mode & 2) {
+        gl += __shfl_down_sync(kFull, gl, 1);
+        const float gload = __shfl_sync(kFull, gl, (4 * max(w.j, 0) + 2) & 31);
+        const float dx = xy.x - xyd.x, dy = xy.y - xyd.y;
+        const float gd = fmaf(gload, g.c, b.gwire * kKrc * g.r * fmaf(g.c, fabsf(dx) + fabsf(dy), cap));
+        const float2 gxy = sink ? make_float2(gd * ((dx > 0.f) - (dx < 0.f)), gd * ((dy > 0.f) - (dy < 0.f)))
+                                : make_float2(0.f, 0.f);
+        if (sink) s.grad[orig] = gxy;
+        float sx = gxy.x, sy = gxy.y;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float u = __shfl_up_sync(kFull, sx, off), v = __shfl_up_sync(kFull, sy, off);
+            const bool take = w.lane - off >= w.hd;
+            sx = take ? sx + u : sx;
+            sy = take ? sy + v : sy;
+        }
+        const int orig_d = __shfl_sync(kFull, orig, w.hd);
+        if (w.valid && w.lane == w.last) s.grad[orig_d] = make_float2(-sx, -sy);
+    }
+}
+
+// fixed-order butterfly reductions across a warp
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, off));
+    return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, off));
+    return v;
+}
+
+// Partial chunk of a large net: 12 partial terms over up to 32 sinks,
+//   0-3 max/max/min/min of RAT_s - Delay_s, 4-5 sums of g_ats, 6-7 sums of
+//   g_slew * slew_d / slew_s, 8-9 sums of sign(x_s - x_d), sign(y_s - y_d),
+//   10-11 sums of sign * g_wire * dDelay/dd (the driver's gradient is
+//   -(gload * c * sums 8-9 + sums 10-11)).
+template <int mode>
+__device__ void bwd_df_part(const DevNet& g, const DevState& s, const DfState& d, int32_t* cnt_arr, int t, int n,
+                            int p0, int cnt, float gamma, const SeedCtx& sc, float* part) {
+    const int lane = threadIdx.x & 31;
+    const int dp = g.net_ptr[n];
+    const float2 sld = (mode & 2) ? reinterpret_cast<const float2*>(s.slew)[2 * dp + 1] : make_float2(0.f, 0.f);
+    const int p = p0 + (lane < cnt ? lane : 0);  // a valid pin for every lane
+    const SinkPre q = sink_pre(s, d, p, mode, gamma, sc);
+    float sx = 0.f, sy = 0.f, fd = 0.f;
+    if (lane < cnt) {
+        if (mode & 2) {
+            const float2 xy = s.xy[p], xyd = s.xy[dp];
+            const float dx = xy.x - xyd.x, dy = xy.y - xyd.y;
+            sx = (dx > 0.f) - (dx < 0.f);
+            sy = (dy > 0.f) - (dy < 0.f);
+            fd = kKrc * g.r * fmaf(g.c, fabsf(dx) + fabsf(dy), g.pin_cap[p]);
+        }
+    }
+
+    wait_ready(cnt_arr, t, d.b_indeg[t], d.abort_word);
+
+    const SinkBwd b = sink_pick(lane < cnt, sink_post(s, p, q, sld, mode), sink_none());
+    float v[kPartFloats];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = b.r[k];
+    v[4] = b.ga[0];
+    v[5] = b.ga[1];
+    v[6] = b.gs[0];
+    v[7] = b.gs[1];
+    const float h = b.gwire * fd;
+    v[8] = sx;
+    v[9] = sy;
+    v[10] = sx * h;
+    v[11] = sy * h;
+    v[0] = warp_max(v[0]);
+    v[1] = warp_max(v[1]);
+    v[2] = warp_min(v[2]);
+    v[3] = warp_min(v[3]);
+#pragma unroll
+    for (int k = 4; k < kPartFloats; ++k) v[k] = warp_sum(v[k]);
+    if (lane < kPartFloats) {
+        float out = v[0];
+#pragma unroll
+        for (int k = 1; k < kPartFloats; ++k)
+            if (lane == k) out = v[k];
+        part[lane] = out;
+    }
+}
+
+// Driver step of a large net: combine its partial chunks in a fixed order, then
+// required times / adjoint through the driver cell and the driver's gradient.
+template <int mode>
+__device__ void bwd_df_driver(const DevNet& g, const DevState& s, const DfState& d, int32_t* cnt, int t, int n,
+                              const float* part, int slot0, int nch, float gamma) {
+    const int lane = threadIdx.x & 31;
+    const int dp = g.net_ptr[n];
+    const BwdPre bp = lane < 4 ? bwd_pre(g, s, n, dp, lane, gamma, mode) : bwd_none();
+
+    wait_ready(cnt, t, d.b_indeg[t], d.abort_word);
+
+    float v[kPartFloats];
+    v[0] = v[1] = -kInf;
+    v[2] = v[3] = kInf;
+#pragma unroll
+    for (int k = 4; k < kPartFloats; ++k) v[k] = 0.f;
+    for (int k = lane; k < nch; k += 32) {
+        const float* q = part + (size_t)(slot0 + k) * kPartFloats;
+        v[0] = fmaxf(v[0], __ldcg(q + 0));
+        v[1] = fmaxf(v[1], __ldcg(q + 1));
+        v[2] = fminf(v[2], __ldcg(q + 2));
+        v[3] = fminf(v[3], __ldcg(q + 3));
+#pragma unroll
+        for (int j = 4; j < kPartFloats; ++j) v[j] += __ldcg(q + j);
+    }
+    v[0] = warp_max(v[0]);
+    v[1] = warp_max(v[1]);
+    v[2] = warp_min(v[2]);
+    v[3] = warp_min(v[3]);
+#pragma unroll
+    for (int k = 4; k < kPartFloats; ++k) v[k] = warp_sum(v[k]);
+    if ((mode & 1) && lane == 0) reinterpret_cast<float4*>(s.rat)[dp] = make_float4(v[0], v[1], v[2], v[3]);
+    const int c = lane & 3;
+    const float Rc = c == 0 ? v[0] : c == 1 ? v[1] : c == 2 ? v[2] : v[3];
+    float gl = bwd_apply(s, bp, c, Rc, (c & 1) ? v[5] : v[4], (c & 1) ? v[7] : v[6], mode);
+    if (mode & 2) {
+        gl += __shfl_down_sync(kFull, gl, 1);
+        const float gload = __shfl_sync(kFull, gl, 2);
+        if (lane == 0) {
+            d.net_gload[n] = gload;
+            s.grad[g.pin_orig[dp]] = make_float2(-fmaf(gload * g.c, v[8], v[10]), -fmaf(gload * g.c, v[9], v[11]));
+        }
+    }
+}
+
+// Gradient chunk of a large net: d loss / d (x, y) of up to 32 sinks, once the
+// driver task has published d loss / d load.  No task waits for these.
+__device__ void bwd_df_grad(const DevNet& g, const DevState& s, const DfState& d, int32_t* cnt_arr, int t, int n,
+                            int p0, int cnt, float gamma, const SeedCtx& sc) {
+    const int lane = threadIdx.x & 31;
+    const int dp = g.net_ptr[n];
+    wait_ready(cnt_arr, t, d.b_indeg[t], d.abort_word);
+    const float gload = __ldcg(d.net_gload + n);
+    if (lane < cnt) {
+        const int p = p0 + lane;
+        const float2 sld = reinterpret_cast<const float2*>(s.slew)[2 * dp + 1];
+        const SinkPre q = sink_pre(s, d, p, 2, gamma, sc);
+        const SinkBwd b = sink_post(s, p, q, sld, 2);
+        s.grad[g.pin_orig[p]] = sink_grad(g, s, p, s.xy[p], s.xy[dp], b.gwire, gload);
+    }
+}
+
+template <int mode>
+__global__ void __launch_bounds__(kBlock) k_bwd_df(DevNet g, DevState s, DfState d, float gamma) {
+    int32_t* cnt = (mode & 2) ? d.acnt : d.rcnt;
+    int32_t* head = d.heads + ((mode & 2) ? 2 : 1);
+    float* part = (mode & 2) ? d.apart : d.rpart;
+    SeedCtx sc;
+    sc.W = (float)s.summary[STA_SUM_WNS_GAMMA];
+    sc.wt = s.params[0];
+    sc.ww = s.params[1];
+    int t = grab(head);
+    while (t < d.TB) {
+        const int next = grab(head);
+        const int4 task = d.btask[t];
+        if (task.y > 0) {
+            bwd_df_warp<mode>(g, s, d, cnt, t, task.x, task.y, gamma, sc);
+        } else if (task.y == -1) {
+            bwd_df_part<mode>(g, s, d, cnt, t, task.x, task.z, task.w, gamma, sc,
+                              part + (size_t)d.baux[t] * kPartFloats);
+        } else if (task.y == -2) {
+            bwd_df_driver<mode>(g, s, d, cnt, t, task.x, part, task.z, task.w, gamma);
+        } else if (mode & 2) {
+            bwd_df_grad(g, s, d, cnt, t, task.x, task.z, task.w, gamma, sc);
+        }
+        signal_consumers(cnt, d.b_out_ptr, d.b_out, t);
+        t = next;
+    }
+}
+
+template <typename K, typename... Args>
+void launch_coop(K kernel, int grid, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+}  // namespace
+
+int dataflow_max_blocks(int fwd) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (fwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_df<true>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_df<3>, kBlock, 0);
+    return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+void launch_fwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int lse,
+                         cudaStream_t st) {
+    if (d.TF == 0) return;
+    if (lse) launch_coop(k_fwd_df<true>, grid, st, g, s, d, gamma);
+    else launch_coop(k_fwd_df<false>, grid, st, g, s, d, gamma);
+}
+
+void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int mode,
+                         cudaStream_t st) {
+    if (d.TB == 0) return;
+    if (mode == 1) launch_coop(k_bwd_df<1>, grid, st, g, s, d, gamma);
+    else if (mode == 2) launch_coop(k_bwd_df<2>, grid, st, g, s, d, gamma);
+    else launch_coop(k_bwd_df<3>, grid, st, g, s, d, gamma);
+}
+
+}  // namespace sta

@@ -21,6 +21,7 @@ struct DevNet {
     const float* lib_inv;        // [T*16]
     const int32_t* lib_unate;    // [T]
     const float* lib_tab;        // [T*4*2*98]
+    const float4* lib_cell;      // [T*4*2*36*2] corner-packed cells (delay float4, slew float4)
     const int32_t* ep_pin;       // [E]
     const float* ep_rat;         // [E*4]
     float r, c;                  // Ohm/um, fF/um
@@ -45,6 +46,37 @@ struct DevState {
     double* summary;   // [STA_SUM_COUNT]
     float* params;     // [4] w_tns, w_wns
 };
+
+// Dataflow schedule: task lists, dependency counters and queue heads.
+struct DfState {
+    const int4* ftask;       // [TF]
+    const int32_t* arc_prod; // [A]
+    const int4* btask;       // [TB]
+    const int32_t* baux;     // [TB]
+    const int32_t* pin_cons; // [P]
+    const int32_t* f_indeg;  // [TF] producers each forward task waits for
+    const int32_t* f_out_ptr;// [TF+1]
+    const int32_t* f_out;    // consumers each forward task signals
+    const int32_t* b_indeg;  // [TB]
+    const int32_t* b_out_ptr;// [TB+1]
+    const int32_t* b_out;
+    int32_t* fcnt;           // [TF] arrived producers, forward sweep
+    int32_t* rcnt;           // [TB] arrived producers, required-time sweep
+    int32_t* acnt;           // [TB] arrived producers, adjoint sweep
+    int32_t* heads;          // [4] queue heads: forward, required time, adjoint
+    float* rpart;            // [npart * kPartFloats] partials, required-time sweep
+    float* apart;            // [npart * kPartFloats] partials, adjoint sweep
+    float* net_gload;        // [N] d loss / d load of large nets
+    int32_t* abort_word;     // [1] set when a bounded wait expires
+    int32_t TF, TB;
+};
+
+void launch_fwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int lse,
+                         cudaStream_t st);
+void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int mode,
+                         cudaStream_t st);
+// largest co-resident grid of the dataflow kernels on the current device
+int dataflow_max_blocks(int fwd);
 
 void launch_gather_xy(const DevNet& g, const DevState& s, const float2* xy_user, cudaStream_t st);
 void launch_rc(const DevNet& g, const DevState& s, int nw, int nc, cudaStream_t st);

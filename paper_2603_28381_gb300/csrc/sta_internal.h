@@ -28,6 +28,7 @@ constexpr int kLibStride = 16;      // floats per type in lib_idx / lib_inv
 constexpr int kTabPerArcRf = 2 * STA_LUT * STA_LUT;  // delay table then slew table
 constexpr int kRedBlocks = 152;     // endpoint reduction partials (one per SM)
 constexpr float kKrc = 1e-3f;       // Ohm * fF in ps
+constexpr int kPartFloats = 12;     // floats per backward partial (large nets)
 
 struct Layout {
     int32_t P = 0;       // pins
@@ -50,6 +51,22 @@ struct Layout {
     std::vector<int32_t> wtask;        // [2*W] (first net, number of nets)
     std::vector<int32_t> ctask;        // [Cb] net of each block task
 
+    // dataflow schedule (one persistent kernel per sweep, tasks in topological order)
+    //   forward task  {first net, nets (> 0) | -1 for a 32-sink chunk of a large net, first pin, pins}
+    //   backward task {net(s), kind, first pin, pins}: kind > 0 packed nets (= count), -1 partial
+    //   chunk of a large net, -2 its driver step (first pin = first partial slot, pins = chunks),
+    //   -3 gradient chunk; aux = partial slot (-1), first partial task (-2), driver task (-3)
+    std::vector<int32_t> ftask;      // [4*TF]
+    std::vector<int32_t> arc_prod;   // [A] forward task that writes the arc's input pin, -1 if asserted
+    std::vector<int32_t> btask;      // [4*TB]
+    std::vector<int32_t> baux;       // [TB]
+    std::vector<int32_t> pin_cons;   // [P] backward task whose arc step writes the pin's RAT / adjoint
+    // dependency counts and consumer lists: a task may start once `indeg` of its
+    // producers have published; a producer signals every task of its out list
+    std::vector<int32_t> f_indeg, f_out_ptr, f_out;  // forward: [TF], [TF+1], [..]
+    std::vector<int32_t> b_indeg, b_out_ptr, b_out;  // backward: [TB], [TB+1], [..]
+    int32_t TF = 0, TB = 0, npart = 0;
+
     // constant per-pin state written once at creation
     std::vector<float> at0, slew0;     // [P*4] asserted values (0 elsewhere)
     std::vector<float> rat0;           // [P*4] endpoint constraint, else -inf/+inf
@@ -61,6 +78,8 @@ struct Layout {
     std::vector<float> lib_inv;        // [T*16] 1/(idx[k+1]-idx[k]) for k = 0..5 (slew), 8..13 (load)
     std::vector<int32_t> lib_unate;    // [T] bit a set = arc a negative unate
     std::vector<float> lib_tab;        // [T*4*2*98] per (type, arc, rf_out): delay 7x7, slew 7x7
+    std::vector<float> lib_cell;       // [T*4*2*36*8] per (type, arc, rf_out, slew seg, load seg): the
+                                       // four delay corners then the four slew corners (one 32-byte sector)
 
     float r_per_um = 0.f, c_per_um = 0.f;
 };

@@ -92,12 +92,13 @@ def edge_netlists():
     return out
 
 
-def run_gpu(nl, lib, xy, gamma=10.0, w=(1.0, 0.5), use_graphs=True, host_xy=False, engine=None):
+def run_gpu(nl, lib, xy, gamma=10.0, w=(1.0, 0.5), use_graphs=True, host_xy=False, engine=None,
+            schedule="dataflow"):
     """One set_positions + forward(LSE, RAT) + backward through the C ABI."""
     import torch
 
     import paper_2603_28381_gb300 as sta
-    eng = engine or sta.StaEngine(nl, lib, use_graphs=use_graphs)
+    eng = engine or sta.StaEngine(nl, lib, use_graphs=use_graphs, schedule=schedule)
     if host_xy:
         eng.set_positions(np.asarray(xy, np.float32))
     else:

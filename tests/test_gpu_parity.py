@@ -18,6 +18,7 @@ def built():
 
 
 def _check(w_or_parts, gamma=10.0, weights=(1.0, 0.5), **kw):
+    """Oracle vs CUDA path through the C ABI on the same seeded inputs."""
     if isinstance(w_or_parts, tuple):
         nl, xy, lib = w_or_parts
     else:
@@ -27,38 +28,47 @@ def _check(w_or_parts, gamma=10.0, weights=(1.0, 0.5), **kw):
     return tp.assert_parity(gpu, ora), gpu, ora
 
 
+SCHEDULES = ["dataflow", "levels"]
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_tiny_design(seed):
-    _check(netgen.tiny_design(seed))
+def test_tiny_design(seed, schedule):
+    _check(netgen.tiny_design(seed), schedule=schedule)
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("seed", range(6))
-def test_tiny_dags_slew_independent_library(seed):
+def test_tiny_dags_slew_independent_library(seed, schedule):
     w = td.tiny_netlist(seed)
     lib, _, _ = td.linear_library(5, [1, 2, 3, 4, 1], seed=seed)
-    _check((w.netlist, w.xy, lib), gamma=3.0)
+    _check((w.netlist, w.xy, lib), gamma=3.0, schedule=schedule)
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("idx", range(3))
-def test_edge_netlists(idx):
+def test_edge_netlists(idx, schedule):
     name, nl, xy, lib = tp.edge_netlists()[idx]
-    errs, gpu, ora = _check((nl, xy, lib))
+    errs, gpu, ora = _check((nl, xy, lib), schedule=schedule)
     if name == "no_endpoints":
         assert gpu["summary"]["tns_late"] == 0.0 and np.isinf(gpu["summary"]["wns_late"])
         assert np.all(gpu["grad"] == 0.0)
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES)
 @pytest.mark.parametrize("gamma", [1.0, 50.0])
-def test_mid_size_many_tiles(gamma):
-    # ~50k pins over 40 levels: thousands of warp tasks, block tasks for the
+def test_mid_size_many_tiles(gamma, schedule):
+    # ~50k pins over 40 levels: thousands of warp tasks, large-net tasks for the
     # power-law nets above 32 pins and the 400-sink primary-input nets
-    _check(netgen.superblue_like(3, scale=0.02, depth=40), gamma=gamma, weights=(0.8, 0.2))
+    _check(netgen.superblue_like(3, scale=0.02, depth=40), gamma=gamma, weights=(0.8, 0.2),
+           schedule=schedule)
 
 
-def test_full_size_superblue_like():
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_full_size_superblue_like(schedule):
     # the benchmark's workload and launch configuration (CUDA graphs), all outputs
     w = netgen.superblue_like(1)
-    errs, gpu, ora = _check(w)
+    errs, gpu, ora = _check(w, schedule=schedule)
     assert gpu["summary"]["num_endpoints"] == w.netlist.end_pins.shape[0]
 
 
@@ -72,6 +82,39 @@ def test_deterministic_graphs_and_host_input():
         for other in (b, c, d):
             assert np.array_equal(a[k], other[k], equal_nan=True), k
     assert a["summary"] == b["summary"] == c["summary"] == d["summary"]
+
+
+def test_required_times_queried_before_gradient():
+    # required times queried right after the forward run on their own; the
+    # gradient sweep then runs alone; both equal the fused sweep's results
+    import torch
+
+    import paper_2603_28381_gb300 as sta
+    w = netgen.superblue_like(6, scale=0.01, depth=30)
+    fused = tp.run_gpu(w.netlist, w.library, w.xy)
+    eng = sta.StaEngine(w.netlist, w.library)
+    eng.set_positions(torch.as_tensor(w.xy).cuda())
+    eng.forward(gamma=10.0)
+    early = eng.pins()
+    g = eng.backward_grad((1.0, 0.5)).cpu().numpy()
+    late = eng.pins()
+    eng.close()
+    for k in ("at", "slew", "rat", "ats", "slack"):
+        assert np.array_equal(early[k], fused[k], equal_nan=True), k
+        assert np.array_equal(late[k], fused[k], equal_nan=True), k
+    assert np.array_equal(g, fused["grad"])
+
+
+def test_schedules_agree():
+    # arrival / slew / LSE / required times bit-identical across schedules;
+    # gradients agree to rounding (large-net sums are reassociated)
+    w = netgen.superblue_like(5, scale=0.01, depth=30)
+    a = tp.run_gpu(w.netlist, w.library, w.xy, schedule="dataflow")
+    b = tp.run_gpu(w.netlist, w.library, w.xy, schedule="levels")
+    for k in ("at", "slew", "rat", "ats", "slack", "ep_slack"):
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+    gmax = np.abs(b["grad"]).max()
+    assert np.abs(a["grad"] - b["grad"]).max() <= 1e-5 * gmax
 
 
 def test_repeated_calls_follow_new_positions():
