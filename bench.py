@@ -47,6 +47,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--schedule", default="dataflow", choices=["dataflow", "levels"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+                    help="single: one placement of the ~2.5M-pin netlist per step (the headline); "
+                         "batch: 64 placements of a ~500k-pin netlist per step")
+    ap.add_argument("--placements", type=int, default=64)
+    ap.add_argument("--verbose", action="store_true", help="per-step times on stderr")
+    ap.add_argument("--tile-pins", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0)
     return ap.parse_args()
 
 
@@ -106,6 +113,24 @@ def algorithmic_bytes(sizes, S, schedule="dataflow", big=(0, 0)):
         out["net_rc"] = rc(big[0], big[1])
         out["forward"] = fwd + rc(N - big[0], S - big[1])
     return out
+
+
+def algorithmic_bytes_batch(sizes, S, B, big=(0, 0)):
+    """Algorithmic bytes of one batched step (B placements) by kernel kind.
+    Per placement every per-pin value crosses HBM once per producer and once per
+    consumer; topology and capacitances are read once per warp of 32 placements."""
+    P, N, A, E = sizes["pins"], sizes["nets"], sizes["arcs"], sizes["endpoints"]
+    topo = (16 * N + 8 * A + 4 * P) * -(-B // 32)
+    # forward, per sink: xy 8, AT+slew+LSE-AT write 40; per net: driver xy 8, load write 4,
+    # driver AT+slew+LSE-AT write 40; per arc: fanin AT+slew+LSE-AT 40
+    fwd = B * (48 * S + 52 * N + 40 * A) + topo
+    # fused backward, per sink: RAT 16, adjoints 16, late slew 8, xy 8, grad write 8; per net:
+    # driver LSE-AT 8 + late slew 8 + xy 8 + load 4, RAT write 16, grad write 8; per arc: fanin
+    # slews 16, LSE-AT 8, RAT + adjoint writes 32
+    bwd = B * (56 * S + 52 * N + 56 * A) + topo
+    return {"positions": 16 * B * P + 4 * P, "net_rc": B * (8 * big[1] + 12 * big[0]),
+            "forward": fwd, "endpoints": B * 32 * E + 20 * E, "required": 0, "seed": 8 * B,
+            "adjoint": bwd, "output": 16 * B * P + 4 * P}
 
 
 def load_peaks():
@@ -281,6 +306,8 @@ def run_ours(args):
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
+    if args.verbose:
+        print("step ms:", " ".join(f"{m:.3f}" for m in ms), file=sys.stderr)
     total_s = sum(ms) / 1e3
     t_local = torch.tensor([total_s], dtype=torch.float64, device=dev)
     if dist is not None:
@@ -375,10 +402,133 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------
+# batched placements: B position sets of one netlist per step
+# --------------------------------------------------------------------------
+def batch_workload(args):
+    import netgen
+    w = netgen.superblue_like(args.seed + 1, scale=0.2 * args.scale, depth=100)
+    xyb = netgen.jitter_positions(w.xy, args.placements, 5.0, args.seed)
+    return w, xyb
+
+
+def run_batch(args):
+    import torch
+
+    import paper_2603_28381_gb300 as sta
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    w, xyb_np = batch_workload(args)
+    nl = w.netlist
+    P, B = nl.num_pins, args.placements
+    S = int(nl.net_ptr[-1]) - nl.num_nets
+    dev = torch.device("cuda", local)
+    xyb = torch.as_tensor(xyb_np).to(dev)
+    W = torch.ones(B, 2, dtype=torch.float32, device=dev)
+    grad = torch.empty(B, P, 2, dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(eng):
+        eng.set_positions(xyb)
+        eng.forward(gamma=GAMMA, lse=True, rat=True)
+        eng.backward_grad(W, out=grad)
+        eng.stream_wait()
+
+    def timed(eng, fn, steps):
+        for _ in range(args.warmup):
+            fn(eng)
+        cur = torch.cuda.current_stream()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(cur)
+            fn(eng)
+            ev[k][1].record(cur)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        if args.verbose:
+            print("step ms:", " ".join(f"{m:.3f}" for m in ms), file=sys.stderr)
+        return sum(ms) / 1e3
+
+    eng = sta.StaEngine(nl, w.library, schedule="batch", num_placements=B, tile_pins=args.tile_pins,
+                        chunk=args.chunk)
+    clocks = Clocks(local)
+    total_s = timed(eng, step, args.steps)
+    clk = clocks.stop()
+    value = B * P * args.steps / total_s
+    _, launches = eng.profile(with_times=False)
+    eng.close()
+
+    # the plain path on the same placements: one placement per call, one after another
+    one = sta.StaEngine(nl, w.library, schedule="dataflow")
+    xs = [xyb[b].contiguous() for b in range(B)]
+    g1 = torch.empty(P, 2, dtype=torch.float32, device=dev)
+    w1 = torch.ones(2, dtype=torch.float32, device=dev)
+
+    def plain(e):
+        for b in range(B):
+            e.set_positions(xs[b])
+            e.forward(gamma=GAMMA, lse=True, rat=True)
+            e.backward_grad(w1, out=g1)
+        e.stream_wait()
+
+    plain_steps = max(1, min(args.steps, 5))
+    plain_s = timed(one, plain, plain_steps)
+    one.close()
+    plain_value = B * P * plain_steps / plain_s
+
+    prof = sta.StaEngine(nl, w.library, schedule="batch", num_placements=B, profile=True,
+                         tile_pins=args.tile_pins, chunk=args.chunk)
+    for _ in range(2):
+        step(prof)
+    acc = {}
+    nprof = min(args.steps, 5)
+    for _ in range(nprof):
+        flush.zero_()
+        step(prof)
+        msk, _ = prof.profile()
+        for k, v in msk.items():
+            acc[k] = acc.get(k, 0.0) + v / nprof
+    sizes = dict(pins=P, nets=prof.sizes["nets"], arcs=prof.sizes["arcs"], endpoints=prof.sizes["endpoints"])
+    prof.close()
+    chunk = args.chunk or 64
+    fan = np.diff(nl.net_ptr)
+    bigm = fan > chunk + 1
+    abytes = algorithmic_bytes_batch(sizes, S, B, big=(int(bigm.sum()), int((fan[bigm] - 1).sum())))
+    peak, peak_src = load_peaks()
+    dom = max(acc, key=lambda k: acc[k])
+    achieved = abytes[dom] / (acc[dom] / 1e3) / 1e9 if acc[dom] > 0 else 0.0
+    st = nl.stats()
+    line = {"metric": "pins/s fwd+grad, batched placements", "value": value, "unit": "pins/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{B} placements (base + N(0, 5 um) jitter) of a {st['pins']}-pin "
+                                   f"synthetic netlist, depth {w.info['depth']}, gamma {GAMMA} ps, "
+                                   f"fwd (AT+LSE+RAT) + gradient per placement",
+                       "pins": st["pins"], "placements": B, "tile_pins": args.tile_pins or 4,
+                       "chunk": chunk, "l2": "flushed between steps (512 MB write)"},
+            "plain": {"value": plain_value, "unit": "pins/s",
+                      "how": "the same placements one per call on the single-placement dataflow schedule",
+                      "ms_per_step": 1e3 * plain_s / plain_steps},
+            "speedup_vs_plain": value / plain_value,
+            "gpu_launches": int(sum(launches.values())) * args.steps,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                         "ms_by_kind": {k: round(v, 4) for k, v in acc.items()},
+                         "step_algorithmic_bytes": int(sum(abytes.values())),
+                         "step_frac": sum(abytes.values()) / (total_s / args.steps) / 1e9 / peak},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -53,8 +53,9 @@ typedef enum {
     STA_ERR_NOT_DAG = 2,     /* the timing graph has a cycle */
     STA_ERR_OOM = 3,         /* device or host allocation failed */
     STA_ERR_CUDA = 4,        /* a CUDA runtime call failed */
-    STA_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired (reported by the next
-                                synchronizing call: summary / host-output queries) */
+    STA_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired; reported once, by the
+                                next synchronizing call (sta_synchronize or a call with
+                                host output); results since the previous report are invalid */
     STA_ERR_STATE = 6        /* call out of order (e.g. gradient before forward) */
 } StaStatus;
 
@@ -96,8 +97,13 @@ typedef struct {
 typedef struct {
     int32_t use_graphs;  /* 1 (default): replay each sweep as a CUDA graph */
     int32_t profile;     /* 1: bracket every launch with CUDA events (see sta_query_profile) */
-    int32_t schedule;    /* STA_SCHED_DATAFLOW (default) or STA_SCHED_LEVELS */
-    int32_t reserved[5];
+    int32_t schedule;    /* STA_SCHED_DATAFLOW (default), STA_SCHED_LEVELS or STA_SCHED_BATCH */
+    int32_t num_placements; /* STA_SCHED_BATCH: placements B analysed together (>= 1; 0 = 1) */
+    int32_t tile_pins;   /* STA_SCHED_BATCH task shape: nets are packed into one task while
+                            their pins total at most tile_pins (0 = default 4) */
+    int32_t chunk;       /* STA_SCHED_BATCH task shape: nets of more than `chunk` sinks are
+                            split into tasks of `chunk` sinks (0 = default 64) */
+    int32_t reserved[2];
 } StaOptions;
 
 /* StaOptions.schedule.  Both compute the same quantities: arrival, slew,
@@ -110,6 +116,15 @@ typedef struct {
  *   LEVELS    one kernel launch per level per sweep (Section 3.1.2). */
 #define STA_SCHED_DATAFLOW 0
 #define STA_SCHED_LEVELS 1
+/*   BATCH     B placements (position sets) of one netlist in every call: the
+ *             dataflow sweeps with lanes mapped to placements (32 placements
+ *             per warp task).  Every per-pin input and output gains a leading
+ *             placement dimension: positions and gradients [B][num_pins][2],
+ *             summaries [B][STA_SUM_COUNT], pin results [B][num_pins][k],
+ *             endpoint slacks [B][num_end][2], loss weights w [B][2].
+ *             A placement's results do not depend on B or on the other
+ *             placements (bit-identical to the same placement alone). */
+#define STA_SCHED_BATCH 2
 
 typedef struct StaHandle StaHandle;
 
@@ -169,6 +184,18 @@ StaStatus sta_backward_grad(StaHandle *h, const float *w, int w_on_device, float
  * the handle's own stream. */
 StaStatus sta_stream_wait(StaHandle *h, void *stream);
 
+/* Block until every sweep of the handle has finished.  Returns STA_ERR_TIMEOUT
+ * if a bounded wait of the dataflow schedule expired since the last report
+ * (each dependency wait gives up after 1 s; the sweep then ends with invalid
+ * results instead of hanging), else STA_OK.  The handle stays usable. */
+StaStatus sta_synchronize(StaHandle *h);
+
+/* Test hook for the bounded waits (dataflow schedule only, else STA_ERR_STATE):
+ * the next sta_forward runs with its last dependent task waiting for one
+ * producer more than it has, so that wait expires after its 1 s budget and the
+ * next synchronizing call returns STA_ERR_TIMEOUT.  Later calls are unaffected. */
+StaStatus sta_debug_expire_wait(StaHandle *h);
+
 /* Copy the STA_SUM_COUNT summary values (double) to out, a device pointer if
  * on_device != 0 (asynchronous), else host (synchronizes `stream`). */
 StaStatus sta_query_summary(StaHandle *h, double *out, int on_device, void *stream);
@@ -208,7 +235,8 @@ enum {
     STA_PROF_REQUIRED = 4,   /* required-time sweep */
     STA_PROF_SEED = 5,       /* loss weights (and, LEVELS only, endpoint seeds) */
     STA_PROF_ADJOINT = 6,    /* adjoint sweep */
-    STA_PROF_KINDS = 7
+    STA_PROF_OUTPUT = 7,     /* BATCH: gradient from device layout to [B][num_pins][2] */
+    STA_PROF_KINDS = 8
 };
 
 /* Per-kind launch counts of one set_positions + forward(LSE|RAT) +

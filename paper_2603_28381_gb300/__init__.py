@@ -37,10 +37,16 @@ def _stream_ptr(stream) -> int:
 
 
 class StaEngine:
-    """One netlist resident on the current CUDA device."""
+    """One netlist resident on the current CUDA device.
+
+    schedule "batch" analyses ``num_placements`` position sets B at once: every
+    per-pin array gains a leading placement dimension ([B, P, 2] positions and
+    gradients, [B, E, 2] endpoint slacks, one summary per placement) and the
+    loss weights are per placement ([B, 2])."""
 
     def __init__(self, netlist, library, use_graphs: bool = True, profile: bool = False,
-                 schedule: str = "dataflow"):
+                 schedule: str = "dataflow", num_placements: int = 1, tile_pins: int = 0,
+                 chunk: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("StaEngine needs a CUDA device (there is no CPU path)")
@@ -48,9 +54,13 @@ class StaEngine:
         self.num_pins = int(netlist.num_pins)
         self.num_end = int(netlist.end_pins.shape[0])
         self.device = torch.device("cuda", torch.cuda.current_device())
-        sched = {"dataflow": _sta.SCHED_DATAFLOW, "levels": _sta.SCHED_LEVELS}[schedule]
+        sched = {"dataflow": _sta.SCHED_DATAFLOW, "levels": _sta.SCHED_LEVELS,
+                 "batch": _sta.SCHED_BATCH}[schedule]
         self.schedule = schedule
-        self.h = _sta.sta_create(netlist, library, use_graphs, profile, sched)
+        self.batched = schedule == "batch"
+        self.B = int(num_placements) if self.batched else 1
+        self.h = _sta.sta_create(netlist, library, use_graphs, profile, sched,
+                                 self.B if self.batched else 0, tile_pins, chunk)
         self.sizes = _sta.sta_query_sizes(self.h)
         self.gamma = None
 
@@ -75,12 +85,12 @@ class StaEngine:
         torch = _torch()
         if isinstance(xy, torch.Tensor):
             t = xy.detach()
-            assert t.dtype == torch.float32 and t.is_contiguous() and t.numel() == 2 * self.num_pins
+            assert t.dtype == torch.float32 and t.is_contiguous() and t.numel() == 2 * self.num_pins * self.B
             _sta.sta_set_positions(self.h, t.data_ptr(), 1 if t.is_cuda else 0, _stream_ptr(stream))
             self._xy_keep = t
         else:
             a = np.ascontiguousarray(np.asarray(xy, np.float32)).reshape(-1)
-            assert a.size == 2 * self.num_pins
+            assert a.size == 2 * self.num_pins * self.B
             _sta.sta_set_positions(self.h, a.ctypes.data, 0, _stream_ptr(stream))
 
     def forward(self, gamma: float = 10.0, lse: bool = True, rat: bool = True, stream=None) -> None:
@@ -92,16 +102,19 @@ class StaEngine:
                       stream=None):
         """d(w[0] TNS_gamma + w[1] WNS_gamma)/d(x, y) as a [P,2] float32 CUDA tensor."""
         torch = _torch()
+        shape = (self.B, self.num_pins, 2) if self.batched else (self.num_pins, 2)
         if out is None:
-            out = torch.empty(self.num_pins, 2, dtype=torch.float32, device=self.device)
-        assert out.dtype == torch.float32 and out.is_contiguous() and out.numel() == 2 * self.num_pins
+            out = torch.empty(*shape, dtype=torch.float32, device=self.device)
+        assert out.dtype == torch.float32 and out.is_contiguous() and out.numel() == 2 * self.num_pins * self.B
         on_dev = 1 if out.is_cuda else 0
         if isinstance(w, torch.Tensor) and w.is_cuda:
             wt = w.detach().to(torch.float32).contiguous()
             _sta.sta_backward_grad(self.h, wt.data_ptr(), 1, out.data_ptr(), on_dev, _stream_ptr(stream))
             self._w_keep = wt
         else:
-            wa = np.asarray(w, np.float32)
+            wa = np.ascontiguousarray(np.asarray(w, np.float32))
+            if self.batched:
+                wa = np.ascontiguousarray(np.broadcast_to(wa, (self.B, 2)))
             _sta.sta_backward_grad(self.h, wa.ctypes.data, 0, out.data_ptr(), on_dev, _stream_ptr(stream))
         return out
 
@@ -109,10 +122,22 @@ class StaEngine:
         """Order `stream` after all queued work of the handle (sta_stream_wait)."""
         _sta.sta_stream_wait(self.h, _stream_ptr(stream))
 
-    def summary(self, stream=None) -> Dict[str, float]:
-        out = np.zeros(8, np.float64)
+    def synchronize(self) -> None:
+        """Wait for the handle's sweeps; raises StaError (STA_ERR_TIMEOUT) if a
+        bounded dependency wait expired since the last report (sta_synchronize)."""
+        _sta.sta_synchronize(self.h)
+
+    def _debug_expire_wait(self) -> None:
+        """Test hook: the next forward runs one dependency wait into its budget
+        (sta_debug_expire_wait)."""
+        _sta.sta_debug_expire_wait(self.h)
+
+    def summary(self, stream=None):
+        """Summary dict (a list of B dicts for the batched schedule)."""
+        out = np.zeros((self.B, 8), np.float64)
         _sta.sta_query_summary(self.h, out.ctypes.data, 0, _stream_ptr(stream))
-        return dict(zip(SUMMARY_KEYS, out.tolist()))
+        rows = [dict(zip(SUMMARY_KEYS, r.tolist())) for r in out]
+        return rows if self.batched else rows[0]
 
     def summary_device(self, out, stream=None):
         _sta.sta_query_summary(self.h, out.data_ptr(), 1, _stream_ptr(stream))
@@ -125,7 +150,7 @@ class StaEngine:
         for k, want, width in (("at", at, 4), ("slew", slew, 4), ("rat", rat, 4), ("ats", ats, 2),
                                ("slack", slack, 2)):
             if want:
-                bufs[k] = np.zeros((P, width), np.float32)
+                bufs[k] = np.zeros((self.B, P, width) if self.batched else (P, width), np.float32)
         ptr = lambda k: bufs[k].ctypes.data if k in bufs else None
         _sta.sta_query_pins(self.h, ptr("at"), ptr("slew"), ptr("rat"), ptr("ats"), ptr("slack"), 0,
                             _stream_ptr(stream))
@@ -133,9 +158,9 @@ class StaEngine:
         return res
 
     def endpoints(self, stream=None) -> np.ndarray:
-        out = np.zeros((max(self.num_end, 1), 2), np.float32)
-        _sta.sta_query_endpoints(self.h, out.ctypes.data, 0, _stream_ptr(stream))
-        return out[:self.num_end]
+        out = np.zeros((self.B, self.num_end, 2), np.float32)
+        _sta.sta_query_endpoints(self.h, out.ctypes.data if self.num_end else None, 0, _stream_ptr(stream))
+        return out if self.batched else out[0]
 
 
 class TimingLoss:

@@ -40,12 +40,14 @@ class StaLibrary(ctypes.Structure):
 
 
 class StaOptions(ctypes.Structure):
-    _fields_ = [("use_graphs", _i32), ("profile", _i32), ("schedule", _i32), ("reserved", _i32 * 5)]
+    _fields_ = [("use_graphs", _i32), ("profile", _i32), ("schedule", _i32), ("num_placements", _i32),
+                ("tile_pins", _i32), ("chunk", _i32), ("reserved", _i32 * 2)]
 
 
-PROF_KINDS = ("positions", "net_rc", "forward", "endpoints", "required", "seed", "adjoint")
+PROF_KINDS = ("positions", "net_rc", "forward", "endpoints", "required", "seed", "adjoint", "output")
 SCHED_DATAFLOW = 0
 SCHED_LEVELS = 1
+SCHED_BATCH = 2
 
 
 class StaError(RuntimeError):
@@ -68,6 +70,8 @@ def _load() -> ctypes.CDLL:
         "sta_backward_grad": ([H, _p, ctypes.c_int, _p, ctypes.c_int, _p], ctypes.c_int),
         "sta_query_summary": ([H, _p, ctypes.c_int, _p], ctypes.c_int),
         "sta_stream_wait": ([H, _p], ctypes.c_int),
+        "sta_synchronize": ([H], ctypes.c_int),
+        "sta_debug_expire_wait": ([H], ctypes.c_int),
         "sta_query_pins": ([H, _p, _p, _p, _p, _p, ctypes.c_int, _p], ctypes.c_int),
         "sta_query_endpoints": ([H, _p, ctypes.c_int, _p], ctypes.c_int),
         "sta_levelize": ([ctypes.POINTER(StaNetlistDesc), _p, _p, _p, _p], ctypes.c_int),
@@ -92,6 +96,7 @@ _lib = _load()
 EXPORTS = ("sta_create", "sta_set_positions", "sta_forward", "sta_backward_grad",
            "sta_query_summary", "sta_query_pins", "sta_query_endpoints", "sta_levelize",
            "sta_query_sizes", "sta_query_profile", "sta_stream_wait", "sta_destroy",
+           "sta_synchronize", "sta_debug_expire_wait",
            "sta_last_error", "sta_abi_version", "sta_endpoint_summary_noalloc")
 
 
@@ -161,12 +166,14 @@ def sta_levelize(nl):
 
 
 def sta_create(nl, lib, use_graphs: bool = True, profile: bool = False,
-               schedule: int = SCHED_DATAFLOW) -> int:
+               schedule: int = SCHED_DATAFLOW, num_placements: int = 0, tile_pins: int = 0,
+               chunk: int = 0) -> int:
     keep = _Keep()
     d = netlist_desc(nl, keep)
     l = library_desc(lib, keep)
     opts = StaOptions(use_graphs=1 if use_graphs else 0, profile=1 if profile else 0,
-                      schedule=int(schedule))
+                      schedule=int(schedule), num_placements=int(num_placements),
+                      tile_pins=int(tile_pins), chunk=int(chunk))
     h = ctypes.c_void_p()
     _check(_lib.sta_create(ctypes.byref(d), ctypes.byref(l), ctypes.byref(opts), ctypes.byref(h)),
            "sta_create")
@@ -193,6 +200,14 @@ def sta_backward_grad(h: int, w_ptr: int, w_on_device: int, grad_ptr: int, on_de
 
 def sta_stream_wait(h: int, stream: int) -> None:
     _check(_lib.sta_stream_wait(h, stream), "sta_stream_wait")
+
+
+def sta_synchronize(h: int) -> None:
+    _check(_lib.sta_synchronize(h), "sta_synchronize")
+
+
+def sta_debug_expire_wait(h: int) -> None:
+    _check(_lib.sta_debug_expire_wait(h), "sta_debug_expire_wait")
 
 
 def sta_query_summary(h: int, out_ptr: int, on_device: int, stream: int) -> None:

@@ -260,6 +260,179 @@ StaStatus ordering(const StaNetlistDesc& nl, std::vector<int32_t>& net_level, in
     return STA_OK;
 }
 
+StaStatus build_tasks(Layout& o, const TaskShape& sh, std::string& err) {
+    if (sh.pack_pins < 1 || sh.pack_nets < 1 || sh.big < 1 || sh.chunk < 1)
+        return err = "task shape: every field must be >= 1", STA_ERR_INVALID_ARG;
+    const int32_t P = o.P, V = o.N, A = o.A;
+    o.shape = sh;
+    // forward: per level, packed nets of at most `big` pins (several nets while
+    // they fit in pack_pins, at most pack_nets), then chunks of `chunk` sinks of
+    // the larger nets
+    std::vector<int32_t> pin_fprod(P, -1), net_step(V, -1);
+    std::vector<int32_t> bigs;
+    std::vector<std::vector<int32_t>> lvl_big(o.L), lvl_pack(o.L);  // pack: (n0, nn) pairs
+    for (int32_t l = 0; l < o.L; ++l) {
+        for (int32_t i = o.lvl_net[l]; i < o.lvl_net[l + 1];) {
+            const int32_t sz = o.net_ptr[i + 1] - o.net_ptr[i];
+            if (sz > sh.big) {
+                lvl_big[l].push_back(i++);
+                continue;
+            }
+            int32_t n0 = i, pins = 0, cnt = 0;
+            while (i < o.lvl_net[l + 1] && cnt < sh.pack_nets) {
+                const int32_t z = o.net_ptr[i + 1] - o.net_ptr[i];
+                if (z > sh.big || (cnt > 0 && pins + z > sh.pack_pins)) break;
+                pins += z;
+                ++cnt;
+                ++i;
+            }
+            lvl_pack[l].push_back(n0);
+            lvl_pack[l].push_back(cnt);
+        }
+    }
+    o.ftask.clear();
+    for (int32_t l = 0; l < o.L; ++l) {
+        for (size_t k = 0; k < lvl_pack[l].size(); k += 2) {
+            const int32_t n0 = lvl_pack[l][k], nn = lvl_pack[l][k + 1];
+            const int32_t t = (int32_t)(o.ftask.size() / 4);
+            const int32_t p0 = o.net_ptr[n0], p1 = o.net_ptr[n0 + nn];
+            o.ftask.insert(o.ftask.end(), {n0, nn, p0, p1 - p0});
+            for (int32_t p = p0; p < p1; ++p) pin_fprod[p] = t;
+        }
+        for (int32_t n : lvl_big[l]) {
+            for (int32_t p0 = o.net_ptr[n] + 1; p0 < o.net_ptr[n + 1]; p0 += sh.chunk) {
+                const int32_t cnt = std::min(sh.chunk, o.net_ptr[n + 1] - p0);
+                const int32_t t = (int32_t)(o.ftask.size() / 4);
+                o.ftask.insert(o.ftask.end(), {n, -1, p0, cnt});
+                for (int32_t p = p0; p < p0 + cnt; ++p) pin_fprod[p] = t;
+            }
+            bigs.push_back(n);
+        }
+    }
+    o.big_nets = bigs;
+    o.TF = (int32_t)(o.ftask.size() / 4);
+    o.arc_prod.resize(A);
+    for (int32_t a = 0; a < A; ++a) o.arc_prod[a] = pin_fprod[o.arc_pin[a]];
+
+    // backward: per level in reverse, partial chunks of the large nets, their
+    // driver steps, the packed nets, then the gradient chunks of the large nets
+    o.btask.clear();
+    o.baux.clear();
+    o.npart = 0;
+    for (int32_t l = o.L - 1; l >= 0; --l) {
+        const size_t nb = lvl_big[l].size();
+        std::vector<int32_t> first_ptask(nb), first_slot(nb), nchunks(nb), dtask(nb);
+        for (size_t k = 0; k < nb; ++k) {
+            const int32_t n = lvl_big[l][k];
+            first_ptask[k] = (int32_t)o.baux.size();
+            first_slot[k] = o.npart;
+            for (int32_t p0 = o.net_ptr[n] + 1; p0 < o.net_ptr[n + 1]; p0 += sh.chunk) {
+                const int32_t cnt = std::min(sh.chunk, o.net_ptr[n + 1] - p0);
+                o.btask.insert(o.btask.end(), {n, -1, p0, cnt});
+                o.baux.push_back(o.npart++);
+            }
+            nchunks[k] = o.npart - first_slot[k];
+        }
+        for (size_t k = 0; k < nb; ++k) {
+            const int32_t n = lvl_big[l][k];
+            dtask[k] = (int32_t)o.baux.size();
+            net_step[n] = dtask[k];
+            o.btask.insert(o.btask.end(), {n, -2, first_slot[k], nchunks[k]});
+            o.baux.push_back(first_ptask[k]);
+        }
+        for (size_t k = 0; k < lvl_pack[l].size(); k += 2) {
+            const int32_t n0 = lvl_pack[l][k], nn = lvl_pack[l][k + 1];
+            const int32_t t = (int32_t)o.baux.size();
+            o.btask.insert(o.btask.end(), {n0, nn, o.net_ptr[n0], o.net_ptr[n0 + nn] - o.net_ptr[n0]});
+            o.baux.push_back(0);
+            for (int32_t n = n0; n < n0 + nn; ++n) net_step[n] = t;
+        }
+        for (size_t k = 0; k < nb; ++k) {
+            const int32_t n = lvl_big[l][k];
+            for (int32_t p0 = o.net_ptr[n] + 1; p0 < o.net_ptr[n + 1]; p0 += sh.chunk) {
+                const int32_t cnt = std::min(sh.chunk, o.net_ptr[n + 1] - p0);
+                o.btask.insert(o.btask.end(), {n, -3, p0, cnt});
+                o.baux.push_back(dtask[k]);
+            }
+        }
+    }
+    o.TB = (int32_t)o.baux.size();
+    o.pin_cons.assign(P, -1);
+    for (int32_t n = 0; n < V; ++n)
+        for (int32_t a = o.net_arc_ptr[n]; a < o.net_arc_ptr[n + 1]; ++a) o.pin_cons[o.arc_pin[a]] = net_step[n];
+
+    // dependency counts and consumer lists (distinct producer per consumer)
+    auto build_edges = [](int32_t T, const std::vector<std::vector<int32_t>>& prods, std::vector<int32_t>& indeg,
+                          std::vector<int32_t>& out_ptr, std::vector<int32_t>& out) {
+        indeg.assign(T, 0);
+        out_ptr.assign(T + 1, 0);
+        for (int32_t t = 0; t < T; ++t) {
+            indeg[t] = (int32_t)prods[t].size();
+            for (int32_t q : prods[t]) ++out_ptr[q + 1];
+        }
+        for (int32_t t = 0; t < T; ++t) out_ptr[t + 1] += out_ptr[t];
+        out.assign(out_ptr[T], 0);
+        std::vector<int32_t> fill(out_ptr.begin(), out_ptr.end() - 1);
+        for (int32_t t = 0; t < T; ++t)
+            for (int32_t q : prods[t]) out[fill[q]++] = t;
+    };
+    auto uniq = [](std::vector<int32_t>& v) {
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        if (!v.empty() && v.front() < 0) v.erase(v.begin());
+    };
+    {
+        std::vector<std::vector<int32_t>> prods(o.TF);
+        for (int32_t t = 0; t < o.TF; ++t) {
+            const int32_t n0 = o.ftask[4 * t], nn = o.ftask[4 * t + 1] > 0 ? o.ftask[4 * t + 1] : 1;
+            for (int32_t a = o.net_arc_ptr[n0]; a < o.net_arc_ptr[n0 + nn]; ++a) prods[t].push_back(o.arc_prod[a]);
+            uniq(prods[t]);
+        }
+        build_edges(o.TF, prods, o.f_indeg, o.f_out_ptr, o.f_out);
+    }
+    {
+        std::vector<std::vector<int32_t>> prods(o.TB);
+        for (int32_t t = 0; t < o.TB; ++t) {
+            const int32_t kind = o.btask[4 * t + 1], p0 = o.btask[4 * t + 2], np = o.btask[4 * t + 3];
+            if (kind == -2) {
+                for (int32_t k = 0; k < np; ++k) prods[t].push_back(o.baux[t] + k);
+            } else if (kind == -3) {
+                prods[t].push_back(o.baux[t]);
+            } else {  // packed nets or a partial chunk: the arc steps that feed its sinks
+                for (int32_t p = p0; p < p0 + np; ++p) prods[t].push_back(o.pin_cons[p]);
+            }
+            uniq(prods[t]);
+        }
+        build_edges(o.TB, prods, o.b_indeg, o.b_out_ptr, o.b_out);
+    }
+
+    // Every task may only wait for tasks listed before it: the dataflow
+    // kernels rely on this for progress.
+    for (int32_t t = 0; t < o.TF; ++t)
+        for (int32_t k = o.f_out_ptr[t]; k < o.f_out_ptr[t + 1]; ++k)
+            if (o.f_out[k] <= t) return err = "internal: forward dependency order", STA_ERR_INVALID_ARG;
+    for (int32_t t = 0; t < o.TB; ++t)
+        for (int32_t k = o.b_out_ptr[t]; k < o.b_out_ptr[t + 1]; ++k)
+            if (o.b_out[k] <= t) return err = "internal: backward dependency order", STA_ERR_INVALID_ARG;
+    for (int32_t t = 0; t < o.TF; ++t) {
+        const int32_t n0 = o.ftask[4 * t], nn = o.ftask[4 * t + 1] > 0 ? o.ftask[4 * t + 1] : 1;
+        for (int32_t n = n0; n < n0 + nn; ++n)
+            for (int32_t a = o.net_arc_ptr[n]; a < o.net_arc_ptr[n + 1]; ++a)
+                if (o.arc_prod[a] >= t) return err = "internal: forward task order", STA_ERR_INVALID_ARG;
+    }
+    for (int32_t t = 0; t < o.TB; ++t) {
+        const int32_t kind = o.btask[4 * t + 1], p0 = o.btask[4 * t + 2], np = o.btask[4 * t + 3];
+        if (kind == -2) {
+            if (o.baux[t] + np > t) return err = "internal: backward task order", STA_ERR_INVALID_ARG;
+            continue;
+        }
+        if (kind == -3 && o.baux[t] >= t) return err = "internal: backward task order", STA_ERR_INVALID_ARG;
+        for (int32_t p = p0; p < p0 + np; ++p)
+            if (o.pin_cons[p] >= t) return err = "internal: backward task order", STA_ERR_INVALID_ARG;
+    }
+    return STA_OK;
+}
+
 StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& out, std::string& err) {
     StaStatus st = check_library(lib, err);
     if (st != STA_OK) return st;
@@ -363,147 +536,11 @@ StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& 
     o.lvl_ctask[o.L] = (int32_t)o.ctask.size();
 
     // ---- dataflow task lists ----
-    {
-        const int32_t A = o.A;
-        std::vector<int32_t> pin_fprod(P, -1), net_step(V, -1);
-        o.ftask.clear();
-        for (int32_t l = 0; l < o.L; ++l) {
-            for (int32_t k = o.lvl_wtask[l]; k < o.lvl_wtask[l + 1]; ++k) {
-                const int32_t n0 = o.wtask[2 * k], nn = o.wtask[2 * k + 1];
-                const int32_t t = (int32_t)(o.ftask.size() / 4);
-                const int32_t p0 = o.net_ptr[n0], p1 = o.net_ptr[n0 + nn];
-                o.ftask.insert(o.ftask.end(), {n0, nn, p0, p1 - p0});
-                for (int32_t p = p0; p < p1; ++p) pin_fprod[p] = t;
-            }
-            for (int32_t k = o.lvl_ctask[l]; k < o.lvl_ctask[l + 1]; ++k) {
-                const int32_t n = o.ctask[k];
-                for (int32_t p0 = o.net_ptr[n] + 1; p0 < o.net_ptr[n + 1]; p0 += kWarpPins) {
-                    const int32_t cnt = std::min(kWarpPins, o.net_ptr[n + 1] - p0);
-                    const int32_t t = (int32_t)(o.ftask.size() / 4);
-                    o.ftask.insert(o.ftask.end(), {n, -1, p0, cnt});
-                    for (int32_t p = p0; p < p0 + cnt; ++p) pin_fprod[p] = t;
-                }
-            }
-        }
-        o.TF = (int32_t)(o.ftask.size() / 4);
-        o.arc_prod.resize(A);
-        for (int32_t a = 0; a < A; ++a) o.arc_prod[a] = pin_fprod[o.arc_pin[a]];
-
-        o.btask.clear();
-        o.baux.clear();
-        o.npart = 0;
-        for (int32_t l = o.L - 1; l >= 0; --l) {
-            const int32_t c0 = o.lvl_ctask[l], c1 = o.lvl_ctask[l + 1];
-            std::vector<int32_t> first_ptask(c1 - c0), first_slot(c1 - c0), nchunks(c1 - c0), dtask(c1 - c0);
-            for (int32_t k = c0; k < c1; ++k) {  // partial chunks of the large nets
-                const int32_t n = o.ctask[k];
-                first_ptask[k - c0] = (int32_t)o.baux.size();
-                first_slot[k - c0] = o.npart;
-                for (int32_t p0 = o.net_ptr[n] + 1; p0 < o.net_ptr[n + 1]; p0 += kWarpPins) {
-                    const int32_t cnt = std::min(kWarpPins, o.net_ptr[n + 1] - p0);
-                    o.btask.insert(o.btask.end(), {n, -1, p0, cnt});
-                    o.baux.push_back(o.npart++);
-                }
-                nchunks[k - c0] = o.npart - first_slot[k - c0];
-            }
-            for (int32_t k = c0; k < c1; ++k) {  // their driver steps
-                const int32_t n = o.ctask[k];
-                dtask[k - c0] = (int32_t)o.baux.size();
-                net_step[n] = dtask[k - c0];
-                o.btask.insert(o.btask.end(), {n, -2, first_slot[k - c0], nchunks[k - c0]});
-                o.baux.push_back(first_ptask[k - c0]);
-            }
-            for (int32_t k = o.lvl_wtask[l]; k < o.lvl_wtask[l + 1]; ++k) {  // packed small nets
-                const int32_t n0 = o.wtask[2 * k], nn = o.wtask[2 * k + 1];
-                const int32_t t = (int32_t)o.baux.size();
-                o.btask.insert(o.btask.end(), {n0, nn, o.net_ptr[n0], o.net_ptr[n0 + nn] - o.net_ptr[n0]});
-                o.baux.push_back(0);
-                for (int32_t n = n0; n < n0 + nn; ++n) net_step[n] = t;
-            }
-            for (int32_t k = c0; k < c1; ++k) {  // gradient chunks of the large nets
-                const int32_t n = o.ctask[k];
-                for (int32_t p0 = o.net_ptr[n] + 1; p0 < o.net_ptr[n + 1]; p0 += kWarpPins) {
-                    const int32_t cnt = std::min(kWarpPins, o.net_ptr[n + 1] - p0);
-                    o.btask.insert(o.btask.end(), {n, -3, p0, cnt});
-                    o.baux.push_back(dtask[k - c0]);
-                }
-            }
-        }
-        o.TB = (int32_t)o.baux.size();
-        o.pin_cons.assign(P, -1);
-        for (int32_t n = 0; n < V; ++n)
-            for (int32_t a = o.net_arc_ptr[n]; a < o.net_arc_ptr[n + 1]; ++a) o.pin_cons[o.arc_pin[a]] = net_step[n];
-
-        // dependency counts and consumer lists (distinct producer per consumer)
-        auto build_edges = [](int32_t T, const std::vector<std::vector<int32_t>>& prods, std::vector<int32_t>& indeg,
-                              std::vector<int32_t>& out_ptr, std::vector<int32_t>& out) {
-            indeg.assign(T, 0);
-            out_ptr.assign(T + 1, 0);
-            for (int32_t t = 0; t < T; ++t) {
-                indeg[t] = (int32_t)prods[t].size();
-                for (int32_t q : prods[t]) ++out_ptr[q + 1];
-            }
-            for (int32_t t = 0; t < T; ++t) out_ptr[t + 1] += out_ptr[t];
-            out.assign(out_ptr[T], 0);
-            std::vector<int32_t> fill(out_ptr.begin(), out_ptr.end() - 1);
-            for (int32_t t = 0; t < T; ++t)
-                for (int32_t q : prods[t]) out[fill[q]++] = t;
-        };
-        auto uniq = [](std::vector<int32_t>& v) {
-            std::sort(v.begin(), v.end());
-            v.erase(std::unique(v.begin(), v.end()), v.end());
-            if (!v.empty() && v.front() < 0) v.erase(v.begin());
-        };
-        {
-            std::vector<std::vector<int32_t>> prods(o.TF);
-            for (int32_t t = 0; t < o.TF; ++t) {
-                const int32_t n0 = o.ftask[4 * t], nn = o.ftask[4 * t + 1] > 0 ? o.ftask[4 * t + 1] : 1;
-                for (int32_t a = o.net_arc_ptr[n0]; a < o.net_arc_ptr[n0 + nn]; ++a) prods[t].push_back(o.arc_prod[a]);
-                uniq(prods[t]);
-            }
-            build_edges(o.TF, prods, o.f_indeg, o.f_out_ptr, o.f_out);
-        }
-        {
-            std::vector<std::vector<int32_t>> prods(o.TB);
-            for (int32_t t = 0; t < o.TB; ++t) {
-                const int32_t kind = o.btask[4 * t + 1], p0 = o.btask[4 * t + 2], np = o.btask[4 * t + 3];
-                if (kind == -2) {
-                    for (int32_t k = 0; k < np; ++k) prods[t].push_back(o.baux[t] + k);
-                } else if (kind == -3) {
-                    prods[t].push_back(o.baux[t]);
-                } else {  // packed nets or a partial chunk: the arc steps that feed its sinks
-                    for (int32_t p = p0; p < p0 + np; ++p) prods[t].push_back(o.pin_cons[p]);
-                }
-                uniq(prods[t]);
-            }
-            build_edges(o.TB, prods, o.b_indeg, o.b_out_ptr, o.b_out);
-        }
-
-        // Every task may only wait for tasks listed before it: the dataflow
-        // kernels rely on this for progress.
-        for (int32_t t = 0; t < o.TF; ++t)
-            for (int32_t k = o.f_out_ptr[t]; k < o.f_out_ptr[t + 1]; ++k)
-                if (o.f_out[k] <= t) return err = "internal: forward dependency order", STA_ERR_INVALID_ARG;
-        for (int32_t t = 0; t < o.TB; ++t)
-            for (int32_t k = o.b_out_ptr[t]; k < o.b_out_ptr[t + 1]; ++k)
-                if (o.b_out[k] <= t) return err = "internal: backward dependency order", STA_ERR_INVALID_ARG;
-        for (int32_t t = 0; t < o.TF; ++t) {
-            const int32_t n0 = o.ftask[4 * t], nn = o.ftask[4 * t + 1] > 0 ? o.ftask[4 * t + 1] : 1;
-            for (int32_t n = n0; n < n0 + nn; ++n)
-                for (int32_t a = o.net_arc_ptr[n]; a < o.net_arc_ptr[n + 1]; ++a)
-                    if (o.arc_prod[a] >= t) return err = "internal: forward task order", STA_ERR_INVALID_ARG;
-        }
-        for (int32_t t = 0; t < o.TB; ++t) {
-            const int32_t kind = o.btask[4 * t + 1], p0 = o.btask[4 * t + 2], np = o.btask[4 * t + 3];
-            if (kind == -2) {
-                if (o.baux[t] + np > t) return err = "internal: backward task order", STA_ERR_INVALID_ARG;
-                continue;
-            }
-            if (kind == -3 && o.baux[t] >= t) return err = "internal: backward task order", STA_ERR_INVALID_ARG;
-            for (int32_t p = p0; p < p0 + np; ++p)
-                if (o.pin_cons[p] >= t) return err = "internal: backward task order", STA_ERR_INVALID_ARG;
-        }
-    }
+    o.lvl_net.assign(o.L + 1, V);
+    for (int32_t k = V - 1; k >= 0; --k) o.lvl_net[no.level[no.order[k]]] = k;
+    for (int32_t l = o.L - 1; l >= 0; --l) o.lvl_net[l] = std::min(o.lvl_net[l], o.lvl_net[l + 1]);
+    st = build_tasks(o, TaskShape{}, err);
+    if (st != STA_OK) return st;
 
     // ---- constant per-pin state ----
     const float inf = std::numeric_limits<float>::infinity();

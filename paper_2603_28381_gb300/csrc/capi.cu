@@ -54,6 +54,15 @@ struct StaHandle {
     DfState d{};
     int schedule = STA_SCHED_DATAFLOW;
     int grid_fwd = 0, grid_bwd = 0;  // dataflow grids (blocks)
+    // batched schedule: B placements, lane per placement
+    int B = 1;
+    BatchState bs{};
+    const int32_t* pin_int = nullptr;  // [P] internal index of each original pin
+    const int32_t* big_dev = nullptr;  // [nbig] nets whose loads the prologue computes
+    int nbig = 0;
+    float* qscratch = nullptr;         // device scratch of the batched pin-slack query
+    size_t qscratch_bytes = 0;
+    bool batch() const { return schedule == STA_SCHED_BATCH; }
     std::vector<void*> allocs;
     size_t dev_bytes = 0;
     int device = 0;
@@ -78,6 +87,10 @@ struct StaHandle {
     // gradient sweep can carry it or a query needs it
     bool rat_pending = false;
     bool last_fused = false;
+    // host-visible words: [0] expiry flag read back, [1] [2] dependency count of the
+    // task a requested wait expiry stalls (raised, original)
+    int32_t* pinned = nullptr;
+    bool expire_next = false;  // the next forward sweep runs one wait into its budget
     // staging for host inputs / outputs
     void* stage = nullptr;
     size_t stage_bytes = 0;
@@ -87,7 +100,7 @@ struct StaHandle {
         std::vector<cudaEvent_t> ev;  // 2 per launch
         std::vector<int> kind;        // 1 per launch
         size_t next = 0;
-    } prof_pos, prof_fwd, prof_rat, prof_adj;
+    } prof_pos, prof_fwd, prof_rat, prof_adj, prof_out;
 
     template <typename T>
     StaStatus alloc(T*& p, size_t n) {
@@ -123,9 +136,11 @@ struct StaHandle {
             if (gx) cudaGraphExecDestroy(gx);
         for (void* p : allocs) cudaFree(p);
         if (stage) cudaFree(stage);
+        if (qscratch) cudaFree(qscratch);
+        if (pinned) cudaFreeHost(pinned);
         for (auto* ev : {ev_at, ev_fwd, ev_bwd})
             if (ev) cudaEventDestroy(ev);
-        for (Prof* pr : {&prof_pos, &prof_fwd, &prof_rat, &prof_adj})
+        for (Prof* pr : {&prof_pos, &prof_fwd, &prof_rat, &prof_adj, &prof_out})
             for (cudaEvent_t e : pr->ev) cudaEventDestroy(e);
         if (cap) cudaStreamDestroy(cap);
         if (side) cudaStreamDestroy(side);
@@ -192,7 +207,40 @@ void enqueue_backward_dataflow(StaHandle* h, int mode, float gamma, cudaStream_t
     launch_bwd_dataflow(h->g, h->s, h->d, h->grid_bwd, gamma, mode, st);
 }
 
+void enqueue_forward_batch(StaHandle* h, int lse, float gamma, cudaStream_t st) {
+    const Layout& L = h->lay;
+    const size_t G = (size_t)h->bs.G;
+    cudaMemsetAsync(h->d.fcnt, 0, sizeof(int32_t) * (L.TF ? L.TF * G : 1), st);
+    cudaMemsetAsync(h->d.heads, 0, sizeof(int32_t), st);
+    cudaMemsetAsync(h->d.abort_word, 0, sizeof(int32_t), st);
+    if (h->nbig) {
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
+        launch_batch_load(h->g, h->bs, h->big_dev, h->nbig, st);
+    }
+    {
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
+        launch_batch_fwd(h->g, h->bs, h->d, h->grid_fwd, gamma, lse, st);
+    }
+    ProfScope ps(h, &h->prof_fwd, STA_PROF_ENDPOINTS, st);
+    launch_batch_endpoints(h->g, h->bs, gamma, lse, st);
+}
+
+void enqueue_backward_batch(StaHandle* h, int mode, float gamma, cudaStream_t st) {
+    const Layout& L = h->lay;
+    StaHandle::Prof* pr = (mode & 2) ? &h->prof_adj : &h->prof_rat;
+    pr->next = 0;
+    cudaMemsetAsync((mode & 2) ? h->d.acnt : h->d.rcnt, 0, sizeof(int32_t) * (L.TB ? L.TB * (size_t)h->bs.G : 1), st);
+    cudaMemsetAsync(h->d.heads + ((mode & 2) ? 2 : 1), 0, sizeof(int32_t), st);
+    ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJOINT : STA_PROF_REQUIRED, st);
+    launch_batch_bwd(h->g, h->bs, h->d, h->grid_bwd, gamma, mode, st);
+}
+
 void enqueue_forward(StaHandle* h, int lse, float gamma, cudaStream_t st) {
+    if (h->batch()) {
+        h->prof_fwd.next = 0;
+        enqueue_forward_batch(h, lse, gamma, st);
+        return;
+    }
     if (h->schedule == STA_SCHED_DATAFLOW) {
         h->prof_fwd.next = 0;
         enqueue_forward_dataflow(h, lse, gamma, st);
@@ -214,6 +262,10 @@ void enqueue_forward(StaHandle* h, int lse, float gamma, cudaStream_t st) {
 }
 
 void enqueue_backward(StaHandle* h, int mode, float gamma, cudaStream_t st) {
+    if (h->batch()) {
+        enqueue_backward_batch(h, mode, gamma, st);
+        return;
+    }
     if (h->schedule == STA_SCHED_DATAFLOW) {
         enqueue_backward_dataflow(h, mode, gamma, st);
         return;
@@ -270,6 +322,21 @@ StaStatus check_launch() {
     return STA_OK;
 }
 
+// Synchronize `st` and report a bounded device-side wait that expired since the
+// last report (the sticky word is read in stream order, then cleared).
+StaStatus sync_checked(StaHandle* h, cudaStream_t st) {
+    CUDA_TRY(cudaMemcpyAsync(h->pinned, h->d.abort_word + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (h->pinned[0] != 0) {
+        CUDA_TRY(cudaMemsetAsync(h->d.abort_word + 1, 0, sizeof(int32_t), st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return set_err(STA_ERR_TIMEOUT,
+                       "a dependency wait of the dataflow schedule exceeded its 1 s budget; the results of "
+                       "the sweeps since the previous report are invalid");
+    }
+    return STA_OK;
+}
+
 // A backward sweep of the given mode, as a cached graph (re-captured when
 // gamma changes) or as direct launches.
 StaStatus launch_graph_or_direct(StaHandle* h, cudaGraphExec_t* gx, float* key, float gamma, int mode,
@@ -285,6 +352,67 @@ StaStatus launch_graph_or_direct(StaHandle* h, cudaGraphExec_t* gx, float* key, 
     }
     enqueue_backward(h, mode, gamma, st);
     return check_launch();
+}
+
+// Device state of the batched schedule: per-placement arrays, the inverse pin
+// permutation, the prologue's net list, constant state broadcast to every
+// placement.
+StaStatus init_batch(StaHandle* h) {
+    const Layout& L = h->lay;
+    BatchState& b = h->bs;
+    b.B = h->B;
+    b.Bp = (h->B + 31) / 32 * 32;
+    b.G = b.Bp / 32;
+    const size_t P = L.P, N = L.N, E = L.E, Bp = b.Bp;
+    StaStatus st = STA_OK;
+#define BSTEP(x)                  \
+    do {                          \
+        st = (x);                 \
+        if (st != STA_OK) return st; \
+    } while (0)
+    BSTEP(h->alloc(b.xy, P * Bp));
+    BSTEP(h->alloc(b.load, N * Bp));
+    BSTEP(h->alloc(b.at, 4 * P * Bp));
+    BSTEP(h->alloc(b.slew, 4 * P * Bp));
+    BSTEP(h->alloc(b.ats, 2 * P * Bp));
+    BSTEP(h->alloc(b.rat, 4 * P * Bp));
+    BSTEP(h->alloc(b.g_ats, 2 * P * Bp));
+    BSTEP(h->alloc(b.g_slew, 2 * P * Bp));
+    BSTEP(h->alloc(b.grad, P * Bp));
+    BSTEP(h->alloc(b.ep_slack, E * Bp));
+    BSTEP(h->alloc(b.summary, STA_SUM_COUNT * Bp));
+    BSTEP(h->alloc(b.red, kRedBlocks * Bp * (kBatchEpBytes / sizeof(double))));
+    BSTEP(h->alloc(b.params, 2 * Bp));
+    BSTEP(h->alloc(b.part, (size_t)L.npart * kPartFloats * Bp));
+    BSTEP(h->alloc(b.rpart, (size_t)L.npart * kPartFloats * Bp));
+    BSTEP(h->alloc(b.net_gload, N * Bp));
+    std::vector<int32_t> inv(P);
+    for (size_t i = 0; i < P; ++i) inv[L.pin_orig[i]] = (int32_t)i;
+    BSTEP(h->upload(h->pin_int, inv));
+    BSTEP(h->upload(h->big_dev, L.big_nets));
+    h->nbig = (int)L.big_nets.size();
+#undef BSTEP
+    auto zero = [&](void* p, size_t bytes) { return cudaMemset(p, 0, bytes); };
+    if (zero(b.xy, P * Bp * 8) || zero(b.load, N * Bp * 4) || zero(b.g_ats, 2 * P * Bp * 4) ||
+        zero(b.g_slew, 2 * P * Bp * 4) || zero(b.grad, P * Bp * 8) || zero(b.summary, STA_SUM_COUNT * Bp * 8) ||
+        zero(b.params, 2 * Bp * 4) || zero(b.net_gload, N * Bp * 4))
+        return set_err(STA_ERR_CUDA, "cudaMemset failed");
+    // asserted arrival / slew and required-time constraints, the same for every placement
+    if (P) {
+        st = h->staging(P * 16);
+        if (st != STA_OK) return st;
+        float* tmp = static_cast<float*>(h->stage);
+        const std::pair<float*, const std::vector<float>*> init[] = {{b.at, &L.at0}, {b.slew, &L.slew0},
+                                                                       {b.rat, &L.rat0}};
+        for (const auto& it : init) {
+            CUDA_TRY(cudaMemcpy(tmp, it.second->data(), P * 16, cudaMemcpyHostToDevice));
+            launch_batch_broadcast(it.first, tmp, (long long)P * 4, (int)Bp, 0);
+            CUDA_TRY(cudaDeviceSynchronize());
+        }
+        launch_batch_init_ats(b, (int)P, 0);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return STA_OK;
 }
 
 }  // namespace
@@ -339,12 +467,33 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     if (opts) {
         h->use_graphs = opts->use_graphs != 0;
         h->profile = opts->profile != 0;
-        if (opts->schedule != STA_SCHED_DATAFLOW && opts->schedule != STA_SCHED_LEVELS) {
-            std::string keep = "StaOptions.schedule must be STA_SCHED_DATAFLOW or STA_SCHED_LEVELS";
-            delete h;
-            return set_err(STA_ERR_INVALID_ARG, keep);
-        }
+        if (opts->schedule != STA_SCHED_DATAFLOW && opts->schedule != STA_SCHED_LEVELS &&
+            opts->schedule != STA_SCHED_BATCH)
+            return fail(set_err(STA_ERR_INVALID_ARG, "StaOptions.schedule must be DATAFLOW, LEVELS or BATCH"));
         h->schedule = opts->schedule;
+        if (h->batch()) {
+            if (opts->num_placements < 0 || opts->num_placements > (1 << 16) || opts->tile_pins < 0 ||
+                opts->chunk < 0)
+                return fail(set_err(STA_ERR_INVALID_ARG, "StaOptions: num_placements in [0, 65536], tile_pins, "
+                                                         "chunk >= 0"));
+            h->B = opts->num_placements > 0 ? opts->num_placements : 1;
+            TaskShape sh;
+            sh.pack_pins = opts->tile_pins > 0 ? opts->tile_pins : 4;
+            sh.pack_nets = 1 << 20;
+            sh.chunk = opts->chunk > 0 ? opts->chunk : 64;
+            sh.big = sh.chunk + 1;  // a driver and `chunk` sinks still form one task
+            try {
+                std::string err;
+                StaStatus st = build_tasks(h->lay, sh, err);
+                if (st != STA_OK) return fail(set_err(st, err));
+                const long long G = (h->B + 31) / 32;
+                if ((long long)h->lay.TF * G >= (1ll << 31) || (long long)h->lay.TB * G >= (1ll << 31) ||
+                    (long long)h->lay.P * 4 * G * 32 >= (1ll << 40))
+                    return fail(set_err(STA_ERR_INVALID_ARG, "num_placements too large for this netlist"));
+            } catch (const std::bad_alloc&) {
+                return fail(set_err(STA_ERR_OOM, "host allocation failed"));
+            }
+        }
     }
     const Layout& L = h->lay;
     cudaError_t ce = cudaGetDevice(&h->device);
@@ -385,21 +534,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     g.E = L.E;
 
     const size_t P = L.P;
-    STEP(h->alloc(s.xy, P));
-    STEP(h->alloc(s.load, L.N));
-    STEP(h->alloc(s.wdi, P));
-    STEP(h->alloc(s.at, 4 * P));
-    STEP(h->alloc(s.slew, 4 * P));
-    STEP(h->alloc(s.ats, 2 * P));
-    STEP(h->alloc(s.adel, 4 * (size_t)L.A));
-    STEP(h->alloc(s.rat, 4 * P));
-    STEP(h->alloc(s.g_ats, 2 * P));
-    STEP(h->alloc(s.g_slew, 2 * P));
-    STEP(h->alloc(s.grad, P));
-    STEP(h->alloc(s.ep_slack, L.E));
-    STEP(h->alloc(s.red, (size_t)kRedBlocks * 8));
-    STEP(h->alloc(s.summary, STA_SUM_COUNT));
-    STEP(h->alloc(s.params, 4));
+    const bool bat = h->batch();
     DfState& d = h->d;
     {
         const int32_t* cp = nullptr;
@@ -417,29 +552,53 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         STEP(h->upload(d.b_out_ptr, L.b_out_ptr));
         STEP(h->upload(d.b_out, L.b_out));
     }
-    STEP(h->alloc(d.fcnt, L.TF));
-    STEP(h->alloc(d.rcnt, L.TB));
-    STEP(h->alloc(d.acnt, L.TB));
+    const size_t G = bat ? (size_t)(h->B + 31) / 32 : 1;
+    STEP(h->alloc(d.fcnt, L.TF * G));
+    STEP(h->alloc(d.rcnt, L.TB * G));
+    STEP(h->alloc(d.acnt, L.TB * G));
     STEP(h->alloc(d.heads, 4));
-    STEP(h->alloc(d.rpart, (size_t)L.npart * kPartFloats));
-    STEP(h->alloc(d.apart, (size_t)L.npart * kPartFloats));
-    STEP(h->alloc(d.net_gload, L.N));
-    STEP(h->alloc(d.abort_word, 1));
+    STEP(h->alloc(d.rpart, bat ? 1 : (size_t)L.npart * kPartFloats));
+    STEP(h->alloc(d.apart, bat ? 1 : (size_t)L.npart * kPartFloats));
+    STEP(h->alloc(d.net_gload, bat ? 1 : L.N));
+    STEP(h->alloc(d.abort_word, 2));
     d.TF = L.TF;
     d.TB = L.TB;
-#undef STEP
-    auto zero = [&](void* p, size_t bytes) { return cudaMemset(p, 0, bytes); };
-    if (zero(s.xy, P * 8) || zero(s.load, L.N * 4) || zero(s.wdi, P * 8) || zero(s.ats, P * 8) ||
-        zero(s.adel, (size_t)L.A * 16) || zero(s.g_ats, P * 8) || zero(s.g_slew, P * 8) || zero(s.grad, P * 8) ||
-        zero(s.summary, STA_SUM_COUNT * 8) || zero(s.params, 16) || zero(s.red, (size_t)kRedBlocks * 64) ||
-        zero(d.abort_word, 4) || zero(d.heads, 16) || zero(d.net_gload, (size_t)L.N * 4))
+    if (bat) {
+        STEP(init_batch(h));
+    } else {
+        STEP(h->alloc(s.xy, P));
+        STEP(h->alloc(s.load, L.N));
+        STEP(h->alloc(s.wdi, P));
+        STEP(h->alloc(s.at, 4 * P));
+        STEP(h->alloc(s.slew, 4 * P));
+        STEP(h->alloc(s.ats, 2 * P));
+        STEP(h->alloc(s.adel, 4 * (size_t)L.A));
+        STEP(h->alloc(s.rat, 4 * P));
+        STEP(h->alloc(s.g_ats, 2 * P));
+        STEP(h->alloc(s.g_slew, 2 * P));
+        STEP(h->alloc(s.grad, P));
+        STEP(h->alloc(s.ep_slack, L.E));
+        STEP(h->alloc(s.red, (size_t)kRedBlocks * 8));
+        STEP(h->alloc(s.summary, STA_SUM_COUNT));
+        STEP(h->alloc(s.params, 4));
+        auto zero = [&](void* p, size_t bytes) { return cudaMemset(p, 0, bytes); };
+        if (zero(s.xy, P * 8) || zero(s.load, L.N * 4) || zero(s.wdi, P * 8) || zero(s.ats, P * 8) ||
+            zero(s.adel, (size_t)L.A * 16) || zero(s.g_ats, P * 8) || zero(s.g_slew, P * 8) || zero(s.grad, P * 8) ||
+            zero(s.summary, STA_SUM_COUNT * 8) || zero(s.params, 16) || zero(s.red, (size_t)kRedBlocks * 64) ||
+            zero(d.net_gload, (size_t)L.N * 4))
+            return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
+        // constant state: asserted AT/slew (and LSE AT = late AT), required-time seeds
+        if (cudaMemcpy(s.at, L.at0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(s.slew, L.slew0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(s.rat, L.rat0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(set_err(STA_ERR_CUDA, "initial state upload failed"));
+        launch_init_ats(s, L.P, 0);
+    }
+    if (cudaMemset(d.abort_word, 0, 8) != cudaSuccess || cudaMemset(d.heads, 0, 16) != cudaSuccess)
         return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
-    // constant state: asserted AT/slew (and LSE AT = late AT), required-time seeds
-    if (cudaMemcpy(s.at, L.at0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(s.slew, L.slew0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(s.rat, L.rat0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess)
-        return fail(set_err(STA_ERR_CUDA, "initial state upload failed"));
-    launch_init_ats(s, L.P, 0);
+#undef STEP
+    if (cudaMallocHost(&h->pinned, 4 * sizeof(int32_t)) != cudaSuccess)
+        return fail(set_err(STA_ERR_OOM, "cudaMallocHost failed"));
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_at, cudaEventDisableTiming) != cudaSuccess ||
@@ -448,15 +607,17 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         return fail(set_err(STA_ERR_CUDA, "stream/event creation failed"));
     {   // dataflow grids: the whole GPU for the forward sweep; half each for the
         // required-time and adjoint sweeps, which run concurrently
-        const int fmax = dataflow_max_blocks(1), bmax = dataflow_max_blocks(0);
+        const int fmax = bat ? batch_max_blocks(1) : dataflow_max_blocks(1);
+        const int bmax = bat ? batch_max_blocks(0) : dataflow_max_blocks(0);
         h->grid_fwd = fmax > 0 ? fmax : 1;
-        h->grid_bwd = bmax > 1 ? bmax / 2 : 1;
+        h->grid_bwd = bat ? (bmax > 0 ? bmax : 1) : (bmax > 1 ? bmax / 2 : 1);
         if (cudaGetLastError() != cudaSuccess) return fail(set_err(STA_ERR_CUDA, "occupancy query failed"));
     }
     if (h->profile) {  // event pairs for every launch of each sequence, made before any capture
         const size_t nl = (size_t)L.L;
         const std::pair<StaHandle::Prof*, size_t> sizes[] = {
-            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 2}, {&h->prof_rat, nl + 1}, {&h->prof_adj, nl + 1}};
+            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 2}, {&h->prof_rat, nl + 1}, {&h->prof_adj, nl + 1},
+            {&h->prof_out, 1}};
         for (const auto& ps : sizes) {
             ps.first->kind.assign(ps.second, 0);
             for (size_t k = 0; k < 2 * ps.second; ++k) {
@@ -488,16 +649,18 @@ StaStatus sta_set_positions(StaHandle* h, const float* xy, int on_device, void* 
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_bwd, 0));
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
     const float2* src = reinterpret_cast<const float2*>(xy);
+    const size_t bytes = (size_t)h->lay.P * 8 * (h->batch() ? h->B : 1);
     if (!on_device) {
-        StaStatus s2 = h->staging((size_t)h->lay.P * 8);
+        StaStatus s2 = h->staging(bytes);
         if (s2 != STA_OK) return s2;
-        CUDA_TRY(cudaMemcpyAsync(h->stage, xy, (size_t)h->lay.P * 8, cudaMemcpyHostToDevice, st));
+        if (bytes) CUDA_TRY(cudaMemcpyAsync(h->stage, xy, bytes, cudaMemcpyHostToDevice, st));
         src = static_cast<const float2*>(h->stage);
     }
     {
         h->prof_pos.next = 0;
         ProfScope ps(h, &h->prof_pos, STA_PROF_POSITIONS, st);
-        launch_gather_xy(h->g, h->s, src, st);
+        if (h->batch()) launch_batch_xy_in(h->bs, h->pin_int, h->lay.P, src, st);
+        else launch_gather_xy(h->g, h->s, src, st);
     }
     StaStatus s3 = check_launch();
     if (s3 != STA_OK) return s3;
@@ -516,7 +679,24 @@ StaStatus sta_forward(StaHandle* h, uint32_t flags, float gamma, void* stream) {
     cudaStream_t st = as_stream(stream);
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_bwd, 0));
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
-    if (h->use_graphs) {
+    if (h->expire_next) {
+        // one forward task waits for one producer more than it has: its wait runs
+        // into the budget, the sweep ends early and the expiry is reported
+        h->expire_next = false;
+        const Layout& L = h->lay;
+        int task = -1;
+        for (int t = L.TF - 1; t >= 0 && task < 0; --t)
+            if (L.f_indeg[t] > 0) task = t;
+        if (task < 0) return set_err(STA_ERR_STATE, "no forward task has producers");
+        int32_t* indeg = const_cast<int32_t*>(h->d.f_indeg) + task;
+        h->pinned[1] = L.f_indeg[task] + 1;
+        h->pinned[2] = L.f_indeg[task];
+        CUDA_TRY(cudaMemcpyAsync(indeg, h->pinned + 1, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        enqueue_forward(h, lse, gamma, st);
+        StaStatus s2 = check_launch();
+        if (s2 != STA_OK) return s2;
+        CUDA_TRY(cudaMemcpyAsync(indeg, h->pinned + 2, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    } else if (h->use_graphs) {
         if (!h->gx_fwd[lse] || h->gx_fwd_gamma[lse] != gamma) {
             StaStatus s2 = capture(h, &h->gx_fwd[lse], [&](cudaStream_t c) { enqueue_forward(h, lse, gamma, c); });
             if (s2 != STA_OK) return s2;
@@ -530,7 +710,7 @@ StaStatus sta_forward(StaHandle* h, uint32_t flags, float gamma, void* stream) {
     }
     CUDA_TRY(cudaEventRecord(h->ev_at, st));
     h->rat_pending = false;
-    if ((flags & STA_FWD_RAT) && h->schedule == STA_SCHED_DATAFLOW) {
+    if ((flags & STA_FWD_RAT) && h->schedule != STA_SCHED_LEVELS) {
         // deferred: carried by the next gradient sweep, or launched when queried
         h->rat_pending = true;
         CUDA_TRY(cudaEventRecord(h->ev_fwd, st));
@@ -555,7 +735,12 @@ StaStatus sta_backward_grad(StaHandle* h, const float* w, int w_on_device, float
     if (!h->have_lse) return set_err(STA_ERR_STATE, "sta_forward with STA_FWD_LSE must come before sta_backward_grad");
     cudaStream_t st = as_stream(stream);
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_at, 0));
-    launch_set_weights(h->s, w_on_device ? w : nullptr, w_on_device ? 0.f : w[0], w_on_device ? 0.f : w[1], st);
+    if (h->batch()) {  // one weight pair per placement
+        CUDA_TRY(cudaMemcpyAsync(h->bs.params, w, sizeof(float) * 2 * h->B,
+                                 w_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    } else {
+        launch_set_weights(h->s, w_on_device ? w : nullptr, w_on_device ? 0.f : w[0], w_on_device ? 0.f : w[1], st);
+    }
     const float gamma = h->gamma_fwd;
     h->last_fused = h->rat_pending;
     if (h->rat_pending) {  // one sweep for the required times and the adjoint
@@ -567,14 +752,31 @@ StaStatus sta_backward_grad(StaHandle* h, const float* w, int w_on_device, float
         StaStatus s2 = launch_graph_or_direct(h, &h->gx_adj, &h->gx_adj_gamma, gamma, 2, st);
         if (s2 != STA_OK) return s2;
     }
-    const size_t bytes = (size_t)h->lay.P * 8;
-    if (bytes) {
-        CUDA_TRY(cudaMemcpyAsync(grad_xy, h->s.grad, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                 st));
+    if (h->batch()) {  // internal [P][Bp] -> the caller's [B][P][2]
+        const size_t bytes = (size_t)h->lay.P * 8 * h->B;
+        float2* dst = reinterpret_cast<float2*>(grad_xy);
+        if (!on_device) {
+            StaStatus s2 = h->staging(bytes);
+            if (s2 != STA_OK) return s2;
+            dst = static_cast<float2*>(h->stage);
+        }
+        {
+            h->prof_out.next = 0;
+            ProfScope ps(h, &h->prof_out, STA_PROF_OUTPUT, st);
+            launch_batch_out2(h->bs, h->pin_int, h->lay.P, h->bs.grad, dst, st);
+        }
+        StaStatus s3 = check_launch();
+        if (s3 != STA_OK) return s3;
+        if (!on_device && bytes) CUDA_TRY(cudaMemcpyAsync(grad_xy, dst, bytes, cudaMemcpyDeviceToHost, st));
+    } else {
+        const size_t bytes = (size_t)h->lay.P * 8;
+        if (bytes) {
+            CUDA_TRY(cudaMemcpyAsync(grad_xy, h->s.grad, bytes,
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        }
     }
     CUDA_TRY(cudaEventRecord(h->ev_bwd, st));
-    if (!on_device) CUDA_TRY(cudaStreamSynchronize(st));
-    return STA_OK;
+    return on_device ? STA_OK : sync_checked(h, st);
 }
 
 StaStatus sta_stream_wait(StaHandle* h, void* stream) {
@@ -585,21 +787,35 @@ StaStatus sta_stream_wait(StaHandle* h, void* stream) {
     return STA_OK;
 }
 
+StaStatus sta_synchronize(StaHandle* h) {
+    if (!h) return set_err(STA_ERR_INVALID_ARG, "null handle");
+    CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fwd, 0));
+    CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_bwd, 0));
+    return sync_checked(h, h->side);
+}
+
+StaStatus sta_debug_expire_wait(StaHandle* h) {
+    if (!h) return set_err(STA_ERR_INVALID_ARG, "null handle");
+    if (h->schedule == STA_SCHED_LEVELS) return set_err(STA_ERR_STATE, "the level schedule has no waits");
+    h->expire_next = true;
+    return STA_OK;
+}
+
 StaStatus sta_query_summary(StaHandle* h, double* out, int on_device, void* stream) {
     if (!h || !out) return set_err(STA_ERR_INVALID_ARG, "null argument");
     if (!h->have_fwd) return set_err(STA_ERR_STATE, "no forward pass yet");
     cudaStream_t st = as_stream(stream);
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
-    CUDA_TRY(cudaMemcpyAsync(out, h->s.summary, STA_SUM_COUNT * sizeof(double),
+    CUDA_TRY(cudaMemcpyAsync(out, h->batch() ? h->bs.summary : h->s.summary,
+                             STA_SUM_COUNT * sizeof(double) * (h->batch() ? h->B : 1),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    if (!on_device) CUDA_TRY(cudaStreamSynchronize(st));
-    return STA_OK;
+    return on_device ? STA_OK : sync_checked(h, st);
 }
 
 namespace {
 
 StaStatus deliver(StaHandle* h, const float* internal, int k, float* out, int on_device, cudaStream_t st) {
-    const size_t bytes = (size_t)h->lay.P * k * sizeof(float);
+    const size_t bytes = (size_t)h->lay.P * k * sizeof(float) * (h->batch() ? h->B : 1);
     if (!bytes) return STA_OK;
     float* dst = out;
     if (!on_device) {
@@ -607,12 +823,13 @@ StaStatus deliver(StaHandle* h, const float* internal, int k, float* out, int on
         if (s2 != STA_OK) return s2;
         dst = static_cast<float*>(h->stage);
     }
-    launch_scatter(h->g, internal, dst, k, h->lay.P, st);
+    if (h->batch()) launch_batch_out(h->bs, h->pin_int, h->lay.P, internal, k, dst, st);
+    else launch_scatter(h->g, internal, dst, k, h->lay.P, st);
     StaStatus s3 = check_launch();
     if (s3 != STA_OK) return s3;
     if (!on_device) {
         CUDA_TRY(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(cudaStreamSynchronize(st));
+        return sync_checked(h, st);
     }
     return STA_OK;
 }
@@ -632,11 +849,26 @@ StaStatus sta_query_pins(StaHandle* h, float* at, float* slew, float* rat, float
     cudaStream_t st = as_stream(stream);
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
     StaStatus s2 = STA_OK;
-    if (at && (s2 = deliver(h, h->s.at, 4, at, on_device, st)) != STA_OK) return s2;
-    if (slew && (s2 = deliver(h, h->s.slew, 4, slew, on_device, st)) != STA_OK) return s2;
-    if (rat && (s2 = deliver(h, h->s.rat, 4, rat, on_device, st)) != STA_OK) return s2;
-    if (ats && (s2 = deliver(h, h->s.ats, 2, ats, on_device, st)) != STA_OK) return s2;
-    if (slack) {
+    const bool bat = h->batch();
+    if (at && (s2 = deliver(h, bat ? h->bs.at : h->s.at, 4, at, on_device, st)) != STA_OK) return s2;
+    if (slew && (s2 = deliver(h, bat ? h->bs.slew : h->s.slew, 4, slew, on_device, st)) != STA_OK) return s2;
+    if (rat && (s2 = deliver(h, bat ? h->bs.rat : h->s.rat, 4, rat, on_device, st)) != STA_OK) return s2;
+    if (ats && (s2 = deliver(h, bat ? h->bs.ats : h->s.ats, 2, ats, on_device, st)) != STA_OK) return s2;
+    if (slack && bat) {
+        const size_t need = (size_t)h->lay.P * 2 * h->bs.Bp * sizeof(float);
+        if (need > h->qscratch_bytes) {
+            if (h->qscratch) cudaFree(h->qscratch);
+            h->qscratch = nullptr;
+            h->qscratch_bytes = 0;
+            CUDA_TRY(cudaMalloc(&h->qscratch, need));
+            h->qscratch_bytes = need;
+        }
+        if (need) {
+            launch_batch_pin_slack(h->bs, h->lay.P, h->qscratch, st);
+            if ((s2 = check_launch()) != STA_OK) return s2;
+            if ((s2 = deliver(h, h->qscratch, 2, slack, on_device, st)) != STA_OK) return s2;
+        }
+    } else if (slack) {
         const size_t bytes = (size_t)h->lay.P * 8;
         if (bytes) {
             float* dst = slack;
@@ -648,7 +880,7 @@ StaStatus sta_query_pins(StaHandle* h, float* at, float* slew, float* rat, float
             if ((s2 = check_launch()) != STA_OK) return s2;
             if (!on_device) {
                 CUDA_TRY(cudaMemcpyAsync(slack, dst, bytes, cudaMemcpyDeviceToHost, st));
-                CUDA_TRY(cudaStreamSynchronize(st));
+                if ((s2 = sync_checked(h, st)) != STA_OK) return s2;
             }
         }
     }
@@ -660,10 +892,25 @@ StaStatus sta_query_endpoints(StaHandle* h, float* slack, int on_device, void* s
     if (!h->have_fwd) return set_err(STA_ERR_STATE, "no forward pass yet");
     cudaStream_t st = as_stream(stream);
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
-    if (h->lay.E) {
+    if (h->lay.E && h->batch()) {
+        const size_t bytes = (size_t)h->lay.E * 8 * h->B;
+        float2* dst = reinterpret_cast<float2*>(slack);
+        if (!on_device) {
+            StaStatus s2 = h->staging(bytes);
+            if (s2 != STA_OK) return s2;
+            dst = static_cast<float2*>(h->stage);
+        }
+        launch_batch_ep_out(h->bs, h->lay.E, dst, st);
+        StaStatus s3 = check_launch();
+        if (s3 != STA_OK) return s3;
+        if (!on_device) {
+            CUDA_TRY(cudaMemcpyAsync(slack, dst, bytes, cudaMemcpyDeviceToHost, st));
+            return sync_checked(h, st);
+        }
+    } else if (h->lay.E) {
         CUDA_TRY(cudaMemcpyAsync(slack, h->s.ep_slack, (size_t)h->lay.E * 8,
                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-        if (!on_device) CUDA_TRY(cudaStreamSynchronize(st));
+        if (!on_device) return sync_checked(h, st);
     }
     return STA_OK;
 }
@@ -678,7 +925,14 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
     const int32_t nw = L.lvl_wtask.empty() ? 0 : L.lvl_wtask.back(), nc = L.lvl_ctask.empty() ? 0 : L.lvl_ctask.back();
     launches[STA_PROF_POSITIONS] = L.P > 0 ? 1 : 0;
     launches[STA_PROF_ENDPOINTS] = 2;
-    if (h->schedule == STA_SCHED_DATAFLOW) {
+    launches[STA_PROF_OUTPUT] = (h->batch() && L.P > 0) ? 1 : 0;
+    if (h->batch()) {
+        launches[STA_PROF_NET_RC] = h->nbig > 0 ? 1 : 0;
+        launches[STA_PROF_FORWARD] = L.TF > 0 ? 1 : 0;
+        launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 1 : 0;
+        launches[STA_PROF_SEED] = 1;
+        launches[STA_PROF_ADJOINT] = L.TB > 0 ? 1 : 0;
+    } else if (h->schedule == STA_SCHED_DATAFLOW) {
         launches[STA_PROF_NET_RC] = nc > 0 ? 1 : 0;
         launches[STA_PROF_FORWARD] = L.TF > 0 ? 1 : 0;
         launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 1 : 0;  // fused into the adjoint sweep
@@ -695,7 +949,7 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
     for (int k = 0; k < STA_PROF_KINDS; ++k) ms[k] = 0.0;
     if (!h->profile) return set_err(STA_ERR_STATE, "handle was created without StaOptions.profile");
     CUDA_TRY(cudaDeviceSynchronize());
-    for (StaHandle::Prof* pr : {&h->prof_pos, &h->prof_fwd, &h->prof_rat, &h->prof_adj}) {
+    for (StaHandle::Prof* pr : {&h->prof_pos, &h->prof_fwd, &h->prof_rat, &h->prof_adj, &h->prof_out}) {
         for (size_t i = 0; i < pr->next && 2 * i + 1 < pr->ev.size(); ++i) {
             float t = 0.f;
             if (cudaEventElapsedTime(&t, pr->ev[2 * i], pr->ev[2 * i + 1]) == cudaSuccess) ms[pr->kind[i]] += t;

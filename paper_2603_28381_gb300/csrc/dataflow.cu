@@ -22,82 +22,11 @@
 // prologue kernel; in the backward pass a large net becomes partial-reduction
 // chunks, one driver task that combines them in a fixed order, and gradient
 // chunks, so every reduction stays deterministic.
+#include "dataflow_sync.cuh"
 #include "device_common.cuh"
 
 namespace sta {
 namespace {
-
-constexpr unsigned long long kWaitBudgetNs = 1000000000ull;  // 1 s per wait
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ int ld_acquire(const int32_t* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ int ld_relaxed(const int32_t* p) {
-    int v;
-    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Wait until cnt[t] reaches need (its producer count).  The whole warp polls
-// the one counter together (the lanes read the same address, one transaction)
-// with relaxed loads and acquires it once the count is reached; every branch
-// is decided by a warp vote, so the warp never splits into a polling lane and
-// waiting lanes (a split warp would run the rest of the task as separate
-// groups).  Bounded: after kWaitBudgetNs, or once any wait of the launch has
-// expired, it sets the abort word and returns (the host then reports
-// STA_ERR_TIMEOUT).
-__device__ __forceinline__ void wait_ready(const int32_t* cnt, int t, int need, int32_t* abort_word) {
-    if (need <= 0) return;
-    if (__all_sync(kFull, ld_acquire(cnt + t) >= need)) return;
-    unsigned long long t0 = 0;
-    for (unsigned it = 1;; ++it) {
-        __nanosleep(64);
-        if (__all_sync(kFull, ld_relaxed(cnt + t) >= need)) {
-            (void)ld_acquire(cnt + t);
-            return;
-        }
-        if ((it & 63) == 0) {
-            if (__any_sync(kFull, ld_relaxed(abort_word) != 0)) return;
-            const unsigned long long now = __shfl_sync(kFull, global_ns(), 0);
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > kWaitBudgetNs) {
-                if ((threadIdx.x & 31) == 0) atomicExch(abort_word, 1);
-                __syncwarp();
-                return;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ int grab(int32_t* head) {
-    int t = 0;
-    if ((threadIdx.x & 31) == 0) t = atomicAdd(head, 1);
-    return __shfl_sync(kFull, t, 0);
-}
-
-__device__ __forceinline__ void red_release_add(int32_t* p, int v) {
-    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Signal the task's consumers: one release increment per consumer, after a
-// warp barrier, so every lane's stores happen before each increment (the
-// barrier orders the lanes, the release makes their writes visible at GPU
-// scope to whoever acquires the counter).
-__device__ __forceinline__ void signal_consumers(int32_t* cnt, const int32_t* out_ptr, const int32_t* out, int t) {
-    __syncwarp();
-    const int k1 = out_ptr[t + 1];
-    for (int k = out_ptr[t] + (int)(threadIdx.x & 31); k < k1; k += 32) red_release_add(cnt + out[k], 1);
-}
 
 // ---------------------------------------------------------------------------
 // Forward
@@ -805,21 +734,6 @@ __global__ void __launch_bounds__(kBlock) k_bwd_df(DevNet g, DevState s, DfState
     }
 }
 
-template <typename K, typename... Args>
-void launch_coop(K kernel, int grid, cudaStream_t st, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kBlock);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
 }  // namespace
 
 int dataflow_max_blocks(int fwd) {
@@ -834,16 +748,16 @@ int dataflow_max_blocks(int fwd) {
 void launch_fwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int lse,
                          cudaStream_t st) {
     if (d.TF == 0) return;
-    if (lse) launch_coop(k_fwd_df<true>, grid, st, g, s, d, gamma);
-    else launch_coop(k_fwd_df<false>, grid, st, g, s, d, gamma);
+    if (lse) launch_coop(k_fwd_df<true>, grid, kBlock, st, g, s, d, gamma);
+    else launch_coop(k_fwd_df<false>, grid, kBlock, st, g, s, d, gamma);
 }
 
 void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int mode,
                          cudaStream_t st) {
     if (d.TB == 0) return;
-    if (mode == 1) launch_coop(k_bwd_df<1>, grid, st, g, s, d, gamma);
-    else if (mode == 2) launch_coop(k_bwd_df<2>, grid, st, g, s, d, gamma);
-    else launch_coop(k_bwd_df<3>, grid, st, g, s, d, gamma);
+    if (mode == 1) launch_coop(k_bwd_df<1>, grid, kBlock, st, g, s, d, gamma);
+    else if (mode == 2) launch_coop(k_bwd_df<2>, grid, kBlock, st, g, s, d, gamma);
+    else launch_coop(k_bwd_df<3>, grid, kBlock, st, g, s, d, gamma);
 }
 
 }  // namespace sta

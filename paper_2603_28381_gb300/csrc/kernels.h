@@ -67,9 +67,49 @@ struct DfState {
     float* rpart;            // [npart * kPartFloats] partials, required-time sweep
     float* apart;            // [npart * kPartFloats] partials, adjoint sweep
     float* net_gload;        // [N] d loss / d load of large nets
-    int32_t* abort_word;     // [1] set when a bounded wait expires
+    int32_t* abort_word;     // [2] [0] a bounded wait of the current sweep expired, [1] sticky copy
     int32_t TF, TB;
 };
+
+// Batched schedule (many placements of one netlist; lane = placement).
+// Per-placement state is pin-major, placement-minor: value[(row) * Bp + b].
+struct BatchState {
+    int32_t B, Bp, G;    // placements, padded to a multiple of 32, groups of 32
+    float2* xy;          // [P][Bp]
+    float* load;         // [N][Bp]
+    float* at;           // [P*4][Bp]
+    float* slew;         // [P*4][Bp]
+    float* ats;          // [P*2][Bp]
+    float* rat;          // [P*4][Bp]
+    float* g_ats;        // [P*2][Bp]
+    float* g_slew;       // [P*2][Bp]
+    float2* grad;        // [P][Bp], internal pin order
+    float2* ep_slack;    // [E][Bp]
+    double* summary;     // [Bp][STA_SUM_COUNT]
+    double* red;         // [kRedBlocks][Bp] endpoint partials (48 bytes each)
+    float* params;       // [Bp][2] w_tns, w_wns of each placement
+    float* part;         // [npart * kPartFloats][Bp] partials of large nets, adjoint sweeps
+    float* rpart;        // the same for required-time sweeps (which may overlap an adjoint sweep)
+    float* net_gload;    // [N][Bp] d loss / d load of large nets
+};
+constexpr size_t kBatchEpBytes = 48;  // one endpoint partial
+
+int batch_max_blocks(int fwd);
+void launch_batch_load(const DevNet& g, const BatchState& bs, const int32_t* big_nets, int nbig, cudaStream_t st);
+void launch_batch_fwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int lse,
+                      cudaStream_t st);
+void launch_batch_endpoints(const DevNet& g, const BatchState& bs, float gamma, int lse, cudaStream_t st);
+void launch_batch_bwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int mode,
+                      cudaStream_t st);
+void launch_batch_xy_in(const BatchState& bs, const int32_t* pin_int, int P, const float2* xy_user, cudaStream_t st);
+void launch_batch_out(const BatchState& bs, const int32_t* pin_int, int P, const float* in, int K, float* out,
+                      cudaStream_t st);
+void launch_batch_out2(const BatchState& bs, const int32_t* pin_int, int P, const float2* in, float2* out,
+                       cudaStream_t st);
+void launch_batch_pin_slack(const BatchState& bs, int P, float* scratch, cudaStream_t st);
+void launch_batch_ep_out(const BatchState& bs, int E, float2* out, cudaStream_t st);
+void launch_batch_broadcast(float* dst, const float* src, long long rows, int Bp, cudaStream_t st);
+void launch_batch_init_ats(const BatchState& bs, int P, cudaStream_t st);
 
 void launch_fwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int lse,
                          cudaStream_t st);

@@ -30,6 +30,19 @@ constexpr int kRedBlocks = 152;     // endpoint reduction partials (one per SM)
 constexpr float kKrc = 1e-3f;       // Ohm * fF in ps
 constexpr int kPartFloats = 12;     // floats per backward partial (large nets)
 
+// Granularity of the dataflow tasks: nets of at most `big` pins are packed
+// (consecutive nets of a level while their pins fit in pack_pins, at most
+// pack_nets of them; a net larger than pack_pins gets a task alone); larger nets
+// are split into chunks of `chunk` sinks.  The default is the single-placement
+// shape (lane per pin: 32 pins, 8 nets); the batched schedule (lane per
+// placement) uses smaller tasks.
+struct TaskShape {
+    int32_t pack_pins = kWarpPins;
+    int32_t pack_nets = kWarpNets;
+    int32_t big = kWarpPins;
+    int32_t chunk = kWarpPins;
+};
+
 struct Layout {
     int32_t P = 0;       // pins
     int32_t Pnet = 0;    // pins on nets (prefix of the internal order)
@@ -51,7 +64,11 @@ struct Layout {
     std::vector<int32_t> wtask;        // [2*W] (first net, number of nets)
     std::vector<int32_t> ctask;        // [Cb] net of each block task
 
+    std::vector<int32_t> lvl_net;      // [L+1] first internal net of each level
+
     // dataflow schedule (one persistent kernel per sweep, tasks in topological order)
+    TaskShape shape;
+    std::vector<int32_t> big_nets;   // nets split into chunks (their load comes from a prologue)
     //   forward task  {first net, nets (> 0) | -1 for a 32-sink chunk of a large net, first pin, pins}
     //   backward task {net(s), kind, first pin, pins}: kind > 0 packed nets (= count), -1 partial
     //   chunk of a large net, -2 its driver step (first pin = first partial slot, pins = chunks),
@@ -94,6 +111,10 @@ StaStatus levelize(const StaNetlistDesc& nl, const StaLibrary* lib, std::vector<
 
 // Full host-side layout for the device.
 StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& out, std::string& err);
+
+// (Re)build the dataflow task lists and dependency lists of a layout for a
+// task shape.  Checks that every task only depends on tasks listed before it.
+StaStatus build_tasks(Layout& o, const TaskShape& sh, std::string& err);
 
 // Processing order of description nets and device pin order (sta_levelize).
 StaStatus ordering(const StaNetlistDesc& nl, std::vector<int32_t>& net_level, int32_t& num_levels,

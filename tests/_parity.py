@@ -115,6 +115,41 @@ def run_gpu(nl, lib, xy, gamma=10.0, w=(1.0, 0.5), use_graphs=True, host_xy=Fals
     return res
 
 
+def run_gpu_batch(nl, lib, xyb, gamma=10.0, w=(1.0, 0.5), use_graphs=True, host_xy=False, engine=None,
+                  tile_pins=0, chunk=0):
+    """The batched schedule on B placements xyb [B,P,2]: one set_positions +
+    forward(LSE, RAT) + backward; a list of B per-placement result dicts."""
+    import torch
+
+    import paper_2603_28381_gb300 as sta
+    xyb = np.ascontiguousarray(np.asarray(xyb, np.float32))
+    B = xyb.shape[0]
+    eng = engine or sta.StaEngine(nl, lib, use_graphs=use_graphs, schedule="batch", num_placements=B,
+                                  tile_pins=tile_pins, chunk=chunk)
+    if host_xy:
+        eng.set_positions(xyb)
+    else:
+        eng.set_positions(torch.as_tensor(xyb).cuda())
+    eng.forward(gamma=gamma, lse=True, rat=True)
+    wb = np.broadcast_to(np.asarray(w, np.float32), (B, 2)) if np.ndim(w) < 2 else np.asarray(w, np.float32)
+    g = eng.backward_grad(torch.as_tensor(np.ascontiguousarray(wb)).cuda())
+    torch.cuda.synchronize()
+    pins = eng.pins()
+    ep = eng.endpoints()
+    summ = eng.summary()
+    g = g.cpu().numpy()
+    out = []
+    for b in range(B):
+        r = {k: v[b] for k, v in pins.items()}
+        r["ep_slack"] = ep[b]
+        r["summary"] = summ[b]
+        r["grad"] = g[b]
+        out.append(r)
+    if engine is None:
+        eng.close()
+    return out
+
+
 def _close(name, gpu, ora, tol):
     gpu = np.asarray(gpu, np.float64)
     ora = np.asarray(ora, np.float64)

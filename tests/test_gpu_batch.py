@@ -1,0 +1,125 @@
+"""Batched schedule: many placements of one netlist per call (lane per
+placement).  Every placement is compared with the FP64 oracle at the parity
+tolerances, and a placement's results must be bit-identical alone and in a
+batch (the per-placement arithmetic does not depend on the batch)."""
+import numpy as np
+import pytest
+
+import netgen
+import oracle
+from tests import _parity as tp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _placements(w, B, sigma=5.0, seed=7):
+    return netgen.jitter_positions(w.xy, B, sigma, seed)
+
+
+def _weights(B, seed=3):
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(0.5, 1.5, B), rng.uniform(0.0, 1.0, B)], 1).astype(np.float32)
+
+
+def _check_all(nl, lib, xyb, W, gamma, res, which=None):
+    for b in (range(len(res)) if which is None else which):
+        ora = oracle.sta(nl, lib, xyb[b], gamma, float(W[b, 0]), float(W[b, 1]))
+        tp.assert_parity(res[b], ora)
+
+
+@pytest.mark.parametrize("B", [1, 5, 33])
+def test_tiny_design_batches(B):
+    w = netgen.tiny_design(0)
+    xyb, W = _placements(w, B), _weights(B)
+    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W)
+    _check_all(w.netlist, w.library, xyb, W, 10.0, res)
+
+
+@pytest.mark.parametrize("tile_pins,chunk", [(1, 1), (16, 8), (4, 64), (64, 200)])
+def test_task_shapes_mid_size(tile_pins, chunk):
+    # power-law fanout and 400-sink primary-input nets: packed nets, single nets
+    # and chunked large nets, two placement groups with a ragged second group
+    w = netgen.superblue_like(3, scale=0.02, depth=40)
+    B = 40
+    xyb, W = _placements(w, B), _weights(B)
+    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 20.0, W, tile_pins=tile_pins, chunk=chunk)
+    _check_all(w.netlist, w.library, xyb, W, 20.0, res, which=[0, 17, 31, 32, 39])
+
+
+@pytest.mark.parametrize("idx", range(3))
+def test_edge_netlists_batched(idx):
+    name, nl, xy, lib = tp.edge_netlists()[idx]
+    B = 3
+    xyb = netgen.jitter_positions(xy, B, 2.0, 5)
+    W = _weights(B)
+    res = tp.run_gpu_batch(nl, lib, xyb, 10.0, W)
+    _check_all(nl, lib, xyb, W, 10.0, res)
+
+
+def test_alone_equals_in_batch_bitwise():
+    w = netgen.superblue_like(5, scale=0.01, depth=30)
+    B = 37
+    xyb, W = _placements(w, B, seed=11), _weights(B, seed=12)
+    full = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W)
+    for b in (0, 21, 36):
+        alone = tp.run_gpu_batch(w.netlist, w.library, xyb[b:b + 1], 10.0, W[b:b + 1])[0]
+        for k in ("at", "slew", "rat", "ats", "slack", "ep_slack", "grad"):
+            assert np.array_equal(alone[k], full[b][k]), (b, k)
+        assert alone["summary"] == full[b]["summary"]
+
+
+def test_host_buffers_graphs_and_repeats():
+    import torch
+    import paper_2603_28381_gb300 as sta
+    w = netgen.superblue_like(6, scale=0.01, depth=30)
+    B = 8
+    xyb, W = _placements(w, B), _weights(B)
+    a = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W)
+    b = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, host_xy=True, use_graphs=False)
+    for r, s in zip(a, b):
+        for k in ("at", "rat", "grad"):
+            assert np.array_equal(r[k], s[k])
+    # one engine, repeated steps with different positions, host gradient output
+    eng = sta.StaEngine(w.netlist, w.library, schedule="batch", num_placements=B)
+    for rep in range(3):
+        xr = _placements(w, B, seed=100 + rep)
+        eng.set_positions(torch.as_tensor(xr).cuda())
+        eng.forward(gamma=10.0)
+        g = eng.backward_grad(W, out=torch.empty(B, w.netlist.num_pins, 2))
+        ora = oracle.sta(w.netlist, w.library, xr[rep], 10.0, float(W[rep, 0]), float(W[rep, 1]))
+        gmax = np.abs(ora["grad"]).max()
+        assert np.abs(g[rep].numpy() - ora["grad"]).max() <= tp.GRAD_RTOL * gmax
+    eng.close()
+
+
+def test_batched_full_size_500k_64_placements():
+    # the batched workload: ~500k pins, depth 100, 64 placements with 5 um jitter;
+    # sampled placements against the oracle
+    w = netgen.superblue_like(2, scale=0.2, depth=100)
+    B = 64
+    xyb, W = _placements(w, B), _weights(B)
+    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W)
+    _check_all(w.netlist, w.library, xyb, W, 10.0, res, which=[0, 63])
+
+
+def test_batched_wait_expiry_reported():
+    import paper_2603_28381_gb300 as sta
+    w = netgen.tiny_design(2)
+    B = 4
+    xyb, W = _placements(w, B), _weights(B)
+    import torch
+    eng = sta.StaEngine(w.netlist, w.library, schedule="batch", num_placements=B)
+    eng.set_positions(torch.as_tensor(xyb).cuda())
+    eng._debug_expire_wait()
+    eng.forward(gamma=10.0)
+    with pytest.raises(sta.StaError) as ei:
+        eng.summary()
+    assert ei.value.status == 5
+    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, engine=eng)
+    _check_all(w.netlist, w.library, xyb, W, 10.0, res, which=[0, 3])
