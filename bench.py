@@ -52,8 +52,12 @@ def parse():
                          "batch: 64 placements of a ~500k-pin netlist per step")
     ap.add_argument("--placements", type=int, default=64)
     ap.add_argument("--verbose", action="store_true", help="per-step times on stderr")
+    ap.add_argument("--no-plain", action="store_true", help="batch: skip the one-placement-per-call comparison")
     ap.add_argument("--tile-pins", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--batch-sweep", default="levels", choices=["levels", "dataflow"])
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batch: use --tile-pins/--chunk/--batch-sweep instead of the autotuner's choice")
     return ap.parse_args()
 
 
@@ -452,7 +456,15 @@ def run_batch(args):
         return sum(ms) / 1e3
 
     eng = sta.StaEngine(nl, w.library, schedule="batch", num_placements=B, tile_pins=args.tile_pins,
-                        chunk=args.chunk)
+                        chunk=args.chunk, batch_sweep=args.batch_sweep)
+    tune = None
+    if not args.no_autotune:  # untimed: pick the task shape on this workload
+        eng.set_positions(xyb)
+        best, table = eng.autotune(tile_pins=(1, 2, 4), chunks=(8, 16, 32), sweeps=("levels", "dataflow"),
+                                   reps=3, gamma=GAMMA)
+        args.tile_pins, args.chunk, args.batch_sweep = best
+        tune = {"best": {"tile_pins": best[0], "chunk": best[1], "batch_sweep": best[2]},
+                "ms": {f"{a}/{c}/{s}": round(v, 3) for (a, c, s), v in table.items()}}
     clocks = Clocks(local)
     total_s = timed(eng, step, args.steps)
     clk = clocks.stop()
@@ -474,12 +486,12 @@ def run_batch(args):
         e.stream_wait()
 
     plain_steps = max(1, min(args.steps, 5))
-    plain_s = timed(one, plain, plain_steps)
+    plain_s = timed(one, plain, plain_steps) if not args.no_plain else float("nan")
     one.close()
     plain_value = B * P * plain_steps / plain_s
 
     prof = sta.StaEngine(nl, w.library, schedule="batch", num_placements=B, profile=True,
-                         tile_pins=args.tile_pins, chunk=args.chunk)
+                         tile_pins=args.tile_pins, chunk=args.chunk, batch_sweep=args.batch_sweep)
     for _ in range(2):
         step(prof)
     acc = {}
@@ -492,7 +504,7 @@ def run_batch(args):
             acc[k] = acc.get(k, 0.0) + v / nprof
     sizes = dict(pins=P, nets=prof.sizes["nets"], arcs=prof.sizes["arcs"], endpoints=prof.sizes["endpoints"])
     prof.close()
-    chunk = args.chunk or 64
+    chunk = args.chunk or 16
     fan = np.diff(nl.net_ptr)
     bigm = fan > chunk + 1
     abytes = algorithmic_bytes_batch(sizes, S, B, big=(int(bigm.sum()), int((fan[bigm] - 1).sum())))
@@ -508,7 +520,8 @@ def run_batch(args):
                                    f"synthetic netlist, depth {w.info['depth']}, gamma {GAMMA} ps, "
                                    f"fwd (AT+LSE+RAT) + gradient per placement",
                        "pins": st["pins"], "placements": B, "tile_pins": args.tile_pins or 4,
-                       "chunk": chunk, "l2": "flushed between steps (512 MB write)"},
+                       "chunk": chunk, "batch_sweep": args.batch_sweep, "autotune": tune,
+                       "l2": "flushed between steps (512 MB write)"},
             "plain": {"value": plain_value, "unit": "pins/s",
                       "how": "the same placements one per call on the single-placement dataflow schedule",
                       "ms_per_step": 1e3 * plain_s / plain_steps},

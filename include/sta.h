@@ -102,8 +102,9 @@ typedef struct {
     int32_t tile_pins;   /* STA_SCHED_BATCH task shape: nets are packed into one task while
                             their pins total at most tile_pins (0 = default 4) */
     int32_t chunk;       /* STA_SCHED_BATCH task shape: nets of more than `chunk` sinks are
-                            split into tasks of `chunk` sinks (0 = default 64) */
-    int32_t reserved[2];
+                            split into tasks of `chunk` sinks (0 = default 16) */
+    int32_t batch_sweep; /* STA_SCHED_BATCH: STA_BATCH_LEVELS (default) or STA_BATCH_DATAFLOW */
+    int32_t reserved[1];
 } StaOptions;
 
 /* StaOptions.schedule.  Both compute the same quantities: arrival, slew,
@@ -125,6 +126,15 @@ typedef struct {
  *             A placement's results do not depend on B or on the other
  *             placements (bit-identical to the same placement alone). */
 #define STA_SCHED_BATCH 2
+/* StaOptions.batch_sweep: how the batched schedule orders its tasks.
+ *   LEVELS    one launch per level (two per level in the backward where a level
+ *             has nets split into chunks), replayed as a CUDA graph; the tasks
+ *             of a level run without any waiting.
+ *   DATAFLOW  one persistent launch per sweep with per-task dependency
+ *             counters, as in STA_SCHED_DATAFLOW.
+ * Both give bit-identical results. */
+#define STA_BATCH_LEVELS 0
+#define STA_BATCH_DATAFLOW 1
 
 typedef struct StaHandle StaHandle;
 
@@ -190,11 +200,26 @@ StaStatus sta_stream_wait(StaHandle *h, void *stream);
  * results instead of hanging), else STA_OK.  The handle stays usable. */
 StaStatus sta_synchronize(StaHandle *h);
 
-/* Test hook for the bounded waits (dataflow schedule only, else STA_ERR_STATE):
+/* Test hook for the bounded waits (dataflow sweeps only: STA_SCHED_DATAFLOW, or
+ * STA_SCHED_BATCH with STA_BATCH_DATAFLOW; else STA_ERR_STATE):
  * the next sta_forward runs with its last dependent task waiting for one
  * producer more than it has, so that wait expires after its 1 s budget and the
  * next synchronizing call returns STA_ERR_TIMEOUT.  Later calls are unaffected. */
 StaStatus sta_debug_expire_wait(StaHandle *h);
+
+/* Autotuner of the batched schedule (STA_SCHED_BATCH only, else STATE): for
+ * every candidate (tile_pins[i], chunks[j], sweeps[k]) it rebuilds the task
+ * lists, replays one step (forward with LSE and required times, then the
+ * gradient sweep; smoothing gamma) as a CUDA graph reps times on the handle's
+ * current positions (sta_set_positions first, else STATE) and times it with
+ * CUDA events; then it keeps the fastest.  ms [n_tile][n_chunk][n_sweep]
+ * receives the mean step times in ms (may be NULL); best[3] = the chosen
+ * (tile_pins, chunk, batch_sweep).  Synchronizes the device; the analysis
+ * state is reset (call sta_forward again).  Results do not depend on the shape
+ * beyond rounding of sums over large nets. */
+StaStatus sta_autotune(StaHandle *h, const int32_t *tile_pins, int32_t n_tile, const int32_t *chunks,
+                       int32_t n_chunk, const int32_t *sweeps, int32_t n_sweep, int32_t reps, float gamma,
+                       float *ms, int32_t *best);
 
 /* Copy the STA_SUM_COUNT summary values (double) to out, a device pointer if
  * on_device != 0 (asynchronous), else host (synchronizes `stream`). */

@@ -46,7 +46,7 @@ class StaEngine:
 
     def __init__(self, netlist, library, use_graphs: bool = True, profile: bool = False,
                  schedule: str = "dataflow", num_placements: int = 1, tile_pins: int = 0,
-                 chunk: int = 0):
+                 chunk: int = 0, batch_sweep: str = "levels"):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("StaEngine needs a CUDA device (there is no CPU path)")
@@ -60,7 +60,8 @@ class StaEngine:
         self.batched = schedule == "batch"
         self.B = int(num_placements) if self.batched else 1
         self.h = _sta.sta_create(netlist, library, use_graphs, profile, sched,
-                                 self.B if self.batched else 0, tile_pins, chunk)
+                                 self.B if self.batched else 0, tile_pins, chunk,
+                                 {"levels": _sta.BATCH_LEVELS, "dataflow": _sta.BATCH_DATAFLOW}[batch_sweep])
         self.sizes = _sta.sta_query_sizes(self.h)
         self.gamma = None
 
@@ -126,6 +127,18 @@ class StaEngine:
         """Wait for the handle's sweeps; raises StaError (STA_ERR_TIMEOUT) if a
         bounded dependency wait expired since the last report (sta_synchronize)."""
         _sta.sta_synchronize(self.h)
+
+    def autotune(self, tile_pins=(1, 2, 4), chunks=(8, 16, 32), sweeps=("levels", "dataflow"), reps: int = 3,
+                 gamma: float = 10.0):
+        """Pick the batched schedule's task shape by timing each candidate on the
+        current positions (sta_autotune).  Returns (best, table): best =
+        (tile_pins, chunk, sweep name), table = {(tile_pins, chunk, sweep): ms}."""
+        names = {"levels": _sta.BATCH_LEVELS, "dataflow": _sta.BATCH_DATAFLOW}
+        inv = {v: k for k, v in names.items()}
+        best, ms = _sta.sta_autotune(self.h, list(tile_pins), list(chunks), [names[s] for s in sweeps], reps, gamma)
+        table = {(int(a), int(c), s): float(ms[i, j, k]) for i, a in enumerate(tile_pins)
+                 for j, c in enumerate(chunks) for k, s in enumerate(sweeps)}
+        return (best[0], best[1], inv[best[2]]), table
 
     def _debug_expire_wait(self) -> None:
         """Test hook: the next forward runs one dependency wait into its budget

@@ -41,13 +41,15 @@ class StaLibrary(ctypes.Structure):
 
 class StaOptions(ctypes.Structure):
     _fields_ = [("use_graphs", _i32), ("profile", _i32), ("schedule", _i32), ("num_placements", _i32),
-                ("tile_pins", _i32), ("chunk", _i32), ("reserved", _i32 * 2)]
+                ("tile_pins", _i32), ("chunk", _i32), ("batch_sweep", _i32), ("reserved", _i32 * 1)]
 
 
 PROF_KINDS = ("positions", "net_rc", "forward", "endpoints", "required", "seed", "adjoint", "output")
 SCHED_DATAFLOW = 0
 SCHED_LEVELS = 1
 SCHED_BATCH = 2
+BATCH_LEVELS = 0
+BATCH_DATAFLOW = 1
 
 
 class StaError(RuntimeError):
@@ -71,6 +73,7 @@ def _load() -> ctypes.CDLL:
         "sta_query_summary": ([H, _p, ctypes.c_int, _p], ctypes.c_int),
         "sta_stream_wait": ([H, _p], ctypes.c_int),
         "sta_synchronize": ([H], ctypes.c_int),
+        "sta_autotune": ([H, _p, _i32, _p, _i32, _p, _i32, _i32, ctypes.c_float, _p, _p], ctypes.c_int),
         "sta_debug_expire_wait": ([H], ctypes.c_int),
         "sta_query_pins": ([H, _p, _p, _p, _p, _p, ctypes.c_int, _p], ctypes.c_int),
         "sta_query_endpoints": ([H, _p, ctypes.c_int, _p], ctypes.c_int),
@@ -96,7 +99,7 @@ _lib = _load()
 EXPORTS = ("sta_create", "sta_set_positions", "sta_forward", "sta_backward_grad",
            "sta_query_summary", "sta_query_pins", "sta_query_endpoints", "sta_levelize",
            "sta_query_sizes", "sta_query_profile", "sta_stream_wait", "sta_destroy",
-           "sta_synchronize", "sta_debug_expire_wait",
+           "sta_synchronize", "sta_debug_expire_wait", "sta_autotune",
            "sta_last_error", "sta_abi_version", "sta_endpoint_summary_noalloc")
 
 
@@ -167,13 +170,13 @@ def sta_levelize(nl):
 
 def sta_create(nl, lib, use_graphs: bool = True, profile: bool = False,
                schedule: int = SCHED_DATAFLOW, num_placements: int = 0, tile_pins: int = 0,
-               chunk: int = 0) -> int:
+               chunk: int = 0, batch_sweep: int = BATCH_LEVELS) -> int:
     keep = _Keep()
     d = netlist_desc(nl, keep)
     l = library_desc(lib, keep)
     opts = StaOptions(use_graphs=1 if use_graphs else 0, profile=1 if profile else 0,
                       schedule=int(schedule), num_placements=int(num_placements),
-                      tile_pins=int(tile_pins), chunk=int(chunk))
+                      tile_pins=int(tile_pins), chunk=int(chunk), batch_sweep=int(batch_sweep))
     h = ctypes.c_void_p()
     _check(_lib.sta_create(ctypes.byref(d), ctypes.byref(l), ctypes.byref(opts), ctypes.byref(h)),
            "sta_create")
@@ -200,6 +203,18 @@ def sta_backward_grad(h: int, w_ptr: int, w_on_device: int, grad_ptr: int, on_de
 
 def sta_stream_wait(h: int, stream: int) -> None:
     _check(_lib.sta_stream_wait(h, stream), "sta_stream_wait")
+
+
+def sta_autotune(h: int, tile_pins, chunks, sweeps, reps: int, gamma: float):
+    """(best (tile_pins, chunk, sweep), ms table [n_tile, n_chunk, n_sweep])."""
+    tp_ = np.ascontiguousarray(tile_pins, np.int32)
+    ch = np.ascontiguousarray(chunks, np.int32)
+    sw = np.ascontiguousarray(sweeps, np.int32)
+    ms = np.zeros((tp_.size, ch.size, sw.size), np.float32)
+    best = np.zeros(3, np.int32)
+    _check(_lib.sta_autotune(h, tp_.ctypes.data, tp_.size, ch.ctypes.data, ch.size, sw.ctypes.data, sw.size,
+                             int(reps), float(gamma), ms.ctypes.data, best.ctypes.data), "sta_autotune")
+    return tuple(int(v) for v in best), ms
 
 
 def sta_synchronize(h: int) -> None:

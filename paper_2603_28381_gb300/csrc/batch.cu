@@ -1,17 +1,17 @@
 // batch.cu -- many placements of one netlist in one sweep.
 //
 // Every placement runs the same timing graph, so the batched schedule maps
-// LANES TO PLACEMENTS: a warp takes one task (a net, or a chunk of a large
-// net's sinks) for 32 placements at once and each lane runs the scalar
-// per-net algorithm for its placement.  All lanes follow the same control
-// flow (the topology is shared), there are no shuffles or segmented scans,
-// and every per-pin access is one coalesced 128-byte row: per-placement state
+// LANES TO (PLACEMENT, CONDITION) PAIRS: a warp takes one task (a net, or a
+// chunk of a large net's sinks) for 8 placements x 4 timing conditions and
+// each lane runs the per-net algorithm for its placement and condition.  All
+// lanes follow the same control flow (the topology is shared), and every
+// per-pin access of a warp is four full 32-byte sectors: per-placement state
 // is stored pin-major, placement-minor, value[(pin * k + component) * Bp + b]
 // with Bp = the batch rounded up to a multiple of 32.  Topology, capacitances
-// and tables are read once per warp for 32 placements.
+// and tables are read once per warp for 8 placements.
 //
 // The sweeps are the dependency-driven persistent kernels of the
-// single-placement schedule with queue index q = task * G + group (G = Bp / 32
+// single-placement schedule with queue index q = task * GT + group (GT = Bp / 8
 // placement groups): task t of group g waits only for its producers in group
 // g, whose queue indices are smaller.  Every placement's arithmetic is the
 // same whatever the batch size or its position in the batch, so a placement's
@@ -46,227 +46,256 @@ __device__ __forceinline__ Wire wire(const DevNet& g, float2 xy, float2 xyd, flo
 }
 
 // ---------------------------------------------------------------------------
+// Lanes: 8 placements x 4 timing conditions per warp (lane = 4 * placement +
+// condition), so each lane evaluates one condition of its placement; the 4
+// lanes of a placement ("quad") exchange values with xor shuffles 1 and 2.
+// Every branch below depends on the task only (warp-uniform), never on data.
+// ---------------------------------------------------------------------------
+struct Lane {
+    int lane, c, el, rf, b;
+};
+
+__device__ __forceinline__ Lane lane_of(int gq) {
+    Lane L;
+    L.lane = threadIdx.x & 31;
+    L.c = L.lane & 3;
+    L.el = L.c >> 1;
+    L.rf = L.c & 1;
+    L.b = gq * kPlacePerWarp + (L.lane >> 2);
+    return L;
+}
+
+// fixed-order sum over the quad: (l0 + l1) + (l2 + l3), the same bits on all 4 lanes
+__device__ __forceinline__ float quad_sum(float v) {
+    v += __shfl_xor_sync(kFull, v, 1);
+    return v + __shfl_xor_sync(kFull, v, 2);
+}
+
+// ---------------------------------------------------------------------------
 // Forward
 // ---------------------------------------------------------------------------
 
-// Static description of a driver cell (the same for every lane).
-struct CellDesc {
-    int t, a0, na, un;
+// What a lane loads before the wait: the driver cell, its arcs' input pins and
+// input transitions for this lane's output transition, the type's slew axis,
+// and the load segment of this placement.
+struct FCell {
+    int t, na, a0, rfi;
     int pin[STA_MAX_ARCS];
+    int jl;
+    float ul;
+    float sidx[6], sinv[6];
 };
 
-__device__ __forceinline__ CellDesc cell_desc(const DevNet& g, int n) {
-    CellDesc c;
-    c.t = g.net_drv[n];
-    c.a0 = g.net_arc_ptr[n];
-    c.na = c.t >= 0 ? g.net_arc_ptr[n + 1] - c.a0 : 0;
-    c.un = c.t >= 0 ? g.lib_unate[c.t] : 0;
+__device__ __forceinline__ FCell fcell(const DevNet& g, int n, int rf, float ld) {
+    FCell f;
+    f.t = g.net_drv[n];
+    f.a0 = g.net_arc_ptr[n];
+    f.na = f.t >= 0 ? g.net_arc_ptr[n + 1] - f.a0 : 0;
+    f.rfi = 0;
+    f.jl = 0;
+    f.ul = 0.f;
 #pragma unroll
-    for (int k = 0; k < STA_MAX_ARCS; ++k) c.pin[k] = k < c.na ? g.arc_pin[c.a0 + k] : 0;
-    return c;
-}
-
-__device__ __forceinline__ void load_seg(const DevNet& g, int t, float ld, int& jl, float& ul, float& inv_l) {
-    const float* li = g.lib_idx + t * kLibStride + 8;
-    jl = axis_seg(li, ld);
-    inv_l = __ldg(g.lib_inv + t * kLibStride + 8 + jl);
-    ul = (ld - __ldg(li + jl)) * inv_l;
-}
-
-__device__ __forceinline__ void slew_seg_g(const DevNet& g, int t, float v, int& is, float& ts, float& inv_s) {
-    const float* si = g.lib_idx + t * kLibStride;
-    is = axis_seg(si, v);
-    inv_s = __ldg(g.lib_inv + t * kLibStride + is);
-    ts = (v - __ldg(si + is)) * inv_s;
-}
-
-// Driver-cell results of one placement for the four conditions (late max /
-// early min over the arcs, worst slew, LSE arrival of Eq. 4 for the late ones).
-struct CellOut {
-    float at[4], sl[4], z[2];
-};
-
-__device__ __forceinline__ CellOut eval_cell(const DevNet& g, const BatchState& bs, const CellDesc& cd, int dp,
-                                             int b, float ld, float gamma, bool lse) {
-    const int Bp = bs.Bp;
-    CellOut o;
-    if (cd.t < 0) {  // asserted driver: constant values set at creation
+    for (int k = 0; k < STA_MAX_ARCS; ++k) f.pin[k] = 0;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            o.at[c] = bs.at[ix(4 * dp + c, Bp, b)];
-            o.sl[c] = bs.slew[ix(4 * dp + c, Bp, b)];
+    for (int j = 0; j < 6; ++j) f.sidx[j] = f.sinv[j] = 0.f;
+    if (f.t < 0) return f;
+    const int un = g.lib_unate[f.t];
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k)
+        if (k < f.na) {
+            f.pin[k] = g.arc_pin[f.a0 + k];
+            f.rfi |= (rf ^ ((un >> k) & 1)) << k;
         }
-        o.z[0] = bs.ats[ix(2 * dp, Bp, b)];
-        o.z[1] = bs.ats[ix(2 * dp + 1, Bp, b)];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        f.sidx[j] = __ldg(g.lib_idx + f.t * kLibStride + j);
+        f.sinv[j] = __ldg(g.lib_inv + f.t * kLibStride + j);
+    }
+    const float* li = g.lib_idx + f.t * kLibStride + 8;
+    f.jl = axis_seg(li, ld);
+    f.ul = (ld - __ldg(li + f.jl)) * __ldg(g.lib_inv + f.t * kLibStride + 8 + f.jl);
+    return f;
+}
+
+// slew segment and fraction from the registers of FCell (same result as axis_seg)
+__device__ __forceinline__ void seg_reg(const float* sidx, const float* sinv, float v, int& is, float& ts) {
+    float base = sidx[0], inv = sinv[0];
+    is = 0;
+#pragma unroll
+    for (int j = 1; j <= 5; ++j)
+        if (sidx[j] <= v) {
+            base = sidx[j];
+            inv = sinv[j];
+            is = j;
+        }
+    ts = (v - base) * inv;
+}
+
+struct FOut {
+    float at, sl, z;  // arrival, slew, LSE arrival (late conditions) of this lane's condition
+};
+
+// Driver-cell evaluation for one condition (late max / early min over the
+// arcs, worst slew, Eq. 4 LSE for the late conditions).  The fanin values of
+// all arcs are loaded together (through L2: other warps of this sweep wrote them).
+__device__ __forceinline__ FOut fcell_eval(const DevNet& g, const BatchState& bs, const FCell& f, int dp,
+                                           const Lane& L, float gamma, bool lse) {
+    const int Bp = bs.Bp, b = L.b, el = L.el, rf = L.rf;
+    FOut o;
+    if (f.t < 0) {  // asserted driver: constant values set at creation
+        o.at = bs.at[ix(4 * dp + L.c, Bp, b)];
+        o.sl = bs.slew[ix(4 * dp + L.c, Bp, b)];
+        o.z = (el && lse) ? bs.ats[ix(2 * dp + rf, Bp, b)] : 0.f;
         return o;
     }
-    int jl;
-    float ul, inv_l;
-    load_seg(g, cd.t, ld, jl, ul, inv_l);
-    o.at[0] = o.at[1] = o.sl[0] = o.sl[1] = kInf;
-    o.at[2] = o.at[3] = o.sl[2] = o.sl[3] = -kInf;
-    float cand[2][STA_MAX_ARCS], m[2] = {-kInf, -kInf};
+    float ain[STA_MAX_ARCS], sin[STA_MAX_ARCS], zin[STA_MAX_ARCS];
 #pragma unroll
     for (int k = 0; k < STA_MAX_ARCS; ++k) {
-        if (k < cd.na) {
-            const int pin = cd.pin[k];
-            float ain[4], sin[4], zin[2];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                ain[q] = __ldcg(bs.at + ix(4 * pin + q, Bp, b));
-                sin[q] = __ldcg(bs.slew + ix(4 * pin + q, Bp, b));
-            }
-            zin[0] = lse ? __ldcg(bs.ats + ix(2 * pin, Bp, b)) : 0.f;
-            zin[1] = lse ? __ldcg(bs.ats + ix(2 * pin + 1, Bp, b)) : 0.f;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int el = c >> 1, rf = c & 1;
-                const int rfi = rf ^ ((cd.un >> k) & 1);
-                // selects, not a runtime index: the arrays stay in registers
-                const float s_in = rfi ? sin[2 * el + 1] : sin[2 * el];
-                const float a_in = rfi ? ain[2 * el + 1] : ain[2 * el];
-                int is;
-                float ts, inv_s;
-                slew_seg_g(g, cd.t, s_in, is, ts, inv_s);
-                float4 dq, sq;
-                cell_corners(g, cd.t, k, rf, is, jl, dq, sq);
-                const float D = lerp_cell(dq, ts, ul);
-                const float S = lerp_cell(sq, ts, ul);
-                const float v = a_in + D;
-                if (el) {
-                    o.at[c] = fmaxf(o.at[c], v);
-                    o.sl[c] = fmaxf(o.sl[c], S);
-                    cand[rf][k] = (rfi ? zin[1] : zin[0]) + D;
-                    m[rf] = fmaxf(m[rf], cand[rf][k]);
-                } else {
-                    o.at[c] = fminf(o.at[c], v);
-                    o.sl[c] = fminf(o.sl[c], S);
-                }
-            }
+        ain[k] = sin[k] = zin[k] = 0.f;
+        if (k < f.na) {
+            const int r = (f.rfi >> k) & 1;
+            const int row = 4 * f.pin[k] + 2 * el + r;
+            ain[k] = __ldcg(bs.at + ix(row, Bp, b));
+            sin[k] = __ldcg(bs.slew + ix(row, Bp, b));
+            if (lse && el) zin[k] = __ldcg(bs.ats + ix(2 * f.pin[k] + r, Bp, b));
         }
     }
-    o.z[0] = o.z[1] = 0.f;
-    if (lse) {
+    float best_at = el ? -kInf : kInf, best_sl = el ? -kInf : kInf, m = -kInf;
+    float cand[STA_MAX_ARCS];
 #pragma unroll
-        for (int rf = 0; rf < 2; ++rf) {
-            float sum = 0.f;
-#pragma unroll
-            for (int k = 0; k < STA_MAX_ARCS; ++k)
-                if (k < cd.na) sum += expf((cand[rf][k] - m[rf]) / gamma);
-            o.z[rf] = m[rf] + gamma * logf(sum);
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        cand[k] = -kInf;
+        if (k < f.na) {
+            int is;
+            float ts;
+            seg_reg(f.sidx, f.sinv, sin[k], is, ts);
+            float4 dq, sq;
+            cell_corners(g, f.t, k, rf, is, f.jl, dq, sq);
+            const float D = lerp_cell(dq, ts, f.ul);
+            const float S = lerp_cell(sq, ts, f.ul);
+            const float v = ain[k] + D;
+            best_at = el ? fmaxf(best_at, v) : fminf(best_at, v);
+            best_sl = el ? fmaxf(best_sl, S) : fminf(best_sl, S);
+            cand[k] = zin[k] + D;
+            m = fmaxf(m, cand[k]);
         }
+    }
+    o.at = best_at;
+    o.sl = best_sl;
+    o.z = 0.f;
+    if (lse && el) {
+        float sum = 0.f;
+#pragma unroll
+        for (int k = 0; k < STA_MAX_ARCS; ++k)
+            if (k < f.na) sum += expf((cand[k] - m) / gamma);
+        o.z = m + gamma * logf(sum);
     }
     return o;
 }
 
-__device__ __forceinline__ void store_driver(const BatchState& bs, int dp, int b, const CellOut& o, bool lse) {
+__device__ __forceinline__ void store_pin(const BatchState& bs, int p, const Lane& L, float at, float sl, float z,
+                                          bool lse) {
     const int Bp = bs.Bp;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        bs.at[ix(4 * dp + c, Bp, b)] = o.at[c];
-        bs.slew[ix(4 * dp + c, Bp, b)] = o.sl[c];
-    }
-    if (lse) {
-        bs.ats[ix(2 * dp, Bp, b)] = o.z[0];
-        bs.ats[ix(2 * dp + 1, Bp, b)] = o.z[1];
-    }
+    bs.at[ix(4 * p + L.c, Bp, L.b)] = at;
+    bs.slew[ix(4 * p + L.c, Bp, L.b)] = sl;
+    if (lse && L.el) bs.ats[ix(2 * p + L.rf, Bp, L.b)] = z;
 }
 
-// wire step to the sinks [s0, s1) of a net with driver values o
-__device__ __forceinline__ void store_sinks(const DevNet& g, const BatchState& bs, int s0, int s1, int b, float2 xyd,
-                                            const CellOut& o, bool lse) {
-    const int Bp = bs.Bp;
-#pragma unroll 2
-    for (int p = s0; p < s1; ++p) {
-        const Wire w = wire(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p));
-        const float i2 = w.I * w.I;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            bs.at[ix(4 * p + c, Bp, b)] = o.at[c] + w.D;
-            bs.slew[ix(4 * p + c, Bp, b)] = sqrtf(fmaf(o.sl[c], o.sl[c], i2));
-        }
-        if (lse) {
-            bs.ats[ix(2 * p, Bp, b)] = o.z[0] + w.D;
-            bs.ats[ix(2 * p + 1, Bp, b)] = o.z[1] + w.D;
-        }
-    }
-}
-
-// net load (Eq. 1): the driver's pin capacitance, then every sink in order
-__device__ __forceinline__ float net_load(const DevNet& g, const BatchState& bs, int dp, int s1, int b, float2 xyd) {
-    float ld = __ldg(g.pin_cap + dp);
+// wire step to the sinks [s0, s1): every lane its condition
+__device__ __forceinline__ void store_sinks(const DevNet& g, const BatchState& bs, int s0, int s1, const Lane& L,
+                                            float2 xyd, const FOut& o, bool lse) {
 #pragma unroll 4
-    for (int p = dp + 1; p < s1; ++p) {
-        const float2 xy = bs.xy[ix(p, bs.Bp, b)];
-        const float dist = fabsf(xy.x - xyd.x) + fabsf(xy.y - xyd.y);
-        ld += fmaf(g.c, dist, __ldg(g.pin_cap + p));
+    for (int p = s0; p < s1; ++p) {
+        const Wire w = wire(g, bs.xy[ix(p, bs.Bp, L.b)], xyd, __ldg(g.pin_cap + p));
+        store_pin(bs, p, L, o.at + w.D, sqrtf(fmaf(o.sl, o.sl, w.I * w.I)), o.z + w.D, lse);
     }
-    return ld;
 }
 
-template <bool lse>
-__device__ void bfwd_nets(const DevNet& g, const BatchState& bs, const DfState& d, int q, int n0, int nn, int b,
-                          float gamma) {
+// net load (Eq. 1): lane c of the quad sums sinks c, c + 4, ..., then the quad
+// sum and the driver's pin capacitance
+__device__ __forceinline__ float net_load(const DevNet& g, const BatchState& bs, int dp, int s1, const Lane& L,
+                                          float2 xyd) {
+    float acc = 0.f;
+#pragma unroll 4
+    for (int p = dp + 1 + L.c; p < s1; p += 4) {
+        const float2 xy = bs.xy[ix(p, bs.Bp, L.b)];
+        const float dist = fabsf(xy.x - xyd.x) + fabsf(xy.y - xyd.y);
+        acc += fmaf(g.c, dist, __ldg(g.pin_cap + p));
+    }
+    return __ldg(g.pin_cap + dp) + quad_sum(acc);
+}
+
+// kWait: dataflow sweep (wait for the producers; the net's load is computed
+// here); otherwise a level-synchronous sweep (producers ran in earlier
+// launches; every load comes from the prologue)
+template <bool lse, bool kWait>
+__device__ void bfwd_nets(const DevNet& g, const BatchState& bs, const DfState& d, int q, int n0, int nn,
+                          const Lane& L, float gamma) {
     const int Bp = bs.Bp;
     // before the wait: the first net's load (static) and its cell description
     const int dp0 = g.net_ptr[n0], e0 = g.net_ptr[n0 + 1];
-    const float2 xyd0 = bs.xy[ix(dp0, Bp, b)];
-    const float ld0 = net_load(g, bs, dp0, e0, b, xyd0);
-    const CellDesc cd0 = cell_desc(g, n0);
-    bs.load[ix(n0, Bp, b)] = ld0;
-
-    wait_ready(d.fcnt, q, d.f_indeg[q / bs.G], d.abort_word);
+    const float2 xyd0 = bs.xy[ix(dp0, Bp, L.b)];
+    const float ld0 = kWait ? net_load(g, bs, dp0, e0, L, xyd0) : bs.load[ix(n0, Bp, L.b)];
+    const FCell f0 = fcell(g, n0, L.rf, ld0);
+    if constexpr (kWait) {
+        if (L.c == 0) bs.load[ix(n0, Bp, L.b)] = ld0;
+        wait_ready(d.fcnt, q, d.f_indeg[q / bs.GT], d.abort_word);
+    }
 
     for (int j = 0; j < nn; ++j) {
         const int n = n0 + j;
         const int dp = j ? g.net_ptr[n] : dp0, e = j ? g.net_ptr[n + 1] : e0;
-        const float2 xyd = j ? bs.xy[ix(dp, Bp, b)] : xyd0;
-        float ld = ld0;
-        CellDesc cd = cd0;
+        const float2 xyd = j ? bs.xy[ix(dp, Bp, L.b)] : xyd0;
+        FCell f = f0;
         if (j) {
-            ld = net_load(g, bs, dp, e, b, xyd);
-            bs.load[ix(n, Bp, b)] = ld;
-            cd = cell_desc(g, n);
+            float ld;
+            if constexpr (kWait) {
+                ld = net_load(g, bs, dp, e, L, xyd);
+                if (L.c == 0) bs.load[ix(n, Bp, L.b)] = ld;
+            } else {
+                ld = bs.load[ix(n, Bp, L.b)];
+            }
+            f = fcell(g, n, L.rf, ld);
         }
-        const CellOut o = eval_cell(g, bs, cd, dp, b, ld, gamma, lse);
-        if (cd.t >= 0) store_driver(bs, dp, b, o, lse);
-        store_sinks(g, bs, dp + 1, e, b, xyd, o, lse);
+        const FOut o = fcell_eval(g, bs, f, dp, L, gamma, lse);
+        if (f.t >= 0) store_pin(bs, dp, L, o.at, o.sl, o.z, lse);
+        store_sinks(g, bs, dp + 1, e, L, xyd, o, lse);
     }
 }
 
 // chunk of a large net: its load comes from the prologue; every chunk
 // evaluates the driver cell, the first one stores it
-template <bool lse>
+template <bool lse, bool kWait>
 __device__ void bfwd_chunk(const DevNet& g, const BatchState& bs, const DfState& d, int q, int n, int p0, int cnt,
-                           int b, float gamma) {
+                           const Lane& L, float gamma) {
     const int Bp = bs.Bp;
     const int dp = g.net_ptr[n];
-    const float2 xyd = bs.xy[ix(dp, Bp, b)];
-    const float ld = bs.load[ix(n, Bp, b)];
-    const CellDesc cd = cell_desc(g, n);
+    const float2 xyd = bs.xy[ix(dp, Bp, L.b)];
+    const FCell f = fcell(g, n, L.rf, bs.load[ix(n, Bp, L.b)]);
 
-    wait_ready(d.fcnt, q, d.f_indeg[q / bs.G], d.abort_word);
+    if constexpr (kWait) wait_ready(d.fcnt, q, d.f_indeg[q / bs.GT], d.abort_word);
 
-    const CellOut o = eval_cell(g, bs, cd, dp, b, ld, gamma, lse);
-    if (cd.t >= 0 && p0 == dp + 1) store_driver(bs, dp, b, o, lse);
-    store_sinks(g, bs, p0, p0 + cnt, b, xyd, o, lse);
+    const FOut o = fcell_eval(g, bs, f, dp, L, gamma, lse);
+    if (f.t >= 0 && p0 == dp + 1) store_pin(bs, dp, L, o.at, o.sl, o.z, lse);
+    store_sinks(g, bs, p0, p0 + cnt, L, xyd, o, lse);
 }
 
 template <bool lse>
 __global__ void __launch_bounds__(kBlock) k_bfwd(DevNet g, BatchState bs, DfState d, float gamma) {
-    const int lane = threadIdx.x & 31;
-    const int Q = d.TF * bs.G;
+    const int GT = bs.GT;
+    const int Q = d.TF * GT;
     int q = grab(d.heads + 0);
     while (q < Q) {
         const int next = grab(d.heads + 0);
-        const int t = q / bs.G, b = (q - t * bs.G) * 32 + lane;
+        const int t = q / GT, gq = q - t * GT;
+        const Lane L = lane_of(gq);
         const int4 task = d.ftask[t];
-        if (task.y > 0) bfwd_nets<lse>(g, bs, d, q, task.x, task.y, b, gamma);
-        else bfwd_chunk<lse>(g, bs, d, q, task.x, task.z, task.w, b, gamma);
-        // consumers of (t, group) are (u, group): counter u * G + group
+        if (task.y > 0) bfwd_nets<lse, true>(g, bs, d, q, task.x, task.y, L, gamma);
+        else bfwd_chunk<lse, true>(g, bs, d, q, task.x, task.z, task.w, L, gamma);
+        // consumers of (t, group) are (u, group): counter u * GT + group
         __syncwarp();
-        const int k1 = d.f_out_ptr[t + 1], gq = q - t * bs.G;
-        for (int k = d.f_out_ptr[t] + lane; k < k1; k += 32) red_release_add(d.fcnt + d.f_out[k] * bs.G + gq, 1);
+        const int k1 = d.f_out_ptr[t + 1];
+        for (int k = d.f_out_ptr[t] + L.lane; k < k1; k += 32) red_release_add(d.fcnt + d.f_out[k] * GT + gq, 1);
         q = next;
     }
 }
@@ -387,168 +416,153 @@ __global__ void k_bep2(DevNet g, BatchState bs, float gamma, int lse, int nparts
 }
 
 // ---------------------------------------------------------------------------
-// Backward (mode 1 required times, 2 adjoint, 3 both)
+// Backward (mode 1 required times, 2 adjoint, 3 both); lanes as in the forward.
+// Every lane carries the required time of its condition; the late lanes (one
+// per output transition) carry the adjoint.
 // ---------------------------------------------------------------------------
 struct BSeed {
     float W, wt, ww;  // WNS_gamma of this placement, w_tns, w_wns
 };
 
-// What one placement's driver cell contributes to the backward sweep, all from
-// forward results: arc delays (required times) and, per late output transition
-// rf, the LSE weights, the delay partials, and the arc of the late slew (first
-// one on ties) with its slew partials.
+// One lane's part of a driver cell's backward step, all from forward results:
+// the arc delays of its condition (required times) and, on late lanes, the LSE
+// weights, the delay partials, and the arc of the late slew (first one on ties)
+// with its slew partials.
 struct BCell {
-    float adel[STA_MAX_ARCS][4];
-    float w[2][STA_MAX_ARCS], dDs[2][STA_MAX_ARCS], dDl[2][STA_MAX_ARCS];
-    int amax[2];
-    float dSs[2], dSl[2];
+    int t, na, rfi;
+    int pin[STA_MAX_ARCS];
+    float adel[STA_MAX_ARCS], w[STA_MAX_ARCS], dDs[STA_MAX_ARCS], dDl[STA_MAX_ARCS];
+    int amax;
+    float dSs, dSl;
 };
 
 template <int mode>
-__device__ __forceinline__ void bcell_pre(const DevNet& g, const BatchState& bs, const CellDesc& cd, int n, int dp,
-                                          int b, float gamma, BCell& bc) {
-    const int Bp = bs.Bp;
-#pragma unroll
-    for (int rf = 0; rf < 2; ++rf) {
-        bc.amax[rf] = -1;
-        bc.dSs[rf] = bc.dSl[rf] = 0.f;
-#pragma unroll
-        for (int k = 0; k < STA_MAX_ARCS; ++k) bc.w[rf][k] = bc.dDs[rf][k] = bc.dDl[rf][k] = 0.f;
-    }
-#pragma unroll
-    for (int k = 0; k < STA_MAX_ARCS; ++k)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) bc.adel[k][c] = 0.f;
-    if (cd.t < 0) return;
-    const float ld = bs.load[ix(n, Bp, b)];
-    int jl;
-    float ul, inv_l;
-    load_seg(g, cd.t, ld, jl, ul, inv_l);
-    const float zd0 = (mode & 2) ? bs.ats[ix(2 * dp, Bp, b)] : 0.f;
-    const float zd1 = (mode & 2) ? bs.ats[ix(2 * dp + 1, Bp, b)] : 0.f;
-    float best[2] = {-kInf, -kInf};
+__device__ __forceinline__ BCell bcell_pre(const DevNet& g, const BatchState& bs, int n, int dp, const Lane& L,
+                                           float gamma) {
+    const int Bp = bs.Bp, b = L.b, el = L.el, rf = L.rf;
+    BCell bc;
+    bc.t = g.net_drv[n];
+    const int a0 = g.net_arc_ptr[n];
+    bc.na = bc.t >= 0 ? g.net_arc_ptr[n + 1] - a0 : 0;
+    bc.rfi = 0;
+    bc.amax = -1;
+    bc.dSs = bc.dSl = 0.f;
 #pragma unroll
     for (int k = 0; k < STA_MAX_ARCS; ++k) {
-        if (k < cd.na) {
-            const int pin = cd.pin[k];
+        bc.pin[k] = 0;
+        bc.adel[k] = bc.w[k] = bc.dDs[k] = bc.dDl[k] = 0.f;
+    }
+    if (bc.t < 0) return bc;
+    const bool need = (mode & 1) || el;  // mode 2 needs the late lanes only
+    const int t = bc.t;
+    const int un = g.lib_unate[t];
+    const float ld = bs.load[ix(n, Bp, b)];
+    const float* li = g.lib_idx + t * kLibStride + 8;
+    const int jl = axis_seg(li, ld);
+    const float inv_l = __ldg(g.lib_inv + t * kLibStride + 8 + jl);
+    const float ul = (ld - __ldg(li + jl)) * inv_l;
+    const float zd = ((mode & 2) && el) ? bs.ats[ix(2 * dp + rf, Bp, b)] : 0.f;
+    float best = -kInf;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int el = c >> 1, rf = c & 1;
-                if (!(mode & 1) && !el) continue;
-                const int rfi = rf ^ ((cd.un >> k) & 1);
-                const float sin = bs.slew[ix(4 * pin + 2 * el + rfi, Bp, b)];
-                int is;
-                float ts, inv_s;
-                slew_seg_g(g, cd.t, sin, is, ts, inv_s);
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        if (k < bc.na) {
+            bc.pin[k] = g.arc_pin[a0 + k];
+            const int r = rf ^ ((un >> k) & 1);
+            bc.rfi |= r << k;
+            if (need) {
+                const float sin = bs.slew[ix(4 * bc.pin[k] + 2 * el + r, Bp, b)];
+                const float* si = g.lib_idx + t * kLibStride;
+                const int is = axis_seg(si, sin);
+                const float inv_s = __ldg(g.lib_inv + t * kLibStride + is);
+                const float ts = (sin - __ldg(si + is)) * inv_s;
                 float4 dq, sq;
-                cell_corners(g, cd.t, k, rf, is, jl, dq, sq);
+                cell_corners(g, t, k, rf, is, jl, dq, sq);
                 float dDs, dDl, dSs, dSl;
                 const float D = lerp_cell_grad(dq, ts, ul, inv_s, inv_l, dDs, dDl);
-                bc.adel[k][c] = D;
+                bc.adel[k] = D;
                 if ((mode & 2) && el) {
                     const float S = lerp_cell_grad(sq, ts, ul, inv_s, inv_l, dSs, dSl);
-                    bc.dDs[rf][k] = dDs;
-                    bc.dDl[rf][k] = dDl;
-                    bc.w[rf][k] = expf((bs.ats[ix(2 * pin + rfi, Bp, b)] + D - (rf ? zd1 : zd0)) / gamma);
-                    if (S > best[rf]) {
-                        best[rf] = S;
-                        bc.amax[rf] = k;
-                        bc.dSs[rf] = dSs;
-                        bc.dSl[rf] = dSl;
+                    bc.dDs[k] = dDs;
+                    bc.dDl[k] = dDl;
+                    bc.w[k] = expf((bs.ats[ix(2 * bc.pin[k] + r, Bp, b)] + D - zd) / gamma);
+                    if (S > best) {
+                        best = S;
+                        bc.amax = k;
+                        bc.dSs = dSs;
+                        bc.dSl = dSl;
                     }
                 }
             }
         }
     }
+    return bc;
 }
 
-// Required times of the cell's inputs and the adjoint through the LSE, the
-// NLDM partials and the late-slew max; returns d loss / d load.
+// Required times of the cell's inputs (R = this lane's condition at the
+// output) and, on late lanes, the adjoint through the LSE, the NLDM partials
+// and the late-slew max; returns the lane's part of d loss / d load.
 template <int mode>
-__device__ __forceinline__ float bcell_apply(const BatchState& bs, const CellDesc& cd, const BCell& bc, int b,
-                                             const float* R, const float* GA, const float* GS) {
-    const int Bp = bs.Bp;
+__device__ __forceinline__ float bcell_apply(const BatchState& bs, const BCell& bc, const Lane& L, float R, float GA,
+                                             float GS) {
+    const int Bp = bs.Bp, b = L.b, el = L.el;
     float gl = 0.f;
 #pragma unroll
     for (int k = 0; k < STA_MAX_ARCS; ++k) {
-        if (k < cd.na) {
-            const int pin = cd.pin[k];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int el = c >> 1, rf = c & 1;
-                const int rfi = rf ^ ((cd.un >> k) & 1);
-                if (mode & 1) bs.rat[ix(4 * pin + 2 * el + rfi, Bp, b)] = R[c] - bc.adel[k][c];
-                if ((mode & 2) && el) {
-                    const float gD = GA[rf] * bc.w[rf][k];
-                    bs.g_ats[ix(2 * pin + rfi, Bp, b)] = gD;
-                    bs.g_slew[ix(2 * pin + rfi, Bp, b)] = fmaf(gD, bc.dDs[rf][k], k == bc.amax[rf] ? GS[rf] * bc.dSs[rf] : 0.f);
-                    gl = fmaf(gD, bc.dDl[rf][k], gl);
-                }
+        if (k < bc.na) {
+            const int r = (bc.rfi >> k) & 1;
+            if (mode & 1) bs.rat[ix(4 * bc.pin[k] + 2 * el + r, Bp, b)] = R - bc.adel[k];
+            if ((mode & 2) && el) {
+                const float gD = GA * bc.w[k];
+                bs.g_ats[ix(2 * bc.pin[k] + r, Bp, b)] = gD;
+                bs.g_slew[ix(2 * bc.pin[k] + r, Bp, b)] = fmaf(gD, bc.dDs[k], k == bc.amax ? GS * bc.dSs : 0.f);
+                gl = fmaf(gD, bc.dDl[k], gl);
             }
         }
     }
-    if (mode & 2) {
-#pragma unroll
-        for (int rf = 0; rf < 2; ++rf)
-            if (bc.amax[rf] >= 0) gl = fmaf(GS[rf], bc.dSl[rf], gl);
-    }
+    if ((mode & 2) && el && bc.amax >= 0) gl = fmaf(GS, bc.dSl, gl);
     return gl;
 }
 
-// One sink's terms of the backward reductions.  Cell-input sinks read their
-// required times / adjoints (written by their cell's task; through L2);
-// endpoints and dangling sinks are constant: the constraint (or +-inf) and the
-// adjoint seed d loss / d LSE-AT = -(w_tns dTNS_g/ds + w_wns dWNS_g/ds).
+// One sink's terms for this lane: r = RAT_s - Delay_s of its condition; on late
+// lanes the sink's LSE-arrival adjoint ga, the slew term gs = g_slew_s *
+// slew_d / slew_s, and this transition's part of the wire adjoint.
+// Cell-input sinks read what their cell's task wrote (through L2); endpoints
+// and dangling sinks are constant: the constraint (or +-inf) and the seed
+// d loss / d LSE-AT = -(w_tns dTNS_g/ds + w_wns dWNS_g/ds).
 struct BSink {
-    float r[4];    // RAT_s - Delay_s
-    float ga[2];   // g_ats of the sink
-    float gs[2];   // g_slew_s * slew_d / slew_s
-    float gwire;   // d loss / d Delay_s + d loss / d Impulse_s
+    float r, ga, gs, gw;
     Wire w;
 };
 
 template <int mode>
-__device__ __forceinline__ BSink bsink(const DevNet& g, const BatchState& bs, const DfState& d, int p, int b,
-                                       float2 xyd, const float* sld, float gamma, const BSeed& sd) {
-    const int Bp = bs.Bp;
+__device__ __forceinline__ BSink bsink(const DevNet& g, const BatchState& bs, const DfState& d, int p, const Lane& L,
+                                       float2 xyd, float sld, float gamma, const BSeed& sd) {
+    const int Bp = bs.Bp, b = L.b;
     BSink s;
     s.w = wire(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p));
-    const bool dyn = d.pin_cons[p] >= 0;
-    if (mode & 1) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) s.r[c] = __ldcg(bs.rat + ix(4 * p + c, Bp, b)) - s.w.D;
-    }
-    s.ga[0] = s.ga[1] = s.gs[0] = s.gs[1] = s.gwire = 0.f;
-    if (mode & 2) {
-        float ga0, ga1, gs0 = 0.f, gs1 = 0.f;
-        if (dyn) {
-            ga0 = __ldcg(bs.g_ats + ix(2 * p, Bp, b));
-            ga1 = __ldcg(bs.g_ats + ix(2 * p + 1, Bp, b));
-            gs0 = __ldcg(bs.g_slew + ix(2 * p, Bp, b));
-            gs1 = __ldcg(bs.g_slew + ix(2 * p + 1, Bp, b));
+    s.r = (mode & 1) ? __ldcg(bs.rat + ix(4 * p + L.c, Bp, b)) - s.w.D : 0.f;
+    s.ga = s.gs = s.gw = 0.f;
+    if ((mode & 2) && L.el) {
+        float ga = 0.f, gs = 0.f;
+        if (d.pin_cons[p] >= 0) {
+            ga = __ldcg(bs.g_ats + ix(2 * p + L.rf, Bp, b));
+            gs = __ldcg(bs.g_slew + ix(2 * p + L.rf, Bp, b));
         } else {
-            ga0 = ga1 = 0.f;
             const float rr = bs.rat[ix(4 * p + 2, Bp, b)], rfl = bs.rat[ix(4 * p + 3, Bp, b)];
             if (isfinite(rr)) {
                 const float sr = rr - bs.ats[ix(2 * p, Bp, b)], sf = rfl - bs.ats[ix(2 * p + 1, Bp, b)];
                 const float te = softmin3(sr, sf, gamma);
-                float gr = sd.wt * expf(-(sr - te) / gamma), gf = sd.wt * expf(-(sf - te) / gamma);
-                if (isfinite(sd.W)) {
-                    gr += sd.ww * expf(-(sr - sd.W) / gamma);
-                    gf += sd.ww * expf(-(sf - sd.W) / gamma);
-                }
-                ga0 = -gr;
-                ga1 = -gf;
+                const float sv = L.rf ? sf : sr;
+                float gv = sd.wt * expf(-(sv - te) / gamma);
+                if (isfinite(sd.W)) gv += sd.ww * expf(-(sv - sd.W) / gamma);
+                ga = -gv;
             }
         }
-        const float sl0 = bs.slew[ix(4 * p + 2, Bp, b)], sl1 = bs.slew[ix(4 * p + 3, Bp, b)];
-        const float q0 = sl0 > 0.f ? gs0 / sl0 : 0.f;
-        const float q1 = sl1 > 0.f ? gs1 / sl1 : 0.f;
-        s.ga[0] = ga0;
-        s.ga[1] = ga1;
-        s.gs[0] = q0 * sld[0];
-        s.gs[1] = q1 * sld[1];
-        s.gwire = ga0 + ga1 + (q0 + q1) * s.w.I;
+        const float sl = bs.slew[ix(4 * p + 2 + L.rf, Bp, b)];
+        const float qv = sl > 0.f ? gs / sl : 0.f;
+        s.ga = ga;
+        s.gs = qv * sld;
+        s.gw = fmaf(qv, s.w.I, ga);
     }
     return s;
 }
@@ -561,196 +575,271 @@ __device__ __forceinline__ float2 bsink_grad(const DevNet& g, float2 xy, float2 
     return make_float2(gd * ((dx > 0.f) - (dx < 0.f)), gd * ((dy > 0.f) - (dy < 0.f)));
 }
 
-template <int mode>
-__device__ void bbwd_nets(const DevNet& g, const BatchState& bs, const DfState& d, int32_t* cnt, int q, int n0, int nn,
-                          int b, float gamma, const BSeed& sd) {
-    const int Bp = bs.Bp;
-    const int dp0 = g.net_ptr[n0];
-    const CellDesc cd0 = cell_desc(g, n0);
-    BCell bc0;
-    bcell_pre<mode>(g, bs, cd0, n0, dp0, b, gamma, bc0);
+__device__ __forceinline__ float late_slew_of_driver(const BatchState& bs, int dp, const Lane& L) {
+    return L.el ? bs.slew[ix(4 * dp + 2 + L.rf, bs.Bp, L.b)] : 0.f;
+}
 
-    wait_ready(cnt, q, d.b_indeg[q / bs.G], d.abort_word);
+template <int mode, bool kWait>
+__device__ void bbwd_nets(const DevNet& g, const BatchState& bs, const DfState& d, int32_t* cnt, int q, int n0, int nn,
+                          const Lane& L, float gamma, const BSeed& sd) {
+    const int Bp = bs.Bp, b = L.b;
+    const int dp0 = g.net_ptr[n0];
+    BCell bc = bcell_pre<mode>(g, bs, n0, dp0, L, gamma);
+    const float2 xyd0 = bs.xy[ix(dp0, Bp, b)];
+    const float sld0 = (mode & 2) ? late_slew_of_driver(bs, dp0, L) : 0.f;
+
+    if constexpr (kWait) wait_ready(cnt, q, d.b_indeg[q / bs.GT], d.abort_word);
 
     for (int j = 0; j < nn; ++j) {
         const int n = n0 + j;
         const int dp = j ? g.net_ptr[n] : dp0, e = g.net_ptr[n + 1];
-        CellDesc cd = cd0;
+        float2 xyd = xyd0;
+        float sld = sld0;
         if (j) {
-            cd = cell_desc(g, n);
-            bcell_pre<mode>(g, bs, cd, n, dp, b, gamma, bc0);
+            bc = bcell_pre<mode>(g, bs, n, dp, L, gamma);
+            xyd = bs.xy[ix(dp, Bp, b)];
+            sld = (mode & 2) ? late_slew_of_driver(bs, dp, L) : 0.f;
         }
-        const float2 xyd = bs.xy[ix(dp, Bp, b)];
-        float sld[2] = {0.f, 0.f};
-        if (mode & 2) {
-            sld[0] = bs.slew[ix(4 * dp + 2, Bp, b)];
-            sld[1] = bs.slew[ix(4 * dp + 3, Bp, b)];
-        }
-        float R[4] = {-kInf, -kInf, kInf, kInf}, GA[2] = {0.f, 0.f}, GS[2] = {0.f, 0.f};
+        float R = L.el ? kInf : -kInf, GA = 0.f, GS = 0.f;
+#pragma unroll 2
         for (int p = dp + 1; p < e; ++p) {
-            const BSink s = bsink<mode>(g, bs, d, p, b, xyd, sld, gamma, sd);
-            if (mode & 1) {
-                R[0] = fmaxf(R[0], s.r[0]);
-                R[1] = fmaxf(R[1], s.r[1]);
-                R[2] = fminf(R[2], s.r[2]);
-                R[3] = fminf(R[3], s.r[3]);
-            }
-            if (mode & 2) {
-                GA[0] += s.ga[0];
-                GA[1] += s.ga[1];
-                GS[0] += s.gs[0];
-                GS[1] += s.gs[1];
-                bs.grad[ix(p, Bp, b)].x = s.gwire;  // kept until d loss / d load is known
+            const BSink s = bsink<mode>(g, bs, d, p, L, xyd, sld, gamma, sd);
+            R = L.el ? fminf(R, s.r) : fmaxf(R, s.r);
+            GA += s.ga;
+            GS += s.gs;
+            if (mode & 2) {  // the sink's wire adjoint, both transitions; kept until d loss / d load is known
+                const float gw = s.gw + __shfl_xor_sync(kFull, s.gw, 1);
+                if (L.c == 2) bs.grad[ix(p, Bp, b)].x = gw;
             }
         }
-        if (mode & 1) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) bs.rat[ix(4 * dp + c, Bp, b)] = R[c];
-        }
-        const float gload = bcell_apply<mode>(bs, cd, bc0, b, R, GA, GS);
+        if (mode & 1) bs.rat[ix(4 * dp + L.c, Bp, b)] = R;
+        const float gl = bcell_apply<mode>(bs, bc, L, R, GA, GS);
         if (mode & 2) {
+            const float gload = quad_sum(gl);  // early lanes contribute 0
+            __syncwarp();                      // the wire adjoints stored by lane 2 of each quad
             float sx = 0.f, sy = 0.f;
-            for (int p = dp + 1; p < e; ++p) {
+            for (int p = dp + 1 + L.c; p < e; p += 4) {
                 const float gw = bs.grad[ix(p, Bp, b)].x;
                 const float2 gxy = bsink_grad(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p), gw, gload);
                 bs.grad[ix(p, Bp, b)] = gxy;
                 sx += gxy.x;
                 sy += gxy.y;
             }
-            bs.grad[ix(dp, Bp, b)] = make_float2(-sx, -sy);
+            sx = quad_sum(sx);
+            sy = quad_sum(sy);
+            if (L.c == 0) bs.grad[ix(dp, Bp, b)] = make_float2(-sx, -sy);
         }
     }
 }
 
-// Partial chunk of a large net: the 12 partial terms of the single-placement
-// schedule over the chunk's sinks, per placement.
-template <int mode>
+// Partial chunk of a large net.  Slots of a partial record (per placement):
+//   0-3 max/max/min/min of RAT_s - Delay_s, 4-5 sums of g_ats, 6-7 sums of
+//   g_slew * slew_d / slew_s, 8-9 sums of sign(x_s - x_d), sign(y_s - y_d),
+//   10-11 sums of sign * g_wire * dDelay/dd (the driver's gradient is
+//   -(gload * c * sums 8-9 + sums 10-11)).
+template <int mode, bool kWait>
 __device__ void bbwd_part(const DevNet& g, const BatchState& bs, const DfState& d, int32_t* cnt, int q, int n, int p0,
-                          int np, int slot, int b, float gamma, const BSeed& sd) {
-    const int Bp = bs.Bp;
+                          int np, int slot, const Lane& L, float gamma, const BSeed& sd) {
+    const int Bp = bs.Bp, b = L.b;
     const int dp = g.net_ptr[n];
     const float2 xyd = bs.xy[ix(dp, Bp, b)];
-    float sld[2] = {0.f, 0.f};
-    if (mode & 2) {
-        sld[0] = bs.slew[ix(4 * dp + 2, Bp, b)];
-        sld[1] = bs.slew[ix(4 * dp + 3, Bp, b)];
-    }
+    const float sld = (mode & 2) ? late_slew_of_driver(bs, dp, L) : 0.f;
 
-    wait_ready(cnt, q, d.b_indeg[q / bs.G], d.abort_word);
+    if constexpr (kWait) wait_ready(cnt, q, d.b_indeg[q / bs.GT], d.abort_word);
 
-    float v[kPartFloats];
-    v[0] = v[1] = -kInf;
-    v[2] = v[3] = kInf;
-#pragma unroll
-    for (int k = 4; k < kPartFloats; ++k) v[k] = 0.f;
+    float R = L.el ? kInf : -kInf, GA = 0.f, GS = 0.f, sx = 0.f, sy = 0.f, hx = 0.f, hy = 0.f;
+#pragma unroll 2
     for (int p = p0; p < p0 + np; ++p) {
-        const BSink s = bsink<mode>(g, bs, d, p, b, xyd, sld, gamma, sd);
-        if (mode & 1) {
-            v[0] = fmaxf(v[0], s.r[0]);
-            v[1] = fmaxf(v[1], s.r[1]);
-            v[2] = fminf(v[2], s.r[2]);
-            v[3] = fminf(v[3], s.r[3]);
-        }
+        const BSink s = bsink<mode>(g, bs, d, p, L, xyd, sld, gamma, sd);
+        R = L.el ? fminf(R, s.r) : fmaxf(R, s.r);
+        GA += s.ga;
+        GS += s.gs;
         if (mode & 2) {
-            v[4] += s.ga[0];
-            v[5] += s.ga[1];
-            v[6] += s.gs[0];
-            v[7] += s.gs[1];
+            const float gw = s.gw + __shfl_xor_sync(kFull, s.gw, 1);
             const float2 xy = bs.xy[ix(p, Bp, b)];
             const float dx = xy.x - xyd.x, dy = xy.y - xyd.y;
-            const float sx = (dx > 0.f) - (dx < 0.f), sy = (dy > 0.f) - (dy < 0.f);
-            const float h = s.gwire * (kKrc * g.r * fmaf(g.c, s.w.dist, __ldg(g.pin_cap + p)));
-            v[8] += sx;
-            v[9] += sy;
-            v[10] += sx * h;
-            v[11] += sy * h;
+            const float ex = (dx > 0.f) - (dx < 0.f), ey = (dy > 0.f) - (dy < 0.f);
+            const float h = gw * (kKrc * g.r * fmaf(g.c, s.w.dist, __ldg(g.pin_cap + p)));
+            sx += ex;
+            sy += ey;
+            hx += ex * h;
+            hy += ey * h;
         }
     }
     float* part = (mode & 2) ? bs.part : bs.rpart;
-#pragma unroll
-    for (int k = 0; k < kPartFloats; ++k) part[ix(slot * kPartFloats + k, Bp, b)] = v[k];
+    const int base = slot * kPartFloats;
+    part[ix(base + L.c, Bp, b)] = R;
+    if ((mode & 2) && L.el) {
+        part[ix(base + 4 + L.rf, Bp, b)] = GA;
+        part[ix(base + 6 + L.rf, Bp, b)] = GS;
+    }
+    if ((mode & 2) && L.c == 2) {  // lane 2 holds the wire adjoints of both transitions
+        part[ix(base + 8, Bp, b)] = sx;
+        part[ix(base + 9, Bp, b)] = sy;
+        part[ix(base + 10, Bp, b)] = hx;
+        part[ix(base + 11, Bp, b)] = hy;
+    }
 }
 
-template <int mode>
+template <int mode, bool kWait>
 __device__ void bbwd_driver(const DevNet& g, const BatchState& bs, const DfState& d, int32_t* cnt, int q, int n,
-                            int slot0, int nch, int b, float gamma) {
-    const int Bp = bs.Bp;
+                            int slot0, int nch, const Lane& L, float gamma) {
+    const int Bp = bs.Bp, b = L.b;
     const int dp = g.net_ptr[n];
-    const CellDesc cd = cell_desc(g, n);
-    BCell bc;
-    bcell_pre<mode>(g, bs, cd, n, dp, b, gamma, bc);
+    const BCell bc = bcell_pre<mode>(g, bs, n, dp, L, gamma);
 
-    wait_ready(cnt, q, d.b_indeg[q / bs.G], d.abort_word);
+    if constexpr (kWait) wait_ready(cnt, q, d.b_indeg[q / bs.GT], d.abort_word);
 
-    float v[kPartFloats];
-    v[0] = v[1] = -kInf;
-    v[2] = v[3] = kInf;
-#pragma unroll
-    for (int k = 4; k < kPartFloats; ++k) v[k] = 0.f;
     const float* part = (mode & 2) ? bs.part : bs.rpart;
+    float R = L.el ? kInf : -kInf, GA = 0.f, GS = 0.f, sx = 0.f, sy = 0.f, hx = 0.f, hy = 0.f;
     for (int k = 0; k < nch; ++k) {
         const int base = (slot0 + k) * kPartFloats;
-        v[0] = fmaxf(v[0], __ldcg(part + ix(base + 0, Bp, b)));
-        v[1] = fmaxf(v[1], __ldcg(part + ix(base + 1, Bp, b)));
-        v[2] = fminf(v[2], __ldcg(part + ix(base + 2, Bp, b)));
-        v[3] = fminf(v[3], __ldcg(part + ix(base + 3, Bp, b)));
-#pragma unroll
-        for (int j = 4; j < kPartFloats; ++j) v[j] += __ldcg(part + ix(base + j, Bp, b));
+        const float r = __ldcg(part + ix(base + L.c, Bp, b));
+        R = L.el ? fminf(R, r) : fmaxf(R, r);
+        if ((mode & 2) && L.el) {
+            GA += __ldcg(part + ix(base + 4 + L.rf, Bp, b));
+            GS += __ldcg(part + ix(base + 6 + L.rf, Bp, b));
+        }
+        if ((mode & 2) && L.c == 2) {
+            sx += __ldcg(part + ix(base + 8, Bp, b));
+            sy += __ldcg(part + ix(base + 9, Bp, b));
+            hx += __ldcg(part + ix(base + 10, Bp, b));
+            hy += __ldcg(part + ix(base + 11, Bp, b));
+        }
     }
-    if (mode & 1) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) bs.rat[ix(4 * dp + c, Bp, b)] = v[c];
-    }
-    const float R[4] = {v[0], v[1], v[2], v[3]}, GA[2] = {v[4], v[5]}, GS[2] = {v[6], v[7]};
-    const float gload = bcell_apply<mode>(bs, cd, bc, b, R, GA, GS);
+    if (mode & 1) bs.rat[ix(4 * dp + L.c, Bp, b)] = R;
+    const float gl = bcell_apply<mode>(bs, bc, L, R, GA, GS);
     if (mode & 2) {
-        bs.net_gload[ix(n, Bp, b)] = gload;
-        bs.grad[ix(dp, Bp, b)] = make_float2(-fmaf(gload * g.c, v[8], v[10]), -fmaf(gload * g.c, v[9], v[11]));
+        const float gload = quad_sum(gl);
+        if (L.c == 2) {
+            bs.net_gload[ix(n, Bp, b)] = gload;
+            bs.grad[ix(dp, Bp, b)] = make_float2(-fmaf(gload * g.c, sx, hx), -fmaf(gload * g.c, sy, hy));
+        }
     }
 }
 
+// Gradient chunk of a large net: d loss / d (x, y) of its sinks once the
+// driver task has published d loss / d load.  No task waits for these.
+template <bool kWait>
 __device__ void bbwd_grad(const DevNet& g, const BatchState& bs, const DfState& d, int32_t* cnt, int q, int n, int p0,
-                          int np, int b, float gamma, const BSeed& sd) {
-    const int Bp = bs.Bp;
+                          int np, const Lane& L, float gamma, const BSeed& sd) {
+    const int Bp = bs.Bp, b = L.b;
     const int dp = g.net_ptr[n];
     const float2 xyd = bs.xy[ix(dp, Bp, b)];
-    const float sld[2] = {bs.slew[ix(4 * dp + 2, Bp, b)], bs.slew[ix(4 * dp + 3, Bp, b)]};
-    wait_ready(cnt, q, d.b_indeg[q / bs.G], d.abort_word);
+    const float sld = late_slew_of_driver(bs, dp, L);
+    if constexpr (kWait) wait_ready(cnt, q, d.b_indeg[q / bs.GT], d.abort_word);
     const float gload = __ldcg(bs.net_gload + ix(n, Bp, b));
+#pragma unroll 2
     for (int p = p0; p < p0 + np; ++p) {
-        const BSink s = bsink<2>(g, bs, d, p, b, xyd, sld, gamma, sd);
-        bs.grad[ix(p, Bp, b)] = bsink_grad(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p), s.gwire, gload);
+        const BSink s = bsink<2>(g, bs, d, p, L, xyd, sld, gamma, sd);
+        const float gw = s.gw + __shfl_xor_sync(kFull, s.gw, 1);
+        if (L.c == 2)
+            bs.grad[ix(p, Bp, b)] = bsink_grad(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p), gw, gload);
     }
+}
+
+template <int mode, bool kWait>
+__device__ __forceinline__ void bbwd_task(const DevNet& g, const BatchState& bs, const DfState& d, int32_t* cnt, int q,
+                                          int t, const Lane& L, float gamma) {
+    BSeed sd;
+    sd.W = (float)bs.summary[(size_t)L.b * STA_SUM_COUNT + STA_SUM_WNS_GAMMA];
+    sd.wt = bs.params[2 * L.b];
+    sd.ww = bs.params[2 * L.b + 1];
+    const int4 task = d.btask[t];
+    if (task.y > 0) {
+        bbwd_nets<mode, kWait>(g, bs, d, cnt, q, task.x, task.y, L, gamma, sd);
+    } else if (task.y == -1) {
+        bbwd_part<mode, kWait>(g, bs, d, cnt, q, task.x, task.z, task.w, d.baux[t], L, gamma, sd);
+    } else if (task.y == -2) {
+        bbwd_driver<mode, kWait>(g, bs, d, cnt, q, task.x, task.z, task.w, L, gamma);
+    } else if (mode & 2) {
+        bbwd_grad<kWait>(g, bs, d, cnt, q, task.x, task.z, task.w, L, gamma, sd);
+    }  // gradient chunks have no work in the required-time sweep
 }
 
 template <int mode>
 __global__ void __launch_bounds__(kBlock) k_bbwd(DevNet g, BatchState bs, DfState d, float gamma) {
-    const int lane = threadIdx.x & 31;
     int32_t* cnt = (mode & 2) ? d.acnt : d.rcnt;
     int32_t* head = d.heads + ((mode & 2) ? 2 : 1);
-    const int Q = d.TB * bs.G;
+    const int GT = bs.GT;
+    const int Q = d.TB * GT;
     int q = grab(head);
     while (q < Q) {
         const int next = grab(head);
-        const int t = q / bs.G, gq = q - t * bs.G, b = gq * 32 + lane;
-        BSeed sd;
-        sd.W = (float)bs.summary[(size_t)b * STA_SUM_COUNT + STA_SUM_WNS_GAMMA];
-        sd.wt = bs.params[2 * b];
-        sd.ww = bs.params[2 * b + 1];
-        const int4 task = d.btask[t];
-        if (task.y > 0) {
-            bbwd_nets<mode>(g, bs, d, cnt, q, task.x, task.y, b, gamma, sd);
-        } else if (task.y == -1) {
-            bbwd_part<mode>(g, bs, d, cnt, q, task.x, task.z, task.w, d.baux[t], b, gamma, sd);
-        } else if (task.y == -2) {
-            bbwd_driver<mode>(g, bs, d, cnt, q, task.x, task.z, task.w, b, gamma);
-        } else if (mode & 2) {
-            bbwd_grad(g, bs, d, cnt, q, task.x, task.z, task.w, b, gamma, sd);
-        }  // gradient chunks have no work in the required-time sweep
+        const int t = q / GT, gq = q - t * GT;
+        const Lane L = lane_of(gq);
+        bbwd_task<mode, true>(g, bs, d, cnt, q, t, L, gamma);
         __syncwarp();
         const int k1 = d.b_out_ptr[t + 1];
-        for (int k = d.b_out_ptr[t] + lane; k < k1; k += 32) red_release_add(cnt + d.b_out[k] * bs.G + gq, 1);
+        for (int k = d.b_out_ptr[t] + L.lane; k < k1; k += 32) red_release_add(cnt + d.b_out[k] * GT + gq, 1);
         q = next;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Level-synchronous batched sweeps: one launch per level (per phase in the
+// backward), replayed from a CUDA graph.  A launch runs every (task, group) of
+// its task ranges, a warp each; kernel boundaries order the levels, so there
+// are no counters, waits or release fences.
+// ---------------------------------------------------------------------------
+struct Ranges {
+    int a0, a1, b0, b1, c0, c1;  // up to three task ranges, run as one
+};
+
+__device__ __forceinline__ int range_task(const Ranges& r, int i) {
+    const int na = r.a1 - r.a0, nb = r.b1 - r.b0;
+    return i < na ? r.a0 + i : (i < na + nb ? r.b0 + i - na : r.c0 + i - na - nb);
+}
+
+template <bool lse>
+__global__ void __launch_bounds__(kBlock) k_bfwd_lvl(DevNet g, BatchState bs, DfState d, int t0, int t1,
+                                                      float gamma) {
+    const int GT = bs.GT;
+    const int nw = (t1 - t0) * GT;
+    for (int i = (blockIdx.x * kBlock + threadIdx.x) >> 5; i < nw; i += gridDim.x * kWarpsPerBlock) {
+        const int t = t0 + i / GT, gq = i - (i / GT) * GT;
+        const Lane L = lane_of(gq);
+        const int4 task = d.ftask[t];
+        if (task.y > 0) bfwd_nets<lse, false>(g, bs, d, 0, task.x, task.y, L, gamma);
+        else bfwd_chunk<lse, false>(g, bs, d, 0, task.x, task.z, task.w, L, gamma);
+    }
+}
+
+template <int mode>
+__global__ void __launch_bounds__(kBlock) k_bbwd_lvl(DevNet g, BatchState bs, DfState d, Ranges r, float gamma) {
+    const int GT = bs.GT;
+    const int nw = ((r.a1 - r.a0) + (r.b1 - r.b0) + (r.c1 - r.c0)) * GT;
+    for (int i = (blockIdx.x * kBlock + threadIdx.x) >> 5; i < nw; i += gridDim.x * kWarpsPerBlock) {
+        const int k = i / GT, gq = i - k * GT;
+        bbwd_task<mode, false>(g, bs, d, nullptr, 0, range_task(r, k), lane_of(gq), gamma);
+    }
+}
+
+// Loads (Eq. 1) of every net of at most `big` pins, before a level-synchronous
+// forward sweep: a warp per (net, 32 placements), lane = placement.  Sinks are
+// summed in four interleaved partial sums combined as (s0 + s1) + (s2 + s3),
+// the order of the quad sums of the dataflow sweep, so both sweeps give the
+// same loads.
+__global__ void __launch_bounds__(kBlock) k_bload_small(DevNet g, BatchState bs, int big) {
+    const int lane = threadIdx.x & 31;
+    const int nw = g.N * bs.G;
+    for (int i = (blockIdx.x * kBlock + threadIdx.x) >> 5; i < nw; i += gridDim.x * kWarpsPerBlock) {
+        const int n = i / bs.G, b = (i - n * bs.G) * 32 + lane;
+        const int dp = g.net_ptr[n], e = g.net_ptr[n + 1];
+        if (e - dp > big) continue;  // a large net: the block kernel
+        const float2 xyd = bs.xy[ix(dp, bs.Bp, b)];
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int p = dp + 1; p < e; ++p) {
+            const float2 xy = bs.xy[ix(p, bs.Bp, b)];
+            const float dist = fabsf(xy.x - xyd.x) + fabsf(xy.y - xyd.y);
+            const int k = (p - dp - 1) & 3;
+            const float v = fmaf(g.c, dist, __ldg(g.pin_cap + p));
+            acc[0] += k == 0 ? v : 0.f;
+            acc[1] += k == 1 ? v : 0.f;
+            acc[2] += k == 2 ? v : 0.f;
+            acc[3] += k == 3 ? v : 0.f;
+        }
+        bs.load[ix(n, bs.Bp, b)] = __ldg(g.pin_cap + dp) + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
     }
 }
 
@@ -906,6 +995,32 @@ void launch_batch_fwd(const DevNet& g, const BatchState& bs, const DfState& d, i
     if (d.TF == 0) return;
     if (lse) launch_coop(k_bfwd<true>, grid, kBlock, st, g, bs, d, gamma);
     else launch_coop(k_bfwd<false>, grid, kBlock, st, g, bs, d, gamma);
+}
+
+void launch_batch_load_small(const DevNet& g, const BatchState& bs, int big, cudaStream_t st) {
+    const long long nw = (long long)g.N * bs.G;
+    if (nw == 0) return;
+    k_bload_small<<<bgrid(nw * 32), kBlock, 0, st>>>(g, bs, big);
+}
+
+void launch_batch_fwd_level(const DevNet& g, const BatchState& bs, const DfState& d, int t0, int t1, float gamma,
+                            int lse, cudaStream_t st) {
+    const long long nw = (long long)(t1 - t0) * bs.GT;
+    if (nw <= 0) return;
+    const int grid = (int)((nw + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    if (lse) k_bfwd_lvl<true><<<grid, kBlock, 0, st>>>(g, bs, d, t0, t1, gamma);
+    else k_bfwd_lvl<false><<<grid, kBlock, 0, st>>>(g, bs, d, t0, t1, gamma);
+}
+
+void launch_batch_bwd_level(const DevNet& g, const BatchState& bs, const DfState& d, const int* r6, float gamma,
+                            int mode, cudaStream_t st) {
+    Ranges r{r6[0], r6[1], r6[2], r6[3], r6[4], r6[5]};
+    const long long nw = (long long)((r.a1 - r.a0) + (r.b1 - r.b0) + (r.c1 - r.c0)) * bs.GT;
+    if (nw <= 0) return;
+    const int grid = (int)((nw + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    if (mode == 1) k_bbwd_lvl<1><<<grid, kBlock, 0, st>>>(g, bs, d, r, gamma);
+    else if (mode == 2) k_bbwd_lvl<2><<<grid, kBlock, 0, st>>>(g, bs, d, r, gamma);
+    else k_bbwd_lvl<3><<<grid, kBlock, 0, st>>>(g, bs, d, r, gamma);
 }
 
 void launch_batch_endpoints(const DevNet& g, const BatchState& bs, float gamma, int lse, cudaStream_t st) {

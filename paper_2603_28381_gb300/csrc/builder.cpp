@@ -291,7 +291,9 @@ StaStatus build_tasks(Layout& o, const TaskShape& sh, std::string& err) {
         }
     }
     o.ftask.clear();
+    o.lvl_ftask.assign(o.L + 1, 0);
     for (int32_t l = 0; l < o.L; ++l) {
+        o.lvl_ftask[l] = (int32_t)(o.ftask.size() / 4);
         for (size_t k = 0; k < lvl_pack[l].size(); k += 2) {
             const int32_t n0 = lvl_pack[l][k], nn = lvl_pack[l][k + 1];
             const int32_t t = (int32_t)(o.ftask.size() / 4);
@@ -311,6 +313,7 @@ StaStatus build_tasks(Layout& o, const TaskShape& sh, std::string& err) {
     }
     o.big_nets = bigs;
     o.TF = (int32_t)(o.ftask.size() / 4);
+    o.lvl_ftask[o.L] = o.TF;
     o.arc_prod.resize(A);
     for (int32_t a = 0; a < A; ++a) o.arc_prod[a] = pin_fprod[o.arc_pin[a]];
 
@@ -319,8 +322,11 @@ StaStatus build_tasks(Layout& o, const TaskShape& sh, std::string& err) {
     o.btask.clear();
     o.baux.clear();
     o.npart = 0;
+    o.lvl_bsec.assign((size_t)o.L * 5, 0);
     for (int32_t l = o.L - 1; l >= 0; --l) {
         const size_t nb = lvl_big[l].size();
+        int32_t* sec = &o.lvl_bsec[(size_t)l * 5];
+        sec[0] = (int32_t)o.baux.size();
         std::vector<int32_t> first_ptask(nb), first_slot(nb), nchunks(nb), dtask(nb);
         for (size_t k = 0; k < nb; ++k) {
             const int32_t n = lvl_big[l][k];
@@ -333,6 +339,7 @@ StaStatus build_tasks(Layout& o, const TaskShape& sh, std::string& err) {
             }
             nchunks[k] = o.npart - first_slot[k];
         }
+        sec[1] = (int32_t)o.baux.size();
         for (size_t k = 0; k < nb; ++k) {
             const int32_t n = lvl_big[l][k];
             dtask[k] = (int32_t)o.baux.size();
@@ -340,6 +347,7 @@ StaStatus build_tasks(Layout& o, const TaskShape& sh, std::string& err) {
             o.btask.insert(o.btask.end(), {n, -2, first_slot[k], nchunks[k]});
             o.baux.push_back(first_ptask[k]);
         }
+        sec[2] = (int32_t)o.baux.size();
         for (size_t k = 0; k < lvl_pack[l].size(); k += 2) {
             const int32_t n0 = lvl_pack[l][k], nn = lvl_pack[l][k + 1];
             const int32_t t = (int32_t)o.baux.size();
@@ -347,6 +355,7 @@ StaStatus build_tasks(Layout& o, const TaskShape& sh, std::string& err) {
             o.baux.push_back(0);
             for (int32_t n = n0; n < n0 + nn; ++n) net_step[n] = t;
         }
+        sec[3] = (int32_t)o.baux.size();
         for (size_t k = 0; k < nb; ++k) {
             const int32_t n = lvl_big[l][k];
             for (int32_t p0 = o.net_ptr[n] + 1; p0 < o.net_ptr[n + 1]; p0 += sh.chunk) {
@@ -355,6 +364,7 @@ StaStatus build_tasks(Layout& o, const TaskShape& sh, std::string& err) {
                 o.baux.push_back(dtask[k]);
             }
         }
+        sec[4] = (int32_t)o.baux.size();
     }
     o.TB = (int32_t)o.baux.size();
     o.pin_cons.assign(P, -1);

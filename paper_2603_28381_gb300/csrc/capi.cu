@@ -11,6 +11,7 @@
 // soon as arrival times exist and a gradient sweep queued there overlaps the
 // required-time sweep on the GPU: the GB300 counterpart of the paper's
 // two-stream operation fusion (Section 3.2).
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -56,6 +57,7 @@ struct StaHandle {
     int grid_fwd = 0, grid_bwd = 0;  // dataflow grids (blocks)
     // batched schedule: B placements, lane per placement
     int B = 1;
+    int bsweep = STA_BATCH_LEVELS;
     BatchState bs{};
     const int32_t* pin_int = nullptr;  // [P] internal index of each original pin
     const int32_t* big_dev = nullptr;  // [nbig] nets whose loads the prologue computes
@@ -63,7 +65,7 @@ struct StaHandle {
     float* qscratch = nullptr;         // device scratch of the batched pin-slack query
     size_t qscratch_bytes = 0;
     bool batch() const { return schedule == STA_SCHED_BATCH; }
-    std::vector<void*> allocs;
+    std::vector<std::pair<void*, size_t>> allocs;  // device allocations and their sizes
     size_t dev_bytes = 0;
     int device = 0;
     bool use_graphs = true;
@@ -108,10 +110,27 @@ struct StaHandle {
         const size_t bytes = (n ? n : 1) * sizeof(T);
         cudaError_t e = cudaMalloc(&q, bytes);
         if (e != cudaSuccess) return set_err(STA_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-        allocs.push_back(q);
+        allocs.emplace_back(q, bytes);
         dev_bytes += bytes;
         p = static_cast<T*>(q);
         return STA_OK;
+    }
+    // free one allocation made by alloc()/upload()
+    void release(const void* p) {
+        for (size_t i = 0; i < allocs.size(); ++i)
+            if (allocs[i].first == p) {
+                cudaFree(allocs[i].first);
+                dev_bytes -= allocs[i].second;
+                allocs.erase(allocs.begin() + (long)i);
+                return;
+            }
+    }
+    void drop_graphs() {
+        for (cudaGraphExec_t* gx : {&gx_fwd[0], &gx_fwd[1], &gx_rat, &gx_adj, &gx_fused})
+            if (*gx) {
+                cudaGraphExecDestroy(*gx);
+                *gx = nullptr;
+            }
     }
     template <typename T>
     StaStatus upload(const T*& dst, const std::vector<T>& src) {
@@ -134,7 +153,7 @@ struct StaHandle {
     ~StaHandle() {
         for (auto* gx : {gx_fwd[0], gx_fwd[1], gx_rat, gx_adj, gx_fused})
             if (gx) cudaGraphExecDestroy(gx);
-        for (void* p : allocs) cudaFree(p);
+        for (auto& a : allocs) cudaFree(a.first);
         if (stage) cudaFree(stage);
         if (qscratch) cudaFree(qscratch);
         if (pinned) cudaFreeHost(pinned);
@@ -207,9 +226,50 @@ void enqueue_backward_dataflow(StaHandle* h, int mode, float gamma, cudaStream_t
     launch_bwd_dataflow(h->g, h->s, h->d, h->grid_bwd, gamma, mode, st);
 }
 
+// Launches of a level-synchronous batched backward sweep: per level (deepest
+// first) the partial chunks and packed nets of the level with the gradient
+// chunks of the level above, then the driver steps of the level's large nets;
+// finally the gradient chunks of level 0.  Each entry holds up to three task ranges.
+void batch_bwd_phases(const Layout& L, int mode, std::vector<std::array<int, 6>>& out) {
+    out.clear();
+    for (int l = L.L - 1; l >= 0; --l) {
+        const int* s = &L.lvl_bsec[(size_t)l * 5];
+        std::array<int, 6> a = {s[0], s[1], s[2], s[3], 0, 0};
+        if ((mode & 2) && l + 1 < L.L) {
+            const int* u = &L.lvl_bsec[(size_t)(l + 1) * 5];
+            a[4] = u[3];
+            a[5] = u[4];
+        }
+        if (a[1] > a[0] || a[3] > a[2] || a[5] > a[4]) out.push_back(a);
+        if (s[2] > s[1]) out.push_back({s[1], s[2], 0, 0, 0, 0});
+    }
+    if ((mode & 2) && L.L > 0 && L.lvl_bsec[4] > L.lvl_bsec[3]) out.push_back({L.lvl_bsec[3], L.lvl_bsec[4], 0, 0, 0, 0});
+}
+
+int batch_fwd_levels(const Layout& L) {
+    int n = 0;
+    for (int l = 0; l < L.L; ++l) n += L.lvl_ftask[l + 1] > L.lvl_ftask[l] ? 1 : 0;
+    return n;
+}
+
 void enqueue_forward_batch(StaHandle* h, int lse, float gamma, cudaStream_t st) {
     const Layout& L = h->lay;
-    const size_t G = (size_t)h->bs.G;
+    if (h->bsweep == STA_BATCH_LEVELS) {
+        {
+            ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
+            launch_batch_load(h->g, h->bs, h->big_dev, h->nbig, st);
+            launch_batch_load_small(h->g, h->bs, L.shape.big, st);
+        }
+        for (int l = 0; l < L.L; ++l) {
+            if (L.lvl_ftask[l + 1] == L.lvl_ftask[l]) continue;
+            ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
+            launch_batch_fwd_level(h->g, h->bs, h->d, L.lvl_ftask[l], L.lvl_ftask[l + 1], gamma, lse, st);
+        }
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_ENDPOINTS, st);
+        launch_batch_endpoints(h->g, h->bs, gamma, lse, st);
+        return;
+    }
+    const size_t G = (size_t)h->bs.GT;
     cudaMemsetAsync(h->d.fcnt, 0, sizeof(int32_t) * (L.TF ? L.TF * G : 1), st);
     cudaMemsetAsync(h->d.heads, 0, sizeof(int32_t), st);
     cudaMemsetAsync(h->d.abort_word, 0, sizeof(int32_t), st);
@@ -229,7 +289,16 @@ void enqueue_backward_batch(StaHandle* h, int mode, float gamma, cudaStream_t st
     const Layout& L = h->lay;
     StaHandle::Prof* pr = (mode & 2) ? &h->prof_adj : &h->prof_rat;
     pr->next = 0;
-    cudaMemsetAsync((mode & 2) ? h->d.acnt : h->d.rcnt, 0, sizeof(int32_t) * (L.TB ? L.TB * (size_t)h->bs.G : 1), st);
+    if (h->bsweep == STA_BATCH_LEVELS) {
+        std::vector<std::array<int, 6>> ph;
+        batch_bwd_phases(L, mode, ph);
+        for (const auto& r : ph) {
+            ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJOINT : STA_PROF_REQUIRED, st);
+            launch_batch_bwd_level(h->g, h->bs, h->d, r.data(), gamma, mode, st);
+        }
+        return;
+    }
+    cudaMemsetAsync((mode & 2) ? h->d.acnt : h->d.rcnt, 0, sizeof(int32_t) * (L.TB ? L.TB * (size_t)h->bs.GT : 1), st);
     cudaMemsetAsync(h->d.heads + ((mode & 2) ? 2 : 1), 0, sizeof(int32_t), st);
     ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJOINT : STA_PROF_REQUIRED, st);
     launch_batch_bwd(h->g, h->bs, h->d, h->grid_bwd, gamma, mode, st);
@@ -363,6 +432,7 @@ StaStatus init_batch(StaHandle* h) {
     b.B = h->B;
     b.Bp = (h->B + 31) / 32 * 32;
     b.G = b.Bp / 32;
+    b.GT = b.Bp / kPlacePerWarp;
     const size_t P = L.P, N = L.N, E = L.E, Bp = b.Bp;
     StaStatus st = STA_OK;
 #define BSTEP(x)                  \
@@ -412,6 +482,64 @@ StaStatus init_batch(StaHandle* h) {
         launch_batch_init_ats(b, (int)P, 0);
     }
     CUDA_TRY(cudaGetLastError());
+    return STA_OK;
+}
+
+// Replace the dataflow task lists of a handle (batched schedule) by those of
+// another task shape: rebuild them on the host, free the old device copies,
+// upload the new ones and drop every captured graph.
+StaStatus set_tasks(StaHandle* h, const TaskShape& sh) {
+    Layout& L = h->lay;
+    try {
+        std::string err;
+        StaStatus st = build_tasks(L, sh, err);
+        if (st != STA_OK) return set_err(st, err);
+    } catch (const std::bad_alloc&) {
+        return set_err(STA_ERR_OOM, "host allocation failed");
+    }
+    const long long GT = h->bs.GT;
+    if ((long long)L.TF * GT >= (1ll << 31) || (long long)L.TB * GT >= (1ll << 31))
+        return set_err(STA_ERR_INVALID_ARG, "num_placements too large for this netlist");
+    DfState& d = h->d;
+    for (const void* p : {(const void*)d.ftask, (const void*)d.arc_prod, (const void*)d.btask, (const void*)d.baux,
+                          (const void*)d.pin_cons, (const void*)d.f_indeg, (const void*)d.f_out_ptr,
+                          (const void*)d.f_out, (const void*)d.b_indeg, (const void*)d.b_out_ptr, (const void*)d.b_out,
+                          (const void*)d.fcnt, (const void*)d.rcnt, (const void*)d.acnt, (const void*)h->bs.part,
+                          (const void*)h->bs.rpart, (const void*)h->big_dev})
+        h->release(p);
+    StaStatus st = STA_OK;
+#define TSTEP(x)                     \
+    do {                             \
+        st = (x);                    \
+        if (st != STA_OK) return st; \
+    } while (0)
+    const int32_t* cp = nullptr;
+    TSTEP(h->upload(cp, L.ftask));
+    d.ftask = reinterpret_cast<const int4*>(cp);
+    TSTEP(h->upload(d.arc_prod, L.arc_prod));
+    TSTEP(h->upload(cp, L.btask));
+    d.btask = reinterpret_cast<const int4*>(cp);
+    TSTEP(h->upload(d.baux, L.baux));
+    TSTEP(h->upload(d.pin_cons, L.pin_cons));
+    TSTEP(h->upload(d.f_indeg, L.f_indeg));
+    TSTEP(h->upload(d.f_out_ptr, L.f_out_ptr));
+    TSTEP(h->upload(d.f_out, L.f_out));
+    TSTEP(h->upload(d.b_indeg, L.b_indeg));
+    TSTEP(h->upload(d.b_out_ptr, L.b_out_ptr));
+    TSTEP(h->upload(d.b_out, L.b_out));
+    TSTEP(h->alloc(d.fcnt, (size_t)L.TF * GT));
+    TSTEP(h->alloc(d.rcnt, (size_t)L.TB * GT));
+    TSTEP(h->alloc(d.acnt, (size_t)L.TB * GT));
+    TSTEP(h->alloc(h->bs.part, (size_t)L.npart * kPartFloats * h->bs.Bp));
+    TSTEP(h->alloc(h->bs.rpart, (size_t)L.npart * kPartFloats * h->bs.Bp));
+    TSTEP(h->upload(h->big_dev, L.big_nets));
+#undef TSTEP
+    h->nbig = (int)L.big_nets.size();
+    d.TF = L.TF;
+    d.TB = L.TB;
+    h->drop_graphs();
+    h->have_fwd = h->have_lse = h->have_rat = false;
+    h->rat_pending = false;
     return STA_OK;
 }
 
@@ -480,13 +608,16 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
             TaskShape sh;
             sh.pack_pins = opts->tile_pins > 0 ? opts->tile_pins : 4;
             sh.pack_nets = 1 << 20;
-            sh.chunk = opts->chunk > 0 ? opts->chunk : 64;
+            sh.chunk = opts->chunk > 0 ? opts->chunk : 16;
+            if (opts->batch_sweep != STA_BATCH_LEVELS && opts->batch_sweep != STA_BATCH_DATAFLOW)
+                return fail(set_err(STA_ERR_INVALID_ARG, "StaOptions.batch_sweep must be LEVELS or DATAFLOW"));
+            h->bsweep = opts->batch_sweep;
             sh.big = sh.chunk + 1;  // a driver and `chunk` sinks still form one task
             try {
                 std::string err;
                 StaStatus st = build_tasks(h->lay, sh, err);
                 if (st != STA_OK) return fail(set_err(st, err));
-                const long long G = (h->B + 31) / 32;
+                const long long G = (h->B + 31) / 32 * (32 / kPlacePerWarp);
                 if ((long long)h->lay.TF * G >= (1ll << 31) || (long long)h->lay.TB * G >= (1ll << 31) ||
                     (long long)h->lay.P * 4 * G * 32 >= (1ll << 40))
                     return fail(set_err(STA_ERR_INVALID_ARG, "num_placements too large for this netlist"));
@@ -552,7 +683,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         STEP(h->upload(d.b_out_ptr, L.b_out_ptr));
         STEP(h->upload(d.b_out, L.b_out));
     }
-    const size_t G = bat ? (size_t)(h->B + 31) / 32 : 1;
+    const size_t G = bat ? (size_t)(h->B + 31) / 32 * (32 / kPlacePerWarp) : 1;
     STEP(h->alloc(d.fcnt, L.TF * G));
     STEP(h->alloc(d.rcnt, L.TB * G));
     STEP(h->alloc(d.acnt, L.TB * G));
@@ -616,7 +747,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     if (h->profile) {  // event pairs for every launch of each sequence, made before any capture
         const size_t nl = (size_t)L.L;
         const std::pair<StaHandle::Prof*, size_t> sizes[] = {
-            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 2}, {&h->prof_rat, nl + 1}, {&h->prof_adj, nl + 1},
+            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 2}, {&h->prof_rat, 2 * nl + 2}, {&h->prof_adj, 2 * nl + 2},
             {&h->prof_out, 1}};
         for (const auto& ps : sizes) {
             ps.first->kind.assign(ps.second, 0);
@@ -796,9 +927,86 @@ StaStatus sta_synchronize(StaHandle* h) {
 
 StaStatus sta_debug_expire_wait(StaHandle* h) {
     if (!h) return set_err(STA_ERR_INVALID_ARG, "null handle");
-    if (h->schedule == STA_SCHED_LEVELS) return set_err(STA_ERR_STATE, "the level schedule has no waits");
+    if (h->schedule == STA_SCHED_LEVELS || (h->batch() && h->bsweep == STA_BATCH_LEVELS))
+        return set_err(STA_ERR_STATE, "level-synchronous sweeps have no waits");
     h->expire_next = true;
     return STA_OK;
+}
+
+StaStatus sta_autotune(StaHandle* h, const int32_t* tile_pins, int32_t n_tile, const int32_t* chunks,
+                       int32_t n_chunk, const int32_t* sweeps, int32_t n_sweep, int32_t reps, float gamma, float* ms,
+                       int32_t* best) {
+    if (!h || !tile_pins || !chunks || !sweeps || n_tile < 1 || n_chunk < 1 || n_sweep < 1 || reps < 1 || !best)
+        return set_err(STA_ERR_INVALID_ARG, "sta_autotune: null or empty candidate lists");
+    if (!h->batch()) return set_err(STA_ERR_STATE, "sta_autotune: the batched schedule only");
+    if (!h->have_pos) return set_err(STA_ERR_STATE, "sta_autotune: sta_set_positions first");
+    if (!(std::isfinite(gamma) && gamma > 0.f)) return set_err(STA_ERR_INVALID_ARG, "gamma must be > 0");
+    for (int32_t i = 0; i < n_tile; ++i)
+        if (tile_pins[i] < 1) return set_err(STA_ERR_INVALID_ARG, "tile_pins must be >= 1");
+    for (int32_t i = 0; i < n_chunk; ++i)
+        if (chunks[i] < 1) return set_err(STA_ERR_INVALID_ARG, "chunk must be >= 1");
+    for (int32_t i = 0; i < n_sweep; ++i)
+        if (sweeps[i] != STA_BATCH_LEVELS && sweeps[i] != STA_BATCH_DATAFLOW)
+            return set_err(STA_ERR_INVALID_ARG, "sweeps: STA_BATCH_LEVELS or STA_BATCH_DATAFLOW");
+    CUDA_TRY(cudaDeviceSynchronize());
+    cudaStream_t st = h->side;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 0.f;
+    int32_t bi = -1;
+    StaStatus status = STA_OK;
+    for (int32_t i = 0; i < n_tile && status == STA_OK; ++i)
+        for (int32_t j = 0; j < n_chunk && status == STA_OK; ++j)
+            for (int32_t k = 0; k < n_sweep && status == STA_OK; ++k) {
+                TaskShape sh;
+                sh.pack_pins = tile_pins[i];
+                sh.pack_nets = 1 << 20;
+                sh.chunk = chunks[j];
+                sh.big = chunks[j] + 1;
+                h->bsweep = sweeps[k];
+                if ((status = set_tasks(h, sh)) != STA_OK) break;
+                // one step (forward with LSE and required times, fused gradient sweep) as a graph
+                cudaGraphExec_t gx = nullptr;
+                status = capture(h, &gx, [&](cudaStream_t c) {
+                    enqueue_forward(h, 1, gamma, c);
+                    enqueue_backward(h, 3, gamma, c);
+                });
+                if (status != STA_OK) break;
+                float t = 0.f;
+                cudaError_t e = cudaGraphLaunch(gx, st);  // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                for (int32_t r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(gx, st);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+                cudaGraphExecDestroy(gx);
+                if (e != cudaSuccess) {
+                    status = set_err(STA_ERR_CUDA, std::string("sta_autotune: ") + cudaGetErrorString(e));
+                    break;
+                }
+                t /= (float)reps;
+                if (ms) ms[((size_t)i * n_chunk + j) * n_sweep + k] = t;
+                if (bi < 0 || t < best_ms) {
+                    best_ms = t;
+                    bi = (int32_t)(((size_t)i * n_chunk + j) * n_sweep + k);
+                    best[0] = tile_pins[i];
+                    best[1] = chunks[j];
+                    best[2] = sweeps[k];
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != STA_OK) return status;
+    StaStatus s2 = sync_checked(h, st);  // a dataflow candidate whose wait expired
+    if (s2 != STA_OK) return s2;
+    TaskShape sh;
+    sh.pack_pins = best[0];
+    sh.pack_nets = 1 << 20;
+    sh.chunk = best[1];
+    sh.big = best[1] + 1;
+    h->bsweep = best[2];
+    return set_tasks(h, sh);
 }
 
 StaStatus sta_query_summary(StaHandle* h, double* out, int on_device, void* stream) {
@@ -926,7 +1134,17 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
     launches[STA_PROF_POSITIONS] = L.P > 0 ? 1 : 0;
     launches[STA_PROF_ENDPOINTS] = 2;
     launches[STA_PROF_OUTPUT] = (h->batch() && L.P > 0) ? 1 : 0;
-    if (h->batch()) {
+    if (h->batch() && h->bsweep == STA_BATCH_LEVELS) {
+        std::vector<std::array<int, 6>> ph;
+        batch_bwd_phases(L, 3, ph);
+        const int32_t nb = (int32_t)ph.size();
+        batch_bwd_phases(L, 1, ph);
+        launches[STA_PROF_NET_RC] = (h->nbig > 0 ? 1 : 0) + (L.N > 0 ? 1 : 0);
+        launches[STA_PROF_FORWARD] = batch_fwd_levels(L);
+        launches[STA_PROF_REQUIRED] = h->last_fused ? 0 : (int32_t)ph.size();
+        launches[STA_PROF_SEED] = 1;
+        launches[STA_PROF_ADJOINT] = nb;
+    } else if (h->batch()) {
         launches[STA_PROF_NET_RC] = h->nbig > 0 ? 1 : 0;
         launches[STA_PROF_FORWARD] = L.TF > 0 ? 1 : 0;
         launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 1 : 0;

@@ -75,6 +75,7 @@ struct DfState {
 // Per-placement state is pin-major, placement-minor: value[(row) * Bp + b].
 struct BatchState {
     int32_t B, Bp, G;    // placements, padded to a multiple of 32, groups of 32
+    int32_t GT;          // task groups of kPlacePerWarp placements (Bp / 8)
     float2* xy;          // [P][Bp]
     float* load;         // [N][Bp]
     float* at;           // [P*4][Bp]
@@ -93,12 +94,20 @@ struct BatchState {
     float* net_gload;    // [N][Bp] d loss / d load of large nets
 };
 constexpr size_t kBatchEpBytes = 48;  // one endpoint partial
+constexpr int kPlacePerWarp = 8;       // sweep tasks: 8 placements x 4 conditions per warp
 
 int batch_max_blocks(int fwd);
 void launch_batch_load(const DevNet& g, const BatchState& bs, const int32_t* big_nets, int nbig, cudaStream_t st);
 void launch_batch_fwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int lse,
                       cudaStream_t st);
 void launch_batch_endpoints(const DevNet& g, const BatchState& bs, float gamma, int lse, cudaStream_t st);
+// level-synchronous batched sweeps
+void launch_batch_load_small(const DevNet& g, const BatchState& bs, int big, cudaStream_t st);
+void launch_batch_fwd_level(const DevNet& g, const BatchState& bs, const DfState& d, int t0, int t1, float gamma,
+                            int lse, cudaStream_t st);
+// r6: up to three backward task ranges [r6[0], r6[1]), [r6[2], r6[3]), [r6[4], r6[5])
+void launch_batch_bwd_level(const DevNet& g, const BatchState& bs, const DfState& d, const int* r6, float gamma,
+                            int mode, cudaStream_t st);
 void launch_batch_bwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int mode,
                       cudaStream_t st);
 void launch_batch_xy_in(const BatchState& bs, const int32_t* pin_int, int P, const float2* xy_user, cudaStream_t st);

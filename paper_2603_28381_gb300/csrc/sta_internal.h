@@ -69,6 +69,10 @@ struct Layout {
     // dataflow schedule (one persistent kernel per sweep, tasks in topological order)
     TaskShape shape;
     std::vector<int32_t> big_nets;   // nets split into chunks (their load comes from a prologue)
+    std::vector<int32_t> lvl_ftask;  // [L+1] forward tasks of each level
+    std::vector<int32_t> lvl_bsec;   // [L][5] backward tasks of level l: partial chunks from [0],
+                                     // driver steps from [1], packed nets from [2], gradient chunks
+                                     // from [3], end [4]
     //   forward task  {first net, nets (> 0) | -1 for a 32-sink chunk of a large net, first pin, pins}
     //   backward task {net(s), kind, first pin, pins}: kind > 0 packed nets (= count), -1 partial
     //   chunk of a large net, -2 its driver step (first pin = first partial slot, pins = chunks),

@@ -116,7 +116,7 @@ def run_gpu(nl, lib, xy, gamma=10.0, w=(1.0, 0.5), use_graphs=True, host_xy=Fals
 
 
 def run_gpu_batch(nl, lib, xyb, gamma=10.0, w=(1.0, 0.5), use_graphs=True, host_xy=False, engine=None,
-                  tile_pins=0, chunk=0):
+                  tile_pins=0, chunk=0, sweep="levels"):
     """The batched schedule on B placements xyb [B,P,2]: one set_positions +
     forward(LSE, RAT) + backward; a list of B per-placement result dicts."""
     import torch
@@ -125,7 +125,7 @@ def run_gpu_batch(nl, lib, xyb, gamma=10.0, w=(1.0, 0.5), use_graphs=True, host_
     xyb = np.ascontiguousarray(np.asarray(xyb, np.float32))
     B = xyb.shape[0]
     eng = engine or sta.StaEngine(nl, lib, use_graphs=use_graphs, schedule="batch", num_placements=B,
-                                  tile_pins=tile_pins, chunk=chunk)
+                                  tile_pins=tile_pins, chunk=chunk, batch_sweep=sweep)
     if host_xy:
         eng.set_positions(xyb)
     else:

@@ -33,32 +33,38 @@ def _check_all(nl, lib, xyb, W, gamma, res, which=None):
         tp.assert_parity(res[b], ora)
 
 
+SWEEPS = ["levels", "dataflow"]
+
+
+@pytest.mark.parametrize("sweep", SWEEPS)
 @pytest.mark.parametrize("B", [1, 5, 33])
-def test_tiny_design_batches(B):
+def test_tiny_design_batches(B, sweep):
     w = netgen.tiny_design(0)
     xyb, W = _placements(w, B), _weights(B)
-    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W)
+    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, sweep=sweep)
     _check_all(w.netlist, w.library, xyb, W, 10.0, res)
 
 
+@pytest.mark.parametrize("sweep", SWEEPS)
 @pytest.mark.parametrize("tile_pins,chunk", [(1, 1), (16, 8), (4, 64), (64, 200)])
-def test_task_shapes_mid_size(tile_pins, chunk):
+def test_task_shapes_mid_size(tile_pins, chunk, sweep):
     # power-law fanout and 400-sink primary-input nets: packed nets, single nets
     # and chunked large nets, two placement groups with a ragged second group
     w = netgen.superblue_like(3, scale=0.02, depth=40)
     B = 40
     xyb, W = _placements(w, B), _weights(B)
-    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 20.0, W, tile_pins=tile_pins, chunk=chunk)
+    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 20.0, W, tile_pins=tile_pins, chunk=chunk, sweep=sweep)
     _check_all(w.netlist, w.library, xyb, W, 20.0, res, which=[0, 17, 31, 32, 39])
 
 
+@pytest.mark.parametrize("sweep", SWEEPS)
 @pytest.mark.parametrize("idx", range(3))
-def test_edge_netlists_batched(idx):
+def test_edge_netlists_batched(idx, sweep):
     name, nl, xy, lib = tp.edge_netlists()[idx]
     B = 3
     xyb = netgen.jitter_positions(xy, B, 2.0, 5)
     W = _weights(B)
-    res = tp.run_gpu_batch(nl, lib, xyb, 10.0, W)
+    res = tp.run_gpu_batch(nl, lib, xyb, 10.0, W, sweep=sweep)
     _check_all(nl, lib, xyb, W, 10.0, res)
 
 
@@ -72,6 +78,18 @@ def test_alone_equals_in_batch_bitwise():
         for k in ("at", "slew", "rat", "ats", "slack", "ep_slack", "grad"):
             assert np.array_equal(alone[k], full[b][k]), (b, k)
         assert alone["summary"] == full[b]["summary"]
+
+
+def test_sweeps_bit_identical():
+    w = netgen.superblue_like(8, scale=0.01, depth=30)
+    B = 12
+    xyb, W = _placements(w, B), _weights(B)
+    a = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, sweep="levels", chunk=8)
+    b = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, sweep="dataflow", chunk=8)
+    for r, s in zip(a, b):
+        for k in ("at", "slew", "rat", "ats", "slack", "ep_slack", "grad"):
+            assert np.array_equal(r[k], s[k]), k
+        assert r["summary"] == s["summary"]
 
 
 def test_host_buffers_graphs_and_repeats():
@@ -98,13 +116,14 @@ def test_host_buffers_graphs_and_repeats():
     eng.close()
 
 
-def test_batched_full_size_500k_64_placements():
+@pytest.mark.parametrize("sweep", SWEEPS)
+def test_batched_full_size_500k_64_placements(sweep):
     # the batched workload: ~500k pins, depth 100, 64 placements with 5 um jitter;
     # sampled placements against the oracle
     w = netgen.superblue_like(2, scale=0.2, depth=100)
     B = 64
     xyb, W = _placements(w, B), _weights(B)
-    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W)
+    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, sweep=sweep)
     _check_all(w.netlist, w.library, xyb, W, 10.0, res, which=[0, 63])
 
 
@@ -114,7 +133,7 @@ def test_batched_wait_expiry_reported():
     B = 4
     xyb, W = _placements(w, B), _weights(B)
     import torch
-    eng = sta.StaEngine(w.netlist, w.library, schedule="batch", num_placements=B)
+    eng = sta.StaEngine(w.netlist, w.library, schedule="batch", num_placements=B, batch_sweep="dataflow")
     eng.set_positions(torch.as_tensor(xyb).cuda())
     eng._debug_expire_wait()
     eng.forward(gamma=10.0)
@@ -123,3 +142,19 @@ def test_batched_wait_expiry_reported():
     assert ei.value.status == 5
     res = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, engine=eng)
     _check_all(w.netlist, w.library, xyb, W, 10.0, res, which=[0, 3])
+
+
+def test_autotune_picks_a_candidate_and_stays_exact():
+    import torch
+    import paper_2603_28381_gb300 as sta
+    w = netgen.superblue_like(9, scale=0.01, depth=30)
+    B = 16
+    xyb, W = _placements(w, B), _weights(B)
+    eng = sta.StaEngine(w.netlist, w.library, schedule="batch", num_placements=B)
+    eng.set_positions(torch.as_tensor(xyb).cuda())
+    best, table = eng.autotune(tile_pins=(1, 4), chunks=(4, 32), sweeps=("levels", "dataflow"), reps=2)
+    assert len(table) == 8 and all(np.isfinite(v) and v > 0 for v in table.values())
+    assert best in table and table[best] == min(table.values())
+    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, engine=eng)
+    _check_all(w.netlist, w.library, xyb, W, 10.0, res, which=[0, 15])
+    eng.close()
