@@ -281,7 +281,7 @@ __device__ void bfwd_chunk(const DevNet& g, const BatchState& bs, const DfState&
 }
 
 template <bool lse>
-__global__ void __launch_bounds__(kBlock) k_bfwd(DevNet g, BatchState bs, DfState d, float gamma) {
+__global__ void __launch_bounds__(kBlock, 4) k_bfwd(DevNet g, BatchState bs, DfState d, float gamma) {
     const int GT = bs.GT;
     const int Q = d.TF * GT;
     int q = grab(d.heads + 0);
@@ -692,20 +692,42 @@ __device__ void bbwd_driver(const DevNet& g, const BatchState& bs, const DfState
 
     const float* part = (mode & 2) ? bs.part : bs.rpart;
     float R = L.el ? kInf : -kInf, GA = 0.f, GS = 0.f, sx = 0.f, sy = 0.f, hx = 0.f, hy = 0.f;
-    for (int k = 0; k < nch; ++k) {
-        const int base = (slot0 + k) * kPartFloats;
-        const float r = __ldcg(part + ix(base + L.c, Bp, b));
-        R = L.el ? fminf(R, r) : fmaxf(R, r);
-        if ((mode & 2) && L.el) {
-            GA += __ldcg(part + ix(base + 4 + L.rf, Bp, b));
-            GS += __ldcg(part + ix(base + 6 + L.rf, Bp, b));
+    // The chunks' partials in chunk order.  Lane c of a quad reads slots c
+    // (its required time), 4 + c and 8 + c of every chunk, loads of 8 chunks
+    // issued together; the sums are then handed to the lanes that use them.
+    constexpr int kU = 8;
+    float v4 = 0.f, v8 = 0.f;
+    for (int k0 = 0; k0 < nch; k0 += kU) {
+        float vr[kU], va[kU], vb[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int base = (slot0 + k0 + u) * kPartFloats;
+            const bool ok = k0 + u < nch;
+            vr[u] = ok ? __ldcg(part + ix(base + L.c, Bp, b)) : (L.el ? kInf : -kInf);
+            va[u] = ((mode & 2) && ok) ? __ldcg(part + ix(base + 4 + L.c, Bp, b)) : 0.f;
+            vb[u] = ((mode & 2) && ok) ? __ldcg(part + ix(base + 8 + L.c, Bp, b)) : 0.f;
         }
-        if ((mode & 2) && L.c == 2) {
-            sx += __ldcg(part + ix(base + 8, Bp, b));
-            sy += __ldcg(part + ix(base + 9, Bp, b));
-            hx += __ldcg(part + ix(base + 10, Bp, b));
-            hy += __ldcg(part + ix(base + 11, Bp, b));
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (k0 + u >= nch) break;
+            R = L.el ? fminf(R, vr[u]) : fmaxf(R, vr[u]);
+            v4 += va[u];
+            v8 += vb[u];
         }
+    }
+    {
+        // slot 4 + c: lanes 0, 1 hold the g_ats sums (rise, fall), lanes 2, 3 the
+        // g_slew sums; slot 8 + c: sx, sy, hx, hy
+        const int q0 = L.lane & ~3;
+        const float ga_src = __shfl_sync(kFull, v4, q0 + (L.c & 1));
+        const float sx_ = __shfl_sync(kFull, v8, q0 + 0), sy_ = __shfl_sync(kFull, v8, q0 + 1);
+        const float hx_ = __shfl_sync(kFull, v8, q0 + 2), hy_ = __shfl_sync(kFull, v8, q0 + 3);
+        GA = L.el ? ga_src : 0.f;
+        GS = L.el ? v4 : 0.f;
+        sx = sx_;
+        sy = sy_;
+        hx = hx_;
+        hy = hy_;
     }
     if (mode & 1) bs.rat[ix(4 * dp + L.c, Bp, b)] = R;
     const float gl = bcell_apply<mode>(bs, bc, L, R, GA, GS);
@@ -758,7 +780,7 @@ __device__ __forceinline__ void bbwd_task(const DevNet& g, const BatchState& bs,
 }
 
 template <int mode>
-__global__ void __launch_bounds__(kBlock) k_bbwd(DevNet g, BatchState bs, DfState d, float gamma) {
+__global__ void __launch_bounds__(kBlock, 3) k_bbwd(DevNet g, BatchState bs, DfState d, float gamma) {
     int32_t* cnt = (mode & 2) ? d.acnt : d.rcnt;
     int32_t* head = d.heads + ((mode & 2) ? 2 : 1);
     const int GT = bs.GT;
@@ -792,7 +814,7 @@ __device__ __forceinline__ int range_task(const Ranges& r, int i) {
 }
 
 template <bool lse>
-__global__ void __launch_bounds__(kBlock) k_bfwd_lvl(DevNet g, BatchState bs, DfState d, int t0, int t1,
+__global__ void __launch_bounds__(kBlock, 4) k_bfwd_lvl(DevNet g, BatchState bs, DfState d, int t0, int t1,
                                                       float gamma) {
     const int GT = bs.GT;
     const int nw = (t1 - t0) * GT;
@@ -806,7 +828,7 @@ __global__ void __launch_bounds__(kBlock) k_bfwd_lvl(DevNet g, BatchState bs, Df
 }
 
 template <int mode>
-__global__ void __launch_bounds__(kBlock) k_bbwd_lvl(DevNet g, BatchState bs, DfState d, Ranges r, float gamma) {
+__global__ void __launch_bounds__(kBlock, 3) k_bbwd_lvl(DevNet g, BatchState bs, DfState d, Ranges r, float gamma) {
     const int GT = bs.GT;
     const int nw = ((r.a1 - r.a0) + (r.b1 - r.b0) + (r.c1 - r.c0)) * GT;
     for (int i = (blockIdx.x * kBlock + threadIdx.x) >> 5; i < nw; i += gridDim.x * kWarpsPerBlock) {
