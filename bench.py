@@ -47,12 +47,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--schedule", default="dataflow", choices=["dataflow", "levels"])
-    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
                     help="single: one placement of the ~2.5M-pin netlist per step (the headline); "
                          "batch: 64 placements of a ~500k-pin netlist per step")
     ap.add_argument("--placements", type=int, default=64)
     ap.add_argument("--verbose", action="store_true", help="per-step times on stderr")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the one-placement-per-call comparison")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
+    ap.add_argument("--netlists", type=int, default=10, help="serve: distinct netlists (20k to 3M pins)")
+    ap.add_argument("--load", type=float, default=0.8,
+                    help="serve: arrival rate as a fraction of the plain loop's service rate")
+    ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--tile-pins", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--batch-sweep", default="levels", choices=["levels", "dataflow"])
@@ -536,12 +541,123 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# serving: a Poisson stream of requests over resident netlists of 20k-3M pins
+# --------------------------------------------------------------------------
+def serve_workload(args):
+    import netgen
+    rng = np.random.default_rng(args.seed + 17)
+    lo, hi = np.log(20e3), np.log(3e6)
+    pins = np.exp(np.linspace(lo, hi, args.netlists))  # log-spaced sizes, in random order
+    rng.shuffle(pins)
+    designs = []
+    for i, p in enumerate(pins):
+        depth = int(np.clip(30 + 120 * (np.log(p) - lo) / (hi - lo), 30, 150))
+        designs.append(netgen.superblue_like(100 + i, scale=float(p / 2.5e6), depth=depth))
+    return designs
+
+
+def run_serve(args):
+    import torch
+
+    import netgen
+    from paper_2603_28381_gb300.serving import StaServer
+    designs = serve_workload(args)
+    rng = np.random.default_rng(args.seed + 29)
+    R = args.requests
+    which = rng.integers(0, len(designs), R)
+    grad = rng.random(R) < 0.3
+    # two position sets per netlist (pinned), alternated: every request uploads a
+    # full position array; gradients go to one pinned buffer per netlist
+    xs = [[torch.from_numpy(netgen.jitter_positions(w.xy, 1, 5.0, 7 + j)[0]).pin_memory() for j in range(2)]
+          for w in designs]
+    gs = [torch.zeros(w.netlist.num_pins, 2).pin_memory() for w in designs]
+    pins = np.array([w.netlist.num_pins for w in designs])
+
+    def play(server, ids, arrivals):
+        """Submit at the arrival times, collect completions; latencies in ms."""
+        done, lat, t_first, t_last = 0, np.zeros(R), None, 0.0
+        rid_of = {}
+        t0 = StaServer.clock() + 0.05
+        i = 0
+        while done < R:
+            now = StaServer.clock()
+            while i < R and now >= t0 + arrivals[i]:
+                k = int(which[i])
+                rid = server.submit(ids[k], xs[k][i & 1], gradient=bool(grad[i]), gamma=GAMMA, w=WEIGHTS,
+                                    grad_out=gs[k])
+                rid_of[rid] = i
+                i += 1
+            wait = 0 if i < R else 50
+            for c in server.poll(wait_ms=wait):
+                j = rid_of.pop(c["id"])
+                if c["status"] != 0:
+                    raise RuntimeError(f"request {j} failed with status {c['status']}")
+                lat[j] = (c["t_done"] - (t0 + arrivals[j])) * 1e3
+                t_last = max(t_last, c["t_done"])
+                done += 1
+            if i < R and wait == 0:
+                time.sleep(max(0.0, min(0.0005, t0 + arrivals[i] - StaServer.clock())))
+        span = t_last - t0
+        return lat, span
+
+    # service times of the plain loop, request by request, to set the arrival rate
+    calib = StaServer(sequential=True)
+    ids = [calib.add_netlist(w.netlist, w.library) for w in designs]
+    cal = []
+    for k in range(len(designs)):
+        for gflag in (False, True):
+            for _ in range(3):
+                rid = calib.submit(ids[k], xs[k][0], gradient=gflag, gamma=GAMMA, w=WEIGHTS, grad_out=gs[k])
+                c = []
+                while not c:
+                    c = calib.poll(wait_ms=100)
+                cal.append((k, gflag, c[0]["t_done"] - c[0]["t_start"]))
+    calib.close()
+    svc = {}
+    for k, gflag, t in cal:
+        svc.setdefault((k, gflag), []).append(t)
+    mean_svc = float(np.mean([np.median(svc[(int(which[i]), bool(grad[i]))]) for i in range(R)]))
+    rate = args.load / mean_svc
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, R))
+
+    out = {}
+    for mode in ("plain", "continuous"):
+        srv = StaServer(sequential=(mode == "plain"), slots=args.slots)
+        ids = [srv.add_netlist(w.netlist, w.library) for w in designs]
+        stats0 = srv.stats()
+        lat, span = play(srv, ids, arrivals)
+        st = srv.stats()
+        srv.close()
+        out[mode] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "mean_ms": float(lat.mean()), "requests_per_s": R / span,
+                     "pins_per_s": float(pins[which].sum() / span), "span_s": span,
+                     "resident_netlists": stats0["resident"], "resident_bytes": stats0["resident_bytes"],
+                     "evictions": st["evictions"]}
+    line = {"metric": "served p50/p99 latency vs plain", "value": out["continuous"]["p99_ms"], "unit": "ms p99",
+            "n_gpus": 1, "steps": R, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{R} Poisson requests ({args.load:.0%} of the plain loop's capacity) over "
+                                   f"{len(designs)} resident netlists of {int(pins.min())}-{int(pins.max())} "
+                                   f"pins (log-spaced sizes), 70% forward (AT, LSE-AT, required times, "
+                                   f"slacks), 30% forward + gradient, new positions per request",
+                       "netlist_pins": pins.tolist(), "arrival_rate_per_s": rate,
+                       "mean_plain_service_ms": mean_svc * 1e3, "slots": args.slots,
+                       "budget": "150 GiB"},
+            "continuous": out["continuous"], "plain": out["plain"],
+            "p99_speedup_vs_plain": out["plain"]["p99_ms"] / out["continuous"]["p99_ms"],
+            "p50_speedup_vs_plain": out["plain"]["p50_ms"] / out["continuous"]["p50_ms"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -104,7 +104,8 @@ typedef struct {
     int32_t chunk;       /* STA_SCHED_BATCH task shape: nets of more than `chunk` sinks are
                             split into tasks of `chunk` sinks (0 = default 16) */
     int32_t batch_sweep; /* STA_SCHED_BATCH: STA_BATCH_LEVELS (default) or STA_BATCH_DATAFLOW */
-    int32_t reserved[1];
+    int32_t grid_blocks; /* dataflow sweeps: blocks of the persistent kernels (0 = every block
+                            that fits on the device; fewer leave room for other work) */
 } StaOptions;
 
 /* StaOptions.schedule.  Both compute the same quantities: arrival, slew,
@@ -141,6 +142,8 @@ typedef struct StaHandle StaHandle;
 /* sta_forward flags */
 #define STA_FWD_LSE 1u  /* also propagate LSE arrival times (needed before sta_backward_grad) */
 #define STA_FWD_RAT 2u  /* also propagate required times and per-pin slack */
+#define STA_FWD_RAT_EAGER 4u /* with STA_FWD_RAT: run the required-time sweep in this call, on
+                                `stream`, instead of deferring it to the next gradient sweep or query */
 
 /* summary slots written by sta_forward and read by sta_query_summary */
 enum {
@@ -313,6 +316,63 @@ const char *sta_last_error(void);
 
 /* STA_ABI_VERSION of the loaded library. */
 int sta_abi_version(void);
+
+
+/* ---------------------------------------------------------------------------
+ * Serving: netlists resident on the device under a memory budget, and a
+ * request loop that runs STA / gradient requests on a pool of CUDA streams
+ * ("slots").  A worker thread admits each request as soon as a slot is free
+ * and its netlist is resident and idle, so requests on different netlists run
+ * concurrently on the device; requests of one netlist run in order.  A
+ * netlist that is not resident is created when the budget allows, evicting
+ * idle netlists in least-recently-used order.  A request's results equal those
+ * of the same request run alone.  All calls are thread-safe.
+ * ------------------------------------------------------------------------- */
+typedef struct StaServer StaServer;
+
+typedef struct {
+    int32_t slots;        /* concurrent requests (0 = 4, at most 64) */
+    int32_t sequential;   /* 1: the plain loop: one request at a time, in arrival order */
+    int64_t budget_bytes; /* device bytes for resident netlists (0 = 150 GiB) */
+    int32_t reserved[4];
+} StaServerOptions;
+
+typedef struct {
+    int32_t netlist;      /* id from sta_server_add_netlist */
+    int32_t gradient;     /* 0: forward (AT, LSE-AT, required times, slacks, WNS/TNS);
+                             1: forward and the gradient of w_tns TNS_gamma + w_wns WNS_gamma */
+    float gamma;          /* smoothing, ps, > 0 */
+    float w_tns, w_wns;
+    const float *xy;      /* host [num_pins][2]; read until the request completes; pinned
+                             memory keeps the copy asynchronous */
+    float *grad;          /* host [num_pins][2] (gradient requests; may be NULL); pinned */
+    double *summary;      /* host [STA_SUM_COUNT] (may be NULL); written before completion */
+} StaServerRequest;
+
+typedef struct {
+    int64_t id;
+    int32_t status;       /* StaStatus of the request */
+    int32_t netlist;
+    double t_submit, t_start, t_done; /* sta_server_clock() seconds: submitted, started, seen done */
+} StaServerCompletion;
+
+StaStatus sta_server_create(const StaServerOptions *opt, StaServer **out);
+/* Register a netlist (arrays are copied); preload != 0 also makes it resident
+ * now (OOM if it does not fit).  *id identifies it in requests. */
+StaStatus sta_server_add_netlist(StaServer *s, const StaNetlistDesc *nl, const StaLibrary *lib,
+                                 int32_t preload, int32_t *id);
+StaStatus sta_server_submit(StaServer *s, const StaServerRequest *req, int64_t *id);
+/* Up to max completions (waiting up to wait_ms for the first one); *n = count. */
+StaStatus sta_server_poll(StaServer *s, StaServerCompletion *out, int32_t max, int32_t *n,
+                          int32_t wait_ms);
+/* Device bytes a netlist takes when resident: an upper-bound estimate from its
+ * sizes until it has been resident once, then the measured amount. */
+StaStatus sta_server_netlist_bytes(StaServer *s, int32_t id, int64_t *bytes);
+/* out4: resident netlists, resident device bytes, admissions, evictions */
+StaStatus sta_server_stats(StaServer *s, int64_t *out4);
+/* Finishes every submitted request, then frees everything. */
+void sta_server_destroy(StaServer *s);
+double sta_server_clock(void); /* steady clock, seconds */
 
 #ifdef __cplusplus
 }

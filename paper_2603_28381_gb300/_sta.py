@@ -18,6 +18,7 @@ STATUS = {0: "STA_OK", 1: "STA_ERR_INVALID_ARG", 2: "STA_ERR_NOT_DAG", 3: "STA_E
           4: "STA_ERR_CUDA", 5: "STA_ERR_TIMEOUT", 6: "STA_ERR_STATE"}
 STA_FWD_LSE = 1
 STA_FWD_RAT = 2
+STA_FWD_RAT_EAGER = 4
 SUMMARY_KEYS = ("wns_early", "tns_early", "wns_late", "tns_late", "tns_gamma", "wns_gamma",
                 "late_violations", "num_endpoints")
 
@@ -41,7 +42,7 @@ class StaLibrary(ctypes.Structure):
 
 class StaOptions(ctypes.Structure):
     _fields_ = [("use_graphs", _i32), ("profile", _i32), ("schedule", _i32), ("num_placements", _i32),
-                ("tile_pins", _i32), ("chunk", _i32), ("batch_sweep", _i32), ("reserved", _i32 * 1)]
+                ("tile_pins", _i32), ("chunk", _i32), ("batch_sweep", _i32), ("grid_blocks", _i32)]
 
 
 PROF_KINDS = ("positions", "net_rc", "forward", "endpoints", "required", "seed", "adjoint", "output")
@@ -50,6 +51,20 @@ SCHED_LEVELS = 1
 SCHED_BATCH = 2
 BATCH_LEVELS = 0
 BATCH_DATAFLOW = 1
+
+
+class StaServerOptions(ctypes.Structure):
+    _fields_ = [("slots", _i32), ("sequential", _i32), ("budget_bytes", ctypes.c_int64), ("reserved", _i32 * 4)]
+
+
+class StaServerRequest(ctypes.Structure):
+    _fields_ = [("netlist", _i32), ("gradient", _i32), ("gamma", ctypes.c_float), ("w_tns", ctypes.c_float),
+                ("w_wns", ctypes.c_float), ("xy", _p), ("grad", _p), ("summary", _p)]
+
+
+class StaServerCompletion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", _i32), ("netlist", _i32), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 class StaError(RuntimeError):
@@ -83,6 +98,16 @@ def _load() -> ctypes.CDLL:
         "sta_endpoint_summary_noalloc": ([_p, _p, _i32, _p, _p, _i32, ctypes.c_float, _p, _p, _p],
                                          ctypes.c_int),
         "sta_destroy": ([H], None),
+        "sta_server_create": ([ctypes.POINTER(StaServerOptions), ctypes.POINTER(H)], ctypes.c_int),
+        "sta_server_add_netlist": ([H, ctypes.POINTER(StaNetlistDesc), ctypes.POINTER(StaLibrary), _i32,
+                                    ctypes.POINTER(_i32)], ctypes.c_int),
+        "sta_server_submit": ([H, ctypes.POINTER(StaServerRequest), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "sta_server_poll": ([H, ctypes.POINTER(StaServerCompletion), _i32, ctypes.POINTER(_i32), _i32],
+                            ctypes.c_int),
+        "sta_server_stats": ([H, _p], ctypes.c_int),
+        "sta_server_netlist_bytes": ([H, _i32, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "sta_server_destroy": ([H], None),
+        "sta_server_clock": ([], ctypes.c_double),
         "sta_last_error": ([], ctypes.c_char_p),
         "sta_abi_version": ([], ctypes.c_int),
     }
@@ -99,7 +124,9 @@ _lib = _load()
 EXPORTS = ("sta_create", "sta_set_positions", "sta_forward", "sta_backward_grad",
            "sta_query_summary", "sta_query_pins", "sta_query_endpoints", "sta_levelize",
            "sta_query_sizes", "sta_query_profile", "sta_stream_wait", "sta_destroy",
-           "sta_synchronize", "sta_debug_expire_wait", "sta_autotune",
+           "sta_synchronize", "sta_debug_expire_wait", "sta_autotune", "sta_server_create",
+           "sta_server_add_netlist", "sta_server_submit", "sta_server_poll", "sta_server_stats",
+           "sta_server_destroy", "sta_server_clock", "sta_server_netlist_bytes",
            "sta_last_error", "sta_abi_version", "sta_endpoint_summary_noalloc")
 
 
@@ -170,13 +197,14 @@ def sta_levelize(nl):
 
 def sta_create(nl, lib, use_graphs: bool = True, profile: bool = False,
                schedule: int = SCHED_DATAFLOW, num_placements: int = 0, tile_pins: int = 0,
-               chunk: int = 0, batch_sweep: int = BATCH_LEVELS) -> int:
+               chunk: int = 0, batch_sweep: int = BATCH_LEVELS, grid_blocks: int = 0) -> int:
     keep = _Keep()
     d = netlist_desc(nl, keep)
     l = library_desc(lib, keep)
     opts = StaOptions(use_graphs=1 if use_graphs else 0, profile=1 if profile else 0,
                       schedule=int(schedule), num_placements=int(num_placements),
-                      tile_pins=int(tile_pins), chunk=int(chunk), batch_sweep=int(batch_sweep))
+                      tile_pins=int(tile_pins), chunk=int(chunk), batch_sweep=int(batch_sweep),
+                      grid_blocks=int(grid_blocks))
     h = ctypes.c_void_p()
     _check(_lib.sta_create(ctypes.byref(d), ctypes.byref(l), ctypes.byref(opts), ctypes.byref(h)),
            "sta_create")

@@ -11,6 +11,7 @@
 // soon as arrival times exist and a gradient sweep queued there overlaps the
 // required-time sweep on the GPU: the GB300 counterpart of the paper's
 // two-stream operation fusion (Section 3.2).
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -595,6 +596,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     if (opts) {
         h->use_graphs = opts->use_graphs != 0;
         h->profile = opts->profile != 0;
+        if (opts->grid_blocks < 0) return fail(set_err(STA_ERR_INVALID_ARG, "StaOptions.grid_blocks must be >= 0"));
         if (opts->schedule != STA_SCHED_DATAFLOW && opts->schedule != STA_SCHED_LEVELS &&
             opts->schedule != STA_SCHED_BATCH)
             return fail(set_err(STA_ERR_INVALID_ARG, "StaOptions.schedule must be DATAFLOW, LEVELS or BATCH"));
@@ -742,6 +744,10 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         const int bmax = bat ? batch_max_blocks(0) : dataflow_max_blocks(0);
         h->grid_fwd = fmax > 0 ? fmax : 1;
         h->grid_bwd = bat ? (bmax > 0 ? bmax : 1) : (bmax > 1 ? bmax / 2 : 1);
+        if (opts && opts->grid_blocks > 0) {
+            h->grid_fwd = std::min(h->grid_fwd, (int)opts->grid_blocks);
+            h->grid_bwd = std::min(h->grid_bwd, (int)opts->grid_blocks);
+        }
         if (cudaGetLastError() != cudaSuccess) return fail(set_err(STA_ERR_CUDA, "occupancy query failed"));
     }
     if (h->profile) {  // event pairs for every launch of each sequence, made before any capture
@@ -841,9 +847,13 @@ StaStatus sta_forward(StaHandle* h, uint32_t flags, float gamma, void* stream) {
     }
     CUDA_TRY(cudaEventRecord(h->ev_at, st));
     h->rat_pending = false;
-    if ((flags & STA_FWD_RAT) && h->schedule != STA_SCHED_LEVELS) {
+    if ((flags & STA_FWD_RAT) && h->schedule != STA_SCHED_LEVELS && !(flags & STA_FWD_RAT_EAGER)) {
         // deferred: carried by the next gradient sweep, or launched when queried
         h->rat_pending = true;
+        CUDA_TRY(cudaEventRecord(h->ev_fwd, st));
+    } else if ((flags & STA_FWD_RAT) && h->schedule != STA_SCHED_LEVELS) {
+        StaStatus s2 = launch_graph_or_direct(h, &h->gx_rat, &h->gx_rat_gamma, 1.f, 1, st);
+        if (s2 != STA_OK) return s2;
         CUDA_TRY(cudaEventRecord(h->ev_fwd, st));
     } else if (flags & STA_FWD_RAT) {
         CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_at, 0));
