@@ -224,6 +224,25 @@ StaStatus sta_autotune(StaHandle *h, const int32_t *tile_pins, int32_t n_tile, c
                        int32_t n_chunk, const int32_t *sweeps, int32_t n_sweep, int32_t reps, float gamma,
                        float *ms, int32_t *best);
 
+/* Net RC results (Eqs. 1-3) of the latest forward pass or RC ablation run, in
+ * the description's order: load [num_nets] (fF), wdelay and impulse
+ * [num_pins] (ps; 0 at pins that are not sinks).  Any output may be NULL.
+ * Host outputs; synchronizes the device.  Single-placement schedules only. */
+StaStatus sta_query_net_rc(StaHandle *h, float *load, float *wdelay, float *impulse);
+
+/* Ablation of the net-RC work decomposition (single-placement schedules, after
+ * sta_set_positions): runs the RC of every net `reps` times with one scheme and
+ * returns the mean time per run in *ms (may be NULL); the results are left for
+ * sta_query_net_rc.  STA_RC_PIN: the pin-based warp tasks of the other kernels
+ * (nets of <= 32 pins packed into warps, larger nets one block each, fixed-order
+ * sums).  STA_RC_CTE: the collaborative task engagement of Algorithm 2 (a
+ * block-wide task pool built by a Blelloch scan, a binary search per task,
+ * shared-memory atomics for the loads).  The analysis state is reset (call
+ * sta_forward again).  Synchronizes the device. */
+#define STA_RC_PIN 0
+#define STA_RC_CTE 1
+StaStatus sta_ablation_net_rc(StaHandle *h, int32_t scheme, int32_t reps, float *ms);
+
 /* Copy the STA_SUM_COUNT summary values (double) to out, a device pointer if
  * on_device != 0 (asynchronous), else host (synchronizes `stream`). */
 StaStatus sta_query_summary(StaHandle *h, double *out, int on_device, void *stream);

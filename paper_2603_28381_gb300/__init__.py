@@ -63,6 +63,7 @@ class StaEngine:
                                  self.B if self.batched else 0, tile_pins, chunk,
                                  {"levels": _sta.BATCH_LEVELS, "dataflow": _sta.BATCH_DATAFLOW}[batch_sweep])
         self.sizes = _sta.sta_query_sizes(self.h)
+        self.sizes["nets_desc"] = int(netlist.num_nets)
         self.gamma = None
 
     # -- lifetime --
@@ -139,6 +140,24 @@ class StaEngine:
         table = {(int(a), int(c), s): float(ms[i, j, k]) for i, a in enumerate(tile_pins)
                  for j, c in enumerate(chunks) for k, s in enumerate(sweeps)}
         return (best[0], best[1], inv[best[2]]), table
+
+    def net_rc(self) -> Dict[str, np.ndarray]:
+        """Net RC results (sta_query_net_rc): load [nets], wdelay / impulse [pins]."""
+        load = np.zeros(self.sizes["nets_desc"], np.float32)
+        wd = np.zeros(self.num_pins, np.float32)
+        im = np.zeros(self.num_pins, np.float32)
+        _sta._check(_sta._lib.sta_query_net_rc(self.h, load.ctypes.data if load.size else None,
+                                               wd.ctypes.data if wd.size else None,
+                                               im.ctypes.data if im.size else None), "sta_query_net_rc")
+        return {"load": load, "wdelay": wd, "impulse": im}
+
+    def ablation_net_rc(self, scheme: str = "cte", reps: int = 10) -> float:
+        """Mean ms of the net RC of every net in one scheme ("pin" or "cte")."""
+        import ctypes as _ct
+        ms = _ct.c_float()
+        _sta._check(_sta._lib.sta_ablation_net_rc(self.h, {"pin": 0, "cte": 1}[scheme], int(reps), _ct.byref(ms)),
+                    "sta_ablation_net_rc")
+        return float(ms.value)
 
     def _debug_expire_wait(self) -> None:
         """Test hook: the next forward runs one dependency wait into its budget

@@ -88,6 +88,8 @@ def _load() -> ctypes.CDLL:
         "sta_query_summary": ([H, _p, ctypes.c_int, _p], ctypes.c_int),
         "sta_stream_wait": ([H, _p], ctypes.c_int),
         "sta_synchronize": ([H], ctypes.c_int),
+        "sta_query_net_rc": ([H, _p, _p, _p], ctypes.c_int),
+        "sta_ablation_net_rc": ([H, _i32, _i32, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "sta_autotune": ([H, _p, _i32, _p, _i32, _p, _i32, _i32, ctypes.c_float, _p, _p], ctypes.c_int),
         "sta_debug_expire_wait": ([H], ctypes.c_int),
         "sta_query_pins": ([H, _p, _p, _p, _p, _p, ctypes.c_int, _p], ctypes.c_int),
@@ -126,7 +128,8 @@ EXPORTS = ("sta_create", "sta_set_positions", "sta_forward", "sta_backward_grad"
            "sta_query_sizes", "sta_query_profile", "sta_stream_wait", "sta_destroy",
            "sta_synchronize", "sta_debug_expire_wait", "sta_autotune", "sta_server_create",
            "sta_server_add_netlist", "sta_server_submit", "sta_server_poll", "sta_server_stats",
-           "sta_server_destroy", "sta_server_clock", "sta_server_netlist_bytes",
+           "sta_server_destroy", "sta_server_clock", "sta_server_netlist_bytes", "sta_query_net_rc",
+           "sta_ablation_net_rc",
            "sta_last_error", "sta_abi_version", "sta_endpoint_summary_noalloc")
 
 

@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libsta.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "dataflow.cu", "batch.cu", "capi.cu", "builder.cpp", "noalloc.cu", "serve.cu"]
+SOURCES = ["kernels.cu", "dataflow.cu", "batch.cu", "capi.cu", "builder.cpp", "noalloc.cu", "serve.cu", "cte.cu"]
 
 
 def _nvcc() -> str:

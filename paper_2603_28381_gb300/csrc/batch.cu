@@ -397,12 +397,28 @@ __global__ void __launch_bounds__(kBlock) k_bep1(DevNet g, BatchState bs, float 
     }
 }
 
-// thread per placement: the partials in block order
+// warp per placement: lane l merges partials l, l + 32, ... in order, then a
+// butterfly across the lanes (each merge is symmetric in its operands, so both
+// lanes of a pair hold the same bits and the result is fixed)
 __global__ void k_bep2(DevNet g, BatchState bs, float gamma, int lse, int nparts) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= bs.Bp) return;
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (b >= bs.Bp) return;  // warp-uniform
     BEp acc = bep_identity();
-    for (int k = 0; k < nparts; ++k) bep_merge(acc, reinterpret_cast<const BEp*>(bs.red)[ix(k, bs.Bp, b)], gamma);
+    for (int k = lane; k < nparts; k += 32) bep_merge(acc, reinterpret_cast<const BEp*>(bs.red)[ix(k, bs.Bp, b)], gamma);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        BEp o;
+        o.tns_e = __shfl_xor_sync(kFull, acc.tns_e, off);
+        o.tns_l = __shfl_xor_sync(kFull, acc.tns_l, off);
+        o.tns_g = __shfl_xor_sync(kFull, acc.tns_g, off);
+        o.viol = __shfl_xor_sync(kFull, acc.viol, off);
+        o.wns_e = __shfl_xor_sync(kFull, acc.wns_e, off);
+        o.wns_l = __shfl_xor_sync(kFull, acc.wns_l, off);
+        o.wmin = __shfl_xor_sync(kFull, acc.wmin, off);
+        o.wsum = __shfl_xor_sync(kFull, acc.wsum, off);
+        bep_merge(acc, o, gamma);
+    }
+    if (lane != 0) return;
     double* o = bs.summary + (size_t)b * STA_SUM_COUNT;
     o[STA_SUM_WNS_EARLY] = acc.wns_e;
     o[STA_SUM_TNS_EARLY] = acc.tns_e;
@@ -1047,7 +1063,7 @@ void launch_batch_bwd_level(const DevNet& g, const BatchState& bs, const DfState
 
 void launch_batch_endpoints(const DevNet& g, const BatchState& bs, float gamma, int lse, cudaStream_t st) {
     k_bep1<<<dim3(kRedBlocks, bs.G), kBlock, 0, st>>>(g, bs, gamma, lse);
-    k_bep2<<<(bs.Bp + 127) / 128, 128, 0, st>>>(g, bs, gamma, lse, kRedBlocks);
+    k_bep2<<<(bs.Bp * 32 + 127) / 128, 128, 0, st>>>(g, bs, gamma, lse, kRedBlocks);
 }
 
 void launch_batch_bwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int mode,

@@ -471,12 +471,14 @@ StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& 
     o.pin_orig.reserve(P);
     o.net_ptr.assign(V + 1, 0);
     o.net_drv.assign(V, -1);
+    o.net_orig.assign(V, -1);
     o.net_arc_ptr.assign(V + 1, 0);
     o.arc_pin.clear();
     std::vector<int32_t> net_cell(V, -1);
     for (int32_t i = 0; i < V; ++i) {
         const int32_t v = no.order[i];
         o.net_ptr[i] = (int32_t)o.pin_orig.size();
+        if (v < Nreal) o.net_orig[i] = v;
         if (v < Nreal) {
             const int32_t b = nl.net_ptr[v], e = nl.net_ptr[v + 1];
             o.pin_orig.push_back(nl.net_pins[b]);

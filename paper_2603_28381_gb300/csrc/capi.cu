@@ -1019,6 +1019,64 @@ StaStatus sta_autotune(StaHandle* h, const int32_t* tile_pins, int32_t n_tile, c
     return set_tasks(h, sh);
 }
 
+StaStatus sta_ablation_net_rc(StaHandle* h, int32_t scheme, int32_t reps, float* ms) {
+    if (!h || reps < 1 || (scheme != STA_RC_PIN && scheme != STA_RC_CTE))
+        return set_err(STA_ERR_INVALID_ARG, "sta_ablation_net_rc: scheme PIN or CTE, reps >= 1");
+    if (h->batch()) return set_err(STA_ERR_STATE, "sta_ablation_net_rc: single-placement schedules only");
+    if (!h->have_pos) return set_err(STA_ERR_STATE, "sta_ablation_net_rc: sta_set_positions first");
+    const Layout& L = h->lay;
+    cudaStream_t st = h->side;
+    CUDA_TRY(cudaDeviceSynchronize());
+    auto launch = [&] {
+        if (scheme == STA_RC_CTE) launch_rc_cte(h->g, h->s, 0, L.N, st);
+        else launch_rc(h->g, h->s, L.lvl_wtask[L.L], L.lvl_ctask[L.L], st);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    launch();  // warm-up
+    cudaEventRecord(e0, st);
+    for (int32_t r = 0; r < reps; ++r) launch();
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(STA_ERR_CUDA, std::string("sta_ablation_net_rc: ") + cudaGetErrorString(e));
+    if (ms) *ms = t / (float)reps;
+    h->have_fwd = h->have_lse = h->have_rat = false;  // the loads were rewritten: run sta_forward again
+    h->rat_pending = false;
+    return STA_OK;
+}
+
+StaStatus sta_query_net_rc(StaHandle* h, float* load, float* wdelay, float* impulse) {
+    if (!h) return set_err(STA_ERR_INVALID_ARG, "null handle");
+    if (h->batch()) return set_err(STA_ERR_STATE, "sta_query_net_rc: single-placement schedules only");
+    const Layout& L = h->lay;
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (load) {
+        std::vector<float> v(L.N);
+        if (L.N) CUDA_TRY(cudaMemcpy(v.data(), h->s.load, (size_t)L.N * 4, cudaMemcpyDeviceToHost));
+        for (int32_t i = 0; i < L.N; ++i)
+            if (L.net_orig[i] >= 0) load[L.net_orig[i]] = v[i];
+    }
+    if (wdelay || impulse) {
+        std::vector<float2> v(L.P);
+        if (L.P) CUDA_TRY(cudaMemcpy(v.data(), h->s.wdi, (size_t)L.P * 8, cudaMemcpyDeviceToHost));
+        std::vector<char> sink(L.P, 0);
+        for (int32_t n = 0; n < L.N; ++n)
+            for (int32_t p = L.net_ptr[n] + 1; p < L.net_ptr[n + 1]; ++p) sink[p] = 1;
+        for (int32_t p = 0; p < L.P; ++p) {
+            const int32_t o = L.pin_orig[p];
+            if (wdelay) wdelay[o] = sink[p] ? v[p].x : 0.f;
+            if (impulse) impulse[o] = sink[p] ? v[p].y : 0.f;
+        }
+    }
+    return STA_OK;
+}
+
 StaStatus sta_query_summary(StaHandle* h, double* out, int on_device, void* stream) {
     if (!h || !out) return set_err(STA_ERR_INVALID_ARG, "null argument");
     if (!h->have_fwd) return set_err(STA_ERR_STATE, "no forward pass yet");

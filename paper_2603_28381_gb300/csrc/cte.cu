@@ -6,8 +6,9 @@
 // with a work-efficient (Blelloch) exclusive scan, and the threads then stride
 // over the pool, each finding the net of its task by a binary search of the
 // scan (lower bound) before doing the per-sink work.  The per-net load sums
-// the sink terms with shared-memory atomics, so its rounding order is not
-// fixed (the pin-based kernels sum in a fixed order).
+// the sink terms of a warp's run of tasks with a shuffle scan and adds the run
+// with one shared-memory atomic, so its rounding order is not fixed (the
+// pin-based kernels sum in a fixed order).
 #include "device_common.cuh"
 
 namespace sta {
@@ -49,20 +50,38 @@ __global__ void __launch_bounds__(kCteNets) k_rc_cte(DevNet g, DevState s, int n
         }
         __syncthreads();
     }
-    for (int task = tid; task < total; task += kCteNets) {
-        // lower bound: the last net whose first task is <= task
-        int lo = 0, hi = kCteNets - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (scan[mid] <= task) lo = mid;
-            else hi = mid - 1;
+    // threads stride over the pool; a warp iterates while any of its lanes has a task
+    const int lane = tid & 31;
+    for (int k0 = tid - lane; k0 < total; k0 += kCteNets) {
+        const int task = k0 + lane;
+        const bool ok = task < total;
+        int lo = 0;
+        float v = 0.f;
+        if (ok) {
+            // lower bound: the last net whose first task is <= task
+            int hi = kCteNets - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (scan[mid] <= task) lo = mid;
+                else hi = mid - 1;
+            }
+            const int d = first_pin[lo];
+            const int p = d + 1 + (task - scan[lo]);
+            v = rc_sink(g, s, p, s.xy[p], s.xy[d], g.pin_cap[p]);
         }
-        const int d = first_pin[lo];
-        const int p = d + 1 + (task - scan[lo]);
-        const float2 xy = s.xy[p], xyd = s.xy[d];
-        const float cap = g.pin_cap[p];
-        const float v = rc_sink(g, s, p, xy, xyd, cap);
-        atomicAdd(&load[lo], v);
+        // tasks of a warp are consecutive, so lanes of one net form runs: sum each
+        // run with a segmented shuffle scan and add it with one atomic
+        const int key = ok ? lo : -1 - lane;
+        const int prev = __shfl_up_sync(kFull, key, 1);
+        const unsigned heads = __ballot_sync(kFull, lane == 0 || prev != key);
+        const int hd = 31 - __clz(heads & (kFull >> (31 - lane)));
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float u = __shfl_up_sync(kFull, v, off);
+            if (lane - off >= hd) v += u;
+        }
+        const int next = __shfl_down_sync(kFull, key, 1);
+        if (ok && (lane == 31 || next != key)) atomicAdd(&load[lo], v);
     }
     __syncthreads();
     if (has) s.load[n] = g.pin_cap[dp] + load[tid];

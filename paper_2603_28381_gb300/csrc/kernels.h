@@ -127,6 +127,9 @@ void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, i
 // largest co-resident grid of the dataflow kernels on the current device
 int dataflow_max_blocks(int fwd);
 
+// net RC in the CTE scheme of Algorithm 2 (ablation), nets [n0, n1)
+void launch_rc_cte(const DevNet& g, const DevState& s, int n0, int n1, cudaStream_t st);
+
 void launch_gather_xy(const DevNet& g, const DevState& s, const float2* xy_user, cudaStream_t st);
 void launch_rc(const DevNet& g, const DevState& s, int nw, int nc, cudaStream_t st);
 void launch_fwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0, int nc, float gamma,

@@ -55,6 +55,7 @@ struct Layout {
 
     std::vector<int32_t> net_ptr;      // [N+1] internal pin range
     std::vector<int32_t> net_drv;      // [N] cell type if cell-driven, -1 if asserted
+    std::vector<int32_t> net_orig;     // [N] description net id, -1 for a dangling cell output
     std::vector<int32_t> net_arc_ptr;  // [N+1]
     std::vector<int32_t> arc_pin;      // [A] internal input pin of each arc
     std::vector<int32_t> pin_orig;     // [P] original id of each internal pin
