@@ -510,6 +510,12 @@ StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& 
     }
     o.net_arc_ptr[V] = (int32_t)o.arc_pin.size();
     o.A = o.net_arc_ptr[V];
+    // pins the forward pass writes: every sink, and the driver of a cell-driven net
+    o.pin_keep.assign(P, 1);
+    for (int32_t i = 0; i < V; ++i) {
+        if (o.net_drv[i] >= 0) o.pin_keep[o.net_ptr[i]] = 0;
+        for (int32_t p = o.net_ptr[i] + 1; p < o.net_ptr[i + 1]; ++p) o.pin_keep[p] = 0;
+    }
 
     o.pin_cap.resize(P);
     for (int32_t i = 0; i < P; ++i) o.pin_cap[i] = nl.pin_cap[o.pin_orig[i]];

@@ -94,6 +94,7 @@ struct StaHandle {
     // task a requested wait expiry stalls (raised, original)
     int32_t* pinned = nullptr;
     bool expire_next = false;  // the next forward sweep runs one wait into its budget
+    int stall_task = -1;       // single-placement dataflow forward: the task whose wait never succeeds
     // staging for host inputs / outputs
     void* stage = nullptr;
     size_t stage_bytes = 0;
@@ -202,16 +203,16 @@ struct ProfScope {
 
 void enqueue_forward_dataflow(StaHandle* h, int lse, float gamma, cudaStream_t st) {
     const Layout& L = h->lay;
-    cudaMemsetAsync(h->d.fcnt, 0, sizeof(int32_t) * (L.TF ? L.TF : 1), st);
     cudaMemsetAsync(h->d.heads, 0, sizeof(int32_t), st);
     cudaMemsetAsync(h->d.abort_word, 0, sizeof(int32_t), st);
     {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
+        launch_fwd_reset(h->s, h->d, L.P, st);           // the words the sweep's tasks poll
         launch_rc(h->g, h->s, 0, L.lvl_ctask[L.L], st);  // load and wire RC of the nets > 32 pins
     }
     {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
-        launch_fwd_dataflow(h->g, h->s, h->d, h->grid_fwd, gamma, lse, st);
+        launch_fwd_dataflow(h->g, h->s, h->d, h->grid_fwd, gamma, lse, h->stall_task, st);
     }
     ProfScope ps(h, &h->prof_fwd, STA_PROF_ENDPOINTS, st);
     launch_endpoints(h->g, h->s, gamma, lse, st);
@@ -678,6 +679,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         d.btask = reinterpret_cast<const int4*>(cp);
         STEP(h->upload(d.baux, L.baux));
         STEP(h->upload(d.pin_cons, L.pin_cons));
+        STEP(h->upload(d.pin_keep, L.pin_keep));
         STEP(h->upload(d.f_indeg, L.f_indeg));
         STEP(h->upload(d.f_out_ptr, L.f_out_ptr));
         STEP(h->upload(d.f_out, L.f_out));
@@ -817,22 +819,31 @@ StaStatus sta_forward(StaHandle* h, uint32_t flags, float gamma, void* stream) {
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_bwd, 0));
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
     if (h->expire_next) {
-        // one forward task waits for one producer more than it has: its wait runs
+        // one forward task waits for a producer that never comes: its wait runs
         // into the budget, the sweep ends early and the expiry is reported
         h->expire_next = false;
         const Layout& L = h->lay;
-        int task = -1;
-        for (int t = L.TF - 1; t >= 0 && task < 0; --t)
-            if (L.f_indeg[t] > 0) task = t;
-        if (task < 0) return set_err(STA_ERR_STATE, "no forward task has producers");
-        int32_t* indeg = const_cast<int32_t*>(h->d.f_indeg) + task;
-        h->pinned[1] = L.f_indeg[task] + 1;
-        h->pinned[2] = L.f_indeg[task];
-        CUDA_TRY(cudaMemcpyAsync(indeg, h->pinned + 1, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        enqueue_forward(h, lse, gamma, st);
-        StaStatus s2 = check_launch();
-        if (s2 != STA_OK) return s2;
-        CUDA_TRY(cudaMemcpyAsync(indeg, h->pinned + 2, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        if (h->schedule == STA_SCHED_DATAFLOW) {  // the sweep polls data words: stall its last task
+            if (L.TF == 0) return set_err(STA_ERR_STATE, "no forward task");
+            h->stall_task = L.TF - 1;
+            enqueue_forward(h, lse, gamma, st);
+            h->stall_task = -1;
+            StaStatus s2 = check_launch();
+            if (s2 != STA_OK) return s2;
+        } else {  // dependency counters: one producer more than the task has
+            int task = -1;
+            for (int t = L.TF - 1; t >= 0 && task < 0; --t)
+                if (L.f_indeg[t] > 0) task = t;
+            if (task < 0) return set_err(STA_ERR_STATE, "no forward task has producers");
+            int32_t* indeg = const_cast<int32_t*>(h->d.f_indeg) + task;
+            h->pinned[1] = L.f_indeg[task] + 1;
+            h->pinned[2] = L.f_indeg[task];
+            CUDA_TRY(cudaMemcpyAsync(indeg, h->pinned + 1, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            enqueue_forward(h, lse, gamma, st);
+            StaStatus s2 = check_launch();
+            if (s2 != STA_OK) return s2;
+            CUDA_TRY(cudaMemcpyAsync(indeg, h->pinned + 2, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        }
     } else if (h->use_graphs) {
         if (!h->gx_fwd[lse] || h->gx_fwd_gamma[lse] != gamma) {
             StaStatus s2 = capture(h, &h->gx_fwd[lse], [&](cudaStream_t c) { enqueue_forward(h, lse, gamma, c); });

@@ -39,6 +39,7 @@ struct FwdPre {
     int a0, na;
     int pin[STA_MAX_ARCS];
     int rfi;  // bit k: input transition of arc k
+    int dyn;  // bit k: arc k's input pin is written during the sweep (not asserted)
     int jl;   // load segment and fraction
     float ul;
     float sidx[6], sinv[6];  // slew index points 0..5 of the type and 1/width of each segment
@@ -58,10 +59,10 @@ __device__ __forceinline__ void slew_seg(const float* sidx, const float* sinv, f
     ts = (v - base) * inv;
 }
 
-__device__ __forceinline__ FwdPre fwd_pre(const DevNet& g, int n, int c, float ld) {
+__device__ __forceinline__ FwdPre fwd_pre(const DevNet& g, const DfState& d, int n, int c, float ld) {
     FwdPre f;
     f.t = g.net_drv[n];
-    f.a0 = f.na = f.rfi = f.jl = 0;
+    f.a0 = f.na = f.rfi = f.jl = f.dyn = 0;
     f.ul = 0.f;
 #pragma unroll
     for (int k = 0; k < STA_MAX_ARCS; ++k) f.pin[k] = 0;
@@ -81,6 +82,7 @@ __device__ __forceinline__ FwdPre fwd_pre(const DevNet& g, int n, int c, float l
         if (k < f.na) {
             f.pin[k] = g.arc_pin[f.a0 + k];
             f.rfi |= (rf ^ ((un >> k) & 1)) << k;
+            f.dyn |= (d.arc_prod[f.a0 + k] >= 0 ? 1 : 0) << k;
         }
     const float* li = g.lib_idx + f.t * kLibStride + 8;
     f.jl = axis_seg(li, ld);
@@ -94,21 +96,84 @@ __device__ __forceinline__ FwdPre fwd_pre(const DevNet& g, int n, int c, float l
 // arcs and asserted drivers read a harmless valid address) and results are
 // selected, so a warp never splits into groups whose memory round trips would
 // run one after another.  `dp` must be a valid pin.
+__device__ __forceinline__ float ld_relaxed_f(const float* p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool written(float v) { return __float_as_uint(v) != kUnwritten; }
+
+// The wait of a forward task: the fanin arrival / slew / LSE arrival words this
+// lane reads, polled (strong relaxed loads, all lanes together) until every one
+// that is written during the sweep holds its value; a word is written once per
+// sweep and reset to kUnwritten before it, so no counter or release fence is
+// needed.  Returns the values.  Bounded like wait_ready: after kWaitBudgetNs or
+// once any wait of the launch has expired it sets the abort word and returns.
+// `stall` makes the wait never succeed (test hook for the bounded wait).
+template <bool lse>
+__device__ __forceinline__ void fwd_fanin(const DevState& s, const FwdPre& f, int dp, int c, float* ain, float* sin,
+                                          float* zin, bool stall, int32_t* abort_word) {
+    const int el = c >> 1;
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        bool ok = !stall;
+#pragma unroll
+        for (int k = 0; k < STA_MAX_ARCS; ++k) {
+            const int pin = k < f.na ? f.pin[k] : dp;
+            const int r = (f.rfi >> k) & 1;
+            const int q = 4 * pin + 2 * el + r;
+            sin[k] = ld_relaxed_f(s.slew + q);
+            ain[k] = ld_relaxed_f(s.at + q);
+            zin[k] = lse ? ld_relaxed_f(s.ats + 2 * pin + r) : 0.f;
+            const bool need = k < f.na && ((f.dyn >> k) & 1);
+            ok = ok && (!need || (written(sin[k]) && written(ain[k]) && (!lse || !el || written(zin[k]))));
+        }
+        if (__all_sync(kFull, ok)) return;
+        __nanosleep(64);
+        if ((it & 63) == 63) {
+            if (__any_sync(kFull, ld_relaxed(abort_word) != 0)) return;
+            const unsigned long long now = __shfl_sync(kFull, global_ns(), 0);
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kWaitBudgetNs) {
+                if ((threadIdx.x & 31) == 0) {
+                    atomicExch(abort_word, 1);
+                    atomicExch(abort_word + 1, 1);
+                }
+                __syncwarp();
+                return;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void st_relaxed_f4(float* p, float4 v) {
+    asm volatile("st.relaxed.gpu.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_f2(float* p, float2 v) {
+    asm volatile("st.relaxed.gpu.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// a sink's arrival / slew / LSE arrival, the words its consumers poll
+__device__ __forceinline__ void store_sink_polled(const DevState& s, int p, const float* A, const float* S, float z0,
+                                                  float z1, float2 wdi, bool lse) {
+    const float i2 = wdi.y * wdi.y;
+    st_relaxed_f4(s.at + 4 * p, make_float4(A[0] + wdi.x, A[1] + wdi.x, A[2] + wdi.x, A[3] + wdi.x));
+    st_relaxed_f4(s.slew + 4 * p, make_float4(sqrtf(fmaf(S[0], S[0], i2)), sqrtf(fmaf(S[1], S[1], i2)),
+                                              sqrtf(fmaf(S[2], S[2], i2)), sqrtf(fmaf(S[3], S[3], i2))));
+    if (lse) st_relaxed_f2(s.ats + 2 * p, make_float2(z0 + wdi.x, z1 + wdi.x));
+}
+
 __device__ __forceinline__ DrvOut fwd_eval(const DevNet& g, const DevState& s, const FwdPre& f, int dp, int c,
-                                           float gamma, bool lse, bool write_adel) {
+                                           float gamma, bool lse, bool write_adel, const float* ain,
+                                           const float* sin, const float* zin) {
     const int el = c >> 1, rf = c & 1;
     const bool cell = f.t >= 0;
     const int ty = cell ? f.t : 0;
-    float sin[STA_MAX_ARCS], ain[STA_MAX_ARCS], zin[STA_MAX_ARCS];
-#pragma unroll
-    for (int k = 0; k < STA_MAX_ARCS; ++k) {
-        const int pin = k < f.na ? f.pin[k] : dp;
-        const int r = (f.rfi >> k) & 1;
-        const int q = 4 * pin + 2 * el + r;
-        sin[k] = __ldcg(s.slew + q);
-        ain[k] = __ldcg(s.at + q);
-        zin[k] = __ldcg(s.ats + 2 * pin + r);
-    }
     // asserted driver: its constant values (set at creation)
     const float at_c = __ldcg(s.at + 4 * dp + c), sl_c = __ldcg(s.slew + 4 * dp + c);
     const float ats_c = __ldcg(s.ats + 2 * dp + rf);
@@ -153,7 +218,7 @@ __device__ __forceinline__ DrvOut fwd_eval(const DevNet& g, const DevState& s, c
 // and the wire step to every sink.
 template <bool lse>
 __device__ void fwd_df_warp(const DevNet& g, const DevState& s, const DfState& d, int t, int n0, int nn,
-                            float gamma) {
+                            float gamma, int stall_task) {
     const WarpGeom w = warp_geom(g, n0, nn);
     const int p = w.pin0 + w.lane;
     const bool sink = w.valid && w.lane != w.hd;
@@ -183,16 +248,17 @@ __device__ void fwd_df_warp(const DevNet& g, const DevState& s, const DfState& d
     const int hj = __shfl_sync(kFull, w.h, j1);
     const int lastj = __shfl_sync(kFull, w.h, j1 + 1) - 1;
     const float ldj = __shfl_sync(kFull, v, lastj & 31);
-    FwdPre f = fwd_pre(g, n0 + min(j1, nn - 1), c, ldj);
+    FwdPre f = fwd_pre(g, d, n0 + min(j1, nn - 1), c, ldj);
     if (j1 >= nn) {  // idle lanes evaluate a dummy: no arcs, results unused
         f.t = -1;
         f.na = 0;
     }
     const int dp = w.pin0 + (j1 < nn ? hj : 0);
 
-    wait_ready(d.fcnt, t, d.f_indeg[t], d.abort_word);
+    float ain[STA_MAX_ARCS], sin[STA_MAX_ARCS], zin[STA_MAX_ARCS];
+    fwd_fanin<lse>(s, f, dp, c, ain, sin, zin, t == stall_task, d.abort_word);
 
-    const DrvOut o = fwd_eval(g, s, f, dp, c, gamma, lse, true);
+    const DrvOut o = fwd_eval(g, s, f, dp, c, gamma, lse, true, ain, sin, zin);
     if (j1 < nn && f.t >= 0) {
         s.at[4 * dp + c] = o.at;
         s.slew[4 * dp + c] = o.slew;
@@ -206,25 +272,18 @@ __device__ void fwd_df_warp(const DevNet& g, const DevState& s, const DfState& d
         S[k] = __shfl_sync(kFull, o.slew, src + k);
     }
     const float z0 = __shfl_sync(kFull, o.ats, src + 2), z1 = __shfl_sync(kFull, o.ats, src + 3);
-    if (sink) {
-        const float i2 = wdi.y * wdi.y;
-        reinterpret_cast<float4*>(s.at)[p] = make_float4(A[0] + wdi.x, A[1] + wdi.x, A[2] + wdi.x, A[3] + wdi.x);
-        reinterpret_cast<float4*>(s.slew)[p] =
-            make_float4(sqrtf(fmaf(S[0], S[0], i2)), sqrtf(fmaf(S[1], S[1], i2)), sqrtf(fmaf(S[2], S[2], i2)),
-                        sqrtf(fmaf(S[3], S[3], i2)));
-        if (lse) reinterpret_cast<float2*>(s.ats)[p] = make_float2(z0 + wdi.x, z1 + wdi.x);
-    }
+    if (sink) store_sink_polled(s, p, A, S, z0, z1, wdi, lse);
 }
 
 // A 32-sink chunk of a large net: the net's load and wire RC come from the
 // prologue kernel; lanes 0-3 evaluate the driver (the first chunk also stores it).
 template <bool lse>
 __device__ void fwd_df_chunk(const DevNet& g, const DevState& s, const DfState& d, int t, int n, int p0, int cnt,
-                             float gamma) {
+                             float gamma, int stall_task) {
     const int lane = threadIdx.x & 31;
     const int dp = g.net_ptr[n];
     const bool first = p0 == dp + 1;
-    FwdPre f = fwd_pre(g, n, lane & 3, s.load[n]);
+    FwdPre f = fwd_pre(g, d, n, lane & 3, s.load[n]);
     if (lane >= 4) {  // lanes 4-31 evaluate a dummy: no arcs, results unused
         f.t = -1;
         f.na = 0;
@@ -232,9 +291,10 @@ __device__ void fwd_df_chunk(const DevNet& g, const DevState& s, const DfState& 
     float2 wdi = make_float2(0.f, 0.f);
     if (lane < cnt) wdi = s.wdi[p0 + lane];
 
-    wait_ready(d.fcnt, t, d.f_indeg[t], d.abort_word);
+    float ain[STA_MAX_ARCS], sin[STA_MAX_ARCS], zin[STA_MAX_ARCS];
+    fwd_fanin<lse>(s, f, dp, lane & 3, ain, sin, zin, t == stall_task, d.abort_word);
 
-    const DrvOut o = fwd_eval(g, s, f, dp, lane & 3, gamma, lse, first && lane < 4);
+    const DrvOut o = fwd_eval(g, s, f, dp, lane & 3, gamma, lse, first && lane < 4, ain, sin, zin);
     if (lane < 4 && first && f.t >= 0) {
         s.at[4 * dp + lane] = o.at;
         s.slew[4 * dp + lane] = o.slew;
@@ -247,27 +307,30 @@ __device__ void fwd_df_chunk(const DevNet& g, const DevState& s, const DfState& 
         S[k] = __shfl_sync(kFull, o.slew, k);
     }
     const float z0 = __shfl_sync(kFull, o.ats, 2), z1 = __shfl_sync(kFull, o.ats, 3);
-    if (lane < cnt) {
-        const int q = p0 + lane;
-        const float i2 = wdi.y * wdi.y;
-        reinterpret_cast<float4*>(s.at)[q] = make_float4(A[0] + wdi.x, A[1] + wdi.x, A[2] + wdi.x, A[3] + wdi.x);
-        reinterpret_cast<float4*>(s.slew)[q] =
-            make_float4(sqrtf(fmaf(S[0], S[0], i2)), sqrtf(fmaf(S[1], S[1], i2)), sqrtf(fmaf(S[2], S[2], i2)),
-                        sqrtf(fmaf(S[3], S[3], i2)));
-        if (lse) reinterpret_cast<float2*>(s.ats)[q] = make_float2(z0 + wdi.x, z1 + wdi.x);
-    }
+    if (lane < cnt) store_sink_polled(s, p0 + lane, A, S, z0, z1, wdi, lse);
 }
 
 template <bool lse>
-__global__ void __launch_bounds__(kBlock) k_fwd_df(DevNet g, DevState s, DfState d, float gamma) {
+__global__ void __launch_bounds__(kBlock) k_fwd_df(DevNet g, DevState s, DfState d, float gamma, int stall_task) {
     int t = grab(d.heads + 0);
     while (t < d.TF) {
         const int next = grab(d.heads + 0);
         const int4 task = d.ftask[t];
-        if (task.y > 0) fwd_df_warp<lse>(g, s, d, t, task.x, task.y, gamma);
-        else fwd_df_chunk<lse>(g, s, d, t, task.x, task.z, task.w, gamma);
-        signal_consumers(d.fcnt, d.f_out_ptr, d.f_out, t);
+        if (task.y > 0) fwd_df_warp<lse>(g, s, d, t, task.x, task.y, gamma, stall_task);
+        else fwd_df_chunk<lse>(g, s, d, t, task.x, task.z, task.w, gamma, stall_task);
         t = next;
+    }
+}
+
+// Before a forward sweep: every arrival / slew / LSE-arrival word the sweep
+// writes is set to kUnwritten (asserted pins keep their constants).
+__global__ void __launch_bounds__(kBlock) k_fwd_reset(DevState s, const uint8_t* __restrict__ keep, int P) {
+    const float u = __uint_as_float(kUnwritten);
+    for (int p = blockIdx.x * kBlock + threadIdx.x; p < P; p += gridDim.x * kBlock) {
+        if (keep[p]) continue;
+        reinterpret_cast<float4*>(s.at)[p] = make_float4(u, u, u, u);
+        reinterpret_cast<float4*>(s.slew)[p] = make_float4(u, u, u, u);
+        reinterpret_cast<float2*>(s.ats)[p] = make_float2(u, u);
     }
 }
 
@@ -746,10 +809,17 @@ int dataflow_max_blocks(int fwd) {
 }
 
 void launch_fwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int lse,
-                         cudaStream_t st) {
+                         int stall_task, cudaStream_t st) {
     if (d.TF == 0) return;
-    if (lse) launch_coop(k_fwd_df<true>, grid, kBlock, st, g, s, d, gamma);
-    else launch_coop(k_fwd_df<false>, grid, kBlock, st, g, s, d, gamma);
+    if (lse) launch_coop(k_fwd_df<true>, grid, kBlock, st, g, s, d, gamma, stall_task);
+    else launch_coop(k_fwd_df<false>, grid, kBlock, st, g, s, d, gamma, stall_task);
+}
+
+void launch_fwd_reset(const DevState& s, const DfState& d, int P, cudaStream_t st) {
+    if (P == 0) return;
+    int blocks = (P + kBlock - 1) / kBlock;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_fwd_reset<<<blocks, kBlock, 0, st>>>(s, d.pin_keep, P);
 }
 
 void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int mode,

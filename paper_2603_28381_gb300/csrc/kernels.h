@@ -68,6 +68,7 @@ struct DfState {
     float* apart;            // [npart * kPartFloats] partials, adjoint sweep
     float* net_gload;        // [N] d loss / d load of large nets
     int32_t* abort_word;     // [2] [0] a bounded wait of the current sweep expired, [1] sticky copy
+    const uint8_t* pin_keep; // [P] 1: the forward sweep does not write the pin (asserted values)
     int32_t TF, TB;
 };
 
@@ -120,8 +121,11 @@ void launch_batch_ep_out(const BatchState& bs, int E, float2* out, cudaStream_t 
 void launch_batch_broadcast(float* dst, const float* src, long long rows, int Bp, cudaStream_t st);
 void launch_batch_init_ats(const BatchState& bs, int P, cudaStream_t st);
 
+// stall_task >= 0: that task's wait never succeeds (test hook for the bounded wait)
 void launch_fwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int lse,
-                         cudaStream_t st);
+                         int stall_task, cudaStream_t st);
+// marks every word the dataflow forward sweep writes as not yet written (kUnwritten)
+void launch_fwd_reset(const DevState& s, const DfState& d, int P, cudaStream_t st);
 void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int mode,
                          cudaStream_t st);
 // largest co-resident grid of the dataflow kernels on the current device

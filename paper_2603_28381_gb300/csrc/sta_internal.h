@@ -29,6 +29,7 @@ constexpr int kTabPerArcRf = 2 * STA_LUT * STA_LUT;  // delay table then slew ta
 constexpr int kRedBlocks = 152;     // endpoint reduction partials (one per SM)
 constexpr float kKrc = 1e-3f;       // Ohm * fF in ps
 constexpr int kPartFloats = 12;     // floats per backward partial (large nets)
+constexpr uint32_t kUnwritten = 0x7fbadbadu;  // a NaN: "not written yet in this sweep"
 
 // Granularity of the dataflow tasks: nets of at most `big` pins are packed
 // (consecutive nets of a level while their pins fit in pack_pins, at most
@@ -83,6 +84,7 @@ struct Layout {
     std::vector<int32_t> btask;      // [4*TB]
     std::vector<int32_t> baux;       // [TB]
     std::vector<int32_t> pin_cons;   // [P] backward task whose arc step writes the pin's RAT / adjoint
+    std::vector<uint8_t> pin_keep;   // [P] 1 if no forward task writes the pin (asserted drivers, clock pins)
     // dependency counts and consumer lists: a task may start once `indeg` of its
     // producers have published; a producer signals every task of its out list
     std::vector<int32_t> f_indeg, f_out_ptr, f_out;  // forward: [TF], [TF+1], [..]
