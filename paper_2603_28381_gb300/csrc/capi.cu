@@ -225,6 +225,7 @@ void enqueue_backward_dataflow(StaHandle* h, int mode, float gamma, cudaStream_t
     cudaMemsetAsync((mode & 2) ? h->d.acnt : h->d.rcnt, 0, sizeof(int32_t) * (L.TB ? L.TB : 1), st);
     cudaMemsetAsync(h->d.heads + ((mode & 2) ? 2 : 1), 0, sizeof(int32_t), st);
     ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJOINT : STA_PROF_REQUIRED, st);
+    launch_bwd_reset(h->s, h->d, L.P, mode, st);  // the words the sweep's tasks poll
     launch_bwd_dataflow(h->g, h->s, h->d, h->grid_bwd, gamma, mode, st);
 }
 
@@ -539,6 +540,7 @@ StaStatus set_tasks(StaHandle* h, const TaskShape& sh) {
     h->nbig = (int)L.big_nets.size();
     d.TF = L.TF;
     d.TB = L.TB;
+    d.npart = L.npart;
     h->drop_graphs();
     h->have_fwd = h->have_lse = h->have_rat = false;
     h->rat_pending = false;
@@ -698,6 +700,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     STEP(h->alloc(d.abort_word, 2));
     d.TF = L.TF;
     d.TB = L.TB;
+    d.npart = L.npart;
     if (bat) {
         STEP(init_batch(h));
     } else {

@@ -154,6 +154,10 @@ __device__ __forceinline__ void st_relaxed_f4(float* p, float4 v) {
                  : "memory");
 }
 
+__device__ __forceinline__ void st_relaxed_f(float* p, float v) {
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
 __device__ __forceinline__ void st_relaxed_f2(float* p, float2 v) {
     asm volatile("st.relaxed.gpu.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
 }
@@ -322,6 +326,22 @@ __global__ void __launch_bounds__(kBlock) k_fwd_df(DevNet g, DevState s, DfState
     }
 }
 
+// Before a backward sweep: the required-time (mode 1) and adjoint (mode 2)
+// words of every cell-input pin, which the sweep writes once, are set to kUnwritten.
+__global__ void __launch_bounds__(kBlock) k_bwd_reset(DevState s, const int32_t* __restrict__ pin_cons, int P,
+                                                      int mode, float* part, int npart_words) {
+    const float u = __uint_as_float(kUnwritten);
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < npart_words; i += gridDim.x * kBlock) part[i] = u;
+    for (int p = blockIdx.x * kBlock + threadIdx.x; p < P; p += gridDim.x * kBlock) {
+        if (pin_cons[p] < 0) continue;
+        if (mode & 1) reinterpret_cast<float4*>(s.rat)[p] = make_float4(u, u, u, u);
+        if (mode & 2) {
+            reinterpret_cast<float2*>(s.g_ats)[p] = make_float2(u, u);
+            reinterpret_cast<float2*>(s.g_slew)[p] = make_float2(u, u);
+        }
+    }
+}
+
 // Before a forward sweep: every arrival / slew / LSE-arrival word the sweep
 // writes is set to kUnwritten (asserted pins keep their constants).
 __global__ void __launch_bounds__(kBlock) k_fwd_reset(DevState s, const uint8_t* __restrict__ keep, int P) {
@@ -379,21 +399,78 @@ __device__ __forceinline__ SinkPre sink_pre(const DevState& s, const DfState& d,
     return q;
 }
 
-// After the wait: the sink's terms of the backward reductions (see sink_bwd).
-// Branch-free across lanes: every lane loads (pin p must be valid) and selects.
-__device__ __forceinline__ SinkBwd sink_post(const DevState& s, int p, const SinkPre& q, float2 sld, int mode) {
+// The words a cell-input sink's backward terms read: its required times and
+// adjoints, written by the task of the cell it feeds.
+struct SinkWords {
+    float4 rat;
+    float2 ga, gs;
+};
+
+__device__ __forceinline__ float4 ld_relaxed_f4(const float* p) {
+    float4 v;
+    asm volatile("ld.relaxed.gpu.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p)
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ float2 ld_relaxed_f2(const float* p) {
+    float2 v;
+    asm volatile("ld.relaxed.gpu.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p) : "memory");
+    return v;
+}
+
+// The wait of a backward task over its sinks: every lane whose sink is a cell
+// input (`need`) polls that sink's words (strong relaxed loads, the warp
+// together) until all of them hold this sweep's values; the words are reset to
+// kUnwritten before the sweep and written once.  Bounded like wait_ready.
+template <int mode>
+__device__ __forceinline__ SinkWords sink_wait(const DevState& s, int p, bool need, int32_t* abort_word) {
+    SinkWords w;
+    w.rat = make_float4(0.f, 0.f, 0.f, 0.f);
+    w.ga = w.gs = make_float2(0.f, 0.f);
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        bool ok = true;
+        if (mode & 1) {
+            w.rat = ld_relaxed_f4(s.rat + 4 * p);
+            ok = ok && written(w.rat.x) && written(w.rat.y) && written(w.rat.z) && written(w.rat.w);
+        }
+        if (mode & 2) {
+            w.ga = ld_relaxed_f2(s.g_ats + 2 * p);
+            w.gs = ld_relaxed_f2(s.g_slew + 2 * p);
+            ok = ok && written(w.ga.x) && written(w.ga.y) && written(w.gs.x) && written(w.gs.y);
+        }
+        if (__all_sync(kFull, ok || !need)) return w;
+        __nanosleep(64);
+        if ((it & 63) == 63) {
+            if (__any_sync(kFull, ld_relaxed(abort_word) != 0)) return w;
+            const unsigned long long now = __shfl_sync(kFull, global_ns(), 0);
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kWaitBudgetNs) {
+                if ((threadIdx.x & 31) == 0) {
+                    atomicExch(abort_word, 1);
+                    atomicExch(abort_word + 1, 1);
+                }
+                __syncwarp();
+                return w;
+            }
+        }
+    }
+}
+
+// After the wait: the sink's terms of the backward reductions (see sink_bwd),
+// from the polled words of a cell-input sink or the constants of another sink.
+__device__ __forceinline__ SinkBwd sink_post(const SinkWords& wd, const SinkPre& q, float2 sld, int mode) {
     const bool dyn = q.cons >= 0;
     float4 rat = q.rat;
     float2 ga = q.ga, gs = make_float2(0.f, 0.f);
-    if (mode & 1) {
-        const float4 r = __ldcg(reinterpret_cast<const float4*>(s.rat) + p);
-        rat = dyn ? r : q.rat;
-    }
+    if (mode & 1) rat = dyn ? wd.rat : q.rat;
     if (mode & 2) {
-        const float2 a = __ldcg(reinterpret_cast<const float2*>(s.g_ats) + p);
-        const float2 b = __ldcg(reinterpret_cast<const float2*>(s.g_slew) + p);
-        ga = dyn ? a : q.ga;
-        gs = dyn ? b : make_float2(0.f, 0.f);
+        ga = dyn ? wd.ga : q.ga;
+        gs = dyn ? wd.gs : make_float2(0.f, 0.f);
     }
     SinkBwd b;
     if (mode & 1) {
@@ -544,9 +621,9 @@ __device__ __forceinline__ float bwd_apply(const DevState& s, const BwdPre& b, i
         const float rv = R - b.adel[k];
         const float gD = GA * b.w[k];
         const float gsv = fmaf(gD, b.dDs[k], k == b.amax ? GS * b.dSs : 0.f);
-        if ((mode & 1) && use) s.rat[qr] = rv;
-        if (adj && use) s.g_ats[qa] = gD;
-        if (adj && use) s.g_slew[qa] = gsv;
+        if ((mode & 1) && use) st_relaxed_f(s.rat + qr, rv);  // words the sink's own task polls
+        if (adj && use) st_relaxed_f(s.g_ats + qa, gD);
+        if (adj && use) st_relaxed_f(s.g_slew + qa, gsv);
         gl = (adj && use) ? fmaf(gD, b.dDl[k], gl) : gl;
     }
     return (adj && b.amax >= 0) ? fmaf(GS, b.dSl, gl) : gl;
@@ -580,9 +657,8 @@ __device__ void bwd_df_warp(const DevNet& g, const DevState& s, const DfState& d
         orig = g.pin_orig[pl];
     }
 
-    wait_ready(cnt, t, d.b_indeg[t], d.abort_word);
-
-    const SinkBwd b = sink_pick(sink, sink_post(s, pl, q, sld, mode), sink_none());
+    const SinkWords wd = sink_wait<mode>(s, pl, sink && q.cons >= 0, d.abort_word);
+    const SinkBwd b = sink_pick(sink, sink_post(wd, q, sld, mode), sink_none());
     float r0 = b.r[0], r1 = b.r[1], r2 = b.r[2], r3 = b.r[3];
     float ga0 = b.ga[0], ga1 = b.ga[1], gs0 = b.gs[0], gs1 = b.gs[1];
     // segmented inclusive scans; updates are selects, not branches, so the
@@ -677,9 +753,8 @@ __device__ void bwd_df_part(const DevNet& g, const DevState& s, const DfState& d
         }
     }
 
-    wait_ready(cnt_arr, t, d.b_indeg[t], d.abort_word);
-
-    const SinkBwd b = sink_pick(lane < cnt, sink_post(s, p, q, sld, mode), sink_none());
+    const SinkWords wd = sink_wait<mode>(s, p, lane < cnt && q.cons >= 0, d.abort_word);
+    const SinkBwd b = sink_pick(lane < cnt, sink_post(wd, q, sld, mode), sink_none());
     float v[kPartFloats];
 #pragma unroll
     for (int k = 0; k < 4; ++k) v[k] = b.r[k];
@@ -703,7 +778,7 @@ __device__ void bwd_df_part(const DevNet& g, const DevState& s, const DfState& d
 #pragma unroll
         for (int k = 1; k < kPartFloats; ++k)
             if (lane == k) out = v[k];
-        part[lane] = out;
+        st_relaxed_f(part + lane, out);  // the driver step polls these words
     }
 }
 
@@ -716,7 +791,36 @@ __device__ void bwd_df_driver(const DevNet& g, const DevState& s, const DfState&
     const int dp = g.net_ptr[n];
     const BwdPre bp = lane < 4 ? bwd_pre(g, s, n, dp, lane, gamma, mode) : bwd_none();
 
-    wait_ready(cnt, t, d.b_indeg[t], d.abort_word);
+    // the wait: poll the chunks' partial words (reset to kUnwritten before the
+    // sweep, written once by the partial tasks) until all are written; bounded
+    // like wait_ready
+    {
+        unsigned long long t0 = 0;
+        for (unsigned it = 0;; ++it) {
+            bool ok = true;
+            for (int k = lane; k < nch; k += 32) {
+                const float* q = part + (size_t)(slot0 + k) * kPartFloats;
+#pragma unroll
+                for (int j = 0; j < kPartFloats; ++j) ok &= written(ld_relaxed_f(q + j));
+            }
+            if (__all_sync(kFull, ok)) break;
+            __nanosleep(64);
+            if ((it & 63) == 63) {
+                if (__any_sync(kFull, ld_relaxed(d.abort_word) != 0)) break;
+                const unsigned long long now = __shfl_sync(kFull, global_ns(), 0);
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > kWaitBudgetNs) {
+                    if (lane == 0) {
+                        atomicExch(d.abort_word, 1);
+                        atomicExch(d.abort_word + 1, 1);
+                    }
+                    __syncwarp();
+                    break;
+                }
+            }
+        }
+    }
 
     float v[kPartFloats];
     v[0] = v[1] = -kInf;
@@ -725,12 +829,12 @@ __device__ void bwd_df_driver(const DevNet& g, const DevState& s, const DfState&
     for (int k = 4; k < kPartFloats; ++k) v[k] = 0.f;
     for (int k = lane; k < nch; k += 32) {
         const float* q = part + (size_t)(slot0 + k) * kPartFloats;
-        v[0] = fmaxf(v[0], __ldcg(q + 0));
-        v[1] = fmaxf(v[1], __ldcg(q + 1));
-        v[2] = fminf(v[2], __ldcg(q + 2));
-        v[3] = fminf(v[3], __ldcg(q + 3));
+        v[0] = fmaxf(v[0], ld_relaxed_f(q + 0));
+        v[1] = fmaxf(v[1], ld_relaxed_f(q + 1));
+        v[2] = fminf(v[2], ld_relaxed_f(q + 2));
+        v[3] = fminf(v[3], ld_relaxed_f(q + 3));
 #pragma unroll
-        for (int j = 4; j < kPartFloats; ++j) v[j] += __ldcg(q + j);
+        for (int j = 4; j < kPartFloats; ++j) v[j] += ld_relaxed_f(q + j);
     }
     v[0] = warp_max(v[0]);
     v[1] = warp_max(v[1]);
@@ -764,7 +868,11 @@ __device__ void bwd_df_grad(const DevNet& g, const DevState& s, const DfState& d
         const int p = p0 + lane;
         const float2 sld = reinterpret_cast<const float2*>(s.slew)[2 * dp + 1];
         const SinkPre q = sink_pre(s, d, p, 2, gamma, sc);
-        const SinkBwd b = sink_post(s, p, q, sld, 2);
+        SinkWords wd;
+        wd.rat = make_float4(0.f, 0.f, 0.f, 0.f);
+        wd.ga = ld_relaxed_f2(s.g_ats + 2 * p);  // final: the driver task saw every partial after its sinks'
+        wd.gs = ld_relaxed_f2(s.g_slew + 2 * p);
+        const SinkBwd b = sink_post(wd, q, sld, 2);
         s.grad[g.pin_orig[p]] = sink_grad(g, s, p, s.xy[p], s.xy[dp], b.gwire, gload);
     }
 }
@@ -792,7 +900,9 @@ __global__ void __launch_bounds__(kBlock) k_bwd_df(DevNet g, DevState s, DfState
         } else if (mode & 2) {
             bwd_df_grad(g, s, d, cnt, t, task.x, task.z, task.w, gamma, sc);
         }
-        signal_consumers(cnt, d.b_out_ptr, d.b_out, t);
+        // every task's consumers poll the words it wrote, except the gradient
+        // chunks of a large net, which wait on a counter that its driver step releases
+        if (task.y == -2) signal_consumers(cnt, d.b_out_ptr, d.b_out, t);
         t = next;
     }
 }
@@ -813,6 +923,14 @@ void launch_fwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, i
     if (d.TF == 0) return;
     if (lse) launch_coop(k_fwd_df<true>, grid, kBlock, st, g, s, d, gamma, stall_task);
     else launch_coop(k_fwd_df<false>, grid, kBlock, st, g, s, d, gamma, stall_task);
+}
+
+void launch_bwd_reset(const DevState& s, const DfState& d, int P, int mode, cudaStream_t st) {
+    if (P == 0 && d.npart == 0) return;
+    int blocks = (P + kBlock - 1) / kBlock;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_bwd_reset<<<blocks, kBlock, 0, st>>>(s, d.pin_cons, P, mode, (mode & 2) ? d.apart : d.rpart,
+                                           d.npart * kPartFloats);
 }
 
 void launch_fwd_reset(const DevState& s, const DfState& d, int P, cudaStream_t st) {

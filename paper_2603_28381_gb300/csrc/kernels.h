@@ -70,6 +70,7 @@ struct DfState {
     int32_t* abort_word;     // [2] [0] a bounded wait of the current sweep expired, [1] sticky copy
     const uint8_t* pin_keep; // [P] 1: the forward sweep does not write the pin (asserted values)
     int32_t TF, TB;
+    int32_t npart;           // partial records of the backward sweeps
 };
 
 // Batched schedule (many placements of one netlist; lane = placement).
@@ -124,6 +125,8 @@ void launch_batch_init_ats(const BatchState& bs, int P, cudaStream_t st);
 // stall_task >= 0: that task's wait never succeeds (test hook for the bounded wait)
 void launch_fwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int lse,
                          int stall_task, cudaStream_t st);
+// marks the words a dataflow backward sweep of this mode writes as not yet written
+void launch_bwd_reset(const DevState& s, const DfState& d, int P, int mode, cudaStream_t st);
 // marks every word the dataflow forward sweep writes as not yet written (kUnwritten)
 void launch_fwd_reset(const DevState& s, const DfState& d, int P, cudaStream_t st);
 void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int mode,
