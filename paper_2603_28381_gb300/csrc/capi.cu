@@ -1233,11 +1233,12 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
         launches[STA_PROF_SEED] = 1;
         launches[STA_PROF_ADJOINT] = L.TB > 0 ? 1 : 0;
     } else if (h->schedule == STA_SCHED_DATAFLOW) {
-        launches[STA_PROF_NET_RC] = nc > 0 ? 1 : 0;
+        // each sweep is preceded by the reset of the words its tasks poll
+        launches[STA_PROF_NET_RC] = (L.P > 0 ? 1 : 0) + (nc > 0 ? 1 : 0);
         launches[STA_PROF_FORWARD] = L.TF > 0 ? 1 : 0;
-        launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 1 : 0;  // fused into the adjoint sweep
+        launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 2 : 0;  // fused into the adjoint sweep
         launches[STA_PROF_SEED] = 1;  // weights
-        launches[STA_PROF_ADJOINT] = L.TB > 0 ? 1 : 0;
+        launches[STA_PROF_ADJOINT] = L.TB > 0 ? 2 : 0;
     } else {
         launches[STA_PROF_NET_RC] = (nw + nc) > 0 ? 1 : 0;
         launches[STA_PROF_FORWARD] = nonempty;

@@ -342,12 +342,15 @@ __global__ void __launch_bounds__(kBlock) k_bwd_reset(DevState s, const int32_t*
     }
 }
 
-// Before a forward sweep: every arrival / slew / LSE-arrival word the sweep
-// writes is set to kUnwritten (asserted pins keep their constants).
-__global__ void __launch_bounds__(kBlock) k_fwd_reset(DevState s, const uint8_t* __restrict__ keep, int P) {
+// Before a forward sweep: the arrival / slew / LSE-arrival words that forward
+// tasks poll -- those of cell-input pins the sweep writes -- are set to
+// kUnwritten (asserted pins keep their constants; sinks that feed no cell are
+// only written).
+__global__ void __launch_bounds__(kBlock) k_fwd_reset(DevState s, const uint8_t* __restrict__ keep,
+                                                      const int32_t* __restrict__ pin_cons, int P) {
     const float u = __uint_as_float(kUnwritten);
     for (int p = blockIdx.x * kBlock + threadIdx.x; p < P; p += gridDim.x * kBlock) {
-        if (keep[p]) continue;
+        if (keep[p] || pin_cons[p] < 0) continue;
         reinterpret_cast<float4*>(s.at)[p] = make_float4(u, u, u, u);
         reinterpret_cast<float4*>(s.slew)[p] = make_float4(u, u, u, u);
         reinterpret_cast<float2*>(s.ats)[p] = make_float2(u, u);
@@ -794,6 +797,9 @@ __device__ void bwd_df_driver(const DevNet& g, const DevState& s, const DfState&
     // the wait: poll the chunks' partial words (reset to kUnwritten before the
     // sweep, written once by the partial tasks) until all are written; bounded
     // like wait_ready
+    float first[kPartFloats];  // the lane's first chunk, as seen by the successful poll
+#pragma unroll
+    for (int j = 0; j < kPartFloats; ++j) first[j] = 0.f;
     {
         unsigned long long t0 = 0;
         for (unsigned it = 0;; ++it) {
@@ -801,7 +807,11 @@ __device__ void bwd_df_driver(const DevNet& g, const DevState& s, const DfState&
             for (int k = lane; k < nch; k += 32) {
                 const float* q = part + (size_t)(slot0 + k) * kPartFloats;
 #pragma unroll
-                for (int j = 0; j < kPartFloats; ++j) ok &= written(ld_relaxed_f(q + j));
+                for (int j = 0; j < kPartFloats; ++j) {
+                    const float x = ld_relaxed_f(q + j);
+                    if (k == lane) first[j] = x;
+                    ok &= written(x);
+                }
             }
             if (__all_sync(kFull, ok)) break;
             __nanosleep(64);
@@ -827,7 +837,15 @@ __device__ void bwd_df_driver(const DevNet& g, const DevState& s, const DfState&
     v[2] = v[3] = kInf;
 #pragma unroll
     for (int k = 4; k < kPartFloats; ++k) v[k] = 0.f;
-    for (int k = lane; k < nch; k += 32) {
+    if (lane < nch) {  // the first chunk from the poll, the rest re-read (already written)
+        v[0] = fmaxf(v[0], first[0]);
+        v[1] = fmaxf(v[1], first[1]);
+        v[2] = fminf(v[2], first[2]);
+        v[3] = fminf(v[3], first[3]);
+#pragma unroll
+        for (int j = 4; j < kPartFloats; ++j) v[j] += first[j];
+    }
+    for (int k = lane + 32; k < nch; k += 32) {
         const float* q = part + (size_t)(slot0 + k) * kPartFloats;
         v[0] = fmaxf(v[0], ld_relaxed_f(q + 0));
         v[1] = fmaxf(v[1], ld_relaxed_f(q + 1));
@@ -937,7 +955,7 @@ void launch_fwd_reset(const DevState& s, const DfState& d, int P, cudaStream_t s
     if (P == 0) return;
     int blocks = (P + kBlock - 1) / kBlock;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    k_fwd_reset<<<blocks, kBlock, 0, st>>>(s, d.pin_keep, P);
+    k_fwd_reset<<<blocks, kBlock, 0, st>>>(s, d.pin_keep, d.pin_cons, P);
 }
 
 void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int mode,
