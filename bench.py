@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--schedule", default="dataflow", choices=["dataflow", "levels"])
+    ap.add_argument("--grid-blocks", type=int, default=0,
+                    help="blocks of the persistent sweeps (0: every block that fits)")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "ablation"],
                     help="single: one placement of the ~2.5M-pin netlist per step (the headline); "
                          "batch: 64 placements of a ~500k-pin netlist per step")
@@ -217,6 +219,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(seconds, dist, device):
+    """The job's time: the slowest rank's.  Ranks are independent replicas (no
+    data-path collective); this scalar is the only value they exchange."""
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return world * units_per_rank / seconds
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -318,7 +335,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    eng = sta.StaEngine(nl, w.library, schedule=args.schedule)
+    eng = sta.StaEngine(nl, w.library, schedule=args.schedule, grid_blocks=args.grid_blocks)
     for _ in range(args.warmup):
         step(eng)
     cur = torch.cuda.current_stream()
@@ -338,12 +355,8 @@ def run_ours(args):
     ms = [a.elapsed_time(b) for a, b in ev]
     if args.verbose:
         print("step ms:", " ".join(f"{m:.3f}" for m in ms), file=sys.stderr)
-    total_s = sum(ms) / 1e3
-    t_local = torch.tensor([total_s], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    total_s = float(t_local.item())
-    value = world * P * args.steps / total_s
+    total_s = max_over_ranks(sum(ms) / 1e3, dist, dev)
+    value = job_throughput(P * args.steps, world, total_s)
     _, launches = eng.profile(with_times=False)
     launches_per_step = int(sum(launches.values()))
 
@@ -366,17 +379,14 @@ def run_ours(args):
             eng.backward_grad(WEIGHTS, out=g_h)
             eng.summary()
         barrier()
-        te = time.perf_counter() - t
-        t_e = torch.tensor([te], dtype=torch.float64, device=dev)
-        if dist is not None:
-            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * P * args.steps / float(t_e.item()), "unit": "pins/s",
+        te = max_over_ranks(time.perf_counter() - t, dist, dev)
+        e2e = {"value": job_throughput(P * args.steps, world, te), "unit": "pins/s",
                "h2d_bytes_per_step": 8 * P, "d2h_bytes_per_step": 8 * P + 64}
     eng.close()
 
     # roofline of the dominant kernel kind, from CUDA events around every launch of
     # the same steps (a handle with StaOptions.profile = 1)
-    prof_eng = sta.StaEngine(nl, w.library, profile=True, schedule=args.schedule)
+    prof_eng = sta.StaEngine(nl, w.library, profile=True, schedule=args.schedule, grid_blocks=args.grid_blocks)
     for _ in range(2):
         step(prof_eng)
     acc = {}

@@ -46,7 +46,7 @@ class StaEngine:
 
     def __init__(self, netlist, library, use_graphs: bool = True, profile: bool = False,
                  schedule: str = "dataflow", num_placements: int = 1, tile_pins: int = 0,
-                 chunk: int = 0, batch_sweep: str = "levels"):
+                 chunk: int = 0, batch_sweep: str = "levels", grid_blocks: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("StaEngine needs a CUDA device (there is no CPU path)")
@@ -61,7 +61,8 @@ class StaEngine:
         self.B = int(num_placements) if self.batched else 1
         self.h = _sta.sta_create(netlist, library, use_graphs, profile, sched,
                                  self.B if self.batched else 0, tile_pins, chunk,
-                                 {"levels": _sta.BATCH_LEVELS, "dataflow": _sta.BATCH_DATAFLOW}[batch_sweep])
+                                 {"levels": _sta.BATCH_LEVELS, "dataflow": _sta.BATCH_DATAFLOW}[batch_sweep],
+                                 grid_blocks)
         self.sizes = _sta.sta_query_sizes(self.h)
         self.sizes["nets_desc"] = int(netlist.num_nets)
         self.gamma = None

@@ -80,18 +80,20 @@ __device__ __forceinline__ float quad_sum(float v) {
 // and the load segment of this placement.
 struct FCell {
     int t, na, a0, rfi;
+    int dyn;  // bit k: arc k's input pin is written during the sweep
     int pin[STA_MAX_ARCS];
     int jl;
     float ul;
     float sidx[6], sinv[6];
 };
 
-__device__ __forceinline__ FCell fcell(const DevNet& g, int n, int rf, float ld) {
+__device__ __forceinline__ FCell fcell(const DevNet& g, const DfState& d, int n, int rf, float ld) {
     FCell f;
     f.t = g.net_drv[n];
     f.a0 = g.net_arc_ptr[n];
     f.na = f.t >= 0 ? g.net_arc_ptr[n + 1] - f.a0 : 0;
     f.rfi = 0;
+    f.dyn = 0;
     f.jl = 0;
     f.ul = 0.f;
 #pragma unroll
@@ -105,6 +107,7 @@ __device__ __forceinline__ FCell fcell(const DevNet& g, int n, int rf, float ld)
         if (k < f.na) {
             f.pin[k] = g.arc_pin[f.a0 + k];
             f.rfi |= (rf ^ ((un >> k) & 1)) << k;
+            f.dyn |= (d.arc_prod[f.a0 + k] >= 0 ? 1 : 0) << k;
         }
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
@@ -138,8 +141,10 @@ struct FOut {
 // Driver-cell evaluation for one condition (late max / early min over the
 // arcs, worst slew, Eq. 4 LSE for the late conditions).  The fanin values of
 // all arcs are loaded together (through L2: other warps of this sweep wrote them).
+template <bool kPoll>
 __device__ __forceinline__ FOut fcell_eval(const DevNet& g, const BatchState& bs, const FCell& f, int dp,
-                                           const Lane& L, float gamma, bool lse) {
+                                           const Lane& L, float gamma, bool lse, int32_t* abort_word,
+                                           bool stall = false) {
     const int Bp = bs.Bp, b = L.b, el = L.el, rf = L.rf;
     FOut o;
     if (f.t < 0) {  // asserted driver: constant values set at creation
@@ -149,17 +154,28 @@ __device__ __forceinline__ FOut fcell_eval(const DevNet& g, const BatchState& bs
         return o;
     }
     float ain[STA_MAX_ARCS], sin[STA_MAX_ARCS], zin[STA_MAX_ARCS];
+    // the fanin words of all arcs together; in the dataflow sweep this is the
+    // wait: repeated until every word written during the sweep holds its value
+    auto load = [&]() {
+        bool ok = !stall;  // the test hook's stalled task never sees its inputs
 #pragma unroll
-    for (int k = 0; k < STA_MAX_ARCS; ++k) {
-        ain[k] = sin[k] = zin[k] = 0.f;
-        if (k < f.na) {
-            const int r = (f.rfi >> k) & 1;
-            const int row = 4 * f.pin[k] + 2 * el + r;
-            ain[k] = __ldcg(bs.at + ix(row, Bp, b));
-            sin[k] = __ldcg(bs.slew + ix(row, Bp, b));
-            if (lse && el) zin[k] = __ldcg(bs.ats + ix(2 * f.pin[k] + r, Bp, b));
+        for (int k = 0; k < STA_MAX_ARCS; ++k) {
+            ain[k] = sin[k] = zin[k] = 0.f;
+            if (k < f.na) {
+                const int r = (f.rfi >> k) & 1;
+                const int row = 4 * f.pin[k] + 2 * el + r;
+                ain[k] = kPoll ? ld_relaxed_f(bs.at + ix(row, Bp, b)) : __ldcg(bs.at + ix(row, Bp, b));
+                sin[k] = kPoll ? ld_relaxed_f(bs.slew + ix(row, Bp, b)) : __ldcg(bs.slew + ix(row, Bp, b));
+                if (lse && el)
+                    zin[k] = kPoll ? ld_relaxed_f(bs.ats + ix(2 * f.pin[k] + r, Bp, b))
+                                   : __ldcg(bs.ats + ix(2 * f.pin[k] + r, Bp, b));
+                if ((f.dyn >> k) & 1) ok &= written(ain[k]) & written(sin[k]) & (!(lse && el) || written(zin[k]));
+            }
         }
-    }
+        return ok;
+    };
+    if constexpr (kPoll) poll_words(load, abort_word);
+    else load();
     float best_at = el ? -kInf : kInf, best_sl = el ? -kInf : kInf, m = -kInf;
     float cand[STA_MAX_ARCS];
 #pragma unroll
@@ -195,10 +211,10 @@ __device__ __forceinline__ FOut fcell_eval(const DevNet& g, const BatchState& bs
 
 __device__ __forceinline__ void store_pin(const BatchState& bs, int p, const Lane& L, float at, float sl, float z,
                                           bool lse) {
-    const int Bp = bs.Bp;
-    bs.at[ix(4 * p + L.c, Bp, L.b)] = at;
-    bs.slew[ix(4 * p + L.c, Bp, L.b)] = sl;
-    if (lse && L.el) bs.ats[ix(2 * p + L.rf, Bp, L.b)] = z;
+    const int Bp = bs.Bp;  // strong stores: words that other tasks of the sweep poll
+    st_relaxed_f(bs.at + ix(4 * p + L.c, Bp, L.b), at);
+    st_relaxed_f(bs.slew + ix(4 * p + L.c, Bp, L.b), sl);
+    if (lse && L.el) st_relaxed_f(bs.ats + ix(2 * p + L.rf, Bp, L.b), z);
 }
 
 // wire step to the sinks [s0, s1): every lane its condition
@@ -230,16 +246,15 @@ __device__ __forceinline__ float net_load(const DevNet& g, const BatchState& bs,
 // launches; every load comes from the prologue)
 template <bool lse, bool kWait>
 __device__ void bfwd_nets(const DevNet& g, const BatchState& bs, const DfState& d, int q, int n0, int nn,
-                          const Lane& L, float gamma) {
+                          const Lane& L, float gamma, bool stall = false) {
     const int Bp = bs.Bp;
     // before the wait: the first net's load (static) and its cell description
     const int dp0 = g.net_ptr[n0], e0 = g.net_ptr[n0 + 1];
     const float2 xyd0 = bs.xy[ix(dp0, Bp, L.b)];
     const float ld0 = kWait ? net_load(g, bs, dp0, e0, L, xyd0) : bs.load[ix(n0, Bp, L.b)];
-    const FCell f0 = fcell(g, n0, L.rf, ld0);
+    const FCell f0 = fcell(g, d, n0, L.rf, ld0);
     if constexpr (kWait) {
         if (L.c == 0) bs.load[ix(n0, Bp, L.b)] = ld0;
-        wait_ready(d.fcnt, q, d.f_indeg[q / bs.GT], d.abort_word);
     }
 
     for (int j = 0; j < nn; ++j) {
@@ -255,9 +270,9 @@ __device__ void bfwd_nets(const DevNet& g, const BatchState& bs, const DfState& 
             } else {
                 ld = bs.load[ix(n, Bp, L.b)];
             }
-            f = fcell(g, n, L.rf, ld);
+            f = fcell(g, d, n, L.rf, ld);
         }
-        const FOut o = fcell_eval(g, bs, f, dp, L, gamma, lse);
+        const FOut o = fcell_eval<kWait>(g, bs, f, dp, L, gamma, lse, d.abort_word, stall);
         if (f.t >= 0) store_pin(bs, dp, L, o.at, o.sl, o.z, lse);
         store_sinks(g, bs, dp + 1, e, L, xyd, o, lse);
     }
@@ -267,21 +282,20 @@ __device__ void bfwd_nets(const DevNet& g, const BatchState& bs, const DfState& 
 // evaluates the driver cell, the first one stores it
 template <bool lse, bool kWait>
 __device__ void bfwd_chunk(const DevNet& g, const BatchState& bs, const DfState& d, int q, int n, int p0, int cnt,
-                           const Lane& L, float gamma) {
+                           const Lane& L, float gamma, bool stall = false) {
     const int Bp = bs.Bp;
     const int dp = g.net_ptr[n];
     const float2 xyd = bs.xy[ix(dp, Bp, L.b)];
-    const FCell f = fcell(g, n, L.rf, bs.load[ix(n, Bp, L.b)]);
+    const FCell f = fcell(g, d, n, L.rf, bs.load[ix(n, Bp, L.b)]);
 
-    if constexpr (kWait) wait_ready(d.fcnt, q, d.f_indeg[q / bs.GT], d.abort_word);
-
-    const FOut o = fcell_eval(g, bs, f, dp, L, gamma, lse);
+    const FOut o = fcell_eval<kWait>(g, bs, f, dp, L, gamma, lse, d.abort_word, stall);
     if (f.t >= 0 && p0 == dp + 1) store_pin(bs, dp, L, o.at, o.sl, o.z, lse);
     store_sinks(g, bs, p0, p0 + cnt, L, xyd, o, lse);
 }
 
 template <bool lse>
-__global__ void __launch_bounds__(kBlock, 4) k_bfwd(DevNet g, BatchState bs, DfState d, float gamma) {
+__global__ void __launch_bounds__(kBlock, 4) k_bfwd(DevNet g, BatchState bs, DfState d, float gamma,
+                                                    int stall_task) {
     const int GT = bs.GT;
     const int Q = d.TF * GT;
     int q = grab(d.heads + 0);
@@ -290,13 +304,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_bfwd(DevNet g, BatchState bs, DfS
         const int t = q / GT, gq = q - t * GT;
         const Lane L = lane_of(gq);
         const int4 task = d.ftask[t];
-        if (task.y > 0) bfwd_nets<lse, true>(g, bs, d, q, task.x, task.y, L, gamma);
-        else bfwd_chunk<lse, true>(g, bs, d, q, task.x, task.z, task.w, L, gamma);
-        // consumers of (t, group) are (u, group): counter u * GT + group
-        __syncwarp();
-        const int k1 = d.f_out_ptr[t + 1];
-        for (int k = d.f_out_ptr[t] + L.lane; k < k1; k += 32) red_release_add(d.fcnt + d.f_out[k] * GT + gq, 1);
-        q = next;
+        if (task.y > 0) bfwd_nets<lse, true>(g, bs, d, q, task.x, task.y, L, gamma, t == stall_task);
+        else bfwd_chunk<lse, true>(g, bs, d, q, task.x, task.z, task.w, L, gamma, t == stall_task);
+        q = next;  // consumers poll the words this task wrote
     }
 }
 
@@ -526,11 +536,13 @@ __device__ __forceinline__ float bcell_apply(const BatchState& bs, const BCell& 
     for (int k = 0; k < STA_MAX_ARCS; ++k) {
         if (k < bc.na) {
             const int r = (bc.rfi >> k) & 1;
-            if (mode & 1) bs.rat[ix(4 * bc.pin[k] + 2 * el + r, Bp, b)] = R - bc.adel[k];
+            // strong stores: words that the sinks' tasks poll
+            if (mode & 1) st_relaxed_f(bs.rat + ix(4 * bc.pin[k] + 2 * el + r, Bp, b), R - bc.adel[k]);
             if ((mode & 2) && el) {
                 const float gD = GA * bc.w[k];
-                bs.g_ats[ix(2 * bc.pin[k] + r, Bp, b)] = gD;
-                bs.g_slew[ix(2 * bc.pin[k] + r, Bp, b)] = fmaf(gD, bc.dDs[k], k == bc.amax ? GS * bc.dSs : 0.f);
+                st_relaxed_f(bs.g_ats + ix(2 * bc.pin[k] + r, Bp, b), gD);
+                st_relaxed_f(bs.g_slew + ix(2 * bc.pin[k] + r, Bp, b),
+                             fmaf(gD, bc.dDs[k], k == bc.amax ? GS * bc.dSs : 0.f));
                 gl = fmaf(gD, bc.dDl[k], gl);
             }
         }
@@ -550,23 +562,41 @@ struct BSink {
     Wire w;
 };
 
-template <int mode>
+template <int mode, bool kPoll>
 __device__ __forceinline__ BSink bsink(const DevNet& g, const BatchState& bs, const DfState& d, int p, const Lane& L,
                                        float2 xyd, float sld, float gamma, const BSeed& sd) {
     const int Bp = bs.Bp, b = L.b;
     BSink s;
     s.w = wire(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p));
-    s.r = (mode & 1) ? __ldcg(bs.rat + ix(4 * p + L.c, Bp, b)) - s.w.D : 0.f;
+    const bool dyn = d.pin_cons[p] >= 0;  // the same for every lane
+    // the sink's words written by the task of the cell it feeds; in the
+    // dataflow sweep this is the wait (repeated until written)
+    float rr = 0.f, ga = 0.f, gs = 0.f;
+    auto load = [&]() {
+        bool ok = true;
+        if (mode & 1) {
+            rr = kPoll ? ld_relaxed_f(bs.rat + ix(4 * p + L.c, Bp, b)) : __ldcg(bs.rat + ix(4 * p + L.c, Bp, b));
+            ok &= written(rr);
+        }
+        if ((mode & 2) && L.el && dyn) {
+            ga = kPoll ? ld_relaxed_f(bs.g_ats + ix(2 * p + L.rf, Bp, b)) : __ldcg(bs.g_ats + ix(2 * p + L.rf, Bp, b));
+            gs = kPoll ? ld_relaxed_f(bs.g_slew + ix(2 * p + L.rf, Bp, b))
+                       : __ldcg(bs.g_slew + ix(2 * p + L.rf, Bp, b));
+            ok &= written(ga) & written(gs);
+        }
+        return ok;
+    };
+    if (kPoll && dyn) poll_words(load, d.abort_word);
+    else load();
+    s.r = (mode & 1) ? rr - s.w.D : 0.f;
     s.ga = s.gs = s.gw = 0.f;
     if ((mode & 2) && L.el) {
-        float ga = 0.f, gs = 0.f;
-        if (d.pin_cons[p] >= 0) {
-            ga = __ldcg(bs.g_ats + ix(2 * p + L.rf, Bp, b));
-            gs = __ldcg(bs.g_slew + ix(2 * p + L.rf, Bp, b));
+        if (dyn) {
+            // ga, gs loaded above
         } else {
-            const float rr = bs.rat[ix(4 * p + 2, Bp, b)], rfl = bs.rat[ix(4 * p + 3, Bp, b)];
-            if (isfinite(rr)) {
-                const float sr = rr - bs.ats[ix(2 * p, Bp, b)], sf = rfl - bs.ats[ix(2 * p + 1, Bp, b)];
+            const float rl = bs.rat[ix(4 * p + 2, Bp, b)], rfl = bs.rat[ix(4 * p + 3, Bp, b)];
+            if (isfinite(rl)) {
+                const float sr = rl - bs.ats[ix(2 * p, Bp, b)], sf = rfl - bs.ats[ix(2 * p + 1, Bp, b)];
                 const float te = softmin3(sr, sf, gamma);
                 const float sv = L.rf ? sf : sr;
                 float gv = sd.wt * expf(-(sv - te) / gamma);
@@ -604,8 +634,6 @@ __device__ void bbwd_nets(const DevNet& g, const BatchState& bs, const DfState& 
     const float2 xyd0 = bs.xy[ix(dp0, Bp, b)];
     const float sld0 = (mode & 2) ? late_slew_of_driver(bs, dp0, L) : 0.f;
 
-    if constexpr (kWait) wait_ready(cnt, q, d.b_indeg[q / bs.GT], d.abort_word);
-
     for (int j = 0; j < nn; ++j) {
         const int n = n0 + j;
         const int dp = j ? g.net_ptr[n] : dp0, e = g.net_ptr[n + 1];
@@ -619,7 +647,7 @@ __device__ void bbwd_nets(const DevNet& g, const BatchState& bs, const DfState& 
         float R = L.el ? kInf : -kInf, GA = 0.f, GS = 0.f;
 #pragma unroll 2
         for (int p = dp + 1; p < e; ++p) {
-            const BSink s = bsink<mode>(g, bs, d, p, L, xyd, sld, gamma, sd);
+            const BSink s = bsink<mode, kWait>(g, bs, d, p, L, xyd, sld, gamma, sd);
             R = L.el ? fminf(R, s.r) : fmaxf(R, s.r);
             GA += s.ga;
             GS += s.gs;
@@ -661,12 +689,10 @@ __device__ void bbwd_part(const DevNet& g, const BatchState& bs, const DfState& 
     const float2 xyd = bs.xy[ix(dp, Bp, b)];
     const float sld = (mode & 2) ? late_slew_of_driver(bs, dp, L) : 0.f;
 
-    if constexpr (kWait) wait_ready(cnt, q, d.b_indeg[q / bs.GT], d.abort_word);
-
     float R = L.el ? kInf : -kInf, GA = 0.f, GS = 0.f, sx = 0.f, sy = 0.f, hx = 0.f, hy = 0.f;
 #pragma unroll 2
     for (int p = p0; p < p0 + np; ++p) {
-        const BSink s = bsink<mode>(g, bs, d, p, L, xyd, sld, gamma, sd);
+        const BSink s = bsink<mode, kWait>(g, bs, d, p, L, xyd, sld, gamma, sd);
         R = L.el ? fminf(R, s.r) : fmaxf(R, s.r);
         GA += s.ga;
         GS += s.gs;
@@ -684,16 +710,17 @@ __device__ void bbwd_part(const DevNet& g, const BatchState& bs, const DfState& 
     }
     float* part = (mode & 2) ? bs.part : bs.rpart;
     const int base = slot * kPartFloats;
-    part[ix(base + L.c, Bp, b)] = R;
+    // strong stores: the driver step polls these words
+    st_relaxed_f(part + ix(base + L.c, Bp, b), R);
     if ((mode & 2) && L.el) {
-        part[ix(base + 4 + L.rf, Bp, b)] = GA;
-        part[ix(base + 6 + L.rf, Bp, b)] = GS;
+        st_relaxed_f(part + ix(base + 4 + L.rf, Bp, b), GA);
+        st_relaxed_f(part + ix(base + 6 + L.rf, Bp, b), GS);
     }
     if ((mode & 2) && L.c == 2) {  // lane 2 holds the wire adjoints of both transitions
-        part[ix(base + 8, Bp, b)] = sx;
-        part[ix(base + 9, Bp, b)] = sy;
-        part[ix(base + 10, Bp, b)] = hx;
-        part[ix(base + 11, Bp, b)] = hy;
+        st_relaxed_f(part + ix(base + 8, Bp, b), sx);
+        st_relaxed_f(part + ix(base + 9, Bp, b), sy);
+        st_relaxed_f(part + ix(base + 10, Bp, b), hx);
+        st_relaxed_f(part + ix(base + 11, Bp, b), hy);
     }
 }
 
@@ -704,8 +731,6 @@ __device__ void bbwd_driver(const DevNet& g, const BatchState& bs, const DfState
     const int dp = g.net_ptr[n];
     const BCell bc = bcell_pre<mode>(g, bs, n, dp, L, gamma);
 
-    if constexpr (kWait) wait_ready(cnt, q, d.b_indeg[q / bs.GT], d.abort_word);
-
     const float* part = (mode & 2) ? bs.part : bs.rpart;
     float R = L.el ? kInf : -kInf, GA = 0.f, GS = 0.f, sx = 0.f, sy = 0.f, hx = 0.f, hy = 0.f;
     // The chunks' partials in chunk order.  Lane c of a quad reads slots c
@@ -715,14 +740,28 @@ __device__ void bbwd_driver(const DevNet& g, const BatchState& bs, const DfState
     float v4 = 0.f, v8 = 0.f;
     for (int k0 = 0; k0 < nch; k0 += kU) {
         float vr[kU], va[kU], vb[kU];
+        // in the dataflow sweep this is the wait: repeated until the 8 chunks'
+        // words this lane reads are written
+        auto load = [&]() {
+            bool all = true;
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int base = (slot0 + k0 + u) * kPartFloats;
-            const bool ok = k0 + u < nch;
-            vr[u] = ok ? __ldcg(part + ix(base + L.c, Bp, b)) : (L.el ? kInf : -kInf);
-            va[u] = ((mode & 2) && ok) ? __ldcg(part + ix(base + 4 + L.c, Bp, b)) : 0.f;
-            vb[u] = ((mode & 2) && ok) ? __ldcg(part + ix(base + 8 + L.c, Bp, b)) : 0.f;
-        }
+            for (int u = 0; u < kU; ++u) {
+                const int base = (slot0 + k0 + u) * kPartFloats;
+                const bool ok = k0 + u < nch;
+                vr[u] = ok ? (kWait ? ld_relaxed_f(part + ix(base + L.c, Bp, b)) : __ldcg(part + ix(base + L.c, Bp, b)))
+                           : (L.el ? kInf : -kInf);
+                va[u] = ((mode & 2) && ok)
+                            ? (kWait ? ld_relaxed_f(part + ix(base + 4 + L.c, Bp, b)) : __ldcg(part + ix(base + 4 + L.c, Bp, b)))
+                            : 0.f;
+                vb[u] = ((mode & 2) && ok)
+                            ? (kWait ? ld_relaxed_f(part + ix(base + 8 + L.c, Bp, b)) : __ldcg(part + ix(base + 8 + L.c, Bp, b)))
+                            : 0.f;
+                if (ok) all &= written(vr[u]) & (!(mode & 2) || (written(va[u]) & written(vb[u])));
+            }
+            return all;
+        };
+        if constexpr (kWait) poll_words(load, d.abort_word);
+        else load();
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             if (k0 + u >= nch) break;
@@ -769,7 +808,7 @@ __device__ void bbwd_grad(const DevNet& g, const BatchState& bs, const DfState& 
     const float gload = __ldcg(bs.net_gload + ix(n, Bp, b));
 #pragma unroll 2
     for (int p = p0; p < p0 + np; ++p) {
-        const BSink s = bsink<2>(g, bs, d, p, L, xyd, sld, gamma, sd);
+        const BSink s = bsink<2, false>(g, bs, d, p, L, xyd, sld, gamma, sd);
         const float gw = s.gw + __shfl_xor_sync(kFull, s.gw, 1);
         if (L.c == 2)
             bs.grad[ix(p, Bp, b)] = bsink_grad(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p), gw, gload);
@@ -807,9 +846,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_bbwd(DevNet g, BatchState bs, DfS
         const int t = q / GT, gq = q - t * GT;
         const Lane L = lane_of(gq);
         bbwd_task<mode, true>(g, bs, d, cnt, q, t, L, gamma);
-        __syncwarp();
-        const int k1 = d.b_out_ptr[t + 1];
-        for (int k = d.b_out_ptr[t] + L.lane; k < k1; k += 32) red_release_add(cnt + d.b_out[k] * GT + gq, 1);
+        // every consumer polls the words its producers wrote, except the gradient
+        // chunks of a large net, which wait on a counter that its driver step releases
+        if (d.btask[t].y == -2) {
+            __syncwarp();
+            const int k1 = d.b_out_ptr[t + 1];
+            for (int k = d.b_out_ptr[t] + L.lane; k < k1; k += 32) red_release_add(cnt + d.b_out[k] * GT + gq, 1);
+        }
         q = next;
     }
 }
@@ -992,6 +1035,46 @@ __global__ void __launch_bounds__(kBlock) k_binit_ats(BatchState bs, int P) {
     }
 }
 
+
+// Before a batched dataflow sweep: the words its tasks poll are set to
+// kUnwritten for every placement.  Forward: arrival / slew / LSE-arrival words
+// of the cell-input pins the sweep writes.  Backward: required times (mode 1)
+// and adjoints (mode 2) of cell-input pins, and the large nets' partial records.
+__global__ void __launch_bounds__(kBlock) k_breset(BatchState bs, const uint8_t* __restrict__ keep,
+                                                   const int32_t* __restrict__ pin_cons, int P, int what,
+                                                   float* part, long long part_words) {
+    const float u = __uint_as_float(kUnwritten);
+    const int Bp = bs.Bp;
+    const long long n = (long long)P * Bp;
+    for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < part_words; i += (long long)gridDim.x * kBlock)
+        part[i] = u;
+    for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < n; i += (long long)gridDim.x * kBlock) {
+        const int p = (int)(i / Bp), b = (int)(i - (long long)p * Bp);
+        if (pin_cons[p] < 0) continue;
+        if (what == 0) {  // forward
+            if (keep[p]) continue;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                bs.at[ix(4 * p + c, Bp, b)] = u;
+                bs.slew[ix(4 * p + c, Bp, b)] = u;
+            }
+            bs.ats[ix(2 * p, Bp, b)] = u;
+            bs.ats[ix(2 * p + 1, Bp, b)] = u;
+        } else {
+            if (what & 1) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) bs.rat[ix(4 * p + c, Bp, b)] = u;
+            }
+            if (what & 2) {
+                bs.g_ats[ix(2 * p, Bp, b)] = u;
+                bs.g_ats[ix(2 * p + 1, Bp, b)] = u;
+                bs.g_slew[ix(2 * p, Bp, b)] = u;
+                bs.g_slew[ix(2 * p + 1, Bp, b)] = u;
+            }
+        }
+    }
+}
+
 int bgrid(long long n) {
     long long b = (n + kBlock - 1) / kBlock;
     if (b < 1) b = 1;
@@ -1029,10 +1112,10 @@ void launch_batch_load(const DevNet& g, const BatchState& bs, const int32_t* big
 }
 
 void launch_batch_fwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int lse,
-                      cudaStream_t st) {
+                      int stall_task, cudaStream_t st) {
     if (d.TF == 0) return;
-    if (lse) launch_coop(k_bfwd<true>, grid, kBlock, st, g, bs, d, gamma);
-    else launch_coop(k_bfwd<false>, grid, kBlock, st, g, bs, d, gamma);
+    if (lse) launch_coop(k_bfwd<true>, grid, kBlock, st, g, bs, d, gamma, stall_task);
+    else launch_coop(k_bfwd<false>, grid, kBlock, st, g, bs, d, gamma, stall_task);
 }
 
 void launch_batch_load_small(const DevNet& g, const BatchState& bs, int big, cudaStream_t st) {
@@ -1064,6 +1147,13 @@ void launch_batch_bwd_level(const DevNet& g, const BatchState& bs, const DfState
 void launch_batch_endpoints(const DevNet& g, const BatchState& bs, float gamma, int lse, cudaStream_t st) {
     k_bep1<<<dim3(kRedBlocks, bs.G), kBlock, 0, st>>>(g, bs, gamma, lse);
     k_bep2<<<(bs.Bp * 32 + 127) / 128, 128, 0, st>>>(g, bs, gamma, lse, kRedBlocks);
+}
+
+void launch_batch_reset(const BatchState& bs, const DfState& d, int P, int what, cudaStream_t st) {
+    const long long pw = what == 0 ? 0 : (long long)d.npart * kPartFloats * bs.Bp;
+    float* part = (what & 2) ? bs.part : bs.rpart;
+    if ((long long)P * bs.Bp + pw == 0) return;
+    k_breset<<<bgrid((long long)P * bs.Bp), kBlock, 0, st>>>(bs, d.pin_keep, d.pin_cons, P, what, part, pw);
 }
 
 void launch_batch_bwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int mode,

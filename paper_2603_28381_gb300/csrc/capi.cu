@@ -272,17 +272,16 @@ void enqueue_forward_batch(StaHandle* h, int lse, float gamma, cudaStream_t st) 
         launch_batch_endpoints(h->g, h->bs, gamma, lse, st);
         return;
     }
-    const size_t G = (size_t)h->bs.GT;
-    cudaMemsetAsync(h->d.fcnt, 0, sizeof(int32_t) * (L.TF ? L.TF * G : 1), st);
     cudaMemsetAsync(h->d.heads, 0, sizeof(int32_t), st);
     cudaMemsetAsync(h->d.abort_word, 0, sizeof(int32_t), st);
-    if (h->nbig) {
+    {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
+        launch_batch_reset(h->bs, h->d, L.P, 0, st);  // the words the sweep's tasks poll
         launch_batch_load(h->g, h->bs, h->big_dev, h->nbig, st);
     }
     {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
-        launch_batch_fwd(h->g, h->bs, h->d, h->grid_fwd, gamma, lse, st);
+        launch_batch_fwd(h->g, h->bs, h->d, h->grid_fwd, gamma, lse, h->stall_task, st);
     }
     ProfScope ps(h, &h->prof_fwd, STA_PROF_ENDPOINTS, st);
     launch_batch_endpoints(h->g, h->bs, gamma, lse, st);
@@ -304,6 +303,7 @@ void enqueue_backward_batch(StaHandle* h, int mode, float gamma, cudaStream_t st
     cudaMemsetAsync((mode & 2) ? h->d.acnt : h->d.rcnt, 0, sizeof(int32_t) * (L.TB ? L.TB * (size_t)h->bs.GT : 1), st);
     cudaMemsetAsync(h->d.heads + ((mode & 2) ? 2 : 1), 0, sizeof(int32_t), st);
     ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJOINT : STA_PROF_REQUIRED, st);
+    launch_batch_reset(h->bs, h->d, L.P, mode, st);  // the words the sweep's tasks poll
     launch_batch_bwd(h->g, h->bs, h->d, h->grid_bwd, gamma, mode, st);
 }
 
@@ -826,7 +826,7 @@ StaStatus sta_forward(StaHandle* h, uint32_t flags, float gamma, void* stream) {
         // into the budget, the sweep ends early and the expiry is reported
         h->expire_next = false;
         const Layout& L = h->lay;
-        if (h->schedule == STA_SCHED_DATAFLOW) {  // the sweep polls data words: stall its last task
+        if (h->schedule == STA_SCHED_DATAFLOW || h->batch()) {  // the sweep polls data words: stall its last task
             if (L.TF == 0) return set_err(STA_ERR_STATE, "no forward task");
             h->stall_task = L.TF - 1;
             enqueue_forward(h, lse, gamma, st);

@@ -96,13 +96,6 @@ __device__ __forceinline__ FwdPre fwd_pre(const DevNet& g, const DfState& d, int
 // arcs and asserted drivers read a harmless valid address) and results are
 // selected, so a warp never splits into groups whose memory round trips would
 // run one after another.  `dp` must be a valid pin.
-__device__ __forceinline__ float ld_relaxed_f(const float* p) {
-    float v;
-    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ bool written(float v) { return __float_as_uint(v) != kUnwritten; }
 
 // The wait of a forward task: the fanin arrival / slew / LSE arrival words this
 // lane reads, polled (strong relaxed loads, all lanes together) until every one
@@ -130,7 +123,7 @@ __device__ __forceinline__ void fwd_fanin(const DevState& s, const FwdPre& f, in
             ok = ok && (!need || (written(sin[k]) && written(ain[k]) && (!lse || !el || written(zin[k]))));
         }
         if (__all_sync(kFull, ok)) return;
-        __nanosleep(64);
+        __nanosleep(STA_POLL_NS);
         if ((it & 63) == 63) {
             if (__any_sync(kFull, ld_relaxed(abort_word) != 0)) return;
             const unsigned long long now = __shfl_sync(kFull, global_ns(), 0);
@@ -152,10 +145,6 @@ __device__ __forceinline__ void st_relaxed_f4(float* p, float4 v) {
     asm volatile("st.relaxed.gpu.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
                  "f"(v.w)
                  : "memory");
-}
-
-__device__ __forceinline__ void st_relaxed_f(float* p, float v) {
-    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
 __device__ __forceinline__ void st_relaxed_f2(float* p, float2 v) {
@@ -446,7 +435,7 @@ __device__ __forceinline__ SinkWords sink_wait(const DevState& s, int p, bool ne
             ok = ok && written(w.ga.x) && written(w.ga.y) && written(w.gs.x) && written(w.gs.y);
         }
         if (__all_sync(kFull, ok || !need)) return w;
-        __nanosleep(64);
+        __nanosleep(STA_POLL_NS);
         if ((it & 63) == 63) {
             if (__any_sync(kFull, ld_relaxed(abort_word) != 0)) return w;
             const unsigned long long now = __shfl_sync(kFull, global_ns(), 0);
@@ -814,7 +803,7 @@ __device__ void bwd_df_driver(const DevNet& g, const DevState& s, const DfState&
                 }
             }
             if (__all_sync(kFull, ok)) break;
-            __nanosleep(64);
+            __nanosleep(STA_POLL_NS);
             if ((it & 63) == 63) {
                 if (__any_sync(kFull, ld_relaxed(d.abort_word) != 0)) break;
                 const unsigned long long now = __shfl_sync(kFull, global_ns(), 0);

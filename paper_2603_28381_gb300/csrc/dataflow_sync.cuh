@@ -13,10 +13,17 @@
 
 #include <cuda_runtime.h>
 
+#include "sta_internal.h"
+
 namespace sta {
 namespace {
 
 constexpr unsigned long long kWaitBudgetNs = 1000000000ull;  // 1 s per wait
+
+// pause between two polls of a wait (ns; a scheduling hint to the SM)
+#ifndef STA_POLL_NS
+#define STA_POLL_NS 256
+#endif
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -49,7 +56,7 @@ __device__ __forceinline__ void wait_ready(const int32_t* cnt, int t, int need, 
     if (__all_sync(0xffffffffu, ld_acquire(cnt + t) >= need)) return;
     unsigned long long t0 = 0;
     for (unsigned it = 1;; ++it) {
-        __nanosleep(64);
+        __nanosleep(STA_POLL_NS);
         if (__all_sync(0xffffffffu, ld_relaxed(cnt + t) >= need)) {
             (void)ld_acquire(cnt + t);
             return;
@@ -63,6 +70,51 @@ __device__ __forceinline__ void wait_ready(const int32_t* cnt, int t, int need, 
                 if ((threadIdx.x & 31) == 0) {
                     atomicExch(abort_word, 1);      // ends the other waits of this launch
                     atomicExch(abort_word + 1, 1);  // sticky until the host reports it
+                }
+                __syncwarp();
+                return;
+            }
+        }
+    }
+}
+
+
+// ---- waiting on data words -------------------------------------------------
+// A word that a sweep's tasks poll is set to kUnwritten (a NaN) before the
+// sweep and written exactly once during it with a strong relaxed store; a
+// waiting task loads it with strong relaxed loads until it holds a value.  A
+// word carries its own value, so no fence or counter is needed, and by
+// per-location coherence a word once seen written stays written for the thread.
+__device__ __forceinline__ float ld_relaxed_f(const float* p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_f(float* p, float v) {
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ bool written(float v) { return __float_as_uint(v) != kUnwritten; }
+
+// Poll until ready() holds on every lane of the warp (ready() reloads the
+// lane's words each call).  Bounded like wait_ready: after kWaitBudgetNs, or
+// once any wait of the launch has expired, it sets the abort words and returns.
+template <typename F>
+__device__ __forceinline__ void poll_words(F&& ready, int32_t* abort_word) {
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        if (__all_sync(0xffffffffu, ready())) return;
+        __nanosleep(STA_POLL_NS);
+        if ((it & 63) == 63) {
+            if (__any_sync(0xffffffffu, ld_relaxed(abort_word) != 0)) return;
+            const unsigned long long now = __shfl_sync(0xffffffffu, global_ns(), 0);
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kWaitBudgetNs) {
+                if ((threadIdx.x & 31) == 0) {
+                    atomicExch(abort_word, 1);
+                    atomicExch(abort_word + 1, 1);
                 }
                 __syncwarp();
                 return;

@@ -101,7 +101,7 @@ constexpr int kPlacePerWarp = 8;       // sweep tasks: 8 placements x 4 conditio
 int batch_max_blocks(int fwd);
 void launch_batch_load(const DevNet& g, const BatchState& bs, const int32_t* big_nets, int nbig, cudaStream_t st);
 void launch_batch_fwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int lse,
-                      cudaStream_t st);
+                      int stall_task, cudaStream_t st);
 void launch_batch_endpoints(const DevNet& g, const BatchState& bs, float gamma, int lse, cudaStream_t st);
 // level-synchronous batched sweeps
 void launch_batch_load_small(const DevNet& g, const BatchState& bs, int big, cudaStream_t st);
@@ -112,6 +112,8 @@ void launch_batch_bwd_level(const DevNet& g, const BatchState& bs, const DfState
                             int mode, cudaStream_t st);
 void launch_batch_bwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int mode,
                       cudaStream_t st);
+// marks the words a batched dataflow sweep polls (what: 0 forward, else the backward mode)
+void launch_batch_reset(const BatchState& bs, const DfState& d, int P, int what, cudaStream_t st);
 void launch_batch_xy_in(const BatchState& bs, const int32_t* pin_int, int P, const float2* xy_user, cudaStream_t st);
 void launch_batch_out(const BatchState& bs, const int32_t* pin_int, int P, const float* in, int K, float* out,
                       cudaStream_t st);
