@@ -268,6 +268,17 @@ StaStatus sta_query_endpoints(StaHandle *h, float *slack, int on_device, void *s
 StaStatus sta_levelize(const StaNetlistDesc *nl, int32_t *net_level, int32_t *num_levels,
                        int32_t *net_order, int32_t *pin_order);
 
+/* Host-only planning of the dataflow task lists for a task shape (no device
+ * use): packed tasks of nets of at most chunk + 1 pins (while their pins fit in
+ * tile_pins, at most tile_nets nets; a larger net alone), larger nets split into
+ * chunks of `chunk` sinks.  The builder checks that every task depends only on
+ * tasks listed before it and that every written pin has exactly one forward
+ * task (INVALID_ARG "internal: ..." otherwise).  out8: forward tasks, backward
+ * tasks, partial records, forward chunk tasks, most pins in a packed task, most
+ * nets in a packed task, forward dependency edges, nets split into chunks. */
+StaStatus sta_plan_tasks(const StaNetlistDesc *nl, const StaLibrary *lib, int32_t tile_pins,
+                         int32_t tile_nets, int32_t chunk, int64_t *out8);
+
 /* Sizes of a created handle: [0] pins, [1] nets (including one internal
  * net per cell output that drives no net), [2] levels, [3] arcs, [4] endpoints,
  * [5] warp tasks, [6] block tasks, [7] device bytes held. */

@@ -96,6 +96,8 @@ def _load() -> ctypes.CDLL:
         "sta_query_endpoints": ([H, _p, ctypes.c_int, _p], ctypes.c_int),
         "sta_levelize": ([ctypes.POINTER(StaNetlistDesc), _p, _p, _p, _p], ctypes.c_int),
         "sta_query_sizes": ([H, _p], ctypes.c_int),
+        "sta_plan_tasks": ([ctypes.POINTER(StaNetlistDesc), ctypes.POINTER(StaLibrary), _i32, _i32, _i32, _p],
+                           ctypes.c_int),
         "sta_query_profile": ([H, _p, _p], ctypes.c_int),
         "sta_endpoint_summary_noalloc": ([_p, _p, _i32, _p, _p, _i32, ctypes.c_float, _p, _p, _p],
                                          ctypes.c_int),
@@ -129,7 +131,7 @@ EXPORTS = ("sta_create", "sta_set_positions", "sta_forward", "sta_backward_grad"
            "sta_synchronize", "sta_debug_expire_wait", "sta_autotune", "sta_server_create",
            "sta_server_add_netlist", "sta_server_submit", "sta_server_poll", "sta_server_stats",
            "sta_server_destroy", "sta_server_clock", "sta_server_netlist_bytes", "sta_query_net_rc",
-           "sta_ablation_net_rc",
+           "sta_ablation_net_rc", "sta_plan_tasks",
            "sta_last_error", "sta_abi_version", "sta_endpoint_summary_noalloc")
 
 
@@ -267,6 +269,18 @@ def sta_query_pins(h: int, at: int, slew: int, rat: int, ats: int, slack: int, o
 
 def sta_query_endpoints(h: int, out_ptr: int, on_device: int, stream: int) -> None:
     _check(_lib.sta_query_endpoints(h, out_ptr, on_device, stream), "sta_query_endpoints")
+
+
+def sta_plan_tasks(nl, lib, tile_pins: int, tile_nets: int, chunk: int):
+    """Host-only task plan of a netlist for a task shape (no device use)."""
+    keep = _Keep()
+    d = netlist_desc(nl, keep)
+    l = library_desc(lib, keep)
+    out = np.zeros(8, np.int64)
+    _check(_lib.sta_plan_tasks(ctypes.byref(d), ctypes.byref(l), int(tile_pins), int(tile_nets), int(chunk),
+                               out.ctypes.data), "sta_plan_tasks")
+    return dict(zip(("forward_tasks", "backward_tasks", "partials", "chunks", "max_pins", "max_nets",
+                     "forward_edges", "split_nets"), out.tolist()))
 
 
 def sta_query_sizes(h: int):

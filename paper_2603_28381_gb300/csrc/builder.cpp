@@ -314,6 +314,11 @@ StaStatus build_tasks(Layout& o, const TaskShape& sh, std::string& err) {
     o.big_nets = bigs;
     o.TF = (int32_t)(o.ftask.size() / 4);
     o.lvl_ftask[o.L] = o.TF;
+    // every pin on a net has exactly one forward task (its net's task, or the
+    // chunk holding the sink; a large net's driver belongs to its chunks)
+    for (int32_t n = 0; n < V; ++n)
+        for (int32_t p = o.net_ptr[n] + 1; p < o.net_ptr[n + 1]; ++p)
+            if (pin_fprod[p] < 0) return err = "internal: a sink without a forward task", STA_ERR_INVALID_ARG;
     o.arc_prod.resize(A);
     for (int32_t a = 0; a < A; ++a) o.arc_prod[a] = pin_fprod[o.arc_pin[a]];
 

@@ -743,12 +743,12 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         cudaEventCreateWithFlags(&h->ev_fwd, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_bwd, cudaEventDisableTiming) != cudaSuccess)
         return fail(set_err(STA_ERR_CUDA, "stream/event creation failed"));
-    {   // dataflow grids: the whole GPU for the forward sweep; half each for the
-        // required-time and adjoint sweeps, which run concurrently
+    {   // dataflow grids: every block that fits (a required-time sweep flushed for a
+        // query and an adjoint sweep on another stream then run one after the other)
         const int fmax = bat ? batch_max_blocks(1) : dataflow_max_blocks(1);
         const int bmax = bat ? batch_max_blocks(0) : dataflow_max_blocks(0);
         h->grid_fwd = fmax > 0 ? fmax : 1;
-        h->grid_bwd = bat ? (bmax > 0 ? bmax : 1) : (bmax > 1 ? bmax / 2 : 1);
+        h->grid_bwd = bmax > 0 ? bmax : 1;
         if (opts && opts->grid_blocks > 0) {
             h->grid_fwd = std::min(h->grid_fwd, (int)opts->grid_blocks);
             h->grid_bwd = std::min(h->grid_bwd, (int)opts->grid_blocks);
@@ -1258,6 +1258,45 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
         }
     }
     return STA_OK;
+}
+
+StaStatus sta_plan_tasks(const StaNetlistDesc* nl, const StaLibrary* lib, int32_t tile_pins, int32_t tile_nets,
+                         int32_t chunk, int64_t* o) {
+    if (!nl || !lib || !o) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    try {
+        Layout L;
+        std::string err;
+        StaStatus st = build_layout(*nl, *lib, L, err);
+        if (st != STA_OK) return set_err(st, err);
+        TaskShape sh;
+        sh.pack_pins = tile_pins;
+        sh.pack_nets = tile_nets;
+        sh.chunk = chunk;
+        sh.big = chunk + 1;
+        st = build_tasks(L, sh, err);
+        if (st != STA_OK) return set_err(st, err);
+        int64_t chunks = 0, max_pins = 0, max_nets = 0, edges_f = (int64_t)L.f_out.size();
+        for (int32_t t = 0; t < L.TF; ++t) {
+            const int32_t nn = L.ftask[4 * t + 1];
+            if (nn < 0) {
+                ++chunks;
+                continue;
+            }
+            max_nets = std::max<int64_t>(max_nets, nn);
+            max_pins = std::max<int64_t>(max_pins, L.ftask[4 * t + 3]);
+        }
+        o[0] = L.TF;
+        o[1] = L.TB;
+        o[2] = L.npart;
+        o[3] = chunks;
+        o[4] = max_pins;
+        o[5] = max_nets;
+        o[6] = edges_f;
+        o[7] = (int64_t)L.big_nets.size();
+        return STA_OK;
+    } catch (const std::bad_alloc&) {
+        return set_err(STA_ERR_OOM, "host allocation failed");
+    }
 }
 
 StaStatus sta_query_sizes(const StaHandle* h, int64_t* o) {

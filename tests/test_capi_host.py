@@ -111,3 +111,24 @@ def test_product_path_fails_loudly_without_gpu(sta):
     with pytest.raises(sta.StaError) as e:
         sta._sta.sta_create(w.netlist, w.library)
     assert e.value.status == 4  # STA_ERR_CUDA, no CPU fallback
+
+
+@pytest.mark.parametrize("tile_pins,tile_nets,chunk", [(32, 8, 32), (1, 1, 1), (4, 1 << 20, 16), (64, 4, 200)])
+def test_task_plans_cover_every_sink_in_dependency_order(tile_pins, tile_nets, chunk):
+    # the builder rejects any plan whose tasks depend on later tasks or leave a
+    # sink without a forward task; here the counts are checked against the netlist
+    import numpy as np
+    import netgen
+    from paper_2603_28381_gb300 import _sta
+    w = netgen.superblue_like(3, scale=0.02, depth=40)
+    nl = w.netlist
+    plan = _sta.sta_plan_tasks(nl, w.library, tile_pins, tile_nets, chunk)
+    fan = np.diff(nl.net_ptr) - 1  # sinks per description net
+    big = fan + 1 > chunk + 1
+    assert plan["split_nets"] == int(big.sum())
+    assert plan["chunks"] == int(np.ceil(fan[big] / chunk).sum())
+    assert plan["partials"] == plan["chunks"]                       # one partial per backward chunk
+    # backward: a task per packed group, a partial, a driver and a gradient task per chunked net
+    assert plan["backward_tasks"] == (plan["forward_tasks"] - plan["chunks"]) + 2 * plan["chunks"] + plan["split_nets"]
+    assert plan["max_nets"] <= tile_nets
+    assert plan["max_pins"] <= max(tile_pins, chunk + 1)
