@@ -205,9 +205,10 @@ StaStatus sta_synchronize(StaHandle *h);
 
 /* Test hook for the bounded waits (dataflow sweeps only: STA_SCHED_DATAFLOW, or
  * STA_SCHED_BATCH with STA_BATCH_DATAFLOW; else STA_ERR_STATE):
- * the next sta_forward runs with its last dependent task waiting for one
- * producer more than it has, so that wait expires after its 1 s budget and the
- * next synchronizing call returns STA_ERR_TIMEOUT.  Later calls are unaffected. */
+ * in the next sta_forward the wait of the sweep's last task for its input
+ * words never succeeds, so it expires after its 1 s budget (the sweep ends with
+ * invalid results) and the next synchronizing call returns STA_ERR_TIMEOUT.
+ * No fault is involved; later calls are unaffected. */
 StaStatus sta_debug_expire_wait(StaHandle *h);
 
 /* Autotuner of the batched schedule (STA_SCHED_BATCH only, else STATE): for

@@ -161,8 +161,8 @@ class StaEngine:
         return float(ms.value)
 
     def _debug_expire_wait(self) -> None:
-        """Test hook: the next forward runs one dependency wait into its budget
-        (sta_debug_expire_wait)."""
+        """Test hook: in the next forward one task's wait never succeeds and
+        runs into its budget (sta_debug_expire_wait)."""
         _sta.sta_debug_expire_wait(self.h)
 
     def summary(self, stream=None):

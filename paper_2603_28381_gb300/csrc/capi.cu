@@ -505,9 +505,8 @@ StaStatus set_tasks(StaHandle* h, const TaskShape& sh) {
         return set_err(STA_ERR_INVALID_ARG, "num_placements too large for this netlist");
     DfState& d = h->d;
     for (const void* p : {(const void*)d.ftask, (const void*)d.arc_prod, (const void*)d.btask, (const void*)d.baux,
-                          (const void*)d.pin_cons, (const void*)d.f_indeg, (const void*)d.f_out_ptr,
-                          (const void*)d.f_out, (const void*)d.b_indeg, (const void*)d.b_out_ptr, (const void*)d.b_out,
-                          (const void*)d.fcnt, (const void*)d.rcnt, (const void*)d.acnt, (const void*)h->bs.part,
+                          (const void*)d.pin_cons, (const void*)d.b_indeg, (const void*)d.b_out_ptr,
+                          (const void*)d.b_out, (const void*)d.rcnt, (const void*)d.acnt, (const void*)h->bs.part,
                           (const void*)h->bs.rpart, (const void*)h->big_dev})
         h->release(p);
     StaStatus st = STA_OK;
@@ -524,13 +523,9 @@ StaStatus set_tasks(StaHandle* h, const TaskShape& sh) {
     d.btask = reinterpret_cast<const int4*>(cp);
     TSTEP(h->upload(d.baux, L.baux));
     TSTEP(h->upload(d.pin_cons, L.pin_cons));
-    TSTEP(h->upload(d.f_indeg, L.f_indeg));
-    TSTEP(h->upload(d.f_out_ptr, L.f_out_ptr));
-    TSTEP(h->upload(d.f_out, L.f_out));
     TSTEP(h->upload(d.b_indeg, L.b_indeg));
     TSTEP(h->upload(d.b_out_ptr, L.b_out_ptr));
     TSTEP(h->upload(d.b_out, L.b_out));
-    TSTEP(h->alloc(d.fcnt, (size_t)L.TF * GT));
     TSTEP(h->alloc(d.rcnt, (size_t)L.TB * GT));
     TSTEP(h->alloc(d.acnt, (size_t)L.TB * GT));
     TSTEP(h->alloc(h->bs.part, (size_t)L.npart * kPartFloats * h->bs.Bp));
@@ -682,15 +677,11 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         STEP(h->upload(d.baux, L.baux));
         STEP(h->upload(d.pin_cons, L.pin_cons));
         STEP(h->upload(d.pin_keep, L.pin_keep));
-        STEP(h->upload(d.f_indeg, L.f_indeg));
-        STEP(h->upload(d.f_out_ptr, L.f_out_ptr));
-        STEP(h->upload(d.f_out, L.f_out));
         STEP(h->upload(d.b_indeg, L.b_indeg));
         STEP(h->upload(d.b_out_ptr, L.b_out_ptr));
         STEP(h->upload(d.b_out, L.b_out));
     }
     const size_t G = bat ? (size_t)(h->B + 31) / 32 * (32 / kPlacePerWarp) : 1;
-    STEP(h->alloc(d.fcnt, L.TF * G));
     STEP(h->alloc(d.rcnt, L.TB * G));
     STEP(h->alloc(d.acnt, L.TB * G));
     STEP(h->alloc(d.heads, 4));
@@ -826,27 +817,13 @@ StaStatus sta_forward(StaHandle* h, uint32_t flags, float gamma, void* stream) {
         // into the budget, the sweep ends early and the expiry is reported
         h->expire_next = false;
         const Layout& L = h->lay;
-        if (h->schedule == STA_SCHED_DATAFLOW || h->batch()) {  // the sweep polls data words: stall its last task
-            if (L.TF == 0) return set_err(STA_ERR_STATE, "no forward task");
-            h->stall_task = L.TF - 1;
-            enqueue_forward(h, lse, gamma, st);
-            h->stall_task = -1;
-            StaStatus s2 = check_launch();
-            if (s2 != STA_OK) return s2;
-        } else {  // dependency counters: one producer more than the task has
-            int task = -1;
-            for (int t = L.TF - 1; t >= 0 && task < 0; --t)
-                if (L.f_indeg[t] > 0) task = t;
-            if (task < 0) return set_err(STA_ERR_STATE, "no forward task has producers");
-            int32_t* indeg = const_cast<int32_t*>(h->d.f_indeg) + task;
-            h->pinned[1] = L.f_indeg[task] + 1;
-            h->pinned[2] = L.f_indeg[task];
-            CUDA_TRY(cudaMemcpyAsync(indeg, h->pinned + 1, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-            enqueue_forward(h, lse, gamma, st);
-            StaStatus s2 = check_launch();
-            if (s2 != STA_OK) return s2;
-            CUDA_TRY(cudaMemcpyAsync(indeg, h->pinned + 2, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        }
+        // (the levels schedules reject the hook: they never wait)
+        if (L.TF == 0) return set_err(STA_ERR_STATE, "no forward task");
+        h->stall_task = L.TF - 1;  // its wait for its fanin words never succeeds
+        enqueue_forward(h, lse, gamma, st);
+        h->stall_task = -1;
+        StaStatus s2 = check_launch();
+        if (s2 != STA_OK) return s2;
     } else if (h->use_graphs) {
         if (!h->gx_fwd[lse] || h->gx_fwd_gamma[lse] != gamma) {
             StaStatus s2 = capture(h, &h->gx_fwd[lse], [&](cudaStream_t c) { enqueue_forward(h, lse, gamma, c); });

@@ -5,23 +5,25 @@
 // dependent loads of the level).  Here each sweep is ONE kernel: the builder
 // lists the warp-sized tasks of the sweep in a topological order (the levels
 // in order, or reversed), every warp takes the next task from a queue
-// (atomicAdd on a head), waits only for the specific tasks that produce what
-// it reads and then signals the tasks that consume its results: every task has
-// a counter that each of its producers increments (red.release at GPU scope)
-// and that one lane polls until it reaches the task's producer count
-// (ld.acquire once reached).  One polled word per waiting warp keeps the
-// polling traffic far below the memory system's capacity.  Work of different
-// levels overlaps; no grid-wide barrier exists.  A waiting warp only ever waits for tasks with smaller
-// indices, which warps that are already running hold, so the sweep always
-// progresses; every wait is nevertheless bounded in time and reports expiry
-// through an abort word instead of spinning forever.
+// (atomicAdd on a head) and waits only for the data it reads: the words its
+// producers write (arrival / slew / LSE arrival of its fanin pins in the
+// forward; required times and adjoints of its sinks, or a large net's partial
+// records, in the backward).  Those words are reset to a NaN marker before the
+// sweep and written once with strong relaxed stores, so the waiting warp polls
+// them directly (strong relaxed loads, the whole warp together) and needs no
+// counter, release fence or acquire.  Work of different levels overlaps; no
+// grid-wide barrier exists.  A waiting warp only ever waits for tasks with
+// smaller indices, which warps that are already running hold, so the sweep
+// always progresses; every wait is nevertheless bounded in time and reports
+// expiry through an abort word instead of spinning forever.
 //
 // Tasks are one warp each: packed small nets (as in the level schedule), and,
 // for nets of more than 32 pins, 32-sink chunks.  In the forward pass a chunk
 // re-evaluates the net's driver cell (cheap) with the load computed by a
 // prologue kernel; in the backward pass a large net becomes partial-reduction
 // chunks, one driver task that combines them in a fixed order, and gradient
-// chunks, so every reduction stays deterministic.
+// chunks (which wait on a counter the driver task releases), so every
+// reduction stays deterministic.
 #include "dataflow_sync.cuh"
 #include "device_common.cuh"
 

@@ -1,12 +1,14 @@
-// dataflow_sync.cuh -- task queue, dependency counters and bounded waits of
-// the persistent dataflow kernels (single-placement and batched schedules).
+// dataflow_sync.cuh -- task queue, waits on data words, dependency counters
+// and their bounds, for the persistent dataflow kernels (single-placement and
+// batched schedules).
 //
-// A sweep's tasks are listed in a topological order.  Warps take the next
-// task from a queue head (atomicAdd); a task waits until all its producers
-// have incremented its counter (red.release at GPU scope, acquired once the
-// count is reached) and then increments the counters of its consumers.  A
-// waiting warp only waits for tasks with smaller queue indices, which running
-// warps hold, so a sweep always progresses; every wait is still bounded in time.
+// A sweep's tasks are listed in a topological order and taken from a queue
+// head (atomicAdd).  A task waits for the data it reads: words reset to
+// kUnwritten before the sweep and written once (poll_words), or, for the
+// gradient chunks of a large net, a counter its driver step increments with a
+// release (wait_ready / signal_consumers).  A waiting warp only waits for tasks
+// with smaller queue indices, which running warps hold, so a sweep always
+// progresses; every wait is still bounded in time.
 #pragma once
 
 #include <cstdint>

@@ -47,22 +47,21 @@ struct DevState {
     float* params;     // [4] w_tns, w_wns
 };
 
-// Dataflow schedule: task lists, dependency counters and queue heads.
+// Dataflow schedule: task lists, the counters of the large nets' gradient
+// chunks, queue heads.  Tasks wait on the data words they read (reset to
+// kUnwritten before each sweep); only a gradient chunk waits on a counter,
+// which its net's driver step releases.
 struct DfState {
     const int4* ftask;       // [TF]
     const int32_t* arc_prod; // [A]
     const int4* btask;       // [TB]
     const int32_t* baux;     // [TB]
     const int32_t* pin_cons; // [P]
-    const int32_t* f_indeg;  // [TF] producers each forward task waits for
-    const int32_t* f_out_ptr;// [TF+1]
-    const int32_t* f_out;    // consumers each forward task signals
-    const int32_t* b_indeg;  // [TB]
+    const int32_t* b_indeg;  // [TB] producers of each backward task (a gradient chunk: its driver step)
     const int32_t* b_out_ptr;// [TB+1]
-    const int32_t* b_out;
-    int32_t* fcnt;           // [TF] arrived producers, forward sweep
-    int32_t* rcnt;           // [TB] arrived producers, required-time sweep
-    int32_t* acnt;           // [TB] arrived producers, adjoint sweep
+    const int32_t* b_out;    // consumers each backward task would signal (driver steps do)
+    int32_t* rcnt;           // [TB x groups] arrived producers, required-time sweep
+    int32_t* acnt;           // [TB x groups] arrived producers, adjoint sweep
     int32_t* heads;          // [4] queue heads: forward, required time, adjoint
     float* rpart;            // [npart * kPartFloats] partials, required-time sweep
     float* apart;            // [npart * kPartFloats] partials, adjoint sweep

@@ -1,7 +1,7 @@
 """Bounded dependency waits of the dataflow schedule.
 
-A host-side hook raises one forward task's producer count by one, so its wait can
-never be satisfied: the wait must give up after its budget, the sweep must end,
+A host-side hook makes one forward task's wait for its input words never
+succeed: the wait must give up after its budget, the sweep must end,
 the next synchronizing call must report STA_ERR_TIMEOUT once, and the handle and
 the CUDA context must stay usable (the next analysis matches the oracle again).
 No fault is injected on the device: the wait simply runs out.
