@@ -101,6 +101,8 @@ def algorithmic_bytes(sizes, S, schedule="dataflow", big=(0, 0)):
 
     fwd = 60 * A + 60 * N + 48 * S
     out = {
+        # marking the words the dataflow sweeps poll: overhead, no algorithmic bytes
+        "reset": 0,
         # xy gather: index 4P + positions read 8P + write 8P
         "positions": 20 * P,
         # per endpoint: pin 4, constraint 16, AT 16, LSE-AT 8, slack write 8
@@ -139,7 +141,7 @@ def algorithmic_bytes_batch(sizes, S, B, big=(0, 0)):
     # driver LSE-AT 8 + late slew 8 + xy 8 + load 4, RAT write 16, grad write 8; per arc: fanin
     # slews 16, LSE-AT 8, RAT + adjoint writes 32
     bwd = B * (56 * S + 52 * N + 56 * A) + topo
-    return {"positions": 16 * B * P + 4 * P, "net_rc": B * (8 * big[1] + 12 * big[0]),
+    return {"reset": 0, "positions": 16 * B * P + 4 * P, "net_rc": B * (8 * big[1] + 12 * big[0]),
             "forward": fwd, "endpoints": B * 32 * E + 20 * E, "required": 0, "seed": 8 * B,
             "adjoint": bwd, "output": 16 * B * P + 4 * P}
 

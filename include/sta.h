@@ -295,7 +295,8 @@ enum {
     STA_PROF_SEED = 5,       /* loss weights (and, LEVELS only, endpoint seeds) */
     STA_PROF_ADJOINT = 6,    /* adjoint sweep */
     STA_PROF_OUTPUT = 7,     /* BATCH: gradient from device layout to [B][num_pins][2] */
-    STA_PROF_KINDS = 8
+    STA_PROF_RESET = 8,      /* dataflow sweeps: marking the words their tasks poll as unwritten */
+    STA_PROF_KINDS = 9
 };
 
 /* Per-kind launch counts of one set_positions + forward(LSE|RAT) +

@@ -22,7 +22,7 @@
  *     adjoint of that loss with respect to every pin position.
  *
  * It walks the pin graph in Kahn topological order, not the GPU's levels.
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - segment of a table axis = largest k in [0,5] with idx[k] <= v (right
  *     continuous); outside the index range the edge segment is extended
  *     linearly (no clamping of the interpolated value).

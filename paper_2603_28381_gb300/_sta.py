@@ -45,7 +45,7 @@ class StaOptions(ctypes.Structure):
                 ("tile_pins", _i32), ("chunk", _i32), ("batch_sweep", _i32), ("grid_blocks", _i32)]
 
 
-PROF_KINDS = ("positions", "net_rc", "forward", "endpoints", "required", "seed", "adjoint", "output")
+PROF_KINDS = ("positions", "net_rc", "forward", "endpoints", "required", "seed", "adjoint", "output", "reset")
 SCHED_DATAFLOW = 0
 SCHED_LEVELS = 1
 SCHED_BATCH = 2

@@ -206,8 +206,11 @@ void enqueue_forward_dataflow(StaHandle* h, int lse, float gamma, cudaStream_t s
     cudaMemsetAsync(h->d.heads, 0, sizeof(int32_t), st);
     cudaMemsetAsync(h->d.abort_word, 0, sizeof(int32_t), st);
     {
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_RESET, st);
+        launch_fwd_reset(h->s, h->d, L.P, st);  // the words the sweep's tasks poll
+    }
+    {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
-        launch_fwd_reset(h->s, h->d, L.P, st);           // the words the sweep's tasks poll
         launch_rc(h->g, h->s, 0, L.lvl_ctask[L.L], st);  // load and wire RC of the nets > 32 pins
     }
     {
@@ -224,8 +227,11 @@ void enqueue_backward_dataflow(StaHandle* h, int mode, float gamma, cudaStream_t
     pr->next = 0;
     cudaMemsetAsync((mode & 2) ? h->d.acnt : h->d.rcnt, 0, sizeof(int32_t) * (L.TB ? L.TB : 1), st);
     cudaMemsetAsync(h->d.heads + ((mode & 2) ? 2 : 1), 0, sizeof(int32_t), st);
+    {
+        ProfScope ps(h, pr, STA_PROF_RESET, st);
+        launch_bwd_reset(h->s, h->d, L.P, mode, st);  // the words the sweep's tasks poll
+    }
     ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJOINT : STA_PROF_REQUIRED, st);
-    launch_bwd_reset(h->s, h->d, L.P, mode, st);  // the words the sweep's tasks poll
     launch_bwd_dataflow(h->g, h->s, h->d, h->grid_bwd, gamma, mode, st);
 }
 
@@ -275,8 +281,11 @@ void enqueue_forward_batch(StaHandle* h, int lse, float gamma, cudaStream_t st) 
     cudaMemsetAsync(h->d.heads, 0, sizeof(int32_t), st);
     cudaMemsetAsync(h->d.abort_word, 0, sizeof(int32_t), st);
     {
-        ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_RESET, st);
         launch_batch_reset(h->bs, h->d, L.P, 0, st);  // the words the sweep's tasks poll
+    }
+    if (h->nbig) {
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
         launch_batch_load(h->g, h->bs, h->big_dev, h->nbig, st);
     }
     {
@@ -302,8 +311,11 @@ void enqueue_backward_batch(StaHandle* h, int mode, float gamma, cudaStream_t st
     }
     cudaMemsetAsync((mode & 2) ? h->d.acnt : h->d.rcnt, 0, sizeof(int32_t) * (L.TB ? L.TB * (size_t)h->bs.GT : 1), st);
     cudaMemsetAsync(h->d.heads + ((mode & 2) ? 2 : 1), 0, sizeof(int32_t), st);
+    {
+        ProfScope ps(h, pr, STA_PROF_RESET, st);
+        launch_batch_reset(h->bs, h->d, L.P, mode, st);  // the words the sweep's tasks poll
+    }
     ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJOINT : STA_PROF_REQUIRED, st);
-    launch_batch_reset(h->bs, h->d, L.P, mode, st);  // the words the sweep's tasks poll
     launch_batch_bwd(h->g, h->bs, h->d, h->grid_bwd, gamma, mode, st);
 }
 
@@ -749,7 +761,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     if (h->profile) {  // event pairs for every launch of each sequence, made before any capture
         const size_t nl = (size_t)L.L;
         const std::pair<StaHandle::Prof*, size_t> sizes[] = {
-            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 2}, {&h->prof_rat, 2 * nl + 2}, {&h->prof_adj, 2 * nl + 2},
+            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 3}, {&h->prof_rat, 2 * nl + 2}, {&h->prof_adj, 2 * nl + 2},
             {&h->prof_out, 1}};
         for (const auto& ps : sizes) {
             ps.first->kind.assign(ps.second, 0);
@@ -1193,6 +1205,7 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
     launches[STA_PROF_POSITIONS] = L.P > 0 ? 1 : 0;
     launches[STA_PROF_ENDPOINTS] = 2;
     launches[STA_PROF_OUTPUT] = (h->batch() && L.P > 0) ? 1 : 0;
+    launches[STA_PROF_RESET] = 0;
     if (h->batch() && h->bsweep == STA_BATCH_LEVELS) {
         std::vector<std::array<int, 6>> ph;
         batch_bwd_phases(L, 3, ph);
@@ -1204,18 +1217,20 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
         launches[STA_PROF_SEED] = 1;
         launches[STA_PROF_ADJOINT] = nb;
     } else if (h->batch()) {
+        // each sweep is preceded by the reset of the words its tasks poll
         launches[STA_PROF_NET_RC] = h->nbig > 0 ? 1 : 0;
         launches[STA_PROF_FORWARD] = L.TF > 0 ? 1 : 0;
         launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 1 : 0;
         launches[STA_PROF_SEED] = 1;
         launches[STA_PROF_ADJOINT] = L.TB > 0 ? 1 : 0;
+        launches[STA_PROF_RESET] = 1 + launches[STA_PROF_REQUIRED] + launches[STA_PROF_ADJOINT];
     } else if (h->schedule == STA_SCHED_DATAFLOW) {
-        // each sweep is preceded by the reset of the words its tasks poll
-        launches[STA_PROF_NET_RC] = (L.P > 0 ? 1 : 0) + (nc > 0 ? 1 : 0);
+        launches[STA_PROF_NET_RC] = nc > 0 ? 1 : 0;
         launches[STA_PROF_FORWARD] = L.TF > 0 ? 1 : 0;
-        launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 2 : 0;  // fused into the adjoint sweep
+        launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 1 : 0;  // fused into the adjoint sweep
         launches[STA_PROF_SEED] = 1;  // weights
-        launches[STA_PROF_ADJOINT] = L.TB > 0 ? 2 : 0;
+        launches[STA_PROF_ADJOINT] = L.TB > 0 ? 1 : 0;
+        launches[STA_PROF_RESET] = (L.P > 0 ? 1 : 0) + launches[STA_PROF_REQUIRED] + launches[STA_PROF_ADJOINT];
     } else {
         launches[STA_PROF_NET_RC] = (nw + nc) > 0 ? 1 : 0;
         launches[STA_PROF_FORWARD] = nonempty;

@@ -67,7 +67,8 @@ def test_sequential_and_fused_gradients_agree():
         torch.cuda.synchronize()
         out[mode] = (g.cpu().numpy(), eng.pins(at=False, slew=False, ats=False, slack=False)["rat"])
         _, launches = eng.profile(with_times=False)
-        assert launches["required"] == (2 if mode == "sequential" else 0)  # reset + sweep
+        assert launches["required"] == (1 if mode == "sequential" else 0)
+        assert launches["reset"] == (3 if mode == "sequential" else 2)  # one per sweep
     assert np.array_equal(out["sequential"][1], out["fused"][1])
     gmax = np.abs(out["fused"][0]).max()
     assert np.abs(out["sequential"][0] - out["fused"][0]).max() <= 1e-5 * gmax
