@@ -255,6 +255,14 @@ StaStatus sta_query_summary(StaHandle *h, double *out, int on_device, void *stre
 StaStatus sta_query_pins(StaHandle *h, float *at, float *slew, float *rat, float *ats,
                          float *slack, int on_device, void *stream);
 
+/* Slack in one call (single-placement schedules; host outputs, synchronizes
+ * the legacy default stream after the handle's work): wns_tns [2][2] =
+ * {early WNS, early TNS, late WNS, late TNS} (ps; TNS sums negative endpoint
+ * slacks, WNS is the unclamped minimum); pin_slack [num_pins][2] and
+ * endpoint_slack [num_end][2] (early, late), each may be NULL.  The per-pin
+ * slacks need a forward pass with STA_FWD_RAT (STATE otherwise). */
+StaStatus sta_query_slack(StaHandle *h, float *wns_tns, float *pin_slack, float *endpoint_slack);
+
 /* Endpoint slacks [num_end][2] (early, late), in the order of end_pins. */
 StaStatus sta_query_endpoints(StaHandle *h, float *slack, int on_device, void *stream);
 

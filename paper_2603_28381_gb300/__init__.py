@@ -190,6 +190,17 @@ class StaEngine:
         res.update(bufs)
         return res
 
+    def slack(self, pins: bool = True, endpoints: bool = True):
+        """sta_query_slack: ({early_wns, early_tns, late_wns, late_tns}, pin slack [P,2] or None,
+        endpoint slack [E,2] or None)."""
+        wt = np.zeros(4, np.float32)
+        ps = np.zeros((max(self.num_pins, 1), 2), np.float32) if pins else None
+        es = np.zeros((max(self.num_end, 1), 2), np.float32) if endpoints else None
+        _sta._check(_sta._lib.sta_query_slack(self.h, wt.ctypes.data, ps.ctypes.data if ps is not None else None,
+                                              es.ctypes.data if es is not None else None), "sta_query_slack")
+        return (dict(zip(("wns_early", "tns_early", "wns_late", "tns_late"), wt.tolist())),
+                ps[:self.num_pins] if ps is not None else None, es[:self.num_end] if es is not None else None)
+
     def endpoints(self, stream=None) -> np.ndarray:
         out = np.zeros((self.B, self.num_end, 2), np.float32)
         _sta.sta_query_endpoints(self.h, out.ctypes.data if self.num_end else None, 0, _stream_ptr(stream))

@@ -1291,6 +1291,22 @@ StaStatus sta_plan_tasks(const StaNetlistDesc* nl, const StaLibrary* lib, int32_
     }
 }
 
+StaStatus sta_query_slack(StaHandle* h, float* wns_tns, float* pin_slack, float* endpoint_slack) {
+    if (!h || !wns_tns) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    if (h->batch()) return set_err(STA_ERR_STATE, "sta_query_slack: single-placement schedules (use the queries)");
+    double sum[STA_SUM_COUNT];
+    StaStatus st = sta_query_summary(h, sum, 0, nullptr);
+    if (st != STA_OK) return st;
+    wns_tns[0] = (float)sum[STA_SUM_WNS_EARLY];
+    wns_tns[1] = (float)sum[STA_SUM_TNS_EARLY];
+    wns_tns[2] = (float)sum[STA_SUM_WNS_LATE];
+    wns_tns[3] = (float)sum[STA_SUM_TNS_LATE];
+    if (pin_slack && (st = sta_query_pins(h, nullptr, nullptr, nullptr, nullptr, pin_slack, 0, nullptr)) != STA_OK)
+        return st;
+    if (endpoint_slack && (st = sta_query_endpoints(h, endpoint_slack, 0, nullptr)) != STA_OK) return st;
+    return STA_OK;
+}
+
 StaStatus sta_query_sizes(const StaHandle* h, int64_t* o) {
     if (!h || !o) return set_err(STA_ERR_INVALID_ARG, "null argument");
     const Layout& L = h->lay;

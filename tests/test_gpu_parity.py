@@ -185,3 +185,19 @@ def test_call_order_and_argument_errors():
     assert e.value.status == 6  # required times were not propagated
     torch.cuda.synchronize()
     eng.close()
+
+
+def test_query_slack_matches_the_other_queries():
+    import torch
+    import paper_2603_28381_gb300 as sta
+    w = netgen.tiny_design(1)
+    eng = sta.StaEngine(w.netlist, w.library)
+    eng.set_positions(torch.as_tensor(w.xy.astype(np.float32)).cuda())
+    eng.forward(gamma=10.0)
+    wt, ps, es = eng.slack()
+    summ = eng.summary()
+    for k in ("wns_early", "tns_early", "wns_late", "tns_late"):
+        assert wt[k] == np.float32(summ[k])
+    assert np.array_equal(ps, eng.pins(at=False, slew=False, rat=False, ats=False)["slack"])
+    assert np.array_equal(es, eng.endpoints())
+    eng.close()
