@@ -54,6 +54,7 @@ class Netlist:
     r_per_um: float
     c_per_um: float
     name: str = ""
+    end_clock: Optional[np.ndarray] = None  # int32 [E] capturing clock pin, -1 none
 
     @property
     def num_nets(self) -> int:
@@ -169,7 +170,7 @@ class NetlistBuilder:
         self.nets: List[List[int]] = []
         self.cells: List[Tuple[int, List[int], int]] = []
         self.starts: List[Tuple[int, List[float], List[float]]] = []
-        self.ends: List[Tuple[int, List[float]]] = []
+        self.ends: List[Tuple[int, List[float], int]] = []
 
     def pin(self, cap: float = 0.0, x: float = 0.0, y: float = 0.0) -> int:
         self.caps.append(cap)
@@ -187,8 +188,9 @@ class NetlistBuilder:
     def start(self, p: int, at=(0.0,) * 4, slew=(PI_SLEW_PS,) * 4) -> None:
         self.starts.append((p, list(at), list(slew)))
 
-    def end(self, p: int, rat=(0.0, 0.0, PERIOD_PS, PERIOD_PS)) -> None:
-        self.ends.append((p, list(rat)))
+    def end(self, p: int, rat=(0.0, 0.0, PERIOD_PS, PERIOD_PS), clock: int = -1) -> None:
+        """``clock``: the clock pin of the flop that captures ``p`` (propagated clock)."""
+        self.ends.append((p, list(rat), clock))
 
     def build(self, name: str = "hand") -> Tuple[Netlist, np.ndarray]:
         net_ptr = np.zeros(len(self.nets) + 1, np.int32)
@@ -208,7 +210,9 @@ class NetlistBuilder:
             start_slew=np.asarray([s[2] for s in self.starts], np.float32).reshape(-1, 4),
             end_pins=np.asarray([e[0] for e in self.ends], np.int32),
             end_rat=np.asarray([e[1] for e in self.ends], np.float32).reshape(-1, 4),
-            r_per_um=float(self.r), c_per_um=float(self.c), name=name)
+            r_per_um=float(self.r), c_per_um=float(self.c), name=name,
+            end_clock=(np.asarray([e[2] for e in self.ends], np.int32)
+                       if any(e[2] >= 0 for e in self.ends) else None))
         return nl, np.asarray(self.xy, np.float32).reshape(-1, 2)
 
 
@@ -233,7 +237,8 @@ def _fanout_targets(rng, n, law):
 def make_netlist(seed: int, *, n_comb: int, arcs_per_type: List[int], n_ff: int,
                  n_pi: int, n_po: int, depth: int, fanout, box: float,
                  n_huge: int = 0, huge_sinks: int = 0, r_per_um: float = 0.1,
-                 c_per_um: float = 0.2, name: str = "") -> Workload:
+                 c_per_um: float = 0.2, name: str = "", clock_nets: int = 0,
+                 clock_at=(0.0, 0.0, 0.0, 0.0)) -> Workload:
     """A levelled random netlist.
 
     Combinational cells get a logic level 1..depth (every level non-empty); the
@@ -243,6 +248,11 @@ def make_netlist(seed: int, *, n_comb: int, arcs_per_type: List[int], n_ff: int,
     Flops are a one-arc clock-to-Q cell whose CK pin is an ideal-clock
     startpoint; their D pins and the primary outputs are endpoints. ``n_huge``
     primary-input nets receive ``huge_sinks`` sinks each on random cell inputs.
+    With ``clock_nets`` > 0 the clock is propagated instead: that many clock
+    sources (startpoints asserted at ``clock_at``) each drive a net whose sinks
+    are the CK pins of a share of the flops, and every flop D endpoint names its
+    own flop's CK pin as its capturing clock (the random draws for this come
+    after all others, so the rest of the design is the ideal-clock one).
     Pins are numbered cell by cell (inputs, then output), then flop D pins,
     primary inputs and primary outputs, so that net order and pin order differ.
     """
@@ -382,24 +392,64 @@ def make_netlist(seed: int, *, n_comb: int, arcs_per_type: List[int], n_ff: int,
     info = dict(seed=seed, depth=depth, box=box, fanout=fanout, extra_po=extra_po,
                 net_level=net_lvl.astype(np.int32),
                 n_comb=n_comb, n_ff=n_ff, n_pi=n_pi, n_po=n_po, n_huge=n_huge,
-                huge_sinks=huge_sinks)
+                huge_sinks=huge_sinks, clock_nets=clock_nets)
+    if clock_nets > 0:
+        nl, xy = _propagate_clock(rng, nl, xy, ck_pins, d_pin0, clock_nets, clock_at, box)
+        info["net_level"] = None  # the clock nets add a level below the flops
+        info["ck_pins"] = ck_pins.astype(np.int32)
     return Workload(nl, lib, xy, info)
+
+
+def _propagate_clock(rng, nl: Netlist, xy: np.ndarray, ck_pins: np.ndarray, d_pin0: int,
+                     clock_nets: int, clock_at, box: float) -> Tuple[Netlist, np.ndarray]:
+    """Turn ideal-clock flop CK startpoints into sinks of ``clock_nets`` clock
+    nets driven by new clock-source pins; D endpoints name their flop's CK pin."""
+    n_ff = ck_pins.shape[0]
+    if n_ff < clock_nets:
+        raise ValueError("fewer flops than clock nets")
+    P0 = nl.num_pins
+    src = P0 + np.arange(clock_nets)
+    assign = np.arange(n_ff) % clock_nets
+    rng.shuffle(assign)
+    nets = [np.concatenate([[src[j]], ck_pins[assign == j]]) for j in range(clock_nets)]
+    net_pins = np.concatenate([nl.net_pins.astype(np.int64)] + nets)
+    net_ptr = np.concatenate([nl.net_ptr.astype(np.int64),
+                              nl.net_ptr[-1] + np.cumsum([len(n) for n in nets])])
+    pin_cap = np.concatenate([nl.pin_cap, np.zeros(clock_nets, np.float32)])
+    pin_cap[ck_pins] = rng.uniform(0.5, 3.0, size=n_ff).astype(np.float32)
+    xy = np.concatenate([xy, rng.uniform(0.0, box, size=(clock_nets, 2)).astype(np.float32)])
+    keep = ~np.isin(nl.start_pins, ck_pins)
+    start_pins = np.concatenate([nl.start_pins[keep], src]).astype(np.int32)
+    start_at = np.concatenate([nl.start_at[keep],
+                               np.tile(np.asarray(clock_at, np.float32), (clock_nets, 1))])
+    start_slew = np.concatenate([nl.start_slew[keep],
+                                 np.full((clock_nets, 4), PI_SLEW_PS, np.float32)])
+    ends = nl.end_pins.astype(np.int64)
+    is_d = (ends >= d_pin0) & (ends < d_pin0 + n_ff)
+    end_clock = np.where(is_d, ck_pins[np.clip(ends - d_pin0, 0, n_ff - 1)], -1).astype(np.int32)
+    out = dataclasses.replace(nl, num_pins=int(P0 + clock_nets), net_ptr=net_ptr.astype(np.int32),
+                              net_pins=net_pins.astype(np.int32), pin_cap=pin_cap,
+                              start_pins=start_pins, start_at=start_at.astype(np.float32),
+                              start_slew=start_slew, end_clock=end_clock,
+                              name=nl.name + f"_clk{clock_nets}")
+    return out, xy
 
 
 # ----------------------------------------------------------------------------
 # the paper-shaped workloads
 # ----------------------------------------------------------------------------
 
-def tiny_design(seed: int = 0) -> Workload:
+def tiny_design(seed: int = 0, clock_nets: int = 0) -> Workload:
     """~8k pins, 30 levels, 16 types with 1-4 inputs, geometric(0.4) fanout
     capped at 16, 100 PIs / 100 POs / 200 flops, 500x500 um."""
     return make_netlist(seed, n_comb=2000, arcs_per_type=[1, 2, 3, 4] * 4, n_ff=200,
                         n_pi=100, n_po=100, depth=30, fanout=("geom", 0.4, 16),
-                        box=500.0, name="tiny_2k_cells_d30")
+                        box=500.0, name="tiny_2k_cells_d30", clock_nets=clock_nets,
+                        clock_at=(0.0, 0.0, 3.0, 3.0))
 
 
 def superblue_like(seed: int = 1, scale: float = 1.0, depth: int = 150,
-                   huge: bool = True) -> Workload:
+                   huge: bool = True, clock_nets: int = 0) -> Workload:
     """~2.5M pins (superblue4-sized at scale 1), 150 levels, 64 types with
     1-4 inputs, power-law(2.2) fanout capped at 2000, 8 primary-input nets with
     20k sinks each (20k * scale below scale 1), 3000x3000 um."""
@@ -411,7 +461,7 @@ def superblue_like(seed: int = 1, scale: float = 1.0, depth: int = 150,
                         fanout=("power", 2.2, 2000), box=3000.0,
                         n_huge=(8 if huge and huge_sinks > 0 else 0),
                         huge_sinks=(huge_sinks if huge else 0),
-                        name=f"superblue_like_x{scale:g}_d{depth}")
+                        name=f"superblue_like_x{scale:g}_d{depth}", clock_nets=clock_nets)
 
 
 def jitter_positions(xy: np.ndarray, batch: int, sigma: float, seed: int) -> np.ndarray:

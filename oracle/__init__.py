@@ -59,7 +59,7 @@ class _Netlist(ctypes.Structure):
                 ("T", ctypes.c_int), ("type_num_arcs", ctypes.c_void_p),
                 ("arc_unate", ctypes.c_void_p), ("slew_index", ctypes.c_void_p),
                 ("load_index", ctypes.c_void_p), ("delay_tab", ctypes.c_void_p),
-                ("slew_tab", ctypes.c_void_p)]
+                ("slew_tab", ctypes.c_void_p), ("end_clk", ctypes.c_void_p)]
 
 
 class _Out(ctypes.Structure):
@@ -123,7 +123,8 @@ class _Pack:
             slew_index=None if lib is None else ptr(lib.slew_index, np.float32),
             load_index=None if lib is None else ptr(lib.load_index, np.float32),
             delay_tab=None if lib is None else ptr(lib.delay_tab, np.float32),
-            slew_tab=None if lib is None else ptr(lib.slew_tab, np.float32))
+            slew_tab=None if lib is None else ptr(lib.slew_tab, np.float32),
+            end_clk=(None if getattr(nl, "end_clock", None) is None else ptr(nl.end_clock, np.int32)))
 
 
 class OracleError(RuntimeError):

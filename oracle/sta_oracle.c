@@ -37,6 +37,13 @@
  *     WNS_gamma = softmin_gamma over every endpoint rise/fall slack, where
  *     softmin_gamma(x) = -LSE_gamma(-x) stabilised by the extremum as in Eq. 4.
  *   - sign(0) = 0 in the derivative of |x_s - x_d|.
+ *   - propagated clock: an endpoint may name the clock pin of the flop that
+ *     captures it.  Its hold bound (early required time) then adds that pin's
+ *     late rising arrival and its setup bound (late required time) the early
+ *     rising arrival (the latest and the earliest capture edge).  The clock pin
+ *     must be a sink of a net driven by a startpoint, so its arrival is the
+ *     startpoint's plus the wire delay and the setup term's adjoint goes to
+ *     that wire delay.
  * Units: ps, fF, Ohm, um; Ohm*fF = 1e-3 ps.  Condition index = 2*el + rf with
  * el 0 early / 1 late and rf 0 rise / 1 fall.
  */
@@ -65,6 +72,7 @@ typedef struct {
     const int *type_num_arcs;
     const signed char *arc_unate;
     const float *slew_index, *load_index, *delay_tab, *slew_tab;
+    const int *end_clk;  /* [E] capturing clock pin of each endpoint, -1 none; NULL = none */
 } OrNetlist;
 
 typedef struct {
@@ -253,6 +261,7 @@ int oracle_sta(const OrNetlist *nl, const double *xy, double gamma, double w_tns
     double *gload = calloc((size_t)P, sizeof(double));
     double *grad = calloc(2 * (size_t)P, sizeof(double));
     double *sm = malloc(sizeof(double) * 2 * (size_t)(E + 1));
+    double *con = malloc(sizeof(double) * 4 * (size_t)(E + 1)); /* effective endpoint bounds */
     int maxdeg = 1;
     for (int n = 0; n < N; ++n)
         if (nl->net_ptr[n + 1] - nl->net_ptr[n] > maxdeg) maxdeg = nl->net_ptr[n + 1] - nl->net_ptr[n];
@@ -262,7 +271,7 @@ int oracle_sta(const OrNetlist *nl, const double *xy, double gamma, double w_tns
     double *timp = malloc(sizeof(double) * (size_t)maxdeg), *twork = malloc(sizeof(double) * 2 * (size_t)maxdeg);
     if (!sink_net || !drv_net || !out_cell || !in_arc || !start_of || !end_of || !indeg || !topo ||
         !arc_cell || !at || !sl || !rat || !ats || !load || !wd || !imp || !dist || !adel || !ga ||
-        !gs || !gwd || !gimp || !gload || !grad || !sm || !tpar || !tres || !tcap || !tload ||
+        !gs || !gwd || !gimp || !gload || !grad || !sm || !con || !tpar || !tres || !tcap || !tload ||
         !tdel || !timp || !twork) { rc = OR_ENOMEM; goto done; }
 
     /* ---- roles of every pin, with validation ---- */
@@ -304,6 +313,15 @@ int oracle_sta(const OrNetlist *nl, const double *xy, double gamma, double w_tns
     for (int p = 0; p < P; ++p) {
         int nsrc = (start_of[p] >= 0) + (sink_net[p] >= 0) + (out_cell[p] >= 0);
         if (nsrc != 1) { rc = OR_EINVAL; goto done; }
+    }
+    /* a capturing clock pin hangs on a net driven by a startpoint */
+    for (int e = 0; nl->end_clk && e < E; ++e) {
+        int k = nl->end_clk[e];
+        if (k < -1 || k >= P) { rc = OR_EINVAL; goto done; }
+        if (k >= 0 && (sink_net[k] < 0 || start_of[nl->net_pins[nl->net_ptr[sink_net[k]]]] < 0)) {
+            rc = OR_EINVAL;
+            goto done;
+        }
     }
 
     /* ---- net RC (Eqs. 1-3) on each star ---- */
@@ -418,12 +436,21 @@ int oracle_sta(const OrNetlist *nl, const double *xy, double gamma, double w_tns
         }
     }
 
+    /* ---- endpoint bounds: the constraint plus the capturing clock's arrival ---- */
+    for (int e = 0; e < E; ++e) {
+        int k = nl->end_clk ? nl->end_clk[e] : -1;
+        for (int q = 0; q < 4; ++q) {
+            con[4 * e + q] = nl->end_rat[4 * e + q];
+            if (k >= 0) con[4 * e + q] += q < 2 ? at[4 * k + 2] : at[4 * k + 0];
+        }
+    }
+
     /* ---- backward: required times in reverse topological order ---- */
     for (int p = 0; p < P; ++p) {
         rat[4 * p] = rat[4 * p + 1] = -INFINITY;
         rat[4 * p + 2] = rat[4 * p + 3] = INFINITY;
         if (end_of[p] >= 0)
-            for (int q = 0; q < 4; ++q) rat[4 * p + q] = nl->end_rat[4 * end_of[p] + q];
+            for (int q = 0; q < 4; ++q) rat[4 * p + q] = con[4 * end_of[p] + q];
     }
     for (int ti = P - 1; ti >= 0; --ti) {
         int p = topo[ti];
@@ -457,16 +484,16 @@ int oracle_sta(const OrNetlist *nl, const double *xy, double gamma, double w_tns
     int nviol = 0;
     for (int e = 0; e < E; ++e) {
         int p = nl->end_pins[e];
-        const float *con = nl->end_rat + 4 * e;
-        double se = fmin(at[4 * p] - con[0], at[4 * p + 1] - con[1]);
-        double sL = fmin(con[2] - at[4 * p + 2], con[3] - at[4 * p + 3]);
+        const double *ce = con + 4 * e;
+        double se = fmin(at[4 * p] - ce[0], at[4 * p + 1] - ce[1]);
+        double sL = fmin(ce[2] - at[4 * p + 2], ce[3] - at[4 * p + 3]);
         if (out && out->ep_slack) { out->ep_slack[2 * e] = se; out->ep_slack[2 * e + 1] = sL; }
         if (se < wns[0]) wns[0] = se;
         if (sL < wns[1]) wns[1] = sL;
         if (se < 0) tns[0] += se;
         if (sL < 0) { tns[1] += sL; ++nviol; }
-        sm[2 * e] = con[2] - ats[2 * p];
-        sm[2 * e + 1] = con[3] - ats[2 * p + 1];
+        sm[2 * e] = ce[2] - ats[2 * p];
+        sm[2 * e + 1] = ce[3] - ats[2 * p + 1];
     }
     double tns_g = 0.0;
     for (int e = 0; e < E; ++e) {
@@ -485,6 +512,9 @@ int oracle_sta(const OrNetlist *nl, const double *xy, double gamma, double w_tns
             double dl_ds = w_tns * exp(-(s - te) / gamma);
             if (isfinite(wns_g)) dl_ds += w_wns * exp(-(s - wns_g) / gamma);
             ga[2 * p + rf] += -dl_ds; /* s = RAT_c - ATs */
+            /* RAT_c = constraint + early rising arrival of the clock pin k =
+             * its startpoint's arrival + wire delay of k */
+            if (nl->end_clk && nl->end_clk[e] >= 0) gwd[nl->end_clk[e]] += dl_ds;
         }
     }
     for (int ti = P - 1; ti >= 0; --ti) {
@@ -579,7 +609,7 @@ done:
     free(sink_net); free(drv_net); free(out_cell); free(in_arc); free(start_of); free(end_of);
     free(indeg); free(topo); free(arc_cell); free(at); free(sl); free(rat); free(ats); free(load);
     free(wd); free(imp); free(dist); free(adel); free(ga); free(gs); free(gwd); free(gimp);
-    free(gload); free(grad); free(sm); free(tpar); free(tres); free(tcap); free(tload); free(tdel);
+    free(gload); free(grad); free(sm); free(con); free(tpar); free(tres); free(tcap); free(tload); free(tdel);
     free(timp); free(twork);
     return rc;
 }

@@ -37,10 +37,10 @@ def linear_library(num_types, arcs_per_type, seed=0):
     return lib, A, B
 
 
-def tiny_netlist(seed, n_comb=10, depth=4):
+def tiny_netlist(seed, n_comb=10, depth=4, clock_nets=0):
     w = netgen.make_netlist(seed, n_comb=n_comb, arcs_per_type=[1, 2, 3, 4], n_ff=2, n_pi=3,
                             n_po=2, depth=depth, fanout=("geom", 0.5, 4), box=100.0,
-                            name=f"tiny{seed}")
+                            name=f"tiny{seed}", clock_nets=clock_nets)
     return w
 
 

@@ -33,8 +33,13 @@ MUTATIONS = {
                         "double w = exp(-(ats[2 * i + rfi] + D - ats[2 * p + rf]) / gamma);"),
     "second_moment_factor": ("double m = 2.0 * beta[u] - delay[u] * delay[u];",
                              "double m = beta[u] - delay[u] * delay[u];"),
-    "endpoint_slack_early_sign": ("double se = fmin(at[4 * p] - con[0], at[4 * p + 1] - con[1]);",
-                                  "double se = fmin(con[0] - at[4 * p], con[1] - at[4 * p + 1]);"),
+    "endpoint_slack_early_sign": ("double se = fmin(at[4 * p] - ce[0], at[4 * p + 1] - ce[1]);",
+                                  "double se = fmin(ce[0] - at[4 * p], ce[1] - at[4 * p + 1]);"),
+    "capture_adjoint_dropped": ("if (nl->end_clk && nl->end_clk[e] >= 0) gwd[nl->end_clk[e]] += dl_ds;", ""),
+    "capture_edges_swapped": ("con[4 * e + q] += q < 2 ? at[4 * k + 2] : at[4 * k + 0];",
+                              "con[4 * e + q] += q < 2 ? at[4 * k + 0] : at[4 * k + 2];"),
+    "capture_arrival_subtracted": ("con[4 * e + q] += q < 2 ? at[4 * k + 2] : at[4 * k + 0];",
+                                   "con[4 * e + q] -= q < 2 ? at[4 * k + 2] : at[4 * k + 0];"),
 }
 
 

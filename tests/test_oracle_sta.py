@@ -17,13 +17,24 @@ import oracle
 from tests import _tinydag as td
 
 
+@pytest.mark.parametrize("clocked", [0, 1])
 @pytest.mark.parametrize("seed", range(6))
-def test_at_rat_equal_path_enumeration(seed):
-    w = td.tiny_netlist(seed)
+def test_at_rat_equal_path_enumeration(seed, clocked):
+    w = td.tiny_netlist(seed, clock_nets=clocked)
     nl = w.netlist
     lib, A, B = td.linear_library(5, [1, 2, 3, 4, 1], seed=seed)
     r = oracle.sta(nl, lib, w.xy)
     arr, req = td.enumerate_paths(nl, lib, A, B, w.xy)
+    # required times of clocked endpoints move with the capturing clock's arrival
+    # (hold: latest rising edge, setup: earliest); unclocked ones are constants
+    hold_shift = np.zeros(nl.end_pins.shape[0])
+    setup_shift = np.zeros(nl.end_pins.shape[0])
+    if nl.end_clock is not None:
+        for e, k in enumerate(nl.end_clock):
+            if k >= 0:
+                hold_shift[e] = max(arr[(int(k), 0)])
+                setup_shift[e] = min(arr[(int(k), 0)])
+        assert np.count_nonzero(setup_shift) > 0
     for p in range(nl.num_pins):
         for rf in range(2):
             vals = arr[(p, rf)]
@@ -33,8 +44,8 @@ def test_at_rat_equal_path_enumeration(seed):
             if not paths:
                 assert r["rat"][p, 2 + rf] == np.inf and r["rat"][p, rf] == -np.inf
                 continue
-            late = min(float(nl.end_rat[e, 2 + rfe]) - d for e, rfe, d in paths)
-            early = max(float(nl.end_rat[e, rfe]) - d for e, rfe, d in paths)
+            late = min(float(nl.end_rat[e, 2 + rfe]) + setup_shift[e] - d for e, rfe, d in paths)
+            early = max(float(nl.end_rat[e, rfe]) + hold_shift[e] - d for e, rfe, d in paths)
             assert r["rat"][p, 2 + rf] == pytest.approx(late, rel=1e-12, abs=1e-9)
             assert r["rat"][p, rf] == pytest.approx(early, rel=1e-12, abs=1e-9)
 
@@ -253,10 +264,11 @@ def _check_fd(nl, lib, xy, pins, gamma, w_tns, w_wns, tol):
     return r
 
 
+@pytest.mark.parametrize("clocked", [0, 1])
 @pytest.mark.parametrize("seed", range(4))
 @pytest.mark.parametrize("weights", [(1.0, 0.0), (0.0, 1.0), (0.7, 0.3)])
-def test_gradient_matches_finite_differences_tiny(seed, weights):
-    w = td.tiny_netlist(seed, n_comb=12, depth=5)
+def test_gradient_matches_finite_differences_tiny(seed, weights, clocked):
+    w = td.tiny_netlist(seed, n_comb=12, depth=5, clock_nets=clocked)
     gamma = 5.0
     r = _check_fd(w.netlist, w.library, w.xy, np.arange(w.netlist.num_pins), gamma,
                   weights[0], weights[1], tol=2e-6)
@@ -279,3 +291,110 @@ def test_gradient_translation_invariance():
     moved = w.xy.astype(np.float64) + np.array([123.25, -45.5])
     r2 = oracle.sta(w.netlist, w.library, moved, 10.0, 1.0, 1.0)
     assert r2["summary"]["loss"] == pytest.approx(r["summary"]["loss"], rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# propagated clock
+# ---------------------------------------------------------------------------
+def _clock_pair():
+    """Clock source c -> (ck1, ck2); flop F1 (ck1 -> q1) launches into d2, the
+    D pin captured by flop F2 (ck2 -> q2 -> po).  Slew-independent tables."""
+    b = netgen.NetlistBuilder(r_per_um=0.5, c_per_um=0.25)
+    c = b.pin(0.0, 5, 7)
+    ck1 = b.pin(1.0, 25, 3)
+    q1 = b.pin(0.0, 27, 6)
+    d2 = b.pin(1.5, 60, 20)
+    ck2 = b.pin(2.0, 9, 45)
+    q2 = b.pin(0.0, 12, 47)
+    po = b.pin(1.0, 80, 31)
+    b.net(c, [ck1, ck2])
+    b.net(q1, [d2])
+    b.net(q2, [po])
+    b.cell(0, [ck1], q1)
+    b.cell(0, [ck2], q2)
+    b.start(c, at=(1.0, 1.0, 4.0, 4.0), slew=(20.0,) * 4)
+    b.end(d2, rat=(2.0, 2.0, 15.0, 15.0), clock=ck2)
+    b.end(po, rat=(0.0, 0.0, 1000.0, 1000.0))
+    nl, xy = b.build()
+    lib, A, B = td.linear_library(1, [1], seed=3)
+    lib.arc_unate[:] = 1
+    return nl, xy, lib, A, B, dict(c=c, ck1=ck1, q1=q1, d2=d2, ck2=ck2)
+
+
+def test_propagated_clock_followed_by_hand():
+    nl, xy, lib, A, B, p = _clock_pair()
+    r = oracle.sta(nl, lib, xy, gamma=5.0)
+
+    x = xy.astype(np.float64)
+
+    def wire(drv, snk, cap):
+        d = abs(x[snk, 0] - x[drv, 0]) + abs(x[snk, 1] - x[drv, 1])
+        return 0.5 * d * (cap + 0.25 * d / 2) * 1e-3, d
+
+    w1, _ = wire(p["c"], p["ck1"], 1.0)
+    w2, _ = wire(p["c"], p["ck2"], 2.0)
+    wd2, dist = wire(p["q1"], p["d2"], 1.5)
+    load1 = 1.5 + 0.25 * dist
+    q = [A[0, 0, rf] + B[0, 0, rf] * load1 for rf in range(2)]
+    at_late = [4.0 + w1 + q[rf] + wd2 for rf in range(2)]
+    at_early = [1.0 + w1 + q[rf] + wd2 for rf in range(2)]
+    np.testing.assert_allclose(r["at"][p["d2"]], at_early + at_late, rtol=1e-13)
+    rat_hold = 2.0 + 4.0 + w2     # latest capture edge
+    rat_setup = 15.0 + 1.0 + w2   # earliest capture edge
+    np.testing.assert_allclose(r["rat"][p["d2"]], [rat_hold, rat_hold, rat_setup, rat_setup], rtol=1e-13)
+    assert r["ep_slack"][0, 1] == pytest.approx(min(rat_setup - a for a in at_late), rel=1e-13)
+    assert r["ep_slack"][0, 0] == pytest.approx(min(a - rat_hold for a in at_early), rel=1e-13)
+    assert r["ep_slack"][0, 1] < 0  # the capture term must reach the gradient below
+
+
+def test_propagated_clock_gradient_by_finite_differences():
+    nl, xy, lib, _, _, p = _clock_pair()
+    r = _check_fd(nl, lib, xy, np.arange(nl.num_pins), 5.0, 1.0, 0.5, tol=2e-6)
+    assert np.abs(r["grad"][p["ck2"]]).max() > 0
+
+
+def test_zero_length_clock_wires_equal_ideal_clock():
+    """With every CK pin at its clock source the wires vanish: the design equals
+    the ideal-clock one with CK asserted at the clock arrival and D bounds moved
+    by the capture edge (hold +late, setup +early)."""
+    wc = netgen.tiny_design(0, clock_nets=2)
+    wi = netgen.tiny_design(0)
+    nc, ni = wc.netlist, wi.netlist
+    P0 = ni.num_pins
+    xy = wc.xy.astype(np.float64).copy()
+    for n in range(ni.num_nets, nc.num_nets):
+        pins = nc.net_pins[nc.net_ptr[n]:nc.net_ptr[n + 1]]
+        xy[pins[1:]] = xy[pins[0]]
+    clock_at = nc.start_at[-1]
+    ideal = netgen.Netlist(**{f.name: getattr(ni, f.name) for f in netgen.dataclasses.fields(ni)})
+    ideal.start_at = ni.start_at.copy()
+    ck = np.isin(ni.start_pins, wc.info["ck_pins"])
+    ideal.start_at[ck] = clock_at
+    ideal.end_rat = ni.end_rat.copy()
+    clocked = nc.end_clock >= 0
+    ideal.end_rat[clocked] += np.array([clock_at[2], clock_at[2], clock_at[0], clock_at[0]], np.float32)
+    rc = oracle.sta(nc, wc.library, xy, 10.0, 1.0, 0.5)
+    ri = oracle.sta(ideal, wi.library, xy[:P0], 10.0, 1.0, 0.5)
+    for k in ("at", "slew", "rat", "ats", "pin_slack"):
+        np.testing.assert_array_equal(rc[k][:P0], ri[k], err_msg=k)
+    np.testing.assert_array_equal(rc["ep_slack"], ri["ep_slack"])
+    np.testing.assert_allclose(rc["grad"][:P0], ri["grad"], rtol=1e-12, atol=1e-12)
+    for k in ri["summary"]:
+        assert rc["summary"][k] == pytest.approx(ri["summary"][k], rel=1e-13)
+
+
+def test_clocked_design_gradient_matches_finite_differences():
+    w = netgen.tiny_design(1, clock_nets=2)
+    nl = w.netlist
+    rng = np.random.default_rng(11)
+    pins = np.concatenate([nl.start_pins[-2:], rng.choice(w.info["ck_pins"], 20, replace=False),
+                           rng.choice(nl.num_pins, 20, replace=False)])
+    _check_fd(nl, w.library, w.xy, pins, 10.0, 1.0, 0.5, tol=2e-6)
+
+
+def test_capturing_clock_must_hang_on_a_startpoint_net():
+    nl, xy, lib, _, _, p = _clock_pair()
+    bad = netgen.Netlist(**{f.name: getattr(nl, f.name) for f in netgen.dataclasses.fields(nl)})
+    bad.end_clock = np.array([p["q1"], -1], np.int32)  # a cell output, not a clock-net sink
+    with pytest.raises(oracle.OracleError, match="invalid"):
+        oracle.sta(bad, lib, xy)
