@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--tile-pins", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--batch-sweep", default="levels", choices=["levels", "dataflow"])
+    ap.add_argument("--clock-nets", type=int, default=0,
+                    help="single: propagate the clock over this many clock nets (0: ideal clock)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batch: use --tile-pins/--chunk/--batch-sweep instead of the autotuner's choice")
     return ap.parse_args()
@@ -70,7 +72,7 @@ def parse():
 
 def workload(args):
     import netgen
-    return netgen.superblue_like(args.seed, scale=args.scale)
+    return netgen.superblue_like(args.seed, scale=args.scale, clock_nets=args.clock_nets)
 
 
 def config_of(w, args, extra=None):
@@ -78,7 +80,9 @@ def config_of(w, args, extra=None):
     cfg = {"workload": f"superblue4-shaped synthetic netlist, seed {args.seed}: {st['pins']} pins, "
                        f"{st['nets']} nets, {st['cells']} cells, depth {w.info['depth']}, "
                        f"power-law(2.2) fanout <= 2000 plus 8 x {w.info['huge_sinks']}-sink nets, "
-                       f"3000x3000 um, gamma {GAMMA} ps, fwd (AT+LSE+RAT) + gradient",
+                       f"3000x3000 um, gamma {GAMMA} ps, fwd (AT+LSE+RAT) + gradient, "
+                       + (f"clock propagated over {w.info['clock_nets']} clock nets to the flop clock pins"
+                          if w.info.get("clock_nets") else "ideal clock"),
            "pins": st["pins"], "nets": st["nets"], "arcs": st["arcs"], "endpoints": st["endpoints"],
            "levels": int(w.info["depth"]) + 1, "gamma_ps": GAMMA}
     if extra:
@@ -90,10 +94,11 @@ def config_of(w, args, extra=None):
 # algorithmic bytes per kernel kind (each array crosses HBM once per producer
 # and once per consumer; tables, level pointers and constants not counted)
 # --------------------------------------------------------------------------
-def algorithmic_bytes(sizes, S, schedule="dataflow", big=(0, 0)):
+def algorithmic_bytes(sizes, S, schedule="dataflow", big=(0, 0), clocked=0):
     """Algorithmic bytes of one step by kernel kind.  big = (nets, sinks) of the
     nets of more than 32 pins (their RC runs in a prologue kernel in the
-    dataflow schedule; every other net's RC runs inside the forward kernel)."""
+    dataflow schedule; every other net's RC runs inside the forward kernel).
+    clocked = endpoints captured by a propagated clock."""
     P, N, A = sizes["pins"], sizes["nets"], sizes["arcs"]
 
     def rc(n, s):  # pin xy 8 + cap 4 per net pin, (delay, impulse) write 8 per sink, topology + load 8 per net
@@ -125,6 +130,13 @@ def algorithmic_bytes(sizes, S, schedule="dataflow", big=(0, 0)):
     else:
         out["net_rc"] = rc(big[0], big[1])
         out["forward"] = fwd + rc(N - big[0], S - big[1])
+    if clocked:
+        # per clocked endpoint: the clock pin's AT 16 + the required-time seed write 16; its
+        # adjoint seed: clock pin 4, constraint 16, pin 4, clock AT 16, LSE-AT 8, seed write 4;
+        # the adjoint sweep reads a seed word per arc
+        out["endpoints"] += 32 * clocked
+        out["seed"] += 52 * clocked
+        out["adjoint"] += 4 * A
     return out
 
 
@@ -153,7 +165,8 @@ def measured_traffic(kind, args):
     changed since the counters were taken (a digest of the sources is kept)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "dram_traffic_dataflow_superblue_2p5M.json")
-    if args.schedule != "dataflow" or args.scale != 1.0 or args.seed != 1 or not os.path.exists(path):
+    if (args.schedule != "dataflow" or args.scale != 1.0 or args.seed != 1 or args.clock_nets
+            or not os.path.exists(path)):
         return None
     with open(path) as f:
         rec = json.load(f)
@@ -275,7 +288,7 @@ def run_reference(args):
     if t_full * (args.steps + args.warmup) > 200.0:
         import netgen
         scale = max(0.002, 200.0 / ((args.steps + args.warmup) * t_full) * args.scale * 0.8)
-        sample = netgen.superblue_like(args.seed, scale=scale)
+        sample = netgen.superblue_like(args.seed, scale=scale, clock_nets=args.clock_nets)
         sample_note = (f"a {sample.netlist.num_pins}-pin netlist from the same generator "
                        f"(scale {scale:.3g}) per step, to bound the run")
     Ps = sample.netlist.num_pins
@@ -403,8 +416,9 @@ def run_ours(args):
     sizes = dict(pins=P, nets=prof_eng.sizes["nets"], arcs=prof_eng.sizes["arcs"],
                  endpoints=prof_eng.sizes["endpoints"])
     fan = np.diff(nl.net_ptr)
+    clocked = 0 if nl.end_clock is None else int((nl.end_clock >= 0).sum())
     abytes = algorithmic_bytes(sizes, S, args.schedule,
-                               big=(int((fan > 32).sum()), int((fan[fan > 32] - 1).sum())))
+                               big=(int((fan > 32).sum()), int((fan[fan > 32] - 1).sum())), clocked=clocked)
     if launches.get("required", 1) == 0:  # required times ran inside the adjoint sweep
         abytes["adjoint"] += abytes["required"]
         abytes["required"] = 0
@@ -433,7 +447,8 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": config_of(w, args, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                "config": config_of(w, args, {"levels": int(prof_eng.sizes["levels"]),
+                                              "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                                               "schedule": args.schedule,
                                               "l2": "flushed between steps (512 MB write)",
                                               "wall_s": round(t_wall, 3)}),

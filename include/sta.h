@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define STA_ABI_VERSION 1
+#define STA_ABI_VERSION 2
 #define STA_LUT 7       /* table points per axis */
 #define STA_MAX_ARCS 4  /* arcs (input pins) per cell type */
 
@@ -79,6 +79,16 @@ typedef struct {
     const float *end_rat;        /* [num_end][4] required time: early = hold bound,
                                     late = setup bound, ps */
     float r_per_um, c_per_um;    /* wire resistance (Ohm/um) and capacitance (fF/um) */
+    const int32_t *end_clock;    /* [num_end] or NULL (ideal clock).  Propagated clock: the
+                                    clock pin of the flop that captures the endpoint, -1 for
+                                    none.  The endpoint's early bound then adds that pin's
+                                    late rising arrival (hold: latest capture edge) and its
+                                    late bound the early rising arrival (setup: earliest
+                                    edge); the adjoint of the smoothed loss follows the
+                                    setup term into the clock wire.  A clock pin must be a
+                                    cell input on a net driven by a startpoint (an unbuffered
+                                    clock net) and capture at most one endpoint
+                                    (STA_ERR_INVALID_ARG otherwise). */
 } StaNetlistDesc;
 
 /* Liberty-like library (Section 3.1.2): per type and arc, per output

@@ -32,7 +32,8 @@ class StaNetlistDesc(ctypes.Structure):
                 ("cell_in_pins", _p), ("cell_out_pin", _p), ("pin_cap", _p),
                 ("num_start", _i32), ("start_pins", _p), ("start_at", _p), ("start_slew", _p),
                 ("num_end", _i32), ("end_pins", _p), ("end_rat", _p),
-                ("r_per_um", ctypes.c_float), ("c_per_um", ctypes.c_float)]
+                ("r_per_um", ctypes.c_float), ("c_per_um", ctypes.c_float),
+                ("end_clock", _p)]
 
 
 class StaLibrary(ctypes.Structure):
@@ -173,7 +174,8 @@ def netlist_desc(nl, keep: _Keep) -> StaNetlistDesc:
         start_at=keep(nl.start_at, np.float32), start_slew=keep(nl.start_slew, np.float32),
         num_end=int(nl.end_pins.shape[0]), end_pins=keep(nl.end_pins, np.int32),
         end_rat=keep(nl.end_rat, np.float32),
-        r_per_um=float(nl.r_per_um), c_per_um=float(nl.c_per_um))
+        r_per_um=float(nl.r_per_um), c_per_um=float(nl.c_per_um),
+        end_clock=(None if getattr(nl, "end_clock", None) is None else keep(nl.end_clock, np.int32)))
 
 
 def library_desc(lib, keep: _Keep) -> StaLibrary:

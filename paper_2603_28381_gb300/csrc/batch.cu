@@ -370,6 +370,46 @@ __device__ __forceinline__ void bep_merge(BEp& a, const BEp& b, float gamma) {
     a.wmin = m;
 }
 
+// Bounds of endpoint e in placement b (hold, hold, setup, setup); a propagated
+// clock adds the capturing clock pin's late rising arrival to the hold bound
+// and its early rising arrival to the setup bound.  Returns the clock pin or -1.
+__device__ __forceinline__ int bep_bounds(const DevNet& g, const BatchState& bs, int e, int b, float4& con) {
+    con = reinterpret_cast<const float4*>(g.ep_rat)[e];
+    const int k = g.ep_clk ? g.ep_clk[e] : -1;
+    if (k >= 0) {
+        const float early = bs.at[ix(4 * k, bs.Bp, b)], late = bs.at[ix(4 * k + 2, bs.Bp, b)];
+        con.x += late;
+        con.y += late;
+        con.z += early;
+        con.w += early;
+    }
+    return k;
+}
+
+// Propagated clock, per placement: d loss / d (setup bound) of each clocked
+// endpoint, which enters the adjoint of its clock pin's rising LSE arrival
+// (the arc step that writes that word adds it).  grid (ceil(E / 8), G).
+__global__ void __launch_bounds__(kBlock) k_bcap_seed(DevNet g, BatchState bs, float gamma) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int b = blockIdx.y * 32 + lane, Bp = bs.Bp;
+    const int e = blockIdx.x * kWarpsPerBlock + w;
+    if (e >= g.E) return;
+    float4 con;
+    const int k = bep_bounds(g, bs, e, b, con);
+    if (k < 0) return;
+    const int p = g.ep_pin[e];
+    const float W = (float)bs.summary[(size_t)b * STA_SUM_COUNT + STA_SUM_WNS_GAMMA];
+    const float wt = bs.params[2 * b], ww = bs.params[2 * b + 1];
+    const float sr = con.z - bs.ats[ix(2 * p, Bp, b)], sf = con.w - bs.ats[ix(2 * p + 1, Bp, b)];
+    const float te = softmin3(sr, sf, gamma);
+    float gr = wt * expf(-(sr - te) / gamma), gf = wt * expf(-(sf - te) / gamma);
+    if (isfinite(W)) {
+        gr += ww * expf(-(sr - W) / gamma);
+        gf += ww * expf(-(sf - W) / gamma);
+    }
+    bs.cap_seed[ix(k, Bp, b)] = gr + gf;
+}
+
 // grid (kRedBlocks, G): block x takes endpoints x*8 + w, stepping by
 // kRedBlocks*8; partial per (block, placement)
 __global__ void __launch_bounds__(kBlock) k_bep1(DevNet g, BatchState bs, float gamma, int lse) {
@@ -379,7 +419,14 @@ __global__ void __launch_bounds__(kBlock) k_bep1(DevNet g, BatchState bs, float 
     BEp acc = bep_identity();
     for (int e = blockIdx.x * kWarpsPerBlock + w; e < g.E; e += gridDim.x * kWarpsPerBlock) {
         const int p = g.ep_pin[e];
-        const float4 con = reinterpret_cast<const float4*>(g.ep_rat)[e];
+        float4 con;
+        // a clocked endpoint's bounds are this placement's required-time seeds
+        if (bep_bounds(g, bs, e, b, con) >= 0) {
+            bs.rat[ix(4 * p, Bp, b)] = con.x;
+            bs.rat[ix(4 * p + 1, Bp, b)] = con.y;
+            bs.rat[ix(4 * p + 2, Bp, b)] = con.z;
+            bs.rat[ix(4 * p + 3, Bp, b)] = con.w;
+        }
         const float a0 = bs.at[ix(4 * p, Bp, b)], a1 = bs.at[ix(4 * p + 1, Bp, b)];
         const float a2 = bs.at[ix(4 * p + 2, Bp, b)], a3 = bs.at[ix(4 * p + 3, Bp, b)];
         const float se = fminf(a0 - con.x, a1 - con.y);
@@ -540,7 +587,9 @@ __device__ __forceinline__ float bcell_apply(const BatchState& bs, const BCell& 
             if (mode & 1) st_relaxed_f(bs.rat + ix(4 * bc.pin[k] + 2 * el + r, Bp, b), R - bc.adel[k]);
             if ((mode & 2) && el) {
                 const float gD = GA * bc.w[k];
-                st_relaxed_f(bs.g_ats + ix(2 * bc.pin[k] + r, Bp, b), gD);
+                // a capturing clock pin also carries its endpoint's setup term
+                st_relaxed_f(bs.g_ats + ix(2 * bc.pin[k] + r, Bp, b),
+                             (bs.cap_seed && r == 0) ? gD + __ldcg(bs.cap_seed + ix(bc.pin[k], Bp, b)) : gD);
                 st_relaxed_f(bs.g_slew + ix(2 * bc.pin[k] + r, Bp, b),
                              fmaf(gD, bc.dDs[k], k == bc.amax ? GS * bc.dSs : 0.f));
                 gl = fmaf(gD, bc.dDl[k], gl);
@@ -1142,6 +1191,11 @@ void launch_batch_bwd_level(const DevNet& g, const BatchState& bs, const DfState
     if (mode == 1) k_bbwd_lvl<1><<<grid, kBlock, 0, st>>>(g, bs, d, r, gamma);
     else if (mode == 2) k_bbwd_lvl<2><<<grid, kBlock, 0, st>>>(g, bs, d, r, gamma);
     else k_bbwd_lvl<3><<<grid, kBlock, 0, st>>>(g, bs, d, r, gamma);
+}
+
+void launch_batch_cap_seed(const DevNet& g, const BatchState& bs, float gamma, cudaStream_t st) {
+    if (g.E == 0 || !g.ep_clk) return;
+    k_bcap_seed<<<dim3((g.E + kWarpsPerBlock - 1) / kWarpsPerBlock, bs.G), kBlock, 0, st>>>(g, bs, gamma);
 }
 
 void launch_batch_endpoints(const DevNet& g, const BatchState& bs, float gamma, int lse, cudaStream_t st) {

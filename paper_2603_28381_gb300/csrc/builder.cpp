@@ -98,6 +98,19 @@ StaStatus check_netlist(const StaNetlistDesc& nl, const StaLibrary* lib, Roles& 
             if (!std::isfinite(nl.end_rat[4 * e + q])) return err = "endpoint RAT must be finite", STA_ERR_INVALID_ARG;
         r.end_of[p] = e;
     }
+    if (nl.end_clock && nl.num_end > 0) {
+        std::vector<uint8_t> used(P, 0);
+        for (int32_t e = 0; e < nl.num_end; ++e) {
+            const int32_t k = nl.end_clock[e];
+            if (k == -1) continue;
+            if (k < -1 || k >= P) return err = "end_clock out of range", STA_ERR_INVALID_ARG;
+            if (r.sink_net[k] < 0 || r.start_of[nl.net_pins[nl.net_ptr[r.sink_net[k]]]] < 0 || r.in_cell[k] < 0)
+                return err = "capturing clock pin " + std::to_string(k) +
+                             " must be a cell input on a net driven by a startpoint", STA_ERR_INVALID_ARG;
+            if (used[k]++) return err = "clock pin " + std::to_string(k) + " captures two endpoints",
+                                  STA_ERR_INVALID_ARG;
+        }
+    }
     for (int32_t p = 0; p < P; ++p) {
         const int nsrc = (r.start_of[p] >= 0) + (r.sink_net[p] >= 0) + (r.out_cell[p] >= 0);
         if (nsrc != 1)
@@ -583,9 +596,16 @@ StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& 
     }
     o.ep_pin.resize(o.E);
     o.ep_rat.resize((size_t)o.E * 4);
+    o.ep_clk.clear();
+    for (int32_t e = 0; nl.end_clock && e < o.E; ++e)
+        if (nl.end_clock[e] >= 0) {
+            o.ep_clk.assign(o.E, -1);
+            break;
+        }
     for (int32_t e = 0; e < o.E; ++e) {
         const int32_t p = internal[nl.end_pins[e]];
         o.ep_pin[e] = p;
+        if (!o.ep_clk.empty() && nl.end_clock[e] >= 0) o.ep_clk[e] = internal[nl.end_clock[e]];
         for (int q = 0; q < 4; ++q) {
             o.ep_rat[4 * (size_t)e + q] = nl.end_rat[4 * e + q];
             o.rat0[4 * (size_t)p + q] = nl.end_rat[4 * e + q];

@@ -231,6 +231,10 @@ void enqueue_backward_dataflow(StaHandle* h, int mode, float gamma, cudaStream_t
         ProfScope ps(h, pr, STA_PROF_RESET, st);
         launch_bwd_reset(h->s, h->d, L.P, mode, st);  // the words the sweep's tasks poll
     }
+    if ((mode & 2) && h->g.ep_clk) {
+        ProfScope ps(h, pr, STA_PROF_SEED, st);
+        launch_cap_seed(h->g, h->s, gamma, st);
+    }
     ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJOINT : STA_PROF_REQUIRED, st);
     launch_bwd_dataflow(h->g, h->s, h->d, h->grid_bwd, gamma, mode, st);
 }
@@ -300,6 +304,10 @@ void enqueue_backward_batch(StaHandle* h, int mode, float gamma, cudaStream_t st
     const Layout& L = h->lay;
     StaHandle::Prof* pr = (mode & 2) ? &h->prof_adj : &h->prof_rat;
     pr->next = 0;
+    if ((mode & 2) && h->g.ep_clk) {
+        ProfScope ps(h, pr, STA_PROF_SEED, st);
+        launch_batch_cap_seed(h->g, h->bs, gamma, st);
+    }
     if (h->bsweep == STA_BATCH_LEVELS) {
         std::vector<std::array<int, 6>> ph;
         batch_bwd_phases(L, mode, ph);
@@ -360,6 +368,10 @@ void enqueue_backward(StaHandle* h, int mode, float gamma, cudaStream_t st) {
     if (mode & 2) {
         ProfScope ps(h, pr, STA_PROF_SEED, st);
         launch_seed(h->g, h->s, gamma, st);
+    }
+    if ((mode & 2) && h->g.ep_clk) {
+        ProfScope ps(h, pr, STA_PROF_SEED, st);
+        launch_cap_seed(h->g, h->s, gamma, st);
     }
     for (int l = L.L - 1; l >= 0; --l) {
         ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJOINT : STA_PROF_REQUIRED, st);
@@ -471,6 +483,11 @@ StaStatus init_batch(StaHandle* h) {
     BSTEP(h->alloc(b.part, (size_t)L.npart * kPartFloats * Bp));
     BSTEP(h->alloc(b.rpart, (size_t)L.npart * kPartFloats * Bp));
     BSTEP(h->alloc(b.net_gload, N * Bp));
+    b.cap_seed = nullptr;
+    if (!L.ep_clk.empty()) {
+        BSTEP(h->alloc(b.cap_seed, P * Bp));
+        if (cudaMemset(b.cap_seed, 0, P * Bp * 4) != cudaSuccess) return set_err(STA_ERR_CUDA, "cudaMemset failed");
+    }
     std::vector<int32_t> inv(P);
     for (size_t i = 0; i < P; ++i) inv[L.pin_orig[i]] = (int32_t)i;
     BSTEP(h->upload(h->pin_int, inv));
@@ -669,6 +686,8 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     }
     STEP(h->upload(g.ep_pin, L.ep_pin));
     STEP(h->upload(g.ep_rat, L.ep_rat));
+    g.ep_clk = nullptr;
+    if (!L.ep_clk.empty()) STEP(h->upload(g.ep_clk, L.ep_clk));
     g.r = L.r_per_um;
     g.c = L.c_per_um;
     g.P = L.P;
@@ -722,6 +741,11 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         STEP(h->alloc(s.red, (size_t)kRedBlocks * 8));
         STEP(h->alloc(s.summary, STA_SUM_COUNT));
         STEP(h->alloc(s.params, 4));
+        s.cap_seed = nullptr;
+        if (!L.ep_clk.empty()) {
+            STEP(h->alloc(s.cap_seed, P));
+            if (cudaMemset(s.cap_seed, 0, P * 4) != cudaSuccess) return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
+        }
         auto zero = [&](void* p, size_t bytes) { return cudaMemset(p, 0, bytes); };
         if (zero(s.xy, P * 8) || zero(s.load, L.N * 4) || zero(s.wdi, P * 8) || zero(s.ats, P * 8) ||
             zero(s.adel, (size_t)L.A * 16) || zero(s.g_ats, P * 8) || zero(s.g_slew, P * 8) || zero(s.grad, P * 8) ||
@@ -761,7 +785,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     if (h->profile) {  // event pairs for every launch of each sequence, made before any capture
         const size_t nl = (size_t)L.L;
         const std::pair<StaHandle::Prof*, size_t> sizes[] = {
-            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 3}, {&h->prof_rat, 2 * nl + 2}, {&h->prof_adj, 2 * nl + 2},
+            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 3}, {&h->prof_rat, 2 * nl + 2}, {&h->prof_adj, 2 * nl + 3},
             {&h->prof_out, 1}};
         for (const auto& ps : sizes) {
             ps.first->kind.assign(ps.second, 0);

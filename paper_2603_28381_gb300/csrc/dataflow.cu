@@ -616,7 +616,8 @@ __device__ __forceinline__ float bwd_apply(const DevState& s, const BwdPre& b, i
         const float gD = GA * b.w[k];
         const float gsv = fmaf(gD, b.dDs[k], k == b.amax ? GS * b.dSs : 0.f);
         if ((mode & 1) && use) st_relaxed_f(s.rat + qr, rv);  // words the sink's own task polls
-        if (adj && use) st_relaxed_f(s.g_ats + qa, gD);
+        // a capturing clock pin also carries its endpoint's setup term
+        if (adj && use) st_relaxed_f(s.g_ats + qa, (s.cap_seed && r == 0) ? gD + __ldcg(s.cap_seed + b.pin[k]) : gD);
         if (adj && use) st_relaxed_f(s.g_slew + qa, gsv);
         gl = (adj && use) ? fmaf(gD, b.dDl[k], gl) : gl;
     }

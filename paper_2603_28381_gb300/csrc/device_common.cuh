@@ -183,7 +183,8 @@ __device__ float arc_adjoint(const DevNet& g, const DevState& s, int n, int d, i
             const float D = s.adel[4 * a + 2 + rf];
             const float w = expf((s.ats[2 * i + rfi] + D - atsd) / gamma);
             const float gD = GA * w;
-            s.g_ats[2 * i + rfi] = gD;
+            // a capturing clock pin also carries its endpoint's setup term
+            s.g_ats[2 * i + rfi] = (s.cap_seed && rfi == 0) ? gD + s.cap_seed[i] : gD;
             gsl[k] = gD * dDs;
             gl = fmaf(gD, dDl, gl);
             pin_c[k] = 2 * i + rfi;

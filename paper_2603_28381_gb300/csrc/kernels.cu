@@ -360,11 +360,43 @@ __device__ void ep_block_reduce(EpAcc& acc, float gamma) {
     acc = sh[0];
 }
 
+// Bounds of endpoint e: the constraint (early = hold, late = setup) and, with a
+// propagated clock, the capturing clock pin's rising arrival: its late arrival
+// moves the hold bound, its early arrival the setup bound.  Returns the clock
+// pin, -1 without one.
+__device__ __forceinline__ int ep_bounds(const DevNet& g, const DevState& s, int e, float4& con) {
+    con = reinterpret_cast<const float4*>(g.ep_rat)[e];
+    const int k = g.ep_clk ? g.ep_clk[e] : -1;
+    if (k >= 0) {
+        const float4 ak = reinterpret_cast<const float4*>(s.at)[k];
+        con.x += ak.z;
+        con.y += ak.z;
+        con.z += ak.x;
+        con.w += ak.x;
+    }
+    return k;
+}
+
+// d loss / d s of an endpoint's late rise / fall slacks s = bound - LSE arrival
+// (TNS_gamma term and, when WNS_gamma is finite, its term)
+__device__ __forceinline__ float2 ep_dloss(float4 con, float2 z, float gamma, float W, float wt, float ww) {
+    const float sr = con.z - z.x, sf = con.w - z.y;
+    const float te = softmin3(sr, sf, gamma);
+    float gr = wt * expf(-(sr - te) / gamma), gf = wt * expf(-(sf - te) / gamma);
+    if (isfinite(W)) {
+        gr += ww * expf(-(sr - W) / gamma);
+        gf += ww * expf(-(sf - W) / gamma);
+    }
+    return make_float2(gr, gf);
+}
+
 __global__ void __launch_bounds__(kBlock) k_ep1(DevNet g, DevState s, float gamma, int lse) {
     EpAcc acc = ep_identity();
     for (int e = blockIdx.x * kBlock + threadIdx.x; e < g.E; e += gridDim.x * kBlock) {
         const int p = g.ep_pin[e];
-        const float4 con = reinterpret_cast<const float4*>(g.ep_rat)[e];
+        float4 con;
+        // a clocked endpoint's bounds are this analysis's required-time seeds
+        if (ep_bounds(g, s, e, con) >= 0) reinterpret_cast<float4*>(s.rat)[p] = con;
         const float4 at = reinterpret_cast<const float4*>(s.at)[p];
         const float se = fminf(at.x - con.x, at.y - con.y);
         const float sl = fminf(con.z - at.z, con.w - at.w);
@@ -412,16 +444,26 @@ __global__ void __launch_bounds__(kBlock) k_seed(DevNet g, DevState s, float gam
     const float wt = s.params[0], ww = s.params[1];
     for (int e = blockIdx.x * kBlock + threadIdx.x; e < g.E; e += gridDim.x * kBlock) {
         const int p = g.ep_pin[e];
-        const float4 con = reinterpret_cast<const float4*>(g.ep_rat)[e];
-        const float2 z = reinterpret_cast<const float2*>(s.ats)[p];
-        const float sr = con.z - z.x, sf = con.w - z.y;
-        const float te = softmin3(sr, sf, gamma);
-        float gr = wt * expf(-(sr - te) / gamma), gf = wt * expf(-(sf - te) / gamma);
-        if (isfinite(W)) {
-            gr += ww * expf(-(sr - W) / gamma);
-            gf += ww * expf(-(sf - W) / gamma);
-        }
-        reinterpret_cast<float2*>(s.g_ats)[p] = make_float2(-gr, -gf);
+        float4 con;
+        ep_bounds(g, s, e, con);
+        const float2 gl = ep_dloss(con, reinterpret_cast<const float2*>(s.ats)[p], gamma, W, wt, ww);
+        reinterpret_cast<float2*>(s.g_ats)[p] = make_float2(-gl.x, -gl.y);
+    }
+}
+
+// Propagated clock: the setup bound of a clocked endpoint holds its clock pin's
+// early rising arrival, which (on a net driven by a startpoint) moves one for
+// one with the pin's wire delay, so d loss / d bound enters the adjoint of the
+// clock pin's rising LSE arrival, added where the arc step writes it.
+__global__ void __launch_bounds__(kBlock) k_cap_seed(DevNet g, DevState s, float gamma) {
+    const float W = (float)s.summary[STA_SUM_WNS_GAMMA];
+    const float wt = s.params[0], ww = s.params[1];
+    for (int e = blockIdx.x * kBlock + threadIdx.x; e < g.E; e += gridDim.x * kBlock) {
+        float4 con;
+        const int k = ep_bounds(g, s, e, con);
+        if (k < 0) continue;
+        const float2 gl = ep_dloss(con, reinterpret_cast<const float2*>(s.ats)[g.ep_pin[e]], gamma, W, wt, ww);
+        s.cap_seed[k] = gl.x + gl.y;
     }
 }
 
@@ -502,6 +544,11 @@ void launch_set_weights(const DevState& s, const float* w_dev, float w0, float w
 void launch_seed(const DevNet& g, const DevState& s, float gamma, cudaStream_t st) {
     if (g.E == 0) return;
     k_seed<<<grid_for(g.E), kBlock, 0, st>>>(g, s, gamma);
+}
+
+void launch_cap_seed(const DevNet& g, const DevState& s, float gamma, cudaStream_t st) {
+    if (g.E == 0 || !g.ep_clk) return;
+    k_cap_seed<<<grid_for(g.E), kBlock, 0, st>>>(g, s, gamma);
 }
 
 void launch_scatter(const DevNet& g, const float* in, float* out, int k, int np, cudaStream_t st) {

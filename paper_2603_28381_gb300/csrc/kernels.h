@@ -24,6 +24,7 @@ struct DevNet {
     const float4* lib_cell;      // [T*4*2*36*2] corner-packed cells (delay float4, slew float4)
     const int32_t* ep_pin;       // [E]
     const float* ep_rat;         // [E*4]
+    const int32_t* ep_clk;       // [E] capturing clock pin (propagated clock), -1 none; null: ideal clock
     float r, c;                  // Ohm/um, fF/um
     int32_t P, Pnet, N, E;
 };
@@ -45,6 +46,8 @@ struct DevState {
     double* red;       // [kRedBlocks * 8] endpoint-reduction partials (scratch)
     double* summary;   // [STA_SUM_COUNT]
     float* params;     // [4] w_tns, w_wns
+    float* cap_seed;   // [P] d loss / d (rising arrival) of capturing clock pins, 0 elsewhere;
+                       // null without a propagated clock
 };
 
 // Dataflow schedule: task lists, the counters of the large nets' gradient
@@ -93,6 +96,7 @@ struct BatchState {
     float* part;         // [npart * kPartFloats][Bp] partials of large nets, adjoint sweeps
     float* rpart;        // the same for required-time sweeps (which may overlap an adjoint sweep)
     float* net_gload;    // [N][Bp] d loss / d load of large nets
+    float* cap_seed;     // [P][Bp] as DevState::cap_seed; null without a propagated clock
 };
 constexpr size_t kBatchEpBytes = 48;  // one endpoint partial
 constexpr int kPlacePerWarp = 8;       // sweep tasks: 8 placements x 4 conditions per warp
@@ -148,6 +152,9 @@ void launch_bwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0
                       int mode, cudaStream_t st);
 void launch_set_weights(const DevState& s, const float* w_dev, float w0, float w1, cudaStream_t st);
 void launch_seed(const DevNet& g, const DevState& s, float gamma, cudaStream_t st);
+// propagated clock: d loss / d (early rising arrival) of each capturing clock pin
+void launch_cap_seed(const DevNet& g, const DevState& s, float gamma, cudaStream_t st);
+void launch_batch_cap_seed(const DevNet& g, const BatchState& bs, float gamma, cudaStream_t st);
 // out[orig(p)*k + q] = in[p*k + q] for the first `np` internal pins
 void launch_scatter(const DevNet& g, const float* in, float* out, int k, int np, cudaStream_t st);
 void launch_pin_slack(const DevNet& g, const DevState& s, float* out, cudaStream_t st);

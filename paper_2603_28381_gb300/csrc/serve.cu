@@ -43,7 +43,8 @@ double now_s() {
 // Host copy of a netlist description and library (the caller's arrays are
 // only borrowed during sta_server_add_netlist).
 struct HostNetlist {
-    std::vector<int32_t> net_ptr, net_pins, cell_type, cell_in_ptr, cell_in_pins, cell_out_pin, start_pins, end_pins;
+    std::vector<int32_t> net_ptr, net_pins, cell_type, cell_in_ptr, cell_in_pins, cell_out_pin, start_pins, end_pins,
+        end_clock;
     std::vector<float> pin_cap, start_at, start_slew, end_rat;
     std::vector<int32_t> type_num_arcs;
     std::vector<int8_t> arc_unate;
@@ -135,6 +136,7 @@ StaStatus copy_netlist(const StaNetlistDesc& d, const StaLibrary& l, HostNetlist
     copy_in(o.start_slew, d.start_slew, (size_t)d.num_start * 4);
     copy_in(o.end_pins, d.end_pins, (size_t)d.num_end);
     copy_in(o.end_rat, d.end_rat, (size_t)d.num_end * 4);
+    if (d.end_clock) copy_in(o.end_clock, d.end_clock, (size_t)d.num_end);
     copy_in(o.type_num_arcs, l.type_num_arcs, T);
     copy_in(o.arc_unate, l.arc_unate, T * STA_MAX_ARCS);
     copy_in(o.slew_index, l.slew_index, T * STA_LUT);
@@ -154,6 +156,7 @@ StaStatus copy_netlist(const StaNetlistDesc& d, const StaLibrary& l, HostNetlist
     o.nl.start_slew = o.start_slew.data();
     o.nl.end_pins = o.end_pins.data();
     o.nl.end_rat = o.end_rat.data();
+    o.nl.end_clock = d.end_clock ? o.end_clock.data() : nullptr;
     o.lib = l;
     o.lib.type_num_arcs = o.type_num_arcs.data();
     o.lib.arc_unate = o.arc_unate.data();
@@ -190,12 +193,14 @@ namespace {
 // scratch, from the description alone (used until it has been created once):
 // per pin the per-pin state, staging and gradient scratch (132 B); per net or
 // cell output the per-net arrays and the task lists (120 B); per arc the arc
-// delays and dependency edges (32 B); per endpoint 28 B.
+// delays and dependency edges (32 B); per endpoint 28 B; with a propagated
+// clock 4 B more per pin (clock seeds) and per endpoint (its clock pin).
 size_t estimate_bytes(const HostNetlist& hn) {
     const StaNetlistDesc& d = hn.nl;
     const size_t A = d.num_cells ? (size_t)hn.cell_in_ptr[d.num_cells] : 0;
-    return (size_t)d.num_pins * 132 + ((size_t)d.num_nets + d.num_cells) * 120 + A * 32 + (size_t)d.num_end * 28 +
-           (1u << 20);
+    const size_t clk = d.end_clock ? 4 : 0;
+    return (size_t)d.num_pins * (132 + clk) + ((size_t)d.num_nets + d.num_cells) * 120 + A * 32 +
+           (size_t)d.num_end * (28 + clk) + (1u << 20);
 }
 
 }  // namespace

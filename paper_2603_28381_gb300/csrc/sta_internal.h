@@ -96,6 +96,7 @@ struct Layout {
     std::vector<float> rat0;           // [P*4] endpoint constraint, else -inf/+inf
     std::vector<int32_t> ep_pin;       // [E] internal pin of each endpoint
     std::vector<float> ep_rat;         // [E*4]
+    std::vector<int32_t> ep_clk;       // [E] internal capturing clock pin, -1 none; empty: ideal clock
 
     // library, device form
     std::vector<float> lib_idx;        // [T*16] slew index (0..6), load index (8..14)

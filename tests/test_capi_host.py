@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol(sta):
     for name in sorted(declared):
         assert hasattr(lib, name), f"libsta.so does not export {name}"
     assert set(sta._sta.EXPORTS) == declared
-    assert sta.sta_abi_version() == 1
+    assert sta.sta_abi_version() == 2
 
 
 @pytest.mark.parametrize("make", [lambda: netgen.tiny_design(0), lambda: netgen.tiny_design(5),
@@ -99,6 +99,56 @@ def test_levelize_rejects_cycles_and_malformed_netlists(sta):
     nl, _ = b.build()
     with pytest.raises(sta.StaError):
         sta.sta_levelize(nl)
+
+
+def test_levelize_checks_capturing_clock_pins(sta):
+    """A propagated clock's capturing pin must be a cell input on a net driven
+    by a startpoint, and capture one endpoint at most."""
+    w = netgen.tiny_design(0, clock_nets=2)
+    nl = w.netlist
+    lv, L, _, _ = sta.sta_levelize(nl)
+    np.testing.assert_array_equal(lv, oracle.levels(nl))
+    bad = []
+    b1 = netgen.Netlist(**{f.name: getattr(nl, f.name) for f in netgen.dataclasses.fields(nl)})
+    b1.end_clock = nl.end_clock.copy()
+    b1.end_clock[np.flatnonzero(nl.end_clock >= 0)[0]] = nl.cell_out_pin[0]  # a cell output
+    bad.append(b1)
+    b2 = netgen.Netlist(**{f.name: getattr(nl, f.name) for f in netgen.dataclasses.fields(nl)})
+    b2.end_clock = nl.end_clock.copy()
+    j = np.flatnonzero(nl.end_clock >= 0)[:2]
+    b2.end_clock[j[1]] = b2.end_clock[j[0]]  # one clock pin capturing two endpoints
+    bad.append(b2)
+    b3 = netgen.Netlist(**{f.name: getattr(nl, f.name) for f in netgen.dataclasses.fields(nl)})
+    b3.end_clock = nl.end_clock.copy()
+    b3.end_clock[0] = nl.num_pins  # out of range
+    bad.append(b3)
+    # a comb cell input on a net driven by a cell output (not a startpoint)
+    b4 = netgen.Netlist(**{f.name: getattr(nl, f.name) for f in netgen.dataclasses.fields(nl)})
+    b4.end_clock = nl.end_clock.copy()
+    drv = set(nl.net_pins[nl.net_ptr[:-1]].tolist())
+    starts = set(nl.start_pins.tolist())
+    for n in range(nl.num_nets):
+        if nl.net_pins[nl.net_ptr[n]] not in starts:
+            s = nl.net_pins[nl.net_ptr[n] + 1:nl.net_ptr[n + 1]]
+            s = [p for p in s if p in set(nl.cell_in_pins.tolist()) and p not in drv]
+            if s:
+                b4.end_clock[np.flatnonzero(nl.end_clock >= 0)[0]] = s[0]
+                break
+    bad.append(b4)
+    for b in bad:
+        with pytest.raises(sta.StaError) as e:
+            sta.sta_levelize(b)
+        assert e.value.status == 1
+        with pytest.raises(oracle.OracleError) if b is not b2 else _nothing():
+            oracle.sta(b, w.library, w.xy)
+
+
+class _nothing:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
 
 
 def test_product_path_fails_loudly_without_gpu(sta):
