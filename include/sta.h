@@ -85,10 +85,11 @@ typedef struct {
                                     late rising arrival (hold: latest capture edge) and its
                                     late bound the early rising arrival (setup: earliest
                                     edge); the adjoint of the smoothed loss follows the
-                                    setup term into the clock wire.  A clock pin must be a
-                                    cell input on a net driven by a startpoint (an unbuffered
-                                    clock net) and capture at most one endpoint
-                                    (STA_ERR_INVALID_ARG otherwise). */
+                                    setup term into the clock wire.  A clock pin must be the
+                                    input of a one-input cell (a flop's clock->Q arc) on a net
+                                    driven by a startpoint (an unbuffered clock net) and
+                                    capture at most one endpoint (STA_ERR_INVALID_ARG
+                                    otherwise). */
 } StaNetlistDesc;
 
 /* Liberty-like library (Section 3.1.2): per type and arc, per output

@@ -507,6 +507,7 @@ struct BCell {
     float adel[STA_MAX_ARCS], w[STA_MAX_ARCS], dDs[STA_MAX_ARCS], dDl[STA_MAX_ARCS];
     int amax;
     float dSs, dSl;
+    float cs;  // propagated clock: the setup seed of a one-input cell's clock pin (rising lane)
 };
 
 template <int mode>
@@ -519,7 +520,7 @@ __device__ __forceinline__ BCell bcell_pre(const DevNet& g, const BatchState& bs
     bc.na = bc.t >= 0 ? g.net_arc_ptr[n + 1] - a0 : 0;
     bc.rfi = 0;
     bc.amax = -1;
-    bc.dSs = bc.dSl = 0.f;
+    bc.dSs = bc.dSl = bc.cs = 0.f;
 #pragma unroll
     for (int k = 0; k < STA_MAX_ARCS; ++k) {
         bc.pin[k] = 0;
@@ -568,6 +569,10 @@ __device__ __forceinline__ BCell bcell_pre(const DevNet& g, const BatchState& bs
             }
         }
     }
+    // a capturing clock pin is the input of a one-input cell; its seed is read
+    // here, before the wait, and added to the rising adjoint it writes
+    if ((mode & 2) && el && bs.cap_seed && bc.na == 1 && (bc.rfi & 1) == 0)
+        bc.cs = __ldcg(bs.cap_seed + ix(bc.pin[0], Bp, b));
     return bc;
 }
 
@@ -588,8 +593,7 @@ __device__ __forceinline__ float bcell_apply(const BatchState& bs, const BCell& 
             if ((mode & 2) && el) {
                 const float gD = GA * bc.w[k];
                 // a capturing clock pin also carries its endpoint's setup term
-                st_relaxed_f(bs.g_ats + ix(2 * bc.pin[k] + r, Bp, b),
-                             (bs.cap_seed && r == 0) ? gD + __ldcg(bs.cap_seed + ix(bc.pin[k], Bp, b)) : gD);
+                st_relaxed_f(bs.g_ats + ix(2 * bc.pin[k] + r, Bp, b), (bs.cap_seed && k == 0) ? gD + bc.cs : gD);
                 st_relaxed_f(bs.g_slew + ix(2 * bc.pin[k] + r, Bp, b),
                              fmaf(gD, bc.dDs[k], k == bc.amax ? GS * bc.dSs : 0.f));
                 gl = fmaf(gD, bc.dDl[k], gl);

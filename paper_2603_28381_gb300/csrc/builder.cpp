@@ -104,9 +104,11 @@ StaStatus check_netlist(const StaNetlistDesc& nl, const StaLibrary* lib, Roles& 
             const int32_t k = nl.end_clock[e];
             if (k == -1) continue;
             if (k < -1 || k >= P) return err = "end_clock out of range", STA_ERR_INVALID_ARG;
-            if (r.sink_net[k] < 0 || r.start_of[nl.net_pins[nl.net_ptr[r.sink_net[k]]]] < 0 || r.in_cell[k] < 0)
+            if (r.sink_net[k] < 0 || r.start_of[nl.net_pins[nl.net_ptr[r.sink_net[k]]]] < 0 || r.in_cell[k] < 0 ||
+                nl.cell_in_ptr[r.in_cell[k] + 1] - nl.cell_in_ptr[r.in_cell[k]] != 1)
                 return err = "capturing clock pin " + std::to_string(k) +
-                             " must be a cell input on a net driven by a startpoint", STA_ERR_INVALID_ARG;
+                             " must be the input of a one-input cell on a net driven by a startpoint",
+                       STA_ERR_INVALID_ARG;
             if (used[k]++) return err = "clock pin " + std::to_string(k) + " captures two endpoints",
                                   STA_ERR_INVALID_ARG;
         }

@@ -523,6 +523,7 @@ struct BwdPre {
     float w[STA_MAX_ARCS], dDs[STA_MAX_ARCS], dDl[STA_MAX_ARCS];
     int amax;
     float dSs, dSl;
+    float cs;  // propagated clock: the setup seed of a one-input cell's clock pin (rising lane)
 };
 
 // a lane with no driver cell (asserted driver or idle lane)
@@ -531,7 +532,7 @@ __device__ __forceinline__ BwdPre bwd_none() {
     b.t = -1;
     b.a0 = b.na = b.rfi = 0;
     b.amax = -1;
-    b.dSs = b.dSl = 0.f;
+    b.dSs = b.dSl = b.cs = 0.f;
 #pragma unroll
     for (int k = 0; k < STA_MAX_ARCS; ++k) {
         b.pin[k] = 0;
@@ -546,7 +547,7 @@ __device__ __forceinline__ BwdPre bwd_pre(const DevNet& g, const DevState& s, in
     b.t = g.net_drv[n];
     b.a0 = b.na = b.rfi = 0;
     b.amax = -1;
-    b.dSs = b.dSl = 0.f;
+    b.dSs = b.dSl = b.cs = 0.f;
 #pragma unroll
     for (int k = 0; k < STA_MAX_ARCS; ++k) {
         b.pin[k] = 0;
@@ -564,6 +565,9 @@ __device__ __forceinline__ BwdPre bwd_pre(const DevNet& g, const DevState& s, in
             b.rfi |= (rf ^ ((un >> k) & 1)) << k;
             if (mode & 1) b.adel[k] = s.adel[4 * (b.a0 + k) + c];
         }
+    // a capturing clock pin is the input of a one-input cell; its seed is read
+    // here, before the wait, and added to the rising adjoint it writes
+    if ((mode & 2) && el == 1 && s.cap_seed && b.na == 1 && (b.rfi & 1) == 0) b.cs = __ldcg(s.cap_seed + b.pin[0]);
     if ((mode & 2) && el == 1) {
         const float ld = s.load[n];
         const float* li = g.lib_idx + b.t * kLibStride + 8;
@@ -617,7 +621,7 @@ __device__ __forceinline__ float bwd_apply(const DevState& s, const BwdPre& b, i
         const float gsv = fmaf(gD, b.dDs[k], k == b.amax ? GS * b.dSs : 0.f);
         if ((mode & 1) && use) st_relaxed_f(s.rat + qr, rv);  // words the sink's own task polls
         // a capturing clock pin also carries its endpoint's setup term
-        if (adj && use) st_relaxed_f(s.g_ats + qa, (s.cap_seed && r == 0) ? gD + __ldcg(s.cap_seed + b.pin[k]) : gD);
+        if (adj && use) st_relaxed_f(s.g_ats + qa, (s.cap_seed && k == 0) ? gD + b.cs : gD);
         if (adj && use) st_relaxed_f(s.g_slew + qa, gsv);
         gl = (adj && use) ? fmaf(gD, b.dDl[k], gl) : gl;
     }
