@@ -306,7 +306,8 @@ def run_reference(args):
             "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(w, args, {"reference": "FP64 CPU oracle (oracle/sta_oracle.c), "
-                                                       "single thread, as it stands"}),
+                                                       "single thread, as it stands",
+                                          "levels": int(oracle.levels(w.netlist).max()) + 1}),
             "cpu_baseline": {"value": value, "unit": "pins/s", "cores": 1, "kind": "oracle",
                              "sample": sample_note},
             "e2e": {"value": value, "unit": "pins/s", "h2d_bytes_per_step": 0,
@@ -434,6 +435,19 @@ def run_ours(args):
                 "ms_by_kind": {k: round(v, 4) for k, v in acc.items()},
                 "step_algorithmic_bytes": int(sum(abytes.values())),
                 "step_frac": sum(abytes.values()) / (total_s / args.steps) / 1e9 / peak}
+    # depth floor: the forward and the fused backward sweep each need at least one
+    # dependent round trip through L2 per level (a task reads what its producers stored)
+    lat_l2 = sta.sta_measure_latency(32 << 20, 20000)
+    lat_dram = sta.sta_measure_latency(512 << 20, 5000)
+    levels = int(prof_eng.sizes["levels"])
+    floor_ms = 2 * levels * lat_l2 / 1e6
+    sweeps_ms = acc.get("forward", 0.0) + acc.get("adjoint", 0.0) + acc.get("required", 0.0)
+    roofline["depth_floor"] = {"levels": levels, "dependent_steps": 2 * levels,
+                               "l2_dependent_load_ns": round(lat_l2, 1),
+                               "dram_dependent_load_ns": round(lat_dram, 1),
+                               "floor_ms": round(floor_ms, 4),
+                               "sweeps_ms": round(sweeps_ms, 4),
+                               "sweeps_over_floor": round(sweeps_ms / floor_ms, 2)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

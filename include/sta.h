@@ -365,6 +365,19 @@ void sta_destroy(StaHandle *h);
 /* Message of the calling thread's last failed call ("" if none). */
 const char *sta_last_error(void);
 
+/* Dependent-load latency of the memory system, the unit of the sweeps' depth
+ * floor (each level of a sweep needs at least one round trip through L2 after
+ * its producers' stores).  One GPU thread follows a random single-cycle
+ * permutation of bytes / 4 int32 indices (Sattolo's algorithm, fixed seed),
+ * every load's address being the previous load's value, for `steps` loads
+ * through L2 (ld.global.cg); the buffer is read once beforehand, so a buffer
+ * well below the L2 size measures an L2 hit and one well above it mostly DRAM.
+ * Writes nanoseconds per load (CUDA events around the chase) to
+ * *ns_per_load.  Allocates and frees its own device buffer on the current
+ * device and synchronizes it.  bytes in [64, 2^33], steps in [1, 10^7]
+ * (STA_ERR_INVALID_ARG otherwise); STA_ERR_OOM / STA_ERR_CUDA on failure. */
+StaStatus sta_measure_latency(int64_t bytes, int32_t steps, double *ns_per_load);
+
 /* STA_ABI_VERSION of the loaded library. */
 int sta_abi_version(void);
 

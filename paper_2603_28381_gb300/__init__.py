@@ -18,10 +18,10 @@ import numpy as np
 
 from . import _sta
 from ._sta import (STA_FWD_LSE, STA_FWD_RAT, SUMMARY_KEYS, StaError, sta_abi_version,
-                   sta_last_error, sta_levelize)
+                   sta_last_error, sta_levelize, sta_measure_latency)
 
 __all__ = ["StaEngine", "timing_loss", "TimingLoss", "StaError", "sta_levelize", "STA_FWD_LSE",
-           "STA_FWD_RAT", "SUMMARY_KEYS", "sta_abi_version", "sta_last_error"]
+           "STA_FWD_RAT", "SUMMARY_KEYS", "sta_abi_version", "sta_last_error", "sta_measure_latency"]
 
 
 def _torch():

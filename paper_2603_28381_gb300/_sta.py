@@ -96,6 +96,7 @@ def _load() -> ctypes.CDLL:
         "sta_query_pins": ([H, _p, _p, _p, _p, _p, ctypes.c_int, _p], ctypes.c_int),
         "sta_query_endpoints": ([H, _p, ctypes.c_int, _p], ctypes.c_int),
         "sta_query_slack": ([H, _p, _p, _p], ctypes.c_int),
+        "sta_measure_latency": ([ctypes.c_int64, ctypes.c_int32, _p], ctypes.c_int),
         "sta_levelize": ([ctypes.POINTER(StaNetlistDesc), _p, _p, _p, _p], ctypes.c_int),
         "sta_query_sizes": ([H, _p], ctypes.c_int),
         "sta_plan_tasks": ([ctypes.POINTER(StaNetlistDesc), ctypes.POINTER(StaLibrary), _i32, _i32, _i32, _p],
@@ -133,7 +134,7 @@ EXPORTS = ("sta_create", "sta_set_positions", "sta_forward", "sta_backward_grad"
            "sta_synchronize", "sta_debug_expire_wait", "sta_autotune", "sta_server_create",
            "sta_server_add_netlist", "sta_server_submit", "sta_server_poll", "sta_server_stats",
            "sta_server_destroy", "sta_server_clock", "sta_server_netlist_bytes", "sta_query_net_rc",
-           "sta_ablation_net_rc", "sta_plan_tasks", "sta_query_slack",
+           "sta_ablation_net_rc", "sta_plan_tasks", "sta_query_slack", "sta_measure_latency",
            "sta_last_error", "sta_abi_version", "sta_endpoint_summary_noalloc")
 
 
@@ -148,6 +149,13 @@ def sta_last_error() -> str:
 
 def sta_abi_version() -> int:
     return int(_lib.sta_abi_version())
+
+
+def sta_measure_latency(nbytes: int, steps: int) -> float:
+    """Nanoseconds per dependent load through L2 over a random cycle of nbytes."""
+    out = ctypes.c_double()
+    _check(_lib.sta_measure_latency(int(nbytes), int(steps), ctypes.byref(out)), "sta_measure_latency")
+    return float(out.value)
 
 
 class _Keep:

@@ -577,6 +577,46 @@ extern "C" {
 
 int sta_abi_version(void) { return STA_ABI_VERSION; }
 
+StaStatus sta_measure_latency(int64_t bytes, int32_t steps, double* ns_per_load) {
+    if (!ns_per_load || bytes < 64 || bytes > (int64_t(1) << 33) || steps < 1 || steps > 10000000)
+        return set_err(STA_ERR_INVALID_ARG, "sta_measure_latency: bytes in [64, 2^33], steps in [1, 1e7]");
+    const int64_t n = bytes / 4;
+    // Sattolo's algorithm: a uniformly random cyclic permutation (one cycle through every index)
+    std::vector<int32_t> next((size_t)n);
+    for (int64_t i = 0; i < n; ++i) next[(size_t)i] = (int32_t)i;
+    uint64_t x = 0x9e3779b97f4a7c15ull;
+    for (int64_t i = n - 1; i > 0; --i) {
+        x ^= x << 13;
+        x ^= x >> 7;
+        x ^= x << 17;
+        const int64_t j = (int64_t)(x % (uint64_t)i);  // j < i
+        std::swap(next[(size_t)i], next[(size_t)j]);
+    }
+    int32_t* d = nullptr;
+    if (cudaMalloc(&d, (size_t)(n + 1) * sizeof(int32_t)) != cudaSuccess)
+        return set_err(STA_ERR_OOM, "sta_measure_latency: cudaMalloc failed");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.f;
+    cudaError_t ce = cudaMemcpy(d, next.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce == cudaSuccess) {
+        launch_touch(d, n, d + n, 0);
+        launch_chase(d, std::min<int64_t>(steps, 64), d + n, 0);  // warm the launch path
+        cudaEventRecord(e0, 0);
+        launch_chase(d, steps, d + n, 0);
+        cudaEventRecord(e1, 0);
+        ce = cudaEventSynchronize(e1);
+    }
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d);
+    if (ce != cudaSuccess) return set_err(STA_ERR_CUDA, std::string("sta_measure_latency: ") + cudaGetErrorString(ce));
+    *ns_per_load = 1e6 * (double)ms / steps;
+    return STA_OK;
+}
+
 const char* sta_last_error(void) { return g_err.c_str(); }
 
 StaStatus sta_levelize(const StaNetlistDesc* nl, int32_t* net_level, int32_t* num_levels, int32_t* net_order,

@@ -152,6 +152,9 @@ void launch_bwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0
                       int mode, cudaStream_t st);
 void launch_set_weights(const DevState& s, const float* w_dev, float w0, float w1, cudaStream_t st);
 void launch_seed(const DevNet& g, const DevState& s, float gamma, cudaStream_t st);
+// memory latency probe: read a buffer once; follow next[] from index 0 for `steps` loads
+void launch_touch(const int32_t* a, long long n, int32_t* sink, cudaStream_t st);
+void launch_chase(const int32_t* next, int steps, int32_t* sink, cudaStream_t st);
 // propagated clock: d loss / d (early rising arrival) of each capturing clock pin
 void launch_cap_seed(const DevNet& g, const DevState& s, float gamma, cudaStream_t st);
 void launch_batch_cap_seed(const DevNet& g, const BatchState& bs, float gamma, cudaStream_t st);

@@ -198,3 +198,10 @@ def test_task_plans_cover_every_sink_in_dependency_order(tile_pins, tile_nets, c
     assert plan["backward_tasks"] == (plan["forward_tasks"] - plan["chunks"]) + 2 * plan["chunks"] + plan["split_nets"]
     assert plan["max_nets"] <= tile_nets
     assert plan["max_pins"] <= max(tile_pins, chunk + 1)
+
+
+def test_latency_probe_checks_its_arguments(sta):
+    for nbytes, steps in ((0, 10), (1 << 20, 0), (1 << 40, 10)):
+        with pytest.raises(sta.StaError) as e:
+            sta.sta_measure_latency(nbytes, steps)
+        assert e.value.status == 1

@@ -201,3 +201,11 @@ def test_query_slack_matches_the_other_queries():
     assert np.array_equal(ps, eng.pins(at=False, slew=False, rat=False, ats=False)["slack"])
     assert np.array_equal(es, eng.endpoints())
     eng.close()
+
+
+def test_latency_probe_l2_and_dram():
+    import paper_2603_28381_gb300 as sta
+    l2 = sta.sta_measure_latency(16 << 20, 4000)
+    dram = sta.sta_measure_latency(512 << 20, 2000)
+    assert 50.0 < l2 < 5000.0
+    assert dram > 0.8 * l2
