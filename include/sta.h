@@ -282,7 +282,9 @@ StaStatus sta_query_endpoints(StaHandle *h, float *slack, int on_device, void *s
  * output, else 1 + the largest level among the nets feeding the driver cell's
  * inputs (Section 2.1 stage 2).  net_level [num_nets]; *num_levels = max + 1.
  * If net_order != NULL it receives the original net ids in processing order
- * (level, then nets of <= 32 pins before larger ones, then original id), and
+ * (level; within a level nets of <= 32 pins before larger ones, then by the
+ * largest position in this order of a net feeding the driver cell, -1 if none,
+ * then original id), and
  * if pin_order != NULL [net_ptr[num_nets]] the original pin ids in device
  * layout order (each net's driver, then its sinks by ascending id). */
 StaStatus sta_levelize(const StaNetlistDesc *nl, int32_t *net_level, int32_t *num_levels,

@@ -46,10 +46,26 @@ def test_levelize_bit_exact_against_oracle_dfs(sta, make):
     ref = oracle.levels(nl)
     np.testing.assert_array_equal(lv, ref)
     assert L == ref.max() + 1
-    # processing order: (level, nets of > 32 pins after the others, id)
+    # processing order: level; within a level nets of > 32 pins after the others,
+    # then the latest position of a net feeding the driver cell (-1: none), then id
     size = np.diff(nl.net_ptr)
-    expect = np.lexsort((np.arange(nl.num_nets), size > 32, ref))
-    np.testing.assert_array_equal(order, expect)
+    sink_net = np.full(nl.num_pins, -1, np.int64)
+    for n in range(nl.num_nets):
+        sink_net[nl.net_pins[nl.net_ptr[n] + 1:nl.net_ptr[n + 1]]] = n
+    out_cell = {int(p): c for c, p in enumerate(nl.cell_out_pin)}
+    pos = np.full(nl.num_nets, -1, np.int64)
+    expect = []
+    for lvl in range(L):
+        nets = np.flatnonzero(ref == lvl)
+        key = []
+        for n in nets:
+            c = out_cell.get(int(nl.net_pins[nl.net_ptr[n]]), -1)
+            ins = nl.cell_in_pins[nl.cell_in_ptr[c]:nl.cell_in_ptr[c + 1]] if c >= 0 else []
+            key.append(max([pos[sink_net[p]] for p in ins if sink_net[p] >= 0], default=-1))
+        o = nets[np.lexsort((nets, np.asarray(key), size[nets] > 32))]
+        pos[o] = len(expect) + np.arange(o.size)
+        expect.extend(o.tolist())
+    np.testing.assert_array_equal(order, np.asarray(expect))
     # device pin order: per net in processing order, driver then sinks ascending
     exp_pins = []
     for n in expect:
