@@ -892,7 +892,9 @@ __device__ void bwd_df_grad(const DevNet& g, const DevState& s, const DfState& d
 }
 
 template <int mode>
-__global__ void __launch_bounds__(kBlock) k_bwd_df(DevNet g, DevState s, DfState d, float gamma) {
+// 3 blocks per SM (80 registers, no spills): more warps hold backward tasks
+// ahead of the front, so a task's pre-wait loads are done when its data arrives
+__global__ void __launch_bounds__(kBlock, 3) k_bwd_df(DevNet g, DevState s, DfState d, float gamma) {
     int32_t* cnt = (mode & 2) ? d.acnt : d.rcnt;
     int32_t* head = d.heads + ((mode & 2) ? 2 : 1);
     float* part = (mode & 2) ? d.apart : d.rpart;

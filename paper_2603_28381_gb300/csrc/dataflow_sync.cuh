@@ -24,7 +24,7 @@ constexpr unsigned long long kWaitBudgetNs = 1000000000ull;  // 1 s per wait
 
 // pause between two polls of a wait (ns; a scheduling hint to the SM)
 #ifndef STA_POLL_NS
-#define STA_POLL_NS 256
+#define STA_POLL_NS 128
 #endif
 
 __device__ __forceinline__ unsigned long long global_ns() {
