@@ -200,11 +200,7 @@ __device__ __forceinline__ FOut fcell_eval(const DevNet& g, const BatchState& bs
     o.sl = best_sl;
     o.z = 0.f;
     if (lse && el) {
-        float sum = 0.f;
-#pragma unroll
-        for (int k = 0; k < STA_MAX_ARCS; ++k)
-            if (k < f.na) sum += expf((cand[k] - m) / gamma);
-        o.z = m + gamma * logf(sum);
+        o.z = lse_arcs(cand, f.na, m, gamma);
     }
     return o;
 }

@@ -193,14 +193,7 @@ __device__ __forceinline__ DrvOut fwd_eval(const DevNet& g, const DevState& s, c
         cand[k] = use ? zin[k] + D : -kInf;
         m = fmaxf(m, cand[k]);
     }
-    float sum = 0.f;
-    const float mm = f.na > 0 ? m : 0.f;
-#pragma unroll
-    for (int k = 0; k < STA_MAX_ARCS; ++k) {
-        const float e = expf((cand[k] - mm) / gamma);
-        sum += k < f.na ? e : 0.f;
-    }
-    const float lse_v = mm + gamma * logf(f.na > 0 ? sum : 1.f);
+    const float lse_v = lse_arcs(cand, f.na, f.na > 0 ? m : 0.f, gamma);
     DrvOut o;
     o.at = cell ? best_at : at_c;
     o.slew = cell ? best_sl : sl_c;

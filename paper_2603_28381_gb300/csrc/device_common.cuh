@@ -71,6 +71,23 @@ __device__ __forceinline__ float lerp_cell_grad(float4 q, float ts, float ul, fl
     return fmaf(ts, r1 - r0, r0);
 }
 
+// Eq. 4 over a cell's arcs: m + gamma * log(sum_k exp((cand_k - m) / gamma)),
+// stabilised by the maximum m of the na candidates (unused slots ignored).  The
+// exponentials and the logarithm are the hardware base-2 forms (__expf, __logf)
+// with the exponent scaled by 1/gamma: a few ulp of relative error, far below
+// the parity tolerance, and a short chain of dependent instructions after a
+// task's wait.  Every schedule evaluates it with these same operations.
+__device__ __forceinline__ float lse_arcs(const float* cand, int na, float m, float gamma) {
+    const float inv_g = 1.f / gamma;
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        const float e = __expf((cand[k] - m) * inv_g);
+        sum += k < na ? e : 0.f;
+    }
+    return m + gamma * __logf(na > 0 ? sum : 1.f);
+}
+
 struct DrvOut {
     float at, slew, ats;
 };
@@ -138,11 +155,7 @@ __device__ DrvOut eval_driver(const DevNet& g, const DevState& s, int n, int d, 
     o.slew = best_sl;
     o.ats = 0.f;
     if (el && lse) {
-        float sum = 0.f;
-#pragma unroll
-        for (int k = 0; k < STA_MAX_ARCS; ++k)
-            if (a0 + k < a1) sum += expf((cand[k] - m) / gamma);
-        o.ats = m + gamma * logf(sum);
+        o.ats = lse_arcs(cand, a1 - a0, m, gamma);
     }
     return o;
 }
