@@ -296,13 +296,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_bfwd(DevNet g, BatchState bs, DfS
     const int Q = d.TF * GT;
     int q = grab(d.heads + 0);
     while (q < Q) {
-        const int next = grab(d.heads + 0);
         const int t = q / GT, gq = q - t * GT;
         const Lane L = lane_of(gq);
         const int4 task = d.ftask[t];
         if (task.y > 0) bfwd_nets<lse, true>(g, bs, d, q, task.x, task.y, L, gamma, t == stall_task);
         else bfwd_chunk<lse, true>(g, bs, d, q, task.x, task.z, task.w, L, gamma, t == stall_task);
-        q = next;  // consumers poll the words this task wrote
+        q = grab(d.heads + 0);  // the next task only once this one is done (none waits reserved)
     }
 }
 
@@ -891,7 +890,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_bbwd(DevNet g, BatchState bs, DfS
     const int Q = d.TB * GT;
     int q = grab(head);
     while (q < Q) {
-        const int next = grab(head);
         const int t = q / GT, gq = q - t * GT;
         const Lane L = lane_of(gq);
         bbwd_task<mode, true>(g, bs, d, cnt, q, t, L, gamma);
@@ -902,7 +900,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_bbwd(DevNet g, BatchState bs, DfS
             const int k1 = d.b_out_ptr[t + 1];
             for (int k = d.b_out_ptr[t] + L.lane; k < k1; k += 32) red_release_add(cnt + d.b_out[k] * GT + gq, 1);
         }
-        q = next;
+        q = grab(head);
     }
 }
 

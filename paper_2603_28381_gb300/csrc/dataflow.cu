@@ -302,11 +302,12 @@ template <bool lse>
 __global__ void __launch_bounds__(kBlock) k_fwd_df(DevNet g, DevState s, DfState d, float gamma, int stall_task) {
     int t = grab(d.heads + 0);
     while (t < d.TF) {
-        const int next = grab(d.heads + 0);
         const int4 task = d.ftask[t];
         if (task.y > 0) fwd_df_warp<lse>(g, s, d, t, task.x, task.y, gamma, stall_task);
         else fwd_df_chunk<lse>(g, s, d, t, task.x, task.z, task.w, gamma, stall_task);
-        t = next;
+        // the next task only once this one is done: a task reserved while this one
+        // waits could not start when its own data arrives (head-of-line blocking)
+        t = grab(d.heads + 0);
     }
 }
 
@@ -897,7 +898,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_bwd_df(DevNet g, DevState s, DfSt
     sc.ww = s.params[1];
     int t = grab(head);
     while (t < d.TB) {
-        const int next = grab(head);
         const int4 task = d.btask[t];
         if (task.y > 0) {
             bwd_df_warp<mode>(g, s, d, cnt, t, task.x, task.y, gamma, sc);
@@ -912,7 +912,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_bwd_df(DevNet g, DevState s, DfSt
         // every task's consumers poll the words it wrote, except the gradient
         // chunks of a large net, which wait on a counter that its driver step releases
         if (task.y == -2) signal_consumers(cnt, d.b_out_ptr, d.b_out, t);
-        t = next;
+        t = grab(head);
     }
 }
 
