@@ -77,6 +77,8 @@ struct StaHandle {
     cudaEvent_t ev_bwd = nullptr;   // latest gradient sweep done
     cudaStream_t cap = nullptr;     // private stream used for graph capture
     cudaStream_t side = nullptr;    // required-time sweep
+    cudaStream_t fork = nullptr;    // a forward's reset beside its net-RC prologue
+    cudaEvent_t ev_fork[2] = {nullptr, nullptr};
     // graph cache
     cudaGraphExec_t gx_fwd[2] = {nullptr, nullptr};  // [lse]
     float gx_fwd_gamma[2] = {0.f, 0.f};
@@ -159,12 +161,13 @@ struct StaHandle {
         if (stage) cudaFree(stage);
         if (qscratch) cudaFree(qscratch);
         if (pinned) cudaFreeHost(pinned);
-        for (auto* ev : {ev_at, ev_fwd, ev_bwd})
+        for (auto* ev : {ev_at, ev_fwd, ev_bwd, ev_fork[0], ev_fork[1]})
             if (ev) cudaEventDestroy(ev);
         for (Prof* pr : {&prof_pos, &prof_fwd, &prof_rat, &prof_adj, &prof_out})
             for (cudaEvent_t e : pr->ev) cudaEventDestroy(e);
         if (cap) cudaStreamDestroy(cap);
         if (side) cudaStreamDestroy(side);
+        if (fork) cudaStreamDestroy(fork);
     }
 };
 
@@ -205,20 +208,37 @@ void enqueue_forward_dataflow(StaHandle* h, int lse, float gamma, cudaStream_t s
     const Layout& L = h->lay;
     cudaMemsetAsync(h->d.heads, 0, sizeof(int32_t), st);
     cudaMemsetAsync(h->d.abort_word, 0, sizeof(int32_t), st);
+    // the reset and the large nets' RC write different words: side by side
+    cudaEventRecord(h->ev_fork[0], st);
+    cudaStreamWaitEvent(h->fork, h->ev_fork[0], 0);
     {
-        ProfScope ps(h, &h->prof_fwd, STA_PROF_RESET, st);
-        launch_fwd_reset(h->s, h->d, L.P, st);  // the words the sweep's tasks poll
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_RESET, h->fork);
+        launch_fwd_reset(h->s, h->d, L.P, h->fork);  // the words the sweep's tasks poll
     }
+    cudaEventRecord(h->ev_fork[1], h->fork);
     {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
         launch_rc(h->g, h->s, 0, L.lvl_ctask[L.L], st);  // load and wire RC of the nets > 32 pins
     }
+    cudaStreamWaitEvent(st, h->ev_fork[1], 0);
     {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
         launch_fwd_dataflow(h->g, h->s, h->d, h->grid_fwd, gamma, lse, h->stall_task, st);
     }
-    ProfScope ps(h, &h->prof_fwd, STA_PROF_ENDPOINTS, st);
-    launch_endpoints(h->g, h->s, gamma, lse, st);
+    // the words the next fused gradient sweep polls, beside the endpoints (a fused
+    // sweep always follows a forward directly, so it needs no reset of its own)
+    cudaEventRecord(h->ev_fork[0], st);
+    cudaStreamWaitEvent(h->fork, h->ev_fork[0], 0);
+    {
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_RESET, h->fork);
+        launch_bwd_reset(h->s, h->d, L.P, 3, h->fork);
+    }
+    cudaEventRecord(h->ev_fork[1], h->fork);
+    {
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_ENDPOINTS, st);
+        launch_endpoints(h->g, h->s, gamma, lse, st);
+    }
+    cudaStreamWaitEvent(st, h->ev_fork[1], 0);
 }
 
 void enqueue_backward_dataflow(StaHandle* h, int mode, float gamma, cudaStream_t st) {
@@ -227,7 +247,7 @@ void enqueue_backward_dataflow(StaHandle* h, int mode, float gamma, cudaStream_t
     pr->next = 0;
     cudaMemsetAsync((mode & 2) ? h->d.acnt : h->d.rcnt, 0, sizeof(int32_t) * (L.TB ? L.TB : 1), st);
     cudaMemsetAsync(h->d.heads + ((mode & 2) ? 2 : 1), 0, sizeof(int32_t), st);
-    {
+    if (mode != 3) {  // the fused sweep's words were reset by the forward before it
         ProfScope ps(h, pr, STA_PROF_RESET, st);
         launch_bwd_reset(h->s, h->d, L.P, mode, st);  // the words the sweep's tasks poll
     }
@@ -284,14 +304,19 @@ void enqueue_forward_batch(StaHandle* h, int lse, float gamma, cudaStream_t st) 
     }
     cudaMemsetAsync(h->d.heads, 0, sizeof(int32_t), st);
     cudaMemsetAsync(h->d.abort_word, 0, sizeof(int32_t), st);
+    // the reset and the large nets' loads write different words: side by side
+    cudaEventRecord(h->ev_fork[0], st);
+    cudaStreamWaitEvent(h->fork, h->ev_fork[0], 0);
     {
-        ProfScope ps(h, &h->prof_fwd, STA_PROF_RESET, st);
-        launch_batch_reset(h->bs, h->d, L.P, 0, st);  // the words the sweep's tasks poll
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_RESET, h->fork);
+        launch_batch_reset(h->bs, h->d, L.P, 0, h->fork);  // the words the sweep's tasks poll
     }
+    cudaEventRecord(h->ev_fork[1], h->fork);
     if (h->nbig) {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
         launch_batch_load(h->g, h->bs, h->big_dev, h->nbig, st);
     }
+    cudaStreamWaitEvent(st, h->ev_fork[1], 0);
     {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
         launch_batch_fwd(h->g, h->bs, h->d, h->grid_fwd, gamma, lse, h->stall_task, st);
@@ -778,7 +803,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         STEP(h->alloc(s.g_slew, 2 * P));
         STEP(h->alloc(s.grad, P));
         STEP(h->alloc(s.ep_slack, L.E));
-        STEP(h->alloc(s.red, (size_t)kRedBlocks * 8));
+        STEP(h->alloc(s.red, (size_t)kEpBlocks * 8));
         STEP(h->alloc(s.summary, STA_SUM_COUNT));
         STEP(h->alloc(s.params, 4));
         s.cap_seed = nullptr;
@@ -789,7 +814,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         auto zero = [&](void* p, size_t bytes) { return cudaMemset(p, 0, bytes); };
         if (zero(s.xy, P * 8) || zero(s.load, L.N * 4) || zero(s.wdi, P * 8) || zero(s.ats, P * 8) ||
             zero(s.adel, (size_t)L.A * 16) || zero(s.g_ats, P * 8) || zero(s.g_slew, P * 8) || zero(s.grad, P * 8) ||
-            zero(s.summary, STA_SUM_COUNT * 8) || zero(s.params, 16) || zero(s.red, (size_t)kRedBlocks * 64) ||
+            zero(s.summary, STA_SUM_COUNT * 8) || zero(s.params, 16) || zero(s.red, (size_t)kEpBlocks * 64) ||
             zero(d.net_gload, (size_t)L.N * 4))
             return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
         // constant state: asserted AT/slew (and LSE AT = late AT), required-time seeds
@@ -806,6 +831,9 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         return fail(set_err(STA_ERR_OOM, "cudaMallocHost failed"));
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->fork, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_at, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fwd, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_bwd, cudaEventDisableTiming) != cudaSuccess)
@@ -825,7 +853,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     if (h->profile) {  // event pairs for every launch of each sequence, made before any capture
         const size_t nl = (size_t)L.L;
         const std::pair<StaHandle::Prof*, size_t> sizes[] = {
-            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 3}, {&h->prof_rat, 2 * nl + 2}, {&h->prof_adj, 2 * nl + 3},
+            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 5}, {&h->prof_rat, 2 * nl + 2}, {&h->prof_adj, 2 * nl + 3},
             {&h->prof_out, 1}};
         for (const auto& ps : sizes) {
             ps.first->kind.assign(ps.second, 0);
@@ -1278,28 +1306,32 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
         launches[STA_PROF_NET_RC] = (h->nbig > 0 ? 1 : 0) + (L.N > 0 ? 1 : 0);
         launches[STA_PROF_FORWARD] = batch_fwd_levels(L);
         launches[STA_PROF_REQUIRED] = h->last_fused ? 0 : (int32_t)ph.size();
-        launches[STA_PROF_SEED] = 1;
+        launches[STA_PROF_SEED] = 1 + (h->g.ep_clk ? 1 : 0);
         launches[STA_PROF_ADJOINT] = nb;
     } else if (h->batch()) {
         // each sweep is preceded by the reset of the words its tasks poll
         launches[STA_PROF_NET_RC] = h->nbig > 0 ? 1 : 0;
         launches[STA_PROF_FORWARD] = L.TF > 0 ? 1 : 0;
         launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 1 : 0;
-        launches[STA_PROF_SEED] = 1;
+        launches[STA_PROF_SEED] = 1 + (h->g.ep_clk ? 1 : 0);  // weights (+ capture-clock seeds)
         launches[STA_PROF_ADJOINT] = L.TB > 0 ? 1 : 0;
         launches[STA_PROF_RESET] = 1 + launches[STA_PROF_REQUIRED] + launches[STA_PROF_ADJOINT];
     } else if (h->schedule == STA_SCHED_DATAFLOW) {
         launches[STA_PROF_NET_RC] = nc > 0 ? 1 : 0;
         launches[STA_PROF_FORWARD] = L.TF > 0 ? 1 : 0;
         launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 1 : 0;  // fused into the adjoint sweep
-        launches[STA_PROF_SEED] = 1;  // weights
+        launches[STA_PROF_SEED] = 1 + (h->g.ep_clk ? 1 : 0);  // weights (+ capture-clock seeds)
         launches[STA_PROF_ADJOINT] = L.TB > 0 ? 1 : 0;
-        launches[STA_PROF_RESET] = (L.P > 0 ? 1 : 0) + launches[STA_PROF_REQUIRED] + launches[STA_PROF_ADJOINT];
+        // the forward resets its own polled words and the fused sweep's; a separate
+        // required-time or adjoint sweep resets its own
+        const int32_t br = (L.P > 0 || L.npart > 0) ? 1 : 0;
+        launches[STA_PROF_RESET] = (L.P > 0 ? 1 : 0) + br +
+                                   (h->last_fused ? 0 : br * (launches[STA_PROF_REQUIRED] + launches[STA_PROF_ADJOINT]));
     } else {
         launches[STA_PROF_NET_RC] = (nw + nc) > 0 ? 1 : 0;
         launches[STA_PROF_FORWARD] = nonempty;
         launches[STA_PROF_REQUIRED] = nonempty;
-        launches[STA_PROF_SEED] = 1 + (L.E > 0 ? 1 : 0);  // weights + seeds
+        launches[STA_PROF_SEED] = 1 + (L.E > 0 ? 1 : 0) + (h->g.ep_clk ? 1 : 0);  // weights + seeds
         launches[STA_PROF_ADJOINT] = nonempty;
     }
     if (!ms) return STA_OK;

@@ -422,7 +422,8 @@ __global__ void __launch_bounds__(kBlock) k_ep1(DevNet g, DevState s, float gamm
 
 __global__ void __launch_bounds__(kBlock) k_ep2(DevNet g, DevState s, float gamma, int lse, int nparts) {
     EpAcc acc = ep_identity();
-    if ((int)threadIdx.x < nparts) acc = reinterpret_cast<const EpAcc*>(s.red)[threadIdx.x];
+    // thread i merges partials i, i + 256, ... in order; then the fixed-order tree
+    for (int k = threadIdx.x; k < nparts; k += kBlock) ep_merge(acc, reinterpret_cast<const EpAcc*>(s.red)[k], gamma);
     ep_block_reduce(acc, gamma);
     if (threadIdx.x == 0) {
         double* o = s.summary;
@@ -526,8 +527,8 @@ void launch_fwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0
 }
 
 void launch_endpoints(const DevNet& g, const DevState& s, float gamma, int lse, cudaStream_t st) {
-    k_ep1<<<kRedBlocks, kBlock, 0, st>>>(g, s, gamma, lse);
-    k_ep2<<<1, kBlock, 0, st>>>(g, s, gamma, lse, kRedBlocks);
+    k_ep1<<<kEpBlocks, kBlock, 0, st>>>(g, s, gamma, lse);
+    k_ep2<<<1, kBlock, 0, st>>>(g, s, gamma, lse, kEpBlocks);
 }
 
 void launch_bwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0, int nc, float gamma, int mode,

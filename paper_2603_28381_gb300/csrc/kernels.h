@@ -43,7 +43,7 @@ struct DevState {
     float* g_slew;     // [P*2] adjoint of the late slews
     float2* grad;      // [P] d loss / d (x, y), ORIGINAL pin order
     float2* ep_slack;  // [E] (early, late)
-    double* red;       // [kRedBlocks * 8] endpoint-reduction partials (scratch)
+    double* red;       // [kEpBlocks * 8] endpoint-reduction partials (scratch)
     double* summary;   // [STA_SUM_COUNT]
     float* params;     // [4] w_tns, w_wns
     float* cap_seed;   // [P] d loss / d (rising arrival) of capturing clock pins, 0 elsewhere;

@@ -26,7 +26,8 @@ constexpr int kBlock = 256;         // threads per block in every task kernel
 constexpr int kWarpsPerBlock = kBlock / 32;
 constexpr int kLibStride = 16;      // floats per type in lib_idx / lib_inv
 constexpr int kTabPerArcRf = 2 * STA_LUT * STA_LUT;  // delay table then slew table
-constexpr int kRedBlocks = 152;     // endpoint reduction partials (one per SM)
+constexpr int kRedBlocks = 152;     // endpoint reduction partials of the batched schedule (one per SM)
+constexpr int kEpBlocks = 4 * 152;  // endpoint reduction partials of one placement
 constexpr float kKrc = 1e-3f;       // Ohm * fF in ps
 constexpr int kPartFloats = 12;     // floats per backward partial (large nets)
 constexpr uint32_t kUnwritten = 0x7fbadbadu;  // a NaN: "not written yet in this sweep"
