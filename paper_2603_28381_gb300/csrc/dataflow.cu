@@ -787,21 +787,31 @@ __device__ void bwd_df_driver(const DevNet& g, const DevState& s, const DfState&
     // the wait: poll the chunks' partial words (reset to kUnwritten before the
     // sweep, written once by the partial tasks) until all are written; bounded
     // like wait_ready
-    float first[kPartFloats];  // the lane's first chunk, as seen by the successful poll
-#pragma unroll
-    for (int j = 0; j < kPartFloats; ++j) first[j] = 0.f;
+    // the lane's chunks lane, lane + 32, ... combined in that order during each poll;
+    // the successful poll's values are final (every word is written once per sweep)
+    float v[kPartFloats];
     {
         unsigned long long t0 = 0;
         for (unsigned it = 0;; ++it) {
             bool ok = true;
+            v[0] = v[1] = -kInf;
+            v[2] = v[3] = kInf;
+#pragma unroll
+            for (int j = 4; j < kPartFloats; ++j) v[j] = 0.f;
             for (int k = lane; k < nch; k += 32) {
                 const float* q = part + (size_t)(slot0 + k) * kPartFloats;
+                float x[kPartFloats];
 #pragma unroll
                 for (int j = 0; j < kPartFloats; ++j) {
-                    const float x = ld_relaxed_f(q + j);
-                    if (k == lane) first[j] = x;
-                    ok &= written(x);
+                    x[j] = ld_relaxed_f(q + j);
+                    ok &= written(x[j]);
                 }
+                v[0] = fmaxf(v[0], x[0]);
+                v[1] = fmaxf(v[1], x[1]);
+                v[2] = fminf(v[2], x[2]);
+                v[3] = fminf(v[3], x[3]);
+#pragma unroll
+                for (int j = 4; j < kPartFloats; ++j) v[j] += x[j];
             }
             if (__all_sync(kFull, ok)) break;
             __nanosleep(STA_POLL_NS);
@@ -820,29 +830,6 @@ __device__ void bwd_df_driver(const DevNet& g, const DevState& s, const DfState&
                 }
             }
         }
-    }
-
-    float v[kPartFloats];
-    v[0] = v[1] = -kInf;
-    v[2] = v[3] = kInf;
-#pragma unroll
-    for (int k = 4; k < kPartFloats; ++k) v[k] = 0.f;
-    if (lane < nch) {  // the first chunk from the poll, the rest re-read (already written)
-        v[0] = fmaxf(v[0], first[0]);
-        v[1] = fmaxf(v[1], first[1]);
-        v[2] = fminf(v[2], first[2]);
-        v[3] = fminf(v[3], first[3]);
-#pragma unroll
-        for (int j = 4; j < kPartFloats; ++j) v[j] += first[j];
-    }
-    for (int k = lane + 32; k < nch; k += 32) {
-        const float* q = part + (size_t)(slot0 + k) * kPartFloats;
-        v[0] = fmaxf(v[0], ld_relaxed_f(q + 0));
-        v[1] = fmaxf(v[1], ld_relaxed_f(q + 1));
-        v[2] = fminf(v[2], ld_relaxed_f(q + 2));
-        v[3] = fminf(v[3], ld_relaxed_f(q + 3));
-#pragma unroll
-        for (int j = 4; j < kPartFloats; ++j) v[j] += ld_relaxed_f(q + j);
     }
     v[0] = warp_max(v[0]);
     v[1] = warp_max(v[1]);
