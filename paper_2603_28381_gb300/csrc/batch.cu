@@ -89,26 +89,25 @@ struct FCell {
 
 __device__ __forceinline__ FCell fcell(const DevNet& g, const DfState& d, int n, int rf, float ld) {
     FCell f;
-    f.t = g.net_drv[n];
-    f.a0 = g.net_arc_ptr[n];
-    f.na = f.t >= 0 ? g.net_arc_ptr[n + 1] - f.a0 : 0;
+    const int4 q0 = __ldg(g.net_desc + 2 * n), q1 = __ldg(g.net_desc + 2 * n + 1);  // one record
+    f.t = q0.x;
+    f.a0 = q0.y;
+    f.na = q0.z;
     f.rfi = 0;
-    f.dyn = 0;
+    f.dyn = q0.w & 15;
     f.jl = 0;
     f.ul = 0.f;
-#pragma unroll
-    for (int k = 0; k < STA_MAX_ARCS; ++k) f.pin[k] = 0;
+    f.pin[0] = q1.x;
+    f.pin[1] = q1.y;
+    f.pin[2] = q1.z;
+    f.pin[3] = q1.w;
 #pragma unroll
     for (int j = 0; j < 6; ++j) f.sidx[j] = f.sinv[j] = 0.f;
     if (f.t < 0) return f;
-    const int un = g.lib_unate[f.t];
+    const int un = q0.w >> 4;
 #pragma unroll
     for (int k = 0; k < STA_MAX_ARCS; ++k)
-        if (k < f.na) {
-            f.pin[k] = g.arc_pin[f.a0 + k];
-            f.rfi |= (rf ^ ((un >> k) & 1)) << k;
-            f.dyn |= (d.arc_prod[f.a0 + k] >= 0 ? 1 : 0) << k;
-        }
+        if (k < f.na) f.rfi |= (rf ^ ((un >> k) & 1)) << k;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
         f.sidx[j] = __ldg(g.lib_idx + f.t * kLibStride + j);
@@ -510,9 +509,10 @@ __device__ __forceinline__ BCell bcell_pre(const DevNet& g, const BatchState& bs
                                            float gamma) {
     const int Bp = bs.Bp, b = L.b, el = L.el, rf = L.rf;
     BCell bc;
-    bc.t = g.net_drv[n];
-    const int a0 = g.net_arc_ptr[n];
-    bc.na = bc.t >= 0 ? g.net_arc_ptr[n + 1] - a0 : 0;
+    const int4 q0 = __ldg(g.net_desc + 2 * n), q1 = __ldg(g.net_desc + 2 * n + 1);  // one record
+    bc.t = q0.x;
+    bc.na = q0.z;
+    const int dpin[STA_MAX_ARCS] = {q1.x, q1.y, q1.z, q1.w};
     bc.rfi = 0;
     bc.amax = -1;
     bc.dSs = bc.dSl = bc.cs = 0.f;
@@ -524,7 +524,7 @@ __device__ __forceinline__ BCell bcell_pre(const DevNet& g, const BatchState& bs
     if (bc.t < 0) return bc;
     const bool need = (mode & 1) || el;  // mode 2 needs the late lanes only
     const int t = bc.t;
-    const int un = g.lib_unate[t];
+    const int un = q0.w >> 4;
     const float ld = bs.load[ix(n, Bp, b)];
     const float* li = g.lib_idx + t * kLibStride + 8;
     const int jl = axis_seg(li, ld);
@@ -535,7 +535,7 @@ __device__ __forceinline__ BCell bcell_pre(const DevNet& g, const BatchState& bs
 #pragma unroll
     for (int k = 0; k < STA_MAX_ARCS; ++k) {
         if (k < bc.na) {
-            bc.pin[k] = g.arc_pin[a0 + k];
+            bc.pin[k] = dpin[k];
             const int r = rf ^ ((un >> k) & 1);
             bc.rfi |= r << k;
             if (need) {

@@ -688,6 +688,23 @@ StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& 
             }
         }
     }
+
+    // ---- per-net driver-cell record (one 32-byte load instead of dependent ones) ----
+    o.net_desc.assign((size_t)o.N * 8, 0);
+    for (int32_t n = 0; n < o.N; ++n) {
+        int32_t* q = &o.net_desc[(size_t)n * 8];
+        const int32_t t = o.net_drv[n];
+        const int32_t a0 = o.net_arc_ptr[n], na = t >= 0 ? o.net_arc_ptr[n + 1] - a0 : 0;
+        int32_t bits = t >= 0 ? (o.lib_unate[t] & 15) << 4 : 0;
+        for (int32_t k = 0; k < na; ++k) {
+            q[4 + k] = o.arc_pin[a0 + k];
+            bits |= (o.arc_prod[a0 + k] >= 0 ? 1 : 0) << k;  // input written during the sweep
+        }
+        q[0] = t;
+        q[1] = a0;
+        q[2] = na;
+        q[3] = bits;
+    }
     return STA_OK;
 }
 

@@ -749,6 +749,11 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         STEP(h->upload(cp, L.lib_cell));
         g.lib_cell = reinterpret_cast<const float4*>(cp);
     }
+    {
+        const int32_t* dp = nullptr;
+        STEP(h->upload(dp, L.net_desc));
+        g.net_desc = reinterpret_cast<const int4*>(dp);
+    }
     STEP(h->upload(g.ep_pin, L.ep_pin));
     STEP(h->upload(g.ep_rat, L.ep_rat));
     g.ep_clk = nullptr;

@@ -22,6 +22,7 @@ struct DevNet {
     const int32_t* lib_unate;    // [T]
     const float* lib_tab;        // [T*4*2*98]
     const float4* lib_cell;      // [T*4*2*36*2] corner-packed cells (delay float4, slew float4)
+    const int4* net_desc;        // [N*2] per-net driver-cell record (see Layout::net_desc)
     const int32_t* ep_pin;       // [E]
     const float* ep_rat;         // [E*4]
     const int32_t* ep_clk;       // [E] capturing clock pin (propagated clock), -1 none; null: ideal clock

@@ -104,6 +104,8 @@ struct Layout {
     std::vector<float> lib_inv;        // [T*16] 1/(idx[k+1]-idx[k]) for k = 0..5 (slew), 8..13 (load)
     std::vector<int32_t> lib_unate;    // [T] bit a set = arc a negative unate
     std::vector<float> lib_tab;        // [T*4*2*98] per (type, arc, rf_out): delay 7x7, slew 7x7
+    std::vector<int32_t> net_desc;     // [N*8] driver type (-1: asserted), first arc, arcs, bits 0-3 input
+                                       // written during the sweep and 4-7 negative unate, input pins 0-3
     std::vector<float> lib_cell;       // [T*4*2*36*8] per (type, arc, rf_out, slew seg, load seg): the
                                        // four delay corners then the four slew corners (one 32-byte sector)
 
