@@ -321,8 +321,20 @@ void enqueue_forward_batch(StaHandle* h, int lse, float gamma, cudaStream_t st) 
         ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
         launch_batch_fwd(h->g, h->bs, h->d, h->grid_fwd, gamma, lse, h->stall_task, st);
     }
-    ProfScope ps(h, &h->prof_fwd, STA_PROF_ENDPOINTS, st);
-    launch_batch_endpoints(h->g, h->bs, gamma, lse, st);
+    // the words the next fused gradient sweep polls, beside the endpoints (as in the
+    // single-placement forward)
+    cudaEventRecord(h->ev_fork[0], st);
+    cudaStreamWaitEvent(h->fork, h->ev_fork[0], 0);
+    {
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_RESET, h->fork);
+        launch_batch_reset(h->bs, h->d, L.P, 3, h->fork);
+    }
+    cudaEventRecord(h->ev_fork[1], h->fork);
+    {
+        ProfScope ps(h, &h->prof_fwd, STA_PROF_ENDPOINTS, st);
+        launch_batch_endpoints(h->g, h->bs, gamma, lse, st);
+    }
+    cudaStreamWaitEvent(st, h->ev_fork[1], 0);
 }
 
 void enqueue_backward_batch(StaHandle* h, int mode, float gamma, cudaStream_t st) {
@@ -344,7 +356,7 @@ void enqueue_backward_batch(StaHandle* h, int mode, float gamma, cudaStream_t st
     }
     cudaMemsetAsync((mode & 2) ? h->d.acnt : h->d.rcnt, 0, sizeof(int32_t) * (L.TB ? L.TB * (size_t)h->bs.GT : 1), st);
     cudaMemsetAsync(h->d.heads + ((mode & 2) ? 2 : 1), 0, sizeof(int32_t), st);
-    {
+    if (mode != 3) {  // the fused sweep's words were reset by the forward before it
         ProfScope ps(h, pr, STA_PROF_RESET, st);
         launch_batch_reset(h->bs, h->d, L.P, mode, st);  // the words the sweep's tasks poll
     }
@@ -1320,7 +1332,8 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
         launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 1 : 0;
         launches[STA_PROF_SEED] = 1 + (h->g.ep_clk ? 1 : 0);  // weights (+ capture-clock seeds)
         launches[STA_PROF_ADJOINT] = L.TB > 0 ? 1 : 0;
-        launches[STA_PROF_RESET] = 1 + launches[STA_PROF_REQUIRED] + launches[STA_PROF_ADJOINT];
+        // the forward resets its own polled words and the fused sweep's
+        launches[STA_PROF_RESET] = 2 + (h->last_fused ? 0 : launches[STA_PROF_REQUIRED] + launches[STA_PROF_ADJOINT]);
     } else if (h->schedule == STA_SCHED_DATAFLOW) {
         launches[STA_PROF_NET_RC] = nc > 0 ? 1 : 0;
         launches[STA_PROF_FORWARD] = L.TF > 0 ? 1 : 0;
