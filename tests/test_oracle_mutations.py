@@ -40,22 +40,49 @@ MUTATIONS = {
                               "con[4 * e + q] += q < 2 ? at[4 * k + 0] : at[4 * k + 2];"),
     "capture_arrival_subtracted": ("con[4 * e + q] += q < 2 ? at[4 * k + 2] : at[4 * k + 0];",
                                    "con[4 * e + q] -= q < 2 ? at[4 * k + 2] : at[4 * k + 0];"),
+    # late output slew taken as the minimum over arcs, in the forward alone and
+    # in the forward and the adjoint together (a consistent mistake)
+    "late_slew_max_becomes_min": ("if (S > best_sl) { best_sl = S; argmax = ai; }",
+                                  "if (argmax < 0 || S < best_sl) { best_sl = S; argmax = ai; }"),
+    "late_slew_min_in_forward_and_adjoint": [
+        ("if (S > best_sl) { best_sl = S; argmax = ai; }",
+         "if (argmax < 0 || S < best_sl) { best_sl = S; argmax = ai; }"),
+        ("if (S > best) { best = S; amax = a; dss = dSs; dsl = dSl; }",
+         "if (amax < 0 || S < best) { best = S; amax = a; dss = dSs; dsl = dSl; }")],
+    "late_slew_tie_to_last_arc": ("if (S > best) { best = S; amax = a; dss = dSs; dsl = dSl; }",
+                                  "if (S >= best) { best = S; amax = a; dss = dSs; dsl = dSl; }"),
+    # smoothed loss: the zero of the TNS soft-min dropped (loss and adjoint
+    # alike), the soft-min's log term with the wrong sign, WNS over half the
+    # slacks, rise and fall soft-minned separately
+    "tns_softmin_drops_zero": [("tns_g += softmin(3, trip, gamma);", "tns_g += softmin(2, trip, gamma);"),
+                               ("double te = softmin(3, trip, gamma);", "double te = softmin(2, trip, gamma);")],
+    "softmin_log_sign": ("return m - gamma * log(s);", "return m + gamma * log(s);"),
+    "wns_softmin_over_rise_only": ("double wns_g = softmin(2 * E, sm, gamma);",
+                                   "double wns_g = softmin(E, sm, gamma);"),
+    "tns_rise_fall_separately": ("tns_g += softmin(3, trip, gamma);",
+                                 "{ double tr[2] = {sm[2 * e], 0.0}, tf[2] = {sm[2 * e + 1], 0.0};\n"
+                                 "          tns_g += softmin(2, tr, gamma) + softmin(2, tf, gamma); }"),
 }
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_pins_catch_planted_mistake(name, tmp_path):
-    old, new = MUTATIONS[name]
+    edits = MUTATIONS[name]
+    if isinstance(edits, tuple):
+        edits = [edits]
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    for old, new in edits:
+        assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+        src = src.replace(old, new)
     mutated = tmp_path / "mut.c"
-    mutated.write_text(src.replace(old, new))
+    mutated.write_text(src)
     so = tmp_path / "libmut.so"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
                            "-o", str(so), str(mutated), "-lm"])
     env = dict(os.environ, ORACLE_SO=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_rc_nldm.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_sta.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_sta.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_loss_slew.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutation {name} survived the pin suite"
