@@ -10,8 +10,18 @@ power-law fanout capped at 2000, eight 20k-sink nets, 3000x3000 um, gamma =
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Prints one JSON line.  `--impl reference` times the FP64 CPU oracle (the only
-reference this method has) on the machine's host cores on the same workload.
+Prints one JSON line.  On one GPU the default line also carries the metric's
+second half as two sub-records, each with its own clock record: `batch` (64
+jittered placements of a ~500k-pin netlist per step, against the same
+placements one per call) and `serve` (a Poisson stream of 2,000 requests over
+ten resident netlists of 20k-3M pins, continuous admission against the plain
+one-request-at-a-time loop); `--no-sub` leaves them out.  `--impl reference`
+times the FP64 CPU oracle (the only reference this method has) on the box's
+host cores on the same workload.
+
+The roofline's `achieved` bytes follow the survey's per-unit count (116 P +
+16 N + 52 S + 84 A per step, split into forward, required times and
+gradient); `per_kind_formula` gives every kernel kind's own reads and writes.
 """
 from __future__ import annotations
 
@@ -54,6 +64,8 @@ def parse():
                          "batch: 64 placements of a ~500k-pin netlist per step")
     ap.add_argument("--placements", type=int, default=64)
     ap.add_argument("--verbose", action="store_true", help="per-step times on stderr")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="single: leave out the batched and served sub-records of the default line")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the one-placement-per-call comparison")
     ap.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     ap.add_argument("--netlists", type=int, default=10, help="serve: distinct netlists (20k to 3M pins)")
@@ -138,6 +150,25 @@ def algorithmic_bytes(sizes, S, schedule="dataflow", big=(0, 0), clocked=0):
         out["seed"] += 52 * clocked
         out["adjoint"] += 4 * A
     return out
+
+
+def survey_bytes(sizes, S):
+    """Algorithmic bytes of one forward + gradient call by the survey's per-unit
+    count (P pins, N nets, S sinks, A arcs; each array crosses HBM once per
+    producer and once per consumer):
+      forward  xy + cap 12P, net_ptr 4N, arc topology 6A, AT + slew write 32P,
+               read by the arcs 32S, load 4N, wire delay 4S, arc delay 16A
+      required wire delay 4S, arc delay 16A, topology 4N + 6A, RAT write + read 32P
+      gradient LSE-AT write 8P + read 8S, late arc delay 8A, wire delay 4S,
+               adjoint write + read 16P, stored partials 32A, xy reread 8P,
+               gradient write 8P, d loss / d load 4N
+    i.e. 116P + 16N + 52S + 84A per step.  The fused backward sweep carries the
+    required times and the gradient."""
+    P, N, A = sizes["pins"], sizes["nets"], sizes["arcs"]
+    fwd = 44 * P + 8 * N + 36 * S + 22 * A
+    req = 32 * P + 4 * N + 4 * S + 22 * A
+    grad = 40 * P + 4 * N + 12 * S + 40 * A
+    return {"forward": fwd, "required": req, "gradient": grad, "step": fwd + req + grad}
 
 
 def algorithmic_bytes_batch(sizes, S, B, big=(0, 0)):
@@ -257,6 +288,26 @@ def dist_env():
 # --------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline leg and the reference arm)
 # --------------------------------------------------------------------------
+def cpu_model():
+    """The host CPU's model name (lscpu / /proc/cpuinfo), for the CPU baseline."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def time_oracle(w, budget_s=20.0, max_calls=5):
     import oracle
     oracle.build()
@@ -309,7 +360,7 @@ def run_reference(args):
                                                        "single thread, as it stands",
                                           "levels": int(oracle.levels(w.netlist).max()) + 1}),
             "cpu_baseline": {"value": value, "unit": "pins/s", "cores": 1, "kind": "oracle",
-                             "sample": sample_note},
+                             "cpu_model": cpu_model(), "host_cores": os.cpu_count(), "sample": sample_note},
             "e2e": {"value": value, "unit": "pins/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -425,16 +476,31 @@ def run_ours(args):
         abytes["required"] = 0
     dom = max(acc, key=lambda k: acc[k])
     peak, peak_src = load_peaks()
-    achieved = abytes[dom] / (acc[dom] / 1e3) / 1e9 if acc[dom] > 0 else 0.0
+    # the dominant kernel's algorithmic bytes by the survey's per-unit count: the
+    # forward sweep the forward's, the backward sweep the required times' and
+    # (adjoint) the gradient's
+    sb = survey_bytes(sizes, S)
+    sweep_bytes = {"forward": sb["forward"], "required": sb["required"],
+                   "adjoint": sb["gradient"] + (sb["required"] if launches.get("required", 1) == 0 else 0)}
+    dom_bytes = sweep_bytes.get(dom, abytes[dom])
+    achieved = dom_bytes / (acc[dom] / 1e3) / 1e9 if acc[dom] > 0 else 0.0
     traffic = measured_traffic(dom, args)
+    step_s = total_s / args.steps
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                 "traffic": None if traffic is None else float(traffic),
+                "bytes_per_launch": int(dom_bytes), "bytes_formula": "survey 116P + 16N + 52S + 84A per step",
                 "launches_per_step": launches[dom],
                 "avg_launch_us": 1e3 * acc[dom] / max(launches[dom], 1),
                 "ms_by_kind": {k: round(v, 4) for k, v in acc.items()},
-                "step_algorithmic_bytes": int(sum(abytes.values())),
-                "step_frac": sum(abytes.values()) / (total_s / args.steps) / 1e9 / peak}
+                "step_algorithmic_bytes": int(sb["step"]),
+                "step_frac": sb["step"] / step_s / 1e9 / peak,
+                "per_kind_formula": {
+                    "how": "every kernel kind's own reads and writes (bench.py algorithmic_bytes), "
+                           "including positions, net RC of large nets and endpoints",
+                    "dominant_frac": (abytes[dom] / (acc[dom] / 1e3) / 1e9 / peak) if acc[dom] > 0 else 0.0,
+                    "step_algorithmic_bytes": int(sum(abytes.values())),
+                    "step_frac": sum(abytes.values()) / step_s / 1e9 / peak}}
     # depth floor: the forward and the fused backward sweep each need at least one
     # dependent round trip through L2 per level (a task reads what its producers stored)
     lat_l2 = sta.sta_measure_latency(32 << 20, 20000)
@@ -451,10 +517,11 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        tc = time_oracle(w, budget_s=20.0, max_calls=4)
+        tc = time_oracle(w, budget_s=20.0, max_calls=8)
         cpu = {"value": P / (sum(tc) / len(tc)), "unit": "pins/s", "cores": 1, "kind": "oracle",
+               "cpu_model": cpu_model(), "host_cores": os.cpu_count(),
                "sample": f"{len(tc)} full FP64 oracle calls (forward, required times, gradient) "
-                         f"on the same {P}-pin netlist, single thread"}
+                         f"on the same {P}-pin netlist, single thread (mean)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world,
@@ -468,6 +535,16 @@ def run_ours(args):
                                               "wall_s": round(t_wall, 3)}),
                 "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk}
+        if world == 1 and not args.no_sub:
+            # the metric's second half: batched placements and the served stream,
+            # each measured here with its own clock record
+            import copy
+            ba = copy.copy(args)
+            ba.steps, ba.warmup, ba.scale = min(args.steps, 20), max(3, min(args.warmup, 5)), 1.0
+            line["batch"] = run_batch(ba, emit=False)
+            sa = copy.copy(args)
+            sa.scale = 1.0
+            line["serve"] = run_serve(sa, emit=False)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -483,7 +560,7 @@ def batch_workload(args):
     return w, xyb
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     import torch
 
     import paper_2603_28381_gb300 as sta
@@ -600,7 +677,9 @@ def run_batch(args):
                          "step_algorithmic_bytes": int(sum(abytes.values())),
                          "step_frac": sum(abytes.values()) / (total_s / args.steps) / 1e9 / peak},
             "clocks": clk}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 # --------------------------------------------------------------------------
@@ -619,7 +698,7 @@ def serve_workload(args):
     return designs
 
 
-def run_serve(args):
+def run_serve(args, emit=True):
     import torch
 
     import netgen
@@ -684,6 +763,7 @@ def run_serve(args):
     arrivals = np.cumsum(rng.exponential(1.0 / rate, R))
 
     out = {}
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
     for mode in ("plain", "continuous"):
         srv = StaServer(sequential=(mode == "plain"), slots=args.slots)
         ids = [srv.add_netlist(w.netlist, w.library) for w in designs]
@@ -696,6 +776,7 @@ def run_serve(args):
                      "pins_per_s": float(pins[which].sum() / span), "span_s": span,
                      "resident_netlists": stats0["resident"], "resident_bytes": stats0["resident_bytes"],
                      "evictions": st["evictions"]}
+    clk = clocks.stop()
     line = {"metric": "served p50/p99 latency vs plain", "value": out["continuous"]["p99_ms"], "unit": "ms p99",
             "n_gpus": 1, "steps": R, "warmup": 0, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -708,8 +789,11 @@ def run_serve(args):
                        "budget": "150 GiB"},
             "continuous": out["continuous"], "plain": out["plain"],
             "p99_speedup_vs_plain": out["plain"]["p99_ms"] / out["continuous"]["p99_ms"],
-            "p50_speedup_vs_plain": out["plain"]["p50_ms"] / out["continuous"]["p50_ms"]}
-    print(json.dumps(line), flush=True)
+            "p50_speedup_vs_plain": out["plain"]["p50_ms"] / out["continuous"]["p50_ms"],
+            "clocks": clk}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 # --------------------------------------------------------------------------

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define STA_ABI_VERSION 2
+#define STA_ABI_VERSION 3
 #define STA_LUT 7       /* table points per axis */
 #define STA_MAX_ARCS 4  /* arcs (input pins) per cell type */
 
@@ -337,29 +337,40 @@ StaStatus sta_query_profile(StaHandle *h, double *ms, int32_t *launches);
  * endpoint slacks, WNS, TNS and smoothed TNS/WNS that sta_forward reduces, and
  * allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
  *
- * at       [num_pins][4] device, arrival times (cond = 2*el + rf)
+ * at       [num_pins][4] device, arrival times (cond = 2*el + rf); 16-byte aligned
  * ats      [num_pins][2] device, late rise/fall LSE arrival times, or NULL
- *          (then the smoothed slots of the summary are 0 / +inf)
+ *          (then the smoothed slots of the summary are 0 / +inf); 8-byte aligned
  * end_pins [num_end] device, pin index of each endpoint; an index outside
  *          [0, num_pins) gives that endpoint NaN slacks and leaves it out of the
  *          summary (STA_SUM_NUM_ENDPOINTS counts the endpoints used)
- * end_rat  [num_end][4] device, endpoint constraints as in StaNetlistDesc
- * ep_slack [num_end][2] device output (early, late); summary [STA_SUM_COUNT]
- *          device output, same slots as sta_query_summary.
+ * end_rat  [num_end][4] device, endpoint constraints as in StaNetlistDesc;
+ *          16-byte aligned
+ * end_clk  [num_end] device, the capturing clock pin of each endpoint (-1: none),
+ *          as StaNetlistDesc.end_clock, or NULL for an ideal clock.  A clocked
+ *          endpoint's hold bound adds the clock pin's late rising arrival and its
+ *          setup bound the early rising arrival, exactly as sta_forward does; a
+ *          clock pin >= num_pins leaves the endpoint out like a bad end pin
+ * ep_slack [num_end][2] device output (early, late), 8-byte aligned; summary
+ *          [STA_SUM_COUNT] device output, 8-byte aligned, same slots as
+ *          sta_query_summary.
  * Asynchronous on `stream`.  num_end may not exceed STA_NOALLOC_MAX_ENDPOINTS
- * (STA_ERR_INVALID_ARG otherwise).
+ * and every pointer must have the alignment stated (end_pins and end_clk 4
+ * bytes): otherwise STA_ERR_INVALID_ARG, before any device work (a sliced
+ * tensor view may start off its element type's vector boundary).
  *
  * Scratch: a file-scope device array of STA_NOALLOC_MAX_ENDPOINTS / 256
  * partials (1 MiB) that every GPU loading libsta holds until the process
- * exits.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * exits.  Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress); the first such lookup on a device may load the
+ * library's device code, so make the first call before any stream capture.
  * All calls share the array and each call rewrites every partial it reads, so
  * nothing needs clearing, but calls that overlap on the GPU (concurrent
  * streams, or graphs replayed concurrently) race on it. */
 #define STA_NOALLOC_MAX_ENDPOINTS (1 << 22)
 StaStatus sta_endpoint_summary_noalloc(const float *at, const float *ats, int32_t num_pins,
-                                       const int32_t *end_pins, const float *end_rat, int32_t num_end,
-                                       float gamma, float *ep_slack, double *summary, void *stream);
+                                       const int32_t *end_pins, const float *end_rat,
+                                       const int32_t *end_clk, int32_t num_end, float gamma,
+                                       float *ep_slack, double *summary, void *stream);
 
 /* Release every resource of the handle (NULL is a no-op). */
 void sta_destroy(StaHandle *h);

@@ -102,7 +102,7 @@ def _load() -> ctypes.CDLL:
         "sta_plan_tasks": ([ctypes.POINTER(StaNetlistDesc), ctypes.POINTER(StaLibrary), _i32, _i32, _i32, _p],
                            ctypes.c_int),
         "sta_query_profile": ([H, _p, _p], ctypes.c_int),
-        "sta_endpoint_summary_noalloc": ([_p, _p, _i32, _p, _p, _i32, ctypes.c_float, _p, _p, _p],
+        "sta_endpoint_summary_noalloc": ([_p, _p, _i32, _p, _p, _p, _i32, ctypes.c_float, _p, _p, _p],
                                          ctypes.c_int),
         "sta_destroy": ([H], None),
         "sta_server_create": ([ctypes.POINTER(StaServerOptions), ctypes.POINTER(H)], ctypes.c_int),
@@ -312,9 +312,10 @@ def sta_query_profile(h: int, with_times: bool = True):
 
 
 def sta_endpoint_summary_noalloc(at_ptr: int, ats_ptr: int, num_pins: int, end_pins_ptr: int,
-                                 end_rat_ptr: int, num_end: int, gamma: float, ep_slack_ptr: int,
-                                 summary_ptr: int, stream: int) -> None:
+                                 end_rat_ptr: int, end_clk_ptr: int, num_end: int, gamma: float,
+                                 ep_slack_ptr: int, summary_ptr: int, stream: int) -> None:
     """Allocation-free endpoint summary on device arrays (see include/sta.h)."""
     _check(_lib.sta_endpoint_summary_noalloc(at_ptr, ats_ptr, num_pins, end_pins_ptr, end_rat_ptr,
-                                             num_end, gamma, ep_slack_ptr, summary_ptr, stream),
+                                             end_clk_ptr, num_end, gamma, ep_slack_ptr, summary_ptr,
+                                             stream),
            "sta_endpoint_summary_noalloc")

@@ -11,7 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
+#include <cstdint>
 #include <string>
 
 #include "sta.h"
@@ -24,7 +24,6 @@ namespace {
 
 constexpr int kNaBlock = 256;
 constexpr int kNaMaxParts = STA_NOALLOC_MAX_ENDPOINTS / kNaBlock;
-constexpr int kNaMaxDevices = 64;
 
 struct NaAcc {
     double tns_e, tns_l, tns_g, count;  // sums in double, fixed order
@@ -37,9 +36,6 @@ struct NaAcc {
 // pass this name to a kernel (on the host it is only a stand-in); the device
 // address comes from cudaGetSymbolAddress in na_scratch().
 static __device__ __align__(256) NaAcc g_na_partials[kNaMaxParts];
-
-std::mutex g_na_mu;
-void* g_na_ptr[kNaMaxDevices] = {};
 
 __device__ __forceinline__ NaAcc na_identity() {
     NaAcc a;
@@ -77,17 +73,29 @@ __device__ void na_block_reduce(NaAcc& acc, float gamma) {
 }
 
 // One block per 256 endpoints: slacks and the block's partial.  An endpoint
-// whose pin index is outside [0, num_pins) gets NaN slacks and is left out.
+// whose pin index (or capturing clock pin) is outside [0, num_pins) gets NaN
+// slacks and is left out.  With a capturing clock pin k the hold bound adds k's
+// late rising arrival and the setup bound its early rising arrival (the latest
+// and the earliest capture edge), as in sta_forward.
 __global__ void __launch_bounds__(kNaBlock) k_na_part(const float4* __restrict__ at, const float2* __restrict__ ats,
                                                       int num_pins, const int32_t* __restrict__ end_pins,
-                                                      const float4* __restrict__ end_rat, int num_end, float gamma,
+                                                      const float4* __restrict__ end_rat,
+                                                      const int32_t* __restrict__ end_clk, int num_end, float gamma,
                                                       float2* __restrict__ ep_slack, NaAcc* __restrict__ parts) {
     NaAcc acc = na_identity();
     const int e = blockIdx.x * kNaBlock + threadIdx.x;
     if (e < num_end) {
         const int p = end_pins[e];
-        if (p >= 0 && p < num_pins) {
-            const float4 con = end_rat[e];
+        const int k = end_clk ? end_clk[e] : -1;
+        if (p >= 0 && p < num_pins && k < num_pins) {
+            float4 con = end_rat[e];
+            if (k >= 0) {
+                const float4 ck = at[k];
+                con.x += ck.z;
+                con.y += ck.z;
+                con.z += ck.x;
+                con.w += ck.x;
+            }
             const float4 a = at[p];
             const float se = fminf(a.x - con.x, a.y - con.y);
             const float sl = fminf(con.z - a.z, con.w - a.w);
@@ -138,37 +146,40 @@ StaStatus na_fail(StaStatus st, const std::string& msg) {
     return st;
 }
 
-// Device address of the scratch for the current device, looked up once per device.
+// Device address of the scratch for the current device.  Looked up on every
+// call (a host query once the module is loaded), so a device reset or a new
+// primary context between calls never leaves a stale address behind.
 StaStatus na_scratch(NaAcc** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return na_fail(STA_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kNaMaxDevices) return na_fail(STA_ERR_INVALID_ARG, "device index beyond 63");
-    std::lock_guard<std::mutex> lock(g_na_mu);
-    if (!g_na_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_na_partials);
-        if (e != cudaSuccess || !p)
-            return na_fail(STA_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_na_ptr[dev] = p;
-    }
-    *out = static_cast<NaAcc*>(g_na_ptr[dev]);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_na_partials);
+    if (e != cudaSuccess || !p)
+        return na_fail(STA_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = static_cast<NaAcc*>(p);
     return STA_OK;
 }
+
+bool na_aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 }  // namespace
 
 extern "C" {
 
 StaStatus sta_endpoint_summary_noalloc(const float* at, const float* ats, int32_t num_pins, const int32_t* end_pins,
-                                       const float* end_rat, int32_t num_end, float gamma, float* ep_slack,
-                                       double* summary, void* stream) {
+                                       const float* end_rat, const int32_t* end_clk, int32_t num_end, float gamma,
+                                       float* ep_slack, double* summary, void* stream) {
     if (num_pins < 0 || num_end < 0) return na_fail(STA_ERR_INVALID_ARG, "negative size");
     if (num_end > STA_NOALLOC_MAX_ENDPOINTS)
         return na_fail(STA_ERR_INVALID_ARG, "num_end " + std::to_string(num_end) + " exceeds STA_NOALLOC_MAX_ENDPOINTS (" +
                                                 std::to_string(STA_NOALLOC_MAX_ENDPOINTS) + ")");
     if (!summary || (num_end > 0 && (!at || !end_pins || !end_rat || !ep_slack)))
         return na_fail(STA_ERR_INVALID_ARG, "null argument");
+    // the kernels read at / end_rat as float4, ats as float2 and write ep_slack
+    // as float2: a misaligned view (a sliced tensor) would fault on the device
+    if (!na_aligned(at, 16) || !na_aligned(end_rat, 16) || !na_aligned(ats, 8) || !na_aligned(ep_slack, 8) ||
+        !na_aligned(summary, 8) || !na_aligned(end_pins, 4) || !na_aligned(end_clk, 4))
+        return na_fail(STA_ERR_INVALID_ARG,
+                       "misaligned pointer: at and end_rat need 16 bytes, ats, ep_slack and summary 8, "
+                       "end_pins and end_clk 4");
     if (ats && !(std::isfinite(gamma) && gamma > 0.f)) return na_fail(STA_ERR_INVALID_ARG, "gamma must be > 0");
     if (!ats) gamma = 1.f;
     NaAcc* parts = nullptr;
@@ -178,8 +189,8 @@ StaStatus sta_endpoint_summary_noalloc(const float* at, const float* ats, int32_
     const int nparts = (num_end + kNaBlock - 1) / kNaBlock;
     if (nparts > 0)
         k_na_part<<<nparts, kNaBlock, 0, s>>>(reinterpret_cast<const float4*>(at), reinterpret_cast<const float2*>(ats),
-                                              num_pins, end_pins, reinterpret_cast<const float4*>(end_rat), num_end,
-                                              gamma, reinterpret_cast<float2*>(ep_slack), parts);
+                                              num_pins, end_pins, reinterpret_cast<const float4*>(end_rat), end_clk,
+                                              num_end, gamma, reinterpret_cast<float2*>(ep_slack), parts);
     k_na_final<<<1, kNaBlock, 0, s>>>(parts, nparts, gamma, ats ? 1 : 0, summary);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(STA_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));

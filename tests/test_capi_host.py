@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol(sta):
     for name in sorted(declared):
         assert hasattr(lib, name), f"libsta.so does not export {name}"
     assert set(sta._sta.EXPORTS) == declared
-    assert sta.sta_abi_version() == 2
+    assert sta.sta_abi_version() == 3
 
 
 @pytest.mark.parametrize("make", [lambda: netgen.tiny_design(0), lambda: netgen.tiny_design(5),
@@ -221,3 +221,20 @@ def test_latency_probe_checks_its_arguments(sta):
         with pytest.raises(sta.StaError) as e:
             sta.sta_measure_latency(nbytes, steps)
         assert e.value.status == 1
+
+
+def test_noalloc_summary_refuses_misaligned_pointers(sta):
+    # the allocation-free summary reads at / end_rat as float4 and ats / ep_slack
+    # as float2; a misaligned view is refused on the host, before any device work
+    # (these pointer values are never dereferenced)
+    good = dict(at=1 << 20, ats=1 << 20, end_pins=1 << 20, end_rat=1 << 20, end_clk=0,
+                ep_slack=1 << 20, summary=1 << 20)
+    for name, off in (("at", 4), ("at", 8), ("end_rat", 8), ("ats", 4), ("ep_slack", 4), ("summary", 4),
+                      ("end_pins", 2), ("end_clk", 2)):
+        a = dict(good)
+        a[name] = (1 << 21) + off
+        with pytest.raises(sta.StaError) as e:
+            sta._sta.sta_endpoint_summary_noalloc(a["at"], a["ats"], 10, a["end_pins"], a["end_rat"],
+                                                  a["end_clk"], 4, 10.0, a["ep_slack"], a["summary"], 0)
+        assert e.value.status == 1, name  # STA_ERR_INVALID_ARG
+        assert "misaligned" in sta.sta_last_error(), name
