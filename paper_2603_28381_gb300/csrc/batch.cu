@@ -1161,8 +1161,8 @@ void launch_batch_load(const DevNet& g, const BatchState& bs, const int32_t* big
 void launch_batch_fwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int lse,
                       int stall_task, cudaStream_t st) {
     if (d.TF == 0) return;
-    if (lse) launch_coop(k_bfwd<true>, grid, kBlock, st, g, bs, d, gamma, stall_task);
-    else launch_coop(k_bfwd<false>, grid, kBlock, st, g, bs, d, gamma, stall_task);
+    if (lse) launch_coop(k_bfwd<true>, grid, kBlock, 0, st, g, bs, d, gamma, stall_task);
+    else launch_coop(k_bfwd<false>, grid, kBlock, 0, st, g, bs, d, gamma, stall_task);
 }
 
 void launch_batch_load_small(const DevNet& g, const BatchState& bs, int big, cudaStream_t st) {
@@ -1211,9 +1211,9 @@ void launch_batch_reset(const BatchState& bs, const DfState& d, int P, int what,
 void launch_batch_bwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int mode,
                       cudaStream_t st) {
     if (d.TB == 0) return;
-    if (mode == 1) launch_coop(k_bbwd<1>, grid, kBlock, st, g, bs, d, gamma);
-    else if (mode == 2) launch_coop(k_bbwd<2>, grid, kBlock, st, g, bs, d, gamma);
-    else launch_coop(k_bbwd<3>, grid, kBlock, st, g, bs, d, gamma);
+    if (mode == 1) launch_coop(k_bbwd<1>, grid, kBlock, 0, st, g, bs, d, gamma);
+    else if (mode == 2) launch_coop(k_bbwd<2>, grid, kBlock, 0, st, g, bs, d, gamma);
+    else launch_coop(k_bbwd<3>, grid, kBlock, 0, st, g, bs, d, gamma);
 }
 
 void launch_batch_xy_in(const BatchState& bs, const int32_t* pin_int, int P, const float2* xy_user, cudaStream_t st) {

@@ -603,6 +603,20 @@ StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& 
     if (i != V) return err = "internal: task layout did not cover every net", STA_ERR_INVALID_ARG;
     o.lvl_wtask[o.L] = (int32_t)(o.wtask.size() / 2);
     o.lvl_ctask[o.L] = (int32_t)o.ctask.size();
+    // RC chunks of the large nets (a net's partial loads are combined in chunk order)
+    o.rc_chunk.clear();
+    o.rc_net.clear();
+    o.rc_slots = 0;
+    for (int32_t n : o.ctask) {
+        const int32_t p0 = o.net_ptr[n] + 1, p1 = o.net_ptr[n + 1];
+        const int32_t nch = (p1 - p0 + kRcChunk - 1) / kRcChunk;
+        for (int32_t k = 0; k < nch; ++k) {
+            const int32_t a = p0 + k * kRcChunk;
+            o.rc_chunk.insert(o.rc_chunk.end(), {n, a, std::min(kRcChunk, p1 - a), nch == 1 ? -1 : o.rc_slots + k});
+            o.rc_net.insert(o.rc_net.end(), {o.rc_slots, nch});
+        }
+        if (nch > 1) o.rc_slots += nch;
+    }
 
     // ---- dataflow task lists ----
     o.lvl_net.assign(o.L + 1, V);
@@ -652,6 +666,7 @@ StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& 
     o.lib_unate.assign(T, 0);
     o.lib_tab.resize((size_t)T * STA_MAX_ARCS * 2 * kTabPerArcRf);
     o.lib_cell.resize((size_t)T * STA_MAX_ARCS * 2 * 36 * 8);
+    o.lib_col.resize((size_t)T * STA_MAX_ARCS * 2 * 6 * STA_LUT * 4);
     for (int32_t t = 0; t < T; ++t) {
         for (int k = 0; k < STA_LUT; ++k) {
             o.lib_idx[t * kLibStride + k] = lib.slew_index[t * STA_LUT + k];
@@ -684,6 +699,15 @@ StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& 
                         q[5] = st[i * STA_LUT + j + 1];
                         q[6] = st[(i + 1) * STA_LUT + j];
                         q[7] = st[(i + 1) * STA_LUT + j + 1];
+                    }
+                float* col = &o.lib_col[(((size_t)t * STA_MAX_ARCS + a) * 2 + rf) * 6 * STA_LUT * 4];
+                for (int j = 0; j < 6; ++j)
+                    for (int i = 0; i < STA_LUT; ++i) {
+                        float* q = col + (j * STA_LUT + i) * 4;
+                        q[0] = lib.delay_tab[src + i * STA_LUT + j];
+                        q[1] = lib.delay_tab[src + i * STA_LUT + j + 1];
+                        q[2] = lib.slew_tab[src + i * STA_LUT + j];
+                        q[3] = lib.slew_tab[src + i * STA_LUT + j + 1];
                     }
             }
         }

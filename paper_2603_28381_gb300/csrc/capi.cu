@@ -208,37 +208,23 @@ void enqueue_forward_dataflow(StaHandle* h, int lse, float gamma, cudaStream_t s
     const Layout& L = h->lay;
     cudaMemsetAsync(h->d.heads, 0, sizeof(int32_t), st);
     cudaMemsetAsync(h->d.abort_word, 0, sizeof(int32_t), st);
-    // the reset and the large nets' RC write different words: side by side
-    cudaEventRecord(h->ev_fork[0], st);
-    cudaStreamWaitEvent(h->fork, h->ev_fork[0], 0);
     {
-        ProfScope ps(h, &h->prof_fwd, STA_PROF_RESET, h->fork);
-        launch_fwd_reset(h->s, h->d, L.P, h->fork);  // the words the sweep's tasks poll
-    }
-    cudaEventRecord(h->ev_fork[1], h->fork);
-    {
+        // load and wire RC of the nets > 32 pins, and the reset of the words the
+        // sweep's tasks poll, in one launch
         ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
-        launch_rc(h->g, h->s, 0, L.lvl_ctask[L.L], st);  // load and wire RC of the nets > 32 pins
+        launch_fwd_prologue(h->g, h->s, h->d, L.P, st);
     }
-    cudaStreamWaitEvent(st, h->ev_fork[1], 0);
     {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
         launch_fwd_dataflow(h->g, h->s, h->d, h->grid_fwd, gamma, lse, h->stall_task, st);
     }
-    // the words the next fused gradient sweep polls, beside the endpoints (a fused
-    // sweep always follows a forward directly, so it needs no reset of its own)
-    cudaEventRecord(h->ev_fork[0], st);
-    cudaStreamWaitEvent(h->fork, h->ev_fork[0], 0);
     {
-        ProfScope ps(h, &h->prof_fwd, STA_PROF_RESET, h->fork);
-        launch_bwd_reset(h->s, h->d, L.P, 3, h->fork);
-    }
-    cudaEventRecord(h->ev_fork[1], h->fork);
-    {
+        // the endpoints, and the reset of the words the next fused gradient sweep
+        // polls (a fused sweep always follows a forward directly, so it needs no
+        // reset of its own), in one launch
         ProfScope ps(h, &h->prof_fwd, STA_PROF_ENDPOINTS, st);
-        launch_endpoints(h->g, h->s, gamma, lse, st);
+        launch_endpoints(h->g, h->s, gamma, lse, st, &h->d, L.P);
     }
-    cudaStreamWaitEvent(st, h->ev_fork[1], 0);
 }
 
 void enqueue_backward_dataflow(StaHandle* h, int mode, float gamma, cudaStream_t st) {
@@ -379,7 +365,7 @@ void enqueue_forward(StaHandle* h, int lse, float gamma, cudaStream_t st) {
     h->prof_fwd.next = 0;
     {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
-        launch_rc(h->g, h->s, L.lvl_wtask[L.L], L.lvl_ctask[L.L], st);
+        launch_rc(h->g, h->s, L.lvl_wtask[L.L], st);
     }
     for (int l = 0; l < L.L; ++l) {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
@@ -752,6 +738,14 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     STEP(h->upload(g.pin_cap, L.pin_cap));
     STEP(h->upload(g.wtask, L.wtask));
     STEP(h->upload(g.ctask, L.ctask));
+    {
+        const int32_t* cp = nullptr;
+        STEP(h->upload(cp, L.rc_chunk));
+        g.rc_chunk = reinterpret_cast<const int4*>(cp);
+        STEP(h->upload(cp, L.rc_net));
+        g.rc_net = reinterpret_cast<const int2*>(cp);
+        g.nrc = (int32_t)(L.rc_chunk.size() / 4);
+    }
     STEP(h->upload(g.lib_idx, L.lib_idx));
     STEP(h->upload(g.lib_inv, L.lib_inv));
     STEP(h->upload(g.lib_unate, L.lib_unate));
@@ -760,6 +754,8 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         const float* cp = nullptr;
         STEP(h->upload(cp, L.lib_cell));
         g.lib_cell = reinterpret_cast<const float4*>(cp);
+        STEP(h->upload(cp, L.lib_col));
+        g.lib_col = reinterpret_cast<const float4*>(cp);
     }
     {
         const int32_t* dp = nullptr;
@@ -823,6 +819,9 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         STEP(h->alloc(s.red, (size_t)kEpBlocks * 8));
         STEP(h->alloc(s.summary, STA_SUM_COUNT));
         STEP(h->alloc(s.params, 4));
+        STEP(h->alloc(s.rc_part, (size_t)std::max(L.rc_slots, 1)));
+        STEP(h->alloc(s.rc_count, (size_t)std::max(L.rc_slots, 1)));
+        STEP(h->alloc(s.ep_count, 1));
         s.cap_seed = nullptr;
         if (!L.ep_clk.empty()) {
             STEP(h->alloc(s.cap_seed, P));
@@ -832,7 +831,8 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         if (zero(s.xy, P * 8) || zero(s.load, L.N * 4) || zero(s.wdi, P * 8) || zero(s.ats, P * 8) ||
             zero(s.adel, (size_t)L.A * 16) || zero(s.g_ats, P * 8) || zero(s.g_slew, P * 8) || zero(s.grad, P * 8) ||
             zero(s.summary, STA_SUM_COUNT * 8) || zero(s.params, 16) || zero(s.red, (size_t)kEpBlocks * 64) ||
-            zero(d.net_gload, (size_t)L.N * 4))
+            zero(d.net_gload, (size_t)L.N * 4) || zero(s.rc_count, (size_t)std::max(L.rc_slots, 1) * 4) ||
+            zero(s.ep_count, 4))
             return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
         // constant state: asserted AT/slew (and LSE AT = late AT), required-time seeds
         if (cudaMemcpy(s.at, L.at0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1141,7 +1141,7 @@ StaStatus sta_ablation_net_rc(StaHandle* h, int32_t scheme, int32_t reps, float*
     CUDA_TRY(cudaDeviceSynchronize());
     auto launch = [&] {
         if (scheme == STA_RC_CTE) launch_rc_cte(h->g, h->s, 0, L.N, st);
-        else launch_rc(h->g, h->s, L.lvl_wtask[L.L], L.lvl_ctask[L.L], st);
+        else launch_rc(h->g, h->s, L.lvl_wtask[L.L], st);
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CUDA_TRY(cudaEventCreate(&e0));
@@ -1312,7 +1312,7 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
         nonempty += (L.lvl_wtask[l + 1] > L.lvl_wtask[l] || L.lvl_ctask[l + 1] > L.lvl_ctask[l]) ? 1 : 0;
     const int32_t nw = L.lvl_wtask.empty() ? 0 : L.lvl_wtask.back(), nc = L.lvl_ctask.empty() ? 0 : L.lvl_ctask.back();
     launches[STA_PROF_POSITIONS] = L.P > 0 ? 1 : 0;
-    launches[STA_PROF_ENDPOINTS] = 2;
+    launches[STA_PROF_ENDPOINTS] = h->batch() ? 2 : 1;
     launches[STA_PROF_OUTPUT] = (h->batch() && L.P > 0) ? 1 : 0;
     launches[STA_PROF_RESET] = 0;
     if (h->batch() && h->bsweep == STA_BATCH_LEVELS) {
@@ -1335,16 +1335,16 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
         // the forward resets its own polled words and the fused sweep's
         launches[STA_PROF_RESET] = 2 + (h->last_fused ? 0 : launches[STA_PROF_REQUIRED] + launches[STA_PROF_ADJOINT]);
     } else if (h->schedule == STA_SCHED_DATAFLOW) {
-        launches[STA_PROF_NET_RC] = nc > 0 ? 1 : 0;
+        // the prologue (large-net RC + reset of the forward's polled words) is one
+        // launch; the endpoint launch also resets the fused sweep's polled words
+        launches[STA_PROF_NET_RC] = (nc > 0 || L.P > 0) ? 1 : 0;
         launches[STA_PROF_FORWARD] = L.TF > 0 ? 1 : 0;
         launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 1 : 0;  // fused into the adjoint sweep
         launches[STA_PROF_SEED] = 1 + (h->g.ep_clk ? 1 : 0);  // weights (+ capture-clock seeds)
         launches[STA_PROF_ADJOINT] = L.TB > 0 ? 1 : 0;
-        // the forward resets its own polled words and the fused sweep's; a separate
-        // required-time or adjoint sweep resets its own
+        // a separate required-time or adjoint sweep resets its own words
         const int32_t br = (L.P > 0 || L.npart > 0) ? 1 : 0;
-        launches[STA_PROF_RESET] = (L.P > 0 ? 1 : 0) + br +
-                                   (h->last_fused ? 0 : br * (launches[STA_PROF_REQUIRED] + launches[STA_PROF_ADJOINT]));
+        launches[STA_PROF_RESET] = h->last_fused ? 0 : br * (launches[STA_PROF_REQUIRED] + launches[STA_PROF_ADJOINT]);
     } else {
         launches[STA_PROF_NET_RC] = (nw + nc) > 0 ? 1 : 0;
         launches[STA_PROF_FORWARD] = nonempty;

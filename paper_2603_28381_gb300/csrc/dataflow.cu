@@ -92,12 +92,42 @@ __device__ __forceinline__ FwdPre fwd_pre(const DevNet& g, const DfState& d, int
     return f;
 }
 
-// After the wait: fanin arrival / slew / LSE arrival (through L2, issued
-// together), NLDM lookups, late max / early min and the LSE of Eq. 4.  The
-// code is branch-free across lanes: every lane issues the same loads (unused
-// arcs and asserted drivers read a harmless valid address) and results are
-// selected, so a warp never splits into groups whose memory round trips would
-// run one after another.  `dp` must be a valid pin.
+// Shared memory of the forward sweep: per warp, per arc k and slew row i of the
+// NLDM tables, (delay, slew) of each lane's cell already interpolated along the
+// load axis at the lane's known load -- [k][i][lane] as float2.
+constexpr int kColPerWarp = STA_MAX_ARCS * STA_LUT * 32;
+constexpr size_t kFwdSmem = sizeof(float2) * kColPerWarp * kWarpsPerBlock;
+
+__device__ __forceinline__ float2* df_cols() {
+    extern __shared__ float2 df_smem[];
+    return df_smem + (threadIdx.x >> 5) * kColPerWarp;
+}
+
+// Before the wait: the lane's slew columns.  Row i of arc k holds
+//   D_i = fma(ul, T_delay(i, j+1) - T_delay(i, j), T_delay(i, j)), S_i likewise,
+// the same first interpolation step (along load, segment j) that a bilinear
+// lookup takes, so the lookup after the wait (along slew, from two rows) gives
+// bit-identical results with a shared-memory access instead of a dependent
+// global one.
+__device__ __forceinline__ void fwd_cols(const DevNet& g, const FwdPre& f, int rf, float2* col, int lane) {
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        if (k < f.na) {
+            const float4* q = g.lib_col + ((((size_t)f.t * STA_MAX_ARCS + k) * 2 + rf) * 6 + f.jl) * STA_LUT;
+#pragma unroll
+            for (int i = 0; i < STA_LUT; ++i) {
+                const float4 v = __ldg(q + i);
+                col[(k * STA_LUT + i) * 32 + lane] =
+                    make_float2(fmaf(f.ul, v.y - v.x, v.x), fmaf(f.ul, v.w - v.z, v.z));
+            }
+        }
+    }
+}
+
+// After the wait: NLDM lookups from the shared-memory columns, late max / early
+// min and the LSE of Eq. 4.  The code is branch-free across lanes (unused arcs
+// read a harmless row of the lane's own columns; results are selected), so a
+// warp never splits.  The arc delays go to D for the caller to store.
 
 // The wait of a forward task: the fanin arrival / slew / LSE arrival words this
 // lane reads, polled (strong relaxed loads, all lanes together) until every one
@@ -115,6 +145,10 @@ __device__ __forceinline__ void fwd_fanin(const DevState& s, const FwdPre& f, in
         bool ok = !stall;
 #pragma unroll
         for (int k = 0; k < STA_MAX_ARCS; ++k) {
+            // every lane issues the same loads (unused arcs read the driver's own
+            // words, a valid address; their values are not used): no branch, so
+            // the warp stays converged.  Loading only the cell's own arcs, as
+            // predicated loads, was measured slower.
             const int pin = k < f.na ? f.pin[k] : dp;
             const int r = (f.rfi >> k) & 1;
             const int q = 4 * pin + 2 * el + r;
@@ -163,15 +197,10 @@ __device__ __forceinline__ void store_sink_polled(const DevState& s, int p, cons
     if (lse) st_relaxed_f2(s.ats + 2 * p, make_float2(z0 + wdi.x, z1 + wdi.x));
 }
 
-__device__ __forceinline__ DrvOut fwd_eval(const DevNet& g, const DevState& s, const FwdPre& f, int dp, int c,
-                                           float gamma, bool lse, bool write_adel, const float* ain,
-                                           const float* sin, const float* zin) {
+__device__ __forceinline__ DrvOut fwd_eval(const DevState& s, const FwdPre& f, int dp, int c, float gamma, bool lse,
+                                           const float* ain, const float* sin, const float* zin, const float2* col,
+                                           int lane, float* D, bool asserted) {
     const int el = c >> 1, rf = c & 1;
-    const bool cell = f.t >= 0;
-    const int ty = cell ? f.t : 0;
-    // asserted driver: its constant values (set at creation)
-    const float at_c = __ldcg(s.at + 4 * dp + c), sl_c = __ldcg(s.slew + 4 * dp + c);
-    const float ats_c = __ldcg(s.ats + 2 * dp + rf);
     float best_at = el ? -kInf : kInf, best_sl = el ? -kInf : kInf, m = -kInf;
     float cand[STA_MAX_ARCS];
 #pragma unroll
@@ -180,24 +209,27 @@ __device__ __forceinline__ DrvOut fwd_eval(const DevNet& g, const DevState& s, c
         int is;
         float ts;
         slew_seg(f.sidx, f.sinv, sin[k], is, ts);
-        float4 dq, sq;
-        cell_corners(g, ty, k, rf, is, f.jl, dq, sq);
-        const float D = lerp_cell(dq, ts, f.ul);
-        const float S = lerp_cell(sq, ts, f.ul);
-        if (write_adel && use) s.adel[4 * (f.a0 + k) + c] = D;
-        const float v = ain[k] + D;
+        const float2 lo = col[(k * STA_LUT + is) * 32 + lane], hi = col[(k * STA_LUT + is + 1) * 32 + lane];
+        D[k] = fmaf(ts, hi.x - lo.x, lo.x);
+        const float S = fmaf(ts, hi.y - lo.y, lo.y);
+        const float v = ain[k] + D[k];
         const float ba = el ? fmaxf(best_at, v) : fminf(best_at, v);
         const float bs = el ? fmaxf(best_sl, S) : fminf(best_sl, S);
         best_at = use ? ba : best_at;
         best_sl = use ? bs : best_sl;
-        cand[k] = use ? zin[k] + D : -kInf;
+        cand[k] = use ? zin[k] + D[k] : -kInf;
         m = fmaxf(m, cand[k]);
     }
     const float lse_v = lse_arcs(cand, f.na, f.na > 0 ? m : 0.f, gamma);
     DrvOut o;
-    o.at = cell ? best_at : at_c;
-    o.slew = cell ? best_sl : sl_c;
-    o.ats = (el && lse) ? (cell ? lse_v : ats_c) : 0.f;
+    o.at = best_at;
+    o.slew = best_sl;
+    o.ats = (el && lse) ? lse_v : 0.f;
+    if (asserted) {  // an asserted driver (level-0 tasks only): its constants, set at creation
+        o.at = __ldcg(s.at + 4 * dp + c);
+        o.slew = __ldcg(s.slew + 4 * dp + c);
+        o.ats = (el && lse) ? __ldcg(s.ats + 2 * dp + rf) : 0.f;
+    }
     return o;
 }
 
@@ -242,16 +274,14 @@ __device__ void fwd_df_warp(const DevNet& g, const DevState& s, const DfState& d
         f.na = 0;
     }
     const int dp = w.pin0 + (j1 < nn ? hj : 0);
+    float2* col = df_cols();
+    fwd_cols(g, f, c & 1, col, w.lane);
 
     float ain[STA_MAX_ARCS], sin[STA_MAX_ARCS], zin[STA_MAX_ARCS];
     fwd_fanin<lse>(s, f, dp, c, ain, sin, zin, t == stall_task, d.abort_word);
 
-    const DrvOut o = fwd_eval(g, s, f, dp, c, gamma, lse, true, ain, sin, zin);
-    if (j1 < nn && f.t >= 0) {
-        s.at[4 * dp + c] = o.at;
-        s.slew[4 * dp + c] = o.slew;
-        if (lse && c >= 2) s.ats[2 * dp + c - 2] = o.ats;
-    }
+    float D[STA_MAX_ARCS];
+    const DrvOut o = fwd_eval(s, f, dp, c, gamma, lse, ain, sin, zin, col, w.lane, D, j1 < nn && f.t < 0);
     const int src = 4 * max(w.j, 0);
     float A[4], S[4];
 #pragma unroll
@@ -260,7 +290,17 @@ __device__ void fwd_df_warp(const DevNet& g, const DevState& s, const DfState& d
         S[k] = __shfl_sync(kFull, o.slew, src + k);
     }
     const float z0 = __shfl_sync(kFull, o.ats, src + 2), z1 = __shfl_sync(kFull, o.ats, src + 3);
+    // the sinks' words first: consumers poll them; the driver's words and the arc
+    // delays are read only after the sweep
     if (sink) store_sink_polled(s, p, A, S, z0, z1, wdi, lse);
+    if (j1 < nn && f.t >= 0) {
+        s.at[4 * dp + c] = o.at;
+        s.slew[4 * dp + c] = o.slew;
+        if (lse && c >= 2) s.ats[2 * dp + c - 2] = o.ats;
+#pragma unroll
+        for (int k = 0; k < STA_MAX_ARCS; ++k)
+            if (k < f.na) s.adel[4 * (f.a0 + k) + c] = D[k];
+    }
 }
 
 // A 32-sink chunk of a large net: the net's load and wire RC come from the
@@ -278,16 +318,14 @@ __device__ void fwd_df_chunk(const DevNet& g, const DevState& s, const DfState& 
     }
     float2 wdi = make_float2(0.f, 0.f);
     if (lane < cnt) wdi = s.wdi[p0 + lane];
+    float2* col = df_cols();
+    fwd_cols(g, f, lane & 1, col, lane);
 
     float ain[STA_MAX_ARCS], sin[STA_MAX_ARCS], zin[STA_MAX_ARCS];
     fwd_fanin<lse>(s, f, dp, lane & 3, ain, sin, zin, t == stall_task, d.abort_word);
 
-    const DrvOut o = fwd_eval(g, s, f, dp, lane & 3, gamma, lse, first && lane < 4, ain, sin, zin);
-    if (lane < 4 && first && f.t >= 0) {
-        s.at[4 * dp + lane] = o.at;
-        s.slew[4 * dp + lane] = o.slew;
-        if (lse && lane >= 2) s.ats[2 * dp + lane - 2] = o.ats;
-    }
+    float D[STA_MAX_ARCS];
+    const DrvOut o = fwd_eval(s, f, dp, lane & 3, gamma, lse, ain, sin, zin, col, lane, D, lane < 4 && f.t < 0);
     float A[4], S[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -296,6 +334,14 @@ __device__ void fwd_df_chunk(const DevNet& g, const DevState& s, const DfState& 
     }
     const float z0 = __shfl_sync(kFull, o.ats, 2), z1 = __shfl_sync(kFull, o.ats, 3);
     if (lane < cnt) store_sink_polled(s, p0 + lane, A, S, z0, z1, wdi, lse);
+    if (lane < 4 && first && f.t >= 0) {  // the first chunk stores the driver and its arc delays
+        s.at[4 * dp + lane] = o.at;
+        s.slew[4 * dp + lane] = o.slew;
+        if (lse && lane >= 2) s.ats[2 * dp + lane - 2] = o.ats;
+#pragma unroll
+        for (int k = 0; k < STA_MAX_ARCS; ++k)
+            if (k < f.na) s.adel[4 * (f.a0 + k) + lane] = D[k];
+    }
 }
 
 template <bool lse>
@@ -327,12 +373,14 @@ __global__ void __launch_bounds__(kBlock) k_bwd_reset(DevState s, const int32_t*
     }
 }
 
-// Before a forward sweep: the arrival / slew / LSE-arrival words that forward
-// tasks poll -- those of cell-input pins the sweep writes -- are set to
-// kUnwritten (asserted pins keep their constants; sinks that feed no cell are
-// only written).
-__global__ void __launch_bounds__(kBlock) k_fwd_reset(DevState s, const uint8_t* __restrict__ keep,
-                                                      const int32_t* __restrict__ pin_cons, int P) {
+// Before a forward sweep, in one launch: the RC of the large nets (one chunk of
+// sinks per block, see rc_chunk), and, on every block, a grid-stride share of
+// the reset of the words that forward tasks poll -- the arrival / slew /
+// LSE-arrival words of the cell-input pins the sweep writes -- to kUnwritten
+// (asserted pins keep their constants; sinks that feed no cell are only written).
+__global__ void __launch_bounds__(kBlock) k_fwd_prologue(DevNet g, DevState s, const uint8_t* __restrict__ keep,
+                                                         const int32_t* __restrict__ pin_cons, int P) {
+    if ((int)blockIdx.x < g.nrc) rc_chunk(g, s, g.rc_chunk[blockIdx.x], g.rc_net[blockIdx.x]);
     const float u = __uint_as_float(kUnwritten);
     for (int p = blockIdx.x * kBlock + threadIdx.x; p < P; p += gridDim.x * kBlock) {
         if (keep[p] || pin_cons[p] < 0) continue;
@@ -905,20 +953,37 @@ __global__ void __launch_bounds__(kBlock, 3) k_bwd_df(DevNet g, DevState s, DfSt
 
 }  // namespace
 
+// Co-resident blocks of a sweep: the smallest count over every variant the
+// sweep may launch (they share one grid size).  Also grants the forward kernels
+// their dynamic shared memory (above the default 48 KB), once per device.
 int dataflow_max_blocks(int fwd) {
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (fwd) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_df<true>, kBlock, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_df<3>, kBlock, 0);
+    int per_sm = 1 << 20;
+    auto take = [&](auto kernel, size_t smem) {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kBlock, smem);
+        per_sm = n < per_sm ? n : per_sm;
+    };
+    if (fwd) {
+        cudaFuncSetAttribute(k_fwd_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+        cudaFuncSetAttribute(k_fwd_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+        take(k_fwd_df<true>, kFwdSmem);
+        take(k_fwd_df<false>, kFwdSmem);
+    } else {
+        take(k_bwd_df<1>, 0);
+        take(k_bwd_df<2>, 0);
+        take(k_bwd_df<3>, 0);
+    }
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 
 void launch_fwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int lse,
                          int stall_task, cudaStream_t st) {
     if (d.TF == 0) return;
-    if (lse) launch_coop(k_fwd_df<true>, grid, kBlock, st, g, s, d, gamma, stall_task);
-    else launch_coop(k_fwd_df<false>, grid, kBlock, st, g, s, d, gamma, stall_task);
+    if (lse) launch_coop(k_fwd_df<true>, grid, kBlock, kFwdSmem, st, g, s, d, gamma, stall_task);
+    else launch_coop(k_fwd_df<false>, grid, kBlock, kFwdSmem, st, g, s, d, gamma, stall_task);
 }
 
 void launch_bwd_reset(const DevState& s, const DfState& d, int P, int mode, cudaStream_t st) {
@@ -929,19 +994,20 @@ void launch_bwd_reset(const DevState& s, const DfState& d, int P, int mode, cuda
                                            d.npart * kPartFloats);
 }
 
-void launch_fwd_reset(const DevState& s, const DfState& d, int P, cudaStream_t st) {
-    if (P == 0) return;
+void launch_fwd_prologue(const DevNet& g, const DevState& s, const DfState& d, int P, cudaStream_t st) {
     int blocks = (P + kBlock - 1) / kBlock;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    k_fwd_reset<<<blocks, kBlock, 0, st>>>(s, d.pin_keep, d.pin_cons, P);
+    if (blocks < g.nrc) blocks = g.nrc;
+    if (blocks == 0) return;
+    k_fwd_prologue<<<blocks, kBlock, 0, st>>>(g, s, d.pin_keep, d.pin_cons, P);
 }
 
 void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int mode,
                          cudaStream_t st) {
     if (d.TB == 0) return;
-    if (mode == 1) launch_coop(k_bwd_df<1>, grid, kBlock, st, g, s, d, gamma);
-    else if (mode == 2) launch_coop(k_bwd_df<2>, grid, kBlock, st, g, s, d, gamma);
-    else launch_coop(k_bwd_df<3>, grid, kBlock, st, g, s, d, gamma);
+    if (mode == 1) launch_coop(k_bwd_df<1>, grid, kBlock, 0, st, g, s, d, gamma);
+    else if (mode == 2) launch_coop(k_bwd_df<2>, grid, kBlock, 0, st, g, s, d, gamma);
+    else launch_coop(k_bwd_df<3>, grid, kBlock, 0, st, g, s, d, gamma);
 }
 
 }  // namespace sta

@@ -148,11 +148,11 @@ __device__ __forceinline__ void signal_consumers(int32_t* cnt, const int32_t* ou
 // cooperative launch: every block of the grid is resident at once (the waits
 // rely on it); `grid` must not exceed the kernel's co-resident block count
 template <typename K, typename... Args>
-void launch_coop(K kernel, int grid, int block, cudaStream_t st, Args... args) {
+void launch_coop(K kernel, int grid, int block, size_t smem, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

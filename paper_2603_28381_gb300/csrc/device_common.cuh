@@ -274,6 +274,41 @@ __device__ __forceinline__ float rc_sink(const DevNet& g, const DevState& s, int
     return fmaf(g.c, dist, cap);
 }
 
+// RC of one chunk of a large net's sinks (one 256-thread block): every sink's
+// (delay, impulse) and the chunk's share of the load, reduced in a fixed order.
+// A net's only chunk writes its load; otherwise the chunk stores its partial and
+// the last chunk of the net to finish (a device-scope counter, reset by that
+// chunk for the next launch) adds the partials in chunk order, so the load does
+// not depend on which block finishes last.
+__device__ __forceinline__ void rc_chunk(const DevNet& g, const DevState& s, int4 ck, int2 cn) {
+    __shared__ float sh[kWarpsPerBlock];
+    __shared__ int last;
+    const int n = ck.x, d = g.net_ptr[n];
+    const float2 xyd = s.xy[d];
+    const int e = ck.y + ck.z;
+    float acc = 0.f;
+#pragma unroll 4
+    for (int p = ck.y + threadIdx.x; p < e; p += kBlock) acc += rc_sink(g, s, p, s.xy[p], xyd, g.pin_cap[p]);
+    acc = block_reduce(acc, sh, OpSum());
+    if (ck.w < 0) {
+        if (threadIdx.x == 0) s.load[n] = g.pin_cap[d] + acc;
+        return;
+    }
+    if (threadIdx.x == 0) {
+        s.rc_part[ck.w] = acc;
+        __threadfence();
+        last = atomicAdd(s.rc_count + cn.x, 1) == cn.y - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        float sum = 0.f;
+        for (int k = 0; k < cn.y; ++k) sum += __ldcg(s.rc_part + cn.x + k);
+        s.load[n] = g.pin_cap[d] + sum;
+        s.rc_count[cn.x] = 0;
+    }
+}
+
 __device__ __forceinline__ void store_sink(const DevState& s, int p, const float* A, const float* S, float z0,
                                            float z1, bool lse) {
     const float2 w = s.wdi[p];

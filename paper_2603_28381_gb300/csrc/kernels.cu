@@ -45,25 +45,16 @@ __device__ void rc_warp(const DevNet& g, const DevState& s, int n0, int nn) {
     if (w.valid && w.lane == w.last) s.load[n0 + w.j] = v;
 }
 
-__device__ void rc_block(const DevNet& g, const DevState& s, int n) {
-    __shared__ float sh[kWarpsPerBlock];
-    const int d = g.net_ptr[n], e = g.net_ptr[n + 1];
-    const float2 xyd = s.xy[d];
-    float acc = 0.f;
-#pragma unroll 4
-    for (int p = d + 1 + threadIdx.x; p < e; p += kBlock) acc += rc_sink(g, s, p, s.xy[p], xyd, g.pin_cap[p]);
-    acc = block_reduce(acc, sh, OpSum());
-    if (threadIdx.x == 0) s.load[n] = g.pin_cap[d] + acc;
-}
-
-__global__ void __launch_bounds__(kBlock) k_rc(DevNet g, DevState s, int nw, int nc) {
+// blocks [0, nwb): 8 warp tasks each; the rest: one large-net RC chunk each
+__global__ void __launch_bounds__(kBlock) k_rc(DevNet g, DevState s, int nw) {
     const int nwb = (nw + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if ((int)blockIdx.x < nwb) {
         const int t = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
         if (t >= nw) return;
         rc_warp(g, s, g.wtask[2 * t], g.wtask[2 * t + 1]);
     } else {
-        rc_block(g, s, g.ctask[blockIdx.x - nwb]);
+        const int k = blockIdx.x - nwb;
+        rc_chunk(g, s, g.rc_chunk[k], g.rc_net[k]);
     }
 }
 
@@ -390,7 +381,34 @@ __device__ __forceinline__ float2 ep_dloss(float4 con, float2 z, float gamma, fl
     return make_float2(gr, gf);
 }
 
-__global__ void __launch_bounds__(kBlock) k_ep1(DevNet g, DevState s, float gamma, int lse) {
+// partial of block b written by another block of the same launch: read through L2
+__device__ __forceinline__ EpAcc ep_load_cg(const EpAcc* p) {
+    static_assert(sizeof(EpAcc) == 48, "EpAcc layout");
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = __ldcg(q), b = __ldcg(q + 1);
+    const float4 c = __ldcg(reinterpret_cast<const float4*>(q + 2));
+    EpAcc r;
+    r.tns_e = a.x;
+    r.tns_l = a.y;
+    r.tns_g = b.x;
+    r.viol = b.y;
+    r.wns_e = c.x;
+    r.wns_l = c.y;
+    r.wmin = c.z;
+    r.wsum = c.w;
+    return r;
+}
+
+// Endpoint slacks, WNS / TNS and the smoothed terms in one launch: each block
+// reduces a grid-stride share of the endpoints in a fixed order and stores its
+// partial; the last block to finish (a device-scope counter, reset by it for
+// the next launch) merges the partials in block order, so the summary does not
+// depend on which block finishes last.  With rs_cons non-null the blocks also
+// mark the words the next fused dataflow backward sweep polls (the required-time
+// and adjoint words of cell-input pins and the large nets' partial records).
+__global__ void __launch_bounds__(kBlock) k_ep(DevNet g, DevState s, float gamma, int lse,
+                                               const int32_t* __restrict__ rs_cons, int P, float* rs_part,
+                                               int rs_part_words) {
     EpAcc acc = ep_identity();
     for (int e = blockIdx.x * kBlock + threadIdx.x; e < g.E; e += gridDim.x * kBlock) {
         const int p = g.ep_pin[e];
@@ -417,13 +435,29 @@ __global__ void __launch_bounds__(kBlock) k_ep1(DevNet g, DevState s, float gamm
         ep_merge(acc, b, gamma);
     }
     ep_block_reduce(acc, gamma);
-    if (threadIdx.x == 0) reinterpret_cast<EpAcc*>(s.red)[blockIdx.x] = acc;
-}
-
-__global__ void __launch_bounds__(kBlock) k_ep2(DevNet g, DevState s, float gamma, int lse, int nparts) {
-    EpAcc acc = ep_identity();
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        reinterpret_cast<EpAcc*>(s.red)[blockIdx.x] = acc;
+        __threadfence();
+        last = atomicAdd(s.ep_count, 1) == (int)gridDim.x - 1;
+    }
+    if (rs_cons) {
+        const float u = __uint_as_float(kUnwritten);
+        for (int i = blockIdx.x * kBlock + threadIdx.x; i < rs_part_words; i += gridDim.x * kBlock) rs_part[i] = u;
+        for (int p = blockIdx.x * kBlock + threadIdx.x; p < P; p += gridDim.x * kBlock) {
+            if (rs_cons[p] < 0) continue;
+            reinterpret_cast<float4*>(s.rat)[p] = make_float4(u, u, u, u);
+            reinterpret_cast<float2*>(s.g_ats)[p] = make_float2(u, u);
+            reinterpret_cast<float2*>(s.g_slew)[p] = make_float2(u, u);
+        }
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    acc = ep_identity();
     // thread i merges partials i, i + 256, ... in order; then the fixed-order tree
-    for (int k = threadIdx.x; k < nparts; k += kBlock) ep_merge(acc, reinterpret_cast<const EpAcc*>(s.red)[k], gamma);
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += kBlock)
+        ep_merge(acc, ep_load_cg(reinterpret_cast<const EpAcc*>(s.red) + k), gamma);
     ep_block_reduce(acc, gamma);
     if (threadIdx.x == 0) {
         double* o = s.summary;
@@ -436,6 +470,7 @@ __global__ void __launch_bounds__(kBlock) k_ep2(DevNet g, DevState s, float gamm
             (lse && acc.wsum > 0.f) ? (double)acc.wmin - (double)gamma * log((double)acc.wsum) : (double)kInf;
         o[STA_SUM_LATE_VIOLATIONS] = acc.viol;
         o[STA_SUM_NUM_ENDPOINTS] = g.E;
+        *s.ep_count = 0;
     }
 }
 
@@ -513,10 +548,10 @@ void launch_gather_xy(const DevNet& g, const DevState& s, const float2* xy_user,
     k_gather_xy<<<grid_for(g.P), kBlock, 0, st>>>(g, s, xy_user);
 }
 
-void launch_rc(const DevNet& g, const DevState& s, int nw, int nc, cudaStream_t st) {
-    const int blocks = (nw + kWarpsPerBlock - 1) / kWarpsPerBlock + nc;
+void launch_rc(const DevNet& g, const DevState& s, int nw, cudaStream_t st) {
+    const int blocks = (nw + kWarpsPerBlock - 1) / kWarpsPerBlock + g.nrc;
     if (blocks == 0) return;
-    k_rc<<<blocks, kBlock, 0, st>>>(g, s, nw, nc);
+    k_rc<<<blocks, kBlock, 0, st>>>(g, s, nw);
 }
 
 void launch_fwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0, int nc, float gamma, int lse,
@@ -526,9 +561,10 @@ void launch_fwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0
     k_fwd<<<blocks, kBlock, 0, st>>>(g, s, w0, nw, c0, nc, gamma, lse);
 }
 
-void launch_endpoints(const DevNet& g, const DevState& s, float gamma, int lse, cudaStream_t st) {
-    k_ep1<<<kEpBlocks, kBlock, 0, st>>>(g, s, gamma, lse);
-    k_ep2<<<1, kBlock, 0, st>>>(g, s, gamma, lse, kEpBlocks);
+void launch_endpoints(const DevNet& g, const DevState& s, float gamma, int lse, cudaStream_t st, const DfState* d,
+                      int P) {
+    if (d) k_ep<<<kEpBlocks, kBlock, 0, st>>>(g, s, gamma, lse, d->pin_cons, P, d->apart, d->npart * kPartFloats);
+    else k_ep<<<kEpBlocks, kBlock, 0, st>>>(g, s, gamma, lse, nullptr, 0, nullptr, 0);
 }
 
 void launch_bwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0, int nc, float gamma, int mode,

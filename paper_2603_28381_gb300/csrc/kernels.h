@@ -17,17 +17,21 @@ struct DevNet {
     const float* pin_cap;        // [P]
     const int32_t* wtask;        // [2W]
     const int32_t* ctask;        // [Cb]
+    const int4* rc_chunk;        // [K] RC chunks of the nets > 32 pins (Layout::rc_chunk)
+    const int2* rc_net;          // [K]
     const float* lib_idx;        // [T*16]
     const float* lib_inv;        // [T*16]
     const int32_t* lib_unate;    // [T]
     const float* lib_tab;        // [T*4*2*98]
     const float4* lib_cell;      // [T*4*2*36*2] corner-packed cells (delay float4, slew float4)
+    const float4* lib_col;       // [T*4*2*6*7] slew rows of each load segment (Layout::lib_col)
     const int4* net_desc;        // [N*2] per-net driver-cell record (see Layout::net_desc)
     const int32_t* ep_pin;       // [E]
     const float* ep_rat;         // [E*4]
     const int32_t* ep_clk;       // [E] capturing clock pin (propagated clock), -1 none; null: ideal clock
     float r, c;                  // Ohm/um, fF/um
     int32_t P, Pnet, N, E;
+    int32_t nrc;                 // RC chunks
 };
 
 // Mutable per-call state (internal order unless stated).
@@ -49,6 +53,9 @@ struct DevState {
     float* params;     // [4] w_tns, w_wns
     float* cap_seed;   // [P] d loss / d (rising arrival) of capturing clock pins, 0 elsewhere;
                        // null without a propagated clock
+    float* rc_part;    // [rc_slots] partial loads of the nets split into several RC chunks
+    int32_t* rc_count; // [rc_slots] chunks done (0 between launches: the last chunk resets it)
+    int32_t* ep_count; // [1] endpoint blocks done (0 between launches)
 };
 
 // Dataflow schedule: task lists, the counters of the large nets' gradient
@@ -133,8 +140,6 @@ void launch_fwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, i
                          int stall_task, cudaStream_t st);
 // marks the words a dataflow backward sweep of this mode writes as not yet written
 void launch_bwd_reset(const DevState& s, const DfState& d, int P, int mode, cudaStream_t st);
-// marks every word the dataflow forward sweep writes as not yet written (kUnwritten)
-void launch_fwd_reset(const DevState& s, const DfState& d, int P, cudaStream_t st);
 void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int mode,
                          cudaStream_t st);
 // largest co-resident grid of the dataflow kernels on the current device
@@ -144,10 +149,16 @@ int dataflow_max_blocks(int fwd);
 void launch_rc_cte(const DevNet& g, const DevState& s, int n0, int n1, cudaStream_t st);
 
 void launch_gather_xy(const DevNet& g, const DevState& s, const float2* xy_user, cudaStream_t st);
-void launch_rc(const DevNet& g, const DevState& s, int nw, int nc, cudaStream_t st);
+// net RC: the first nw warp tasks (packed small nets) and every large-net chunk
+void launch_rc(const DevNet& g, const DevState& s, int nw, cudaStream_t st);
+// dataflow forward prologue: large-net RC chunks and the reset of the sweep's polled words
+void launch_fwd_prologue(const DevNet& g, const DevState& s, const DfState& d, int P, cudaStream_t st);
 void launch_fwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0, int nc, float gamma,
                       int lse, cudaStream_t st);
-void launch_endpoints(const DevNet& g, const DevState& s, float gamma, int lse, cudaStream_t st);
+// endpoint slacks and the summary in one launch; with d non-null it also marks the words
+// the next fused (mode 3) dataflow backward sweep polls
+void launch_endpoints(const DevNet& g, const DevState& s, float gamma, int lse, cudaStream_t st,
+                      const DfState* d = nullptr, int P = 0);
 // mode bit 1 = required times, bit 2 = adjoint
 void launch_bwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0, int nc, float gamma,
                       int mode, cudaStream_t st);

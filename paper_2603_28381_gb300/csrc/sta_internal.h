@@ -31,6 +31,7 @@ constexpr int kEpBlocks = 4 * 152;  // endpoint reduction partials of one placem
 constexpr float kKrc = 1e-3f;       // Ohm * fF in ps
 constexpr int kPartFloats = 12;     // floats per backward partial (large nets)
 constexpr uint32_t kUnwritten = 0x7fbadbadu;  // a NaN: "not written yet in this sweep"
+constexpr int kRcChunk = 1024;      // sinks per block of the large nets' RC prologue
 
 // Granularity of the dataflow tasks: nets of at most `big` pins are packed
 // (consecutive nets of a level while their pins fit in pack_pins, at most
@@ -66,6 +67,12 @@ struct Layout {
     std::vector<int32_t> lvl_ctask;    // [L+1] block-task ranges per level
     std::vector<int32_t> wtask;        // [2*W] (first net, number of nets)
     std::vector<int32_t> ctask;        // [Cb] net of each block task
+    // RC of the nets of more than 32 pins in chunks of kRcChunk sinks, one block
+    // each: {net, first sink, sinks, partial slot (-1: the net's only chunk)} and
+    // {first slot of the net, chunks of the net}
+    std::vector<int32_t> rc_chunk;     // [4*K]
+    std::vector<int32_t> rc_net;       // [2*K]
+    int32_t rc_slots = 0;
 
     std::vector<int32_t> lvl_net;      // [L+1] first internal net of each level
 
@@ -108,6 +115,8 @@ struct Layout {
                                        // written during the sweep and 4-7 negative unate, input pins 0-3
     std::vector<float> lib_cell;       // [T*4*2*36*8] per (type, arc, rf_out, slew seg, load seg): the
                                        // four delay corners then the four slew corners (one 32-byte sector)
+    std::vector<float> lib_col;        // [T*4*2*6*7*4] per (type, arc, rf_out, load seg j, slew row i):
+                                       // delay at (i, j), (i, j+1), slew at (i, j), (i, j+1)
 
     float r_per_um = 0.f, c_per_um = 0.f;
 };
