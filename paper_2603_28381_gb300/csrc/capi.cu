@@ -840,6 +840,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
             cudaMemcpy(s.rat, L.rat0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(set_err(STA_ERR_CUDA, "initial state upload failed"));
         launch_init_ats(s, L.P, 0);
+        STEP(h->alloc(d.brec, 8 * (size_t)std::max(L.N, 1)));
     }
     if (cudaMemset(d.abort_word, 0, 8) != cudaSuccess || cudaMemset(d.heads, 0, 16) != cudaSuccess)
         return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));

@@ -43,7 +43,7 @@ struct FwdPre {
     int rfi;  // bit k: input transition of arc k
     int dyn;  // bit k: arc k's input pin is written during the sweep (not asserted)
     int jl;   // load segment and fraction
-    float ul;
+    float ul, inv_l;
     float sidx[6], sinv[6];  // slew index points 0..5 of the type and 1/width of each segment
 };
 
@@ -65,7 +65,7 @@ __device__ __forceinline__ FwdPre fwd_pre(const DevNet& g, const DfState& d, int
     FwdPre f;
     f.t = g.net_drv[n];
     f.a0 = f.na = f.rfi = f.jl = f.dyn = 0;
-    f.ul = 0.f;
+    f.ul = f.inv_l = 0.f;
 #pragma unroll
     for (int k = 0; k < STA_MAX_ARCS; ++k) f.pin[k] = 0;
 #pragma unroll
@@ -88,7 +88,8 @@ __device__ __forceinline__ FwdPre fwd_pre(const DevNet& g, const DfState& d, int
         }
     const float* li = g.lib_idx + f.t * kLibStride + 8;
     f.jl = axis_seg(li, ld);
-    f.ul = (ld - __ldg(li + f.jl)) * __ldg(g.lib_inv + f.t * kLibStride + 8 + f.jl);
+    f.inv_l = __ldg(g.lib_inv + f.t * kLibStride + 8 + f.jl);
+    f.ul = (ld - __ldg(li + f.jl)) * f.inv_l;
     return f;
 }
 
@@ -233,6 +234,49 @@ __device__ __forceinline__ DrvOut fwd_eval(const DevState& s, const FwdPre& f, i
     return o;
 }
 
+// After a late lane's critical stores: the terms the backward sweep needs for
+// this (net, output transition), which depend on forward results only -- per
+// arc the LSE weight w_k = exp((LSE-AT_in + delay - LSE-AT_out) / gamma) (Eq. 4's
+// softmax), the bilinear partials of the delay along slew and load, and, for
+// the arc attaining the late output slew (first one on ties), the slew
+// partials.  Same operations as a lookup from the raw tables, so the backward
+// reads bit-identical values in one record instead of recomputing them from
+// scattered loads before its wait.
+__device__ __forceinline__ void fwd_brec(const DevNet& g, const DfState& d, const FwdPre& f, int n, int rf,
+                                         const float* sin, const float* zin, const float* D, float ats_out,
+                                         float gamma) {
+    float w[STA_MAX_ARCS], dds[STA_MAX_ARCS], ddl[STA_MAX_ARCS];
+    float best = -kInf, dss = 0.f, dsl = 0.f;
+    int amax = -1;
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        w[k] = dds[k] = ddl[k] = 0.f;
+        if (k < f.na) {
+            int is;
+            float ts;
+            slew_seg(f.sidx, f.sinv, sin[k], is, ts);
+            const float inv_s = f.sinv[is];
+            const float4* q = g.lib_col + ((((size_t)f.t * STA_MAX_ARCS + k) * 2 + rf) * 6 + f.jl) * STA_LUT + is;
+            const float4 r0 = __ldg(q), r1 = __ldg(q + 1);  // rows is, is+1: delay (j, j+1), slew (j, j+1)
+            float dSs, dSl;
+            lerp_cell_grad(make_float4(r0.x, r0.y, r1.x, r1.y), ts, f.ul, inv_s, f.inv_l, dds[k], ddl[k]);
+            const float S = lerp_cell_grad(make_float4(r0.z, r0.w, r1.z, r1.w), ts, f.ul, inv_s, f.inv_l, dSs, dSl);
+            w[k] = expf((zin[k] + D[k] - ats_out) / gamma);
+            if (S > best) {
+                best = S;
+                amax = k;
+                dss = dSs;
+                dsl = dSl;
+            }
+        }
+    }
+    float4* r = d.brec + ((size_t)n * 2 + rf) * 4;
+    r[0] = make_float4(w[0], w[1], w[2], w[3]);
+    r[1] = make_float4(dds[0], dds[1], dds[2], dds[3]);
+    r[2] = make_float4(ddl[0], ddl[1], ddl[2], ddl[3]);
+    r[3] = make_float4(dss, dsl, __int_as_float(amax), 0.f);
+}
+
 // Packed small nets: net RC (Eqs. 1-3) of the task's own pins and every
 // static load first; then the wait; then the driver cells (4 lanes per net)
 // and the wire step to every sink.
@@ -300,6 +344,7 @@ __device__ void fwd_df_warp(const DevNet& g, const DevState& s, const DfState& d
 #pragma unroll
         for (int k = 0; k < STA_MAX_ARCS; ++k)
             if (k < f.na) s.adel[4 * (f.a0 + k) + c] = D[k];
+        if (lse && c >= 2) fwd_brec(g, d, f, n0 + j1, c & 1, sin, zin, D, o.ats, gamma);
     }
 }
 
@@ -341,6 +386,7 @@ __device__ void fwd_df_chunk(const DevNet& g, const DevState& s, const DfState& 
 #pragma unroll
         for (int k = 0; k < STA_MAX_ARCS; ++k)
             if (k < f.na) s.adel[4 * (f.a0 + k) + lane] = D[k];
+        if (lse && lane >= 2) fwd_brec(g, d, f, n, lane & 1, sin, zin, D, o.ats, gamma);
     }
 }
 
@@ -583,7 +629,7 @@ __device__ __forceinline__ BwdPre bwd_none() {
     return b;
 }
 
-__device__ __forceinline__ BwdPre bwd_pre(const DevNet& g, const DevState& s, int n, int dp, int c, float gamma,
+__device__ __forceinline__ BwdPre bwd_pre(const DevNet& g, const DevState& s, const DfState& d, int n, int c,
                                           int mode) {
     BwdPre b;
     b.t = g.net_drv[n];
@@ -610,36 +656,15 @@ __device__ __forceinline__ BwdPre bwd_pre(const DevNet& g, const DevState& s, in
     // a capturing clock pin is the input of a one-input cell; its seed is read
     // here, before the wait, and added to the rising adjoint it writes
     if ((mode & 2) && el == 1 && s.cap_seed && b.na == 1 && (b.rfi & 1) == 0) b.cs = __ldcg(s.cap_seed + b.pin[0]);
-    if ((mode & 2) && el == 1) {
-        const float ld = s.load[n];
-        const float* li = g.lib_idx + b.t * kLibStride + 8;
-        const int jl = axis_seg(li, ld);
-        const float inv_l = __ldg(g.lib_inv + b.t * kLibStride + 8 + jl);
-        const float ul = (ld - __ldg(li + jl)) * inv_l;
-        const float* si = g.lib_idx + b.t * kLibStride;
-        const float atsd = s.ats[2 * dp + rf];
-        float best = -kInf;
-#pragma unroll
-        for (int k = 0; k < STA_MAX_ARCS; ++k)
-            if (k < b.na) {
-                const int r = (b.rfi >> k) & 1;
-                const float sin = s.slew[4 * b.pin[k] + 2 + r];
-                const int is = axis_seg(si, sin);
-                const float inv_s = __ldg(g.lib_inv + b.t * kLibStride + is);
-                const float ts = (sin - __ldg(si + is)) * inv_s;
-                float4 dq, sq;
-                cell_corners(g, b.t, k, rf, is, jl, dq, sq);
-                float dSs, dSl;
-                lerp_cell_grad(dq, ts, ul, inv_s, inv_l, b.dDs[k], b.dDl[k]);
-                const float S = lerp_cell_grad(sq, ts, ul, inv_s, inv_l, dSs, dSl);
-                b.w[k] = expf((s.ats[2 * b.pin[k] + r] + s.adel[4 * (b.a0 + k) + 2 + rf] - atsd) / gamma);
-                if (S > best) {
-                    best = S;
-                    b.amax = k;
-                    b.dSs = dSs;
-                    b.dSl = dSl;
-                }
-            }
+    if ((mode & 2) && el == 1) {  // the terms the forward sweep stored for (net, rf)
+        const float4* r = d.brec + ((size_t)n * 2 + rf) * 4;
+        const float4 w = r[0], dds = r[1], ddl = r[2], x = r[3];
+        b.w[0] = w.x, b.w[1] = w.y, b.w[2] = w.z, b.w[3] = w.w;
+        b.dDs[0] = dds.x, b.dDs[1] = dds.y, b.dDs[2] = dds.z, b.dDs[3] = dds.w;
+        b.dDl[0] = ddl.x, b.dDl[1] = ddl.y, b.dDl[2] = ddl.z, b.dDl[3] = ddl.w;
+        b.dSs = x.x;
+        b.dSl = x.y;
+        b.amax = __float_as_int(x.z);
     }
     return b;
 }
@@ -687,7 +712,7 @@ __device__ void bwd_df_warp(const DevNet& g, const DevState& s, const DfState& d
     const int j1 = w.lane >> 2, c = w.lane & 3;
     const int hj = __shfl_sync(kFull, w.h, j1);
     const int lastj = (__shfl_sync(kFull, w.h, j1 + 1) - 1) & 31;
-    const BwdPre bp = j1 < nn ? bwd_pre(g, s, n0 + j1, w.pin0 + hj, c, gamma, mode) : bwd_none();
+    const BwdPre bp = j1 < nn ? bwd_pre(g, s, d, n0 + j1, c, mode) : bwd_none();
     float2 xy = make_float2(0.f, 0.f), xyd = make_float2(0.f, 0.f);
     float cap = 0.f;
     int orig = 0;
@@ -830,7 +855,7 @@ __device__ void bwd_df_driver(const DevNet& g, const DevState& s, const DfState&
                               const float* part, int slot0, int nch, float gamma) {
     const int lane = threadIdx.x & 31;
     const int dp = g.net_ptr[n];
-    const BwdPre bp = lane < 4 ? bwd_pre(g, s, n, dp, lane, gamma, mode) : bwd_none();
+    const BwdPre bp = lane < 4 ? bwd_pre(g, s, d, n, lane, mode) : bwd_none();
 
     // the wait: poll the chunks' partial words (reset to kUnwritten before the
     // sweep, written once by the partial tasks) until all are written; bounded

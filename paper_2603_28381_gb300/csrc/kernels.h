@@ -81,6 +81,8 @@ struct DfState {
     const uint8_t* pin_keep; // [P] 1: the forward sweep does not write the pin (asserted values)
     int32_t TF, TB;
     int32_t npart;           // partial records of the backward sweeps
+    float4* brec;            // [N*2*4] per (net, late output transition): the adjoint terms of the
+                             // driver cell the forward sweep computed (see fwd_brec)
 };
 
 // Batched schedule (many placements of one netlist; lane = placement).
