@@ -72,6 +72,10 @@ def parse():
     ap.add_argument("--load", type=float, default=0.8,
                     help="serve: arrival rate as a fraction of the plain loop's service rate")
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--replicas", type=int, default=2,
+                    help="serve: resident copies per netlist in the replicas mode")
+    ap.add_argument("--merge", type=int, default=8,
+                    help="serve: requests of one netlist merged into one batched launch in the merged mode")
     ap.add_argument("--tile-pins", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--batch-sweep", default="levels", choices=["levels", "dataflow"])
@@ -716,8 +720,10 @@ def run_serve(args, emit=True):
     pins = np.array([w.netlist.num_pins for w in designs])
 
     def play(server, ids, arrivals):
-        """Submit at the arrival times, collect completions; latencies in ms."""
+        """Submit at the arrival times, collect completions; latencies in ms and
+        how many requests ran in each request's launch."""
         done, lat, t_first, t_last = 0, np.zeros(R), None, 0.0
+        merged = np.ones(R)
         rid_of = {}
         t0 = StaServer.clock() + 0.05
         i = 0
@@ -735,12 +741,13 @@ def run_serve(args, emit=True):
                 if c["status"] != 0:
                     raise RuntimeError(f"request {j} failed with status {c['status']}")
                 lat[j] = (c["t_done"] - (t0 + arrivals[j])) * 1e3
+                merged[j] = c.get("merged", 1)
                 t_last = max(t_last, c["t_done"])
                 done += 1
             if i < R and wait == 0:
                 time.sleep(max(0.0, min(0.0005, t0 + arrivals[i] - StaServer.clock())))
         span = t_last - t0
-        return lat, span
+        return lat, span, merged
 
     # service times of the plain loop, request by request, to set the arrival rate
     calib = StaServer(sequential=True)
@@ -764,11 +771,13 @@ def run_serve(args, emit=True):
 
     out = {}
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
-    for mode in ("plain", "continuous"):
-        srv = StaServer(sequential=(mode == "plain"), slots=args.slots)
+    for mode in ("plain", "continuous", "replicas", "merged"):
+        srv = StaServer(sequential=(mode == "plain"), slots=args.slots,
+                        merge=args.merge if mode == "merged" else 0,
+                        replicas=args.replicas if mode == "replicas" else 0)
         ids = [srv.add_netlist(w.netlist, w.library) for w in designs]
         stats0 = srv.stats()
-        lat, span = play(srv, ids, arrivals)
+        lat, span, merged = play(srv, ids, arrivals)
         st = srv.stats()
         srv.close()
         out[mode] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -776,6 +785,13 @@ def run_serve(args, emit=True):
                      "pins_per_s": float(pins[which].sum() / span), "span_s": span,
                      "resident_netlists": stats0["resident"], "resident_bytes": stats0["resident_bytes"],
                      "evictions": st["evictions"]}
+        if mode == "replicas":
+            out[mode]["replicas"] = args.replicas
+            out[mode]["copies_made"] = st["admissions"]
+        if mode == "merged":
+            out[mode]["merge_lanes"] = args.merge
+            out[mode]["requests_merged"] = float((merged > 1).mean())
+            out[mode]["mean_requests_per_launch"] = float(R / np.sum(1.0 / merged))
     clk = clocks.stop()
     line = {"metric": "served p50/p99 latency vs plain", "value": out["continuous"]["p99_ms"], "unit": "ms p99",
             "n_gpus": 1, "steps": R, "warmup": 0, "higher_is_better": False, "scaling": "weak",
@@ -787,9 +803,12 @@ def run_serve(args, emit=True):
                        "netlist_pins": pins.tolist(), "arrival_rate_per_s": rate,
                        "mean_plain_service_ms": mean_svc * 1e3, "slots": args.slots,
                        "budget": "150 GiB"},
-            "continuous": out["continuous"], "plain": out["plain"],
+            "continuous": out["continuous"], "plain": out["plain"], "replicas": out["replicas"],
+            "merged": out["merged"],
             "p99_speedup_vs_plain": out["plain"]["p99_ms"] / out["continuous"]["p99_ms"],
             "p50_speedup_vs_plain": out["plain"]["p50_ms"] / out["continuous"]["p50_ms"],
+            "replicas_p99_speedup_vs_plain": out["plain"]["p99_ms"] / out["replicas"]["p99_ms"],
+            "merged_p99_speedup_vs_plain": out["plain"]["p99_ms"] / out["merged"]["p99_ms"],
             "clocks": clk}
     if emit:
         print(json.dumps(line), flush=True)

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define STA_ABI_VERSION 3
+#define STA_ABI_VERSION 4
 #define STA_LUT 7       /* table points per axis */
 #define STA_MAX_ARCS 4  /* arcs (input pins) per cell type */
 
@@ -402,8 +402,11 @@ int sta_abi_version(void);
  * and its netlist is resident and idle, so requests on different netlists run
  * concurrently on the device; requests of one netlist run in order.  A
  * netlist that is not resident is created when the budget allows, evicting
- * idle netlists in least-recently-used order.  A request's results equal those
- * of the same request run alone.  All calls are thread-safe.
+ * idle netlists in least-recently-used order.  Requests of one netlist run one
+ * after another on its resident copy, concurrently on several copies
+ * (replicas), or together as the placements of one batched call (merge).  A
+ * request's results equal those of the same request run alone.  All calls are
+ * thread-safe.
  * ------------------------------------------------------------------------- */
 typedef struct StaServer StaServer;
 
@@ -411,7 +414,17 @@ typedef struct {
     int32_t slots;        /* concurrent requests (0 = 4, at most 64) */
     int32_t sequential;   /* 1: the plain loop: one request at a time, in arrival order */
     int64_t budget_bytes; /* device bytes for resident netlists (0 = 150 GiB) */
-    int32_t reserved[4];
+    int32_t merge;        /* 0: one request per launch.  M in [1, 64]: pending requests of one
+                             netlist with the same gamma and kind (forward / gradient) run
+                             together, up to M at a time, as the placements of one batched
+                             call (STA_SCHED_BATCH with M placements).  Every request of the
+                             netlist then takes that path, alone too, so a request's results
+                             are bit-identical alone and merged.  Not with sequential. */
+    int32_t replicas;     /* resident copies of a netlist, at most (0 = 1): with R > 1, pending
+                             requests of one netlist run concurrently on up to R copies (each
+                             its own handle; copies beyond the first are made only while the
+                             budget allows without evicting).  Not with sequential or merge. */
+    int32_t reserved[2];
 } StaServerOptions;
 
 typedef struct {
@@ -431,11 +444,14 @@ typedef struct {
     int32_t status;       /* StaStatus of the request */
     int32_t netlist;
     double t_submit, t_start, t_done; /* sta_server_clock() seconds: submitted, started, seen done */
+    int32_t merged;       /* requests that ran in the same launch as this one (1: alone) */
+    int32_t reserved;
 } StaServerCompletion;
 
 StaStatus sta_server_create(const StaServerOptions *opt, StaServer **out);
 /* Register a netlist (arrays are copied); preload != 0 also makes it resident
- * now (OOM if it does not fit).  *id identifies it in requests. */
+ * now (OOM if it does not fit), with its further copies (replicas) while the
+ * budget allows without evicting.  *id identifies it in requests. */
 StaStatus sta_server_add_netlist(StaServer *s, const StaNetlistDesc *nl, const StaLibrary *lib,
                                  int32_t preload, int32_t *id);
 StaStatus sta_server_submit(StaServer *s, const StaServerRequest *req, int64_t *id);

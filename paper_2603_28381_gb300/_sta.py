@@ -55,7 +55,8 @@ BATCH_DATAFLOW = 1
 
 
 class StaServerOptions(ctypes.Structure):
-    _fields_ = [("slots", _i32), ("sequential", _i32), ("budget_bytes", ctypes.c_int64), ("reserved", _i32 * 4)]
+    _fields_ = [("slots", _i32), ("sequential", _i32), ("budget_bytes", ctypes.c_int64), ("merge", _i32),
+                ("replicas", _i32), ("reserved", _i32 * 2)]
 
 
 class StaServerRequest(ctypes.Structure):
@@ -65,7 +66,7 @@ class StaServerRequest(ctypes.Structure):
 
 class StaServerCompletion(ctypes.Structure):
     _fields_ = [("id", ctypes.c_int64), ("status", _i32), ("netlist", _i32), ("t_submit", ctypes.c_double),
-                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double), ("merged", _i32), ("reserved", _i32)]
 
 
 class StaError(RuntimeError):

@@ -482,7 +482,10 @@ StaStatus init_batch(StaHandle* h) {
     b.B = h->B;
     b.Bp = (h->B + 31) / 32 * 32;
     b.G = b.Bp / 32;
-    b.GT = b.Bp / kPlacePerWarp;
+    // sweep task groups of 8 placements: only the groups that hold placements
+    // (the padding lanes of the last group ride along; whole padding groups are
+    // not swept)
+    b.GT = (h->B + kPlacePerWarp - 1) / kPlacePerWarp;
     const size_t P = L.P, N = L.N, E = L.E, Bp = b.Bp;
     StaStatus st = STA_OK;
 #define BSTEP(x)                  \

@@ -11,6 +11,11 @@
 // Every request's result is that of the same request run alone: the kernels
 // are deterministic and a netlist's state is only touched by its own requests.
 //
+// With merge = M > 0, pending requests of one netlist with the same gamma and
+// kind run together, up to M at a time, as the placements of one batched call
+// (every netlist's handle is then a batched one, and a request alone is a batch
+// with one real placement, so its results are bit-identical alone and merged).
+//
 // With sequential = 1 the server is the plain one-request-per-launch loop:
 // one slot, strict arrival order.
 #include <algorithm>
@@ -58,15 +63,25 @@ void copy_in(std::vector<T>& v, const T* p, size_t n) {
     v.assign(p, p + n);
 }
 
-struct Net {
-    HostNetlist host;
+// One resident copy of a netlist: a handle and its request scratch.  A netlist
+// may have several (StaServerOptions.replicas), so that its requests run
+// concurrently, each on its own state.
+struct Rep {
     StaHandle* h = nullptr;
-    size_t bytes = 0;        // device bytes while resident (estimate before the first creation)
+    size_t bytes = 0;           // device bytes (the handle's allocations and the scratch)
     bool busy = false;
     double last_use = 0.0;
+    float* grad_dev = nullptr;  // [M][P][2] device gradient of the request(s) in flight (M = 1 unmerged)
+    double* sum_dev = nullptr;  // [M][STA_SUM_COUNT]
+    float* xy_dev = nullptr;    // merged: [M][P][2] positions of the placements in flight
+    float* w_host = nullptr;    // merged: pinned [M][2] loss weights of the placements in flight
+};
+
+struct Net {
+    HostNetlist host;
+    std::vector<Rep*> reps;     // resident copies
+    size_t rep_bytes = 0;       // measured bytes of one copy (0: not created yet, estimate)
     int32_t P = 0;
-    float* grad_dev = nullptr;  // [P][2] device gradient of the request in flight
-    double* sum_dev = nullptr;  // [STA_SUM_COUNT]
 };
 
 struct Req {
@@ -79,9 +94,10 @@ struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
-    Req req{};
+    std::vector<Req> reqs;       // the request(s) in flight (several when merged)
+    Rep* rep = nullptr;          // the netlist copy they run on
     double t_start = 0.0;
-    double* sum_host = nullptr;  // pinned [STA_SUM_COUNT]
+    double* sum_host = nullptr;  // pinned [M][STA_SUM_COUNT]
 };
 
 }  // namespace
@@ -169,6 +185,15 @@ StaStatus copy_netlist(const StaNetlistDesc& d, const StaLibrary& l, HostNetlist
 
 }  // namespace
 
+static void release_rep(Rep* r) {
+    if (r->h) sta_destroy(r->h);
+    if (r->grad_dev) cudaFree(r->grad_dev);
+    if (r->sum_dev) cudaFree(r->sum_dev);
+    if (r->xy_dev) cudaFree(r->xy_dev);
+    if (r->w_host) cudaFreeHost(r->w_host);
+    delete r;
+}
+
 StaServer::~StaServer() {
     stop = true;
     cv.notify_all();
@@ -180,9 +205,7 @@ StaServer::~StaServer() {
         if (s.sum_host) cudaFreeHost(s.sum_host);
     }
     for (Net* n : nets) {
-        if (n->h) sta_destroy(n->h);
-        if (n->grad_dev) cudaFree(n->grad_dev);
-        if (n->sum_dev) cudaFree(n->sum_dev);
+        for (Rep* r : n->reps) release_rep(r);
         delete n;
     }
 }
@@ -195,115 +218,193 @@ namespace {
 // cell output the per-net arrays and the task lists (120 B); per arc the arc
 // delays and dependency edges (32 B); per endpoint 28 B; with a propagated
 // clock 4 B more per pin (clock seeds) and per endpoint (its clock pin).
-size_t estimate_bytes(const HostNetlist& hn) {
+// A batched handle of M placements (merged requests) holds its per-placement
+// state for the padded batch Bp (M rounded up to 32): per pin and placement
+// the positions, arrival / slew / LSE / required times, adjoints, gradient and
+// staging (136 B), per net and placement 12 B, per endpoint and placement 24 B.
+size_t estimate_bytes(const HostNetlist& hn, int merge) {
     const StaNetlistDesc& d = hn.nl;
     const size_t A = d.num_cells ? (size_t)hn.cell_in_ptr[d.num_cells] : 0;
     const size_t clk = d.end_clock ? 4 : 0;
-    return (size_t)d.num_pins * (132 + clk) + ((size_t)d.num_nets + d.num_cells) * 120 + A * 32 +
-           (size_t)d.num_end * (28 + clk) + (1u << 20);
+    const size_t base = (size_t)d.num_pins * (132 + clk) + ((size_t)d.num_nets + d.num_cells) * 120 + A * 32 +
+                        (size_t)d.num_end * (28 + clk) + (1u << 20);
+    if (merge <= 0) return base;
+    const size_t Bp = (size_t)(merge + 31) / 32 * 32;
+    return base + Bp * ((size_t)d.num_pins * (136 + clk) + ((size_t)d.num_nets + d.num_cells) * 12 +
+                        (size_t)d.num_end * 24);
 }
 
 }  // namespace
 
-// Make netlist k resident (create its handle) if the budget allows, evicting
-// idle netlists in least-recently-used order.  Returns false if it cannot be
-// admitted now (the request waits).
-static bool admit(StaServer* S, int k, std::string& err) {
+// Evict the least recently used idle copy of any netlist (not `keep`); false
+// if every resident copy is busy.
+static bool evict_one(StaServer* S, const Rep* keep) {
+    Net* vn = nullptr;
+    size_t vi = 0;
+    for (Net* m : S->nets)
+        for (size_t i = 0; i < m->reps.size(); ++i) {
+            Rep* r = m->reps[i];
+            if (r == keep || r->busy) continue;
+            if (!vn || r->last_use < vn->reps[vi]->last_use) {
+                vn = m;
+                vi = i;
+            }
+        }
+    if (!vn) return false;
+    Rep* r = vn->reps[vi];
+    S->resident_bytes -= r->bytes;
+    release_rep(r);
+    vn->reps.erase(vn->reps.begin() + (long)vi);
+    ++S->evictions;
+    return true;
+}
+
+// An idle resident copy of netlist k for a request: an idle one if there is
+// one; otherwise a new copy -- the first one evicting idle copies of other
+// netlists in least-recently-used order if the budget needs it, further ones
+// (up to StaServerOptions.replicas) only while the budget allows without
+// evicting.  nullptr: none now (the request waits); err set: never.
+static Rep* create_rep(StaServer* S, Net* n, std::string& err);
+
+static int max_copies(const StaServer* S) { return S->opt.merge > 0 ? 1 : std::max(S->opt.replicas, 1); }
+
+static Rep* admit(StaServer* S, int k, std::string& err) {
     Net* n = S->nets[k];
-    if (n->h) return true;
-    const size_t need = n->bytes ? n->bytes : estimate_bytes(n->host);
+    for (Rep* r : n->reps)
+        if (!r->busy) return r;
+    if ((int)n->reps.size() >= max_copies(S)) return nullptr;
+    return create_rep(S, n, err);
+}
+
+// A new resident copy of netlist n (see admit).
+static Rep* create_rep(StaServer* S, Net* n, std::string& err) {
+    const size_t need = n->rep_bytes ? n->rep_bytes : estimate_bytes(n->host, S->opt.merge);
     const size_t budget = (size_t)S->opt.budget_bytes;
     if (need > budget) {
         err = "netlist larger than the memory budget";
-        return false;
+        return nullptr;
     }
-    while (S->resident_bytes + need > budget) {
-        int victim = -1;
-        for (int i = 0; i < (int)S->nets.size(); ++i) {
-            Net* m = S->nets[i];
-            if (m->h && !m->busy && (victim < 0 || m->last_use < S->nets[victim]->last_use)) victim = i;
-        }
-        if (victim < 0) return false;  // everything resident is busy: wait
-        Net* m = S->nets[victim];
-        sta_destroy(m->h);
-        m->h = nullptr;
-        cudaFree(m->grad_dev);
-        cudaFree(m->sum_dev);
-        m->grad_dev = nullptr;
-        m->sum_dev = nullptr;
-        S->resident_bytes -= m->bytes;
-        ++S->evictions;
-    }
+    const bool first = n->reps.empty();
+    while (S->resident_bytes + need > budget)
+        if (!first || !evict_one(S, nullptr)) return nullptr;  // wait
+    const int M = S->opt.merge > 0 ? S->opt.merge : 1;
     StaOptions o{};
     o.use_graphs = 1;
-    o.schedule = STA_SCHED_DATAFLOW;
+    o.schedule = S->opt.merge > 0 ? STA_SCHED_BATCH : STA_SCHED_DATAFLOW;
+    if (S->opt.merge > 0) {  // the lane-per-placement dataflow sweeps, small tasks
+        o.num_placements = M;
+        o.batch_sweep = STA_BATCH_DATAFLOW;
+        o.tile_pins = 2;
+        o.chunk = 8;
+    }
     // a netlist's persistent sweeps use a grid in proportion to its size, so the
     // sweeps of small netlists leave room for others on the device
     o.grid_blocks = S->opt.sequential ? 0 : std::max(8, n->P / 4000);
-    StaStatus st = sta_create(&n->host.nl, &n->host.lib, &o, &n->h);
-    if (st != STA_OK) {
-        err = std::string("sta_create: ") + sta_last_error();
-        n->h = nullptr;
-        return false;
+    Rep* r = new (std::nothrow) Rep();
+    if (!r) {
+        err = "host allocation failed";
+        return nullptr;
     }
-    if (cudaMalloc(&n->grad_dev, (size_t)std::max(n->P, 1) * 8) != cudaSuccess ||
-        cudaMalloc(&n->sum_dev, STA_SUM_COUNT * sizeof(double)) != cudaSuccess) {
+    if (sta_create(&n->host.nl, &n->host.lib, &o, &r->h) != STA_OK) {
+        err = std::string("sta_create: ") + sta_last_error();
+        r->h = nullptr;
+        release_rep(r);
+        return nullptr;
+    }
+    const size_t P1 = (size_t)std::max(n->P, 1);
+    if (cudaMalloc(&r->grad_dev, M * P1 * 8) != cudaSuccess ||
+        cudaMalloc(&r->sum_dev, M * STA_SUM_COUNT * sizeof(double)) != cudaSuccess ||
+        (S->opt.merge > 0 && (cudaMalloc(&r->xy_dev, M * P1 * 8) != cudaSuccess ||
+                              cudaMallocHost(&r->w_host, M * 2 * sizeof(float)) != cudaSuccess))) {
         err = "cudaMalloc of request scratch failed";
-        sta_destroy(n->h);
-        n->h = nullptr;
-        return false;
+        release_rep(r);
+        return nullptr;
     }
     int64_t sz[8];
-    sta_query_sizes(n->h, sz);
+    sta_query_sizes(r->h, sz);
     // measured size (the handle's allocations, its host-input staging, the scratch)
-    n->bytes = (size_t)sz[7] + 2 * (size_t)std::max(n->P, 1) * 8 + STA_SUM_COUNT * sizeof(double);
-    S->resident_bytes += n->bytes;
+    r->bytes = (size_t)sz[7] + (S->opt.merge > 0 ? 3 : 2) * M * P1 * 8 + M * STA_SUM_COUNT * sizeof(double);
+    n->rep_bytes = r->bytes;
+    n->reps.push_back(r);
+    S->resident_bytes += r->bytes;
     ++S->admissions;
     while (S->resident_bytes > budget) {  // the estimate was low: make room, or give up
-        int victim = -1;
-        for (int i = 0; i < (int)S->nets.size(); ++i) {
-            Net* m = S->nets[i];
-            if (m != n && m->h && !m->busy && (victim < 0 || m->last_use < S->nets[victim]->last_use)) victim = i;
-        }
-        Net* m = victim >= 0 ? S->nets[victim] : n;
-        sta_destroy(m->h);
-        m->h = nullptr;
-        cudaFree(m->grad_dev);
-        cudaFree(m->sum_dev);
-        m->grad_dev = nullptr;
-        m->sum_dev = nullptr;
-        S->resident_bytes -= m->bytes;
+        if (first && evict_one(S, r)) continue;
+        S->resident_bytes -= r->bytes;
+        n->reps.pop_back();
+        release_rep(r);
         ++S->evictions;
-        if (m == n) {
-            if (n->bytes > budget) err = "netlist larger than the memory budget";
-            return false;
-        }
+        if (n->rep_bytes > budget) err = "netlist larger than the memory budget";
+        return nullptr;
     }
-    return true;
+    return r;
 }
 
 // Queue one request's work on a slot's stream: positions in, forward, gradient
 // if asked, results out; an event marks its end.
 static StaStatus dispatch(StaServer* S, Slot& sl, Net* n) {
-    const StaServerRequest& r = sl.req.r;
-    StaHandle* h = n->h;
+    const StaServerRequest& r = sl.reqs[0].r;
+    Rep* rp = sl.rep;
+    StaHandle* h = rp->h;
     void* st = sl.st;
     StaStatus s = sta_set_positions(h, r.xy, 0, st);
     if (s == STA_OK)
         s = sta_forward(h, STA_FWD_LSE | STA_FWD_RAT | (r.gradient ? 0u : STA_FWD_RAT_EAGER), r.gamma, st);
     if (s == STA_OK && r.gradient) {
         const float w[2] = {r.w_tns, r.w_wns};
-        s = sta_backward_grad(h, w, 0, n->grad_dev, 1, st);
+        s = sta_backward_grad(h, w, 0, rp->grad_dev, 1, st);
         if (s == STA_OK && r.grad &&
-            cudaMemcpyAsync(r.grad, n->grad_dev, (size_t)n->P * 8, cudaMemcpyDeviceToHost, sl.st) != cudaSuccess)
+            cudaMemcpyAsync(r.grad, rp->grad_dev, (size_t)n->P * 8, cudaMemcpyDeviceToHost, sl.st) != cudaSuccess)
             s = STA_ERR_CUDA;
     }
-    if (s == STA_OK) s = sta_query_summary(h, n->sum_dev, 1, st);
-    if (s == STA_OK && cudaMemcpyAsync(sl.sum_host, n->sum_dev, STA_SUM_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+    if (s == STA_OK) s = sta_query_summary(h, rp->sum_dev, 1, st);
+    if (s == STA_OK && cudaMemcpyAsync(sl.sum_host, rp->sum_dev, STA_SUM_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
                                        sl.st) != cudaSuccess)
         s = STA_ERR_CUDA;
     if (s == STA_OK && cudaEventRecord(sl.done, sl.st) != cudaSuccess) s = STA_ERR_CUDA;
     (void)S;
+    return s;
+}
+
+// Merged: the slot's k requests (same netlist, gamma and kind) are placements
+// 0..k-1 of one batched call of M placements; the other lanes repeat
+// placement 0's positions (their results are not read).  Each request's
+// gradient and summary are copied out of its own lane.
+static StaStatus dispatch_merged(StaServer* S, Slot& sl, Net* n) {
+    const int M = S->opt.merge, k = (int)sl.reqs.size();
+    const StaServerRequest& r0 = sl.reqs[0].r;
+    const size_t P = (size_t)n->P;
+    Rep* rp = sl.rep;
+    cudaStream_t cst = sl.st;
+    void* st = sl.st;
+    StaStatus s = STA_OK;
+    for (int b = 0; b < M && s == STA_OK; ++b) {
+        if (P == 0) break;
+        const void* src = b < k ? (const void*)sl.reqs[b].r.xy : (const void*)rp->xy_dev;
+        if (cudaMemcpyAsync(rp->xy_dev + b * P * 2, src, P * 8, b < k ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                            cst) != cudaSuccess)
+            s = STA_ERR_CUDA;
+    }
+    if (s == STA_OK) s = sta_set_positions(rp->h, rp->xy_dev, 1, st);
+    if (s == STA_OK)
+        s = sta_forward(rp->h, STA_FWD_LSE | STA_FWD_RAT | (r0.gradient ? 0u : STA_FWD_RAT_EAGER), r0.gamma, st);
+    if (s == STA_OK && r0.gradient) {
+        for (int b = 0; b < M; ++b) {
+            rp->w_host[2 * b] = b < k ? sl.reqs[b].r.w_tns : 0.f;
+            rp->w_host[2 * b + 1] = b < k ? sl.reqs[b].r.w_wns : 0.f;
+        }
+        s = sta_backward_grad(rp->h, rp->w_host, 0, rp->grad_dev, 1, st);
+        for (int b = 0; b < k && s == STA_OK; ++b)
+            if (sl.reqs[b].r.grad && P &&
+                cudaMemcpyAsync(sl.reqs[b].r.grad, rp->grad_dev + b * P * 2, P * 8, cudaMemcpyDeviceToHost, cst) !=
+                    cudaSuccess)
+                s = STA_ERR_CUDA;
+    }
+    if (s == STA_OK) s = sta_query_summary(rp->h, rp->sum_dev, 1, st);
+    if (s == STA_OK && cudaMemcpyAsync(sl.sum_host, rp->sum_dev, (size_t)k * STA_SUM_COUNT * sizeof(double),
+                                       cudaMemcpyDeviceToHost, cst) != cudaSuccess)
+        s = STA_ERR_CUDA;
+    if (s == STA_OK && cudaEventRecord(sl.done, cst) != cudaSuccess) s = STA_ERR_CUDA;
     return s;
 }
 
@@ -329,25 +430,34 @@ void StaServer::run() {
             if (!s.busy) continue;
             const cudaError_t q = cudaEventQuery(s.done);
             if (q == cudaErrorNotReady) continue;
-            Net* n = nets[s.req.r.netlist];
-            StaServerCompletion c{};
-            c.id = s.req.id;
-            c.netlist = s.req.r.netlist;
-            c.t_submit = s.req.t_arrival;
-            c.t_start = s.t_start;
-            c.t_done = now_s();
-            c.status = q == cudaSuccess ? STA_OK : STA_ERR_CUDA;
-            if (c.status == STA_OK) c.status = sta_synchronize(n->h);  // a bounded wait that expired
-            if (s.req.r.summary) std::memcpy(s.req.r.summary, s.sum_host, STA_SUM_COUNT * sizeof(double));
-            n->busy = false;
-            n->last_use = c.t_done;
+            StaStatus status = q == cudaSuccess ? STA_OK : STA_ERR_CUDA;
+            if (status == STA_OK) status = sta_synchronize(s.rep->h);  // a bounded wait that expired
+            const double t_done = now_s();
+            for (size_t b = 0; b < s.reqs.size(); ++b) {
+                const Req& rq = s.reqs[b];
+                StaServerCompletion c{};
+                c.id = rq.id;
+                c.netlist = rq.r.netlist;
+                c.t_submit = rq.t_arrival;
+                c.t_start = s.t_start;
+                c.t_done = t_done;
+                c.status = status;
+                c.merged = (int32_t)s.reqs.size();
+                if (rq.r.summary)
+                    std::memcpy(rq.r.summary, s.sum_host + b * STA_SUM_COUNT, STA_SUM_COUNT * sizeof(double));
+                done.push_back(c);
+            }
+            s.rep->busy = false;
+            s.rep->last_use = t_done;
+            s.rep = nullptr;
             s.busy = false;
-            done.push_back(c);
             finished = true;
         }
         // admissions: the earliest pending request first; later ones go ahead
         // while it waits for its netlist (busy, or not yet admitted), except in
-        // the sequential loop, which keeps strict arrival order on one slot
+        // the sequential loop, which keeps strict arrival order on one slot.
+        // With merging, the later pending requests of the same netlist, gamma and
+        // kind join it, up to `merge` of them, in arrival order.
         for (size_t i = 0; i < pending.size();) {
             int free_slot = -1;
             for (int k = 0; k < (int)slots.size(); ++k)
@@ -359,7 +469,8 @@ void StaServer::run() {
             Req& rq = pending[i];
             Net* n = nets[rq.r.netlist];
             std::string err;
-            if (n->busy || !admit(this, rq.r.netlist, err)) {
+            Rep* rep = admit(this, rq.r.netlist, err);
+            if (!rep) {
                 if (!err.empty()) {  // can never run
                     StaServerCompletion c{};
                     c.id = rq.id;
@@ -367,6 +478,7 @@ void StaServer::run() {
                     c.t_submit = rq.t_arrival;
                     c.t_start = c.t_done = now_s();
                     c.status = STA_ERR_OOM;
+                    c.merged = 1;
                     done.push_back(c);
                     finished = true;
                     pending.erase(pending.begin() + (long)i);
@@ -377,26 +489,45 @@ void StaServer::run() {
                 continue;
             }
             Slot& sl = slots[free_slot];
-            sl.req = rq;
+            sl.reqs.clear();
+            sl.reqs.push_back(rq);
+            pending.erase(pending.begin() + (long)i);
+            if (opt.merge > 0) {
+                for (size_t j = i; j < pending.size() && (int)sl.reqs.size() < opt.merge;) {
+                    const StaServerRequest& a = sl.reqs[0].r;
+                    const StaServerRequest& b = pending[j].r;
+                    if (b.netlist == a.netlist && b.gradient == a.gradient && b.gamma == a.gamma) {
+                        sl.reqs.push_back(pending[j]);
+                        pending.erase(pending.begin() + (long)j);
+                    } else {
+                        ++j;
+                    }
+                }
+            }
             sl.t_start = now_s();
-            n->busy = true;
+            sl.rep = rep;
+            rep->busy = true;
             sl.busy = true;
-            const StaStatus s = dispatch(this, sl, n);
+            const StaStatus s = opt.merge > 0 ? dispatch_merged(this, sl, n) : dispatch(this, sl, n);
             if (s != STA_OK) {  // report at once, after what was queued has run
                 cudaStreamSynchronize(sl.st);
-                StaServerCompletion c{};
-                c.id = rq.id;
-                c.netlist = rq.r.netlist;
-                c.t_submit = rq.t_arrival;
-                c.t_start = sl.t_start;
-                c.t_done = now_s();
-                c.status = s;
-                done.push_back(c);
+                const double t_done = now_s();
+                for (const Req& r : sl.reqs) {
+                    StaServerCompletion c{};
+                    c.id = r.id;
+                    c.netlist = r.r.netlist;
+                    c.t_submit = r.t_arrival;
+                    c.t_start = sl.t_start;
+                    c.t_done = t_done;
+                    c.status = s;
+                    c.merged = (int32_t)sl.reqs.size();
+                    done.push_back(c);
+                }
                 finished = true;
-                n->busy = false;
+                rep->busy = false;
+                sl.rep = nullptr;
                 sl.busy = false;
             }
-            pending.erase(pending.begin() + (long)i);
         }
         if (finished) cv.notify_all();
         any_busy = false;
@@ -418,7 +549,10 @@ StaStatus sta_server_create(const StaServerOptions* opt, StaServer** out) {
     *out = nullptr;
     StaServerOptions o{};
     if (opt) o = *opt;
-    if (o.slots < 0 || o.slots > 64 || o.budget_bytes < 0) return fail("sta_server_create: slots in [0, 64], budget >= 0");
+    if (o.slots < 0 || o.slots > 64 || o.budget_bytes < 0 || o.merge < 0 || o.merge > 64 || (o.merge && o.sequential) ||
+        o.replicas < 0 || o.replicas > 64 || (o.replicas > 1 && (o.sequential || o.merge)))
+        return fail("sta_server_create: slots in [0, 64], budget >= 0, merge and replicas in [0, 64], "
+                    "neither with sequential, not both");
     if (o.slots == 0) o.slots = 4;
     if (o.sequential) o.slots = 1;
     if (o.budget_bytes == 0) o.budget_bytes = 150ll << 30;
@@ -437,7 +571,7 @@ StaStatus sta_server_create(const StaServerOptions* opt, StaServer** out) {
     for (Slot& s : S->slots) {
         if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMallocHost(&s.sum_host, STA_SUM_COUNT * sizeof(double)) != cudaSuccess) {
+            cudaMallocHost(&s.sum_host, (size_t)std::max(o.merge, 1) * STA_SUM_COUNT * sizeof(double)) != cudaSuccess) {
             delete S;
             return fail("stream / event / pinned allocation failed", STA_ERR_CUDA);
         }
@@ -472,10 +606,14 @@ StaStatus sta_server_add_netlist(StaServer* S, const StaNetlistDesc* nl, const S
     S->nets.push_back(n);
     *id = (int32_t)S->nets.size() - 1;
     if (preload) {
+        // the first copy, or an error; then the further copies (replicas) while
+        // the budget allows, so that none is built while requests wait
         std::string err;
         if (!admit(S, *id, err)) {
             if (err.empty()) err = "over the memory budget";
             return fail("sta_server_add_netlist: preload: " + err, STA_ERR_OOM);
+        }
+        while ((int)n->reps.size() < max_copies(S) && create_rep(S, n, err)) {
         }
     }
     return STA_OK;
@@ -514,7 +652,7 @@ StaStatus sta_server_netlist_bytes(StaServer* S, int32_t id, int64_t* bytes) {
     std::lock_guard<std::mutex> lk(S->mu);
     if (id < 0 || id >= (int32_t)S->nets.size()) return fail("sta_server_netlist_bytes: unknown netlist");
     const Net* n = S->nets[id];
-    *bytes = (int64_t)(n->bytes ? n->bytes : estimate_bytes(n->host));
+    *bytes = (int64_t)(n->rep_bytes ? n->rep_bytes : estimate_bytes(n->host, S->opt.merge));
     return STA_OK;
 }
 
@@ -522,7 +660,7 @@ StaStatus sta_server_stats(StaServer* S, int64_t* out4) {
     if (!S || !out4) return fail("sta_server_stats: null argument");
     std::lock_guard<std::mutex> lk(S->mu);
     int64_t res = 0;
-    for (Net* n : S->nets) res += n->h ? 1 : 0;
+    for (Net* n : S->nets) res += n->reps.empty() ? 0 : 1;
     out4[0] = res;
     out4[1] = (int64_t)S->resident_bytes;
     out4[2] = S->admissions;

@@ -5,7 +5,7 @@ onto CUDA-stream slots as they free up, keeps netlists resident under a device
 memory budget and reports completions with timestamps.  This module only
 marshals arguments and keeps request buffers alive until their completion.
 
-    srv = StaServer(slots=4)
+    srv = StaServer(slots=4, replicas=2)              # same-netlist requests concurrent on 2 copies
     k = srv.add_netlist(netlist, library)             # copied, made resident
     rid = srv.submit(k, xy_pinned, gradient=True, grad_out=g_pinned)
     done = srv.poll(wait_ms=100)                      # [{"id", "status", "t_submit", ...}]
@@ -31,9 +31,10 @@ def _ptr(a):
 class StaServer:
     """One server on the current CUDA device (sta_server_create)."""
 
-    def __init__(self, slots: int = 4, sequential: bool = False, budget_bytes: int = 0):
+    def __init__(self, slots: int = 4, sequential: bool = False, budget_bytes: int = 0, merge: int = 0,
+                 replicas: int = 0):
         opts = _sta.StaServerOptions(slots=int(slots), sequential=1 if sequential else 0,
-                                     budget_bytes=int(budget_bytes))
+                                     budget_bytes=int(budget_bytes), merge=int(merge), replicas=int(replicas))
         h = ctypes.c_void_p()
         _sta._check(_sta._lib.sta_server_create(ctypes.byref(opts), ctypes.byref(h)), "sta_server_create")
         self.h = h.value
@@ -77,7 +78,7 @@ class StaServer:
             xy, g, s = self._keep.pop(int(c.id), (None, None, None))
             out.append({"id": int(c.id), "status": int(c.status), "netlist": int(c.netlist),
                         "t_submit": c.t_submit, "t_start": c.t_start, "t_done": c.t_done, "summary": s,
-                        "grad": g})
+                        "grad": g, "merged": int(c.merged)})
         return out
 
     def netlist_bytes(self, netlist: int) -> int:

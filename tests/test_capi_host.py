@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol(sta):
     for name in sorted(declared):
         assert hasattr(lib, name), f"libsta.so does not export {name}"
     assert set(sta._sta.EXPORTS) == declared
-    assert sta.sta_abi_version() == 3
+    assert sta.sta_abi_version() == 4
 
 
 @pytest.mark.parametrize("make", [lambda: netgen.tiny_design(0), lambda: netgen.tiny_design(5),

@@ -95,6 +95,71 @@ def test_mixed_requests_equal_alone_and_oracle(designs):
             assert np.abs(res_mix[i]["grad"].numpy() - ora["grad"]).max() <= tp.GRAD_RTOL * gmax
 
 
+def _check_oracle(reqs, res, designs, idx):
+    for i in idx:
+        r, w = reqs[i], designs[reqs[i]["net"]]
+        ora = oracle.sta(w.netlist, w.library, r["xy"].numpy(), r["gamma"], r["w"][0], r["w"][1])
+        s = dict(zip(["wns_early", "tns_early", "wns_late", "tns_late", "tns_gamma", "wns_gamma",
+                      "late_violations", "num_endpoints"], res[i]["summary"].tolist()))
+        scale = float(np.abs(ora["at"][:, 2:][np.isfinite(ora["at"][:, 2:])]).max())
+        for k in ("wns_late", "wns_gamma"):
+            assert abs(s[k] - ora["summary"][k]) <= tp.AT_RTOL * scale, (i, k)
+        for k in ("tns_late", "tns_gamma"):
+            assert abs(s[k] - ora["summary"][k]) <= tp.AT_RTOL * max(abs(ora["summary"][k]), scale), (i, k)
+        assert s["late_violations"] == ora["summary"]["late_violations"]
+        if r["gradient"]:
+            gmax = np.abs(ora["grad"]).max()
+            assert np.abs(res[i]["grad"].numpy() - ora["grad"]).max() <= tp.GRAD_RTOL * gmax, i
+
+
+def test_merged_requests_equal_alone_and_oracle(designs):
+    # merging server: pending requests of one netlist (same gamma and kind) run as
+    # the placements of one batched call; submitted all at once most of them merge.
+    # The same requests one at a time on a merging server run alone (a batch with
+    # one real placement): results must be bit-identical, and match the oracle.
+    from paper_2603_28381_gb300.serving import StaServer
+    reqs = _requests(designs, 40, seed=7)
+    mrg = StaServer(slots=2, merge=8)
+    ids = [mrg.add_netlist(w.netlist, w.library) for w in designs]
+    res_m = _run(mrg, ids, reqs)
+    mrg.close()
+    alone = StaServer(slots=2, merge=8)
+    ids2 = [alone.add_netlist(w.netlist, w.library) for w in designs]
+    res_a = _run(alone, ids2, reqs, one_at_a_time=True)
+    alone.close()
+    assert max(c["merged"] for c in res_m) > 1, "no requests were merged"
+    assert sum(c["merged"] > 1 for c in res_m) >= len(reqs) // 2
+    assert all(c["merged"] == 1 for c in res_a)
+    for a, b in zip(res_m, res_a):
+        _same(a, b)
+    merged_grad = [i for i, c in enumerate(res_m) if c["merged"] > 1 and reqs[i]["gradient"]]
+    merged_fwd = [i for i, c in enumerate(res_m) if c["merged"] > 1 and not reqs[i]["gradient"]]
+    _check_oracle(reqs, res_m, designs, merged_grad[:2] + merged_fwd[:2])
+
+
+def test_replicas_run_one_netlist_concurrently_results_unchanged(designs):
+    # replicas: pending requests of one netlist run concurrently on separate
+    # resident copies; results must be bit-identical to the same requests alone
+    from paper_2603_28381_gb300.serving import StaServer
+    reqs = _requests(designs, 30, seed=9)
+    rep = StaServer(slots=4, replicas=3)
+    ids = [rep.add_netlist(w.netlist, w.library) for w in designs]
+    res_r = _run(rep, ids, reqs)
+    st = rep.stats()
+    rep.close()
+    alone = StaServer(sequential=True)
+    ids2 = [alone.add_netlist(w.netlist, w.library) for w in designs]
+    res_a = _run(alone, ids2, reqs, one_at_a_time=True)
+    alone.close()
+    assert st["admissions"] > len(designs)  # copies beyond the first were made
+    # two requests of one netlist in flight at the same time
+    overlap = any(a["netlist"] == b["netlist"] and a["t_start"] < b["t_done"] and b["t_start"] < a["t_done"]
+                  for i, a in enumerate(res_r) for b in res_r[i + 1:])
+    assert overlap
+    for a, b in zip(res_r, res_a):
+        _same(a, b)
+
+
 def test_budget_forces_evictions_results_unchanged(designs):
     from paper_2603_28381_gb300.serving import StaServer
     reqs = _requests(designs, 16, seed=4)
