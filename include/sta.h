@@ -114,7 +114,8 @@ typedef struct {
                             their pins total at most tile_pins (0 = default 4) */
     int32_t chunk;       /* STA_SCHED_BATCH task shape: nets of more than `chunk` sinks are
                             split into tasks of `chunk` sinks (0 = default 16) */
-    int32_t batch_sweep; /* STA_SCHED_BATCH: STA_BATCH_LEVELS (default) or STA_BATCH_DATAFLOW */
+    int32_t batch_sweep; /* STA_SCHED_BATCH: STA_BATCH_LEVELS (default), STA_BATCH_DATAFLOW or
+                            STA_BATCH_LANES */
     int32_t grid_blocks; /* dataflow sweeps: blocks of the persistent kernels (0 = every block
                             that fits on the device; fewer leave room for other work) */
 } StaOptions;
@@ -144,9 +145,17 @@ typedef struct {
  *             of a level run without any waiting.
  *   DATAFLOW  one persistent launch per sweep with per-task dependency
  *             counters, as in STA_SCHED_DATAFLOW.
- * Both give bit-identical results. */
+ * Both give bit-identical results.
+ *   LANES     the placements as independent lanes of the single-placement
+ *             dataflow sweeps (STA_SCHED_DATAFLOW): each placement has its own
+ *             state, laid out as for one placement, and one persistent launch
+ *             per sweep takes task t of every placement in turn.  A placement's
+ *             results are bit-identical to the same placement in a
+ *             single-placement handle.  tile_pins and chunk do not apply;
+ *             sta_autotune is not available (STA_ERR_STATE). */
 #define STA_BATCH_LEVELS 0
 #define STA_BATCH_DATAFLOW 1
+#define STA_BATCH_LANES 2
 
 typedef struct StaHandle StaHandle;
 
@@ -372,6 +381,15 @@ StaStatus sta_endpoint_summary_noalloc(const float *at, const float *ats, int32_
                                        const int32_t *end_clk, int32_t num_end, float gamma,
                                        float *ep_slack, double *summary, void *stream);
 
+/* Handles with STA_BATCH_LANES: run only placements [0, lanes) (1 <= lanes <=
+ * num_placements) from the next sta_set_positions on, until changed.  That call
+ * and the following ones then take and give [lanes][...] arrays (positions
+ * [lanes][num_pins][2], weights [lanes][2], gradients, summaries and queries
+ * likewise) and the sweeps run those lanes only, so a call costs what its
+ * placements need.  Results are those of each placement alone.
+ * STA_ERR_STATE on other handles. */
+StaStatus sta_set_active(StaHandle *h, int32_t lanes);
+
 /* Release every resource of the handle (NULL is a no-op). */
 void sta_destroy(StaHandle *h);
 
@@ -416,10 +434,10 @@ typedef struct {
     int64_t budget_bytes; /* device bytes for resident netlists (0 = 150 GiB) */
     int32_t merge;        /* 0: one request per launch.  M in [1, 64]: pending requests of one
                              netlist with the same gamma and kind (forward / gradient) run
-                             together, up to M at a time, as the placements of one batched
-                             call (STA_SCHED_BATCH with M placements).  Every request of the
-                             netlist then takes that path, alone too, so a request's results
-                             are bit-identical alone and merged.  Not with sequential. */
+                             together, up to M at a time, as the lanes of one call of a lanes
+                             handle (STA_BATCH_LANES with M placements, sta_set_active to
+                             the requests present).  A lane's results are bit-identical to
+                             the same request alone.  Not with sequential. */
     int32_t replicas;     /* resident copies of a netlist, at most (0 = 1): with R > 1, pending
                              requests of one netlist run concurrently on up to R copies (each
                              its own handle; copies beyond the first are made only while the

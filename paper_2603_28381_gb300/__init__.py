@@ -42,7 +42,9 @@ class StaEngine:
     schedule "batch" analyses ``num_placements`` position sets B at once: every
     per-pin array gains a leading placement dimension ([B, P, 2] positions and
     gradients, [B, E, 2] endpoint slacks, one summary per placement) and the
-    loss weights are per placement ([B, 2])."""
+    loss weights are per placement ([B, 2]).  batch_sweep "lanes" runs the B
+    placements as independent lanes of the single-placement sweeps (results
+    bit-identical to one placement per handle)."""
 
     def __init__(self, netlist, library, use_graphs: bool = True, profile: bool = False,
                  schedule: str = "dataflow", num_placements: int = 1, tile_pins: int = 0,
@@ -61,7 +63,8 @@ class StaEngine:
         self.B = int(num_placements) if self.batched else 1
         self.h = _sta.sta_create(netlist, library, use_graphs, profile, sched,
                                  self.B if self.batched else 0, tile_pins, chunk,
-                                 {"levels": _sta.BATCH_LEVELS, "dataflow": _sta.BATCH_DATAFLOW}[batch_sweep],
+                                 {"levels": _sta.BATCH_LEVELS, "dataflow": _sta.BATCH_DATAFLOW,
+                                  "lanes": _sta.BATCH_LANES}[batch_sweep],
                                  grid_blocks)
         self.sizes = _sta.sta_query_sizes(self.h)
         self.sizes["nets_desc"] = int(netlist.num_nets)
@@ -80,6 +83,12 @@ class StaEngine:
             pass
 
     # -- calls --
+    def set_active(self, lanes: int) -> None:
+        """batch_sweep "lanes": run placements [0, lanes) from the next
+        set_positions on (sta_set_active); arrays then have `lanes` rows."""
+        _sta.sta_set_active(self.h, lanes)
+        self.B = int(lanes)
+
     def profile(self, with_times: bool = True):
         """(ms by kernel kind, launches by kind) of the latest step (sta_query_profile)."""
         return _sta.sta_query_profile(self.h, with_times)

@@ -52,6 +52,7 @@ SCHED_LEVELS = 1
 SCHED_BATCH = 2
 BATCH_LEVELS = 0
 BATCH_DATAFLOW = 1
+BATCH_LANES = 2
 
 
 class StaServerOptions(ctypes.Structure):
@@ -105,6 +106,7 @@ def _load() -> ctypes.CDLL:
         "sta_query_profile": ([H, _p, _p], ctypes.c_int),
         "sta_endpoint_summary_noalloc": ([_p, _p, _i32, _p, _p, _p, _i32, ctypes.c_float, _p, _p, _p],
                                          ctypes.c_int),
+        "sta_set_active": ([H, _i32], ctypes.c_int),
         "sta_destroy": ([H], None),
         "sta_server_create": ([ctypes.POINTER(StaServerOptions), ctypes.POINTER(H)], ctypes.c_int),
         "sta_server_add_netlist": ([H, ctypes.POINTER(StaNetlistDesc), ctypes.POINTER(StaLibrary), _i32,
@@ -136,7 +138,7 @@ EXPORTS = ("sta_create", "sta_set_positions", "sta_forward", "sta_backward_grad"
            "sta_server_add_netlist", "sta_server_submit", "sta_server_poll", "sta_server_stats",
            "sta_server_destroy", "sta_server_clock", "sta_server_netlist_bytes", "sta_query_net_rc",
            "sta_ablation_net_rc", "sta_plan_tasks", "sta_query_slack", "sta_measure_latency",
-           "sta_last_error", "sta_abi_version", "sta_endpoint_summary_noalloc")
+           "sta_last_error", "sta_abi_version", "sta_endpoint_summary_noalloc", "sta_set_active")
 
 
 def _check(status: int, where: str) -> None:
@@ -226,6 +228,10 @@ def sta_create(nl, lib, use_graphs: bool = True, profile: bool = False,
     _check(_lib.sta_create(ctypes.byref(d), ctypes.byref(l), ctypes.byref(opts), ctypes.byref(h)),
            "sta_create")
     return h.value
+
+
+def sta_set_active(h: int, lanes: int) -> None:
+    _check(_lib.sta_set_active(h, int(lanes)), "sta_set_active")
 
 
 def sta_destroy(h: int) -> None:

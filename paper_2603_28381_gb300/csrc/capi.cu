@@ -59,6 +59,10 @@ struct StaHandle {
     // batched schedule: B placements, lane per placement
     int B = 1;
     int bsweep = STA_BATCH_LEVELS;
+    // independent placements of the single-placement schedule (StaOptions
+    // batch_sweep = STA_BATCH_LANES): lanes, each with its own state slab
+    int nl = 1;
+    int active = 1, active_next = 1;  // lanes the current / the next positions' calls run
     BatchState bs{};
     const int32_t* pin_int = nullptr;  // [P] internal index of each original pin
     const int32_t* big_dev = nullptr;  // [nbig] nets whose loads the prologue computes
@@ -231,7 +235,9 @@ void enqueue_backward_dataflow(StaHandle* h, int mode, float gamma, cudaStream_t
     const Layout& L = h->lay;
     StaHandle::Prof* pr = (mode & 2) ? &h->prof_adj : &h->prof_rat;
     pr->next = 0;
-    cudaMemsetAsync((mode & 2) ? h->d.acnt : h->d.rcnt, 0, sizeof(int32_t) * (L.TB ? L.TB : 1), st);
+    // every lane's counters (lane l's sit l * lane_bytes after lane 0's)
+    cudaMemset2DAsync((mode & 2) ? h->d.acnt : h->d.rcnt, h->s.lane_bytes, 0, sizeof(int32_t) * (L.TB ? L.TB : 1),
+                      h->nl, st);  // (every lane: the count a call runs is on the device)
     cudaMemsetAsync(h->d.heads + ((mode & 2) ? 2 : 1), 0, sizeof(int32_t), st);
     if (mode != 3) {  // the fused sweep's words were reset by the forward before it
         ProfScope ps(h, pr, STA_PROF_RESET, st);
@@ -694,7 +700,16 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
             opts->schedule != STA_SCHED_BATCH)
             return fail(set_err(STA_ERR_INVALID_ARG, "StaOptions.schedule must be DATAFLOW, LEVELS or BATCH"));
         h->schedule = opts->schedule;
-        if (h->batch()) {
+        if (h->batch() && opts->batch_sweep == STA_BATCH_LANES) {
+            // B placements as lanes of the single-placement dataflow sweeps
+            if (opts->num_placements < 0 || opts->num_placements > 1024)
+                return fail(set_err(STA_ERR_INVALID_ARG, "StaOptions: num_placements in [0, 1024] for LANES"));
+            h->schedule = STA_SCHED_DATAFLOW;
+            h->B = h->nl = opts->num_placements > 0 ? opts->num_placements : 1;
+            h->bsweep = STA_BATCH_LANES;
+            if ((long long)h->lay.TF * h->nl >= (1ll << 31) || (long long)h->lay.TB * h->nl >= (1ll << 31))
+                return fail(set_err(STA_ERR_INVALID_ARG, "num_placements too large for this netlist"));
+        } else if (h->batch()) {
             if (opts->num_placements < 0 || opts->num_placements > (1 << 16) || opts->tile_pins < 0 ||
                 opts->chunk < 0)
                 return fail(set_err(STA_ERR_INVALID_ARG, "StaOptions: num_placements in [0, 65536], tile_pins, "
@@ -793,57 +808,88 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         STEP(h->upload(d.b_out_ptr, L.b_out_ptr));
         STEP(h->upload(d.b_out, L.b_out));
     }
-    const size_t G = bat ? (size_t)(h->B + 31) / 32 * (32 / kPlacePerWarp) : 1;
-    STEP(h->alloc(d.rcnt, L.TB * G));
-    STEP(h->alloc(d.acnt, L.TB * G));
     STEP(h->alloc(d.heads, 4));
-    STEP(h->alloc(d.rpart, bat ? 1 : (size_t)L.npart * kPartFloats));
-    STEP(h->alloc(d.apart, bat ? 1 : (size_t)L.npart * kPartFloats));
-    STEP(h->alloc(d.net_gload, bat ? 1 : L.N));
     STEP(h->alloc(d.abort_word, 2));
     d.TF = L.TF;
     d.TB = L.TB;
     d.npart = L.npart;
     if (bat) {
+        const size_t G = (size_t)(h->B + 31) / 32 * (32 / kPlacePerWarp);
+        STEP(h->alloc(d.rcnt, L.TB * G));
+        STEP(h->alloc(d.acnt, L.TB * G));
+        STEP(h->alloc(d.rpart, 1));
+        STEP(h->alloc(d.apart, 1));
+        STEP(h->alloc(d.net_gload, 1));
         STEP(init_batch(h));
     } else {
-        STEP(h->alloc(s.xy, P));
-        STEP(h->alloc(s.load, L.N));
-        STEP(h->alloc(s.wdi, P));
-        STEP(h->alloc(s.at, 4 * P));
-        STEP(h->alloc(s.slew, 4 * P));
-        STEP(h->alloc(s.ats, 2 * P));
-        STEP(h->alloc(s.adel, 4 * (size_t)L.A));
-        STEP(h->alloc(s.rat, 4 * P));
-        STEP(h->alloc(s.g_ats, 2 * P));
-        STEP(h->alloc(s.g_slew, 2 * P));
-        STEP(h->alloc(s.grad, P));
-        STEP(h->alloc(s.ep_slack, L.E));
-        STEP(h->alloc(s.red, (size_t)kEpBlocks * 8));
-        STEP(h->alloc(s.summary, STA_SUM_COUNT));
-        STEP(h->alloc(s.params, 4));
-        STEP(h->alloc(s.rc_part, (size_t)std::max(L.rc_slots, 1)));
-        STEP(h->alloc(s.rc_count, (size_t)std::max(L.rc_slots, 1)));
-        STEP(h->alloc(s.ep_count, 1));
-        s.cap_seed = nullptr;
-        if (!L.ep_clk.empty()) {
-            STEP(h->alloc(s.cap_seed, P));
-            if (cudaMemset(s.cap_seed, 0, P * 4) != cudaSuccess) return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
+        // The per-placement state: one slab per lane (a single placement: one),
+        // every array at the same offset in each slab, so that lane l's state is
+        // lane 0's shifted by l * lane_bytes (lane_state, lane_df).
+        struct Carve {
+            size_t bytes = 0;
+            size_t add(size_t n, size_t elem) {
+                const size_t off = (bytes + 255) / 256 * 256;
+                bytes = off + std::max<size_t>(n, 1) * elem;
+                return off;
+            }
+        } cv;
+        const size_t NS = (size_t)std::max(L.rc_slots, 1), NP = (size_t)L.npart * kPartFloats;
+        const size_t o_xy = cv.add(P, 8), o_load = cv.add(L.N, 4), o_wdi = cv.add(P, 8), o_at = cv.add(4 * P, 4),
+                     o_slew = cv.add(4 * P, 4), o_ats = cv.add(2 * P, 4), o_adel = cv.add(4 * (size_t)L.A, 4),
+                     o_rat = cv.add(4 * P, 4), o_gats = cv.add(2 * P, 4), o_gslew = cv.add(2 * P, 4),
+                     o_grad = cv.add(P, 8), o_eps = cv.add(L.E, 8), o_red = cv.add((size_t)kEpBlocks * 8, 8),
+                     o_sum = cv.add(STA_SUM_COUNT, 8), o_par = cv.add(4, 4), o_rcp = cv.add(NS, 4),
+                     o_rcc = cv.add(NS, 4), o_epc = cv.add(1, 4), o_cap = L.ep_clk.empty() ? 0 : cv.add(P, 4),
+                     o_rcnt = cv.add(L.TB, 4), o_acnt = cv.add(L.TB, 4), o_rpart = cv.add(NP, 4),
+                     o_apart = cv.add(NP, 4), o_gload = cv.add(L.N, 4), o_brec = cv.add(8 * (size_t)L.N, 16);
+        const size_t lb = (cv.bytes + 255) / 256 * 256;
+        char* slab = nullptr;
+        STEP(h->alloc(slab, lb * (size_t)h->nl));
+        if (cudaMemset(slab, 0, lb * (size_t)h->nl) != cudaSuccess) return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
+        s.xy = reinterpret_cast<float2*>(slab + o_xy);
+        s.load = reinterpret_cast<float*>(slab + o_load);
+        s.wdi = reinterpret_cast<float2*>(slab + o_wdi);
+        s.at = reinterpret_cast<float*>(slab + o_at);
+        s.slew = reinterpret_cast<float*>(slab + o_slew);
+        s.ats = reinterpret_cast<float*>(slab + o_ats);
+        s.adel = reinterpret_cast<float*>(slab + o_adel);
+        s.rat = reinterpret_cast<float*>(slab + o_rat);
+        s.g_ats = reinterpret_cast<float*>(slab + o_gats);
+        s.g_slew = reinterpret_cast<float*>(slab + o_gslew);
+        s.grad = reinterpret_cast<float2*>(slab + o_grad);
+        s.ep_slack = reinterpret_cast<float2*>(slab + o_eps);
+        s.red = reinterpret_cast<double*>(slab + o_red);
+        s.summary = reinterpret_cast<double*>(slab + o_sum);
+        s.params = reinterpret_cast<float*>(slab + o_par);
+        s.rc_part = reinterpret_cast<float*>(slab + o_rcp);
+        s.rc_count = reinterpret_cast<int32_t*>(slab + o_rcc);
+        s.ep_count = reinterpret_cast<int32_t*>(slab + o_epc);
+        s.cap_seed = L.ep_clk.empty() ? nullptr : reinterpret_cast<float*>(slab + o_cap);
+        d.rcnt = reinterpret_cast<int32_t*>(slab + o_rcnt);
+        d.acnt = reinterpret_cast<int32_t*>(slab + o_acnt);
+        d.rpart = reinterpret_cast<float*>(slab + o_rpart);
+        d.apart = reinterpret_cast<float*>(slab + o_apart);
+        d.net_gload = reinterpret_cast<float*>(slab + o_gload);
+        d.brec = reinterpret_cast<float4*>(slab + o_brec);
+        s.lane_bytes = lb;
+        s.nl = h->nl;
+        s.active = nullptr;
+        h->active = h->active_next = h->nl;
+        if (h->nl > 1) {
+            STEP(h->alloc(s.active, 1));
+            if (cudaMemcpy(s.active, &h->nl, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(set_err(STA_ERR_CUDA, "initial state upload failed"));
         }
-        auto zero = [&](void* p, size_t bytes) { return cudaMemset(p, 0, bytes); };
-        if (zero(s.xy, P * 8) || zero(s.load, L.N * 4) || zero(s.wdi, P * 8) || zero(s.ats, P * 8) ||
-            zero(s.adel, (size_t)L.A * 16) || zero(s.g_ats, P * 8) || zero(s.g_slew, P * 8) || zero(s.grad, P * 8) ||
-            zero(s.summary, STA_SUM_COUNT * 8) || zero(s.params, 16) || zero(s.red, (size_t)kEpBlocks * 64) ||
-            zero(d.net_gload, (size_t)L.N * 4) || zero(s.rc_count, (size_t)std::max(L.rc_slots, 1) * 4) ||
-            zero(s.ep_count, 4))
-            return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
-        // constant state: asserted AT/slew (and LSE AT = late AT), required-time seeds
-        if (cudaMemcpy(s.at, L.at0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(s.slew, L.slew0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(s.rat, L.rat0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess)
-            return fail(set_err(STA_ERR_CUDA, "initial state upload failed"));
-        launch_init_ats(s, L.P, 0);
-        STEP(h->alloc(d.brec, 8 * (size_t)std::max(L.N, 1)));
+        // constant state of every lane: asserted AT/slew (and LSE AT = late AT),
+        // required-time seeds
+        for (int l = 0; l < h->nl; ++l) {
+            const DevState sl = lane_state(s, l);
+            if (cudaMemcpy(sl.at, L.at0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(sl.slew, L.slew0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(sl.rat, L.rat0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(set_err(STA_ERR_CUDA, "initial state upload failed"));
+            launch_init_ats(sl, L.P, 0);
+        }
     }
     if (cudaMemset(d.abort_word, 0, 8) != cudaSuccess || cudaMemset(d.heads, 0, 16) != cudaSuccess)
         return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
@@ -861,8 +907,8 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         return fail(set_err(STA_ERR_CUDA, "stream/event creation failed"));
     {   // dataflow grids: every block that fits (a required-time sweep flushed for a
         // query and an adjoint sweep on another stream then run one after the other)
-        const int fmax = bat ? batch_max_blocks(1) : dataflow_max_blocks(1);
-        const int bmax = bat ? batch_max_blocks(0) : dataflow_max_blocks(0);
+        const int fmax = bat ? batch_max_blocks(1) : dataflow_max_blocks(1, h->nl > 1);
+        const int bmax = bat ? batch_max_blocks(0) : dataflow_max_blocks(0, h->nl > 1);
         h->grid_fwd = fmax > 0 ? fmax : 1;
         h->grid_bwd = bmax > 0 ? bmax : 1;
         if (opts && opts->grid_blocks > 0) {
@@ -907,7 +953,8 @@ StaStatus sta_set_positions(StaHandle* h, const float* xy, int on_device, void* 
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_bwd, 0));
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
     const float2* src = reinterpret_cast<const float2*>(xy);
-    const size_t bytes = (size_t)h->lay.P * 8 * (h->batch() ? h->B : 1);
+    if (!h->batch()) h->active = h->active_next;  // lanes: the placements of this and the following calls
+    const size_t bytes = (size_t)h->lay.P * 8 * (h->batch() ? h->B : h->active);
     if (!on_device) {
         StaStatus s2 = h->staging(bytes);
         if (s2 != STA_OK) return s2;
@@ -918,7 +965,7 @@ StaStatus sta_set_positions(StaHandle* h, const float* xy, int on_device, void* 
         h->prof_pos.next = 0;
         ProfScope ps(h, &h->prof_pos, STA_PROF_POSITIONS, st);
         if (h->batch()) launch_batch_xy_in(h->bs, h->pin_int, h->lay.P, src, st);
-        else launch_gather_xy(h->g, h->s, src, st);
+        else launch_gather_xy(h->g, h->s, src, h->active, st);
     }
     StaStatus s3 = check_launch();
     if (s3 != STA_OK) return s3;
@@ -995,6 +1042,9 @@ StaStatus sta_backward_grad(StaHandle* h, const float* w, int w_on_device, float
     if (h->batch()) {  // one weight pair per placement
         CUDA_TRY(cudaMemcpyAsync(h->bs.params, w, sizeof(float) * 2 * h->B,
                                  w_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    } else if (h->nl > 1) {  // lanes: pair l into lane l's parameters
+        CUDA_TRY(cudaMemcpy2DAsync(h->s.params, h->s.lane_bytes, w, 2 * sizeof(float), 2 * sizeof(float), h->active,
+                                   w_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     } else {
         launch_set_weights(h->s, w_on_device ? w : nullptr, w_on_device ? 0.f : w[0], w_on_device ? 0.f : w[1], st);
     }
@@ -1026,14 +1076,23 @@ StaStatus sta_backward_grad(StaHandle* h, const float* w, int w_on_device, float
         if (s3 != STA_OK) return s3;
         if (!on_device && bytes) CUDA_TRY(cudaMemcpyAsync(grad_xy, dst, bytes, cudaMemcpyDeviceToHost, st));
     } else {
+        // lane l's gradient (caller's pin order) to [l][P][2]
         const size_t bytes = (size_t)h->lay.P * 8;
         if (bytes) {
-            CUDA_TRY(cudaMemcpyAsync(grad_xy, h->s.grad, bytes,
-                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaMemcpy2DAsync(grad_xy, bytes, h->s.grad, h->s.lane_bytes, bytes, h->active,
+                                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
         }
     }
     CUDA_TRY(cudaEventRecord(h->ev_bwd, st));
     return on_device ? STA_OK : sync_checked(h, st);
+}
+
+StaStatus sta_set_active(StaHandle* h, int32_t lanes) {
+    if (!h) return set_err(STA_ERR_INVALID_ARG, "null handle");
+    if (h->nl <= 1) return set_err(STA_ERR_STATE, "sta_set_active: handles with STA_BATCH_LANES only");
+    if (lanes < 1 || lanes > h->nl) return set_err(STA_ERR_INVALID_ARG, "sta_set_active: lanes in [1, num_placements]");
+    h->active_next = lanes;
+    return STA_OK;
 }
 
 StaStatus sta_stream_wait(StaHandle* h, void* stream) {
@@ -1198,16 +1257,20 @@ StaStatus sta_query_summary(StaHandle* h, double* out, int on_device, void* stre
     if (!h->have_fwd) return set_err(STA_ERR_STATE, "no forward pass yet");
     cudaStream_t st = as_stream(stream);
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
-    CUDA_TRY(cudaMemcpyAsync(out, h->batch() ? h->bs.summary : h->s.summary,
-                             STA_SUM_COUNT * sizeof(double) * (h->batch() ? h->B : 1),
-                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (h->batch()) {
+        CUDA_TRY(cudaMemcpyAsync(out, h->bs.summary, STA_SUM_COUNT * sizeof(double) * h->B, kind, st));
+    } else {  // lane l's summary to out[l]
+        CUDA_TRY(cudaMemcpy2DAsync(out, STA_SUM_COUNT * sizeof(double), h->s.summary, h->s.lane_bytes,
+                                   STA_SUM_COUNT * sizeof(double), h->active, kind, st));
+    }
     return on_device ? STA_OK : sync_checked(h, st);
 }
 
 namespace {
 
 StaStatus deliver(StaHandle* h, const float* internal, int k, float* out, int on_device, cudaStream_t st) {
-    const size_t bytes = (size_t)h->lay.P * k * sizeof(float) * (h->batch() ? h->B : 1);
+    const size_t bytes = (size_t)h->lay.P * k * sizeof(float) * (h->batch() ? h->B : h->active);
     if (!bytes) return STA_OK;
     float* dst = out;
     if (!on_device) {
@@ -1215,8 +1278,13 @@ StaStatus deliver(StaHandle* h, const float* internal, int k, float* out, int on
         if (s2 != STA_OK) return s2;
         dst = static_cast<float*>(h->stage);
     }
-    if (h->batch()) launch_batch_out(h->bs, h->pin_int, h->lay.P, internal, k, dst, st);
-    else launch_scatter(h->g, internal, dst, k, h->lay.P, st);
+    if (h->batch()) {
+        launch_batch_out(h->bs, h->pin_int, h->lay.P, internal, k, dst, st);
+    } else {  // lane l (internal points at lane 0's array) to out[l]
+        for (int l = 0; l < h->active; ++l)
+            launch_scatter(h->g, lane_ptr(internal, (size_t)l * h->s.lane_bytes), dst + (size_t)l * h->lay.P * k, k,
+                           h->lay.P, st);
+    }
     StaStatus s3 = check_launch();
     if (s3 != STA_OK) return s3;
     if (!on_device) {
@@ -1261,14 +1329,15 @@ StaStatus sta_query_pins(StaHandle* h, float* at, float* slew, float* rat, float
             if ((s2 = deliver(h, h->qscratch, 2, slack, on_device, st)) != STA_OK) return s2;
         }
     } else if (slack) {
-        const size_t bytes = (size_t)h->lay.P * 8;
+        const size_t bytes = (size_t)h->lay.P * 8 * h->active;
         if (bytes) {
             float* dst = slack;
             if (!on_device) {
                 if ((s2 = h->staging(bytes)) != STA_OK) return s2;
                 dst = static_cast<float*>(h->stage);
             }
-            launch_pin_slack(h->g, h->s, dst, st);
+            for (int l = 0; l < h->active; ++l)
+                launch_pin_slack(h->g, lane_state(h->s, l), dst + (size_t)l * h->lay.P * 2, st);
             if ((s2 = check_launch()) != STA_OK) return s2;
             if (!on_device) {
                 CUDA_TRY(cudaMemcpyAsync(slack, dst, bytes, cudaMemcpyDeviceToHost, st));
@@ -1299,9 +1368,9 @@ StaStatus sta_query_endpoints(StaHandle* h, float* slack, int on_device, void* s
             CUDA_TRY(cudaMemcpyAsync(slack, dst, bytes, cudaMemcpyDeviceToHost, st));
             return sync_checked(h, st);
         }
-    } else if (h->lay.E) {
-        CUDA_TRY(cudaMemcpyAsync(slack, h->s.ep_slack, (size_t)h->lay.E * 8,
-                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    } else if (h->lay.E) {  // lane l's endpoint slacks to slack[l]
+        CUDA_TRY(cudaMemcpy2DAsync(slack, (size_t)h->lay.E * 8, h->s.ep_slack, h->s.lane_bytes, (size_t)h->lay.E * 8,
+                                   h->active, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
         if (!on_device) return sync_checked(h, st);
     }
     return STA_OK;
@@ -1411,7 +1480,8 @@ StaStatus sta_plan_tasks(const StaNetlistDesc* nl, const StaLibrary* lib, int32_
 
 StaStatus sta_query_slack(StaHandle* h, float* wns_tns, float* pin_slack, float* endpoint_slack) {
     if (!h || !wns_tns) return set_err(STA_ERR_INVALID_ARG, "null argument");
-    if (h->batch()) return set_err(STA_ERR_STATE, "sta_query_slack: single-placement schedules (use the queries)");
+    if (h->batch() || h->nl > 1)
+        return set_err(STA_ERR_STATE, "sta_query_slack: single-placement handles (use the queries)");
     double sum[STA_SUM_COUNT];
     StaStatus st = sta_query_summary(h, sum, 0, nullptr);
     if (st != STA_OK) return st;

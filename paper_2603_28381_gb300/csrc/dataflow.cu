@@ -390,23 +390,35 @@ __device__ void fwd_df_chunk(const DevNet& g, const DevState& s, const DfState& 
     }
 }
 
-template <bool lse>
+// With several lanes (independent placements) queue index q is task q / nl of
+// lane q % nl: a task only waits for tasks of its own lane with smaller task
+// indices, which have smaller queue indices, so the sweep still progresses.
+// (kLanes: the lane variant; the single-placement one carries no lane arithmetic)
+template <bool lse, bool kLanes>
 __global__ void __launch_bounds__(kBlock) k_fwd_df(DevNet g, DevState s, DfState d, float gamma, int stall_task) {
-    int t = grab(d.heads + 0);
-    while (t < d.TF) {
+    const int nl = kLanes ? *s.active : 1;  // the lanes this call runs
+    int q = grab(d.heads + 0);
+    while (q < d.TF * nl) {
+        const int t = kLanes ? q / nl : q, l = kLanes ? q - t * nl : 0;
+        const DevState sl = kLanes ? lane_state(s, l) : s;
+        const DfState dl = kLanes ? lane_df(d, l, s.lane_bytes) : d;
         const int4 task = d.ftask[t];
-        if (task.y > 0) fwd_df_warp<lse>(g, s, d, t, task.x, task.y, gamma, stall_task);
-        else fwd_df_chunk<lse>(g, s, d, t, task.x, task.z, task.w, gamma, stall_task);
+        const int stall = l == 0 ? stall_task : -1;
+        if (task.y > 0) fwd_df_warp<lse>(g, sl, dl, t, task.x, task.y, gamma, stall);
+        else fwd_df_chunk<lse>(g, sl, dl, t, task.x, task.z, task.w, gamma, stall);
         // the next task only once this one is done: a task reserved while this one
         // waits could not start when its own data arrives (head-of-line blocking)
-        t = grab(d.heads + 0);
+        q = grab(d.heads + 0);
     }
 }
 
 // Before a backward sweep: the required-time (mode 1) and adjoint (mode 2)
 // words of every cell-input pin, which the sweep writes once, are set to kUnwritten.
-__global__ void __launch_bounds__(kBlock) k_bwd_reset(DevState s, const int32_t* __restrict__ pin_cons, int P,
-                                                      int mode, float* part, int npart_words) {
+__global__ void __launch_bounds__(kBlock) k_bwd_reset(DevState s0, const int32_t* __restrict__ pin_cons, int P,
+                                                      int mode, float* part0, int npart_words) {
+    if (s0.active && (int)blockIdx.y >= *s0.active) return;  // a lane this call does not run
+    const DevState s = lane_state(s0, blockIdx.y);            // one lane per grid row
+    float* part = lane_ptr(part0, (size_t)blockIdx.y * s0.lane_bytes);
     const float u = __uint_as_float(kUnwritten);
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < npart_words; i += gridDim.x * kBlock) part[i] = u;
     for (int p = blockIdx.x * kBlock + threadIdx.x; p < P; p += gridDim.x * kBlock) {
@@ -424,8 +436,10 @@ __global__ void __launch_bounds__(kBlock) k_bwd_reset(DevState s, const int32_t*
 // the reset of the words that forward tasks poll -- the arrival / slew /
 // LSE-arrival words of the cell-input pins the sweep writes -- to kUnwritten
 // (asserted pins keep their constants; sinks that feed no cell are only written).
-__global__ void __launch_bounds__(kBlock) k_fwd_prologue(DevNet g, DevState s, const uint8_t* __restrict__ keep,
+__global__ void __launch_bounds__(kBlock) k_fwd_prologue(DevNet g, DevState s0, const uint8_t* __restrict__ keep,
                                                          const int32_t* __restrict__ pin_cons, int P) {
+    if (s0.active && (int)blockIdx.y >= *s0.active) return;  // a lane this call does not run
+    const DevState s = lane_state(s0, blockIdx.y);            // one lane per grid row
     if ((int)blockIdx.x < g.nrc) rc_chunk(g, s, g.rc_chunk[blockIdx.x], g.rc_net[blockIdx.x]);
     const float u = __uint_as_float(kUnwritten);
     for (int p = blockIdx.x * kBlock + threadIdx.x; p < P; p += gridDim.x * kBlock) {
@@ -945,34 +959,38 @@ __device__ void bwd_df_grad(const DevNet& g, const DevState& s, const DfState& d
     }
 }
 
-template <int mode>
+template <int mode, bool kLanes>
 // 3 blocks per SM (80 registers, no spills): more warps hold backward tasks
 // ahead of the front, so a task's pre-wait loads are done when its data arrives
 __global__ void __launch_bounds__(kBlock, 3) k_bwd_df(DevNet g, DevState s, DfState d, float gamma) {
-    int32_t* cnt = (mode & 2) ? d.acnt : d.rcnt;
     int32_t* head = d.heads + ((mode & 2) ? 2 : 1);
-    float* part = (mode & 2) ? d.apart : d.rpart;
-    SeedCtx sc;
-    sc.W = (float)s.summary[STA_SUM_WNS_GAMMA];
-    sc.wt = s.params[0];
-    sc.ww = s.params[1];
-    int t = grab(head);
-    while (t < d.TB) {
+    const int nl = kLanes ? *s.active : 1;  // the lanes this call runs
+    int q = grab(head);
+    while (q < d.TB * nl) {  // queue index q: task q / nl of lane q % nl (see k_fwd_df)
+        const int t = kLanes ? q / nl : q, l = kLanes ? q - t * nl : 0;
+        const DevState sl = kLanes ? lane_state(s, l) : s;
+        const DfState dl = kLanes ? lane_df(d, l, s.lane_bytes) : d;
+        int32_t* cnt = (mode & 2) ? dl.acnt : dl.rcnt;
+        float* part = (mode & 2) ? dl.apart : dl.rpart;
+        SeedCtx sc;
+        sc.W = (float)sl.summary[STA_SUM_WNS_GAMMA];
+        sc.wt = sl.params[0];
+        sc.ww = sl.params[1];
         const int4 task = d.btask[t];
         if (task.y > 0) {
-            bwd_df_warp<mode>(g, s, d, cnt, t, task.x, task.y, gamma, sc);
+            bwd_df_warp<mode>(g, sl, dl, cnt, t, task.x, task.y, gamma, sc);
         } else if (task.y == -1) {
-            bwd_df_part<mode>(g, s, d, cnt, t, task.x, task.z, task.w, gamma, sc,
+            bwd_df_part<mode>(g, sl, dl, cnt, t, task.x, task.z, task.w, gamma, sc,
                               part + (size_t)d.baux[t] * kPartFloats);
         } else if (task.y == -2) {
-            bwd_df_driver<mode>(g, s, d, cnt, t, task.x, part, task.z, task.w, gamma);
+            bwd_df_driver<mode>(g, sl, dl, cnt, t, task.x, part, task.z, task.w, gamma);
         } else if (mode & 2) {
-            bwd_df_grad(g, s, d, cnt, t, task.x, task.z, task.w, gamma, sc);
+            bwd_df_grad(g, sl, dl, cnt, t, task.x, task.z, task.w, gamma, sc);
         }
         // every task's consumers poll the words it wrote, except the gradient
         // chunks of a large net, which wait on a counter that its driver step releases
         if (task.y == -2) signal_consumers(cnt, d.b_out_ptr, d.b_out, t);
-        t = grab(head);
+        q = grab(head);
     }
 }
 
@@ -981,7 +999,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_bwd_df(DevNet g, DevState s, DfSt
 // Co-resident blocks of a sweep: the smallest count over every variant the
 // sweep may launch (they share one grid size).  Also grants the forward kernels
 // their dynamic shared memory (above the default 48 KB), once per device.
-int dataflow_max_blocks(int fwd) {
+int dataflow_max_blocks(int fwd, int lanes) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -991,15 +1009,24 @@ int dataflow_max_blocks(int fwd) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kBlock, smem);
         per_sm = n < per_sm ? n : per_sm;
     };
-    if (fwd) {
-        cudaFuncSetAttribute(k_fwd_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-        cudaFuncSetAttribute(k_fwd_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-        take(k_fwd_df<true>, kFwdSmem);
-        take(k_fwd_df<false>, kFwdSmem);
+    if (fwd && lanes) {
+        cudaFuncSetAttribute(k_fwd_df<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+        cudaFuncSetAttribute(k_fwd_df<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+        take(k_fwd_df<true, true>, kFwdSmem);
+        take(k_fwd_df<false, true>, kFwdSmem);
+    } else if (fwd) {
+        cudaFuncSetAttribute(k_fwd_df<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+        cudaFuncSetAttribute(k_fwd_df<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+        take(k_fwd_df<true, false>, kFwdSmem);
+        take(k_fwd_df<false, false>, kFwdSmem);
+    } else if (lanes) {
+        take(k_bwd_df<1, true>, 0);
+        take(k_bwd_df<2, true>, 0);
+        take(k_bwd_df<3, true>, 0);
     } else {
-        take(k_bwd_df<1>, 0);
-        take(k_bwd_df<2>, 0);
-        take(k_bwd_df<3>, 0);
+        take(k_bwd_df<1, false>, 0);
+        take(k_bwd_df<2, false>, 0);
+        take(k_bwd_df<3, false>, 0);
     }
     return sms * (per_sm > 0 ? per_sm : 1);
 }
@@ -1007,16 +1034,21 @@ int dataflow_max_blocks(int fwd) {
 void launch_fwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int lse,
                          int stall_task, cudaStream_t st) {
     if (d.TF == 0) return;
-    if (lse) launch_coop(k_fwd_df<true>, grid, kBlock, kFwdSmem, st, g, s, d, gamma, stall_task);
-    else launch_coop(k_fwd_df<false>, grid, kBlock, kFwdSmem, st, g, s, d, gamma, stall_task);
+    if (s.nl > 1) {
+        if (lse) launch_coop(k_fwd_df<true, true>, grid, kBlock, kFwdSmem, st, g, s, d, gamma, stall_task);
+        else launch_coop(k_fwd_df<false, true>, grid, kBlock, kFwdSmem, st, g, s, d, gamma, stall_task);
+    } else {
+        if (lse) launch_coop(k_fwd_df<true, false>, grid, kBlock, kFwdSmem, st, g, s, d, gamma, stall_task);
+        else launch_coop(k_fwd_df<false, false>, grid, kBlock, kFwdSmem, st, g, s, d, gamma, stall_task);
+    }
 }
 
 void launch_bwd_reset(const DevState& s, const DfState& d, int P, int mode, cudaStream_t st) {
     if (P == 0 && d.npart == 0) return;
     int blocks = (P + kBlock - 1) / kBlock;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    k_bwd_reset<<<blocks, kBlock, 0, st>>>(s, d.pin_cons, P, mode, (mode & 2) ? d.apart : d.rpart,
-                                           d.npart * kPartFloats);
+    k_bwd_reset<<<dim3(blocks, s.nl), kBlock, 0, st>>>(s, d.pin_cons, P, mode, (mode & 2) ? d.apart : d.rpart,
+                                                       d.npart * kPartFloats);
 }
 
 void launch_fwd_prologue(const DevNet& g, const DevState& s, const DfState& d, int P, cudaStream_t st) {
@@ -1024,15 +1056,21 @@ void launch_fwd_prologue(const DevNet& g, const DevState& s, const DfState& d, i
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < g.nrc) blocks = g.nrc;
     if (blocks == 0) return;
-    k_fwd_prologue<<<blocks, kBlock, 0, st>>>(g, s, d.pin_keep, d.pin_cons, P);
+    k_fwd_prologue<<<dim3(blocks, s.nl), kBlock, 0, st>>>(g, s, d.pin_keep, d.pin_cons, P);
 }
 
 void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int mode,
                          cudaStream_t st) {
     if (d.TB == 0) return;
-    if (mode == 1) launch_coop(k_bwd_df<1>, grid, kBlock, 0, st, g, s, d, gamma);
-    else if (mode == 2) launch_coop(k_bwd_df<2>, grid, kBlock, 0, st, g, s, d, gamma);
-    else launch_coop(k_bwd_df<3>, grid, kBlock, 0, st, g, s, d, gamma);
+    if (s.nl > 1) {
+        if (mode == 1) launch_coop(k_bwd_df<1, true>, grid, kBlock, 0, st, g, s, d, gamma);
+        else if (mode == 2) launch_coop(k_bwd_df<2, true>, grid, kBlock, 0, st, g, s, d, gamma);
+        else launch_coop(k_bwd_df<3, true>, grid, kBlock, 0, st, g, s, d, gamma);
+    } else {
+        if (mode == 1) launch_coop(k_bwd_df<1, false>, grid, kBlock, 0, st, g, s, d, gamma);
+        else if (mode == 2) launch_coop(k_bwd_df<2, false>, grid, kBlock, 0, st, g, s, d, gamma);
+        else launch_coop(k_bwd_df<3, false>, grid, kBlock, 0, st, g, s, d, gamma);
+    }
 }
 
 }  // namespace sta

@@ -19,7 +19,13 @@ namespace {
 // ---------------------------------------------------------------------------
 // positions: internal order <- caller's pin order
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_gather_xy(DevNet g, DevState s, const float2* __restrict__ xy) {
+// one lane per grid row: lane l reads the caller's placement l ([lanes][P][2]);
+// the grid has a row per lane the following calls run, and it records that
+// count for them (lanes handles)
+__global__ void __launch_bounds__(kBlock) k_gather_xy(DevNet g, DevState s0, const float2* __restrict__ xy0) {
+    if (s0.active && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *s0.active = (int)gridDim.y;
+    const DevState s = lane_state(s0, blockIdx.y);
+    const float2* xy = xy0 + (size_t)blockIdx.y * g.P;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x)
         s.xy[p] = xy[g.pin_orig[p]];
 }
@@ -406,9 +412,12 @@ __device__ __forceinline__ EpAcc ep_load_cg(const EpAcc* p) {
 // depend on which block finishes last.  With rs_cons non-null the blocks also
 // mark the words the next fused dataflow backward sweep polls (the required-time
 // and adjoint words of cell-input pins and the large nets' partial records).
-__global__ void __launch_bounds__(kBlock) k_ep(DevNet g, DevState s, float gamma, int lse,
-                                               const int32_t* __restrict__ rs_cons, int P, float* rs_part,
+__global__ void __launch_bounds__(kBlock) k_ep(DevNet g, DevState s0, float gamma, int lse,
+                                               const int32_t* __restrict__ rs_cons, int P, float* rs_part0,
                                                int rs_part_words) {
+    if (s0.active && (int)blockIdx.y >= *s0.active) return;  // a lane this call does not run
+    const DevState s = lane_state(s0, blockIdx.y);            // one lane per grid row
+    float* rs_part = lane_ptr(rs_part0, (size_t)blockIdx.y * s0.lane_bytes);
     EpAcc acc = ep_identity();
     for (int e = blockIdx.x * kBlock + threadIdx.x; e < g.E; e += gridDim.x * kBlock) {
         const int p = g.ep_pin[e];
@@ -491,7 +500,9 @@ __global__ void __launch_bounds__(kBlock) k_seed(DevNet g, DevState s, float gam
 // early rising arrival, which (on a net driven by a startpoint) moves one for
 // one with the pin's wire delay, so d loss / d bound enters the adjoint of the
 // clock pin's rising LSE arrival, added where the arc step writes it.
-__global__ void __launch_bounds__(kBlock) k_cap_seed(DevNet g, DevState s, float gamma) {
+__global__ void __launch_bounds__(kBlock) k_cap_seed(DevNet g, DevState s0, float gamma) {
+    if (s0.active && (int)blockIdx.y >= *s0.active) return;  // a lane this call does not run
+    const DevState s = lane_state(s0, blockIdx.y);            // one lane per grid row
     const float W = (float)s.summary[STA_SUM_WNS_GAMMA];
     const float wt = s.params[0], ww = s.params[1];
     for (int e = blockIdx.x * kBlock + threadIdx.x; e < g.E; e += gridDim.x * kBlock) {
@@ -543,9 +554,9 @@ int grid_for(long long n) {
 
 }  // namespace
 
-void launch_gather_xy(const DevNet& g, const DevState& s, const float2* xy_user, cudaStream_t st) {
-    if (g.P == 0) return;
-    k_gather_xy<<<grid_for(g.P), kBlock, 0, st>>>(g, s, xy_user);
+void launch_gather_xy(const DevNet& g, const DevState& s, const float2* xy_user, int lanes, cudaStream_t st) {
+    if (g.P == 0 && !s.active) return;
+    k_gather_xy<<<dim3(grid_for(g.P), lanes), kBlock, 0, st>>>(g, s, xy_user);
 }
 
 void launch_rc(const DevNet& g, const DevState& s, int nw, cudaStream_t st) {
@@ -563,8 +574,9 @@ void launch_fwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0
 
 void launch_endpoints(const DevNet& g, const DevState& s, float gamma, int lse, cudaStream_t st, const DfState* d,
                       int P) {
-    if (d) k_ep<<<kEpBlocks, kBlock, 0, st>>>(g, s, gamma, lse, d->pin_cons, P, d->apart, d->npart * kPartFloats);
-    else k_ep<<<kEpBlocks, kBlock, 0, st>>>(g, s, gamma, lse, nullptr, 0, nullptr, 0);
+    const dim3 grid(kEpBlocks, s.nl);
+    if (d) k_ep<<<grid, kBlock, 0, st>>>(g, s, gamma, lse, d->pin_cons, P, d->apart, d->npart * kPartFloats);
+    else k_ep<<<grid, kBlock, 0, st>>>(g, s, gamma, lse, nullptr, 0, nullptr, 0);
 }
 
 void launch_bwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0, int nc, float gamma, int mode,
@@ -585,7 +597,7 @@ void launch_seed(const DevNet& g, const DevState& s, float gamma, cudaStream_t s
 
 void launch_cap_seed(const DevNet& g, const DevState& s, float gamma, cudaStream_t st) {
     if (g.E == 0 || !g.ep_clk) return;
-    k_cap_seed<<<grid_for(g.E), kBlock, 0, st>>>(g, s, gamma);
+    k_cap_seed<<<dim3(grid_for(g.E), s.nl), kBlock, 0, st>>>(g, s, gamma);
 }
 
 void launch_scatter(const DevNet& g, const float* in, float* out, int k, int np, cudaStream_t st) {

@@ -56,7 +56,44 @@ struct DevState {
     float* rc_part;    // [rc_slots] partial loads of the nets split into several RC chunks
     int32_t* rc_count; // [rc_slots] chunks done (0 between launches: the last chunk resets it)
     int32_t* ep_count; // [1] endpoint blocks done (0 between launches)
+    // Independent placements ("lanes") of one handle: every array above of lane
+    // l sits l * lane_bytes after lane 0's (one slab per lane, same layout).
+    size_t lane_bytes;
+    int32_t nl;        // lanes (1: a single placement)
+    int32_t* active;   // lanes handles: device word, the lanes [0, *active) a call runs (set by the
+                       // position gather); null for a single placement.  Not per lane.
 };
+
+template <typename T>
+__host__ __device__ inline T* lane_ptr(T* p, size_t off) {
+    return p ? reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(p) + off) : p;
+}
+
+// The per-placement state of lane l.
+__host__ __device__ inline DevState lane_state(const DevState& s, int l) {
+    const size_t off = (size_t)l * s.lane_bytes;
+    DevState r = s;
+    r.xy = lane_ptr(s.xy, off);
+    r.load = lane_ptr(s.load, off);
+    r.wdi = lane_ptr(s.wdi, off);
+    r.at = lane_ptr(s.at, off);
+    r.slew = lane_ptr(s.slew, off);
+    r.ats = lane_ptr(s.ats, off);
+    r.adel = lane_ptr(s.adel, off);
+    r.rat = lane_ptr(s.rat, off);
+    r.g_ats = lane_ptr(s.g_ats, off);
+    r.g_slew = lane_ptr(s.g_slew, off);
+    r.grad = lane_ptr(s.grad, off);
+    r.ep_slack = lane_ptr(s.ep_slack, off);
+    r.red = lane_ptr(s.red, off);
+    r.summary = lane_ptr(s.summary, off);
+    r.params = lane_ptr(s.params, off);
+    r.cap_seed = lane_ptr(s.cap_seed, off);
+    r.rc_part = lane_ptr(s.rc_part, off);
+    r.rc_count = lane_ptr(s.rc_count, off);
+    r.ep_count = lane_ptr(s.ep_count, off);
+    return r;
+}
 
 // Dataflow schedule: task lists, the counters of the large nets' gradient
 // chunks, queue heads.  Tasks wait on the data words they read (reset to
@@ -83,7 +120,23 @@ struct DfState {
     int32_t npart;           // partial records of the backward sweeps
     float4* brec;            // [N*2*4] per (net, late output transition): the adjoint terms of the
                              // driver cell the forward sweep computed (see fwd_brec)
+    // rcnt, acnt, rpart, apart, net_gload and brec are per lane (in the lane's slab,
+    // DevState::lane_bytes apart); the task lists, queue heads and abort words are
+    // shared: a sweep's queue holds task t of lane l at index t * nl + l
 };
+
+// The dataflow bookkeeping of lane l.
+__host__ __device__ inline DfState lane_df(const DfState& d, int l, size_t lane_bytes) {
+    const size_t off = (size_t)l * lane_bytes;
+    DfState r = d;
+    r.rcnt = lane_ptr(d.rcnt, off);
+    r.acnt = lane_ptr(d.acnt, off);
+    r.rpart = lane_ptr(d.rpart, off);
+    r.apart = lane_ptr(d.apart, off);
+    r.net_gload = lane_ptr(d.net_gload, off);
+    r.brec = lane_ptr(d.brec, off);
+    return r;
+}
 
 // Batched schedule (many placements of one netlist; lane = placement).
 // Per-placement state is pin-major, placement-minor: value[(row) * Bp + b].
@@ -144,13 +197,16 @@ void launch_fwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, i
 void launch_bwd_reset(const DevState& s, const DfState& d, int P, int mode, cudaStream_t st);
 void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int mode,
                          cudaStream_t st);
-// largest co-resident grid of the dataflow kernels on the current device
-int dataflow_max_blocks(int fwd);
+// largest co-resident grid of the dataflow kernels on the current device (lanes:
+// the variants of a handle with several independent placements)
+int dataflow_max_blocks(int fwd, int lanes);
 
 // net RC in the CTE scheme of Algorithm 2 (ablation), nets [n0, n1)
 void launch_rc_cte(const DevNet& g, const DevState& s, int n0, int n1, cudaStream_t st);
 
-void launch_gather_xy(const DevNet& g, const DevState& s, const float2* xy_user, cudaStream_t st);
+// positions of `lanes` placements ([lanes][P][2], caller's pin order); a lanes
+// handle's following calls run those lanes
+void launch_gather_xy(const DevNet& g, const DevState& s, const float2* xy_user, int lanes, cudaStream_t st);
 // net RC: the first nw warp tasks (packed small nets) and every large-net chunk
 void launch_rc(const DevNet& g, const DevState& s, int nw, cudaStream_t st);
 // dataflow forward prologue: large-net RC chunks and the reset of the sweep's polled words

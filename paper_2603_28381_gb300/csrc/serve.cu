@@ -12,9 +12,10 @@
 // are deterministic and a netlist's state is only touched by its own requests.
 //
 // With merge = M > 0, pending requests of one netlist with the same gamma and
-// kind run together, up to M at a time, as the placements of one batched call
-// (every netlist's handle is then a batched one, and a request alone is a batch
-// with one real placement, so its results are bit-identical alone and merged).
+// kind run together, up to M at a time, as the lanes of one call of a lanes
+// handle (STA_BATCH_LANES: independent placements of the single-placement
+// sweeps), which runs only the lanes it is given; each lane's results are those
+// of the same placement alone.
 //
 // With sequential = 1 the server is the plain one-request-per-launch loop:
 // one slot, strict arrival order.
@@ -218,20 +219,15 @@ namespace {
 // cell output the per-net arrays and the task lists (120 B); per arc the arc
 // delays and dependency edges (32 B); per endpoint 28 B; with a propagated
 // clock 4 B more per pin (clock seeds) and per endpoint (its clock pin).
-// A batched handle of M placements (merged requests) holds its per-placement
-// state for the padded batch Bp (M rounded up to 32): per pin and placement
-// the positions, arrival / slew / LSE / required times, adjoints, gradient and
-// staging (136 B), per net and placement 12 B, per endpoint and placement 24 B.
+// A lanes handle of M placements (merged requests) holds M copies of the
+// per-placement state (at most the whole single-placement estimate each).
 size_t estimate_bytes(const HostNetlist& hn, int merge) {
     const StaNetlistDesc& d = hn.nl;
     const size_t A = d.num_cells ? (size_t)hn.cell_in_ptr[d.num_cells] : 0;
     const size_t clk = d.end_clock ? 4 : 0;
     const size_t base = (size_t)d.num_pins * (132 + clk) + ((size_t)d.num_nets + d.num_cells) * 120 + A * 32 +
                         (size_t)d.num_end * (28 + clk) + (1u << 20);
-    if (merge <= 0) return base;
-    const size_t Bp = (size_t)(merge + 31) / 32 * 32;
-    return base + Bp * ((size_t)d.num_pins * (136 + clk) + ((size_t)d.num_nets + d.num_cells) * 12 +
-                        (size_t)d.num_end * 24);
+    return merge <= 0 ? base : base * (size_t)merge;
 }
 
 }  // namespace
@@ -291,11 +287,9 @@ static Rep* create_rep(StaServer* S, Net* n, std::string& err) {
     StaOptions o{};
     o.use_graphs = 1;
     o.schedule = S->opt.merge > 0 ? STA_SCHED_BATCH : STA_SCHED_DATAFLOW;
-    if (S->opt.merge > 0) {  // the lane-per-placement dataflow sweeps, small tasks
+    if (S->opt.merge > 0) {  // M placements as lanes of the single-placement sweeps
         o.num_placements = M;
-        o.batch_sweep = STA_BATCH_DATAFLOW;
-        o.tile_pins = 2;
-        o.chunk = 8;
+        o.batch_sweep = STA_BATCH_LANES;
     }
     // a netlist's persistent sweeps use a grid in proportion to its size, so the
     // sweeps of small netlists leave room for others on the device
@@ -366,25 +360,22 @@ static StaStatus dispatch(StaServer* S, Slot& sl, Net* n) {
     return s;
 }
 
-// Merged: the slot's k requests (same netlist, gamma and kind) are placements
-// 0..k-1 of one batched call of M placements; the other lanes repeat
-// placement 0's positions (their results are not read).  Each request's
-// gradient and summary are copied out of its own lane.
+// Merged: the slot's k requests (same netlist, gamma and kind) are lanes
+// 0..k-1 of one call of the netlist's lanes handle, which runs those k lanes
+// only (sta_set_active).  Each request's gradient and summary are copied out of
+// its own lane.
 static StaStatus dispatch_merged(StaServer* S, Slot& sl, Net* n) {
-    const int M = S->opt.merge, k = (int)sl.reqs.size();
+    const int M = (int)sl.reqs.size(), k = M;
+    (void)S;
     const StaServerRequest& r0 = sl.reqs[0].r;
     const size_t P = (size_t)n->P;
     Rep* rp = sl.rep;
     cudaStream_t cst = sl.st;
     void* st = sl.st;
-    StaStatus s = STA_OK;
-    for (int b = 0; b < M && s == STA_OK; ++b) {
-        if (P == 0) break;
-        const void* src = b < k ? (const void*)sl.reqs[b].r.xy : (const void*)rp->xy_dev;
-        if (cudaMemcpyAsync(rp->xy_dev + b * P * 2, src, P * 8, b < k ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                            cst) != cudaSuccess)
+    StaStatus s = sta_set_active(rp->h, k);
+    for (int b = 0; b < k && s == STA_OK && P; ++b)
+        if (cudaMemcpyAsync(rp->xy_dev + b * P * 2, sl.reqs[b].r.xy, P * 8, cudaMemcpyHostToDevice, cst) != cudaSuccess)
             s = STA_ERR_CUDA;
-    }
     if (s == STA_OK) s = sta_set_positions(rp->h, rp->xy_dev, 1, st);
     if (s == STA_OK)
         s = sta_forward(rp->h, STA_FWD_LSE | STA_FWD_RAT | (r0.gradient ? 0u : STA_FWD_RAT_EAGER), r0.gamma, st);

@@ -158,3 +158,63 @@ def test_autotune_picks_a_candidate_and_stays_exact():
     res = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, engine=eng)
     _check_all(w.netlist, w.library, xyb, W, 10.0, res, which=[0, 15])
     eng.close()
+
+
+# ---------------------------------------------------------------------------
+# lanes: the placements as independent lanes of the single-placement sweeps
+# ---------------------------------------------------------------------------
+def _same_as_single(nl, lib, xyb, W, gamma, res, which):
+    for b in which:
+        one = tp.run_gpu(nl, lib, xyb[b], gamma, (float(W[b, 0]), float(W[b, 1])))
+        for k in ("at", "slew", "rat", "ats", "slack", "ep_slack", "grad"):
+            assert np.array_equal(res[b][k], one[k], equal_nan=True), (b, k)
+        assert res[b]["summary"] == one["summary"], b
+
+
+@pytest.mark.parametrize("make,B", [(lambda: netgen.superblue_like(3, scale=0.02, depth=40), 5),
+                                    (lambda: netgen.tiny_design(1, clock_nets=2), 3),
+                                    (lambda: netgen.tiny_design(0), 33)],
+                         ids=["sb_50k_x5", "tiny_clocked_x3", "tiny_x33"])
+def test_lanes_equal_single_placements_bitwise(make, B):
+    # each lane's every output is bit-identical to the same placement in a
+    # single-placement handle; one lane is also checked against the oracle
+    w = make()
+    xyb, W = _placements(w, B, seed=21), _weights(B, seed=22)
+    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, sweep="lanes")
+    _same_as_single(w.netlist, w.library, xyb, W, 10.0, res, sorted({0, B // 2, B - 1}))
+    _check_all(w.netlist, w.library, xyb, W, 10.0, res, which=[B - 1])
+
+
+def test_lanes_host_buffers_repeats_and_edge_netlists():
+    import torch
+    import paper_2603_28381_gb300 as sta
+    w = netgen.superblue_like(6, scale=0.01, depth=30)
+    B = 4
+    xyb, W = _placements(w, B), _weights(B)
+    a = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, sweep="lanes")
+    b = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, sweep="lanes", host_xy=True, use_graphs=False)
+    for r, s in zip(a, b):
+        for k in ("at", "rat", "grad", "ep_slack"):
+            assert np.array_equal(r[k], s[k])
+        assert r["summary"] == s["summary"]
+    eng = sta.StaEngine(w.netlist, w.library, schedule="batch", num_placements=B, batch_sweep="lanes")
+    for rep in range(2):
+        xr = _placements(w, B, seed=200 + rep)
+        got = tp.run_gpu_batch(w.netlist, w.library, xr, 10.0, W, engine=eng)
+        _same_as_single(w.netlist, w.library, xr, W, 10.0, got, [rep, B - 1])
+    eng.close()
+    # fewer lanes than the handle holds (sta_set_active), then all again
+    eng = sta.StaEngine(w.netlist, w.library, schedule="batch", num_placements=B, batch_sweep="lanes")
+    for k in (2, 1, B):
+        eng.set_active(k)
+        xr = _placements(w, k, seed=300 + k)
+        got = tp.run_gpu_batch(w.netlist, w.library, xr, 10.0, W[:k], engine=eng)
+        assert len(got) == k
+        _same_as_single(w.netlist, w.library, xr, W[:k], 10.0, got, sorted({0, k - 1}))
+    eng.close()
+    for idx in range(3):  # ragged and degenerate netlists
+        name, nl, xy, lib = tp.edge_netlists()[idx]
+        xe = netgen.jitter_positions(xy, 2, 2.0, 5)
+        We = _weights(2)
+        res = tp.run_gpu_batch(nl, lib, xe, 10.0, We, sweep="lanes")
+        _check_all(nl, lib, xe, We, 10.0, res)
