@@ -620,6 +620,30 @@ def run_batch(args, emit=True):
     _, launches = eng.profile(with_times=False)
     eng.close()
 
+    # the same placements as lanes of the single-placement sweeps (results equal
+    # to one placement per handle), and their latency for small groups
+    lanes = {}
+    ln = sta.StaEngine(nl, w.library, schedule="batch", num_placements=B, batch_sweep="lanes")
+    lanes_s = timed(ln, step, max(1, min(args.steps, 10)))
+    lanes["ms_per_step"] = 1e3 * lanes_s / max(1, min(args.steps, 10))
+    lanes["value"] = B * P / (lanes["ms_per_step"] / 1e3)
+    lanes["small_groups_ms"] = {}
+    for k in (1, 2, 4, 8):
+        if k > B:
+            break
+        ln.set_active(k)
+        xk = xyb[:k].contiguous()
+        wk = W[:k].contiguous()
+        gk = torch.empty(k, P, 2, dtype=torch.float32, device=dev)
+
+        def stepk(e):
+            e.set_positions(xk)
+            e.forward(gamma=GAMMA, lse=True, rat=True)
+            e.backward_grad(wk, out=gk)
+            e.stream_wait()
+        lanes["small_groups_ms"][str(k)] = round(1e3 * timed(ln, stepk, 5) / 5, 4)
+    ln.close()
+
     # the plain path on the same placements: one placement per call, one after another
     one = sta.StaEngine(nl, w.library, schedule="dataflow")
     xs = [xyb[b].contiguous() for b in range(B)]
@@ -674,6 +698,10 @@ def run_batch(args, emit=True):
                       "how": "the same placements one per call on the single-placement dataflow schedule",
                       "ms_per_step": 1e3 * plain_s / plain_steps},
             "speedup_vs_plain": value / plain_value,
+            "lanes": {"how": "the same placements as lanes of the single-placement sweeps in one launch "
+                             "(STA_BATCH_LANES; results bit-identical to one placement per handle); "
+                             "small_groups_ms: a call on the first 1, 2, 4, 8 placements",
+                      **lanes},
             "gpu_launches": int(sum(launches.values())) * args.steps,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
