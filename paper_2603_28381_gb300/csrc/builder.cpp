@@ -567,6 +567,11 @@ StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& 
         if (o.net_drv[i] >= 0) o.pin_keep[o.net_ptr[i]] = 0;
         for (int32_t p = o.net_ptr[i] + 1; p < o.net_ptr[i + 1]; ++p) o.pin_keep[p] = 0;
     }
+    o.pin_mask.assign(((size_t)P + 3) / 4 * 4, 0);
+    for (int32_t a = 0; a < o.A; ++a) {
+        const int32_t p = o.arc_pin[a];
+        o.pin_mask[p] = (uint8_t)((o.pin_keep[p] ? 0 : 1) | 2);
+    }
 
     o.pin_cap.resize(P);
     for (int32_t i = 0; i < P; ++i) o.pin_cap[i] = nl.pin_cap[o.pin_orig[i]];

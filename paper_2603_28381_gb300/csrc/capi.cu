@@ -804,6 +804,11 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         STEP(h->upload(d.baux, L.baux));
         STEP(h->upload(d.pin_cons, L.pin_cons));
         STEP(h->upload(d.pin_keep, L.pin_keep));
+        {
+            const uint8_t* mp = nullptr;
+            STEP(h->upload(mp, L.pin_mask));
+            d.pin_mask = reinterpret_cast<const uchar4*>(mp);
+        }
         STEP(h->upload(d.b_indeg, L.b_indeg));
         STEP(h->upload(d.b_out_ptr, L.b_out_ptr));
         STEP(h->upload(d.b_out, L.b_out));

@@ -436,17 +436,29 @@ __global__ void __launch_bounds__(kBlock) k_bwd_reset(DevState s0, const int32_t
 // the reset of the words that forward tasks poll -- the arrival / slew /
 // LSE-arrival words of the cell-input pins the sweep writes -- to kUnwritten
 // (asserted pins keep their constants; sinks that feed no cell are only written).
-__global__ void __launch_bounds__(kBlock) k_fwd_prologue(DevNet g, DevState s0, const uint8_t* __restrict__ keep,
-                                                         const int32_t* __restrict__ pin_cons, int P) {
+__global__ void __launch_bounds__(kBlock) k_fwd_prologue(DevNet g, DevState s0, const uchar4* __restrict__ mask,
+                                                         int P) {
     if (s0.active && (int)blockIdx.y >= *s0.active) return;  // a lane this call does not run
     const DevState s = lane_state(s0, blockIdx.y);            // one lane per grid row
     if ((int)blockIdx.x < g.nrc) rc_chunk(g, s, g.rc_chunk[blockIdx.x], g.rc_net[blockIdx.x]);
     const float u = __uint_as_float(kUnwritten);
-    for (int p = blockIdx.x * kBlock + threadIdx.x; p < P; p += gridDim.x * kBlock) {
-        if (keep[p] || pin_cons[p] < 0) continue;
-        reinterpret_cast<float4*>(s.at)[p] = make_float4(u, u, u, u);
-        reinterpret_cast<float4*>(s.slew)[p] = make_float4(u, u, u, u);
-        reinterpret_cast<float2*>(s.ats)[p] = make_float2(u, u);
+    const float4 u4 = make_float4(u, u, u, u);
+    // four grid strides per step: the four mask bytes are loaded together, and
+    // consecutive threads store consecutive pins
+    const int stride = gridDim.x * kBlock;
+    const uint8_t* mk = reinterpret_cast<const uint8_t*>(mask);
+    for (int p0 = blockIdx.x * kBlock + threadIdx.x; p0 < P; p0 += 4 * stride) {
+        unsigned m[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m[j] = p0 + j * stride < P ? mk[p0 + j * stride] : 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (m[j] & 1) {
+                const int p = p0 + j * stride;
+                reinterpret_cast<float4*>(s.at)[p] = u4;
+                reinterpret_cast<float4*>(s.slew)[p] = u4;
+                reinterpret_cast<float2*>(s.ats)[p] = make_float2(u, u);
+            }
     }
 }
 
@@ -1056,7 +1068,7 @@ void launch_fwd_prologue(const DevNet& g, const DevState& s, const DfState& d, i
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < g.nrc) blocks = g.nrc;
     if (blocks == 0) return;
-    k_fwd_prologue<<<dim3(blocks, s.nl), kBlock, 0, st>>>(g, s, d.pin_keep, d.pin_cons, P);
+    k_fwd_prologue<<<dim3(blocks, s.nl), kBlock, 0, st>>>(g, s, d.pin_mask, P);
 }
 
 void launch_bwd_dataflow(const DevNet& g, const DevState& s, const DfState& d, int grid, float gamma, int mode,

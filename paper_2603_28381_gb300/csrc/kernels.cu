@@ -413,7 +413,7 @@ __device__ __forceinline__ EpAcc ep_load_cg(const EpAcc* p) {
 // mark the words the next fused dataflow backward sweep polls (the required-time
 // and adjoint words of cell-input pins and the large nets' partial records).
 __global__ void __launch_bounds__(kBlock) k_ep(DevNet g, DevState s0, float gamma, int lse,
-                                               const int32_t* __restrict__ rs_cons, int P, float* rs_part0,
+                                               const uchar4* __restrict__ rs_mask, int P, float* rs_part0,
                                                int rs_part_words) {
     if (s0.active && (int)blockIdx.y >= *s0.active) return;  // a lane this call does not run
     const DevState s = lane_state(s0, blockIdx.y);            // one lane per grid row
@@ -450,14 +450,25 @@ __global__ void __launch_bounds__(kBlock) k_ep(DevNet g, DevState s0, float gamm
         __threadfence();
         last = atomicAdd(s.ep_count, 1) == (int)gridDim.x - 1;
     }
-    if (rs_cons) {
+    if (rs_mask) {
         const float u = __uint_as_float(kUnwritten);
         for (int i = blockIdx.x * kBlock + threadIdx.x; i < rs_part_words; i += gridDim.x * kBlock) rs_part[i] = u;
-        for (int p = blockIdx.x * kBlock + threadIdx.x; p < P; p += gridDim.x * kBlock) {
-            if (rs_cons[p] < 0) continue;
-            reinterpret_cast<float4*>(s.rat)[p] = make_float4(u, u, u, u);
-            reinterpret_cast<float2*>(s.g_ats)[p] = make_float2(u, u);
-            reinterpret_cast<float2*>(s.g_slew)[p] = make_float2(u, u);
+        // four grid strides per step: the four mask bytes are loaded together, and
+        // consecutive threads store consecutive pins
+        const int stride = gridDim.x * kBlock;
+        const uint8_t* mk = reinterpret_cast<const uint8_t*>(rs_mask);
+        for (int p0 = blockIdx.x * kBlock + threadIdx.x; p0 < P; p0 += 4 * stride) {
+            unsigned m[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) m[j] = p0 + j * stride < P ? mk[p0 + j * stride] : 0u;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (m[j] & 2) {
+                    const int p = p0 + j * stride;
+                    reinterpret_cast<float4*>(s.rat)[p] = make_float4(u, u, u, u);
+                    reinterpret_cast<float2*>(s.g_ats)[p] = make_float2(u, u);
+                    reinterpret_cast<float2*>(s.g_slew)[p] = make_float2(u, u);
+                }
         }
     }
     __syncthreads();
@@ -575,7 +586,7 @@ void launch_fwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0
 void launch_endpoints(const DevNet& g, const DevState& s, float gamma, int lse, cudaStream_t st, const DfState* d,
                       int P) {
     const dim3 grid(kEpBlocks, s.nl);
-    if (d) k_ep<<<grid, kBlock, 0, st>>>(g, s, gamma, lse, d->pin_cons, P, d->apart, d->npart * kPartFloats);
+    if (d) k_ep<<<grid, kBlock, 0, st>>>(g, s, gamma, lse, d->pin_mask, P, d->apart, d->npart * kPartFloats);
     else k_ep<<<grid, kBlock, 0, st>>>(g, s, gamma, lse, nullptr, 0, nullptr, 0);
 }
 

@@ -116,6 +116,7 @@ struct DfState {
     float* net_gload;        // [N] d loss / d load of large nets
     int32_t* abort_word;     // [2] [0] a bounded wait of the current sweep expired, [1] sticky copy
     const uint8_t* pin_keep; // [P] 1: the forward sweep does not write the pin (asserted values)
+    const uchar4* pin_mask;  // [P/4 rounded up] Layout::pin_mask (read a byte per pin)
     int32_t TF, TB;
     int32_t npart;           // partial records of the backward sweeps
     float4* brec;            // [N*2*4] per (net, late output transition): the adjoint terms of the

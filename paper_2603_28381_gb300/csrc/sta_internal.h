@@ -93,6 +93,8 @@ struct Layout {
     std::vector<int32_t> baux;       // [TB]
     std::vector<int32_t> pin_cons;   // [P] backward task whose arc step writes the pin's RAT / adjoint
     std::vector<uint8_t> pin_keep;   // [P] 1 if no forward task writes the pin (asserted drivers, clock pins)
+    std::vector<uint8_t> pin_mask;   // [P rounded up to 4] bit 0: words of the pin the forward sweep polls
+                                     // (a cell input it writes), bit 1: the backward's (a cell input)
     // dependency counts and consumer lists: a task may start once `indeg` of its
     // producers have published; a producer signals every task of its out list
     std::vector<int32_t> f_indeg, f_out_ptr, f_out;  // forward: [TF], [TF+1], [..]
