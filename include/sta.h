@@ -467,9 +467,12 @@ typedef struct {
 } StaServerCompletion;
 
 StaStatus sta_server_create(const StaServerOptions *opt, StaServer **out);
-/* Register a netlist (arrays are copied); preload != 0 also makes it resident
- * now (OOM if it does not fit), with its further copies (replicas) while the
- * budget allows without evicting.  *id identifies it in requests. */
+/* Register a netlist (arrays are copied) and build its host layout once (the
+ * errors of sta_create are reported here); every resident copy is created from
+ * that layout, so a netlist evicted under the budget comes back with device
+ * allocations and uploads only.  preload != 0 also makes it resident now (OOM
+ * if it does not fit), with its further copies (replicas) while the budget
+ * allows without evicting.  *id identifies it in requests. */
 StaStatus sta_server_add_netlist(StaServer *s, const StaNetlistDesc *nl, const StaLibrary *lib,
                                  int32_t preload, int32_t *id);
 StaStatus sta_server_submit(StaServer *s, const StaServerRequest *req, int64_t *id);

@@ -737,4 +737,12 @@ StaStatus build_layout(const StaNetlistDesc& nl, const StaLibrary& lib, Layout& 
     return STA_OK;
 }
 
+StaStatus build_layout_shared(const StaNetlistDesc& nl, const StaLibrary& lib, std::shared_ptr<const Layout>& out,
+                              std::string& err) {
+    auto lay = std::make_shared<Layout>();
+    const StaStatus st = build_layout(nl, lib, *lay, err);
+    if (st == STA_OK) out = std::move(lay);
+    return st;
+}
+
 }  // namespace sta

@@ -15,6 +15,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -44,13 +45,43 @@ StaStatus set_err(StaStatus st, const std::string& msg) {
 
 }  // namespace
 
+namespace {
+// 16-byte host-visible words for the handles' stream-ordered readbacks, carved
+// from pinned pages kept for the life of the process: creating and destroying
+// a handle never calls cudaMallocHost / cudaFreeHost (which waits for the
+// whole device)
+std::mutex g_pin_mu;
+std::vector<int32_t*> g_pin_free;
+
+int32_t* pinned_acquire() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        int32_t* page = nullptr;
+        if (cudaMallocHost(&page, 4096) != cudaSuccess) return nullptr;
+        for (int k = 4096 / 16 - 1; k >= 0; --k) g_pin_free.push_back(page + 4 * k);
+    }
+    int32_t* p = g_pin_free.back();
+    g_pin_free.pop_back();
+    p[0] = p[1] = p[2] = p[3] = 0;
+    return p;
+}
+
+void pinned_release(int32_t* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+}  // namespace
+
 namespace sta {
 // lets other translation units of the library report through sta_last_error()
 void set_last_error_text(const std::string& msg) { g_err = msg; }
 }  // namespace sta
 
 struct StaHandle {
-    Layout lay;
+    explicit StaHandle(std::shared_ptr<Layout> l) : lay_sp(std::move(l)), lay(*lay_sp) {}
+    std::shared_ptr<Layout> lay_sp;  // the host layout, possibly shared with other handles of the netlist
+    Layout& lay;
     DevNet g{};
     DevState s{};
     DfState d{};
@@ -112,11 +143,24 @@ struct StaHandle {
         size_t next = 0;
     } prof_pos, prof_fwd, prof_rat, prof_adj, prof_out;
 
+    // device memory from a stream-ordered pool (handles of a server, created and
+    // destroyed while other requests run: no device-wide synchronization), else
+    // cudaMalloc.  Pool allocations are made on the legacy stream, which the
+    // creating call synchronizes before any other stream uses them; a pooled
+    // handle is destroyed only once none of its work is in flight.
+    cudaMemPool_t pool = nullptr;
+    cudaError_t dev_malloc(void** q, size_t bytes) {
+        return pool ? cudaMallocFromPoolAsync(q, bytes, pool, 0) : cudaMalloc(q, bytes);
+    }
+    void dev_free(void* q) {
+        if (pool) cudaFreeAsync(q, 0);
+        else cudaFree(q);
+    }
     template <typename T>
     StaStatus alloc(T*& p, size_t n) {
         void* q = nullptr;
         const size_t bytes = (n ? n : 1) * sizeof(T);
-        cudaError_t e = cudaMalloc(&q, bytes);
+        cudaError_t e = dev_malloc(&q, bytes);
         if (e != cudaSuccess) return set_err(STA_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         allocs.emplace_back(q, bytes);
         dev_bytes += bytes;
@@ -127,7 +171,7 @@ struct StaHandle {
     void release(const void* p) {
         for (size_t i = 0; i < allocs.size(); ++i)
             if (allocs[i].first == p) {
-                cudaFree(allocs[i].first);
+                dev_free(allocs[i].first);
                 dev_bytes -= allocs[i].second;
                 allocs.erase(allocs.begin() + (long)i);
                 return;
@@ -151,20 +195,21 @@ struct StaHandle {
     }
     StaStatus staging(size_t bytes) {
         if (bytes <= stage_bytes) return STA_OK;
-        if (stage) cudaFree(stage);
+        if (stage) dev_free(stage);
         stage = nullptr;
         stage_bytes = 0;
-        CUDA_TRY(cudaMalloc(&stage, bytes));
+        CUDA_TRY(dev_malloc(&stage, bytes));
+        if (pool) CUDA_TRY(cudaStreamSynchronize(0));  // usable from any stream
         stage_bytes = bytes;
         return STA_OK;
     }
     ~StaHandle() {
         for (auto* gx : {gx_fwd[0], gx_fwd[1], gx_rat, gx_adj, gx_fused})
             if (gx) cudaGraphExecDestroy(gx);
-        for (auto& a : allocs) cudaFree(a.first);
-        if (stage) cudaFree(stage);
+        for (auto& a : allocs) dev_free(a.first);
+        if (stage) dev_free(stage);
         if (qscratch) cudaFree(qscratch);
-        if (pinned) cudaFreeHost(pinned);
+        pinned_release(pinned);
         for (auto* ev : {ev_at, ev_fwd, ev_bwd, ev_fork[0], ev_fork[1]})
             if (ev) cudaEventDestroy(ev);
         for (Prof* pr : {&prof_pos, &prof_fwd, &prof_rat, &prof_adj, &prof_out})
@@ -670,12 +715,41 @@ StaStatus sta_levelize(const StaNetlistDesc* nl, int32_t* net_level, int32_t* nu
     }
 }
 
-StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaOptions* opts, StaHandle** out) {
+}  // extern "C"
+
+namespace {
+StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDesc* nl, const StaLibrary* lib,
+                        const StaOptions* opts, cudaMemPool_t pool, StaHandle** out);
+}  // namespace
+
+extern "C" StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaOptions* opts,
+                                StaHandle** out) {
     if (!nl || !lib || !out) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    return create_handle(nullptr, nl, lib, opts, nullptr, out);
+}
+
+StaStatus sta_create_from_layout(std::shared_ptr<const Layout> lay, const StaOptions* opts, void* pool,
+                                 StaHandle** out) {
+    if (!lay || !out) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    return create_handle(std::move(lay), nullptr, nullptr, opts, static_cast<cudaMemPool_t>(pool), out);
+}
+
+namespace {
+// The handle of sta_create (nl, lib: build the layout) or of
+// sta_create_from_layout (shared: a built layout, shared unless the options
+// make a batched handle with its own task lists, which gets a copy).
+StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDesc* nl, const StaLibrary* lib,
+                        const StaOptions* opts, cudaMemPool_t pool, StaHandle** out) {
     *out = nullptr;
     StaHandle* h = nullptr;
+    const bool own_tasks = opts && opts->schedule == STA_SCHED_BATCH && opts->batch_sweep != STA_BATCH_LANES;
     try {
-        h = new StaHandle();
+        std::shared_ptr<Layout> lay;
+        if (!shared) lay = std::make_shared<Layout>();
+        else if (own_tasks) lay = std::make_shared<Layout>(*shared);
+        else lay = std::const_pointer_cast<Layout>(shared);  // never modified: no task re-planning
+        h = new StaHandle(std::move(lay));
+        h->pool = pool;
     } catch (const std::bad_alloc&) {
         return set_err(STA_ERR_OOM, "host allocation failed");
     }
@@ -685,12 +759,14 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
         g_err = keep;
         return st;
     };
-    try {
-        std::string err;
-        StaStatus st = build_layout(*nl, *lib, h->lay, err);
-        if (st != STA_OK) return fail(set_err(st, err));
-    } catch (const std::bad_alloc&) {
-        return fail(set_err(STA_ERR_OOM, "host allocation failed"));
+    if (!shared) {
+        try {
+            std::string err;
+            StaStatus st = build_layout(*nl, *lib, h->lay, err);
+            if (st != STA_OK) return fail(set_err(st, err));
+        } catch (const std::bad_alloc&) {
+            return fail(set_err(STA_ERR_OOM, "host allocation failed"));
+        }
     }
     if (opts) {
         h->use_graphs = opts->use_graphs != 0;
@@ -899,8 +975,7 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     if (cudaMemset(d.abort_word, 0, 8) != cudaSuccess || cudaMemset(d.heads, 0, 16) != cudaSuccess)
         return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
 #undef STEP
-    if (cudaMallocHost(&h->pinned, 4 * sizeof(int32_t)) != cudaSuccess)
-        return fail(set_err(STA_ERR_OOM, "cudaMallocHost failed"));
+    if (!(h->pinned = pinned_acquire())) return fail(set_err(STA_ERR_OOM, "cudaMallocHost failed"));
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->fork, cudaStreamNonBlocking) != cudaSuccess ||
@@ -936,7 +1011,8 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
             }
         }
     }
-    ce = cudaDeviceSynchronize();
+    // (a pooled handle waits for its own work only: the legacy stream it used)
+    ce = pool ? cudaStreamSynchronize(0) : cudaDeviceSynchronize();
     if (ce != cudaSuccess) return fail(set_err(STA_ERR_CUDA, std::string("init: ") + cudaGetErrorString(ce)));
     cudaEventRecord(h->ev_at, 0);
     cudaEventRecord(h->ev_fwd, 0);
@@ -944,10 +1020,13 @@ StaStatus sta_create(const StaNetlistDesc* nl, const StaLibrary* lib, const StaO
     *out = h;
     return STA_OK;
 }
+}  // namespace
+
+extern "C" {
 
 void sta_destroy(StaHandle* h) {
     if (!h) return;
-    cudaDeviceSynchronize();
+    if (!h->pool) cudaDeviceSynchronize();  // (a pooled handle's owner knows it idle)
     delete h;
 }
 

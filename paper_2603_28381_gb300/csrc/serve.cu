@@ -6,8 +6,12 @@
 // is resident and idle starts on a free slot at once, whatever the requests
 // before it wait for, so the work of requests on different netlists overlaps
 // on the device.  Requests of one netlist run one after another (they share
-// the netlist's device state).  A netlist that is not resident is created
-// when the budget allows, evicting the least recently used idle netlists.
+// the netlist's device state), or concurrently on its copies (replicas).
+// When the budget binds, requests of resident netlists go first; a netlist
+// that is not resident is brought in by evicting least recently used idle
+// netlists without pending requests (any idle one once the oldest request has
+// waited 20 ms), and it serves its queue before it can be evicted; bringing it
+// in allocates and uploads the host layout built once at registration.
 // Every request's result is that of the same request run alone: the kernels
 // are deterministic and a netlist's state is only touched by its own requests.
 //
@@ -25,6 +29,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -45,6 +50,10 @@ namespace {
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
+
+// how long the oldest pending request may wait before an admission for it may
+// evict netlists that still have pending requests
+constexpr double kStarveS = 0.02;
 
 // Host copy of a netlist description and library (the caller's arrays are
 // only borrowed during sta_server_add_netlist).
@@ -76,10 +85,12 @@ struct Rep {
     double* sum_dev = nullptr;  // [M][STA_SUM_COUNT]
     float* xy_dev = nullptr;    // merged: [M][P][2] positions of the placements in flight
     float* w_host = nullptr;    // merged: pinned [M][2] loss weights of the placements in flight
+    bool pooled = false;        // the scratch (and the handle's memory) came from the server's pool
 };
 
 struct Net {
     HostNetlist host;
+    std::shared_ptr<const sta::Layout> layout;  // built once at registration; every copy is created from it
     std::vector<Rep*> reps;     // resident copies
     size_t rep_bytes = 0;       // measured bytes of one copy (0: not created yet, estimate)
     int32_t P = 0;
@@ -115,6 +126,15 @@ struct StaServer {
     std::vector<StaServerCompletion> done;
     int64_t next_id = 0;
     int64_t admissions = 0, evictions = 0;
+    // during an admission round: pending requests per netlist, and whether an
+    // eviction may take a netlist that still has some (the oldest request has
+    // waited kStarveS)
+    std::vector<int32_t> npend;
+    bool evict_pending = true;
+    // device memory of the resident copies: a stream-ordered pool that keeps
+    // up to the budget, so that admissions and evictions while other requests
+    // run neither go to the driver's allocator nor wait for the whole device
+    cudaMemPool_t pool = nullptr;
     std::atomic<bool> stop{false};
     std::thread worker;
     std::string fatal;  // first worker error, reported by later calls
@@ -186,11 +206,14 @@ StaStatus copy_netlist(const StaNetlistDesc& d, const StaLibrary& l, HostNetlist
 
 }  // namespace
 
+// (only for a copy none of whose work is in flight)
 static void release_rep(Rep* r) {
     if (r->h) sta_destroy(r->h);
-    if (r->grad_dev) cudaFree(r->grad_dev);
-    if (r->sum_dev) cudaFree(r->sum_dev);
-    if (r->xy_dev) cudaFree(r->xy_dev);
+    for (void* p : {(void*)r->grad_dev, (void*)r->sum_dev, (void*)r->xy_dev})
+        if (p) {
+            if (r->pooled) cudaFreeAsync(p, 0);
+            else cudaFree(p);
+        }
     if (r->w_host) cudaFreeHost(r->w_host);
     delete r;
 }
@@ -208,6 +231,10 @@ StaServer::~StaServer() {
     for (Net* n : nets) {
         for (Rep* r : n->reps) release_rep(r);
         delete n;
+    }
+    if (pool) {
+        cudaDeviceSynchronize();  // the stream-ordered frees above
+        cudaMemPoolDestroy(pool);
     }
 }
 
@@ -232,12 +259,14 @@ size_t estimate_bytes(const HostNetlist& hn, int merge) {
 
 }  // namespace
 
-// Evict the least recently used idle copy of any netlist (not `keep`); false
-// if every resident copy is busy.
+// Evict the least recently used idle copy (not `keep`) of a netlist with no
+// pending request -- of any netlist if S->evict_pending; false if there is none.
 static bool evict_one(StaServer* S, const Rep* keep) {
     Net* vn = nullptr;
     size_t vi = 0;
-    for (Net* m : S->nets)
+    for (size_t k = 0; k < S->nets.size(); ++k) {
+        Net* m = S->nets[k];
+        if (!S->evict_pending && k < S->npend.size() && S->npend[k] > 0) continue;
         for (size_t i = 0; i < m->reps.size(); ++i) {
             Rep* r = m->reps[i];
             if (r == keep || r->busy) continue;
@@ -246,6 +275,7 @@ static bool evict_one(StaServer* S, const Rep* keep) {
                 vi = i;
             }
         }
+    }
     if (!vn) return false;
     Rep* r = vn->reps[vi];
     S->resident_bytes -= r->bytes;
@@ -299,17 +329,24 @@ static Rep* create_rep(StaServer* S, Net* n, std::string& err) {
         err = "host allocation failed";
         return nullptr;
     }
-    if (sta_create(&n->host.nl, &n->host.lib, &o, &r->h) != STA_OK) {
+    // from the layout built at registration: an evicted netlist comes back
+    // with allocations and uploads only, no host rebuild
+    if (sta_create_from_layout(n->layout, &o, S->pool, &r->h) != STA_OK) {
         err = std::string("sta_create: ") + sta_last_error();
         r->h = nullptr;
         release_rep(r);
         return nullptr;
     }
     const size_t P1 = (size_t)std::max(n->P, 1);
-    if (cudaMalloc(&r->grad_dev, M * P1 * 8) != cudaSuccess ||
-        cudaMalloc(&r->sum_dev, M * STA_SUM_COUNT * sizeof(double)) != cudaSuccess ||
-        (S->opt.merge > 0 && (cudaMalloc(&r->xy_dev, M * P1 * 8) != cudaSuccess ||
-                              cudaMallocHost(&r->w_host, M * 2 * sizeof(float)) != cudaSuccess))) {
+    r->pooled = S->pool != nullptr;
+    auto dmalloc = [&](auto** p, size_t bytes) {
+        void** q = reinterpret_cast<void**>(p);
+        return (S->pool ? cudaMallocFromPoolAsync(q, bytes, S->pool, 0) : cudaMalloc(q, bytes)) == cudaSuccess;
+    };
+    if (!dmalloc(&r->grad_dev, M * P1 * 8) || !dmalloc(&r->sum_dev, M * STA_SUM_COUNT * sizeof(double)) ||
+        (S->opt.merge > 0 && (!dmalloc(&r->xy_dev, M * P1 * 8) ||
+                              cudaMallocHost(&r->w_host, M * 2 * sizeof(float)) != cudaSuccess)) ||
+        (S->pool && cudaStreamSynchronize(0) != cudaSuccess)) {  // (pool: usable from the slots' streams)
         err = "cudaMalloc of request scratch failed";
         release_rep(r);
         return nullptr;
@@ -444,11 +481,20 @@ void StaServer::run() {
             s.busy = false;
             finished = true;
         }
-        // admissions: the earliest pending request first; later ones go ahead
-        // while it waits for its netlist (busy, or not yet admitted), except in
-        // the sequential loop, which keeps strict arrival order on one slot.
-        // With merging, the later pending requests of the same netlist, gamma and
+        // admissions, residency first: pass 0 starts, in arrival order, the
+        // pending requests whose netlist has an idle resident copy; pass 1 the
+        // rest in arrival order, making copies -- evicting least recently used
+        // idle netlists that have no pending request (any idle one once the
+        // oldest request has waited kStarveS), so an admitted netlist serves its
+        // queue before it can go.  A request waits while its netlist is busy or
+        // cannot be admitted; later ones go ahead, except in the sequential
+        // loop, which keeps strict arrival order on one slot (one pass).  With
+        // merging, the later pending requests of the same netlist, gamma and
         // kind join it, up to `merge` of them, in arrival order.
+        npend.assign(nets.size(), 0);
+        for (const Req& r : pending) ++npend[r.r.netlist];
+        evict_pending = !pending.empty() && now_s() - pending.front().t_arrival > kStarveS;
+        for (int pass = opt.sequential ? 1 : 0; pass < 2; ++pass)
         for (size_t i = 0; i < pending.size();) {
             int free_slot = -1;
             for (int k = 0; k < (int)slots.size(); ++k)
@@ -459,6 +505,10 @@ void StaServer::run() {
             if (free_slot < 0) break;
             Req& rq = pending[i];
             Net* n = nets[rq.r.netlist];
+            if (pass == 0 && std::none_of(n->reps.begin(), n->reps.end(), [](const Rep* r) { return !r->busy; })) {
+                ++i;
+                continue;
+            }
             std::string err;
             Rep* rep = admit(this, rq.r.netlist, err);
             if (!rep) {
@@ -558,6 +608,18 @@ StaStatus sta_server_create(const StaServerOptions* opt, StaServer** out) {
         delete S;
         return fail("cudaGetDevice failed", STA_ERR_CUDA);
     }
+    {
+        cudaMemPoolProps pp{};
+        pp.allocType = cudaMemAllocationTypePinned;
+        pp.location.type = cudaMemLocationTypeDevice;
+        pp.location.id = S->device;
+        uint64_t keep = (uint64_t)o.budget_bytes;  // freed memory stays in the pool up to the budget
+        if (cudaMemPoolCreate(&S->pool, &pp) != cudaSuccess ||
+            cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            delete S;
+            return fail("cudaMemPoolCreate failed", STA_ERR_CUDA);
+        }
+    }
     S->slots.resize(o.slots);
     for (Slot& s : S->slots) {
         if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
@@ -588,6 +650,13 @@ StaStatus sta_server_add_netlist(StaServer* S, const StaNetlistDesc* nl, const S
             delete n;
             return st;
         }
+        // the host layout, once (outside the server's lock: the worker runs on)
+        std::string err;
+        st = sta::build_layout_shared(n->host.nl, n->host.lib, n->layout, err);
+        if (st != STA_OK) {
+            delete n;
+            return fail("sta_server_add_netlist: " + err, st);
+        }
     } catch (const std::bad_alloc&) {
         delete n;
         return fail("host allocation failed", STA_ERR_OOM);
@@ -599,6 +668,7 @@ StaStatus sta_server_add_netlist(StaServer* S, const StaNetlistDesc* nl, const S
     if (preload) {
         // the first copy, or an error; then the further copies (replicas) while
         // the budget allows, so that none is built while requests wait
+        S->evict_pending = true;  // (the worker sets it again for its next round)
         std::string err;
         if (!admit(S, *id, err)) {
             if (err.empty()) err = "over the memory budget";

@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -142,4 +143,20 @@ StaStatus build_tasks(Layout& o, const TaskShape& sh, std::string& err);
 StaStatus ordering(const StaNetlistDesc& nl, std::vector<int32_t>& net_level, int32_t& num_levels,
                    std::vector<int32_t>& net_order, std::vector<int32_t>& pin_order, std::string& err);
 
+// A netlist's host layout built once and shared by the handles created from
+// it with sta_create_from_layout: the serving layer keeps one per registered
+// netlist, so that re-admitting an evicted netlist allocates and uploads
+// without rebuilding the layout on the host.
+StaStatus build_layout_shared(const StaNetlistDesc& nl, const StaLibrary& lib, std::shared_ptr<const Layout>& out,
+                              std::string& err);
+
 }  // namespace sta
+
+// sta_create on a layout from build_layout_shared (same options and errors).
+// The handle shares the layout, which stays unmodified; a BATCH handle with
+// its own task lists (batch_sweep LEVELS or DATAFLOW) works on a copy.  With
+// pool (a cudaMemPool_t) its device memory comes from that stream-ordered pool
+// and neither its creation nor sta_destroy synchronizes the whole device: the
+// caller destroys it only once none of its work is in flight.
+StaStatus sta_create_from_layout(std::shared_ptr<const sta::Layout> lay, const StaOptions* opts, void* pool,
+                                 StaHandle** out);

@@ -196,4 +196,16 @@ def test_bad_requests_rejected(designs):
         s.submit(k + 5, xy)
     with pytest.raises(StaError):
         s.submit(k, xy, gamma=0.0)
+    # the host layout is built at registration: a combinational loop is
+    # reported there (STA_ERR_NOT_DAG), not when a request first needs it
+    b = netgen.NetlistBuilder()
+    i0, o0, i1, o1 = (b.pin(1.0) for _ in range(4))
+    b.net(o0, [i1])
+    b.net(o1, [i0])
+    b.cell(0, [i0], o0)
+    b.cell(0, [i1], o1)
+    loop, _ = b.build()
+    with pytest.raises(StaError) as e:
+        s.add_netlist(loop, designs[0].library, preload=False)
+    assert e.value.status == 2
     s.close()
