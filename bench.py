@@ -59,10 +59,12 @@ def parse():
     ap.add_argument("--schedule", default="dataflow", choices=["dataflow", "levels"])
     ap.add_argument("--grid-blocks", type=int, default=0,
                     help="blocks of the persistent sweeps (0: every block that fits)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "ablation"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "multi", "ablation"],
                     help="single: one placement of the ~2.5M-pin netlist per step (the headline); "
                          "batch: 64 placements of a ~500k-pin netlist per step")
     ap.add_argument("--placements", type=int, default=64)
+    ap.add_argument("--multi-netlists", type=int, default=64,
+                    help="multi: netlists of 5k-40k pins in one handle (sta_create_multi)")
     ap.add_argument("--verbose", action="store_true", help="per-step times on stderr")
     ap.add_argument("--no-sub", action="store_true",
                     help="single: leave out the batched and served sub-records of the default line")
@@ -549,6 +551,9 @@ def run_ours(args):
             sa = copy.copy(args)
             sa.scale = 1.0
             line["serve"] = run_serve(sa, emit=False)
+            ma = copy.copy(args)
+            ma.steps, ma.warmup = min(args.steps, 20), max(3, min(args.warmup, 5))
+            line["multi"] = run_multi(ma, emit=False)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -857,6 +862,112 @@ def run_serve(args, emit=True):
 
 
 # --------------------------------------------------------------------------
+# many small netlists per step in one handle (sta_create_multi)
+# --------------------------------------------------------------------------
+def multi_workload(args):
+    """args.multi_netlists superblue-shaped netlists of log-uniform 5k-40k pins
+    and depth 20-150, over the first one's library (every one has the same
+    type structure)."""
+    import netgen
+    rng = np.random.default_rng(args.seed + 61)
+    ws = []
+    for k in range(args.multi_netlists):
+        sc = float(np.exp(rng.uniform(np.log(0.002), np.log(0.016))))
+        ws.append(netgen.superblue_like(args.seed + 100 + k, scale=sc, depth=int(rng.integers(20, 151))))
+    return ws
+
+
+def run_multi(args, emit=True):
+    import torch
+
+    import paper_2603_28381_gb300 as sta
+    ws = multi_workload(args)
+    lib = ws[0].library
+    nls = [w.netlist for w in ws]
+    K = len(nls)
+    pins = np.array([nl.num_pins for nl in nls])
+    P = int(pins.sum())
+    dev = torch.device("cuda", 0)
+    xy = torch.as_tensor(np.concatenate([w.xy for w in ws]).astype(np.float32)).to(dev)
+    W = torch.ones(K, 2, dtype=torch.float32, device=dev)
+    grad = torch.empty(P, 2, dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        cur = torch.cuda.current_stream()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(cur)
+            fn()
+            ev[k][1].record(cur)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / 1e3
+
+    eng = sta.StaEngine.multi(nls, lib)
+
+    def step():
+        eng.set_positions(xy)
+        eng.forward(gamma=GAMMA, lse=True, rat=True)
+        eng.backward_grad(W, out=grad)
+        eng.stream_wait()
+
+    clocks = Clocks(0)
+    total_s = timed(step, args.steps)
+    clk = clocks.stop()
+    _, launches = eng.profile(with_times=False)
+    eng.close()
+
+    # the plain path: one handle per netlist, called one after another
+    ones = [sta.StaEngine(nl, lib) for nl in nls]
+    offs = np.concatenate([[0], np.cumsum(pins)])
+
+    def plain():
+        for k, e in enumerate(ones):
+            e.set_positions(xy[offs[k]:offs[k + 1]])
+            e.forward(gamma=GAMMA, lse=True, rat=True)
+            e.backward_grad(W[k], out=grad[offs[k]:offs[k + 1]])
+        for e in ones:
+            e.stream_wait()
+
+    plain_steps = max(1, min(args.steps, 5))
+    plain_s = timed(plain, plain_steps)
+    for e in ones:
+        e.close()
+    sb = 0
+    for nl in nls:
+        st = nl.stats()
+        sb += survey_bytes({"pins": st["pins"], "nets": st["nets"], "arcs": st["arcs"]},
+                           int(nl.net_ptr[-1]) - st["nets"])["step"]
+    peak, peak_src = load_peaks()
+    value = P * args.steps / total_s
+    plain_value = P * plain_steps / plain_s
+    depths = [int(w.info["depth"]) for w in ws]
+    line = {"metric": "pins/s fwd+grad, many netlists in one launch", "value": value, "unit": "pins/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{K} superblue-shaped synthetic netlists of {int(pins.min())}-{int(pins.max())} "
+                                   f"pins (log-uniform), depth {min(depths)}-{max(depths)}, {P} pins in all, one "
+                                   f"library, gamma {GAMMA} ps, fwd (AT+LSE+RAT) + gradient of each netlist's "
+                                   f"own loss, in one handle (sta_create_multi)",
+                       "netlists": K, "pins": P, "l2": "flushed between steps (512 MB write)"},
+            "plain": {"value": plain_value, "unit": "pins/s", "ms_per_step": 1e3 * plain_s / plain_steps,
+                      "how": "one handle per netlist, called one after another on one stream"},
+            "speedup_vs_plain": value / plain_value,
+            "gpu_launches": int(sum(launches.values())) * args.steps,
+            "roofline": {"bound": "hbm", "step_algorithmic_bytes": int(sb), "peak": peak, "unit": "GB/s",
+                         "peak_source": peak_src,
+                         "step_frac": sb / (total_s / args.steps) / 1e9 / peak},
+            "clocks": clk}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+# --------------------------------------------------------------------------
 # ablations on the 2.5M-pin workload: CTE vs pin-based net RC (Algorithm 2),
 # forward only vs sequential vs fused gradient (the Diff / Diff+Fusion ratio)
 # --------------------------------------------------------------------------
@@ -932,6 +1043,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "multi":
+        run_multi(args)
     elif args.workload == "ablation":
         run_ablation(args)
     else:

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define STA_ABI_VERSION 4
+#define STA_ABI_VERSION 5
 #define STA_LUT 7       /* table points per axis */
 #define STA_MAX_ARCS 4  /* arcs (input pins) per cell type */
 
@@ -181,6 +181,23 @@ enum {
 StaStatus sta_create(const StaNetlistDesc *nl, const StaLibrary *lib, const StaOptions *opts,
                      StaHandle **out);
 
+/* Many netlists in one handle: the disjoint union of nls[0..count-1] (one
+ * library, the same r_per_um and c_per_um), swept together, one launch per
+ * sweep and one endpoint launch for all of them.  Netlist k's pins, nets,
+ * cells, startpoints and endpoints follow those of netlists 0..k-1: positions
+ * (sta_set_positions), pin queries, endpoint slacks and gradients are over the
+ * union in that order, netlist k's pin i at the number of pins before it plus
+ * i.  The endpoint reduction, the smoothed loss and its adjoint seeds are per
+ * netlist: sta_query_summary writes [count][STA_SUM_COUNT], and
+ * sta_backward_grad takes w [count][2] (the loss of netlist k weighted by
+ * w[k]; the gradient of each netlist's pins is that of its own loss).  Every
+ * result of netlist k equals that of the same netlist in its own handle.
+ * opts may be NULL; only the DATAFLOW schedule (INVALID_ARG otherwise);
+ * sta_query_slack is not available (STATE).  Errors as sta_create, and
+ * INVALID_ARG for count < 1 or a null description. */
+StaStatus sta_create_multi(const StaNetlistDesc *const *nls, int32_t count, const StaLibrary *lib,
+                           const StaOptions *opts, StaHandle **out);
+
 /* Set pin positions xy [num_pins][2] (um, the netlist's pin order).  xy is a
  * device pointer if on_device != 0, else host memory (copied through pinned
  * staging inside this call).  The positions are copied; the caller may reuse
@@ -275,7 +292,7 @@ StaStatus sta_query_summary(StaHandle *h, double *out, int on_device, void *stre
 StaStatus sta_query_pins(StaHandle *h, float *at, float *slew, float *rat, float *ats,
                          float *slack, int on_device, void *stream);
 
-/* Slack in one call (single-placement schedules; host outputs, synchronizes
+/* Slack in one call (single-placement, single-netlist handles; host outputs, synchronizes
  * the legacy default stream after the handle's work): wns_tns [2][2] =
  * {early WNS, early TNS, late WNS, late TNS} (ps; TNS sums negative endpoint
  * slacks, WNS is the unclamped minimum); pin_slack [num_pins][2] and

@@ -69,6 +69,34 @@ class StaEngine:
         self.sizes = _sta.sta_query_sizes(self.h)
         self.sizes["nets_desc"] = int(netlist.num_nets)
         self.gamma = None
+        self.groups = 1
+
+    @classmethod
+    def multi(cls, netlists, library, use_graphs: bool = True, profile: bool = False, grid_blocks: int = 0):
+        """Many netlists in one handle (sta_create_multi): positions, pins,
+        endpoint slacks and gradients are over the netlists concatenated in
+        order (`pin_offsets`, `end_offsets`); summary() is a list with one dict
+        per netlist and backward_grad takes one weight pair per netlist."""
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("StaEngine needs a CUDA device (there is no CPU path)")
+        torch.cuda.init()
+        self = cls.__new__(cls)
+        nls = list(netlists)
+        self.pin_offsets = np.concatenate([[0], np.cumsum([int(n.num_pins) for n in nls])]).astype(np.int64)
+        self.end_offsets = np.concatenate([[0], np.cumsum([int(n.end_pins.shape[0]) for n in nls])]).astype(np.int64)
+        self.num_pins = int(self.pin_offsets[-1])
+        self.num_end = int(self.end_offsets[-1])
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.schedule = "dataflow"
+        self.batched = False
+        self.B = 1
+        self.h = _sta.sta_create_multi(nls, library, use_graphs, profile, grid_blocks)
+        self.sizes = _sta.sta_query_sizes(self.h)
+        self.sizes["nets_desc"] = int(sum(int(n.num_nets) for n in nls))
+        self.gamma = None
+        self.groups = len(nls)
+        return self
 
     # -- lifetime --
     def close(self) -> None:
@@ -127,6 +155,8 @@ class StaEngine:
             wa = np.ascontiguousarray(np.asarray(w, np.float32))
             if self.batched:
                 wa = np.ascontiguousarray(np.broadcast_to(wa, (self.B, 2)))
+            elif self.groups > 1:  # one pair per netlist
+                wa = np.ascontiguousarray(np.broadcast_to(wa, (self.groups, 2)))
             _sta.sta_backward_grad(self.h, wa.ctypes.data, 0, out.data_ptr(), on_dev, _stream_ptr(stream))
         return out
 
@@ -175,11 +205,12 @@ class StaEngine:
         _sta.sta_debug_expire_wait(self.h)
 
     def summary(self, stream=None):
-        """Summary dict (a list of B dicts for the batched schedule)."""
-        out = np.zeros((self.B, 8), np.float64)
+        """Summary dict (a list of B dicts for the batched schedule, one per
+        netlist for a handle of several netlists)."""
+        out = np.zeros((max(self.B, self.groups), 8), np.float64)
         _sta.sta_query_summary(self.h, out.ctypes.data, 0, _stream_ptr(stream))
         rows = [dict(zip(SUMMARY_KEYS, r.tolist())) for r in out]
-        return rows if self.batched else rows[0]
+        return rows if (self.batched or self.groups > 1) else rows[0]
 
     def summary_device(self, out, stream=None):
         _sta.sta_query_summary(self.h, out.data_ptr(), 1, _stream_ptr(stream))

@@ -85,6 +85,8 @@ def _load() -> ctypes.CDLL:
     sig = {
         "sta_create": ([ctypes.POINTER(StaNetlistDesc), ctypes.POINTER(StaLibrary),
                         ctypes.POINTER(StaOptions), ctypes.POINTER(H)], ctypes.c_int),
+        "sta_create_multi": ([ctypes.POINTER(ctypes.POINTER(StaNetlistDesc)), _i32, ctypes.POINTER(StaLibrary),
+                              ctypes.POINTER(StaOptions), ctypes.POINTER(H)], ctypes.c_int),
         "sta_set_positions": ([H, _p, ctypes.c_int, _p], ctypes.c_int),
         "sta_forward": ([H, ctypes.c_uint32, ctypes.c_float, _p], ctypes.c_int),
         "sta_backward_grad": ([H, _p, ctypes.c_int, _p, ctypes.c_int, _p], ctypes.c_int),
@@ -131,7 +133,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 
 # the header's entry points, for the export check
-EXPORTS = ("sta_create", "sta_set_positions", "sta_forward", "sta_backward_grad",
+EXPORTS = ("sta_create", "sta_create_multi", "sta_set_positions", "sta_forward", "sta_backward_grad",
            "sta_query_summary", "sta_query_pins", "sta_query_endpoints", "sta_levelize",
            "sta_query_sizes", "sta_query_profile", "sta_stream_wait", "sta_destroy",
            "sta_synchronize", "sta_debug_expire_wait", "sta_autotune", "sta_server_create",
@@ -227,6 +229,20 @@ def sta_create(nl, lib, use_graphs: bool = True, profile: bool = False,
     h = ctypes.c_void_p()
     _check(_lib.sta_create(ctypes.byref(d), ctypes.byref(l), ctypes.byref(opts), ctypes.byref(h)),
            "sta_create")
+    return h.value
+
+
+def sta_create_multi(nls, lib, use_graphs: bool = True, profile: bool = False, grid_blocks: int = 0) -> int:
+    """One handle over the disjoint union of the netlists `nls` (sta_create_multi)."""
+    keep = _Keep()
+    descs = [netlist_desc(nl, keep) for nl in nls]
+    arr = (ctypes.POINTER(StaNetlistDesc) * max(len(descs), 1))(*[ctypes.pointer(d) for d in descs])
+    l = library_desc(lib, keep)
+    opts = StaOptions(use_graphs=1 if use_graphs else 0, profile=1 if profile else 0, schedule=SCHED_DATAFLOW,
+                      grid_blocks=int(grid_blocks))
+    h = ctypes.c_void_p()
+    _check(_lib.sta_create_multi(arr, len(descs), ctypes.byref(l), ctypes.byref(opts), ctypes.byref(h)),
+           "sta_create_multi")
     return h.value
 
 

@@ -745,4 +745,124 @@ StaStatus build_layout_shared(const StaNetlistDesc& nl, const StaLibrary& lib, s
     return st;
 }
 
+StaStatus build_union(const StaNetlistDesc* const* nls, int32_t count, UnionNetlist& u, std::string& err) {
+    if (!nls || count < 1) {
+        err = "sta_create_multi: count >= 1 netlists";
+        return STA_ERR_INVALID_ARG;
+    }
+    // sizes first (the arrays are read up to net_ptr[N] and cell_in_ptr[C], as by sta_create)
+    int64_t P = 0, N = 0, C = 0, NP = 0, CI = 0, S = 0, E = 0;
+    bool clocked = false;
+    for (int32_t k = 0; k < count; ++k) {
+        const StaNetlistDesc* d = nls[k];
+        if (!d || d->num_pins < 0 || d->num_nets < 0 || d->num_cells < 0 || d->num_start < 0 || d->num_end < 0 ||
+            !d->net_ptr || !d->cell_in_ptr) {
+            err = "sta_create_multi: netlist " + std::to_string(k) + ": null description, array or negative size";
+            return STA_ERR_INVALID_ARG;
+        }
+        if (d->net_ptr[0] != 0 || d->net_ptr[d->num_nets] < 0 || d->cell_in_ptr[0] != 0 ||
+            d->cell_in_ptr[d->num_cells] < 0) {
+            err = "sta_create_multi: netlist " + std::to_string(k) + ": net_ptr / cell_in_ptr must start at 0";
+            return STA_ERR_INVALID_ARG;
+        }
+        if (d->r_per_um != nls[0]->r_per_um || d->c_per_um != nls[0]->c_per_um) {
+            err = "sta_create_multi: every netlist must have the same r_per_um and c_per_um";
+            return STA_ERR_INVALID_ARG;
+        }
+        P += d->num_pins;
+        N += d->num_nets;
+        C += d->num_cells;
+        NP += d->net_ptr[d->num_nets];
+        CI += d->cell_in_ptr[d->num_cells];
+        S += d->num_start;
+        E += d->num_end;
+        clocked = clocked || d->end_clock;
+    }
+    if (P >= (1ll << 31) - 1 || NP >= (1ll << 31) - 1 || CI >= (1ll << 31) - 1 || N >= (1ll << 31) - 1 ||
+        E >= (1ll << 31) - 1) {
+        err = "sta_create_multi: the union exceeds 2^31 pins, nets or endpoints";
+        return STA_ERR_INVALID_ARG;
+    }
+    u = UnionNetlist();
+    u.net_ptr.reserve(N + 1);
+    u.net_ptr.push_back(0);
+    u.net_pins.reserve(NP);
+    u.cell_type.reserve(C);
+    u.cell_in_ptr.reserve(C + 1);
+    u.cell_in_ptr.push_back(0);
+    u.cell_in_pins.reserve(CI);
+    u.cell_out_pin.reserve(C);
+    u.pin_cap.reserve(P);
+    u.pin_off.assign(1, 0);
+    u.end_off.assign(1, 0);
+    auto missing = [&](int32_t k, const char* what) {
+        err = "sta_create_multi: netlist " + std::to_string(k) + ": null " + what;
+        return STA_ERR_INVALID_ARG;
+    };
+    for (int32_t k = 0; k < count; ++k) {
+        const StaNetlistDesc& d = *nls[k];
+        const int32_t po = u.pin_off.back();
+        const int32_t np = d.net_ptr[d.num_nets], ci = d.cell_in_ptr[d.num_cells];
+        if ((np > 0 && !d.net_pins) || (d.num_cells > 0 && (!d.cell_type || !d.cell_out_pin)) ||
+            (ci > 0 && !d.cell_in_pins))
+            return missing(k, "net_pins / cell array");
+        if ((d.num_pins > 0 && !d.pin_cap) || (d.num_start > 0 && (!d.start_pins || !d.start_at || !d.start_slew)) ||
+            (d.num_end > 0 && (!d.end_pins || !d.end_rat)))
+            return missing(k, "pin_cap / startpoint / endpoint array");
+        const int32_t nb = (int32_t)u.net_pins.size(), cb = (int32_t)u.cell_in_pins.size();
+        for (int32_t i = 1; i <= d.num_nets; ++i) u.net_ptr.push_back(nb + d.net_ptr[i]);
+        for (int32_t i = 0; i < np; ++i) u.net_pins.push_back(po + d.net_pins[i]);
+        for (int32_t i = 0; i < d.num_cells; ++i) {
+            u.cell_type.push_back(d.cell_type[i]);
+            u.cell_in_ptr.push_back(cb + d.cell_in_ptr[i + 1]);
+            u.cell_out_pin.push_back(po + d.cell_out_pin[i]);
+        }
+        for (int32_t i = 0; i < ci; ++i) u.cell_in_pins.push_back(po + d.cell_in_pins[i]);
+        u.pin_cap.insert(u.pin_cap.end(), d.pin_cap, d.pin_cap + d.num_pins);
+        for (int32_t i = 0; i < d.num_start; ++i) u.start_pins.push_back(po + d.start_pins[i]);
+        u.start_at.insert(u.start_at.end(), d.start_at, d.start_at + 4 * (size_t)d.num_start);
+        u.start_slew.insert(u.start_slew.end(), d.start_slew, d.start_slew + 4 * (size_t)d.num_start);
+        for (int32_t i = 0; i < d.num_end; ++i) {
+            u.end_pins.push_back(po + d.end_pins[i]);
+            // a clock pin index moves with its netlist; -1 (none) stays
+            if (clocked) u.end_clock.push_back(d.end_clock && d.end_clock[i] >= 0 ? po + d.end_clock[i] : -1);
+        }
+        u.end_rat.insert(u.end_rat.end(), d.end_rat, d.end_rat + 4 * (size_t)d.num_end);
+        u.pin_off.push_back(po + d.num_pins);
+        u.end_off.push_back(u.end_off.back() + d.num_end);
+    }
+    StaNetlistDesc& o = u.nl;
+    o.num_pins = (int32_t)P;
+    o.num_nets = (int32_t)N;
+    o.num_cells = (int32_t)C;
+    o.net_ptr = u.net_ptr.data();
+    o.net_pins = u.net_pins.data();
+    o.cell_type = u.cell_type.data();
+    o.cell_in_ptr = u.cell_in_ptr.data();
+    o.cell_in_pins = u.cell_in_pins.data();
+    o.cell_out_pin = u.cell_out_pin.data();
+    o.pin_cap = u.pin_cap.data();
+    o.num_start = (int32_t)S;
+    o.start_pins = u.start_pins.data();
+    o.start_at = u.start_at.data();
+    o.start_slew = u.start_slew.data();
+    o.num_end = (int32_t)E;
+    o.end_pins = u.end_pins.data();
+    o.end_rat = u.end_rat.data();
+    o.r_per_um = nls[0]->r_per_um;
+    o.c_per_um = nls[0]->c_per_um;
+    o.end_clock = clocked ? u.end_clock.data() : nullptr;
+    return STA_OK;
+}
+
+void set_groups(Layout& o, const UnionNetlist& u) {
+    o.G = (int32_t)u.pin_off.size() - 1;
+    o.grp_ep = u.end_off;  // endpoints keep the description's order
+    o.pin_grp.resize(o.P);
+    for (int32_t p = 0; p < o.P; ++p) {
+        const int32_t orig = o.pin_orig[p];
+        o.pin_grp[p] = (int32_t)(std::upper_bound(u.pin_off.begin(), u.pin_off.end(), orig) - u.pin_off.begin()) - 1;
+    }
+}
+
 }  // namespace sta

@@ -734,6 +734,27 @@ StaStatus sta_create_from_layout(std::shared_ptr<const Layout> lay, const StaOpt
     return create_handle(std::move(lay), nullptr, nullptr, opts, static_cast<cudaMemPool_t>(pool), out);
 }
 
+extern "C" StaStatus sta_create_multi(const StaNetlistDesc* const* nls, int32_t count, const StaLibrary* lib,
+                                      const StaOptions* opts, StaHandle** out) {
+    if (!nls || !lib || !out) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (opts && opts->schedule != STA_SCHED_DATAFLOW)
+        return set_err(STA_ERR_INVALID_ARG, "sta_create_multi: the DATAFLOW schedule only");
+    auto lay = std::make_shared<Layout>();
+    try {
+        UnionNetlist u;
+        std::string err;
+        StaStatus st = build_union(nls, count, u, err);
+        if (st != STA_OK) return set_err(st, err);
+        st = build_layout(u.nl, *lib, *lay, err);
+        if (st != STA_OK) return set_err(st, err);
+        if (count > 1) set_groups(*lay, u);
+    } catch (const std::bad_alloc&) {
+        return set_err(STA_ERR_OOM, "host allocation failed");
+    }
+    return create_handle(std::move(lay), nullptr, nullptr, opts, nullptr, out);
+}
+
 namespace {
 // The handle of sta_create (nl, lib: build the layout) or of
 // sta_create_from_layout (shared: a built layout, shared unless the options
@@ -866,6 +887,20 @@ StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDe
     g.Pnet = L.Pnet;
     g.N = L.N;
     g.E = L.E;
+    g.G = L.G;
+    g.ep_gx = kEpBlocks;
+    g.grp_ep = g.pin_grp = nullptr;
+    if (L.G > 1) {  // several netlists: per-netlist endpoint ranges and pin owners
+        if (h->batch() || h->schedule != STA_SCHED_DATAFLOW || h->nl > 1)
+            return fail(set_err(STA_ERR_INVALID_ARG, "sta_create_multi: the DATAFLOW schedule only"));
+        STEP(h->upload(g.grp_ep, L.grp_ep));
+        STEP(h->upload(g.pin_grp, L.pin_grp));
+        // blocks per netlist: every endpoint of the largest one at one thread (at
+        // most kEpBlocks), so each netlist reduces in the order it has alone
+        int32_t emax = 0;
+        for (int32_t k = 0; k < L.G; ++k) emax = std::max(emax, L.grp_ep[k + 1] - L.grp_ep[k]);
+        g.ep_gx = std::max(1, std::min(kEpBlocks, (emax + kBlock - 1) / kBlock));
+    }
 
     const size_t P = L.P;
     const bool bat = h->batch();
@@ -880,6 +915,7 @@ StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDe
         STEP(h->upload(d.baux, L.baux));
         STEP(h->upload(d.pin_cons, L.pin_cons));
         STEP(h->upload(d.pin_keep, L.pin_keep));
+        d.pin_grp = g.pin_grp;
         {
             const uint8_t* mp = nullptr;
             STEP(h->upload(mp, L.pin_mask));
@@ -918,9 +954,9 @@ StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDe
         const size_t o_xy = cv.add(P, 8), o_load = cv.add(L.N, 4), o_wdi = cv.add(P, 8), o_at = cv.add(4 * P, 4),
                      o_slew = cv.add(4 * P, 4), o_ats = cv.add(2 * P, 4), o_adel = cv.add(4 * (size_t)L.A, 4),
                      o_rat = cv.add(4 * P, 4), o_gats = cv.add(2 * P, 4), o_gslew = cv.add(2 * P, 4),
-                     o_grad = cv.add(P, 8), o_eps = cv.add(L.E, 8), o_red = cv.add((size_t)kEpBlocks * 8, 8),
-                     o_sum = cv.add(STA_SUM_COUNT, 8), o_par = cv.add(4, 4), o_rcp = cv.add(NS, 4),
-                     o_rcc = cv.add(NS, 4), o_epc = cv.add(1, 4), o_cap = L.ep_clk.empty() ? 0 : cv.add(P, 4),
+                     o_grad = cv.add(P, 8), o_eps = cv.add(L.E, 8), o_red = cv.add(std::max<size_t>((size_t)kEpBlocks * 8, (size_t)L.G * g.ep_gx * 6), 8),
+                     o_sum = cv.add((size_t)STA_SUM_COUNT * L.G, 8), o_par = cv.add(2 * (size_t)L.G + 2, 4), o_rcp = cv.add(NS, 4),
+                     o_rcc = cv.add(NS, 4), o_epc = cv.add(L.G, 4), o_cap = L.ep_clk.empty() ? 0 : cv.add(P, 4),
                      o_rcnt = cv.add(L.TB, 4), o_acnt = cv.add(L.TB, 4), o_rpart = cv.add(NP, 4),
                      o_apart = cv.add(NP, 4), o_gload = cv.add(L.N, 4), o_brec = cv.add(8 * (size_t)L.N, 16);
         const size_t lb = (cv.bytes + 255) / 256 * 256;
@@ -1125,6 +1161,9 @@ StaStatus sta_backward_grad(StaHandle* h, const float* w, int w_on_device, float
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_at, 0));
     if (h->batch()) {  // one weight pair per placement
         CUDA_TRY(cudaMemcpyAsync(h->bs.params, w, sizeof(float) * 2 * h->B,
+                                 w_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    } else if (h->lay.G > 1) {  // several netlists: one weight pair each
+        CUDA_TRY(cudaMemcpyAsync(h->s.params, w, sizeof(float) * 2 * h->lay.G,
                                  w_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     } else if (h->nl > 1) {  // lanes: pair l into lane l's parameters
         CUDA_TRY(cudaMemcpy2DAsync(h->s.params, h->s.lane_bytes, w, 2 * sizeof(float), 2 * sizeof(float), h->active,
@@ -1344,6 +1383,8 @@ StaStatus sta_query_summary(StaHandle* h, double* out, int on_device, void* stre
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (h->batch()) {
         CUDA_TRY(cudaMemcpyAsync(out, h->bs.summary, STA_SUM_COUNT * sizeof(double) * h->B, kind, st));
+    } else if (h->lay.G > 1) {  // several netlists: netlist k's summary to out[k]
+        CUDA_TRY(cudaMemcpyAsync(out, h->s.summary, STA_SUM_COUNT * sizeof(double) * h->lay.G, kind, st));
     } else {  // lane l's summary to out[l]
         CUDA_TRY(cudaMemcpy2DAsync(out, STA_SUM_COUNT * sizeof(double), h->s.summary, h->s.lane_bytes,
                                    STA_SUM_COUNT * sizeof(double), h->active, kind, st));
@@ -1564,8 +1605,8 @@ StaStatus sta_plan_tasks(const StaNetlistDesc* nl, const StaLibrary* lib, int32_
 
 StaStatus sta_query_slack(StaHandle* h, float* wns_tns, float* pin_slack, float* endpoint_slack) {
     if (!h || !wns_tns) return set_err(STA_ERR_INVALID_ARG, "null argument");
-    if (h->batch() || h->nl > 1)
-        return set_err(STA_ERR_STATE, "sta_query_slack: single-placement handles (use the queries)");
+    if (h->batch() || h->nl > 1 || h->lay.G > 1)
+        return set_err(STA_ERR_STATE, "sta_query_slack: single-placement, single-netlist handles (use the queries)");
     double sum[STA_SUM_COUNT];
     StaStatus st = sta_query_summary(h, sum, 0, nullptr);
     if (st != STA_OK) return st;

@@ -493,13 +493,20 @@ __device__ __forceinline__ SinkPre sink_pre(const DevState& s, const DfState& d,
     if (q.cons < 0) {
         q.rat = reinterpret_cast<const float4*>(s.rat)[p];
         if ((mode & 2) && isfinite(q.rat.z)) {
+            SeedCtx c = sc;
+            if (d.pin_grp) {  // several netlists: the endpoint's own WNS_gamma and weights
+                const int gi = d.pin_grp[p];
+                c.W = (float)s.summary[(size_t)gi * STA_SUM_COUNT + STA_SUM_WNS_GAMMA];
+                c.wt = s.params[2 * gi];
+                c.ww = s.params[2 * gi + 1];
+            }
             const float2 z = reinterpret_cast<const float2*>(s.ats)[p];
             const float sr = q.rat.z - z.x, sf = q.rat.w - z.y;
             const float te = softmin3(sr, sf, gamma);
-            float gr = sc.wt * expf(-(sr - te) / gamma), gf = sc.wt * expf(-(sf - te) / gamma);
-            if (isfinite(sc.W)) {
-                gr += sc.ww * expf(-(sr - sc.W) / gamma);
-                gf += sc.ww * expf(-(sf - sc.W) / gamma);
+            float gr = c.wt * expf(-(sr - te) / gamma), gf = c.wt * expf(-(sf - te) / gamma);
+            if (isfinite(c.W)) {
+                gr += c.ww * expf(-(sr - c.W) / gamma);
+                gf += c.ww * expf(-(sf - c.W) / gamma);
             }
             q.ga = make_float2(-gr, -gf);
         }

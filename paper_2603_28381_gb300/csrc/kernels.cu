@@ -416,10 +416,24 @@ __global__ void __launch_bounds__(kBlock) k_ep(DevNet g, DevState s0, float gamm
                                                const uchar4* __restrict__ rs_mask, int P, float* rs_part0,
                                                int rs_part_words) {
     if (s0.active && (int)blockIdx.y >= *s0.active) return;  // a lane this call does not run
-    const DevState s = lane_state(s0, blockIdx.y);            // one lane per grid row
-    float* rs_part = lane_ptr(rs_part0, (size_t)blockIdx.y * s0.lane_bytes);
+    // grid row: a lane (its own state), or with several netlists a netlist (its
+    // endpoint range, partials, counter and summary; the reset is spread over
+    // every block of the grid)
+    const bool grp = g.G > 1;
+    const int gi = grp ? (int)blockIdx.y : 0;
+    DevState s = grp ? s0 : lane_state(s0, blockIdx.y);
+    float* rs_part = grp ? rs_part0 : lane_ptr(rs_part0, (size_t)blockIdx.y * s0.lane_bytes);
+    int e0 = 0, e1 = g.E;
+    if (grp) {
+        e0 = g.grp_ep[gi];
+        e1 = g.grp_ep[gi + 1];
+        s.red += (size_t)gi * gridDim.x * (sizeof(EpAcc) / sizeof(double));
+        s.summary += (size_t)gi * STA_SUM_COUNT;
+        s.ep_count += gi;
+    }
+    // (relative to the netlist's first endpoint: the same blocks and order as alone)
     EpAcc acc = ep_identity();
-    for (int e = blockIdx.x * kBlock + threadIdx.x; e < g.E; e += gridDim.x * kBlock) {
+    for (int e = e0 + blockIdx.x * kBlock + threadIdx.x; e < e1; e += gridDim.x * kBlock) {
         const int p = g.ep_pin[e];
         float4 con;
         // a clocked endpoint's bounds are this analysis's required-time seeds
@@ -452,12 +466,13 @@ __global__ void __launch_bounds__(kBlock) k_ep(DevNet g, DevState s0, float gamm
     }
     if (rs_mask) {
         const float u = __uint_as_float(kUnwritten);
-        for (int i = blockIdx.x * kBlock + threadIdx.x; i < rs_part_words; i += gridDim.x * kBlock) rs_part[i] = u;
+        const int bx = grp ? (int)(blockIdx.y * gridDim.x + blockIdx.x) : (int)blockIdx.x;
+        const int stride = (grp ? (int)(gridDim.x * gridDim.y) : (int)gridDim.x) * kBlock;
+        for (int i = bx * kBlock + threadIdx.x; i < rs_part_words; i += stride) rs_part[i] = u;
         // four grid strides per step: the four mask bytes are loaded together, and
         // consecutive threads store consecutive pins
-        const int stride = gridDim.x * kBlock;
         const uint8_t* mk = reinterpret_cast<const uint8_t*>(rs_mask);
-        for (int p0 = blockIdx.x * kBlock + threadIdx.x; p0 < P; p0 += 4 * stride) {
+        for (int p0 = bx * kBlock + threadIdx.x; p0 < P; p0 += 4 * stride) {
             unsigned m[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) m[j] = p0 + j * stride < P ? mk[p0 + j * stride] : 0u;
@@ -489,7 +504,7 @@ __global__ void __launch_bounds__(kBlock) k_ep(DevNet g, DevState s0, float gamm
         o[STA_SUM_WNS_GAMMA] =
             (lse && acc.wsum > 0.f) ? (double)acc.wmin - (double)gamma * log((double)acc.wsum) : (double)kInf;
         o[STA_SUM_LATE_VIOLATIONS] = acc.viol;
-        o[STA_SUM_NUM_ENDPOINTS] = g.E;
+        o[STA_SUM_NUM_ENDPOINTS] = e1 - e0;
         *s.ep_count = 0;
     }
 }
@@ -514,12 +529,18 @@ __global__ void __launch_bounds__(kBlock) k_seed(DevNet g, DevState s, float gam
 __global__ void __launch_bounds__(kBlock) k_cap_seed(DevNet g, DevState s0, float gamma) {
     if (s0.active && (int)blockIdx.y >= *s0.active) return;  // a lane this call does not run
     const DevState s = lane_state(s0, blockIdx.y);            // one lane per grid row
-    const float W = (float)s.summary[STA_SUM_WNS_GAMMA];
-    const float wt = s.params[0], ww = s.params[1];
+    float W = (float)s.summary[STA_SUM_WNS_GAMMA];
+    float wt = s.params[0], ww = s.params[1];
     for (int e = blockIdx.x * kBlock + threadIdx.x; e < g.E; e += gridDim.x * kBlock) {
         float4 con;
         const int k = ep_bounds(g, s, e, con);
         if (k < 0) continue;
+        if (g.G > 1) {  // several netlists: the endpoint's own WNS_gamma and weights
+            const int gi = g.pin_grp[g.ep_pin[e]];
+            W = (float)s.summary[(size_t)gi * STA_SUM_COUNT + STA_SUM_WNS_GAMMA];
+            wt = s.params[2 * gi];
+            ww = s.params[2 * gi + 1];
+        }
         const float2 gl = ep_dloss(con, reinterpret_cast<const float2*>(s.ats)[g.ep_pin[e]], gamma, W, wt, ww);
         s.cap_seed[k] = gl.x + gl.y;
     }
@@ -585,7 +606,7 @@ void launch_fwd_level(const DevNet& g, const DevState& s, int w0, int nw, int c0
 
 void launch_endpoints(const DevNet& g, const DevState& s, float gamma, int lse, cudaStream_t st, const DfState* d,
                       int P) {
-    const dim3 grid(kEpBlocks, s.nl);
+    const dim3 grid = g.G > 1 ? dim3(g.ep_gx, g.G) : dim3(kEpBlocks, s.nl);
     if (d) k_ep<<<grid, kBlock, 0, st>>>(g, s, gamma, lse, d->pin_mask, P, d->apart, d->npart * kPartFloats);
     else k_ep<<<grid, kBlock, 0, st>>>(g, s, gamma, lse, nullptr, 0, nullptr, 0);
 }

@@ -32,6 +32,12 @@ struct DevNet {
     float r, c;                  // Ohm/um, fF/um
     int32_t P, Pnet, N, E;
     int32_t nrc;                 // RC chunks
+    // several netlists in one handle (sta_create_multi; G = 1 and nulls otherwise):
+    // per netlist its endpoint range, summary, loss weights and reduction counter
+    const int32_t* grp_ep;       // [G+1] endpoint range of each netlist
+    const int32_t* pin_grp;      // [P] netlist of each pin
+    int32_t G;                   // netlists
+    int32_t ep_gx;               // endpoint-reduction blocks per netlist
 };
 
 // Mutable per-call state (internal order unless stated).
@@ -48,14 +54,14 @@ struct DevState {
     float* g_slew;     // [P*2] adjoint of the late slews
     float2* grad;      // [P] d loss / d (x, y), ORIGINAL pin order
     float2* ep_slack;  // [E] (early, late)
-    double* red;       // [kEpBlocks * 8] endpoint-reduction partials (scratch)
-    double* summary;   // [STA_SUM_COUNT]
-    float* params;     // [4] w_tns, w_wns
+    double* red;       // [G][ep_gx] endpoint-reduction partials (scratch, 48 bytes each)
+    double* summary;   // [G][STA_SUM_COUNT]
+    float* params;     // [G][2] w_tns, w_wns (padded to 4 floats)
     float* cap_seed;   // [P] d loss / d (rising arrival) of capturing clock pins, 0 elsewhere;
                        // null without a propagated clock
     float* rc_part;    // [rc_slots] partial loads of the nets split into several RC chunks
     int32_t* rc_count; // [rc_slots] chunks done (0 between launches: the last chunk resets it)
-    int32_t* ep_count; // [1] endpoint blocks done (0 between launches)
+    int32_t* ep_count; // [G] endpoint blocks done (0 between launches)
     // Independent placements ("lanes") of one handle: every array above of lane
     // l sits l * lane_bytes after lane 0's (one slab per lane, same layout).
     size_t lane_bytes;
@@ -116,6 +122,7 @@ struct DfState {
     float* net_gload;        // [N] d loss / d load of large nets
     int32_t* abort_word;     // [2] [0] a bounded wait of the current sweep expired, [1] sticky copy
     const uint8_t* pin_keep; // [P] 1: the forward sweep does not write the pin (asserted values)
+    const int32_t* pin_grp;  // [P] several netlists: each pin's (DevNet::pin_grp), else null
     const uchar4* pin_mask;  // [P/4 rounded up] Layout::pin_mask (read a byte per pin)
     int32_t TF, TB;
     int32_t npart;           // partial records of the backward sweeps

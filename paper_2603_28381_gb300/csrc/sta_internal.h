@@ -94,6 +94,12 @@ struct Layout {
     std::vector<int32_t> baux;       // [TB]
     std::vector<int32_t> pin_cons;   // [P] backward task whose arc step writes the pin's RAT / adjoint
     std::vector<uint8_t> pin_keep;   // [P] 1 if no forward task writes the pin (asserted drivers, clock pins)
+    // several netlists in one layout (sta_create_multi): G netlists, the
+    // endpoint range of each (grp_ep [G+1], description order = layout order)
+    // and the netlist of each device pin (pin_grp [P]); G = 1 and both empty
+    // for one netlist
+    int32_t G = 1;
+    std::vector<int32_t> grp_ep, pin_grp;
     std::vector<uint8_t> pin_mask;   // [P rounded up to 4] bit 0: words of the pin the forward sweep polls
                                      // (a cell input it writes), bit 1: the backward's (a cell input)
     // dependency counts and consumer lists: a task may start once `indeg` of its
@@ -142,6 +148,22 @@ StaStatus build_tasks(Layout& o, const TaskShape& sh, std::string& err);
 // Processing order of description nets and device pin order (sta_levelize).
 StaStatus ordering(const StaNetlistDesc& nl, std::vector<int32_t>& net_level, int32_t& num_levels,
                    std::vector<int32_t>& net_order, std::vector<int32_t>& pin_order, std::string& err);
+
+// The disjoint union of `count` netlists over one library (sta_create_multi):
+// netlist k's pins, nets, cells, startpoints and endpoints follow those of
+// netlists 0..k-1, its pin indices shifted by the pins before it.  The wire
+// parameters must agree (INVALID_ARG otherwise); build_layout validates the rest.
+struct UnionNetlist {
+    std::vector<int32_t> net_ptr, net_pins, cell_type, cell_in_ptr, cell_in_pins, cell_out_pin, start_pins, end_pins,
+        end_clock;
+    std::vector<float> pin_cap, start_at, start_slew, end_rat;
+    std::vector<int32_t> pin_off, end_off;  // [count + 1] first pin / endpoint of each netlist
+    StaNetlistDesc nl{};
+};
+StaStatus build_union(const StaNetlistDesc* const* nls, int32_t count, UnionNetlist& u, std::string& err);
+
+// The netlist groups of a union's layout: endpoint ranges and each device pin's netlist.
+void set_groups(Layout& o, const UnionNetlist& u);
 
 // A netlist's host layout built once and shared by the handles created from
 // it with sta_create_from_layout: the serving layer keeps one per registered

@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol(sta):
     for name in sorted(declared):
         assert hasattr(lib, name), f"libsta.so does not export {name}"
     assert set(sta._sta.EXPORTS) == declared
-    assert sta.sta_abi_version() == 4
+    assert sta.sta_abi_version() == 5
 
 
 @pytest.mark.parametrize("make", [lambda: netgen.tiny_design(0), lambda: netgen.tiny_design(5),
@@ -238,3 +238,30 @@ def test_noalloc_summary_refuses_misaligned_pointers(sta):
                                                   a["end_clk"], 4, 10.0, a["ep_slack"], a["summary"], 0)
         assert e.value.status == 1, name  # STA_ERR_INVALID_ARG
         assert "misaligned" in sta.sta_last_error(), name
+
+
+def test_multi_rejects_bad_unions_before_any_device_use(sta):
+    # sta_create_multi checks the netlists and builds the union's layout on the
+    # host; these are refused there, with the documented status codes
+    from paper_2603_28381_gb300 import _sta
+    a = netgen.superblue_like(3, scale=0.002, depth=10)
+    b = netgen.superblue_like(4, scale=0.002, depth=10)
+    with pytest.raises(sta.StaError) as e:
+        _sta.sta_create_multi([], a.library)
+    assert e.value.status == 1 and "count" in sta.sta_last_error()
+    odd = netgen.superblue_like(4, scale=0.002, depth=10).netlist
+    odd.r_per_um = 0.25
+    with pytest.raises(sta.StaError) as e:
+        _sta.sta_create_multi([a.netlist, odd], a.library)
+    assert e.value.status == 1 and "r_per_um" in sta.sta_last_error()
+    # a combinational loop in the second netlist: the union is not a DAG
+    bl = netgen.NetlistBuilder()
+    i0, o0, i1, o1 = (bl.pin(1.0) for _ in range(4))
+    bl.net(o0, [i1])
+    bl.net(o1, [i0])
+    bl.cell(0, [i0], o0)
+    bl.cell(0, [i1], o1)
+    loop, _ = bl.build()
+    with pytest.raises(sta.StaError) as e:
+        _sta.sta_create_multi([a.netlist, loop, b.netlist], a.library)
+    assert e.value.status == 2  # STA_ERR_NOT_DAG
