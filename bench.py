@@ -80,7 +80,7 @@ def parse():
                     help="serve: requests of one netlist merged into one batched launch in the merged mode")
     ap.add_argument("--tile-pins", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
-    ap.add_argument("--batch-sweep", default="levels", choices=["levels", "dataflow"])
+    ap.add_argument("--batch-sweep", default="levels", choices=["levels", "dataflow", "wide"])
     ap.add_argument("--clock-nets", type=int, default=0,
                     help="single: propagate the clock over this many clock nets (0: ideal clock)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -613,7 +613,7 @@ def run_batch(args, emit=True):
     tune = None
     if not args.no_autotune:  # untimed: pick the task shape on this workload
         eng.set_positions(xyb)
-        best, table = eng.autotune(tile_pins=(1, 2, 4), chunks=(8, 16, 32), sweeps=("levels", "dataflow"),
+        best, table = eng.autotune(tile_pins=(1, 2, 4), chunks=(8, 16, 32), sweeps=("levels", "dataflow", "wide"),
                                    reps=3, gamma=GAMMA)
         args.tile_pins, args.chunk, args.batch_sweep = best
         tune = {"best": {"tile_pins": best[0], "chunk": best[1], "batch_sweep": best[2]},

@@ -143,9 +143,13 @@ typedef struct {
  *   LEVELS    one launch per level (two per level in the backward where a level
  *             has nets split into chunks), replayed as a CUDA graph; the tasks
  *             of a level run without any waiting.
- *   DATAFLOW  one persistent launch per sweep with per-task dependency
- *             counters, as in STA_SCHED_DATAFLOW.
- * Both give bit-identical results.
+ *   DATAFLOW  one persistent launch per sweep whose tasks wait on the data
+ *             words they read, as in STA_SCHED_DATAFLOW; a warp takes a task
+ *             for 8 placements x 4 timing conditions.
+ *   WIDE      as DATAFLOW, but a warp takes a task for 32 placements and each
+ *             lane runs the four timing conditions of its placement (more
+ *             independent memory round trips per warp).
+ * LEVELS, DATAFLOW and WIDE give bit-identical results.
  *   LANES     the placements as independent lanes of the single-placement
  *             dataflow sweeps (STA_SCHED_DATAFLOW): each placement has its own
  *             state, laid out as for one placement, and one persistent launch
@@ -156,6 +160,7 @@ typedef struct {
 #define STA_BATCH_LEVELS 0
 #define STA_BATCH_DATAFLOW 1
 #define STA_BATCH_LANES 2
+#define STA_BATCH_WIDE 3
 
 typedef struct StaHandle StaHandle;
 
@@ -199,9 +204,10 @@ StaStatus sta_create_multi(const StaNetlistDesc *const *nls, int32_t count, cons
                            const StaOptions *opts, StaHandle **out);
 
 /* Set pin positions xy [num_pins][2] (um, the netlist's pin order).  xy is a
- * device pointer if on_device != 0, else host memory (copied through pinned
- * staging inside this call).  The positions are copied; the caller may reuse
- * xy when the call's work on `stream` completes. */
+ * device pointer if on_device != 0 (8-byte aligned: it is read as float2;
+ * INVALID_ARG otherwise, before any device work), else host memory (copied
+ * through pinned staging inside this call).  The positions are copied; the
+ * caller may reuse xy when the call's work on `stream` completes. */
 StaStatus sta_set_positions(StaHandle *h, const float *xy, int on_device, void *stream);
 
 /* One forward pass: net RC for every net (Eqs. 1-3), then, level by level,
@@ -220,8 +226,9 @@ StaStatus sta_forward(StaHandle *h, uint32_t flags, float gamma, void *stream);
  * pin positions, by a hand-written adjoint swept over the levels in reverse
  * (Section 3.2).  w is a device pointer if w_on_device != 0, else host.  The
  * result goes to grad_xy [num_pins][2] in the netlist's pin order, a device
- * pointer if on_device != 0, else host memory (this call then synchronizes
- * `stream`).  Requires a preceding sta_forward with STA_FWD_LSE (STATE).
+ * pointer if on_device != 0 (8-byte aligned; a device w 4-byte aligned; else
+ * INVALID_ARG before any device work), else host memory (this call then
+ * synchronizes `stream`).  Requires a preceding sta_forward with STA_FWD_LSE (STATE).
  * The sweep waits for the forward's arrival-time pass only, so it overlaps the
  * forward's required-time sweep on the GPU (operation fusion, Section 3.2).
  * Positions, forward state and the gradient buffer are shared by every call on
@@ -288,7 +295,8 @@ StaStatus sta_query_summary(StaHandle *h, double *out, int on_device, void *stre
 /* Per-pin results in the netlist's pin order (any output may be NULL):
  * at, slew, rat [num_pins][4]; ats [num_pins][2] (late rise/fall LSE arrival);
  * slack [num_pins][2] (early, late; minimum over rise/fall).  Device pointers if
- * on_device != 0 (asynchronous), else host (synchronizes `stream`). */
+ * on_device != 0 (asynchronous; 4-byte aligned, slack 8-byte aligned, else
+ * INVALID_ARG before any device work), else host (synchronizes `stream`). */
 StaStatus sta_query_pins(StaHandle *h, float *at, float *slew, float *rat, float *ats,
                          float *slack, int on_device, void *stream);
 

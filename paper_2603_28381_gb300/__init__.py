@@ -64,7 +64,7 @@ class StaEngine:
         self.h = _sta.sta_create(netlist, library, use_graphs, profile, sched,
                                  self.B if self.batched else 0, tile_pins, chunk,
                                  {"levels": _sta.BATCH_LEVELS, "dataflow": _sta.BATCH_DATAFLOW,
-                                  "lanes": _sta.BATCH_LANES}[batch_sweep],
+                                  "lanes": _sta.BATCH_LANES, "wide": _sta.BATCH_WIDE}[batch_sweep],
                                  grid_blocks)
         self.sizes = _sta.sta_query_sizes(self.h)
         self.sizes["nets_desc"] = int(netlist.num_nets)
@@ -174,7 +174,7 @@ class StaEngine:
         """Pick the batched schedule's task shape by timing each candidate on the
         current positions (sta_autotune).  Returns (best, table): best =
         (tile_pins, chunk, sweep name), table = {(tile_pins, chunk, sweep): ms}."""
-        names = {"levels": _sta.BATCH_LEVELS, "dataflow": _sta.BATCH_DATAFLOW}
+        names = {"levels": _sta.BATCH_LEVELS, "dataflow": _sta.BATCH_DATAFLOW, "wide": _sta.BATCH_WIDE}
         inv = {v: k for k, v in names.items()}
         best, ms = _sta.sta_autotune(self.h, list(tile_pins), list(chunks), [names[s] for s in sweeps], reps, gamma)
         table = {(int(a), int(c), s): float(ms[i, j, k]) for i, a in enumerate(tile_pins)

@@ -53,6 +53,7 @@ SCHED_BATCH = 2
 BATCH_LEVELS = 0
 BATCH_DATAFLOW = 1
 BATCH_LANES = 2
+BATCH_WIDE = 3
 
 
 class StaServerOptions(ctypes.Structure):

@@ -1,6 +1,6 @@
 """Build libsta.so (the C-ABI library) in-tree for sm_103a.
 
-Five translation units are compiled in parallel (four CUDA, one host C++) and
+The translation units are compiled in parallel (CUDA and one host C++ file) and
 linked with a static CUDA runtime into ``paper_2603_28381_gb300/_build/libsta.so``.
 """
 from __future__ import annotations
@@ -19,7 +19,12 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libsta.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "dataflow.cu", "batch.cu", "capi.cu", "builder.cpp", "noalloc.cu", "serve.cu", "cte.cu"]
+SOURCES = ["kernels.cu", "dataflow.cu", "batch.cu", "batch_wide.cu", "capi.cu", "builder.cpp", "noalloc.cu", "serve.cu",
+           "cte.cu"]
+# The two batched sweeps (a lane per placement and condition, a lane per
+# placement) must round alike: no implicit multiply-add contraction, whose
+# choice can differ with the surrounding code; explicit fmaf() calls stay fused.
+PER_FILE = {"batch.cu": ["-fmad=false"], "batch_wide.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -46,7 +51,7 @@ def build(force: bool = False, verbose: bool = False, extra: tuple = ()) -> str:
         obj = os.path.join(OUT_DIR, src + ".o")
         path = os.path.join(CSRC, src)
         if src.endswith(".cu"):
-            cmd = [nvcc, *ARCH, "-lineinfo", *common, *extra, "-c", path, "-o", obj]
+            cmd = [nvcc, *ARCH, "-lineinfo", *common, *PER_FILE.get(src, []), *extra, "-c", path, "-o", obj]
         else:
             cmd = [nvcc, *common, *extra, "-x", "c++", "-c", path, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)

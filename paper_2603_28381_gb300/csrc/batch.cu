@@ -18,32 +18,10 @@
 // results are bit-identical alone and in a batch.
 #include <algorithm>
 
-#include "dataflow_sync.cuh"
-#include "device_common.cuh"
+#include "batch_common.cuh"
 
 namespace sta {
 namespace {
-
-__device__ __forceinline__ size_t ix(int row, int Bp, int b) { return (size_t)row * Bp + b; }
-
-// ---------------------------------------------------------------------------
-// Wire step of one sink (Eqs. 1-3 on a star) -- same arithmetic as the
-// single-placement kernels.
-// ---------------------------------------------------------------------------
-struct Wire {
-    float D, I, dist;  // Elmore delay, impulse, Manhattan distance
-};
-
-__device__ __forceinline__ Wire wire(const DevNet& g, float2 xy, float2 xyd, float cap) {
-    Wire w;
-    w.dist = fabsf(xy.x - xyd.x) + fabsf(xy.y - xyd.y);
-    const float R = g.r * w.dist;
-    const float C = fmaf(0.5f * g.c, w.dist, cap);
-    w.D = R * C * kKrc;
-    const float m = 2.f * R * C * w.D * kKrc - w.D * w.D;
-    w.I = sqrtf(fmaxf(m, 0.f));
-    return w;
-}
 
 // ---------------------------------------------------------------------------
 // Lanes: 8 placements x 4 timing conditions per warp (lane = 4 * placement +
@@ -119,19 +97,6 @@ __device__ __forceinline__ FCell fcell(const DevNet& g, const DfState& d, int n,
     return f;
 }
 
-// slew segment and fraction from the registers of FCell (same result as axis_seg)
-__device__ __forceinline__ void seg_reg(const float* sidx, const float* sinv, float v, int& is, float& ts) {
-    float base = sidx[0], inv = sinv[0];
-    is = 0;
-#pragma unroll
-    for (int j = 1; j <= 5; ++j)
-        if (sidx[j] <= v) {
-            base = sidx[j];
-            inv = sinv[j];
-            is = j;
-        }
-    ts = (v - base) * inv;
-}
 
 struct FOut {
     float at, sl, z;  // arrival, slew, LSE arrival (late conditions) of this lane's condition
@@ -487,9 +452,6 @@ __global__ void k_bep2(DevNet g, BatchState bs, float gamma, int lse, int nparts
 // Every lane carries the required time of its condition; the late lanes (one
 // per output transition) carry the adjoint.
 // ---------------------------------------------------------------------------
-struct BSeed {
-    float W, wt, ww;  // WNS_gamma of this placement, w_tns, w_wns
-};
 
 // One lane's part of a driver cell's backward step, all from forward results:
 // the arc delays of its condition (required times) and, on late lanes, the LSE
@@ -661,13 +623,6 @@ __device__ __forceinline__ BSink bsink(const DevNet& g, const BatchState& bs, co
     return s;
 }
 
-// d loss / d (x, y) of a sink from its wire adjoint and the net's d loss / d load
-__device__ __forceinline__ float2 bsink_grad(const DevNet& g, float2 xy, float2 xyd, float cap, float gwire,
-                                             float gload) {
-    const float dx = xy.x - xyd.x, dy = xy.y - xyd.y;
-    const float gd = fmaf(gload, g.c, gwire * kKrc * g.r * fmaf(g.c, fabsf(dx) + fabsf(dy), cap));
-    return make_float2(gd * ((dx > 0.f) - (dx < 0.f)), gd * ((dy > 0.f) - (dy < 0.f)));
-}
 
 __device__ __forceinline__ float late_slew_of_driver(const BatchState& bs, int dp, const Lane& L) {
     return L.el ? bs.slew[ix(4 * dp + 2 + L.rf, bs.Bp, L.b)] : 0.f;

@@ -1,0 +1,718 @@
+// batch_wide.cu -- the batched dataflow sweeps with a lane per placement.
+//
+// Same tasks, queue and polled data words as the batched dataflow sweeps of
+// batch.cu, same per-placement layout value[row * Bp + b], but a warp takes a
+// task for 32 placements and each lane runs all four timing conditions of its
+// placement (early / late x rise / fall).  A warp task then carries four
+// independent chains of memory round trips per lane instead of one, and a
+// task's topology loads serve 32 placements instead of 8: the sweeps are bound
+// by each warp's chain of dependent loads, so this is what raises the memory
+// parallelism per SM.  Queue index q = task * G + group (G = Bp / 32).
+//
+// Every value is computed with the same operations in the same order as in
+// batch.cu: where the lanes of a quad exchanged values there (the net load's
+// four interleaved partial sums, the sink wire adjoints of the two late
+// conditions, the quad sums of d loss / d load and of the driver's gradient),
+// one lane now adds the same terms in the same association, so the results
+// are bit-identical to the narrow sweeps.
+#include <algorithm>
+
+#include "batch_common.cuh"
+
+namespace sta {
+namespace {
+
+struct WLane {
+    int lane, b;  // b = placement
+};
+
+__device__ __forceinline__ WLane wlane(int gw) {
+    WLane L;
+    L.lane = threadIdx.x & 31;
+    L.b = gw * 32 + L.lane;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Forward
+// ---------------------------------------------------------------------------
+
+// The driver cell of net n for one placement: as FCell of batch.cu, with the
+// input transitions of both output transitions (rfi[rf], bit k for arc k).
+struct WCell {
+    int t, na, dyn;
+    int rfi[2];
+    int pin[STA_MAX_ARCS];
+    int jl;
+    float ul;
+    float sidx[6], sinv[6];
+};
+
+__device__ __forceinline__ WCell wcell(const DevNet& g, int n, float ld) {
+    WCell f;
+    const int4 q0 = __ldg(g.net_desc + 2 * n), q1 = __ldg(g.net_desc + 2 * n + 1);  // one record
+    f.t = q0.x;
+    f.na = q0.z;
+    f.rfi[0] = f.rfi[1] = 0;
+    f.dyn = q0.w & 15;
+    f.jl = 0;
+    f.ul = 0.f;
+    f.pin[0] = q1.x;
+    f.pin[1] = q1.y;
+    f.pin[2] = q1.z;
+    f.pin[3] = q1.w;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) f.sidx[j] = f.sinv[j] = 0.f;
+    if (f.t < 0) return f;
+    const int un = q0.w >> 4;
+#pragma unroll
+    for (int rf = 0; rf < 2; ++rf)
+#pragma unroll
+        for (int k = 0; k < STA_MAX_ARCS; ++k)
+            if (k < f.na) f.rfi[rf] |= (rf ^ ((un >> k) & 1)) << k;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        f.sidx[j] = __ldg(g.lib_idx + f.t * kLibStride + j);
+        f.sinv[j] = __ldg(g.lib_inv + f.t * kLibStride + j);
+    }
+    const float* li = g.lib_idx + f.t * kLibStride + 8;
+    f.jl = axis_seg(li, ld);
+    f.ul = (ld - __ldg(li + f.jl)) * __ldg(g.lib_inv + f.t * kLibStride + 8 + f.jl);
+    return f;
+}
+
+struct WOut {
+    float at[4], sl[4], z[2];  // by condition c = 2 el + rf; LSE arrival by rf (late)
+};
+
+// The driver cell for the four conditions of one placement.  The fanin words
+// of every arc (its pin's four arrival and slew rows and two LSE-arrival rows)
+// are loaded together; in the dataflow sweep this is the wait, repeated until
+// every word written during the sweep holds its value.
+__device__ __forceinline__ WOut wcell_eval(const DevNet& g, const BatchState& bs, const WCell& f, int dp, int b,
+                                           float gamma, bool lse, int32_t* abort_word, bool stall) {
+    const int Bp = bs.Bp;
+    WOut o;
+    if (f.t < 0) {  // asserted driver: constant values set at creation
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            o.at[c] = bs.at[ix(4 * dp + c, Bp, b)];
+            o.sl[c] = bs.slew[ix(4 * dp + c, Bp, b)];
+        }
+        o.z[0] = lse ? bs.ats[ix(2 * dp, Bp, b)] : 0.f;
+        o.z[1] = lse ? bs.ats[ix(2 * dp + 1, Bp, b)] : 0.f;
+        return o;
+    }
+    float ain[STA_MAX_ARCS][4], sin[STA_MAX_ARCS][4], zin[STA_MAX_ARCS][2];
+    auto load = [&]() {
+        bool ok = !stall;  // the test hook's stalled task never sees its inputs
+#pragma unroll
+        for (int k = 0; k < STA_MAX_ARCS; ++k) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ain[k][j] = sin[k][j] = 0.f;
+            zin[k][0] = zin[k][1] = 0.f;
+            if (k < f.na) {
+                bool w = true;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {  // row 4 pin + j: condition j of the fanin pin
+                    ain[k][j] = ld_relaxed_f(bs.at + ix(4 * f.pin[k] + j, Bp, b));
+                    sin[k][j] = ld_relaxed_f(bs.slew + ix(4 * f.pin[k] + j, Bp, b));
+                    w &= written(ain[k][j]) & written(sin[k][j]);
+                }
+                if (lse) {
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        zin[k][r] = ld_relaxed_f(bs.ats + ix(2 * f.pin[k] + r, Bp, b));
+                        w &= written(zin[k][r]);
+                    }
+                }
+                if ((f.dyn >> k) & 1) ok &= w;
+            }
+        }
+        return ok;
+    };
+    poll_words(load, abort_word);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int el = c >> 1, rf = c & 1;
+        float best_at = el ? -kInf : kInf, best_sl = el ? -kInf : kInf, m = -kInf;
+        float cand[STA_MAX_ARCS];
+#pragma unroll
+        for (int k = 0; k < STA_MAX_ARCS; ++k) {
+            cand[k] = -kInf;
+            if (k < f.na) {
+                // the input transition r is data: select between registers
+                // (a runtime index would put the arrays in local memory)
+                const bool r = (f.rfi[rf] >> k) & 1;
+                const float sv = r ? sin[k][2 * el + 1] : sin[k][2 * el];
+                const float av = r ? ain[k][2 * el + 1] : ain[k][2 * el];
+                const float zv = r ? zin[k][1] : zin[k][0];
+                int is;
+                float ts;
+                seg_reg(f.sidx, f.sinv, sv, is, ts);
+                float4 dq, sq;
+                cell_corners(g, f.t, k, rf, is, f.jl, dq, sq);
+                const float D = lerp_cell(dq, ts, f.ul);
+                const float S = lerp_cell(sq, ts, f.ul);
+                const float v = av + D;
+                best_at = el ? fmaxf(best_at, v) : fminf(best_at, v);
+                best_sl = el ? fmaxf(best_sl, S) : fminf(best_sl, S);
+                cand[k] = (el ? zv : 0.f) + D;
+                m = fmaxf(m, cand[k]);
+            }
+        }
+        o.at[c] = best_at;
+        o.sl[c] = best_sl;
+        if (el) o.z[rf] = lse ? lse_arcs(cand, f.na, m, gamma) : 0.f;
+    }
+    return o;
+}
+
+__device__ __forceinline__ void wstore_pin(const BatchState& bs, int p, int b, const float* at, const float* sl,
+                                           const float* z, bool lse) {
+    const int Bp = bs.Bp;  // strong stores: words that other tasks of the sweep poll
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        st_relaxed_f(bs.at + ix(4 * p + c, Bp, b), at[c]);
+        st_relaxed_f(bs.slew + ix(4 * p + c, Bp, b), sl[c]);
+    }
+    if (lse) {
+        st_relaxed_f(bs.ats + ix(2 * p, Bp, b), z[0]);
+        st_relaxed_f(bs.ats + ix(2 * p + 1, Bp, b), z[1]);
+    }
+}
+
+// wire step to the sinks [s0, s1), all four conditions
+__device__ __forceinline__ void wstore_sinks(const DevNet& g, const BatchState& bs, int s0, int s1, int b, float2 xyd,
+                                             const WOut& o, bool lse) {
+#pragma unroll 2
+    for (int p = s0; p < s1; ++p) {
+        const Wire w = wire(g, bs.xy[ix(p, bs.Bp, b)], xyd, __ldg(g.pin_cap + p));
+        float at[4], sl[4], z[2];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            at[c] = o.at[c] + w.D;
+            sl[c] = sqrtf(fmaf(o.sl[c], o.sl[c], w.I * w.I));
+        }
+        z[0] = o.z[0] + w.D;
+        z[1] = o.z[1] + w.D;
+        wstore_pin(bs, p, b, at, sl, z, lse);
+    }
+}
+
+// net load (Eq. 1): four interleaved partial sums over sinks c, c + 4, ...,
+// added as (s0 + s1) + (s2 + s3), then the driver's pin capacitance
+__device__ __forceinline__ float wnet_load(const DevNet& g, const BatchState& bs, int dp, int s1, int b, float2 xyd) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        for (int p = dp + 1 + c; p < s1; p += 4) {
+            const float2 xy = bs.xy[ix(p, bs.Bp, b)];
+            const float dist = fabsf(xy.x - xyd.x) + fabsf(xy.y - xyd.y);
+            acc[c] += fmaf(g.c, dist, __ldg(g.pin_cap + p));
+        }
+    return __ldg(g.pin_cap + dp) + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+}
+
+template <bool lse>
+__device__ void wfwd_nets(const DevNet& g, const BatchState& bs, const DfState& d, int n0, int nn, int b,
+                          float gamma, bool stall) {
+    const int Bp = bs.Bp;
+    for (int j = 0; j < nn; ++j) {
+        const int n = n0 + j;
+        const int dp = g.net_ptr[n], e = g.net_ptr[n + 1];
+        const float2 xyd = bs.xy[ix(dp, Bp, b)];
+        const float ld = wnet_load(g, bs, dp, e, b, xyd);
+        bs.load[ix(n, Bp, b)] = ld;
+        const WCell f = wcell(g, n, ld);
+        const WOut o = wcell_eval(g, bs, f, dp, b, gamma, lse, d.abort_word, stall);
+        if (f.t >= 0) wstore_pin(bs, dp, b, o.at, o.sl, o.z, lse);
+        wstore_sinks(g, bs, dp + 1, e, b, xyd, o, lse);
+    }
+}
+
+// chunk of a large net: its load comes from the prologue; every chunk
+// evaluates the driver cell, the first one stores it
+template <bool lse>
+__device__ void wfwd_chunk(const DevNet& g, const BatchState& bs, const DfState& d, int n, int p0, int cnt, int b,
+                           float gamma, bool stall) {
+    const int Bp = bs.Bp;
+    const int dp = g.net_ptr[n];
+    const float2 xyd = bs.xy[ix(dp, Bp, b)];
+    const WCell f = wcell(g, n, bs.load[ix(n, Bp, b)]);
+    const WOut o = wcell_eval(g, bs, f, dp, b, gamma, lse, d.abort_word, stall);
+    if (f.t >= 0 && p0 == dp + 1) wstore_pin(bs, dp, b, o.at, o.sl, o.z, lse);
+    wstore_sinks(g, bs, p0, p0 + cnt, b, xyd, o, lse);
+}
+
+template <bool lse>
+__global__ void __launch_bounds__(kBlock, 2) k_bfwd_w(DevNet g, BatchState bs, DfState d, float gamma, int stall_task) {
+    const int G = bs.G;
+    const int Q = d.TF * G;
+    int q = grab(d.heads + 0);
+    while (q < Q) {
+        const int t = q / G, gw = q - t * G;
+        const WLane L = wlane(gw);
+        const int4 task = d.ftask[t];
+        if (task.y > 0) wfwd_nets<lse>(g, bs, d, task.x, task.y, L.b, gamma, t == stall_task);
+        else wfwd_chunk<lse>(g, bs, d, task.x, task.z, task.w, L.b, gamma, t == stall_task);
+        q = grab(d.heads + 0);  // the next task only once this one is done
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward
+// ---------------------------------------------------------------------------
+
+// The driver cell's backward terms for the four conditions of one placement,
+// all from forward results (as BCell of batch.cu): arc delays of every
+// condition (required times); for the late conditions (index rf) the LSE
+// weights, the NLDM partials, the late-slew arc and its slew partials.
+struct WBCell {
+    int t, na;
+    int rfi[2];
+    int pin[STA_MAX_ARCS];
+    float adel[STA_MAX_ARCS][4];
+    float w[STA_MAX_ARCS][2], dDs[STA_MAX_ARCS][2], dDl[STA_MAX_ARCS][2];
+    int amax[2];
+    float dSs[2], dSl[2];
+    float cs[2];  // propagated clock: the setup seed of a one-input cell's clock pin (rising input)
+};
+
+template <int mode>
+__device__ __forceinline__ WBCell wbcell_pre(const DevNet& g, const BatchState& bs, int n, int dp, int b,
+                                             float gamma) {
+    const int Bp = bs.Bp;
+    WBCell bc;
+    const int4 q0 = __ldg(g.net_desc + 2 * n), q1 = __ldg(g.net_desc + 2 * n + 1);  // one record
+    bc.t = q0.x;
+    bc.na = q0.z;
+    const int dpin[STA_MAX_ARCS] = {q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+    for (int rf = 0; rf < 2; ++rf) {
+        bc.rfi[rf] = 0;
+        bc.amax[rf] = -1;
+        bc.dSs[rf] = bc.dSl[rf] = bc.cs[rf] = 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        bc.pin[k] = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bc.adel[k][c] = 0.f;
+#pragma unroll
+        for (int rf = 0; rf < 2; ++rf) bc.w[k][rf] = bc.dDs[k][rf] = bc.dDl[k][rf] = 0.f;
+    }
+    if (bc.t < 0) return bc;
+    const int t = bc.t;
+    const int un = q0.w >> 4;
+    const float ld = bs.load[ix(n, Bp, b)];
+    const float* li = g.lib_idx + t * kLibStride + 8;
+    const int jl = axis_seg(li, ld);
+    const float inv_l = __ldg(g.lib_inv + t * kLibStride + 8 + jl);
+    const float ul = (ld - __ldg(li + jl)) * inv_l;
+    float zd[2] = {0.f, 0.f};
+    if (mode & 2) {
+        zd[0] = bs.ats[ix(2 * dp, Bp, b)];
+        zd[1] = bs.ats[ix(2 * dp + 1, Bp, b)];
+    }
+    float best[2] = {-kInf, -kInf};
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        if (k < bc.na) {
+            bc.pin[k] = dpin[k];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int el = c >> 1, rf = c & 1;
+                const int r = rf ^ ((un >> k) & 1);
+                if (el == 0) bc.rfi[rf] |= r << k;
+                if (!((mode & 1) || el)) continue;  // mode 2 needs the late conditions only
+                const float sin = bs.slew[ix(4 * bc.pin[k] + 2 * el + r, Bp, b)];
+                const float* si = g.lib_idx + t * kLibStride;
+                const int is = axis_seg(si, sin);
+                const float inv_s = __ldg(g.lib_inv + t * kLibStride + is);
+                const float ts = (sin - __ldg(si + is)) * inv_s;
+                float4 dq, sq;
+                cell_corners(g, t, k, rf, is, jl, dq, sq);
+                float dDs, dDl, dSs, dSl;
+                const float D = lerp_cell_grad(dq, ts, ul, inv_s, inv_l, dDs, dDl);
+                bc.adel[k][c] = D;
+                if ((mode & 2) && el) {
+                    const float S = lerp_cell_grad(sq, ts, ul, inv_s, inv_l, dSs, dSl);
+                    bc.dDs[k][rf] = dDs;
+                    bc.dDl[k][rf] = dDl;
+                    bc.w[k][rf] = expf((bs.ats[ix(2 * bc.pin[k] + r, Bp, b)] + D - zd[rf]) / gamma);
+                    if (S > best[rf]) {
+                        best[rf] = S;
+                        bc.amax[rf] = k;
+                        bc.dSs[rf] = dSs;
+                        bc.dSl[rf] = dSl;
+                    }
+                }
+            }
+        }
+    }
+    // a capturing clock pin is the input of a one-input cell; its seed is read
+    // here, before the wait, and added to the rising adjoint it writes
+    if ((mode & 2) && bs.cap_seed && bc.na == 1) {
+#pragma unroll
+        for (int rf = 0; rf < 2; ++rf)
+            if ((bc.rfi[rf] & 1) == 0) bc.cs[rf] = __ldcg(bs.cap_seed + ix(bc.pin[0], Bp, b));
+    }
+    return bc;
+}
+
+// Required times of the cell's inputs (R[c] at the output) and the adjoint of
+// the late conditions; returns each condition's part of d loss / d load in gl
+// (zero for the early ones).
+template <int mode>
+__device__ __forceinline__ void wbcell_apply(const BatchState& bs, const WBCell& bc, int b, const float* R,
+                                             const float* GA, const float* GS, float* gl) {
+    const int Bp = bs.Bp;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) gl[c] = 0.f;
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        if (k < bc.na) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int el = c >> 1, rf = c & 1;
+                const int r = (bc.rfi[rf] >> k) & 1;
+                // strong stores: words that the sinks' tasks poll
+                if (mode & 1) st_relaxed_f(bs.rat + ix(4 * bc.pin[k] + 2 * el + r, Bp, b), R[c] - bc.adel[k][c]);
+                if ((mode & 2) && el) {
+                    const float gD = GA[rf] * bc.w[k][rf];
+                    // a capturing clock pin also carries its endpoint's setup term
+                    st_relaxed_f(bs.g_ats + ix(2 * bc.pin[k] + r, Bp, b), (bs.cap_seed && k == 0) ? gD + bc.cs[rf] : gD);
+                    st_relaxed_f(bs.g_slew + ix(2 * bc.pin[k] + r, Bp, b),
+                                 fmaf(gD, bc.dDs[k][rf], k == bc.amax[rf] ? GS[rf] * bc.dSs[rf] : 0.f));
+                    gl[c] = fmaf(gD, bc.dDl[k][rf], gl[c]);
+                }
+            }
+        }
+    }
+    if (mode & 2) {
+#pragma unroll
+        for (int rf = 0; rf < 2; ++rf)
+            if (bc.amax[rf] >= 0) gl[2 + rf] = fmaf(GS[rf], bc.dSl[rf], gl[2 + rf]);
+    }
+}
+
+// One sink's terms for the four conditions of one placement (as bsink of
+// batch.cu): r[c] = RAT_s - Delay_s; for the late conditions (rf) the sink's
+// LSE-arrival adjoint, the slew term and the wire adjoint.
+struct WSink {
+    float r[4], ga[2], gs[2], gw[2];
+    Wire w;
+};
+
+template <int mode, bool kPoll>
+__device__ __forceinline__ WSink wsink(const DevNet& g, const BatchState& bs, const DfState& d, int p, int b,
+                                       float2 xyd, const float* sld, float gamma, const BSeed& sd) {
+    const int Bp = bs.Bp;
+    WSink s;
+    s.w = wire(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p));
+    const bool dyn = d.pin_cons[p] >= 0;  // the same for every lane
+    float rr[4] = {0.f, 0.f, 0.f, 0.f}, ga[2] = {0.f, 0.f}, gs[2] = {0.f, 0.f};
+    auto load = [&]() {
+        bool ok = true;
+        if (mode & 1) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                rr[c] = kPoll ? ld_relaxed_f(bs.rat + ix(4 * p + c, Bp, b)) : __ldcg(bs.rat + ix(4 * p + c, Bp, b));
+                ok &= written(rr[c]);
+            }
+        }
+        if ((mode & 2) && dyn) {
+#pragma unroll
+            for (int rf = 0; rf < 2; ++rf) {
+                ga[rf] = kPoll ? ld_relaxed_f(bs.g_ats + ix(2 * p + rf, Bp, b)) : __ldcg(bs.g_ats + ix(2 * p + rf, Bp, b));
+                gs[rf] = kPoll ? ld_relaxed_f(bs.g_slew + ix(2 * p + rf, Bp, b))
+                               : __ldcg(bs.g_slew + ix(2 * p + rf, Bp, b));
+                ok &= written(ga[rf]) & written(gs[rf]);
+            }
+        }
+        return ok;
+    };
+    if (kPoll && dyn) poll_words(load, d.abort_word);
+    else load();
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s.r[c] = (mode & 1) ? rr[c] - s.w.D : 0.f;
+#pragma unroll
+    for (int rf = 0; rf < 2; ++rf) s.ga[rf] = s.gs[rf] = s.gw[rf] = 0.f;
+    if (mode & 2) {
+        if (!dyn) {
+            const float rl = bs.rat[ix(4 * p + 2, Bp, b)], rfl = bs.rat[ix(4 * p + 3, Bp, b)];
+            if (isfinite(rl)) {
+                const float sr = rl - bs.ats[ix(2 * p, Bp, b)], sf = rfl - bs.ats[ix(2 * p + 1, Bp, b)];
+                const float te = softmin3(sr, sf, gamma);
+#pragma unroll
+                for (int rf = 0; rf < 2; ++rf) {
+                    const float sv = rf ? sf : sr;
+                    float gv = sd.wt * expf(-(sv - te) / gamma);
+                    if (isfinite(sd.W)) gv += sd.ww * expf(-(sv - sd.W) / gamma);
+                    ga[rf] = -gv;
+                }
+            }
+        }
+#pragma unroll
+        for (int rf = 0; rf < 2; ++rf) {
+            const float sl = bs.slew[ix(4 * p + 2 + rf, Bp, b)];
+            const float qv = sl > 0.f ? gs[rf] / sl : 0.f;
+            s.ga[rf] = ga[rf];
+            s.gs[rf] = qv * sld[rf];
+            s.gw[rf] = fmaf(qv, s.w.I, ga[rf]);
+        }
+    }
+    return s;
+}
+
+// Packed small nets: per net the sinks' terms (the wait), the driver's arc
+// step, then the sinks' and the driver's gradients.
+template <int mode>
+__device__ void wbwd_nets(const DevNet& g, const BatchState& bs, const DfState& d, int n0, int nn, int b,
+                          float gamma, const BSeed& sd) {
+    const int Bp = bs.Bp;
+    for (int j = 0; j < nn; ++j) {
+        const int n = n0 + j;
+        const int dp = g.net_ptr[n], e = g.net_ptr[n + 1];
+        const WBCell bc = wbcell_pre<mode>(g, bs, n, dp, b, gamma);
+        const float2 xyd = bs.xy[ix(dp, Bp, b)];
+        float sld[2] = {0.f, 0.f};
+        if (mode & 2) {
+            sld[0] = bs.slew[ix(4 * dp + 2, Bp, b)];
+            sld[1] = bs.slew[ix(4 * dp + 3, Bp, b)];
+        }
+        float R[4] = {kInf, kInf, kInf, kInf}, GA[2] = {0.f, 0.f}, GS[2] = {0.f, 0.f};
+        R[0] = R[1] = -kInf;  // early conditions: max
+#pragma unroll 2
+        for (int p = dp + 1; p < e; ++p) {
+            const WSink s = wsink<mode, true>(g, bs, d, p, b, xyd, sld, gamma, sd);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) R[c] = (c >> 1) ? fminf(R[c], s.r[c]) : fmaxf(R[c], s.r[c]);
+#pragma unroll
+            for (int rf = 0; rf < 2; ++rf) {
+                GA[rf] += s.ga[rf];
+                GS[rf] += s.gs[rf];
+            }
+            // the sink's wire adjoint, both transitions; kept until d loss / d load is known
+            if (mode & 2) bs.grad[ix(p, Bp, b)].x = s.gw[0] + s.gw[1];
+        }
+        if (mode & 1) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) bs.rat[ix(4 * dp + c, Bp, b)] = R[c];
+        }
+        float gl[4];
+        wbcell_apply<mode>(bs, bc, b, R, GA, GS, gl);
+        if (mode & 2) {
+            const float gload = (gl[0] + gl[1]) + (gl[2] + gl[3]);  // early conditions contribute 0
+            float sx[4] = {0.f, 0.f, 0.f, 0.f}, sy[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                for (int p = dp + 1 + c; p < e; p += 4) {
+                    const float gw = bs.grad[ix(p, Bp, b)].x;
+                    const float2 gxy = bsink_grad(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p), gw, gload);
+                    bs.grad[ix(p, Bp, b)] = gxy;
+                    sx[c] += gxy.x;
+                    sy[c] += gxy.y;
+                }
+            bs.grad[ix(dp, Bp, b)] = make_float2(-((sx[0] + sx[1]) + (sx[2] + sx[3])),
+                                                 -((sy[0] + sy[1]) + (sy[2] + sy[3])));
+        }
+    }
+}
+
+// Partial chunk of a large net (slots as in batch.cu: 0-3 required times by
+// condition, 4-5 sums of g_ats, 6-7 of g_slew * slew_d / slew_s, 8-11 the
+// sign sums and sign-weighted wire adjoints of the driver's gradient).
+template <int mode>
+__device__ void wbwd_part(const DevNet& g, const BatchState& bs, const DfState& d, int n, int p0, int np, int slot,
+                          int b, float gamma, const BSeed& sd) {
+    const int Bp = bs.Bp;
+    const int dp = g.net_ptr[n];
+    const float2 xyd = bs.xy[ix(dp, Bp, b)];
+    float sld[2] = {0.f, 0.f};
+    if (mode & 2) {
+        sld[0] = bs.slew[ix(4 * dp + 2, Bp, b)];
+        sld[1] = bs.slew[ix(4 * dp + 3, Bp, b)];
+    }
+    float R[4] = {-kInf, -kInf, kInf, kInf}, GA[2] = {0.f, 0.f}, GS[2] = {0.f, 0.f};
+    float sx = 0.f, sy = 0.f, hx = 0.f, hy = 0.f;
+#pragma unroll 2
+    for (int p = p0; p < p0 + np; ++p) {
+        const WSink s = wsink<mode, true>(g, bs, d, p, b, xyd, sld, gamma, sd);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) R[c] = (c >> 1) ? fminf(R[c], s.r[c]) : fmaxf(R[c], s.r[c]);
+#pragma unroll
+        for (int rf = 0; rf < 2; ++rf) {
+            GA[rf] += s.ga[rf];
+            GS[rf] += s.gs[rf];
+        }
+        if (mode & 2) {
+            const float gw = s.gw[0] + s.gw[1];
+            const float2 xy = bs.xy[ix(p, Bp, b)];
+            const float dx = xy.x - xyd.x, dy = xy.y - xyd.y;
+            const float ex = (dx > 0.f) - (dx < 0.f), ey = (dy > 0.f) - (dy < 0.f);
+            const float h = gw * (kKrc * g.r * fmaf(g.c, s.w.dist, __ldg(g.pin_cap + p)));
+            sx += ex;
+            sy += ey;
+            hx += ex * h;
+            hy += ey * h;
+        }
+    }
+    float* part = (mode & 2) ? bs.part : bs.rpart;
+    const int base = slot * kPartFloats;
+    // strong stores: the driver step polls these words
+#pragma unroll
+    for (int c = 0; c < 4; ++c) st_relaxed_f(part + ix(base + c, Bp, b), R[c]);
+    if (mode & 2) {
+#pragma unroll
+        for (int rf = 0; rf < 2; ++rf) {
+            st_relaxed_f(part + ix(base + 4 + rf, Bp, b), GA[rf]);
+            st_relaxed_f(part + ix(base + 6 + rf, Bp, b), GS[rf]);
+        }
+        st_relaxed_f(part + ix(base + 8, Bp, b), sx);
+        st_relaxed_f(part + ix(base + 9, Bp, b), sy);
+        st_relaxed_f(part + ix(base + 10, Bp, b), hx);
+        st_relaxed_f(part + ix(base + 11, Bp, b), hy);
+    }
+}
+
+// Driver step of a large net: the chunks' partials combined in chunk order,
+// then the arc step and the driver's gradient; publishes d loss / d load.
+template <int mode>
+__device__ void wbwd_driver(const DevNet& g, const BatchState& bs, const DfState& d, int n, int slot0, int nch, int b,
+                            float gamma) {
+    const int Bp = bs.Bp;
+    const int dp = g.net_ptr[n];
+    const WBCell bc = wbcell_pre<mode>(g, bs, n, dp, b, gamma);
+    const float* part = (mode & 2) ? bs.part : bs.rpart;
+    constexpr int kS = (mode & 2) ? 12 : 4;  // slots read
+    constexpr int kU = 2;                    // chunks per poll round
+    float R[4] = {-kInf, -kInf, kInf, kInf}, v[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) v[i] = 0.f;
+    for (int k0 = 0; k0 < nch; k0 += kU) {
+        float x[kU][kS];
+        // in the dataflow sweep this is the wait: repeated until the chunks'
+        // words are written
+        auto load = [&]() {
+            bool all = true;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int base = (slot0 + k0 + u) * kPartFloats;
+                const bool ok = k0 + u < nch;
+#pragma unroll
+                for (int i = 0; i < kS; ++i) {
+                    x[u][i] = ok ? ld_relaxed_f(part + ix(base + i, Bp, b)) : 0.f;
+                    if (ok) all &= written(x[u][i]);
+                }
+            }
+            return all;
+        };
+        poll_words(load, d.abort_word);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (k0 + u >= nch) break;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) R[c] = (c >> 1) ? fminf(R[c], x[u][c]) : fmaxf(R[c], x[u][c]);
+#pragma unroll
+            for (int i = 4; i < kS; ++i) v[i] += x[u][i];
+        }
+    }
+    if (mode & 1) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bs.rat[ix(4 * dp + c, Bp, b)] = R[c];
+    }
+    const float GA[2] = {v[4], v[5]}, GS[2] = {v[6], v[7]};
+    float gl[4];
+    wbcell_apply<mode>(bs, bc, b, R, GA, GS, gl);
+    if (mode & 2) {
+        const float gload = (gl[0] + gl[1]) + (gl[2] + gl[3]);
+        bs.net_gload[ix(n, Bp, b)] = gload;
+        bs.grad[ix(dp, Bp, b)] = make_float2(-fmaf(gload * g.c, v[8], v[10]), -fmaf(gload * g.c, v[9], v[11]));
+    }
+}
+
+// Gradient chunk of a large net: d loss / d (x, y) of its sinks once the
+// driver step has published d loss / d load.  No task waits for these.
+__device__ void wbwd_grad(const DevNet& g, const BatchState& bs, const DfState& d, int32_t* cnt, int q, int n, int p0,
+                          int np, int b, float gamma, const BSeed& sd) {
+    const int Bp = bs.Bp;
+    const int dp = g.net_ptr[n];
+    const float2 xyd = bs.xy[ix(dp, Bp, b)];
+    const float sld[2] = {bs.slew[ix(4 * dp + 2, Bp, b)], bs.slew[ix(4 * dp + 3, Bp, b)]};
+    wait_ready(cnt, q, d.b_indeg[q / bs.G], d.abort_word);
+    const float gload = __ldcg(bs.net_gload + ix(n, Bp, b));
+#pragma unroll 2
+    for (int p = p0; p < p0 + np; ++p) {
+        const WSink s = wsink<2, false>(g, bs, d, p, b, xyd, sld, gamma, sd);
+        bs.grad[ix(p, Bp, b)] =
+            bsink_grad(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p), s.gw[0] + s.gw[1], gload);
+    }
+}
+
+template <int mode>
+__global__ void __launch_bounds__(kBlock, 2) k_bbwd_w(DevNet g, BatchState bs, DfState d, float gamma) {
+    int32_t* cnt = (mode & 2) ? d.acnt : d.rcnt;
+    int32_t* head = d.heads + ((mode & 2) ? 2 : 1);
+    const int G = bs.G;
+    const int Q = d.TB * G;
+    int q = grab(head);
+    while (q < Q) {
+        const int t = q / G, gw = q - t * G;
+        const WLane L = wlane(gw);
+        BSeed sd;
+        sd.W = (float)bs.summary[(size_t)L.b * STA_SUM_COUNT + STA_SUM_WNS_GAMMA];
+        sd.wt = bs.params[2 * L.b];
+        sd.ww = bs.params[2 * L.b + 1];
+        const int4 task = d.btask[t];
+        if (task.y > 0) wbwd_nets<mode>(g, bs, d, task.x, task.y, L.b, gamma, sd);
+        else if (task.y == -1) wbwd_part<mode>(g, bs, d, task.x, task.z, task.w, d.baux[t], L.b, gamma, sd);
+        else if (task.y == -2) wbwd_driver<mode>(g, bs, d, task.x, task.z, task.w, L.b, gamma);
+        else if (mode & 2) wbwd_grad(g, bs, d, cnt, q, task.x, task.z, task.w, L.b, gamma, sd);
+        // every consumer polls the words its producers wrote, except the gradient
+        // chunks of a large net, which wait on a counter that its driver step releases
+        if (task.y == -2) {
+            __syncwarp();
+            const int k1 = d.b_out_ptr[t + 1];
+            for (int k = d.b_out_ptr[t] + L.lane; k < k1; k += 32) red_release_add(cnt + d.b_out[k] * G + gw, 1);
+        }
+        q = grab(head);
+    }
+}
+
+}  // namespace
+
+int batch_wide_max_blocks(int fwd) {
+    int dev = 0, sms = 0, a = 0, b = 0, c = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (fwd) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bfwd_w<true>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bfwd_w<false>, kBlock, 0);
+        c = a;
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bbwd_w<1>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bbwd_w<2>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_bbwd_w<3>, kBlock, 0);
+    }
+    const int per_sm = std::min(a, std::min(b, c));
+    return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+void launch_batch_fwd_wide(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int lse,
+                           int stall_task, cudaStream_t st) {
+    if (d.TF == 0) return;
+    if (lse) launch_coop(k_bfwd_w<true>, grid, kBlock, 0, st, g, bs, d, gamma, stall_task);
+    else launch_coop(k_bfwd_w<false>, grid, kBlock, 0, st, g, bs, d, gamma, stall_task);
+}
+
+void launch_batch_bwd_wide(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int mode,
+                           cudaStream_t st) {
+    if (d.TB == 0) return;
+    if (mode == 1) launch_coop(k_bbwd_w<1>, grid, kBlock, 0, st, g, bs, d, gamma);
+    else if (mode == 2) launch_coop(k_bbwd_w<2>, grid, kBlock, 0, st, g, bs, d, gamma);
+    else launch_coop(k_bbwd_w<3>, grid, kBlock, 0, st, g, bs, d, gamma);
+}
+
+}  // namespace sta

@@ -87,6 +87,7 @@ struct StaHandle {
     DfState d{};
     int schedule = STA_SCHED_DATAFLOW;
     int grid_fwd = 0, grid_bwd = 0;  // dataflow grids (blocks)
+    int grid_fwd_w = 0, grid_bwd_w = 0;  // batched: the lane-per-placement sweeps' grids
     // batched schedule: B placements, lane per placement
     int B = 1;
     int bsweep = STA_BATCH_LEVELS;
@@ -356,7 +357,10 @@ void enqueue_forward_batch(StaHandle* h, int lse, float gamma, cudaStream_t st) 
     cudaStreamWaitEvent(st, h->ev_fork[1], 0);
     {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
-        launch_batch_fwd(h->g, h->bs, h->d, h->grid_fwd, gamma, lse, h->stall_task, st);
+        if (h->bsweep == STA_BATCH_WIDE)
+            launch_batch_fwd_wide(h->g, h->bs, h->d, h->grid_fwd_w, gamma, lse, h->stall_task, st);
+        else
+            launch_batch_fwd(h->g, h->bs, h->d, h->grid_fwd, gamma, lse, h->stall_task, st);
     }
     // the words the next fused gradient sweep polls, beside the endpoints (as in the
     // single-placement forward)
@@ -398,7 +402,8 @@ void enqueue_backward_batch(StaHandle* h, int mode, float gamma, cudaStream_t st
         launch_batch_reset(h->bs, h->d, L.P, mode, st);  // the words the sweep's tasks poll
     }
     ProfScope ps(h, pr, (mode & 2) ? STA_PROF_ADJOINT : STA_PROF_REQUIRED, st);
-    launch_batch_bwd(h->g, h->bs, h->d, h->grid_bwd, gamma, mode, st);
+    if (h->bsweep == STA_BATCH_WIDE) launch_batch_bwd_wide(h->g, h->bs, h->d, h->grid_bwd_w, gamma, mode, st);
+    else launch_batch_bwd(h->g, h->bs, h->d, h->grid_bwd, gamma, mode, st);
 }
 
 void enqueue_forward(StaHandle* h, int lse, float gamma, cudaStream_t st) {
@@ -816,8 +821,10 @@ StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDe
             sh.pack_pins = opts->tile_pins > 0 ? opts->tile_pins : 4;
             sh.pack_nets = 1 << 20;
             sh.chunk = opts->chunk > 0 ? opts->chunk : 16;
-            if (opts->batch_sweep != STA_BATCH_LEVELS && opts->batch_sweep != STA_BATCH_DATAFLOW)
-                return fail(set_err(STA_ERR_INVALID_ARG, "StaOptions.batch_sweep must be LEVELS or DATAFLOW"));
+            if (opts->batch_sweep != STA_BATCH_LEVELS && opts->batch_sweep != STA_BATCH_DATAFLOW &&
+                opts->batch_sweep != STA_BATCH_WIDE)
+                return fail(set_err(STA_ERR_INVALID_ARG,
+                                    "StaOptions.batch_sweep must be LEVELS, DATAFLOW, LANES or WIDE"));
             h->bsweep = opts->batch_sweep;
             sh.big = sh.chunk + 1;  // a driver and `chunk` sinks still form one task
             try {
@@ -1027,9 +1034,15 @@ StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDe
         const int bmax = bat ? batch_max_blocks(0) : dataflow_max_blocks(0, h->nl > 1);
         h->grid_fwd = fmax > 0 ? fmax : 1;
         h->grid_bwd = bmax > 0 ? bmax : 1;
+        if (bat) {  // the lane-per-placement sweeps (sta_autotune may switch to them)
+            h->grid_fwd_w = std::max(1, batch_wide_max_blocks(1));
+            h->grid_bwd_w = std::max(1, batch_wide_max_blocks(0));
+        }
         if (opts && opts->grid_blocks > 0) {
             h->grid_fwd = std::min(h->grid_fwd, (int)opts->grid_blocks);
             h->grid_bwd = std::min(h->grid_bwd, (int)opts->grid_blocks);
+            h->grid_fwd_w = std::min(h->grid_fwd_w, (int)opts->grid_blocks);
+            h->grid_bwd_w = std::min(h->grid_bwd_w, (int)opts->grid_blocks);
         }
         if (cudaGetLastError() != cudaSuccess) return fail(set_err(STA_ERR_CUDA, "occupancy query failed"));
     }
@@ -1068,6 +1081,8 @@ void sta_destroy(StaHandle* h) {
 
 StaStatus sta_set_positions(StaHandle* h, const float* xy, int on_device, void* stream) {
     if (!h || (!xy && h->lay.P > 0)) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    if (on_device && reinterpret_cast<uintptr_t>(xy) % 8)  // read as float2 by the gather kernels
+        return set_err(STA_ERR_INVALID_ARG, "sta_set_positions: device xy must be 8-byte aligned");
     cudaStream_t st = as_stream(stream);
     // do not overwrite positions that a pending sweep still reads
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_bwd, 0));
@@ -1156,6 +1171,8 @@ StaStatus sta_forward(StaHandle* h, uint32_t flags, float gamma, void* stream) {
 StaStatus sta_backward_grad(StaHandle* h, const float* w, int w_on_device, float* grad_xy, int on_device,
                             void* stream) {
     if (!h || !w || (!grad_xy && h->lay.P > 0)) return set_err(STA_ERR_INVALID_ARG, "null argument");
+    if ((on_device && reinterpret_cast<uintptr_t>(grad_xy) % 8) || (w_on_device && reinterpret_cast<uintptr_t>(w) % 4))
+        return set_err(STA_ERR_INVALID_ARG, "sta_backward_grad: device grad_xy must be 8-byte, w 4-byte aligned");
     if (!h->have_lse) return set_err(STA_ERR_STATE, "sta_forward with STA_FWD_LSE must come before sta_backward_grad");
     cudaStream_t st = as_stream(stream);
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_at, 0));
@@ -1254,8 +1271,8 @@ StaStatus sta_autotune(StaHandle* h, const int32_t* tile_pins, int32_t n_tile, c
     for (int32_t i = 0; i < n_chunk; ++i)
         if (chunks[i] < 1) return set_err(STA_ERR_INVALID_ARG, "chunk must be >= 1");
     for (int32_t i = 0; i < n_sweep; ++i)
-        if (sweeps[i] != STA_BATCH_LEVELS && sweeps[i] != STA_BATCH_DATAFLOW)
-            return set_err(STA_ERR_INVALID_ARG, "sweeps: STA_BATCH_LEVELS or STA_BATCH_DATAFLOW");
+        if (sweeps[i] != STA_BATCH_LEVELS && sweeps[i] != STA_BATCH_DATAFLOW && sweeps[i] != STA_BATCH_WIDE)
+            return set_err(STA_ERR_INVALID_ARG, "sweeps: STA_BATCH_LEVELS, STA_BATCH_DATAFLOW or STA_BATCH_WIDE");
     CUDA_TRY(cudaDeviceSynchronize());
     cudaStream_t st = h->side;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1424,6 +1441,13 @@ StaStatus deliver(StaHandle* h, const float* internal, int k, float* out, int on
 StaStatus sta_query_pins(StaHandle* h, float* at, float* slew, float* rat, float* ats, float* slack, int on_device,
                          void* stream) {
     if (!h) return set_err(STA_ERR_INVALID_ARG, "null handle");
+    if (on_device) {  // written by kernels: floats, and the slack pairs as float2
+        for (const float* q : {at, slew, rat, ats})
+            if (reinterpret_cast<uintptr_t>(q) % 4)
+                return set_err(STA_ERR_INVALID_ARG, "sta_query_pins: device outputs must be 4-byte aligned");
+        if (reinterpret_cast<uintptr_t>(slack) % 8)
+            return set_err(STA_ERR_INVALID_ARG, "sta_query_pins: device slack must be 8-byte aligned");
+    }
     if (!h->have_fwd) return set_err(STA_ERR_STATE, "no forward pass yet");
     if ((rat || slack) && !h->have_rat) return set_err(STA_ERR_STATE, "required times need STA_FWD_RAT");
     if (ats && !h->have_lse) return set_err(STA_ERR_STATE, "LSE arrival times need STA_FWD_LSE");

@@ -33,7 +33,7 @@ def _check_all(nl, lib, xyb, W, gamma, res, which=None):
         tp.assert_parity(res[b], ora)
 
 
-SWEEPS = ["levels", "dataflow"]
+SWEEPS = ["levels", "dataflow", "wide"]
 
 
 @pytest.mark.parametrize("sweep", SWEEPS)
@@ -218,3 +218,34 @@ def test_lanes_host_buffers_repeats_and_edge_netlists():
         We = _weights(2)
         res = tp.run_gpu_batch(nl, lib, xe, 10.0, We, sweep="lanes")
         _check_all(nl, lib, xe, We, 10.0, res)
+
+
+def _edge(name):
+    return next((nl, xy, lib) for n, nl, xy, lib in tp.edge_netlists() if n == name)
+
+
+@pytest.mark.parametrize("case", ["sb_50k_x5", "tiny_clocked_x3", "ragged_x40", "sb_50k_chunk8_x70"])
+def test_wide_sweep_equals_narrow_bitwise(case):
+    # a lane per placement (all four conditions in one lane) gives every output
+    # bit-identical to the 8-placement x 4-condition sweep: padding lanes of a
+    # 32-placement group, several groups, a propagated clock, and the large
+    # nets' partial / driver / gradient tasks (8-sink chunks)
+    if case == "ragged_x40":
+        nl, xy, lib = _edge("ragged")
+        xyb = netgen.jitter_positions(np.asarray(xy, np.float32), 40, 5.0, 3)
+        W, chunk = _weights(40, seed=9), 0
+    else:
+        w = {"sb_50k_x5": lambda: netgen.superblue_like(3, scale=0.02, depth=40),
+             "tiny_clocked_x3": lambda: netgen.tiny_design(1, clock_nets=2),
+             "sb_50k_chunk8_x70": lambda: netgen.superblue_like(4, scale=0.02, depth=40)}[case]()
+        nl, lib = w.netlist, w.library
+        B = {"sb_50k_x5": 5, "tiny_clocked_x3": 3, "sb_50k_chunk8_x70": 70}[case]
+        xyb, W = _placements(w, B, seed=13), _weights(B, seed=14)
+        chunk = 8 if case.endswith("chunk8_x70") else 0
+    narrow = tp.run_gpu_batch(nl, lib, xyb, 10.0, W, sweep="dataflow", chunk=chunk)
+    wide = tp.run_gpu_batch(nl, lib, xyb, 10.0, W, sweep="wide", chunk=chunk)
+    for b in range(len(narrow)):
+        for k in ("at", "slew", "rat", "ats", "slack", "ep_slack", "grad"):
+            assert np.array_equal(wide[b][k], narrow[b][k], equal_nan=True), (case, b, k)
+        assert wide[b]["summary"] == narrow[b]["summary"], (case, b)
+    _check_all(nl, lib, xyb, W, 10.0, wide, which=[len(wide) - 1])

@@ -187,6 +187,38 @@ def test_call_order_and_argument_errors():
     eng.close()
 
 
+def test_misaligned_device_pointers_refused_before_device_work():
+    # the entry points whose kernels read or write caller device pointers as
+    # float2 refuse pointers off their alignment on the host (INVALID_ARG);
+    # the handle then runs a normal step
+    import torch
+
+    import paper_2603_28381_gb300 as sta
+    w = netgen.tiny_design(0)
+    P = w.netlist.num_pins
+    eng = sta.StaEngine(w.netlist, w.library)
+    stream = torch.cuda.current_stream().cuda_stream
+    big = torch.zeros(2 * P + 2, dtype=torch.float32, device="cuda")
+    odd = big[1:]  # 4 bytes past an 8-byte boundary
+    with pytest.raises(sta.StaError) as e:
+        sta._sta.sta_set_positions(eng.h, odd.data_ptr(), 1, stream)
+    assert e.value.status == 1 and "aligned" in sta.sta_last_error()
+    eng.set_positions(torch.as_tensor(w.xy).cuda())
+    eng.forward(gamma=10.0)
+    wts = torch.ones(2, dtype=torch.float32, device="cuda")
+    with pytest.raises(sta.StaError) as e:
+        sta._sta.sta_backward_grad(eng.h, wts.data_ptr(), 1, odd.data_ptr(), 1, stream)
+    assert e.value.status == 1
+    with pytest.raises(sta.StaError) as e:
+        sta._sta.sta_query_pins(eng.h, None, None, None, None, odd.data_ptr(), 1, stream)
+    assert e.value.status == 1
+    res = tp.run_gpu(w.netlist, w.library, w.xy, engine=eng)
+    ref = tp.run_gpu(w.netlist, w.library, w.xy)
+    for k in ("at", "slew", "rat", "ats", "slack", "ep_slack", "grad"):
+        assert np.array_equal(res[k], ref[k], equal_nan=True), k
+    eng.close()
+
+
 def test_query_slack_matches_the_other_queries():
     import torch
     import paper_2603_28381_gb300 as sta
