@@ -1,20 +1,22 @@
-// batch_wide.cu -- the batched dataflow sweeps with a lane per placement.
+// batch_wide.cu -- the batched backward sweeps with a lane per placement.
 //
 // Same tasks, queue and polled data words as the batched dataflow sweeps of
 // batch.cu, same per-placement layout value[row * Bp + b], but a warp takes a
-// task for 32 placements and each lane runs all four timing conditions of its
-// placement (early / late x rise / fall).  A warp task then carries four
-// independent chains of memory round trips per lane instead of one, and a
-// task's topology loads serve 32 placements instead of 8: the sweeps are bound
-// by each warp's chain of dependent loads, so this is what raises the memory
-// parallelism per SM.  Queue index q = task * G + group (G = Bp / 32).
+// backward task for 32 placements and each lane runs all four timing
+// conditions of its placement (early / late x rise / fall).  A warp task then
+// carries four independent chains of memory round trips per lane instead of
+// one, and its topology loads serve 32 placements instead of 8: the batched
+// backward is bound by each warp's chain of dependent loads, so this raises
+// the memory parallelism per SM.  Queue index q = task * G + group (G = Bp /
+// 32).  (The same mapping for the forward sweep measured slower than
+// batch.cu's: its per-lane code ran at 128 registers and 2 blocks per SM.)
 //
 // Every value is computed with the same operations in the same order as in
-// batch.cu: where the lanes of a quad exchanged values there (the net load's
-// four interleaved partial sums, the sink wire adjoints of the two late
-// conditions, the quad sums of d loss / d load and of the driver's gradient),
-// one lane now adds the same terms in the same association, so the results
-// are bit-identical to the narrow sweeps.
+// batch.cu: where the lanes of a quad exchanged values there (the sink wire
+// adjoints of the two late conditions, the quad sums of d loss / d load and
+// of the driver's gradient), one lane now adds the same terms in the same
+// association; with both files compiled without implicit multiply-add
+// contraction the results are bit-identical to the narrow sweeps.
 #include <algorithm>
 
 #include "batch_common.cuh"
@@ -31,233 +33,6 @@ __device__ __forceinline__ WLane wlane(int gw) {
     L.lane = threadIdx.x & 31;
     L.b = gw * 32 + L.lane;
     return L;
-}
-
-// ---------------------------------------------------------------------------
-// Forward
-// ---------------------------------------------------------------------------
-
-// The driver cell of net n for one placement: as FCell of batch.cu, with the
-// input transitions of both output transitions (rfi[rf], bit k for arc k).
-struct WCell {
-    int t, na, dyn;
-    int rfi[2];
-    int pin[STA_MAX_ARCS];
-    int jl;
-    float ul;
-    float sidx[6], sinv[6];
-};
-
-__device__ __forceinline__ WCell wcell(const DevNet& g, int n, float ld) {
-    WCell f;
-    const int4 q0 = __ldg(g.net_desc + 2 * n), q1 = __ldg(g.net_desc + 2 * n + 1);  // one record
-    f.t = q0.x;
-    f.na = q0.z;
-    f.rfi[0] = f.rfi[1] = 0;
-    f.dyn = q0.w & 15;
-    f.jl = 0;
-    f.ul = 0.f;
-    f.pin[0] = q1.x;
-    f.pin[1] = q1.y;
-    f.pin[2] = q1.z;
-    f.pin[3] = q1.w;
-#pragma unroll
-    for (int j = 0; j < 6; ++j) f.sidx[j] = f.sinv[j] = 0.f;
-    if (f.t < 0) return f;
-    const int un = q0.w >> 4;
-#pragma unroll
-    for (int rf = 0; rf < 2; ++rf)
-#pragma unroll
-        for (int k = 0; k < STA_MAX_ARCS; ++k)
-            if (k < f.na) f.rfi[rf] |= (rf ^ ((un >> k) & 1)) << k;
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        f.sidx[j] = __ldg(g.lib_idx + f.t * kLibStride + j);
-        f.sinv[j] = __ldg(g.lib_inv + f.t * kLibStride + j);
-    }
-    const float* li = g.lib_idx + f.t * kLibStride + 8;
-    f.jl = axis_seg(li, ld);
-    f.ul = (ld - __ldg(li + f.jl)) * __ldg(g.lib_inv + f.t * kLibStride + 8 + f.jl);
-    return f;
-}
-
-struct WOut {
-    float at[4], sl[4], z[2];  // by condition c = 2 el + rf; LSE arrival by rf (late)
-};
-
-// The driver cell for the four conditions of one placement.  The fanin words
-// of every arc (its pin's four arrival and slew rows and two LSE-arrival rows)
-// are loaded together; in the dataflow sweep this is the wait, repeated until
-// every word written during the sweep holds its value.
-__device__ __forceinline__ WOut wcell_eval(const DevNet& g, const BatchState& bs, const WCell& f, int dp, int b,
-                                           float gamma, bool lse, int32_t* abort_word, bool stall) {
-    const int Bp = bs.Bp;
-    WOut o;
-    if (f.t < 0) {  // asserted driver: constant values set at creation
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            o.at[c] = bs.at[ix(4 * dp + c, Bp, b)];
-            o.sl[c] = bs.slew[ix(4 * dp + c, Bp, b)];
-        }
-        o.z[0] = lse ? bs.ats[ix(2 * dp, Bp, b)] : 0.f;
-        o.z[1] = lse ? bs.ats[ix(2 * dp + 1, Bp, b)] : 0.f;
-        return o;
-    }
-    float ain[STA_MAX_ARCS][4], sin[STA_MAX_ARCS][4], zin[STA_MAX_ARCS][2];
-    auto load = [&]() {
-        bool ok = !stall;  // the test hook's stalled task never sees its inputs
-#pragma unroll
-        for (int k = 0; k < STA_MAX_ARCS; ++k) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) ain[k][j] = sin[k][j] = 0.f;
-            zin[k][0] = zin[k][1] = 0.f;
-            if (k < f.na) {
-                bool w = true;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {  // row 4 pin + j: condition j of the fanin pin
-                    ain[k][j] = ld_relaxed_f(bs.at + ix(4 * f.pin[k] + j, Bp, b));
-                    sin[k][j] = ld_relaxed_f(bs.slew + ix(4 * f.pin[k] + j, Bp, b));
-                    w &= written(ain[k][j]) & written(sin[k][j]);
-                }
-                if (lse) {
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        zin[k][r] = ld_relaxed_f(bs.ats + ix(2 * f.pin[k] + r, Bp, b));
-                        w &= written(zin[k][r]);
-                    }
-                }
-                if ((f.dyn >> k) & 1) ok &= w;
-            }
-        }
-        return ok;
-    };
-    poll_words(load, abort_word);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int el = c >> 1, rf = c & 1;
-        float best_at = el ? -kInf : kInf, best_sl = el ? -kInf : kInf, m = -kInf;
-        float cand[STA_MAX_ARCS];
-#pragma unroll
-        for (int k = 0; k < STA_MAX_ARCS; ++k) {
-            cand[k] = -kInf;
-            if (k < f.na) {
-                // the input transition r is data: select between registers
-                // (a runtime index would put the arrays in local memory)
-                const bool r = (f.rfi[rf] >> k) & 1;
-                const float sv = r ? sin[k][2 * el + 1] : sin[k][2 * el];
-                const float av = r ? ain[k][2 * el + 1] : ain[k][2 * el];
-                const float zv = r ? zin[k][1] : zin[k][0];
-                int is;
-                float ts;
-                seg_reg(f.sidx, f.sinv, sv, is, ts);
-                float4 dq, sq;
-                cell_corners(g, f.t, k, rf, is, f.jl, dq, sq);
-                const float D = lerp_cell(dq, ts, f.ul);
-                const float S = lerp_cell(sq, ts, f.ul);
-                const float v = av + D;
-                best_at = el ? fmaxf(best_at, v) : fminf(best_at, v);
-                best_sl = el ? fmaxf(best_sl, S) : fminf(best_sl, S);
-                cand[k] = (el ? zv : 0.f) + D;
-                m = fmaxf(m, cand[k]);
-            }
-        }
-        o.at[c] = best_at;
-        o.sl[c] = best_sl;
-        if (el) o.z[rf] = lse ? lse_arcs(cand, f.na, m, gamma) : 0.f;
-    }
-    return o;
-}
-
-__device__ __forceinline__ void wstore_pin(const BatchState& bs, int p, int b, const float* at, const float* sl,
-                                           const float* z, bool lse) {
-    const int Bp = bs.Bp;  // strong stores: words that other tasks of the sweep poll
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        st_relaxed_f(bs.at + ix(4 * p + c, Bp, b), at[c]);
-        st_relaxed_f(bs.slew + ix(4 * p + c, Bp, b), sl[c]);
-    }
-    if (lse) {
-        st_relaxed_f(bs.ats + ix(2 * p, Bp, b), z[0]);
-        st_relaxed_f(bs.ats + ix(2 * p + 1, Bp, b), z[1]);
-    }
-}
-
-// wire step to the sinks [s0, s1), all four conditions
-__device__ __forceinline__ void wstore_sinks(const DevNet& g, const BatchState& bs, int s0, int s1, int b, float2 xyd,
-                                             const WOut& o, bool lse) {
-#pragma unroll 2
-    for (int p = s0; p < s1; ++p) {
-        const Wire w = wire(g, bs.xy[ix(p, bs.Bp, b)], xyd, __ldg(g.pin_cap + p));
-        float at[4], sl[4], z[2];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            at[c] = o.at[c] + w.D;
-            sl[c] = sqrtf(fmaf(o.sl[c], o.sl[c], w.I * w.I));
-        }
-        z[0] = o.z[0] + w.D;
-        z[1] = o.z[1] + w.D;
-        wstore_pin(bs, p, b, at, sl, z, lse);
-    }
-}
-
-// net load (Eq. 1): four interleaved partial sums over sinks c, c + 4, ...,
-// added as (s0 + s1) + (s2 + s3), then the driver's pin capacitance
-__device__ __forceinline__ float wnet_load(const DevNet& g, const BatchState& bs, int dp, int s1, int b, float2 xyd) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-        for (int p = dp + 1 + c; p < s1; p += 4) {
-            const float2 xy = bs.xy[ix(p, bs.Bp, b)];
-            const float dist = fabsf(xy.x - xyd.x) + fabsf(xy.y - xyd.y);
-            acc[c] += fmaf(g.c, dist, __ldg(g.pin_cap + p));
-        }
-    return __ldg(g.pin_cap + dp) + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
-}
-
-template <bool lse>
-__device__ void wfwd_nets(const DevNet& g, const BatchState& bs, const DfState& d, int n0, int nn, int b,
-                          float gamma, bool stall) {
-    const int Bp = bs.Bp;
-    for (int j = 0; j < nn; ++j) {
-        const int n = n0 + j;
-        const int dp = g.net_ptr[n], e = g.net_ptr[n + 1];
-        const float2 xyd = bs.xy[ix(dp, Bp, b)];
-        const float ld = wnet_load(g, bs, dp, e, b, xyd);
-        bs.load[ix(n, Bp, b)] = ld;
-        const WCell f = wcell(g, n, ld);
-        const WOut o = wcell_eval(g, bs, f, dp, b, gamma, lse, d.abort_word, stall);
-        if (f.t >= 0) wstore_pin(bs, dp, b, o.at, o.sl, o.z, lse);
-        wstore_sinks(g, bs, dp + 1, e, b, xyd, o, lse);
-    }
-}
-
-// chunk of a large net: its load comes from the prologue; every chunk
-// evaluates the driver cell, the first one stores it
-template <bool lse>
-__device__ void wfwd_chunk(const DevNet& g, const BatchState& bs, const DfState& d, int n, int p0, int cnt, int b,
-                           float gamma, bool stall) {
-    const int Bp = bs.Bp;
-    const int dp = g.net_ptr[n];
-    const float2 xyd = bs.xy[ix(dp, Bp, b)];
-    const WCell f = wcell(g, n, bs.load[ix(n, Bp, b)]);
-    const WOut o = wcell_eval(g, bs, f, dp, b, gamma, lse, d.abort_word, stall);
-    if (f.t >= 0 && p0 == dp + 1) wstore_pin(bs, dp, b, o.at, o.sl, o.z, lse);
-    wstore_sinks(g, bs, p0, p0 + cnt, b, xyd, o, lse);
-}
-
-template <bool lse>
-__global__ void __launch_bounds__(kBlock, 2) k_bfwd_w(DevNet g, BatchState bs, DfState d, float gamma, int stall_task) {
-    const int G = bs.G;
-    const int Q = d.TF * G;
-    int q = grab(d.heads + 0);
-    while (q < Q) {
-        const int t = q / G, gw = q - t * G;
-        const WLane L = wlane(gw);
-        const int4 task = d.ftask[t];
-        if (task.y > 0) wfwd_nets<lse>(g, bs, d, task.x, task.y, L.b, gamma, t == stall_task);
-        else wfwd_chunk<lse>(g, bs, d, task.x, task.z, task.w, L.b, gamma, t == stall_task);
-        q = grab(d.heads + 0);  // the next task only once this one is done
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -683,28 +458,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_bbwd_w(DevNet g, BatchState bs, D
 
 }  // namespace
 
-int batch_wide_max_blocks(int fwd) {
+int batch_wide_max_blocks() {
     int dev = 0, sms = 0, a = 0, b = 0, c = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (fwd) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bfwd_w<true>, kBlock, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bfwd_w<false>, kBlock, 0);
-        c = a;
-    } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bbwd_w<1>, kBlock, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bbwd_w<2>, kBlock, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_bbwd_w<3>, kBlock, 0);
-    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bbwd_w<1>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bbwd_w<2>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_bbwd_w<3>, kBlock, 0);
     const int per_sm = std::min(a, std::min(b, c));
     return sms * (per_sm > 0 ? per_sm : 1);
-}
-
-void launch_batch_fwd_wide(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int lse,
-                           int stall_task, cudaStream_t st) {
-    if (d.TF == 0) return;
-    if (lse) launch_coop(k_bfwd_w<true>, grid, kBlock, 0, st, g, bs, d, gamma, stall_task);
-    else launch_coop(k_bfwd_w<false>, grid, kBlock, 0, st, g, bs, d, gamma, stall_task);
 }
 
 void launch_batch_bwd_wide(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int mode,

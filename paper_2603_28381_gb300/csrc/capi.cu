@@ -87,7 +87,7 @@ struct StaHandle {
     DfState d{};
     int schedule = STA_SCHED_DATAFLOW;
     int grid_fwd = 0, grid_bwd = 0;  // dataflow grids (blocks)
-    int grid_fwd_w = 0, grid_bwd_w = 0;  // batched: the lane-per-placement sweeps' grids
+    int grid_bwd_w = 0;  // batched: the lane-per-placement backward sweeps' grid
     // batched schedule: B placements, lane per placement
     int B = 1;
     int bsweep = STA_BATCH_LEVELS;
@@ -357,10 +357,10 @@ void enqueue_forward_batch(StaHandle* h, int lse, float gamma, cudaStream_t st) 
     cudaStreamWaitEvent(st, h->ev_fork[1], 0);
     {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
-        if (h->bsweep == STA_BATCH_WIDE)
-            launch_batch_fwd_wide(h->g, h->bs, h->d, h->grid_fwd_w, gamma, lse, h->stall_task, st);
-        else
-            launch_batch_fwd(h->g, h->bs, h->d, h->grid_fwd, gamma, lse, h->stall_task, st);
+        // (STA_BATCH_WIDE runs the lane-per-placement kernels for the backward
+        // sweeps only: the 8-placement forward measured as fast or faster, and
+        // both forwards give bit-identical results)
+        launch_batch_fwd(h->g, h->bs, h->d, h->grid_fwd, gamma, lse, h->stall_task, st);
     }
     // the words the next fused gradient sweep polls, beside the endpoints (as in the
     // single-placement forward)
@@ -1034,14 +1034,10 @@ StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDe
         const int bmax = bat ? batch_max_blocks(0) : dataflow_max_blocks(0, h->nl > 1);
         h->grid_fwd = fmax > 0 ? fmax : 1;
         h->grid_bwd = bmax > 0 ? bmax : 1;
-        if (bat) {  // the lane-per-placement sweeps (sta_autotune may switch to them)
-            h->grid_fwd_w = std::max(1, batch_wide_max_blocks(1));
-            h->grid_bwd_w = std::max(1, batch_wide_max_blocks(0));
-        }
+        if (bat) h->grid_bwd_w = std::max(1, batch_wide_max_blocks());  // (sta_autotune may switch to them)
         if (opts && opts->grid_blocks > 0) {
             h->grid_fwd = std::min(h->grid_fwd, (int)opts->grid_blocks);
             h->grid_bwd = std::min(h->grid_bwd, (int)opts->grid_blocks);
-            h->grid_fwd_w = std::min(h->grid_fwd_w, (int)opts->grid_blocks);
             h->grid_bwd_w = std::min(h->grid_bwd_w, (int)opts->grid_blocks);
         }
         if (cudaGetLastError() != cudaSuccess) return fail(set_err(STA_ERR_CUDA, "occupancy query failed"));

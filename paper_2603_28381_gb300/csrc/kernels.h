@@ -173,10 +173,8 @@ constexpr size_t kBatchEpBytes = 48;  // one endpoint partial
 constexpr int kPlacePerWarp = 8;       // sweep tasks: 8 placements x 4 conditions per warp
 
 int batch_max_blocks(int fwd);
-// the batched dataflow sweeps with a lane per placement (batch_wide.cu)
-int batch_wide_max_blocks(int fwd);
-void launch_batch_fwd_wide(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int lse,
-                           int stall_task, cudaStream_t st);
+// the batched backward sweeps with a lane per placement (batch_wide.cu)
+int batch_wide_max_blocks();
 void launch_batch_bwd_wide(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int mode,
                            cudaStream_t st);
 void launch_batch_load(const DevNet& g, const BatchState& bs, const int32_t* big_nets, int nbig, cudaStream_t st);
