@@ -259,7 +259,8 @@ __device__ void wbwd_nets(const DevNet& g, const BatchState& bs, const DfState& 
         }
         float R[4] = {kInf, kInf, kInf, kInf}, GA[2] = {0.f, 0.f}, GS[2] = {0.f, 0.f};
         R[0] = R[1] = -kInf;  // early conditions: max
-#pragma unroll 2
+// (not unrolled: the smaller loop body measured 6% faster, fewer instruction-fetch stalls)
+#pragma unroll 1
         for (int p = dp + 1; p < e; ++p) {
             const WSink s = wsink<mode, true>(g, bs, d, p, b, xyd, sld, gamma, sd);
 #pragma unroll
@@ -312,7 +313,7 @@ __device__ void wbwd_part(const DevNet& g, const BatchState& bs, const DfState& 
     }
     float R[4] = {-kInf, -kInf, kInf, kInf}, GA[2] = {0.f, 0.f}, GS[2] = {0.f, 0.f};
     float sx = 0.f, sy = 0.f, hx = 0.f, hy = 0.f;
-#pragma unroll 2
+#pragma unroll 1
     for (int p = p0; p < p0 + np; ++p) {
         const WSink s = wsink<mode, true>(g, bs, d, p, b, xyd, sld, gamma, sd);
 #pragma unroll
@@ -418,7 +419,7 @@ __device__ void wbwd_grad(const DevNet& g, const BatchState& bs, const DfState& 
     const float sld[2] = {bs.slew[ix(4 * dp + 2, Bp, b)], bs.slew[ix(4 * dp + 3, Bp, b)]};
     wait_ready(cnt, q, d.b_indeg[q / bs.G], d.abort_word);
     const float gload = __ldcg(bs.net_gload + ix(n, Bp, b));
-#pragma unroll 2
+#pragma unroll 1
     for (int p = p0; p < p0 + np; ++p) {
         const WSink s = wsink<2, false>(g, bs, d, p, b, xyd, sld, gamma, sd);
         bs.grad[ix(p, Bp, b)] =
