@@ -855,6 +855,24 @@ StaStatus build_union(const StaNetlistDesc* const* nls, int32_t count, UnionNetl
     return STA_OK;
 }
 
+}  // namespace sta
+
+std::vector<std::pair<const void*, size_t>> layout_host_buffers(const sta::Layout& L) {
+    std::vector<std::pair<const void*, size_t>> out;
+    auto add = [&](const auto& v) {
+        if (!v.empty()) out.emplace_back(static_cast<const void*>(v.data()), v.size() * sizeof(v[0]));
+    };
+    add(L.net_ptr), add(L.net_drv), add(L.net_arc_ptr), add(L.arc_pin), add(L.pin_orig), add(L.pin_cap);
+    add(L.wtask), add(L.ctask), add(L.rc_chunk), add(L.rc_net), add(L.ftask), add(L.arc_prod), add(L.btask);
+    add(L.baux), add(L.pin_cons), add(L.pin_keep), add(L.grp_ep), add(L.pin_grp), add(L.pin_mask), add(L.f_indeg);
+    add(L.f_out_ptr), add(L.f_out), add(L.b_indeg), add(L.b_out_ptr), add(L.b_out), add(L.at0), add(L.slew0);
+    add(L.rat0), add(L.ep_pin), add(L.ep_rat), add(L.ep_clk), add(L.lib_idx), add(L.lib_inv), add(L.lib_unate);
+    add(L.lib_tab), add(L.net_desc), add(L.lib_cell), add(L.lib_col);
+    return out;
+}
+
+namespace sta {
+
 void set_groups(Layout& o, const UnionNetlist& u) {
     o.G = (int32_t)u.pin_off.size() - 1;
     o.grp_ep = u.end_off;  // endpoints keep the description's order

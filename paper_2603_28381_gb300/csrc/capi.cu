@@ -190,7 +190,12 @@ struct StaHandle {
         T* p = nullptr;
         StaStatus st = alloc(p, src.size());
         if (st != STA_OK) return st;
-        if (!src.empty()) CUDA_TRY(cudaMemcpy(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+        // a pooled handle's uploads are queued on the legacy stream, which its
+        // creation synchronizes at the end (page-locked sources: plain DMA)
+        if (!src.empty() && pool)
+            CUDA_TRY(cudaMemcpyAsync(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, 0));
+        else if (!src.empty())
+            CUDA_TRY(cudaMemcpy(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
         dst = p;
         return STA_OK;
     }

@@ -91,6 +91,10 @@ struct Rep {
 struct Net {
     HostNetlist host;
     std::shared_ptr<const sta::Layout> layout;  // built once at registration; every copy is created from it
+    std::vector<const void*> pinned;            // layout arrays page-locked for the copies' uploads
+    ~Net() {
+        for (const void* p : pinned) cudaHostUnregister(const_cast<void*>(p));
+    }
     std::vector<Rep*> reps;     // resident copies
     size_t rep_bytes = 0;       // measured bytes of one copy (0: not created yet, estimate)
     int32_t P = 0;
@@ -657,6 +661,13 @@ StaStatus sta_server_add_netlist(StaServer* S, const StaNetlistDesc* nl, const S
             delete n;
             return fail("sta_server_add_netlist: " + err, st);
         }
+        // page-lock the arrays every copy uploads (best effort: a refusal leaves
+        // an array pageable, and its uploads slower)
+        for (const auto& buf : layout_host_buffers(*n->layout))
+            if (buf.second >= (64u << 10) &&
+                cudaHostRegister(const_cast<void*>(buf.first), buf.second, cudaHostRegisterDefault) == cudaSuccess)
+                n->pinned.push_back(buf.first);
+        cudaGetLastError();  // (clear a refusal)
     } catch (const std::bad_alloc&) {
         delete n;
         return fail("host allocation failed", STA_ERR_OOM);

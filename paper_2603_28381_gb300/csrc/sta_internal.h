@@ -15,6 +15,7 @@
 #include <cstdint>
 #include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sta.h"
@@ -173,6 +174,11 @@ StaStatus build_layout_shared(const StaNetlistDesc& nl, const StaLibrary& lib, s
                               std::string& err);
 
 }  // namespace sta
+
+// The host arrays of a layout that sta_create uploads, as (address, bytes):
+// a caller that keeps a layout for many handles may page-lock them once, so
+// that the uploads of each new handle run as asynchronous DMA.
+std::vector<std::pair<const void*, size_t>> layout_host_buffers(const sta::Layout& L);
 
 // sta_create on a layout from build_layout_shared (same options and errors).
 // The handle shares the layout, which stays unmodified; a BATCH handle with
