@@ -427,8 +427,12 @@ __device__ void wbwd_grad(const DevNet& g, const BatchState& bs, const DfState& 
     }
 }
 
+// 128-thread blocks, 5 per SM (96 registers, small spills in the fused mode): 20
+// warps per SM against 16 with 256-thread blocks at 128 registers; measured 5% faster
+constexpr int kWBlock = 128;
+
 template <int mode>
-__global__ void __launch_bounds__(kBlock, 2) k_bbwd_w(DevNet g, BatchState bs, DfState d, float gamma) {
+__global__ void __launch_bounds__(kWBlock, 5) k_bbwd_w(DevNet g, BatchState bs, DfState d, float gamma) {
     int32_t* cnt = (mode & 2) ? d.acnt : d.rcnt;
     int32_t* head = d.heads + ((mode & 2) ? 2 : 1);
     const int G = bs.G;
@@ -463,9 +467,9 @@ int batch_wide_max_blocks() {
     int dev = 0, sms = 0, a = 0, b = 0, c = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bbwd_w<1>, kBlock, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bbwd_w<2>, kBlock, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_bbwd_w<3>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bbwd_w<1>, kWBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bbwd_w<2>, kWBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_bbwd_w<3>, kWBlock, 0);
     const int per_sm = std::min(a, std::min(b, c));
     return sms * (per_sm > 0 ? per_sm : 1);
 }
@@ -473,9 +477,9 @@ int batch_wide_max_blocks() {
 void launch_batch_bwd_wide(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int mode,
                            cudaStream_t st) {
     if (d.TB == 0) return;
-    if (mode == 1) launch_coop(k_bbwd_w<1>, grid, kBlock, 0, st, g, bs, d, gamma);
-    else if (mode == 2) launch_coop(k_bbwd_w<2>, grid, kBlock, 0, st, g, bs, d, gamma);
-    else launch_coop(k_bbwd_w<3>, grid, kBlock, 0, st, g, bs, d, gamma);
+    if (mode == 1) launch_coop(k_bbwd_w<1>, grid, kWBlock, 0, st, g, bs, d, gamma);
+    else if (mode == 2) launch_coop(k_bbwd_w<2>, grid, kWBlock, 0, st, g, bs, d, gamma);
+    else launch_coop(k_bbwd_w<3>, grid, kWBlock, 0, st, g, bs, d, gamma);
 }
 
 }  // namespace sta
