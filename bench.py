@@ -19,7 +19,7 @@ one-request-at-a-time loop); `--no-sub` leaves them out.  `--impl reference`
 times the FP64 CPU oracle (the only reference this method has) on the box's
 host cores on the same workload.
 
-The roofline's `achieved` bytes follow the survey's per-unit count (116 P +
+The roofline's `achieved` bytes follow the per-unit algorithmic count (116 P +
 16 N + 52 S + 84 A per step, split into forward, required times and
 gradient); `per_kind_formula` gives every kernel kind's own reads and writes.
 """
@@ -158,8 +158,8 @@ def algorithmic_bytes(sizes, S, schedule="dataflow", big=(0, 0), clocked=0):
     return out
 
 
-def survey_bytes(sizes, S):
-    """Algorithmic bytes of one forward + gradient call by the survey's per-unit
+def unit_bytes(sizes, S):
+    """Algorithmic bytes of one forward + gradient call by the per-unit
     count (P pins, N nets, S sinks, A arcs; each array crosses HBM once per
     producer and once per consumer):
       forward  xy + cap 12P, net_ptr 4N, arc topology 6A, AT + slew write 32P,
@@ -482,10 +482,10 @@ def run_ours(args):
         abytes["required"] = 0
     dom = max(acc, key=lambda k: acc[k])
     peak, peak_src = load_peaks()
-    # the dominant kernel's algorithmic bytes by the survey's per-unit count: the
+    # the dominant kernel's algorithmic bytes by the per-unit count: the
     # forward sweep the forward's, the backward sweep the required times' and
     # (adjoint) the gradient's
-    sb = survey_bytes(sizes, S)
+    sb = unit_bytes(sizes, S)
     sweep_bytes = {"forward": sb["forward"], "required": sb["required"],
                    "adjoint": sb["gradient"] + (sb["required"] if launches.get("required", 1) == 0 else 0)}
     dom_bytes = sweep_bytes.get(dom, abytes[dom])
@@ -495,7 +495,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                 "traffic": None if traffic is None else float(traffic),
-                "bytes_per_launch": int(dom_bytes), "bytes_formula": "survey 116P + 16N + 52S + 84A per step",
+                "bytes_per_launch": int(dom_bytes), "bytes_formula": "per-unit count 116P + 16N + 52S + 84A per step",
                 "launches_per_step": launches[dom],
                 "avg_launch_us": 1e3 * acc[dom] / max(launches[dom], 1),
                 "ms_by_kind": {k: round(v, 4) for k, v in acc.items()},
@@ -940,7 +940,7 @@ def run_multi(args, emit=True):
     sb = 0
     for nl in nls:
         st = nl.stats()
-        sb += survey_bytes({"pins": st["pins"], "nets": st["nets"], "arcs": st["arcs"]},
+        sb += unit_bytes({"pins": st["pins"], "nets": st["nets"], "arcs": st["arcs"]},
                            int(nl.net_ptr[-1]) - st["nets"])["step"]
     peak, peak_src = load_peaks()
     value = P * args.steps / total_s
