@@ -346,15 +346,41 @@ __device__ __forceinline__ EpAcc ep_identity() {
     return a;
 }
 
+__device__ __forceinline__ EpAcc ep_shfl_down(const EpAcc& a, int off) {
+    EpAcc b;
+    b.tns_e = __shfl_down_sync(kFull, a.tns_e, off);
+    b.tns_l = __shfl_down_sync(kFull, a.tns_l, off);
+    b.tns_g = __shfl_down_sync(kFull, a.tns_g, off);
+    b.viol = __shfl_down_sync(kFull, a.viol, off);
+    b.wns_e = __shfl_down_sync(kFull, a.wns_e, off);
+    b.wns_l = __shfl_down_sync(kFull, a.wns_l, off);
+    b.wmin = __shfl_down_sync(kFull, a.wmin, off);
+    b.wsum = __shfl_down_sync(kFull, a.wsum, off);
+    return b;
+}
+
+// Fixed-order reduction of a block's accumulators, the result on thread 0: a
+// shuffle tree within each warp (lane i takes lane i + 16, 8, 4, 2, 1), then
+// warp 0 combines the warps' results the same way (one barrier; the
+// shared-memory tree it replaces spent most of its time in eight of them).
 __device__ void ep_block_reduce(EpAcc& acc, float gamma) {
-    __shared__ EpAcc sh[kBlock];
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int stride = kBlock / 2; stride > 0; stride >>= 1) {
-        if ((int)threadIdx.x < stride) ep_merge(sh[threadIdx.x], sh[threadIdx.x + stride], gamma);
-        __syncthreads();
+    __shared__ EpAcc sh[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const EpAcc b = ep_shfl_down(acc, off);
+        if (lane < off) ep_merge(acc, b, gamma);
     }
-    acc = sh[0];
+    if (lane == 0) sh[w] = acc;
+    __syncthreads();
+    if (w == 0) {
+        acc = lane < kWarpsPerBlock ? sh[lane] : ep_identity();
+#pragma unroll
+        for (int off = kWarpsPerBlock / 2; off > 0; off >>= 1) {
+            const EpAcc b = ep_shfl_down(acc, off);
+            if (lane < off) ep_merge(acc, b, gamma);
+        }
+    }
 }
 
 // Bounds of endpoint e: the constraint (early = hold, late = setup) and, with a
