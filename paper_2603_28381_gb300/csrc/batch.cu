@@ -65,7 +65,8 @@ struct FCell {
     float sidx[6], sinv[6];
 };
 
-__device__ __forceinline__ FCell fcell(const DevNet& g, const DfState& d, int n, int rf, float ld) {
+// the driver cell's record: type, arcs, input pins, input transitions
+__device__ __forceinline__ FCell fcell_topo(const DevNet& g, int n, int rf) {
     FCell f;
     const int4 q0 = __ldg(g.net_desc + 2 * n), q1 = __ldg(g.net_desc + 2 * n + 1);  // one record
     f.t = q0.x;
@@ -86,6 +87,12 @@ __device__ __forceinline__ FCell fcell(const DevNet& g, const DfState& d, int n,
 #pragma unroll
     for (int k = 0; k < STA_MAX_ARCS; ++k)
         if (k < f.na) f.rfi |= (rf ^ ((un >> k) & 1)) << k;
+    return f;
+}
+
+// the type's slew axis and the load's table segment and fraction
+__device__ __forceinline__ void fcell_lib(const DevNet& g, FCell& f, float ld) {
+    if (f.t < 0) return;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
         f.sidx[j] = __ldg(g.lib_idx + f.t * kLibStride + j);
@@ -94,21 +101,52 @@ __device__ __forceinline__ FCell fcell(const DevNet& g, const DfState& d, int n,
     const float* li = g.lib_idx + f.t * kLibStride + 8;
     f.jl = axis_seg(li, ld);
     f.ul = (ld - __ldg(li + f.jl)) * __ldg(g.lib_inv + f.t * kLibStride + 8 + f.jl);
-    return f;
 }
-
 
 struct FOut {
     float at, sl, z;  // arrival, slew, LSE arrival (late conditions) of this lane's condition
 };
 
+// The fanin arrival / slew / LSE-arrival words of the lane's arcs, all
+// together (through L2: other warps of this sweep wrote them).  Returns
+// whether every word written during the sweep holds its value; the dataflow
+// sweep issues this first round as soon as the cell's record is known and
+// repeats it in the wait only if a word was missing.
+struct FIn {
+    float ain[STA_MAX_ARCS], sin[STA_MAX_ARCS], zin[STA_MAX_ARCS];
+};
+
+template <bool kPoll>
+__device__ __forceinline__ bool fcell_fanin(const BatchState& bs, const FCell& f, const Lane& L, bool lse, bool stall,
+                                            FIn& in) {
+    const int Bp = bs.Bp, b = L.b, el = L.el;
+    bool ok = !stall;  // the test hook's stalled task never sees its inputs
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        in.ain[k] = in.sin[k] = in.zin[k] = 0.f;
+        if (f.t >= 0 && k < f.na) {
+            const int r = (f.rfi >> k) & 1;
+            const int row = 4 * f.pin[k] + 2 * el + r;
+            in.ain[k] = kPoll ? ld_poll(bs.at + ix(row, Bp, b)) : __ldcg(bs.at + ix(row, Bp, b));
+            in.sin[k] = kPoll ? ld_poll(bs.slew + ix(row, Bp, b)) : __ldcg(bs.slew + ix(row, Bp, b));
+            if (lse && el)
+                in.zin[k] = kPoll ? ld_poll(bs.ats + ix(2 * f.pin[k] + r, Bp, b))
+                                  : __ldcg(bs.ats + ix(2 * f.pin[k] + r, Bp, b));
+            if ((f.dyn >> k) & 1)
+                ok &= written(in.ain[k]) & written(in.sin[k]) & (!(lse && el) || written(in.zin[k]));
+        }
+    }
+    return ok;
+}
+
 // Driver-cell evaluation for one condition (late max / early min over the
-// arcs, worst slew, Eq. 4 LSE for the late conditions).  The fanin values of
-// all arcs are loaded together (through L2: other warps of this sweep wrote them).
+// arcs, worst slew, Eq. 4 LSE for the late conditions) from the fanin words
+// of fcell_fanin; `ok` is its first round's result, and in the dataflow sweep
+// the wait repeats the round until every lane has all its words.
 template <bool kPoll>
 __device__ __forceinline__ FOut fcell_eval(const DevNet& g, const BatchState& bs, const FCell& f, int dp,
-                                           const Lane& L, float gamma, bool lse, int32_t* abort_word,
-                                           bool stall = false) {
+                                           const Lane& L, float gamma, bool lse, int32_t* abort_word, bool stall,
+                                           FIn& in, bool ok) {
     const int Bp = bs.Bp, b = L.b, el = L.el, rf = L.rf;
     FOut o;
     if (f.t < 0) {  // asserted driver: constant values set at creation
@@ -117,29 +155,9 @@ __device__ __forceinline__ FOut fcell_eval(const DevNet& g, const BatchState& bs
         o.z = (el && lse) ? bs.ats[ix(2 * dp + rf, Bp, b)] : 0.f;
         return o;
     }
-    float ain[STA_MAX_ARCS], sin[STA_MAX_ARCS], zin[STA_MAX_ARCS];
-    // the fanin words of all arcs together; in the dataflow sweep this is the
-    // wait: repeated until every word written during the sweep holds its value
-    auto load = [&]() {
-        bool ok = !stall;  // the test hook's stalled task never sees its inputs
-#pragma unroll
-        for (int k = 0; k < STA_MAX_ARCS; ++k) {
-            ain[k] = sin[k] = zin[k] = 0.f;
-            if (k < f.na) {
-                const int r = (f.rfi >> k) & 1;
-                const int row = 4 * f.pin[k] + 2 * el + r;
-                ain[k] = kPoll ? ld_relaxed_f(bs.at + ix(row, Bp, b)) : __ldcg(bs.at + ix(row, Bp, b));
-                sin[k] = kPoll ? ld_relaxed_f(bs.slew + ix(row, Bp, b)) : __ldcg(bs.slew + ix(row, Bp, b));
-                if (lse && el)
-                    zin[k] = kPoll ? ld_relaxed_f(bs.ats + ix(2 * f.pin[k] + r, Bp, b))
-                                   : __ldcg(bs.ats + ix(2 * f.pin[k] + r, Bp, b));
-                if ((f.dyn >> k) & 1) ok &= written(ain[k]) & written(sin[k]) & (!(lse && el) || written(zin[k]));
-            }
-        }
-        return ok;
-    };
-    if constexpr (kPoll) poll_words(load, abort_word);
-    else load();
+    if constexpr (kPoll) {
+        if (!__all_sync(kFull, ok)) poll_words([&]() { return fcell_fanin<true>(bs, f, L, lse, stall, in); }, abort_word);
+    }
     float best_at = el ? -kInf : kInf, best_sl = el ? -kInf : kInf, m = -kInf;
     float cand[STA_MAX_ARCS];
 #pragma unroll
@@ -148,15 +166,15 @@ __device__ __forceinline__ FOut fcell_eval(const DevNet& g, const BatchState& bs
         if (k < f.na) {
             int is;
             float ts;
-            seg_reg(f.sidx, f.sinv, sin[k], is, ts);
+            seg_reg(f.sidx, f.sinv, in.sin[k], is, ts);
             float4 dq, sq;
             cell_corners(g, f.t, k, rf, is, f.jl, dq, sq);
             const float D = lerp_cell(dq, ts, f.ul);
             const float S = lerp_cell(sq, ts, f.ul);
-            const float v = ain[k] + D;
+            const float v = in.ain[k] + D;
             best_at = el ? fmaxf(best_at, v) : fminf(best_at, v);
             best_sl = el ? fmaxf(best_sl, S) : fminf(best_sl, S);
-            cand[k] = zin[k] + D;
+            cand[k] = in.zin[k] + D;
             m = fmaxf(m, cand[k]);
         }
     }
@@ -172,18 +190,31 @@ __device__ __forceinline__ FOut fcell_eval(const DevNet& g, const BatchState& bs
 __device__ __forceinline__ void store_pin(const BatchState& bs, int p, const Lane& L, float at, float sl, float z,
                                           bool lse) {
     const int Bp = bs.Bp;  // strong stores: words that other tasks of the sweep poll
-    st_relaxed_f(bs.at + ix(4 * p + L.c, Bp, L.b), at);
-    st_relaxed_f(bs.slew + ix(4 * p + L.c, Bp, L.b), sl);
-    if (lse && L.el) st_relaxed_f(bs.ats + ix(2 * p + L.rf, Bp, L.b), z);
+    st_poll(bs.at + ix(4 * p + L.c, Bp, L.b), at);
+    st_poll(bs.slew + ix(4 * p + L.c, Bp, L.b), sl);
+    if (lse && L.el) st_poll(bs.ats + ix(2 * p + L.rf, Bp, L.b), z);
 }
 
-// wire step to the sinks [s0, s1): every lane its condition
+// wire step to the sinks [s0, s1): every lane its condition; the positions and
+// capacitances of four sinks are loaded before their stores
 __device__ __forceinline__ void store_sinks(const DevNet& g, const BatchState& bs, int s0, int s1, const Lane& L,
                                             float2 xyd, const FOut& o, bool lse) {
-#pragma unroll 4
-    for (int p = s0; p < s1; ++p) {
-        const Wire w = wire(g, bs.xy[ix(p, bs.Bp, L.b)], xyd, __ldg(g.pin_cap + p));
-        store_pin(bs, p, L, o.at + w.D, sqrtf(fmaf(o.sl, o.sl, w.I * w.I)), o.z + w.D, lse);
+    for (int p0 = s0; p0 < s1; p0 += 4) {
+        float2 xy[4];
+        float cap[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = min(p0 + u, s1 - 1);
+            xy[u] = bs.xy[ix(p, bs.Bp, L.b)];
+            cap[u] = __ldg(g.pin_cap + p);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (p0 + u < s1) {
+                const Wire w = wire(g, xy[u], xyd, cap[u]);
+                store_pin(bs, p0 + u, L, o.at + w.D, sqrtf(fmaf(o.sl, o.sl, w.I * w.I)), o.z + w.D, lse);
+            }
+        }
     }
 }
 
@@ -203,36 +234,29 @@ __device__ __forceinline__ float net_load(const DevNet& g, const BatchState& bs,
 
 // kWait: dataflow sweep (wait for the producers; the net's load is computed
 // here); otherwise a level-synchronous sweep (producers ran in earlier
-// launches; every load comes from the prologue)
+// launches; every load comes from the prologue).  The first round of the
+// wait is issued as soon as the cell's record is known, before the net's load
+// and the table segment.
 template <bool lse, bool kWait>
 __device__ void bfwd_nets(const DevNet& g, const BatchState& bs, const DfState& d, int q, int n0, int nn,
                           const Lane& L, float gamma, bool stall = false) {
     const int Bp = bs.Bp;
-    // before the wait: the first net's load (static) and its cell description
-    const int dp0 = g.net_ptr[n0], e0 = g.net_ptr[n0 + 1];
-    const float2 xyd0 = bs.xy[ix(dp0, Bp, L.b)];
-    const float ld0 = kWait ? net_load(g, bs, dp0, e0, L, xyd0) : bs.load[ix(n0, Bp, L.b)];
-    const FCell f0 = fcell(g, d, n0, L.rf, ld0);
-    if constexpr (kWait) {
-        if (L.c == 0) bs.load[ix(n0, Bp, L.b)] = ld0;
-    }
-
     for (int j = 0; j < nn; ++j) {
         const int n = n0 + j;
-        const int dp = j ? g.net_ptr[n] : dp0, e = j ? g.net_ptr[n + 1] : e0;
-        const float2 xyd = j ? bs.xy[ix(dp, Bp, L.b)] : xyd0;
-        FCell f = f0;
-        if (j) {
-            float ld;
-            if constexpr (kWait) {
-                ld = net_load(g, bs, dp, e, L, xyd);
-                if (L.c == 0) bs.load[ix(n, Bp, L.b)] = ld;
-            } else {
-                ld = bs.load[ix(n, Bp, L.b)];
-            }
-            f = fcell(g, d, n, L.rf, ld);
+        const int dp = g.net_ptr[n], e = g.net_ptr[n + 1];
+        FCell f = fcell_topo(g, n, L.rf);
+        FIn in;
+        const bool ok = fcell_fanin<kWait>(bs, f, L, lse, stall, in);
+        const float2 xyd = bs.xy[ix(dp, Bp, L.b)];
+        float ld;
+        if constexpr (kWait) {
+            ld = net_load(g, bs, dp, e, L, xyd);
+            if (L.c == 0) bs.load[ix(n, Bp, L.b)] = ld;
+        } else {
+            ld = bs.load[ix(n, Bp, L.b)];
         }
-        const FOut o = fcell_eval<kWait>(g, bs, f, dp, L, gamma, lse, d.abort_word, stall);
+        fcell_lib(g, f, ld);
+        const FOut o = fcell_eval<kWait>(g, bs, f, dp, L, gamma, lse, d.abort_word, stall, in, ok);
         if (f.t >= 0) store_pin(bs, dp, L, o.at, o.sl, o.z, lse);
         store_sinks(g, bs, dp + 1, e, L, xyd, o, lse);
     }
@@ -245,10 +269,12 @@ __device__ void bfwd_chunk(const DevNet& g, const BatchState& bs, const DfState&
                            const Lane& L, float gamma, bool stall = false) {
     const int Bp = bs.Bp;
     const int dp = g.net_ptr[n];
+    FCell f = fcell_topo(g, n, L.rf);
+    FIn in;
+    const bool ok = fcell_fanin<kWait>(bs, f, L, lse, stall, in);
     const float2 xyd = bs.xy[ix(dp, Bp, L.b)];
-    const FCell f = fcell(g, d, n, L.rf, bs.load[ix(n, Bp, L.b)]);
-
-    const FOut o = fcell_eval<kWait>(g, bs, f, dp, L, gamma, lse, d.abort_word, stall);
+    fcell_lib(g, f, bs.load[ix(n, Bp, L.b)]);
+    const FOut o = fcell_eval<kWait>(g, bs, f, dp, L, gamma, lse, d.abort_word, stall, in, ok);
     if (f.t >= 0 && p0 == dp + 1) store_pin(bs, dp, L, o.at, o.sl, o.z, lse);
     store_sinks(g, bs, p0, p0 + cnt, L, xyd, o, lse);
 }

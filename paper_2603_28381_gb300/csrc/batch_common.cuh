@@ -13,6 +13,22 @@ namespace {
 // per-placement state is pin-major, placement-minor: value[row * Bp + b]
 __device__ __forceinline__ size_t ix(int row, int Bp, int b) { return (size_t)row * Bp + b; }
 
+// Strong relaxed load / store of a polled word without a compiler memory
+// barrier.  A batched task takes each polled value from the poll itself and
+// never reads data that another word's store publishes (the one such hand-off,
+// a large net's d loss / d load, goes through wait_ready's acquire), so the
+// compiler may issue the task's independent plain loads and arithmetic across
+// these; the accesses themselves stay in program order (volatile).
+__device__ __forceinline__ float ld_poll(const float* p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_poll(float* p, float v) {
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
+}
+
 // ---------------------------------------------------------------------------
 // Wire step of one sink (Eqs. 1-3 on a star) -- same arithmetic as the
 // single-placement kernels.

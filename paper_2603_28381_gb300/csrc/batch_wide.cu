@@ -153,12 +153,12 @@ __device__ __forceinline__ void wbcell_apply(const BatchState& bs, const WBCell&
                 const int el = c >> 1, rf = c & 1;
                 const int r = (bc.rfi[rf] >> k) & 1;
                 // strong stores: words that the sinks' tasks poll
-                if (mode & 1) st_relaxed_f(bs.rat + ix(4 * bc.pin[k] + 2 * el + r, Bp, b), R[c] - bc.adel[k][c]);
+                if (mode & 1) st_poll(bs.rat + ix(4 * bc.pin[k] + 2 * el + r, Bp, b), R[c] - bc.adel[k][c]);
                 if ((mode & 2) && el) {
                     const float gD = GA[rf] * bc.w[k][rf];
                     // a capturing clock pin also carries its endpoint's setup term
-                    st_relaxed_f(bs.g_ats + ix(2 * bc.pin[k] + r, Bp, b), (bs.cap_seed && k == 0) ? gD + bc.cs[rf] : gD);
-                    st_relaxed_f(bs.g_slew + ix(2 * bc.pin[k] + r, Bp, b),
+                    st_poll(bs.g_ats + ix(2 * bc.pin[k] + r, Bp, b), (bs.cap_seed && k == 0) ? gD + bc.cs[rf] : gD);
+                    st_poll(bs.g_slew + ix(2 * bc.pin[k] + r, Bp, b),
                                  fmaf(gD, bc.dDs[k][rf], k == bc.amax[rf] ? GS[rf] * bc.dSs[rf] : 0.f));
                     gl[c] = fmaf(gD, bc.dDl[k][rf], gl[c]);
                 }
@@ -185,38 +185,53 @@ __device__ __forceinline__ WSink wsink(const DevNet& g, const BatchState& bs, co
                                        float2 xyd, const float* sld, float gamma, const BSeed& sd) {
     const int Bp = bs.Bp;
     WSink s;
-    s.w = wire(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p));
-    const bool dyn = d.pin_cons[p] >= 0;  // the same for every lane
+    // one round of loads: the sink's position, capacitance, consumer and late
+    // slews (plain) together with the words its producers write (polled); the
+    // wait repeats only the polled ones.  A sink without a consumer task
+    // (pin_cons < 0, the same for every lane) holds no word of the sweep: its
+    // adjoint loads are discarded and its seed computed below.
+    const float2 xy = bs.xy[ix(p, Bp, b)];
+    const float cap = __ldg(g.pin_cap + p);
+    const int cons = d.pin_cons[p];
+    float sl[2] = {0.f, 0.f};
+    if (mode & 2) {
+        sl[0] = bs.slew[ix(4 * p + 2, Bp, b)];
+        sl[1] = bs.slew[ix(4 * p + 3, Bp, b)];
+    }
     float rr[4] = {0.f, 0.f, 0.f, 0.f}, ga[2] = {0.f, 0.f}, gs[2] = {0.f, 0.f};
     auto load = [&]() {
         bool ok = true;
         if (mode & 1) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                rr[c] = kPoll ? ld_relaxed_f(bs.rat + ix(4 * p + c, Bp, b)) : __ldcg(bs.rat + ix(4 * p + c, Bp, b));
+                rr[c] = kPoll ? ld_poll(bs.rat + ix(4 * p + c, Bp, b)) : __ldcg(bs.rat + ix(4 * p + c, Bp, b));
                 ok &= written(rr[c]);
             }
         }
-        if ((mode & 2) && dyn) {
+        if (mode & 2) {
 #pragma unroll
             for (int rf = 0; rf < 2; ++rf) {
-                ga[rf] = kPoll ? ld_relaxed_f(bs.g_ats + ix(2 * p + rf, Bp, b)) : __ldcg(bs.g_ats + ix(2 * p + rf, Bp, b));
-                gs[rf] = kPoll ? ld_relaxed_f(bs.g_slew + ix(2 * p + rf, Bp, b))
-                               : __ldcg(bs.g_slew + ix(2 * p + rf, Bp, b));
+                ga[rf] = kPoll ? ld_poll(bs.g_ats + ix(2 * p + rf, Bp, b)) : __ldcg(bs.g_ats + ix(2 * p + rf, Bp, b));
+                gs[rf] = kPoll ? ld_poll(bs.g_slew + ix(2 * p + rf, Bp, b)) : __ldcg(bs.g_slew + ix(2 * p + rf, Bp, b));
                 ok &= written(ga[rf]) & written(gs[rf]);
             }
         }
         return ok;
     };
-    if (kPoll && dyn) poll_words(load, d.abort_word);
-    else load();
+    const bool ok = load();
+    const bool dyn = cons >= 0;  // the same for every lane
+    if (kPoll && dyn && !__all_sync(kFull, ok)) poll_words(load, d.abort_word);
+    s.w = wire(g, xy, xyd, cap);
 #pragma unroll
     for (int c = 0; c < 4; ++c) s.r[c] = (mode & 1) ? rr[c] - s.w.D : 0.f;
 #pragma unroll
     for (int rf = 0; rf < 2; ++rf) s.ga[rf] = s.gs[rf] = s.gw[rf] = 0.f;
     if (mode & 2) {
         if (!dyn) {
-            const float rl = bs.rat[ix(4 * p + 2, Bp, b)], rfl = bs.rat[ix(4 * p + 3, Bp, b)];
+#pragma unroll
+            for (int rf = 0; rf < 2; ++rf) ga[rf] = gs[rf] = 0.f;
+            const float rl = (mode & 1) ? rr[2] : bs.rat[ix(4 * p + 2, Bp, b)];
+            const float rfl = (mode & 1) ? rr[3] : bs.rat[ix(4 * p + 3, Bp, b)];
             if (isfinite(rl)) {
                 const float sr = rl - bs.ats[ix(2 * p, Bp, b)], sf = rfl - bs.ats[ix(2 * p + 1, Bp, b)];
                 const float te = softmin3(sr, sf, gamma);
@@ -231,8 +246,7 @@ __device__ __forceinline__ WSink wsink(const DevNet& g, const BatchState& bs, co
         }
 #pragma unroll
         for (int rf = 0; rf < 2; ++rf) {
-            const float sl = bs.slew[ix(4 * p + 2 + rf, Bp, b)];
-            const float qv = sl > 0.f ? gs[rf] / sl : 0.f;
+            const float qv = sl[rf] > 0.f ? gs[rf] / sl[rf] : 0.f;
             s.ga[rf] = ga[rf];
             s.gs[rf] = qv * sld[rf];
             s.gw[rf] = fmaf(qv, s.w.I, ga[rf]);
@@ -339,17 +353,17 @@ __device__ void wbwd_part(const DevNet& g, const BatchState& bs, const DfState& 
     const int base = slot * kPartFloats;
     // strong stores: the driver step polls these words
 #pragma unroll
-    for (int c = 0; c < 4; ++c) st_relaxed_f(part + ix(base + c, Bp, b), R[c]);
+    for (int c = 0; c < 4; ++c) st_poll(part + ix(base + c, Bp, b), R[c]);
     if (mode & 2) {
 #pragma unroll
         for (int rf = 0; rf < 2; ++rf) {
-            st_relaxed_f(part + ix(base + 4 + rf, Bp, b), GA[rf]);
-            st_relaxed_f(part + ix(base + 6 + rf, Bp, b), GS[rf]);
+            st_poll(part + ix(base + 4 + rf, Bp, b), GA[rf]);
+            st_poll(part + ix(base + 6 + rf, Bp, b), GS[rf]);
         }
-        st_relaxed_f(part + ix(base + 8, Bp, b), sx);
-        st_relaxed_f(part + ix(base + 9, Bp, b), sy);
-        st_relaxed_f(part + ix(base + 10, Bp, b), hx);
-        st_relaxed_f(part + ix(base + 11, Bp, b), hy);
+        st_poll(part + ix(base + 8, Bp, b), sx);
+        st_poll(part + ix(base + 9, Bp, b), sy);
+        st_poll(part + ix(base + 10, Bp, b), hx);
+        st_poll(part + ix(base + 11, Bp, b), hy);
     }
 }
 
@@ -379,7 +393,7 @@ __device__ void wbwd_driver(const DevNet& g, const BatchState& bs, const DfState
                 const bool ok = k0 + u < nch;
 #pragma unroll
                 for (int i = 0; i < kS; ++i) {
-                    x[u][i] = ok ? ld_relaxed_f(part + ix(base + i, Bp, b)) : 0.f;
+                    x[u][i] = ok ? ld_poll(part + ix(base + i, Bp, b)) : 0.f;
                     if (ok) all &= written(x[u][i]);
                 }
             }
