@@ -295,19 +295,27 @@ __global__ void __launch_bounds__(kBlock, 4) k_bfwd(DevNet g, BatchState bs, DfS
     }
 }
 
-// Loads of the large nets (the chunk tasks read them): a block per (net,
-// placement group); warp w sums sinks w, w + 8, ... and the warps' sums are
-// added in warp order, so the result is fixed.
-__global__ void __launch_bounds__(kBlock) k_bload(DevNet g, BatchState bs, const int32_t* __restrict__ nets) {
+// Loads of the large nets (the chunk tasks read them), in chunks of at most
+// kLoadChunk sinks: a block per (chunk, group of 32 placements).  Warp w sums
+// the chunk's sinks w, w + 8, ..., the warps' sums are added in warp order,
+// and the last block of a net to finish adds the driver's capacitance and the
+// chunks' sums in chunk order, so the result is fixed (and a 20,000-sink net
+// is 79 blocks, not one).  The per-net counters return to zero for the next
+// launch.
+__global__ void __launch_bounds__(kBlock) k_bload(DevNet g, BatchState bs, const int4* __restrict__ chunks,
+                                                  float* __restrict__ part, int32_t* __restrict__ cnt) {
     __shared__ float sh[kWarpsPerBlock][32];
-    const int n = nets[blockIdx.x];
+    __shared__ int last;
+    // net, first sink, the net's first chunk, sinks | (chunks of the net << 16)
+    const int4 c = chunks[blockIdx.x];
+    const int n = c.x, p0 = c.y, first = c.z, np = c.w & 0xffff, nch = c.w >> 16;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int b = blockIdx.y * 32 + lane, Bp = bs.Bp;
-    const int dp = g.net_ptr[n], e = g.net_ptr[n + 1];
+    const int dp = g.net_ptr[n];
     const float2 xyd = bs.xy[ix(dp, Bp, b)];
     float acc = 0.f;
 #pragma unroll 4
-    for (int p = dp + 1 + w; p < e; p += kWarpsPerBlock) {
+    for (int p = p0 + w; p < p0 + np; p += kWarpsPerBlock) {
         const float2 xy = bs.xy[ix(p, Bp, b)];
         const float dist = fabsf(xy.x - xyd.x) + fabsf(xy.y - xyd.y);
         acc += fmaf(g.c, dist, __ldg(g.pin_cap + p));
@@ -315,9 +323,23 @@ __global__ void __launch_bounds__(kBlock) k_bload(DevNet g, BatchState bs, const
     sh[w][lane] = acc;
     __syncthreads();
     if (w == 0) {
-        float ld = __ldg(g.pin_cap + dp);
+        float v = 0.f;
 #pragma unroll
-        for (int k = 0; k < kWarpsPerBlock; ++k) ld += sh[k][lane];
+        for (int k = 0; k < kWarpsPerBlock; ++k) v += sh[k][lane];
+        part[(size_t)blockIdx.x * Bp + b] = v;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t* ct = cnt + (size_t)first * bs.G + blockIdx.y;
+        last = atomicAdd(ct, 1) == nch - 1;
+        if (last) *ct = 0;  // every chunk of this net and group has counted
+    }
+    __syncthreads();
+    if (last && w == 0) {
+        __threadfence();
+        float ld = __ldg(g.pin_cap + dp);
+        for (int k = 0; k < nch; ++k) ld += __ldcg(part + (size_t)(first + k) * Bp + b);
         bs.load[ix(n, Bp, b)] = ld;
     }
 }
@@ -1134,9 +1156,22 @@ int batch_max_blocks(int fwd) {
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 
-void launch_batch_load(const DevNet& g, const BatchState& bs, const int32_t* big_nets, int nbig, cudaStream_t st) {
-    if (nbig == 0) return;
-    k_bload<<<dim3(nbig, bs.G), kBlock, 0, st>>>(g, bs, big_nets);
+void launch_batch_load(const DevNet& g, const BatchState& bs, const BigChunks& c, cudaStream_t st) {
+    if (c.n == 0) return;
+    k_bload<<<dim3(c.n, bs.G), kBlock, 0, st>>>(g, bs, c.rec, c.part, c.cnt);
+}
+
+std::vector<int32_t> big_chunk_list(const std::vector<int32_t>& big_nets, const std::vector<int32_t>& net_ptr) {
+    std::vector<int32_t> rec;
+    for (int32_t n : big_nets) {
+        const int32_t dp = net_ptr[n], ns = net_ptr[n + 1] - dp - 1;
+        const int32_t nch = (ns + kLoadChunk - 1) / kLoadChunk, first = (int32_t)(rec.size() / 4);
+        for (int32_t k = 0; k < nch; ++k) {
+            const int32_t cnt = std::min(kLoadChunk, ns - k * kLoadChunk);
+            rec.insert(rec.end(), {n, dp + 1 + k * kLoadChunk, first, cnt | (nch << 16)});
+        }
+    }
+    return rec;
 }
 
 void launch_batch_fwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int lse,

@@ -97,8 +97,7 @@ struct StaHandle {
     int active = 1, active_next = 1;  // lanes the current / the next positions' calls run
     BatchState bs{};
     const int32_t* pin_int = nullptr;  // [P] internal index of each original pin
-    const int32_t* big_dev = nullptr;  // [nbig] nets whose loads the prologue computes
-    int nbig = 0;
+    BigChunks bload;  // batched: the large nets' sinks in chunks, whose loads k_bload computes
     float* qscratch = nullptr;         // device scratch of the batched pin-slack query
     size_t qscratch_bytes = 0;
     bool batch() const { return schedule == STA_SCHED_BATCH; }
@@ -113,8 +112,12 @@ struct StaHandle {
     cudaEvent_t ev_bwd = nullptr;   // latest gradient sweep done
     cudaStream_t cap = nullptr;     // private stream used for graph capture
     cudaStream_t side = nullptr;    // required-time sweep
-    cudaStream_t fork = nullptr;    // a forward's reset beside its net-RC prologue
+    cudaStream_t fork = nullptr;    // the batched sweeps' resets beside the position transpose
     cudaEvent_t ev_fork[2] = {nullptr, nullptr};
+    // batched dataflow handles: the words the next forward and fused gradient
+    // sweeps poll were reset by sta_set_positions (on `fork`, done at ev_fork[1]);
+    // a forward without new positions resets them itself
+    bool pre_reset = false;
     // graph cache
     cudaGraphExec_t gx_fwd[2] = {nullptr, nullptr};  // [lse]
     float gx_fwd_gamma[2] = {0.f, 0.f};
@@ -333,7 +336,7 @@ void enqueue_forward_batch(StaHandle* h, int lse, float gamma, cudaStream_t st) 
     if (h->bsweep == STA_BATCH_LEVELS) {
         {
             ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
-            launch_batch_load(h->g, h->bs, h->big_dev, h->nbig, st);
+            launch_batch_load(h->g, h->bs, h->bload, st);
             launch_batch_load_small(h->g, h->bs, L.shape.big, st);
         }
         for (int l = 0; l < L.L; ++l) {
@@ -347,19 +350,11 @@ void enqueue_forward_batch(StaHandle* h, int lse, float gamma, cudaStream_t st) 
     }
     cudaMemsetAsync(h->d.heads, 0, sizeof(int32_t), st);
     cudaMemsetAsync(h->d.abort_word, 0, sizeof(int32_t), st);
-    // the reset and the large nets' loads write different words: side by side
-    cudaEventRecord(h->ev_fork[0], st);
-    cudaStreamWaitEvent(h->fork, h->ev_fork[0], 0);
-    {
-        ProfScope ps(h, &h->prof_fwd, STA_PROF_RESET, h->fork);
-        launch_batch_reset(h->bs, h->d, L.P, 0, h->fork);  // the words the sweep's tasks poll
-    }
-    cudaEventRecord(h->ev_fork[1], h->fork);
-    if (h->nbig) {
+    // (the words the sweeps poll were reset before: enqueue_batch_resets)
+    if (h->bload.n) {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_NET_RC, st);
-        launch_batch_load(h->g, h->bs, h->big_dev, h->nbig, st);
+        launch_batch_load(h->g, h->bs, h->bload, st);
     }
-    cudaStreamWaitEvent(st, h->ev_fork[1], 0);
     {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_FORWARD, st);
         // (STA_BATCH_WIDE runs the lane-per-placement kernels for the backward
@@ -367,20 +362,25 @@ void enqueue_forward_batch(StaHandle* h, int lse, float gamma, cudaStream_t st) 
         // both forwards give bit-identical results)
         launch_batch_fwd(h->g, h->bs, h->d, h->grid_fwd, gamma, lse, h->stall_task, st);
     }
-    // the words the next fused gradient sweep polls, beside the endpoints (as in the
-    // single-placement forward)
-    cudaEventRecord(h->ev_fork[0], st);
-    cudaStreamWaitEvent(h->fork, h->ev_fork[0], 0);
-    {
-        ProfScope ps(h, &h->prof_fwd, STA_PROF_RESET, h->fork);
-        launch_batch_reset(h->bs, h->d, L.P, 3, h->fork);
-    }
-    cudaEventRecord(h->ev_fork[1], h->fork);
     {
         ProfScope ps(h, &h->prof_fwd, STA_PROF_ENDPOINTS, st);
         launch_batch_endpoints(h->g, h->bs, gamma, lse, st);
     }
-    cudaStreamWaitEvent(st, h->ev_fork[1], 0);
+}
+
+// The batched dataflow sweeps' polled words, set to kUnwritten before a forward:
+// the forward's (arrival / slew / LSE arrival of cell-input pins) and those of
+// the fused gradient sweep that follows it (required times, adjoints, large
+// nets' partial records).  Bandwidth-bound writes: sta_set_positions runs them
+// on the fork stream beside its position transpose (the previous positions'
+// results cannot be queried any more), a forward without new positions on its
+// own stream, the autotuner inside each candidate step.
+bool batch_resets_needed(const StaHandle* h) { return h->batch() && h->bsweep != STA_BATCH_LEVELS; }
+
+void enqueue_batch_resets(StaHandle* h, StaHandle::Prof* pr, cudaStream_t st) {
+    ProfScope ps(h, pr, STA_PROF_RESET, st);
+    launch_batch_reset(h->bs, h->d, h->lay.P, 0, st);
+    launch_batch_reset(h->bs, h->d, h->lay.P, 3, st);
 }
 
 void enqueue_backward_batch(StaHandle* h, int mode, float gamma, cudaStream_t st) {
@@ -534,8 +534,27 @@ StaStatus launch_graph_or_direct(StaHandle* h, cudaGraphExec_t* gx, float* key, 
     return check_launch();
 }
 
+// The large nets' sink chunks of the batched handle's task shape, their chunk
+// sums and their per-net counters (zero).
+StaStatus upload_big_chunks(StaHandle* h) {
+    const Layout& L = h->lay;
+    const std::vector<int32_t> rec = big_chunk_list(L.big_nets, L.net_ptr);
+    const int32_t* cp = nullptr;
+    StaStatus st = h->upload(cp, rec);
+    if (st != STA_OK) return st;
+    h->bload.rec = reinterpret_cast<const int4*>(cp);
+    h->bload.n = (int)(rec.size() / 4);
+    st = h->alloc(h->bload.part, (size_t)h->bload.n * h->bs.Bp);
+    if (st != STA_OK) return st;
+    st = h->alloc(h->bload.cnt, (size_t)h->bload.n * h->bs.G);
+    if (st != STA_OK) return st;
+    const size_t bytes = sizeof(int32_t) * (h->bload.n ? (size_t)h->bload.n * h->bs.G : 1);
+    CUDA_TRY(h->pool ? cudaMemsetAsync(h->bload.cnt, 0, bytes, 0) : cudaMemset(h->bload.cnt, 0, bytes));
+    return STA_OK;
+}
+
 // Device state of the batched schedule: per-placement arrays, the inverse pin
-// permutation, the prologue's net list, constant state broadcast to every
+// permutation, the prologue's chunk list, constant state broadcast to every
 // placement.
 StaStatus init_batch(StaHandle* h) {
     const Layout& L = h->lay;
@@ -578,8 +597,7 @@ StaStatus init_batch(StaHandle* h) {
     std::vector<int32_t> inv(P);
     for (size_t i = 0; i < P; ++i) inv[L.pin_orig[i]] = (int32_t)i;
     BSTEP(h->upload(h->pin_int, inv));
-    BSTEP(h->upload(h->big_dev, L.big_nets));
-    h->nbig = (int)L.big_nets.size();
+    BSTEP(upload_big_chunks(h));
 #undef BSTEP
     auto zero = [&](void* p, size_t bytes) { return cudaMemset(p, 0, bytes); };
     if (zero(b.xy, P * Bp * 8) || zero(b.load, N * Bp * 4) || zero(b.g_ats, 2 * P * Bp * 4) ||
@@ -623,7 +641,8 @@ StaStatus set_tasks(StaHandle* h, const TaskShape& sh) {
     for (const void* p : {(const void*)d.ftask, (const void*)d.arc_prod, (const void*)d.btask, (const void*)d.baux,
                           (const void*)d.pin_cons, (const void*)d.b_indeg, (const void*)d.b_out_ptr,
                           (const void*)d.b_out, (const void*)d.rcnt, (const void*)d.acnt, (const void*)h->bs.part,
-                          (const void*)h->bs.rpart, (const void*)h->big_dev})
+                          (const void*)h->bs.rpart, (const void*)h->bload.rec, (const void*)h->bload.part,
+                          (const void*)h->bload.cnt})
         h->release(p);
     StaStatus st = STA_OK;
 #define TSTEP(x)                     \
@@ -646,15 +665,15 @@ StaStatus set_tasks(StaHandle* h, const TaskShape& sh) {
     TSTEP(h->alloc(d.acnt, (size_t)L.TB * GT));
     TSTEP(h->alloc(h->bs.part, (size_t)L.npart * kPartFloats * h->bs.Bp));
     TSTEP(h->alloc(h->bs.rpart, (size_t)L.npart * kPartFloats * h->bs.Bp));
-    TSTEP(h->upload(h->big_dev, L.big_nets));
+    TSTEP(upload_big_chunks(h));
 #undef TSTEP
-    h->nbig = (int)L.big_nets.size();
     d.TF = L.TF;
     d.TB = L.TB;
     d.npart = L.npart;
     h->drop_graphs();
     h->have_fwd = h->have_lse = h->have_rat = false;
     h->rat_pending = false;
+    h->pre_reset = false;  // new partial-record buffers: the next forward resets them
     return STA_OK;
 }
 
@@ -1050,7 +1069,7 @@ StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDe
     if (h->profile) {  // event pairs for every launch of each sequence, made before any capture
         const size_t nl = (size_t)L.L;
         const std::pair<StaHandle::Prof*, size_t> sizes[] = {
-            {&h->prof_pos, 1}, {&h->prof_fwd, nl + 5}, {&h->prof_rat, 2 * nl + 2}, {&h->prof_adj, 2 * nl + 3},
+            {&h->prof_pos, 3}, {&h->prof_fwd, nl + 5}, {&h->prof_rat, 2 * nl + 2}, {&h->prof_adj, 2 * nl + 3},
             {&h->prof_out, 1}};
         for (const auto& ps : sizes) {
             ps.first->kind.assign(ps.second, 0);
@@ -1097,14 +1116,21 @@ StaStatus sta_set_positions(StaHandle* h, const float* xy, int on_device, void* 
         if (bytes) CUDA_TRY(cudaMemcpyAsync(h->stage, xy, bytes, cudaMemcpyHostToDevice, st));
         src = static_cast<const float2*>(h->stage);
     }
+    h->prof_pos.next = 0;
+    if (batch_resets_needed(h)) {  // beside the transpose: the next forward waits for them
+        CUDA_TRY(cudaEventRecord(h->ev_fork[0], st));
+        CUDA_TRY(cudaStreamWaitEvent(h->fork, h->ev_fork[0], 0));
+        enqueue_batch_resets(h, &h->prof_pos, h->fork);
+        CUDA_TRY(cudaEventRecord(h->ev_fork[1], h->fork));
+    }
     {
-        h->prof_pos.next = 0;
         ProfScope ps(h, &h->prof_pos, STA_PROF_POSITIONS, st);
         if (h->batch()) launch_batch_xy_in(h->bs, h->pin_int, h->lay.P, src, st);
         else launch_gather_xy(h->g, h->s, src, h->active, st);
     }
     StaStatus s3 = check_launch();
     if (s3 != STA_OK) return s3;
+    h->pre_reset = batch_resets_needed(h);
     h->have_pos = true;
     h->have_fwd = h->have_lse = h->have_rat = false;
     h->rat_pending = false;  // its results could no longer be queried
@@ -1120,6 +1146,11 @@ StaStatus sta_forward(StaHandle* h, uint32_t flags, float gamma, void* stream) {
     cudaStream_t st = as_stream(stream);
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_bwd, 0));
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
+    if (batch_resets_needed(h)) {  // the sweeps' polled words: reset with the positions, or now
+        if (h->pre_reset) CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fork[1], 0));
+        else enqueue_batch_resets(h, &h->prof_pos, st);
+        h->pre_reset = false;
+    }
     if (h->expire_next) {
         // one forward task waits for a producer that never comes: its wait runs
         // into the budget, the sweep ends early and the expiry is reported
@@ -1295,6 +1326,7 @@ StaStatus sta_autotune(StaHandle* h, const int32_t* tile_pins, int32_t n_tile, c
                 // one step (forward with LSE and required times, fused gradient sweep) as a graph
                 cudaGraphExec_t gx = nullptr;
                 status = capture(h, &gx, [&](cudaStream_t c) {
+                    if (batch_resets_needed(h)) enqueue_batch_resets(h, nullptr, c);
                     enqueue_forward(h, 1, gamma, c);
                     enqueue_backward(h, 3, gamma, c);
                 });
@@ -1543,19 +1575,19 @@ StaStatus sta_query_profile(StaHandle* h, double* ms, int32_t* launches) {
         batch_bwd_phases(L, 3, ph);
         const int32_t nb = (int32_t)ph.size();
         batch_bwd_phases(L, 1, ph);
-        launches[STA_PROF_NET_RC] = (h->nbig > 0 ? 1 : 0) + (L.N > 0 ? 1 : 0);
+        launches[STA_PROF_NET_RC] = (h->bload.n > 0 ? 1 : 0) + (L.N > 0 ? 1 : 0);
         launches[STA_PROF_FORWARD] = batch_fwd_levels(L);
         launches[STA_PROF_REQUIRED] = h->last_fused ? 0 : (int32_t)ph.size();
         launches[STA_PROF_SEED] = 1 + (h->g.ep_clk ? 1 : 0);
         launches[STA_PROF_ADJOINT] = nb;
     } else if (h->batch()) {
         // each sweep is preceded by the reset of the words its tasks poll
-        launches[STA_PROF_NET_RC] = h->nbig > 0 ? 1 : 0;
+        launches[STA_PROF_NET_RC] = h->bload.n > 0 ? 1 : 0;
         launches[STA_PROF_FORWARD] = L.TF > 0 ? 1 : 0;
         launches[STA_PROF_REQUIRED] = (L.TB > 0 && !h->last_fused) ? 1 : 0;
         launches[STA_PROF_SEED] = 1 + (h->g.ep_clk ? 1 : 0);  // weights (+ capture-clock seeds)
         launches[STA_PROF_ADJOINT] = L.TB > 0 ? 1 : 0;
-        // the forward resets its own polled words and the fused sweep's
+        // the forward's polled words and the fused sweep's, reset with the positions
         launches[STA_PROF_RESET] = 2 + (h->last_fused ? 0 : launches[STA_PROF_REQUIRED] + launches[STA_PROF_ADJOINT]);
     } else if (h->schedule == STA_SCHED_DATAFLOW) {
         // the prologue (large-net RC + reset of the forward's polled words) is one

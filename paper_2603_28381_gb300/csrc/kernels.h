@@ -177,7 +177,17 @@ int batch_max_blocks(int fwd);
 int batch_wide_max_blocks();
 void launch_batch_bwd_wide(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int mode,
                            cudaStream_t st);
-void launch_batch_load(const DevNet& g, const BatchState& bs, const int32_t* big_nets, int nbig, cudaStream_t st);
+// the large nets' sinks in chunks of at most kLoadChunk (k_bload): per chunk an
+// int4 {net, first sink, the net's first chunk, sinks | (chunks of the net << 16)}
+constexpr int kLoadChunk = 256;
+struct BigChunks {
+    const int4* rec = nullptr;  // [n]
+    int n = 0;
+    float* part = nullptr;      // [n][Bp] chunk sums
+    int32_t* cnt = nullptr;     // [n][G] finished chunks of a net (at its first chunk), zero between launches
+};
+std::vector<int32_t> big_chunk_list(const std::vector<int32_t>& big_nets, const std::vector<int32_t>& net_ptr);
+void launch_batch_load(const DevNet& g, const BatchState& bs, const BigChunks& c, cudaStream_t st);
 void launch_batch_fwd(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int lse,
                       int stall_task, cudaStream_t st);
 void launch_batch_endpoints(const DevNet& g, const BatchState& bs, float gamma, int lse, cudaStream_t st);
