@@ -279,19 +279,29 @@ __device__ void bfwd_chunk(const DevNet& g, const BatchState& bs, const DfState&
     store_sinks(g, bs, p0, p0 + cnt, L, xyd, o, lse);
 }
 
+constexpr int kFwdGrab = 2;
+
 template <bool lse>
 __global__ void __launch_bounds__(kBlock, 4) k_bfwd(DevNet g, BatchState bs, DfState d, float gamma,
                                                     int stall_task) {
     const int GT = bs.GT;
     const int Q = d.TF * GT;
-    int q = grab(d.heads + 0);
-    while (q < Q) {
-        const int t = q / GT, gq = q - t * GT;
-        const Lane L = lane_of(gq);
-        const int4 task = d.ftask[t];
-        if (task.y > 0) bfwd_nets<lse, true>(g, bs, d, q, task.x, task.y, L, gamma, t == stall_task);
-        else bfwd_chunk<lse, true>(g, bs, d, q, task.x, task.z, task.w, L, gamma, t == stall_task);
-        q = grab(d.heads + 0);  // the next task only once this one is done (none waits reserved)
+    // Two queue entries per grab (usually one task for two groups of 8
+    // placements), taken in order: half the atomics on the queue head, which
+    // at 64 placements sees a million grabs per sweep (measured 13% faster than
+    // one entry, 4 and 8 entries slower again).  The smallest unfinished entry
+    // is always the one its warp is running, and its producers have smaller
+    // entries, so the sweep still progresses.
+    int q0 = grab_n(d.heads + 0, kFwdGrab);
+    while (q0 < Q) {
+        for (int q = q0; q < q0 + kFwdGrab && q < Q; ++q) {
+            const int t = q / GT, gq = q - t * GT;
+            const Lane L = lane_of(gq);
+            const int4 task = d.ftask[t];
+            if (task.y > 0) bfwd_nets<lse, true>(g, bs, d, q, task.x, task.y, L, gamma, t == stall_task);
+            else bfwd_chunk<lse, true>(g, bs, d, q, task.x, task.z, task.w, L, gamma, t == stall_task);
+        }
+        q0 = grab_n(d.heads + 0, kFwdGrab);  // the next entries only once these are done
     }
 }
 

@@ -29,6 +29,13 @@ __device__ __forceinline__ void st_poll(float* p, float v) {
     asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
 }
 
+// the first of n consecutive queue entries for the warp
+__device__ __forceinline__ int grab_n(int32_t* head, int n) {
+    int t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(head, n);
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
 // ---------------------------------------------------------------------------
 // Wire step of one sink (Eqs. 1-3 on a star) -- same arithmetic as the
 // single-placement kernels.
