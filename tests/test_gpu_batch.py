@@ -249,3 +249,43 @@ def test_wide_sweep_equals_narrow_bitwise(case):
             assert np.array_equal(wide[b][k], narrow[b][k], equal_nan=True), (case, b, k)
         assert wide[b]["summary"] == narrow[b]["summary"], (case, b)
     _check_all(nl, lib, xyb, W, 10.0, wide, which=[len(wide) - 1])
+
+
+@pytest.mark.parametrize("sweep", ["dataflow", "wide"])
+def test_repeated_forward_without_new_positions(sweep):
+    # the sweeps' polled words are reset with the positions; a second forward on
+    # the same positions (here with another gamma, so every LSE arrival changes)
+    # resets them itself, and an autotuned handle resets inside each candidate:
+    # every result equals the one-forward sequence bit for bit
+    import torch
+    import paper_2603_28381_gb300 as sta
+    w = netgen.superblue_like(3, scale=0.02, depth=40)
+    B = 12
+    xyb, W = _placements(w, B), _weights(B)
+    ref = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, sweep=sweep, tile_pins=1, chunk=16)
+    eng = sta.StaEngine(w.netlist, w.library, schedule="batch", num_placements=B, tile_pins=1, chunk=16,
+                        batch_sweep=sweep)
+    eng.set_positions(torch.as_tensor(xyb).cuda())
+    eng.forward(gamma=3.0, lse=True, rat=True)
+    eng.backward_grad(torch.as_tensor(W).cuda())
+    eng.forward(gamma=10.0, lse=True, rat=True)  # no new positions: resets on its own stream
+    g2 = eng.backward_grad(torch.as_tensor(W).cuda()).cpu().numpy()
+    pins, ep, summ = eng.pins(), eng.endpoints(), eng.summary()
+    for b in range(B):
+        for k in ("at", "slew", "rat", "ats", "slack"):
+            assert np.array_equal(pins[k][b], ref[b][k], equal_nan=True), (b, k)
+        assert np.array_equal(ep[b], ref[b]["ep_slack"], equal_nan=True), b
+        assert summ[b] == ref[b]["summary"], b
+        assert np.array_equal(g2[b], ref[b]["grad"]), b
+    eng.forward(gamma=3.0, lse=True, rat=True)
+    res = tp.run_gpu_batch(w.netlist, w.library, xyb, 10.0, W, engine=eng)  # new positions: reset beside them
+    for b in range(B):
+        for k in ("at", "slew", "rat", "ats", "slack", "ep_slack", "grad"):
+            assert np.array_equal(res[b][k], ref[b][k], equal_nan=True), (b, k)
+        assert res[b]["summary"] == ref[b]["summary"], b
+    eng.autotune(tile_pins=(1, 2), chunks=(16,), sweeps=(sweep,), reps=2)
+    eng.forward(gamma=10.0, lse=True, rat=True)
+    g3 = eng.backward_grad(torch.as_tensor(W).cuda()).cpu().numpy()
+    eng.close()
+    _check_all(w.netlist, w.library, xyb, W, 10.0,
+               [dict(ref[b], grad=g3[b]) for b in range(B)], which=[0, 11])
