@@ -146,9 +146,11 @@ __device__ __forceinline__ void signal_consumers(int32_t* cnt, const int32_t* ou
 }
 
 // cooperative launch: every block of the grid is resident at once (the waits
-// rely on it); `grid` must not exceed the kernel's co-resident block count
+// rely on it); `grid` must not exceed the kernel's co-resident block count.  A
+// refused launch returns its error, which also stays the thread's last runtime
+// error for the caller's check after the launch.
 template <typename K, typename... Args>
-void launch_coop(K kernel, int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+cudaError_t launch_coop(K kernel, int grid, int block, size_t smem, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
@@ -159,7 +161,7 @@ void launch_coop(K kernel, int grid, int block, size_t smem, cudaStream_t st, Ar
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, args...);
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 
