@@ -39,47 +39,84 @@ __device__ __forceinline__ WLane wlane(int gw) {
 // Backward
 // ---------------------------------------------------------------------------
 
+// 128-thread blocks, 5 per SM: 20 warps per SM (with 256-thread blocks at 128
+// registers 16 fitted; measured 5% slower)
+constexpr int kWBlock = 128;
+
 // The driver cell's backward terms for the four conditions of one placement,
 // all from forward results (as BCell of batch.cu): arc delays of every
 // condition (required times); for the late conditions (index rf) the LSE
-// weights, the NLDM partials, the late-slew arc and its slew partials.
+// weights, the NLDM partials, the late-slew arc and its slew partials.  The
+// per-arc terms live in the lane's column of shared memory (WArc), so the arc
+// loops run rolled: loops unrolled over register arrays made four copies of
+// the cell's lookups, and the kernel's instruction fetch stalled on them.
 struct WBCell {
     int t, na;
     int rfi[2];
-    int pin[STA_MAX_ARCS];
-    float adel[STA_MAX_ARCS][4];
-    float w[STA_MAX_ARCS][2], dDs[STA_MAX_ARCS][2], dDl[STA_MAX_ARCS][2];
+    int pin0;  // the first arc's input pin (a capturing clock pin's seed)
     int amax[2];
     float dSs[2], dSl[2];
     float cs[2];  // propagated clock: the setup seed of a one-input cell's clock pin (rising input)
 };
 
+// Word w of the lane's column: [w * kWBlock + threadIdx.x].  Per arc k: input
+// pin, input slews of the four conditions, LSE arrivals of the two late input
+// transitions, delays of the four conditions, and per late condition the LSE
+// weight, d delay / d slew and d delay / d load.
+struct WArc {
+    int* pin;  // [k]
+    float* f;  // kSin + 4k + c, kZin + 2k + rf, kDel + 4k + c, kW / kDs / kDl + 2k + rf
+    static constexpr int kSin = 0, kZin = 16, kDel = 24, kW = 40, kDs = 48, kDl = 56, kWords = 64;
+    __device__ __forceinline__ float& at(int w) const { return f[w * kWBlock + threadIdx.x]; }
+    __device__ __forceinline__ int& pin_of(int k) const { return pin[k * kWBlock + threadIdx.x]; }
+};
+
+__device__ __forceinline__ WArc warc() {
+    __shared__ float f[WArc::kWords * kWBlock];
+    __shared__ int pin[STA_MAX_ARCS * kWBlock];
+    WArc a;
+    a.f = f;
+    a.pin = pin;
+    return a;
+}
+
 template <int mode>
 __device__ __forceinline__ WBCell wbcell_pre(const DevNet& g, const BatchState& bs, int n, int dp, int b,
                                              float gamma) {
     const int Bp = bs.Bp;
+    const WArc A = warc();
     WBCell bc;
     const int4 q0 = __ldg(g.net_desc + 2 * n), q1 = __ldg(g.net_desc + 2 * n + 1);  // one record
     bc.t = q0.x;
     bc.na = q0.z;
-    const int dpin[STA_MAX_ARCS] = {q1.x, q1.y, q1.z, q1.w};
+    bc.pin0 = q1.x;
 #pragma unroll
     for (int rf = 0; rf < 2; ++rf) {
         bc.rfi[rf] = 0;
         bc.amax[rf] = -1;
         bc.dSs[rf] = bc.dSl[rf] = bc.cs[rf] = 0.f;
     }
-#pragma unroll
-    for (int k = 0; k < STA_MAX_ARCS; ++k) {
-        bc.pin[k] = 0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) bc.adel[k][c] = 0.f;
-#pragma unroll
-        for (int rf = 0; rf < 2; ++rf) bc.w[k][rf] = bc.dDs[k][rf] = bc.dDl[k][rf] = 0.f;
-    }
     if (bc.t < 0) return bc;
     const int t = bc.t;
     const int un = q0.w >> 4;
+    const int dpin[STA_MAX_ARCS] = {q1.x, q1.y, q1.z, q1.w};
+    // the arcs' input words first, all loads in one round (unrolled: loads and
+    // shared-memory stores only)
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        if (k < bc.na) {
+            A.pin_of(k) = dpin[k];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int el = c >> 1, rf = c & 1;
+                const int r = rf ^ ((un >> k) & 1);
+                if (el == 0) bc.rfi[rf] |= r << k;
+                if (!((mode & 1) || el)) continue;  // mode 2 needs the late conditions only
+                A.at(WArc::kSin + 4 * k + c) = bs.slew[ix(4 * dpin[k] + 2 * el + r, Bp, b)];
+                if ((mode & 2) && el) A.at(WArc::kZin + 2 * k + rf) = bs.ats[ix(2 * dpin[k] + r, Bp, b)];
+            }
+        }
+    }
     const float ld = bs.load[ix(n, Bp, b)];
     const float* li = g.lib_idx + t * kLibStride + 8;
     const int jl = axis_seg(li, ld);
@@ -91,37 +128,32 @@ __device__ __forceinline__ WBCell wbcell_pre(const DevNet& g, const BatchState& 
         zd[1] = bs.ats[ix(2 * dp + 1, Bp, b)];
     }
     float best[2] = {-kInf, -kInf};
+#pragma unroll 1
+    for (int k = 0; k < bc.na; ++k) {
 #pragma unroll
-    for (int k = 0; k < STA_MAX_ARCS; ++k) {
-        if (k < bc.na) {
-            bc.pin[k] = dpin[k];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int el = c >> 1, rf = c & 1;
-                const int r = rf ^ ((un >> k) & 1);
-                if (el == 0) bc.rfi[rf] |= r << k;
-                if (!((mode & 1) || el)) continue;  // mode 2 needs the late conditions only
-                const float sin = bs.slew[ix(4 * bc.pin[k] + 2 * el + r, Bp, b)];
-                const float* si = g.lib_idx + t * kLibStride;
-                const int is = axis_seg(si, sin);
-                const float inv_s = __ldg(g.lib_inv + t * kLibStride + is);
-                const float ts = (sin - __ldg(si + is)) * inv_s;
-                float4 dq, sq;
-                cell_corners(g, t, k, rf, is, jl, dq, sq);
-                float dDs, dDl, dSs, dSl;
-                const float D = lerp_cell_grad(dq, ts, ul, inv_s, inv_l, dDs, dDl);
-                bc.adel[k][c] = D;
-                if ((mode & 2) && el) {
-                    const float S = lerp_cell_grad(sq, ts, ul, inv_s, inv_l, dSs, dSl);
-                    bc.dDs[k][rf] = dDs;
-                    bc.dDl[k][rf] = dDl;
-                    bc.w[k][rf] = expf((bs.ats[ix(2 * bc.pin[k] + r, Bp, b)] + D - zd[rf]) / gamma);
-                    if (S > best[rf]) {
-                        best[rf] = S;
-                        bc.amax[rf] = k;
-                        bc.dSs[rf] = dSs;
-                        bc.dSl[rf] = dSl;
-                    }
+        for (int c = 0; c < 4; ++c) {
+            const int el = c >> 1, rf = c & 1;
+            if (!((mode & 1) || el)) continue;
+            const float sin = A.at(WArc::kSin + 4 * k + c);
+            const float* si = g.lib_idx + t * kLibStride;
+            const int is = axis_seg(si, sin);
+            const float inv_s = __ldg(g.lib_inv + t * kLibStride + is);
+            const float ts = (sin - __ldg(si + is)) * inv_s;
+            float4 dq, sq;
+            cell_corners(g, t, k, rf, is, jl, dq, sq);
+            float dDs, dDl, dSs, dSl;
+            const float D = lerp_cell_grad(dq, ts, ul, inv_s, inv_l, dDs, dDl);
+            A.at(WArc::kDel + 4 * k + c) = D;
+            if ((mode & 2) && el) {
+                const float S = lerp_cell_grad(sq, ts, ul, inv_s, inv_l, dSs, dSl);
+                A.at(WArc::kDs + 2 * k + rf) = dDs;
+                A.at(WArc::kDl + 2 * k + rf) = dDl;
+                A.at(WArc::kW + 2 * k + rf) = expf((A.at(WArc::kZin + 2 * k + rf) + D - zd[rf]) / gamma);
+                if (S > best[rf]) {
+                    best[rf] = S;
+                    bc.amax[rf] = k;
+                    bc.dSs[rf] = dSs;
+                    bc.dSl[rf] = dSl;
                 }
             }
         }
@@ -131,7 +163,7 @@ __device__ __forceinline__ WBCell wbcell_pre(const DevNet& g, const BatchState& 
     if ((mode & 2) && bs.cap_seed && bc.na == 1) {
 #pragma unroll
         for (int rf = 0; rf < 2; ++rf)
-            if ((bc.rfi[rf] & 1) == 0) bc.cs[rf] = __ldcg(bs.cap_seed + ix(bc.pin[0], Bp, b));
+            if ((bc.rfi[rf] & 1) == 0) bc.cs[rf] = __ldcg(bs.cap_seed + ix(bc.pin0, Bp, b));
     }
     return bc;
 }
@@ -143,25 +175,26 @@ template <int mode>
 __device__ __forceinline__ void wbcell_apply(const BatchState& bs, const WBCell& bc, int b, const float* R,
                                              const float* GA, const float* GS, float* gl) {
     const int Bp = bs.Bp;
+    const WArc A = warc();
 #pragma unroll
     for (int c = 0; c < 4; ++c) gl[c] = 0.f;
+    if (bc.t < 0) return;
+#pragma unroll 1
+    for (int k = 0; k < bc.na; ++k) {
+        const int pin = A.pin_of(k);
 #pragma unroll
-    for (int k = 0; k < STA_MAX_ARCS; ++k) {
-        if (k < bc.na) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int el = c >> 1, rf = c & 1;
-                const int r = (bc.rfi[rf] >> k) & 1;
-                // strong stores: words that the sinks' tasks poll
-                if (mode & 1) st_poll(bs.rat + ix(4 * bc.pin[k] + 2 * el + r, Bp, b), R[c] - bc.adel[k][c]);
-                if ((mode & 2) && el) {
-                    const float gD = GA[rf] * bc.w[k][rf];
-                    // a capturing clock pin also carries its endpoint's setup term
-                    st_poll(bs.g_ats + ix(2 * bc.pin[k] + r, Bp, b), (bs.cap_seed && k == 0) ? gD + bc.cs[rf] : gD);
-                    st_poll(bs.g_slew + ix(2 * bc.pin[k] + r, Bp, b),
-                                 fmaf(gD, bc.dDs[k][rf], k == bc.amax[rf] ? GS[rf] * bc.dSs[rf] : 0.f));
-                    gl[c] = fmaf(gD, bc.dDl[k][rf], gl[c]);
-                }
+        for (int c = 0; c < 4; ++c) {
+            const int el = c >> 1, rf = c & 1;
+            const int r = (bc.rfi[rf] >> k) & 1;
+            // strong stores: words that the sinks' tasks poll
+            if (mode & 1) st_poll(bs.rat + ix(4 * pin + 2 * el + r, Bp, b), R[c] - A.at(WArc::kDel + 4 * k + c));
+            if ((mode & 2) && el) {
+                const float gD = GA[rf] * A.at(WArc::kW + 2 * k + rf);
+                // a capturing clock pin also carries its endpoint's setup term
+                st_poll(bs.g_ats + ix(2 * pin + r, Bp, b), (bs.cap_seed && k == 0) ? gD + bc.cs[rf] : gD);
+                st_poll(bs.g_slew + ix(2 * pin + r, Bp, b),
+                        fmaf(gD, A.at(WArc::kDs + 2 * k + rf), k == bc.amax[rf] ? GS[rf] * bc.dSs[rf] : 0.f));
+                gl[c] = fmaf(gD, A.at(WArc::kDl + 2 * k + rf), gl[c]);
             }
         }
     }
@@ -440,10 +473,6 @@ __device__ void wbwd_grad(const DevNet& g, const BatchState& bs, const DfState& 
             bsink_grad(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p), s.gw[0] + s.gw[1], gload);
     }
 }
-
-// 128-thread blocks, 5 per SM (96 registers, small spills in the fused mode): 20
-// warps per SM against 16 with 256-thread blocks at 128 registers; measured 5% faster
-constexpr int kWBlock = 128;
 
 template <int mode>
 __global__ void __launch_bounds__(kWBlock, 5) k_bbwd_w(DevNet g, BatchState bs, DfState d, float gamma) {
