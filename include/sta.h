@@ -146,10 +146,10 @@ typedef struct {
  *   DATAFLOW  one persistent launch per sweep whose tasks wait on the data
  *             words they read, as in STA_SCHED_DATAFLOW; a warp takes a task
  *             for 8 placements x 4 timing conditions.
- *   WIDE      as DATAFLOW, but the backward sweeps take a task for 32
- *             placements per warp, each lane running the four timing
- *             conditions of its placement (more independent memory round trips
- *             per warp); the forward sweep is DATAFLOW's.
+ *   WIDE      as DATAFLOW, but every sweep takes a task for 32 placements
+ *             per warp, each lane running the four timing conditions of its
+ *             placement (more independent memory round trips per warp, the
+ *             task's topology read once for 32 placements).
  * LEVELS, DATAFLOW and WIDE give bit-identical results.
  *   LANES     the placements as independent lanes of the single-placement
  *             dataflow sweeps (STA_SCHED_DATAFLOW): each placement has its own

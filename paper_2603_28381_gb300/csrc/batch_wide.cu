@@ -1,22 +1,24 @@
-// batch_wide.cu -- the batched backward sweeps with a lane per placement.
+// batch_wide.cu -- the batched sweeps with a lane per placement.
 //
 // Same tasks, queue and polled data words as the batched dataflow sweeps of
 // batch.cu, same per-placement layout value[row * Bp + b], but a warp takes a
-// backward task for 32 placements and each lane runs all four timing
-// conditions of its placement (early / late x rise / fall).  A warp task then
-// carries four independent chains of memory round trips per lane instead of
-// one, and its topology loads serve 32 placements instead of 8: the batched
-// backward is bound by each warp's chain of dependent loads, so this raises
-// the memory parallelism per SM.  Queue index q = task * G + group (G = Bp /
-// 32).  (The same mapping for the forward sweep measured slower than
-// batch.cu's: its per-lane code ran at 128 registers and 2 blocks per SM.)
+// task for 32 placements and each lane runs all four timing conditions of its
+// placement (early / late x rise / fall).  A warp task then carries four
+// independent chains of memory round trips per lane instead of one, and its
+// topology loads serve 32 placements instead of 8: the batched sweeps are
+// bound by each warp's chain of dependent loads and by instruction issue, so
+// this raises the memory parallelism per SM and issues fewer instructions per
+// placement.  Queue index q = task * G + group (G = Bp / 32).  The per-arc
+// terms live in a column of shared memory per lane, so the arc loops run
+// rolled; loops unrolled over register arrays copied the cell's lookups for
+// every arc and condition, and the kernels stalled on instruction fetch.
 //
 // Every value is computed with the same operations in the same order as in
-// batch.cu: where the lanes of a quad exchanged values there (the sink wire
-// adjoints of the two late conditions, the quad sums of d loss / d load and
-// of the driver's gradient), one lane now adds the same terms in the same
-// association; with both files compiled without implicit multiply-add
-// contraction the results are bit-identical to the narrow sweeps.
+// batch.cu: where the lanes of a quad exchanged values there (the net load's
+// quad sum, the sink wire adjoints of the two late conditions, the quad sums
+// of d loss / d load and of the driver's gradient), one lane now adds the same
+// terms in the same association; with both files compiled without implicit
+// multiply-add contraction the results are bit-identical to the narrow sweeps.
 #include <algorithm>
 
 #include "batch_common.cuh"
@@ -35,13 +37,367 @@ __device__ __forceinline__ WLane wlane(int gw) {
     return L;
 }
 
-// ---------------------------------------------------------------------------
-// Backward
-// ---------------------------------------------------------------------------
-
 // 128-thread blocks, 5 per SM: 20 warps per SM (with 256-thread blocks at 128
 // registers 16 fitted; measured 5% slower)
 constexpr int kWBlock = 128;
+
+// ---------------------------------------------------------------------------
+// Forward
+// ---------------------------------------------------------------------------
+
+// The driver cell of net n: type, arcs, input pins, which arcs' input pins the
+// sweep writes, unateness (bit k: arc k inverts), the type's slew axis and,
+// once the load is known, the load's table segment and fraction.
+struct WFCell {
+    int t, na, dyn, un;
+    int pin[STA_MAX_ARCS];
+    int jl;
+    float ul;
+    float sidx[6], sinv[6];
+};
+
+__device__ __forceinline__ WFCell wfcell_topo(const DevNet& g, int n) {
+    WFCell f;
+    const int4 q0 = __ldg(g.net_desc + 2 * n), q1 = __ldg(g.net_desc + 2 * n + 1);  // one record
+    f.t = q0.x;
+    f.na = q0.z;
+    f.dyn = q0.w & 15;
+    f.un = q0.w >> 4;
+    f.pin[0] = q1.x;
+    f.pin[1] = q1.y;
+    f.pin[2] = q1.z;
+    f.pin[3] = q1.w;
+    f.jl = 0;
+    f.ul = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) f.sidx[j] = f.sinv[j] = 0.f;
+    return f;
+}
+
+__device__ __forceinline__ void wfcell_lib(const DevNet& g, WFCell& f, float ld) {
+    if (f.t < 0) return;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        f.sidx[j] = __ldg(g.lib_idx + f.t * kLibStride + j);
+        f.sinv[j] = __ldg(g.lib_inv + f.t * kLibStride + j);
+    }
+    const float* li = g.lib_idx + f.t * kLibStride + 8;
+    f.jl = axis_seg(li, ld);
+    f.ul = (ld - __ldg(li + f.jl)) * __ldg(g.lib_inv + f.t * kLibStride + 8 + f.jl);
+}
+
+// The fanin words of every arc for one placement: the input pin's four arrival
+// and slew rows and its two LSE-arrival rows, all loaded together (polled:
+// other warps of this sweep write them).  Returns whether every word written
+// during the sweep holds its value.
+struct WFIn {
+    float a[STA_MAX_ARCS][4], s[STA_MAX_ARCS][4], z[STA_MAX_ARCS][2];
+};
+
+__device__ __forceinline__ bool wfcell_fanin(const BatchState& bs, const WFCell& f, int b, bool lse, bool stall,
+                                             WFIn& in) {
+    const int Bp = bs.Bp;
+    bool ok = !stall;  // the test hook's stalled task never sees its inputs
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) in.a[k][j] = in.s[k][j] = 0.f;
+        in.z[k][0] = in.z[k][1] = 0.f;
+        if (f.t >= 0 && k < f.na) {
+            bool w = true;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                in.a[k][j] = ld_poll(bs.at + ix(4 * f.pin[k] + j, Bp, b));
+                in.s[k][j] = ld_poll(bs.slew + ix(4 * f.pin[k] + j, Bp, b));
+                w &= written(in.a[k][j]) & written(in.s[k][j]);
+            }
+            if (lse) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    in.z[k][r] = ld_poll(bs.ats + ix(2 * f.pin[k] + r, Bp, b));
+                    w &= written(in.z[k][r]);
+                }
+            }
+            if ((f.dyn >> k) & 1) ok &= w;
+        }
+    }
+    return ok;
+}
+
+// Word w of the lane's forward column: [w * kWBlock + threadIdx.x].  Per arc k:
+// the input pin's four arrival rows and four slew rows (row 2 el + r: mode el,
+// input transition r), its two LSE-arrival rows, and the LSE candidates of the
+// two late output transitions.
+struct WFArc {
+    float* f;
+    static constexpr int kAin = 0, kSin = 16, kZin = 32, kCand = 40, kWords = 48;
+    __device__ __forceinline__ float& at(int w) const { return f[w * kWBlock + threadIdx.x]; }
+};
+
+__device__ __forceinline__ WFArc wfarc() {
+    __shared__ float f[WFArc::kWords * kWBlock];
+    WFArc a;
+    a.f = f;
+    return a;
+}
+
+// the wait's later rounds: the same words as wfcell_fanin, loaded straight
+// into the column (no register copy of every word lives across the polls)
+__device__ __forceinline__ bool wfcell_fanin_col(const BatchState& bs, const WFCell& f, int b, bool lse, bool stall,
+                                                 const WFArc& A) {
+    const int Bp = bs.Bp;
+    bool ok = !stall;
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        if (f.t >= 0 && k < f.na) {
+            bool w = true;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float a = ld_poll(bs.at + ix(4 * f.pin[k] + j, Bp, b));
+                const float s = ld_poll(bs.slew + ix(4 * f.pin[k] + j, Bp, b));
+                A.at(WFArc::kAin + 4 * k + j) = a;
+                A.at(WFArc::kSin + 4 * k + j) = s;
+                w &= written(a) & written(s);
+            }
+            if (lse) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float z = ld_poll(bs.ats + ix(2 * f.pin[k] + r, Bp, b));
+                    A.at(WFArc::kZin + 2 * k + r) = z;
+                    w &= written(z);
+                }
+            }
+            if ((f.dyn >> k) & 1) ok &= w;
+        }
+    }
+    return ok;
+}
+
+// the first fanin round into the column (once the round's loads are back)
+__device__ __forceinline__ void wfcell_to_col(const WFCell& f, const WFIn& in) {
+    if (f.t < 0) return;
+    const WFArc A = wfarc();
+#pragma unroll
+    for (int k = 0; k < STA_MAX_ARCS; ++k) {
+        if (k < f.na) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                A.at(WFArc::kAin + 4 * k + j) = in.a[k][j];
+                A.at(WFArc::kSin + 4 * k + j) = in.s[k][j];
+            }
+            A.at(WFArc::kZin + 2 * k) = in.z[k][0];
+            A.at(WFArc::kZin + 2 * k + 1) = in.z[k][1];
+        }
+    }
+}
+
+struct WOut {
+    float at[4], sl[4], z[2];  // by condition c = 2 el + rf; LSE arrival by rf (late)
+};
+
+// The driver cell for the four conditions of one placement (late max / early
+// min over the arcs in arc order, worst slew, Eq. 4 for the late conditions),
+// with the operations and order of batch.cu's fcell_eval, so the results are
+// bit-identical.  `ok` is the first fanin round's result; in the dataflow sweep
+// the wait repeats the round until every lane has all its words.  The arc loop
+// runs rolled over the lane's shared-memory column (unrolled over register
+// arrays, the cell's lookups would be copied for every arc and condition).
+template <bool kPoll>
+__device__ __forceinline__ WOut wfcell_eval(const DevNet& g, const BatchState& bs, const WFCell& f, int dp, int b,
+                                            float gamma, bool lse, int32_t* abort_word, bool stall, bool ok) {
+    const int Bp = bs.Bp;
+    WOut o;
+    if (f.t < 0) {  // asserted driver: constant values set at creation
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            o.at[c] = bs.at[ix(4 * dp + c, Bp, b)];
+            o.sl[c] = bs.slew[ix(4 * dp + c, Bp, b)];
+        }
+        o.z[0] = lse ? bs.ats[ix(2 * dp, Bp, b)] : 0.f;
+        o.z[1] = lse ? bs.ats[ix(2 * dp + 1, Bp, b)] : 0.f;
+        return o;
+    }
+    const WFArc A = wfarc();
+    if constexpr (kPoll) {
+        if (!__all_sync(kFull, ok))
+            poll_words([&]() { return wfcell_fanin_col(bs, f, b, lse, stall, A); }, abort_word);
+    }
+    float m[2] = {-kInf, -kInf};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o.at[c] = o.sl[c] = (c >> 1) ? -kInf : kInf;
+#pragma unroll 1
+    for (int k = 0; k < f.na; ++k) {
+        const int u = (f.un >> k) & 1;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int el = c >> 1, rf = c & 1;
+            const int row = 2 * el + (rf ^ u);  // the input transition of output transition rf
+            int is;
+            float ts;
+            seg_reg(f.sidx, f.sinv, A.at(WFArc::kSin + 4 * k + row), is, ts);
+            float4 dq, sq;
+            cell_corners(g, f.t, k, rf, is, f.jl, dq, sq);
+            const float D = lerp_cell(dq, ts, f.ul);
+            const float S = lerp_cell(sq, ts, f.ul);
+            const float v = A.at(WFArc::kAin + 4 * k + row) + D;
+            o.at[c] = el ? fmaxf(o.at[c], v) : fminf(o.at[c], v);
+            o.sl[c] = el ? fmaxf(o.sl[c], S) : fminf(o.sl[c], S);
+            if (el) {
+                const float cand = (lse ? A.at(WFArc::kZin + 2 * k + (rf ^ u)) : 0.f) + D;
+                A.at(WFArc::kCand + 2 * k + rf) = cand;
+                m[rf] = fmaxf(m[rf], cand);
+            }
+        }
+    }
+    // Eq. 4 over the arcs in arc order (lse_arcs' arithmetic: the terms of
+    // absent arcs it adds are exact zeros)
+    const float inv_g = 1.f / gamma;
+#pragma unroll
+    for (int rf = 0; rf < 2; ++rf) {
+        o.z[rf] = 0.f;
+        if (lse) {
+            float sum = 0.f;
+#pragma unroll 1
+            for (int k = 0; k < f.na; ++k) sum += __expf((A.at(WFArc::kCand + 2 * k + rf) - m[rf]) * inv_g);
+            o.z[rf] = m[rf] + gamma * __logf(f.na > 0 ? sum : 1.f);
+        }
+    }
+    return o;
+}
+
+__device__ __forceinline__ void wstore_pin(const BatchState& bs, int p, int b, const float* at, const float* sl,
+                                           const float* z, bool lse) {
+    const int Bp = bs.Bp;  // strong stores: words that other tasks of the sweep poll
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        st_poll(bs.at + ix(4 * p + c, Bp, b), at[c]);
+        st_poll(bs.slew + ix(4 * p + c, Bp, b), sl[c]);
+    }
+    if (lse) {
+        st_poll(bs.ats + ix(2 * p, Bp, b), z[0]);
+        st_poll(bs.ats + ix(2 * p + 1, Bp, b), z[1]);
+    }
+}
+
+// wire step to the sinks [s0, s1), all four conditions; the positions and
+// capacitances of two sinks are loaded before their stores
+__device__ __forceinline__ void wstore_sinks(const DevNet& g, const BatchState& bs, int s0, int s1, int b, float2 xyd,
+                                             const WOut& o, bool lse) {
+#pragma unroll 1
+    for (int p0 = s0; p0 < s1; p0 += 2) {
+        float2 xy[2];
+        float cap[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int p = min(p0 + u, s1 - 1);
+            xy[u] = bs.xy[ix(p, bs.Bp, b)];
+            cap[u] = __ldg(g.pin_cap + p);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (p0 + u < s1) {
+                const Wire w = wire(g, xy[u], xyd, cap[u]);
+                float at[4], sl[4], z[2];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    at[c] = o.at[c] + w.D;
+                    sl[c] = sqrtf(fmaf(o.sl[c], o.sl[c], w.I * w.I));
+                }
+                z[0] = o.z[0] + w.D;
+                z[1] = o.z[1] + w.D;
+                wstore_pin(bs, p0 + u, b, at, sl, z, lse);
+            }
+        }
+    }
+}
+
+// net load (Eq. 1): four interleaved partial sums over sinks c, c + 4, ...,
+// added as (s0 + s1) + (s2 + s3), then the driver's pin capacitance (batch.cu's
+// quad sum, in one lane); four sinks' loads per round
+__device__ __forceinline__ float wnet_load(const DevNet& g, const BatchState& bs, int dp, int s1, int b, float2 xyd) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int p0 = dp + 1; p0 < s1; p0 += 4) {
+        float2 xy[4];
+        float cap[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = min(p0 + u, s1 - 1);
+            xy[u] = bs.xy[ix(p, bs.Bp, b)];
+            cap[u] = __ldg(g.pin_cap + p);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float dist = fabsf(xy[u].x - xyd.x) + fabsf(xy[u].y - xyd.y);
+            if (p0 + u < s1) acc[u] += fmaf(g.c, dist, cap[u]);
+        }
+    }
+    return __ldg(g.pin_cap + dp) + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+}
+
+// packed small nets; the first fanin round is issued as soon as the cell's
+// record is known, before the net's load and the table segment
+template <bool lse>
+__device__ void wfwd_nets(const DevNet& g, const BatchState& bs, const DfState& d, int n0, int nn, int b,
+                          float gamma, bool stall) {
+    const int Bp = bs.Bp;
+    for (int j = 0; j < nn; ++j) {
+        const int n = n0 + j;
+        const int dp = g.net_ptr[n], e = g.net_ptr[n + 1];
+        WFCell f = wfcell_topo(g, n);
+        WFIn in;
+        const bool ok = wfcell_fanin(bs, f, b, lse, stall, in);
+        const float2 xyd = bs.xy[ix(dp, Bp, b)];
+        const float ld = wnet_load(g, bs, dp, e, b, xyd);
+        bs.load[ix(n, Bp, b)] = ld;
+        wfcell_to_col(f, in);
+        wfcell_lib(g, f, ld);
+        const WOut o = wfcell_eval<true>(g, bs, f, dp, b, gamma, lse, d.abort_word, stall, ok);
+        if (f.t >= 0) wstore_pin(bs, dp, b, o.at, o.sl, o.z, lse);
+        wstore_sinks(g, bs, dp + 1, e, b, xyd, o, lse);
+    }
+}
+
+// chunk of a large net: its load comes from the prologue; every chunk
+// evaluates the driver cell, the first one stores it
+template <bool lse>
+__device__ void wfwd_chunk(const DevNet& g, const BatchState& bs, const DfState& d, int n, int p0, int cnt, int b,
+                           float gamma, bool stall) {
+    const int Bp = bs.Bp;
+    const int dp = g.net_ptr[n];
+    WFCell f = wfcell_topo(g, n);
+    WFIn in;
+    const bool ok = wfcell_fanin(bs, f, b, lse, stall, in);
+    const float2 xyd = bs.xy[ix(dp, Bp, b)];
+    const float ld = bs.load[ix(n, Bp, b)];
+    wfcell_to_col(f, in);
+    wfcell_lib(g, f, ld);
+    const WOut o = wfcell_eval<true>(g, bs, f, dp, b, gamma, lse, d.abort_word, stall, ok);
+    if (f.t >= 0 && p0 == dp + 1) wstore_pin(bs, dp, b, o.at, o.sl, o.z, lse);
+    wstore_sinks(g, bs, p0, p0 + cnt, b, xyd, o, lse);
+}
+
+// 4 blocks per SM (126 registers, no spills): measured faster than 5 (96
+// registers with spills) and than a search of the slew axis per lookup
+template <bool lse>
+__global__ void __launch_bounds__(kWBlock, 4) k_bfwd_w(DevNet g, BatchState bs, DfState d, float gamma,
+                                                       int stall_task) {
+    const int G = bs.G;
+    const int Q = d.TF * G;
+    int q = grab(d.heads + 0);
+    while (q < Q) {
+        const int t = q / G, gw = q - t * G;
+        const WLane L = wlane(gw);
+        const int4 task = d.ftask[t];
+        if (task.y > 0) wfwd_nets<lse>(g, bs, d, task.x, task.y, L.b, gamma, t == stall_task);
+        else wfwd_chunk<lse>(g, bs, d, task.x, task.z, task.w, L.b, gamma, t == stall_task);
+        q = grab(d.heads + 0);  // the next task only once this one is done
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward
+// ---------------------------------------------------------------------------
 
 // The driver cell's backward terms for the four conditions of one placement,
 // all from forward results (as BCell of batch.cu): arc delays of every
@@ -505,6 +861,23 @@ __global__ void __launch_bounds__(kWBlock, 5) k_bbwd_w(DevNet g, BatchState bs, 
 }
 
 }  // namespace
+
+int batch_wide_fwd_max_blocks() {
+    int dev = 0, sms = 0, a = 0, b = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bfwd_w<true>, kWBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bfwd_w<false>, kWBlock, 0);
+    const int per_sm = std::min(a, b);
+    return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+void launch_batch_fwd_wide(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int lse,
+                           int stall_task, cudaStream_t st) {
+    if (d.TF == 0) return;
+    if (lse) launch_coop(k_bfwd_w<true>, grid, kWBlock, 0, st, g, bs, d, gamma, stall_task);
+    else launch_coop(k_bfwd_w<false>, grid, kWBlock, 0, st, g, bs, d, gamma, stall_task);
+}
 
 int batch_wide_max_blocks() {
     int dev = 0, sms = 0, a = 0, b = 0, c = 0;

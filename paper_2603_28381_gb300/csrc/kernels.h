@@ -173,8 +173,11 @@ constexpr size_t kBatchEpBytes = 48;  // one endpoint partial
 constexpr int kPlacePerWarp = 8;       // sweep tasks: 8 placements x 4 conditions per warp
 
 int batch_max_blocks(int fwd);
-// the batched backward sweeps with a lane per placement (batch_wide.cu)
+// the batched sweeps with a lane per placement (batch_wide.cu)
 int batch_wide_max_blocks();
+int batch_wide_fwd_max_blocks();
+void launch_batch_fwd_wide(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int lse,
+                           int stall_task, cudaStream_t st);
 void launch_batch_bwd_wide(const DevNet& g, const BatchState& bs, const DfState& d, int grid, float gamma, int mode,
                            cudaStream_t st);
 // the large nets' sinks in chunks of at most kLoadChunk (k_bload): per chunk an
