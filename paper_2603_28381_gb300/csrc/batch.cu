@@ -630,6 +630,19 @@ struct BSink {
     Wire w;
 };
 
+// An endpoint sink's adjoint seed for output transition rf, from its slacks
+// sr, sf: d loss / d LSE-arrival (the TNS soft-min with the zero term, and the
+// WNS soft-min's share).  Out of line, like batch_wide.cu's: endpoints are a
+// small share of the sinks, and the accurate exponentials inlined in every
+// sink loop crowd the instruction cache.  Same operations, same bits.
+__device__ __noinline__ float bsink_seed(float sr, float sf, int rf, float gamma, float W, float wt, float ww) {
+    const float te = softmin3(sr, sf, gamma);
+    const float sv = rf ? sf : sr;
+    float gv = wt * expf(-(sv - te) / gamma);
+    if (isfinite(W)) gv += ww * expf(-(sv - W) / gamma);
+    return -gv;
+}
+
 template <int mode, bool kPoll>
 __device__ __forceinline__ BSink bsink(const DevNet& g, const BatchState& bs, const DfState& d, int p, const Lane& L,
                                        float2 xyd, float sld, float gamma, const BSeed& sd) {
@@ -665,11 +678,7 @@ __device__ __forceinline__ BSink bsink(const DevNet& g, const BatchState& bs, co
             const float rl = bs.rat[ix(4 * p + 2, Bp, b)], rfl = bs.rat[ix(4 * p + 3, Bp, b)];
             if (isfinite(rl)) {
                 const float sr = rl - bs.ats[ix(2 * p, Bp, b)], sf = rfl - bs.ats[ix(2 * p + 1, Bp, b)];
-                const float te = softmin3(sr, sf, gamma);
-                const float sv = L.rf ? sf : sr;
-                float gv = sd.wt * expf(-(sv - te) / gamma);
-                if (isfinite(sd.W)) gv += sd.ww * expf(-(sv - sd.W) / gamma);
-                ga = -gv;
+                ga = bsink_seed(sr, sf, L.rf, gamma, sd.W, sd.wt, sd.ww);
             }
         }
         const float sl = bs.slew[ix(4 * p + 2 + L.rf, Bp, b)];

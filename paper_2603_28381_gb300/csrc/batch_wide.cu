@@ -569,6 +569,24 @@ struct WSink {
     Wire w;
 };
 
+// The adjoint seeds of an endpoint sink (a sink without a consumer task):
+// d loss / d LSE-arrival of both transitions from its slacks sr, sf (the TNS
+// soft-min with the zero term, and the WNS soft-min's share).  Out of line:
+// endpoints are a small share of the sinks, and the accurate exponentials
+// inlined in every sink loop crowded the instruction cache.
+__device__ __noinline__ float2 wsink_seed(float sr, float sf, float gamma, float W, float wt, float ww) {
+    const float te = softmin3(sr, sf, gamma);
+    float g[2];
+#pragma unroll
+    for (int rf = 0; rf < 2; ++rf) {
+        const float sv = rf ? sf : sr;
+        float gv = wt * expf(-(sv - te) / gamma);
+        if (isfinite(W)) gv += ww * expf(-(sv - W) / gamma);
+        g[rf] = -gv;
+    }
+    return make_float2(g[0], g[1]);
+}
+
 template <int mode, bool kPoll>
 __device__ __forceinline__ WSink wsink(const DevNet& g, const BatchState& bs, const DfState& d, int p, int b,
                                        float2 xyd, const float* sld, float gamma, const BSeed& sd) {
@@ -623,14 +641,9 @@ __device__ __forceinline__ WSink wsink(const DevNet& g, const BatchState& bs, co
             const float rfl = (mode & 1) ? rr[3] : bs.rat[ix(4 * p + 3, Bp, b)];
             if (isfinite(rl)) {
                 const float sr = rl - bs.ats[ix(2 * p, Bp, b)], sf = rfl - bs.ats[ix(2 * p + 1, Bp, b)];
-                const float te = softmin3(sr, sf, gamma);
-#pragma unroll
-                for (int rf = 0; rf < 2; ++rf) {
-                    const float sv = rf ? sf : sr;
-                    float gv = sd.wt * expf(-(sv - te) / gamma);
-                    if (isfinite(sd.W)) gv += sd.ww * expf(-(sv - sd.W) / gamma);
-                    ga[rf] = -gv;
-                }
+                const float2 gg = wsink_seed(sr, sf, gamma, sd.W, sd.wt, sd.ww);
+                ga[0] = gg.x;
+                ga[1] = gg.y;
             }
         }
 #pragma unroll
