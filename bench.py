@@ -26,6 +26,7 @@ gradient); `per_kind_formula` gives every kernel kind's own reads and writes.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -819,7 +820,17 @@ def run_serve(args, emit=True):
         stats0 = srv.stats()
         if mode == "continuous":
             sizes = [srv.netlist_bytes(k) for k in ids]
-        lat, span, merged = play(srv, ids, arrivals)
+        # the client loop is the load generator, not the system measured: no
+        # collector pass of the process's older objects inside it (in the default
+        # line those include the earlier records' netlists)
+        gc.collect()
+        gc.freeze()
+        gc.disable()
+        try:
+            lat, span, merged = play(srv, ids, arrivals)
+        finally:
+            gc.enable()
+            gc.unfreeze()
         st = srv.stats()
         srv.close()
         out[mode] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
