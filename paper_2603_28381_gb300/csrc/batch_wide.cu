@@ -697,16 +697,30 @@ __device__ void wbwd_nets(const DevNet& g, const BatchState& bs, const DfState& 
         wbcell_apply<mode>(bs, bc, b, R, GA, GS, gl);
         if (mode & 2) {
             const float gload = (gl[0] + gl[1]) + (gl[2] + gl[3]);  // early conditions contribute 0
+            // sums over the sinks c, c + 4, ... (batch.cu's quad lanes), four
+            // sinks' loads per round
             float sx[4] = {0.f, 0.f, 0.f, 0.f}, sy[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+            for (int p0 = dp + 1; p0 < e; p0 += 4) {
+                float gw[4], cap[4];
+                float2 xy[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                for (int p = dp + 1 + c; p < e; p += 4) {
-                    const float gw = bs.grad[ix(p, Bp, b)].x;
-                    const float2 gxy = bsink_grad(g, bs.xy[ix(p, Bp, b)], xyd, __ldg(g.pin_cap + p), gw, gload);
-                    bs.grad[ix(p, Bp, b)] = gxy;
-                    sx[c] += gxy.x;
-                    sy[c] += gxy.y;
+                for (int u = 0; u < 4; ++u) {
+                    const int p = min(p0 + u, e - 1);
+                    gw[u] = bs.grad[ix(p, Bp, b)].x;
+                    xy[u] = bs.xy[ix(p, Bp, b)];
+                    cap[u] = __ldg(g.pin_cap + p);
                 }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (p0 + u < e) {
+                        const float2 gxy = bsink_grad(g, xy[u], xyd, cap[u], gw[u], gload);
+                        bs.grad[ix(p0 + u, Bp, b)] = gxy;
+                        sx[u] += gxy.x;
+                        sy[u] += gxy.y;
+                    }
+                }
+            }
             bs.grad[ix(dp, Bp, b)] = make_float2(-((sx[0] + sx[1]) + (sx[2] + sx[3])),
                                                  -((sy[0] + sy[1]) + (sy[2] + sy[3])));
         }
