@@ -115,6 +115,7 @@ struct StaHandle {
     cudaStream_t side = nullptr;    // required-time sweep
     cudaStream_t fork = nullptr;    // the batched sweeps' resets beside the position transpose
     cudaEvent_t ev_fork[2] = {nullptr, nullptr};
+    cudaEvent_t ev_pool = nullptr;  // pooled handle: legacy-stream allocations -> the caller's stream
     // batched dataflow handles: the words the next forward and fused gradient
     // sweeps poll were reset by sta_set_positions (on `fork`, done at ev_fork[1]);
     // a forward without new positions resets them itself
@@ -150,9 +151,10 @@ struct StaHandle {
 
     // device memory from a stream-ordered pool (handles of a server, created and
     // destroyed while other requests run: no device-wide synchronization), else
-    // cudaMalloc.  Pool allocations are made on the legacy stream, which the
-    // creating call synchronizes before any other stream uses them; a pooled
-    // handle is destroyed only once none of its work is in flight.
+    // cudaMalloc.  Pool allocations, uploads and creation-time fills are queued
+    // on the legacy stream; events recorded there order every later call after
+    // them, so creation does not wait for them on the host.  A pooled handle is
+    // destroyed only once none of its work is in flight.
     cudaMemPool_t pool = nullptr;
     cudaError_t dev_malloc(void** q, size_t bytes) {
         return pool ? cudaMallocFromPoolAsync(q, bytes, pool, 0) : cudaMalloc(q, bytes);
@@ -194,8 +196,8 @@ struct StaHandle {
         T* p = nullptr;
         StaStatus st = alloc(p, src.size());
         if (st != STA_OK) return st;
-        // a pooled handle's uploads are queued on the legacy stream, which its
-        // creation synchronizes at the end (page-locked sources: plain DMA)
+        // a pooled handle's uploads are queued on the legacy stream (page-locked
+        // sources: plain DMA, overlapping other requests' work)
         if (!src.empty() && pool)
             CUDA_TRY(cudaMemcpyAsync(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, 0));
         else if (!src.empty())
@@ -203,16 +205,35 @@ struct StaHandle {
         dst = p;
         return STA_OK;
     }
-    StaStatus staging(size_t bytes) {
+    // host-input / host-output staging of at least `bytes`, for work on `st`.
+    // A pooled buffer is allocated on the legacy stream; `st` waits for that
+    // (an event, not a host synchronization: the server's worker thread keeps
+    // dispatching meanwhile).
+    StaStatus staging(size_t bytes, cudaStream_t st) {
         if (bytes <= stage_bytes) return STA_OK;
+        if (stage && pool) {  // the buffer's last use on `st` before it goes back to the pool
+            CUDA_TRY(cudaEventRecord(ev_pool, st));
+            CUDA_TRY(cudaStreamWaitEvent(0, ev_pool, 0));
+        }
         if (stage) dev_free(stage);
         stage = nullptr;
         stage_bytes = 0;
         CUDA_TRY(dev_malloc(&stage, bytes));
-        if (pool) CUDA_TRY(cudaStreamSynchronize(0));  // usable from any stream
+        if (pool) {
+            CUDA_TRY(cudaEventRecord(ev_pool, 0));
+            CUDA_TRY(cudaStreamWaitEvent(st, ev_pool, 0));
+        }
         stage_bytes = bytes;
         return STA_OK;
     }
+    // creation-time copies and fills: a pooled handle queues them on the legacy
+    // stream (ordered after its allocations and uploads; every later call waits
+    // for them through the events recorded there at the end of creation)
+    cudaError_t init_h2d(void* dst, const void* src, size_t n) {
+        return pool ? cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, 0)
+                    : cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+    }
+    cudaError_t init_zero(void* p, size_t n) { return pool ? cudaMemsetAsync(p, 0, n, 0) : cudaMemset(p, 0, n); }
     ~StaHandle() {
         for (auto* gx : {gx_fwd[0], gx_fwd[1], gx_rat, gx_adj, gx_fused})
             if (gx) cudaGraphExecDestroy(gx);
@@ -220,7 +241,7 @@ struct StaHandle {
         if (stage) dev_free(stage);
         if (qscratch) cudaFree(qscratch);
         pinned_release(pinned);
-        for (auto* ev : {ev_at, ev_fwd, ev_bwd, ev_fork[0], ev_fork[1]})
+        for (auto* ev : {ev_at, ev_fwd, ev_bwd, ev_fork[0], ev_fork[1], ev_pool})
             if (ev) cudaEventDestroy(ev);
         for (Prof* pr : {&prof_pos, &prof_fwd, &prof_rat, &prof_adj, &prof_out})
             for (cudaEvent_t e : pr->ev) cudaEventDestroy(e);
@@ -608,7 +629,7 @@ StaStatus init_batch(StaHandle* h) {
         return set_err(STA_ERR_CUDA, "cudaMemset failed");
     // asserted arrival / slew and required-time constraints, the same for every placement
     if (P) {
-        st = h->staging(P * 16);
+        st = h->staging(P * 16, 0);
         if (st != STA_OK) return st;
         float* tmp = static_cast<float*>(h->stage);
         const std::pair<float*, const std::vector<float>*> init[] = {{b.at, &L.at0}, {b.slew, &L.slew0},
@@ -811,6 +832,8 @@ StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDe
         g_err = keep;
         return st;
     };
+    if (pool && cudaEventCreateWithFlags(&h->ev_pool, cudaEventDisableTiming) != cudaSuccess)
+        return fail(set_err(STA_ERR_CUDA, "cudaEventCreate failed"));
     if (!shared) {
         try {
             std::string err;
@@ -995,7 +1018,7 @@ StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDe
         const size_t lb = (cv.bytes + 255) / 256 * 256;
         char* slab = nullptr;
         STEP(h->alloc(slab, lb * (size_t)h->nl));
-        if (cudaMemset(slab, 0, lb * (size_t)h->nl) != cudaSuccess) return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
+        if (h->init_zero(slab, lb * (size_t)h->nl) != cudaSuccess) return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
         s.xy = reinterpret_cast<float2*>(slab + o_xy);
         s.load = reinterpret_cast<float*>(slab + o_load);
         s.wdi = reinterpret_cast<float2*>(slab + o_wdi);
@@ -1027,21 +1050,26 @@ StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDe
         h->active = h->active_next = h->nl;
         if (h->nl > 1) {
             STEP(h->alloc(s.active, 1));
-            if (cudaMemcpy(s.active, &h->nl, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+            // (two fills, not a copy from pageable memory: an asynchronous copy
+            // from pageable memory would first wait for the legacy stream's
+            // uploads; the lane count is at most 64, one little-endian byte)
+            if ((h->pool ? (cudaMemsetAsync(s.active, 0, sizeof(int32_t), 0) != cudaSuccess ||
+                            cudaMemsetAsync(s.active, h->nl, 1, 0) != cudaSuccess)
+                         : cudaMemcpy(s.active, &h->nl, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess))
                 return fail(set_err(STA_ERR_CUDA, "initial state upload failed"));
         }
         // constant state of every lane: asserted AT/slew (and LSE AT = late AT),
         // required-time seeds
         for (int l = 0; l < h->nl; ++l) {
             const DevState sl = lane_state(s, l);
-            if (cudaMemcpy(sl.at, L.at0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
-                cudaMemcpy(sl.slew, L.slew0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
-                cudaMemcpy(sl.rat, L.rat0.data(), P * 16, cudaMemcpyHostToDevice) != cudaSuccess)
+            if (h->init_h2d(sl.at, L.at0.data(), P * 16) != cudaSuccess ||
+                h->init_h2d(sl.slew, L.slew0.data(), P * 16) != cudaSuccess ||
+                h->init_h2d(sl.rat, L.rat0.data(), P * 16) != cudaSuccess)
                 return fail(set_err(STA_ERR_CUDA, "initial state upload failed"));
             launch_init_ats(sl, L.P, 0);
         }
     }
-    if (cudaMemset(d.abort_word, 0, 8) != cudaSuccess || cudaMemset(d.heads, 0, 16) != cudaSuccess)
+    if (h->init_zero(d.abort_word, 8) != cudaSuccess || h->init_zero(d.heads, 16) != cudaSuccess)
         return fail(set_err(STA_ERR_CUDA, "cudaMemset failed"));
 #undef STEP
     if (!(h->pinned = pinned_acquire())) return fail(set_err(STA_ERR_OOM, "cudaMallocHost failed"));
@@ -1086,8 +1114,11 @@ StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDe
             }
         }
     }
-    // (a pooled handle waits for its own work only: the legacy stream it used)
-    ce = pool ? cudaStreamSynchronize(0) : cudaDeviceSynchronize();
+    // A pooled handle (the server's) does not wait for its creation work: its
+    // allocations, uploads and fills are queued on the legacy stream, and the
+    // events recorded there below order every later call after them (each call
+    // waits for ev_fwd / ev_bwd / ev_at before touching the handle's memory).
+    ce = pool ? cudaGetLastError() : cudaDeviceSynchronize();
     if (ce != cudaSuccess) return fail(set_err(STA_ERR_CUDA, std::string("init: ") + cudaGetErrorString(ce)));
     cudaEventRecord(h->ev_at, 0);
     cudaEventRecord(h->ev_fwd, 0);
@@ -1117,7 +1148,7 @@ StaStatus sta_set_positions(StaHandle* h, const float* xy, int on_device, void* 
     if (!h->batch()) h->active = h->active_next;  // lanes: the placements of this and the following calls
     const size_t bytes = (size_t)h->lay.P * 8 * (h->batch() ? h->B : h->active);
     if (!on_device) {
-        StaStatus s2 = h->staging(bytes);
+        StaStatus s2 = h->staging(bytes, st);
         if (s2 != STA_OK) return s2;
         if (bytes) CUDA_TRY(cudaMemcpyAsync(h->stage, xy, bytes, cudaMemcpyHostToDevice, st));
         src = static_cast<const float2*>(h->stage);
@@ -1241,7 +1272,7 @@ StaStatus sta_backward_grad(StaHandle* h, const float* w, int w_on_device, float
         const size_t bytes = (size_t)h->lay.P * 8 * h->B;
         float2* dst = reinterpret_cast<float2*>(grad_xy);
         if (!on_device) {
-            StaStatus s2 = h->staging(bytes);
+            StaStatus s2 = h->staging(bytes, st);
             if (s2 != STA_OK) return s2;
             dst = static_cast<float2*>(h->stage);
         }
@@ -1455,7 +1486,7 @@ StaStatus deliver(StaHandle* h, const float* internal, int k, float* out, int on
     if (!bytes) return STA_OK;
     float* dst = out;
     if (!on_device) {
-        StaStatus s2 = h->staging(bytes);
+        StaStatus s2 = h->staging(bytes, st);
         if (s2 != STA_OK) return s2;
         dst = static_cast<float*>(h->stage);
     }
@@ -1521,7 +1552,7 @@ StaStatus sta_query_pins(StaHandle* h, float* at, float* slew, float* rat, float
         if (bytes) {
             float* dst = slack;
             if (!on_device) {
-                if ((s2 = h->staging(bytes)) != STA_OK) return s2;
+                if ((s2 = h->staging(bytes, st)) != STA_OK) return s2;
                 dst = static_cast<float*>(h->stage);
             }
             for (int l = 0; l < h->active; ++l)
@@ -1545,7 +1576,7 @@ StaStatus sta_query_endpoints(StaHandle* h, float* slack, int on_device, void* s
         const size_t bytes = (size_t)h->lay.E * 8 * h->B;
         float2* dst = reinterpret_cast<float2*>(slack);
         if (!on_device) {
-            StaStatus s2 = h->staging(bytes);
+            StaStatus s2 = h->staging(bytes, st);
             if (s2 != STA_OK) return s2;
             dst = static_cast<float2*>(h->stage);
         }

@@ -86,6 +86,7 @@ struct Rep {
     float* xy_dev = nullptr;    // merged: [M][P][2] positions of the placements in flight
     float* w_host = nullptr;    // merged: pinned [M][2] loss weights of the placements in flight
     bool pooled = false;        // the scratch (and the handle's memory) came from the server's pool
+    cudaEvent_t ready = nullptr;  // pooled: the copy's allocations and uploads (legacy stream) done
 };
 
 struct Net {
@@ -219,6 +220,7 @@ static void release_rep(Rep* r) {
             else cudaFree(p);
         }
     if (r->w_host) cudaFreeHost(r->w_host);
+    if (r->ready) cudaEventDestroy(r->ready);
     delete r;
 }
 
@@ -350,7 +352,11 @@ static Rep* create_rep(StaServer* S, Net* n, std::string& err) {
     if (!dmalloc(&r->grad_dev, M * P1 * 8) || !dmalloc(&r->sum_dev, M * STA_SUM_COUNT * sizeof(double)) ||
         (S->opt.merge > 0 && (!dmalloc(&r->xy_dev, M * P1 * 8) ||
                               cudaMallocHost(&r->w_host, M * 2 * sizeof(float)) != cudaSuccess)) ||
-        (S->pool && cudaStreamSynchronize(0) != cudaSuccess)) {  // (pool: usable from the slots' streams)
+        // pool: the slot stream of the copy's first request waits for this event
+        // (its allocations, uploads and fills on the legacy stream), so the
+        // worker dispatches other requests while the copy loads
+        (S->pool && (cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming) != cudaSuccess ||
+                     cudaEventRecord(r->ready, 0) != cudaSuccess))) {
         err = "cudaMalloc of request scratch failed";
         release_rep(r);
         return nullptr;
@@ -377,12 +383,18 @@ static Rep* create_rep(StaServer* S, Net* n, std::string& err) {
 
 // Queue one request's work on a slot's stream: positions in, forward, gradient
 // if asked, results out; an event marks its end.
+// a pooled copy's requests wait on the device for its loading (legacy stream)
+static StaStatus wait_loaded(const Rep* rp, cudaStream_t st) {
+    return (rp->ready && cudaStreamWaitEvent(st, rp->ready, 0) != cudaSuccess) ? STA_ERR_CUDA : STA_OK;
+}
+
 static StaStatus dispatch(StaServer* S, Slot& sl, Net* n) {
     const StaServerRequest& r = sl.reqs[0].r;
     Rep* rp = sl.rep;
     StaHandle* h = rp->h;
     void* st = sl.st;
-    StaStatus s = sta_set_positions(h, r.xy, 0, st);
+    StaStatus s = wait_loaded(rp, sl.st);
+    if (s == STA_OK) s = sta_set_positions(h, r.xy, 0, st);
     if (s == STA_OK)
         s = sta_forward(h, STA_FWD_LSE | STA_FWD_RAT | (r.gradient ? 0u : STA_FWD_RAT_EAGER), r.gamma, st);
     if (s == STA_OK && r.gradient) {
@@ -413,7 +425,8 @@ static StaStatus dispatch_merged(StaServer* S, Slot& sl, Net* n) {
     Rep* rp = sl.rep;
     cudaStream_t cst = sl.st;
     void* st = sl.st;
-    StaStatus s = sta_set_active(rp->h, k);
+    StaStatus s = wait_loaded(rp, cst);
+    if (s == STA_OK) s = sta_set_active(rp->h, k);
     for (int b = 0; b < k && s == STA_OK && P; ++b)
         if (cudaMemcpyAsync(rp->xy_dev + b * P * 2, sl.reqs[b].r.xy, P * 8, cudaMemcpyHostToDevice, cst) != cudaSuccess)
             s = STA_ERR_CUDA;
