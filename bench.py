@@ -15,7 +15,8 @@ second half as two sub-records, each with its own clock record: `batch` (64
 jittered placements of a ~500k-pin netlist per step, against the same
 placements one per call) and `serve` (a Poisson stream of 2,000 requests over
 ten resident netlists of 20k-3M pins, continuous admission against the plain
-one-request-at-a-time loop); `--no-sub` leaves them out.  `--impl reference`
+one-request-at-a-time loop, measured in a process of its own), and `multi` (64
+small netlists in one handle); `--no-sub` leaves them out.  `--impl reference`
 times the FP64 CPU oracle (the only reference this method has) on the box's
 host cores on the same workload.
 
@@ -549,9 +550,7 @@ def run_ours(args):
             ba = copy.copy(args)
             ba.steps, ba.warmup, ba.scale = min(args.steps, 20), max(3, min(args.warmup, 5)), 1.0
             line["batch"] = run_batch(ba, emit=False)
-            sa = copy.copy(args)
-            sa.scale = 1.0
-            line["serve"] = run_serve(sa, emit=False)
+            line["serve"] = serve_own_process(args)
             ma = copy.copy(args)
             ma.steps, ma.warmup = min(args.steps, 20), max(3, min(args.warmup, 5))
             line["multi"] = run_multi(ma, emit=False)
@@ -734,6 +733,22 @@ def serve_workload(args):
         depth = int(np.clip(30 + 120 * (np.log(p) - lo) / (hi - lo), 30, 150))
         designs.append(netgen.superblue_like(100 + i, scale=float(p / 2.5e6), depth=depth))
     return designs
+
+
+def serve_own_process(args):
+    """The serving record of the default line, measured in a process of its own
+    (a fresh interpreter and CUDA context, as a serving process would have) so
+    that the host state the earlier records leave behind does not time the
+    request loop: `bench.py --workload serve` with the same stream arguments."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", "serve", "--seed", str(args.seed),
+           "--requests", str(args.requests), "--netlists", str(args.netlists), "--load", str(args.load),
+           "--slots", str(args.slots), "--replicas", str(args.replicas), "--merge", str(args.merge)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"serving record failed ({r.returncode}): {r.stderr[-2000:]}")
+    rec = json.loads(r.stdout.strip().splitlines()[-1])
+    rec["process"] = "own process: bench.py --workload serve with the same stream arguments"
+    return rec
 
 
 def run_serve(args, emit=True):
