@@ -1050,12 +1050,13 @@ StaStatus create_handle(std::shared_ptr<const Layout> shared, const StaNetlistDe
         h->active = h->active_next = h->nl;
         if (h->nl > 1) {
             STEP(h->alloc(s.active, 1));
-            // (two fills, not a copy from pageable memory: an asynchronous copy
-            // from pageable memory would first wait for the legacy stream's
-            // uploads; the lane count is at most 64, one little-endian byte)
-            if ((h->pool ? (cudaMemsetAsync(s.active, 0, sizeof(int32_t), 0) != cudaSuccess ||
-                            cudaMemsetAsync(s.active, h->nl, 1, 0) != cudaSuccess)
-                         : cudaMemcpy(s.active, &h->nl, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess))
+            // (pooled and under 256 lanes: two fills, the count as its low,
+            // little-endian byte, instead of a copy from pageable memory, which
+            // would first wait for the legacy stream's uploads)
+            const bool fill = h->pool && h->nl < 256;
+            if ((fill ? (cudaMemsetAsync(s.active, 0, sizeof(int32_t), 0) != cudaSuccess ||
+                         cudaMemsetAsync(s.active, h->nl, 1, 0) != cudaSuccess)
+                      : cudaMemcpy(s.active, &h->nl, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess))
                 return fail(set_err(STA_ERR_CUDA, "initial state upload failed"));
         }
         // constant state of every lane: asserted AT/slew (and LSE AT = late AT),

@@ -363,6 +363,85 @@ __device__ __forceinline__ EpAcc ep_shfl_down(const EpAcc& a, int off) {
 // shuffle tree within each warp (lane i takes lane i + 16, 8, 4, 2, 1), then
 // warp 0 combines the warps' results the same way (one barrier; the
 // shared-memory tree it replaces spent most of its time in eight of them).
+// The first stage in single precision: a thread's endpoints and the warp's
+// shuffle tree (a few dozen terms per partial, so float sums stay within a few
+// ulps), converted to double once per warp.  Double arithmetic runs at a small
+// fraction of the float rate on this part, and 608 blocks each reducing every
+// lane in double kept the endpoint launch busy on it.
+struct EpAccF {
+    float tns_e, tns_l, tns_g, viol;
+    float wns_e, wns_l, wmin, wsum;
+};
+
+__device__ __forceinline__ EpAccF epf_identity() {
+    EpAccF a;
+    a.tns_e = a.tns_l = a.tns_g = a.viol = 0.f;
+    a.wns_e = a.wns_l = a.wmin = kInf;
+    a.wsum = 0.f;
+    return a;
+}
+
+__device__ __forceinline__ void epf_merge(EpAccF& a, const EpAccF& b, float gamma) {
+    a.tns_e += b.tns_e;
+    a.tns_l += b.tns_l;
+    a.tns_g += b.tns_g;
+    a.viol += b.viol;
+    a.wns_e = fminf(a.wns_e, b.wns_e);
+    a.wns_l = fminf(a.wns_l, b.wns_l);
+    const float m = fminf(a.wmin, b.wmin);
+    float sum = 0.f;
+    if (a.wsum > 0.f) sum += a.wsum * expf(-(a.wmin - m) / gamma);
+    if (b.wsum > 0.f) sum += b.wsum * expf(-(b.wmin - m) / gamma);
+    a.wsum = sum;
+    a.wmin = m;
+}
+
+__device__ __forceinline__ EpAccF epf_shfl_down(const EpAccF& a, int off) {
+    EpAccF b;
+    b.tns_e = __shfl_down_sync(kFull, a.tns_e, off);
+    b.tns_l = __shfl_down_sync(kFull, a.tns_l, off);
+    b.tns_g = __shfl_down_sync(kFull, a.tns_g, off);
+    b.viol = __shfl_down_sync(kFull, a.viol, off);
+    b.wns_e = __shfl_down_sync(kFull, a.wns_e, off);
+    b.wns_l = __shfl_down_sync(kFull, a.wns_l, off);
+    b.wmin = __shfl_down_sync(kFull, a.wmin, off);
+    b.wsum = __shfl_down_sync(kFull, a.wsum, off);
+    return b;
+}
+
+// block partial: warp trees in float, then the warps' partials in double
+// (warp 0 holds the block's result)
+__device__ void ep_block_reduce_f(EpAccF a, EpAcc& acc, float gamma) {
+    __shared__ EpAcc shf[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const EpAccF b = epf_shfl_down(a, off);
+        if (lane < off) epf_merge(a, b, gamma);
+    }
+    if (lane == 0) {
+        EpAcc d;
+        d.tns_e = a.tns_e;
+        d.tns_l = a.tns_l;
+        d.tns_g = a.tns_g;
+        d.viol = a.viol;
+        d.wns_e = a.wns_e;
+        d.wns_l = a.wns_l;
+        d.wmin = a.wmin;
+        d.wsum = a.wsum;
+        shf[w] = d;
+    }
+    __syncthreads();
+    if (w == 0) {
+        acc = lane < kWarpsPerBlock ? shf[lane] : ep_identity();
+#pragma unroll
+        for (int off = kWarpsPerBlock / 2; off > 0; off >>= 1) {
+            const EpAcc b = ep_shfl_down(acc, off);
+            if (lane < off) ep_merge(acc, b, gamma);
+        }
+    }
+}
+
 __device__ void ep_block_reduce(EpAcc& acc, float gamma) {
     __shared__ EpAcc sh[kWarpsPerBlock];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -458,7 +537,7 @@ __global__ void __launch_bounds__(kBlock) k_ep(DevNet g, DevState s0, float gamm
         s.ep_count += gi;
     }
     // (relative to the netlist's first endpoint: the same blocks and order as alone)
-    EpAcc acc = ep_identity();
+    EpAccF accf = epf_identity();
     for (int e = e0 + blockIdx.x * kBlock + threadIdx.x; e < e1; e += gridDim.x * kBlock) {
         const int p = g.ep_pin[e];
         float4 con;
@@ -468,12 +547,12 @@ __global__ void __launch_bounds__(kBlock) k_ep(DevNet g, DevState s0, float gamm
         const float se = fminf(at.x - con.x, at.y - con.y);
         const float sl = fminf(con.z - at.z, con.w - at.w);
         s.ep_slack[e] = make_float2(se, sl);
-        EpAcc b = ep_identity();
+        EpAccF b = epf_identity();
         b.wns_e = se;
         b.wns_l = sl;
         b.tns_e = fminf(se, 0.f);
         b.tns_l = fminf(sl, 0.f);
-        b.viol = sl < 0.f ? 1.0 : 0.0;
+        b.viol = sl < 0.f ? 1.f : 0.f;
         if (lse) {
             const float2 z = reinterpret_cast<const float2*>(s.ats)[p];
             const float sr = con.z - z.x, sf = con.w - z.y;
@@ -481,9 +560,10 @@ __global__ void __launch_bounds__(kBlock) k_ep(DevNet g, DevState s0, float gamm
             b.wmin = fminf(sr, sf);
             b.wsum = expf(-(sr - b.wmin) / gamma) + expf(-(sf - b.wmin) / gamma);
         }
-        ep_merge(acc, b, gamma);
+        epf_merge(accf, b, gamma);
     }
-    ep_block_reduce(acc, gamma);
+    EpAcc acc = ep_identity();
+    ep_block_reduce_f(accf, acc, gamma);
     __shared__ int last;
     if (threadIdx.x == 0) {
         reinterpret_cast<EpAcc*>(s.red)[blockIdx.x] = acc;
