@@ -427,13 +427,44 @@ __global__ void __launch_bounds__(kBlock) k_bcap_seed(DevNet g, BatchState bs, f
     bs.cap_seed[ix(k, Bp, b)] = gr + gf;
 }
 
+// A lane's own endpoints are summed in float (a handful per lane, so the sums
+// stay within a few ulps), then the lanes' partials in double: double
+// arithmetic runs at a small fraction of the float rate on this part.
+struct BEpF {
+    float tns_e, tns_l, tns_g, viol;
+    float wns_e, wns_l, wmin, wsum;
+};
+
+__device__ __forceinline__ BEpF bepf_identity() {
+    BEpF a;
+    a.tns_e = a.tns_l = a.tns_g = a.viol = 0.f;
+    a.wns_e = a.wns_l = a.wmin = kInf;
+    a.wsum = 0.f;
+    return a;
+}
+
+__device__ __forceinline__ void bepf_merge(BEpF& a, const BEpF& b, float gamma) {
+    a.tns_e += b.tns_e;
+    a.tns_l += b.tns_l;
+    a.tns_g += b.tns_g;
+    a.viol += b.viol;
+    a.wns_e = fminf(a.wns_e, b.wns_e);
+    a.wns_l = fminf(a.wns_l, b.wns_l);
+    const float m = fminf(a.wmin, b.wmin);
+    float sum = 0.f;
+    if (a.wsum > 0.f) sum += a.wsum * expf(-(a.wmin - m) / gamma);
+    if (b.wsum > 0.f) sum += b.wsum * expf(-(b.wmin - m) / gamma);
+    a.wsum = sum;
+    a.wmin = m;
+}
+
 // grid (kRedBlocks, G): block x takes endpoints x*8 + w, stepping by
 // kRedBlocks*8; partial per (block, placement)
 __global__ void __launch_bounds__(kBlock) k_bep1(DevNet g, BatchState bs, float gamma, int lse) {
     __shared__ BEp sh[kWarpsPerBlock][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int b = blockIdx.y * 32 + lane, Bp = bs.Bp;
-    BEp acc = bep_identity();
+    BEpF accf = bepf_identity();
     for (int e = blockIdx.x * kWarpsPerBlock + w; e < g.E; e += gridDim.x * kWarpsPerBlock) {
         const int p = g.ep_pin[e];
         float4 con;
@@ -449,20 +480,29 @@ __global__ void __launch_bounds__(kBlock) k_bep1(DevNet g, BatchState bs, float 
         const float se = fminf(a0 - con.x, a1 - con.y);
         const float sl = fminf(con.z - a2, con.w - a3);
         bs.ep_slack[ix(e, Bp, b)] = make_float2(se, sl);
-        BEp v = bep_identity();
+        BEpF v = bepf_identity();
         v.wns_e = se;
         v.wns_l = sl;
         v.tns_e = fminf(se, 0.f);
         v.tns_l = fminf(sl, 0.f);
-        v.viol = sl < 0.f ? 1.0 : 0.0;
+        v.viol = sl < 0.f ? 1.f : 0.f;
         if (lse) {
             const float sr = con.z - bs.ats[ix(2 * p, Bp, b)], sf = con.w - bs.ats[ix(2 * p + 1, Bp, b)];
             v.tns_g = softmin3(sr, sf, gamma);
             v.wmin = fminf(sr, sf);
             v.wsum = expf(-(sr - v.wmin) / gamma) + expf(-(sf - v.wmin) / gamma);
         }
-        bep_merge(acc, v, gamma);
+        bepf_merge(accf, v, gamma);
     }
+    BEp acc;
+    acc.tns_e = accf.tns_e;
+    acc.tns_l = accf.tns_l;
+    acc.tns_g = accf.tns_g;
+    acc.viol = accf.viol;
+    acc.wns_e = accf.wns_e;
+    acc.wns_l = accf.wns_l;
+    acc.wmin = accf.wmin;
+    acc.wsum = accf.wsum;
     sh[w][lane] = acc;
     __syncthreads();
     if (w == 0) {
