@@ -737,9 +737,9 @@ def serve_workload(args):
 
 def serve_own_process(args):
     """The serving record of the default line, measured in a process of its own
-    (a fresh interpreter and CUDA context, as a serving process would have) so
-    that the host state the earlier records leave behind does not time the
-    request loop: `bench.py --workload serve` with the same stream arguments."""
+    (a fresh interpreter and CUDA context, as a serving process would have, with
+    none of the earlier records' objects): `bench.py --workload serve` with the
+    same stream arguments."""
     cmd = [sys.executable, os.path.abspath(__file__), "--workload", "serve", "--seed", str(args.seed),
            "--requests", str(args.requests), "--netlists", str(args.netlists), "--load", str(args.load),
            "--slots", str(args.slots), "--replicas", str(args.replicas), "--merge", str(args.merge)]
