@@ -794,7 +794,16 @@ def run_serve(args, emit=True):
                 t_last = max(t_last, c["t_done"])
                 done += 1
             if i < R and wait == 0:
-                time.sleep(max(0.0, min(0.0005, t0 + arrivals[i] - StaServer.clock())))
+                # until the next arrival: a short sleep while it is more than a
+                # millisecond away, then a spin on the clock (a late wake-up of the
+                # load generator would count as latency; completions carry the
+                # server's own stamps, so polling them later changes nothing)
+                dt = t0 + arrivals[i] - StaServer.clock()
+                if dt > 1e-3:
+                    time.sleep(min(dt - 8e-4, 5e-4))
+                else:
+                    while StaServer.clock() < t0 + arrivals[i]:
+                        pass
         span = t_last - t0
         return lat, span, merged
 
