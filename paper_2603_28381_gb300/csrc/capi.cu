@@ -106,6 +106,12 @@ struct StaHandle {
     size_t dev_bytes = 0;
     int device = 0;
     bool use_graphs = true;
+    // forward calls begun.  A pooled handle (a server's resident copy, often
+    // evicted after a request or two) launches directly on its first request and
+    // captures its graphs from the second on: a capture and instantiation costs
+    // the server's worker thread more than one request's direct launches.
+    long long nforward = 0;
+    bool graphs_now() const { return use_graphs && (!pool || nforward >= 2); }
     bool have_pos = false, have_fwd = false, have_lse = false, have_rat = false;
     float gamma_fwd = 1.f;
     cudaEvent_t ev_at = nullptr;    // arrival-time pass of the latest forward done
@@ -544,7 +550,7 @@ StaStatus sync_checked(StaHandle* h, cudaStream_t st) {
 // gamma changes) or as direct launches.
 StaStatus launch_graph_or_direct(StaHandle* h, cudaGraphExec_t* gx, float* key, float gamma, int mode,
                                  cudaStream_t st) {
-    if (h->use_graphs) {
+    if (h->graphs_now()) {
         if (!*gx || *key != gamma) {
             StaStatus s2 = capture(h, gx, [&](cudaStream_t c) { enqueue_backward(h, mode, gamma, c); });
             if (s2 != STA_OK) return s2;
@@ -1181,6 +1187,7 @@ StaStatus sta_forward(StaHandle* h, uint32_t flags, float gamma, void* stream) {
     const int lse = (flags & STA_FWD_LSE) ? 1 : 0;
     if (lse && !(std::isfinite(gamma) && gamma > 0.f)) return set_err(STA_ERR_INVALID_ARG, "gamma must be > 0");
     if (!lse) gamma = 1.f;
+    ++h->nforward;
     cudaStream_t st = as_stream(stream);
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_bwd, 0));
     CUDA_TRY(cudaStreamWaitEvent(st, h->ev_fwd, 0));
@@ -1201,7 +1208,7 @@ StaStatus sta_forward(StaHandle* h, uint32_t flags, float gamma, void* stream) {
         h->stall_task = -1;
         StaStatus s2 = check_launch();
         if (s2 != STA_OK) return s2;
-    } else if (h->use_graphs) {
+    } else if (h->graphs_now()) {
         if (!h->gx_fwd[lse] || h->gx_fwd_gamma[lse] != gamma) {
             StaStatus s2 = capture(h, &h->gx_fwd[lse], [&](cudaStream_t c) { enqueue_forward(h, lse, gamma, c); });
             if (s2 != STA_OK) return s2;

@@ -24,6 +24,8 @@
 // chunks, one driver task that combines them in a fixed order, and gradient
 // chunks (which wait on a counter the driver task releases), so every
 // reduction stays deterministic.
+#include <mutex>
+
 #include "dataflow_sync.cuh"
 #include "device_common.cuh"
 
@@ -1018,7 +1020,31 @@ __global__ void __launch_bounds__(kBlock, 3) k_bwd_df(DevNet g, DevState s, DfSt
 // Co-resident blocks of a sweep: the smallest count over every variant the
 // sweep may launch (they share one grid size).  Also grants the forward kernels
 // their dynamic shared memory (above the default 48 KB), once per device.
+// (the result depends on the device and the kernels only: it is computed once
+// per device and variant, since a server creates handles at request rate)
+static int dataflow_max_blocks_query(int fwd, int lanes);
+
 int dataflow_max_blocks(int fwd, int lanes) {
+    constexpr int kDevs = 64;
+    static std::mutex mu;
+    static int cache[kDevs][2][2] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int f = fwd ? 1 : 0, l = lanes ? 1 : 0;
+    if (dev < 0 || dev >= kDevs) return dataflow_max_blocks_query(fwd, lanes);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (cache[dev][f][l] > 0) return cache[dev][f][l];
+    }
+    const int v = dataflow_max_blocks_query(fwd, lanes);
+    if (cudaPeekAtLastError() == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[dev][f][l] = v;
+    }
+    return v;
+}
+
+static int dataflow_max_blocks_query(int fwd, int lanes) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
